@@ -1,0 +1,352 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: hand-derived
+entries of the difference operators, closed forms, invariants, a textbook
+update (MLEM), an independent minimiser (L-BFGS-B) and finite differences.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+
+from oracle import appga_oracle as O
+from paper_2409_13344_gb300 import workload as W
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _read_matrix(name):
+    rows = []
+    with open(f"{GOLDEN}/{name}") as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+# ---------------------------------------------------------------- operators
+
+def test_difference_matrix_matches_definition_n4():
+    # Sec. 2.1: D_jj = 1, D_j,j-1 = -1 for j = 2..N, all else 0 (row 1 zero).
+    D = O.difference_matrix(4).toarray()
+    np.testing.assert_array_equal(D, _read_matrix("difference_matrix_n4.txt"))
+
+
+def _stencil_by_loops(F):
+    """The six difference fields written out pixel by pixel from the
+    definition of D (row 1 zero) applied along columns (c) and rows (r)."""
+    n = F.shape[0]
+
+    def D_apply(x):  # (D x)_i = x_i - x_{i-1} for i >= 1, 0 for i = 0
+        return [0.0] + [x[i] - x[i - 1] for i in range(1, n)]
+
+    def Dt_apply(y):  # (D^T y)_i = sum_k D_ki y_k
+        out = []
+        for i in range(n):
+            v = 0.0
+            if i >= 1:
+                v += y[i]          # D_ii = 1 for i >= 1
+            if i + 1 <= n - 1:
+                v -= y[i + 1]      # D_{i+1,i} = -1
+            out.append(v)
+        return out
+
+    def along_c(G, op):
+        return np.array([op(list(G[r, :])) for r in range(n)])
+
+    def along_r(G, op):
+        return np.array([op(list(G[:, c])) for c in range(n)]).T
+
+    neg = lambda op: (lambda x: [-v for v in op(x)])
+    mDtD = lambda x: [-v for v in Dt_apply(D_apply(x))]
+    u1 = along_c(F, D_apply)
+    u2 = along_r(F, D_apply)
+    u3 = along_c(F, mDtD)
+    u4 = along_r(along_c(F, D_apply), neg(Dt_apply))
+    u5 = along_r(F, mDtD)
+    u6 = along_r(along_c(F, neg(Dt_apply)), D_apply)
+    return [u.reshape(-1) for u in (u1, u2, u3, u4, u5, u6)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_b_blocks_match_pixelwise_definition(n):
+    rng = np.random.default_rng(n)
+    F = rng.standard_normal((n, n))
+    u = O.b_matrix(n) @ F.reshape(-1)
+    d = n * n
+    ref = _stencil_by_loops(F)
+    for blk in range(6):
+        np.testing.assert_allclose(u[blk * d:(blk + 1) * d], ref[blk], rtol=0, atol=1e-12)
+
+
+def test_b_constant_image_is_zero():
+    u = O.b_matrix(7) @ np.full(49, 3.25)
+    assert np.max(np.abs(u)) == 0.0
+
+
+def test_b_ramp_special_case():
+    # F[r][c] = c: hand-derived from the definition of D.
+    n = 6
+    F = np.tile(np.arange(n, dtype=float), (n, 1))
+    u = (O.b_matrix(n) @ F.reshape(-1)).reshape(6, n, n)
+    c = np.arange(n)
+    np.testing.assert_array_equal(u[0], np.tile((c >= 1).astype(float), (n, 1)))  # I(x)D
+    assert np.all(u[1] == 0)                                                     # D(x)I
+    exp3 = np.zeros((n, n)); exp3[:, 0] = 1.0; exp3[:, -1] = -1.0                 # I(x)(-D^T D)
+    np.testing.assert_array_equal(u[2], exp3)
+    exp4 = np.zeros((n, n)); exp4[0, 1:] = 1.0; exp4[-1, 1:] = -1.0               # (-D^T)(x)D
+    np.testing.assert_array_equal(u[3], exp4)
+    assert np.all(u[4] == 0)                                                     # (-D^T D)(x)I
+    assert np.all(u[5] == 0)                                                     # D(x)(-D^T)
+
+
+def test_regulariser_transpose_invariant():
+    # Under F -> F^T the pair (u1,u2) swaps and B2's blocks swap (3<->5, 4<->6).
+    n = 9
+    rng = np.random.default_rng(3)
+    F = rng.uniform(0, 2, (n, n))
+    B = O.b_matrix(n)
+    a = O.phi_tilde(B @ F.reshape(-1), n * n, 0.3, 0.7, 0.05)
+    b = O.phi_tilde(B @ F.T.reshape(-1), n * n, 0.3, 0.7, 0.05)
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_b_operator_norm_bounds():
+    # ||B1||^2 <= 8 and ||B2||^2 <= 64 (the bounds behind rho1, rho2 of Sec. 4.3).
+    n = 10
+    s1 = np.linalg.norm(O.b1_matrix(n).toarray(), 2) ** 2
+    s2 = np.linalg.norm(O.b2_matrix(n).toarray(), 2) ** 2
+    assert s1 <= 8.0 + 1e-9 and s2 <= 64.0 + 1e-9
+    assert s1 > 7.0 and s2 > 50.0
+
+
+# ------------------------------------------------------- smoothed l2 norm
+
+def test_s_eps_branches_and_continuity():
+    eps = 0.2
+    x_out = np.array([[0.0, 0.4]])   # ||x|| = 2 eps -> ||x|| - eps/2 = 0.3
+    x_in = np.array([[0.06, 0.08]])  # ||x|| = 0.1 -> 0.1^2 / (2 eps) = 0.025
+    assert O.s_eps(x_out, eps)[0] == pytest.approx(0.3, abs=1e-15)
+    assert O.s_eps(x_in, eps)[0] == pytest.approx(0.025, abs=1e-15)
+    edge = np.array([[0.12, 0.16]])  # ||x|| = eps exactly: both branches give eps/2
+    assert O.s_eps(edge, eps)[0] == pytest.approx(eps / 2, abs=1e-15)
+    for xx in (x_out, x_in, edge, np.array([[0.3, -0.1, 0.05, 0.2]])):
+        g = O.grad_s_eps(xx, eps)[0]
+        h = 1e-7
+        fd = [(O.s_eps(xx + h * e, eps)[0] - O.s_eps(xx - h * e, eps)[0]) / (2 * h)
+              for e in np.eye(xx.shape[1])]
+        np.testing.assert_allclose(g, fd, atol=1e-7)
+
+
+def test_s_eps_tends_to_norm():
+    x = np.array([[0.3, -0.4]])
+    for eps in (1e-2, 1e-4, 1e-6):
+        assert abs(O.s_eps(x, eps)[0] - 0.5) <= eps / 2 + 1e-15
+
+
+# ------------------------------------------------------------- momentum
+
+@pytest.mark.parametrize("k", list(range(1, 40)))
+def test_gn_theta_closed_forms(k):
+    # a = 1/8, b = 1 (Sec. 4.1): omega = 1 -> (k-1)/(k+8); omega = 1/2 -> sqrt(k-1)/(sqrt(k)+8)
+    th1 = O.gn_theta(k, 0.125, 1.0, 1.0)
+    assert th1 == pytest.approx(float(Fraction(k - 1, k + 8)), abs=1e-15)
+    th2 = O.gn_theta(k, 0.125, 1.0, 0.5)
+    assert th2 == pytest.approx(math.sqrt(k - 1) / (math.sqrt(k) + 8), abs=1e-15)
+    assert 0.0 <= th2 < 1.0 and 0.0 <= th1 < 1.0
+
+
+def test_gn_momentum_condition_and_limit():
+    # Lemma (t_k = a k^w + b satisfies the Momentum-Condition): t_k (t_k - 1) <= t_{k-1}^2
+    # eventually, and theta_k -> 1.
+    for omega in (0.25, 0.5, 0.75, 1.0):
+        ts = [O.gn_t(k, 0.125, 1.0, omega) for k in range(0, 4000)]
+        ok = [ts[k] * (ts[k] - 1) <= ts[k - 1] ** 2 for k in range(1, 4000)]
+        assert all(ok[100:])
+    assert O.gn_theta(10 ** 8, 0.125, 1.0, 1.0) > 0.999999
+
+
+def test_nesterov_thetas():
+    th = O.nesterov_thetas(50)
+    assert th[0] == 0.0                                         # t_0 = 1
+    phi = (1 + math.sqrt(5)) / 2                                # t_1 = golden ratio
+    t2 = (1 + math.sqrt(1 + 4 * phi * phi)) / 2
+    assert th[1] == pytest.approx((phi - 1) / t2, abs=1e-15)
+    assert th[49] == pytest.approx(49 / 52, abs=0.01)           # ~ (k-1)/(k+2)
+
+
+# ------------------------------------------------------ fidelity / phi
+
+def _small_problem(n=8, m=96, seed=5):
+    A, f, g, gamma = W.dense_problem(n, m, seed)
+    return O.Problem(A, g, gamma, n), f
+
+
+def test_fidelity_gradient_fd():
+    prob, f = _small_problem()
+    gr = prob.grad_phi(f, 0.05, 0.02, 0.01)
+    h = 1e-6
+    for j in range(0, prob.d, 7):
+        e = np.zeros(prob.d); e[j] = h
+        fd = (prob.phi(f + e, 0.05, 0.02, 0.01) - prob.phi(f - e, 0.05, 0.02, 0.01)) / (2 * h)
+        assert gr[j] == pytest.approx(fd, rel=1e-6, abs=1e-6)
+
+
+def test_phi_directional_fd_on_siddon_geometry():
+    A = W.system_matrix("64")
+    geom = W.GEOMETRIES["64"]
+    sl = W.make_slice(A, geom, 1e5, W.seed_for(1))
+    prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+    rng = np.random.default_rng(0)
+    f = sl.f_true + 0.05 * rng.uniform(0, 1, prob.d) * sl.f_true.max()
+    gr = prob.grad_phi(f, 0.1, 0.05, 1e-3)
+    for _ in range(3):
+        v = rng.standard_normal(prob.d)
+        h = 1e-6 * np.linalg.norm(f) / np.linalg.norm(v)
+        fd = (prob.phi(f + h * v, 0.1, 0.05, 1e-3) - prob.phi(f - h * v, 0.1, 0.05, 1e-3)) / (2 * h)
+        assert float(gr @ v) == pytest.approx(fd, rel=2e-5)
+
+
+def test_objective_is_infinite_off_orthant():
+    prob, f = _small_problem()
+    f2 = f.copy(); f2[3] = -1e-9
+    assert prob.objective(f2, 0.1, 0.1, 0.01) == math.inf
+
+
+# ------------------------------------------------------------- MLEM
+
+def test_unregularised_momentum_free_step_is_mlem():
+    A = W.system_matrix("64")
+    geom = W.GEOMETRIES["64"]
+    sl = W.make_slice(A, geom, 1e5, W.seed_for(1))
+    prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+    f = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    p = O.Params(lambda1=0.0, lambda2=0.0, beta=1.0, momentum="none", max_iters=3)
+    res = O.appga(prob, p, f_init=f, track_phi=False)
+    ref = f.copy()
+    for _ in range(3):
+        ref = O.mlem_step(prob, ref)
+    assert np.max(np.abs(res.f - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_mlem_count_identity():
+    # For the EM step: sum_i (A f+)_i = sum_i g_i y_i / (y_i + gamma_i), y = A f.
+    A = W.system_matrix("64")
+    geom = W.GEOMETRIES["64"]
+    sl = W.make_slice(A, geom, 1e5, W.seed_for(1))
+    prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+    f = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    p = O.Params(lambda1=0.0, lambda2=0.0, beta=1.0, momentum="none", max_iters=1)
+    f1 = O.appga(prob, p, f_init=f, track_phi=False).f
+    y = prob.A @ f
+    lhs = float(np.sum(prob.A @ f1))
+    rhs = float(np.sum(prob.g * y / (y + prob.gamma)))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+# ---------------------------------------------------- initial image
+
+def test_disk_mask_small():
+    # N = 4: centres at +-0.5, +-1.5; x^2+y^2 <= 4 keeps all but the 4 corners.
+    m = O.disk_mask(4).reshape(4, 4)
+    exp = np.ones((4, 4), bool); exp[0, 0] = exp[0, 3] = exp[3, 0] = exp[3, 3] = False
+    np.testing.assert_array_equal(m, exp)
+
+
+def test_initial_image_tmc():
+    g = np.array([10.0, 20.0, 30.0]); gamma = np.array([1.0, 2.0, 3.0])
+    f = O.initial_image(g, gamma, 4, n_angles=3)
+    # ACTc = 60 - 6 = 54; NPFOV = 12; NPA = 3 -> TMC = 1.5
+    np.testing.assert_array_equal(f.reshape(4, 4)[1], [1.5, 1.5, 1.5, 1.5])
+    assert f.reshape(4, 4)[0, 0] == 0.0
+
+
+# ------------------------------------------------------------ guard
+
+def test_guarded_ratio_hand_case():
+    # N = 1 (B = 0), A = [[2]], gamma = 1, g = 3; f^k = 1, f^{k-1} = 4, theta = 1:
+    # f~ = 1 + (1 - 4) = -2, A f~ + gamma = -3 < 1e-3 -> den = 1e-3, one hit.
+    prob = O.Problem(np.array([[2.0]]), np.array([3.0]), np.array([1.0]), 1)
+    lam = prob.em_lambda()  # [2]
+    p = O.Params(lambda1=0.0, lambda2=0.0, beta=0.5)
+    f_next, hits = O.appga_step(prob, np.array([1.0]), np.array([4.0]), 1.0, p, lam)
+    grad = 2.0 * (1.0 - 3.0 / 1e-3)
+    assert hits == 1
+    assert f_next[0] == pytest.approx(max(-2.0 - 0.5 * 1.0 / 2.0 * grad, 0.0), rel=1e-15)
+
+
+# ---------------------------------------------------- fixed point / KKT
+
+def _kkt_setup():
+    A, f_true, g, gamma = W.dense_problem(8, 96, seed=11)
+    prob = O.Problem(A, g, gamma, 8)
+    lam1, lam2, eps = 0.05, 0.02, 0.05
+    return prob, lam1, lam2, eps
+
+
+def _lbfgsb(prob, lam1, lam2, eps):
+    x0 = np.full(prob.d, float(np.sum(prob.g)) / float(np.sum(prob.A.toarray())))
+    res = so.minimize(lambda x: prob.phi(x, lam1, lam2, eps), x0,
+                      jac=lambda x: prob.grad_phi(x, lam1, lam2, eps),
+                      method="L-BFGS-B", bounds=[(0, None)] * prob.d,
+                      options=dict(maxiter=20000, ftol=1e-15, gtol=1e-12, maxcor=30))
+    return res.x
+
+
+def test_appga_reaches_lbfgsb_minimiser_and_kkt():
+    prob, lam1, lam2, eps = _kkt_setup()
+    L = O.lipschitz_bound(prob, lam1, lam2, eps)
+    lam = prob.em_lambda()
+    p_fixed = (1.0 / L) * np.ones(prob.d)  # p_max <= 1/L_phi (Thm. 10)
+    x0 = np.full(prob.d, float(np.sum(prob.g)) / float(np.sum(prob.A.toarray())))
+    par = O.Params(lambda1=lam1, lambda2=lam2, eps=eps, omega=1.0, max_iters=20000)
+    res = O.appga(prob, par, f_init=x0, p_fixed=p_fixed, track_phi=False)
+    f_star = _lbfgsb(prob, lam1, lam2, eps)
+    phi_a = prob.phi(res.f, lam1, lam2, eps)
+    phi_b = prob.phi(f_star, lam1, lam2, eps)
+    assert phi_a <= phi_b + 1e-9 * abs(phi_b)
+    assert np.linalg.norm(res.f - f_star) <= 1e-5 * np.linalg.norm(f_star)
+    # KKT of min phi + iota (Prop. 1): f >= 0, grad >= 0, f * grad = 0
+    gr = prob.grad_phi(res.f, lam1, lam2, eps)
+    scale = np.max(np.abs(prob.grad_fidelity(x0)))
+    assert np.all(res.f >= 0)
+    assert np.min(gr) >= -1e-6 * scale
+    assert np.max(np.abs(res.f * gr)) <= 1e-6 * scale * np.max(res.f)
+    # fixed point of T (Prop. 1): one momentum-free map leaves f* in place
+    f_fp, _ = O.appga_step(prob, res.f, res.f, 0.0, par, lam, p_fixed)
+    assert np.linalg.norm(f_fp - res.f) <= 1e-7 * np.linalg.norm(res.f)
+
+
+def test_rate_and_omega_ordering():
+    # Thm. 10: k^{2w} (Phi(f^k) - Phi*) -> 0 (checked for w = 1, where the
+    # transient is short); larger omega converges faster (Sec. 4.2).
+    prob, lam1, lam2, eps = _kkt_setup()
+    L = O.lipschitz_bound(prob, lam1, lam2, eps)
+    p_fixed = (1.0 / L) * np.ones(prob.d)
+    x0 = np.full(prob.d, float(np.sum(prob.g)) / float(np.sum(prob.A.toarray())))
+    phi_star = prob.phi(_lbfgsb(prob, lam1, lam2, eps), lam1, lam2, eps)
+    gaps = {}
+    for omega, iters in ((0.25, 800), (0.5, 800), (1.0, 3000)):
+        par = O.Params(lambda1=lam1, lambda2=lam2, eps=eps, omega=omega, max_iters=iters)
+        res = O.appga(prob, par, f_init=x0, p_fixed=p_fixed, track_phi=True)
+        gaps[omega] = np.array(res.phi) - phi_star
+    eta = gaps[1.0]
+    k = np.arange(1, len(eta) + 1)
+    scaled = k ** 2 * np.maximum(eta, 0)
+    assert scaled[-1] < 1e-2 * scaled.max()
+    for kk in (100, 300, 800):
+        assert gaps[1.0][kk] < gaps[0.5][kk] < gaps[0.25][kk]
+
+
+def test_ppga_is_monotone_with_small_fixed_step():
+    # With theta = 0 and p_max <= 1/L, Lemma 5 gives Phi(T f) <= Phi(f).
+    prob, lam1, lam2, eps = _kkt_setup()
+    L = O.lipschitz_bound(prob, lam1, lam2, eps)
+    x0 = np.full(prob.d, float(np.sum(prob.g)) / float(np.sum(prob.A.toarray())))
+    par = O.Params(lambda1=lam1, lambda2=lam2, eps=eps, momentum="none", max_iters=200)
+    res = O.appga(prob, par, f_init=x0, p_fixed=np.full(prob.d, 1.0 / L))
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(res.phi, res.phi[1:]))

@@ -1,0 +1,71 @@
+"""Pins of the seeded input generator (not the method): ray sums equal the
+closed-form chord length of each ray through the image square, the CSR is
+canonical, and the draws are reproducible from the seed."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2409_13344_gb300 import workload as W
+
+
+@pytest.mark.parametrize("name", ["64", "128"])
+def test_row_sums_equal_chord_length(name):
+    g = W.GEOMETRIES[name]
+    A = W.system_matrix(name)
+    s = np.arange(g.n_bins) - (g.n_bins - 1) / 2.0
+    h = g.n / 2.0
+    sums = np.asarray(A.astype(np.float64).sum(axis=1)).ravel()
+    for a in range(g.n_angles):
+        phi = a * math.pi / g.n_angles
+        ref = W.chord_length(g.n, phi, s)
+        got = sums[a * g.n_bins:(a + 1) * g.n_bins]
+        # rays lying exactly on the square's edge are a convention (half-open): skip
+        ok = ~np.isclose(np.abs(s), h)
+        np.testing.assert_allclose(got[ok], ref[ok], rtol=0, atol=2e-4 * g.n)
+
+
+def test_csr_is_canonical_and_sized():
+    A = W.system_matrix("64")
+    assert A.dtype == np.float32 and A.indices.dtype == np.int32
+    assert A.has_sorted_indices
+    assert np.all(A.data > 0)
+    assert A.shape == (90 * 95, 64 * 64)
+    # nnz of the 64^2 geometry (exact pixel-crossing count)
+    assert abs(A.nnz - 469_640) < 2_000
+    rl = np.diff(A.indptr)
+    assert rl.max() <= 2 * 64
+    assert 0.05 < np.mean(rl == 0) < 0.2   # rays missing the square
+
+
+def test_every_pixel_is_seen_at_every_angle():
+    g = W.GEOMETRIES["64"]
+    A = W.system_matrix("64").tocsc()
+    rows = A.indices // g.n_bins
+    for j in range(0, g.d, 97):
+        seen = np.unique(rows[A.indptr[j]:A.indptr[j + 1]])
+        assert seen.size == g.n_angles
+
+
+def test_slice_is_seeded_and_scaled():
+    g = W.GEOMETRIES["64"]
+    A = W.system_matrix("64")
+    s1 = W.make_slice(A, g, 1e5, W.seed_for(1))
+    s2 = W.make_slice(A, g, 1e5, W.seed_for(1))
+    s3 = W.make_slice(A, g, 1e5, W.seed_for(1, 1))
+    np.testing.assert_array_equal(s1.g, s2.g)
+    assert not np.array_equal(s1.g, s3.g)
+    proj = A.astype(np.float64) @ s1.f_true
+    assert float(np.sum(proj + s1.gamma.astype(np.float64))) == pytest.approx(1e5, rel=1e-6)
+    assert np.allclose(s1.gamma, 0.1 * proj.mean(), rtol=1e-6)
+    # Poisson counts: total within 5 sigma of the mean
+    assert abs(float(s1.g.sum()) - 1e5) < 5 * math.sqrt(1e5)
+    assert np.all(s1.g == np.round(s1.g)) and np.all(s1.g >= 0)
+
+
+def test_phantoms():
+    rng = np.random.default_rng(0)
+    f = W.ellipse_phantom(64, rng, lesions=True)
+    assert f.shape == (4096,) and f.min() >= 0 and f.max() > 0
+    u = W.uniform_phantom(256).reshape(256, 256)
+    assert set(np.unique(u)) == {0.0, 1.0, 4.0}
