@@ -1,0 +1,379 @@
+"""Benchmark of the APPGA hot path on GB300.
+
+One step = one APPGA iteration (steps a0-a6: extrapolation, forward projection
+with the Poisson-ratio epilogue, transposed-CSR back-projection, SHOITV
+stencil, EM-preconditioned projected update, FP64 objective) of a 256x256
+slice with 180 angles x 367 bins.  The timed steps run as back-to-back
+reconstructions of 500 iterations each (the workload's iteration count),
+each from the TMC initial image.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank reconstructs its own slice (independent
+replicas, weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "APPGA iters/s per 256² slice & projector HBM GB/s; p50/p99 recon latency"
+UNIT = "iters/s"
+GEOM = "256"
+COUNTS = 1e6
+OMEGA = 0.5
+LAM1, LAM2, EPS = 0.1, 0.05, 1e-3
+ITERS_PER_RECON = 500
+WORKLOAD = ("single 256x256 slice, parallel beam 180 angles x 367 bins, Siddon CSR A "
+            "(15.02M nnz, FP32 values, int32 columns) + transposed CSR, lesion phantom, "
+            "1e6 counts, gamma 10%, lambda1/lambda2 0.1/0.05, eps 1e-3, omega 0.5, beta 1, "
+            "FP64 objective every iteration; 500-iteration reconstructions back to back")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=1000)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- inputs
+
+def make_inputs(rank: int):
+    from paper_2409_13344_gb300 import workload as W
+    geom = W.GEOMETRIES[GEOM]
+    A = W.system_matrix(GEOM)
+    sl = W.make_slice(A, geom, COUNTS, W.seed_for(2, rank), phantom="lesions")
+    return geom, A, sl
+
+
+# ------------------------------------------------------------- clock sampling
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, period_ms: int = 100):
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms", str(self.period)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        idxs = sorted({r[0] for r in rows})
+        want = vis.split(",")[0] if vis and vis.split(",")[0].isdigit() and vis.split(",")[0] in idxs \
+            else idxs[0]
+        rows = [r for r in rows if r[0] == want]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- roofline data
+
+def kernel_bytes(m: int, d: int, nnz: int):
+    """Algorithmic bytes per launch of the two iteration kernels."""
+    fwd = 8 * nnz + 4 * (m + 1) + 4 * d + 28 * m   # A stream, f once, g/gamma/y_prev/y/w
+    pix = 8 * nnz + 4 * (d + 1) + 4 * m + 16 * d   # A^T stream, w once, f^k/f^{k-1}/1/Lambda/f^{k+1}
+    return fwd, pix
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    src = os.path.join(ROOT, "paper_2409_13344_gb300", "csrc", "kernels.cu")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        with open(src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernels_cu_sha256") != sha:
+        return None
+    ent = rec.get("kernels", {}).get(kernel)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------- oracle
+
+def oracle_rate(geom, A, sl, seconds: float, min_iters: int = 3):
+    """Plain FP64 oracle on the same slice, timed on the host (one core)."""
+    from oracle import appga_oracle as O
+    prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+    par = O.Params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA)
+    lam = prob.em_lambda()
+    f = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    fm = f.copy()
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        k += 1
+        th = O.gn_theta(k, par.a, par.b, par.omega)
+        fn, _ = O.appga_step(prob, f, fm, th, par, lam)
+        prob.objective(fn, LAM1, LAM2, EPS)  # the objective is part of every step
+        fm, f = f, fn
+        el = time.perf_counter() - t0
+        if k >= min_iters and el >= seconds:
+            break
+    return k, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    geom, A, sl = make_inputs(0)
+    from oracle import appga_oracle as O
+    prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+    par = O.Params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA)
+    lam = prob.em_lambda()
+    f = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    fm = f.copy()
+
+    def step(k):
+        nonlocal f, fm
+        th = O.gn_theta(k, par.a, par.b, par.omega)
+        fn, _ = O.appga_step(prob, f, fm, th, par, lam)
+        prob.objective(fn, LAM1, LAM2, EPS)
+        fm, f = f, fn
+
+    k = 0
+    for _ in range(args.warmup):
+        k += 1
+        step(k)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        k += 1
+        step(k)
+    el = time.perf_counter() - t0
+    val = args.steps / el
+    sample = f"{args.steps} APPGA iterations of the 256x256 slice (after {args.warmup} warm-up)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "FP64 NumPy/SciPy oracle on the host"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2409_13344_gb300 import build, replicas
+    from paper_2409_13344_gb300 import appga as AP
+
+    rank, world, local = replicas.dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    geom, A, sl = make_inputs(rank)
+    ctx = AP.Context(dev.index)
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
+    g = torch.from_numpy(sl.g).to(dev)
+    gamma = torch.from_numpy(sl.gamma).to(dev)
+    f_out = torch.empty(geom.d, dtype=torch.float32, device=dev)
+
+    def params(iters):
+        return AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA,
+                                 max_iters=iters, track_objective=1)
+
+    def chunks(total):
+        out = []
+        while total > 0:
+            out.append(min(ITERS_PER_RECON, total))
+            total -= out[-1]
+        return out
+
+    def run_device(total):
+        for it in chunks(total):
+            AP.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, params(it), f_out)
+
+    S = 16  # library default iterations per graph replay
+
+    def launches(total):
+        n = 0
+        for it in chunks(total):
+            n += 8 + 2 * S * math.ceil(it / S)
+        return n
+
+    # warm-up
+    run_device(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler()
+    stream = torch.cuda.current_stream()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run_device(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = replicas.max_over_ranks(ms, device=dev)
+    total_steps = replicas.sum_over_ranks(args.steps, device=dev)
+    value = total_steps / (ms_max / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    g_h = torch.from_numpy(sl.g).pin_memory()
+    gam_h = torch.from_numpy(sl.gamma).pin_memory()
+    f_h = torch.empty(geom.d, dtype=torch.float32).pin_memory()
+    e_steps = min(args.steps, 20 * ITERS_PER_RECON)
+    for it in chunks(min(e_steps, ITERS_PER_RECON)):
+        AP.appga_reconstruct_host(ctx.handle, mat.handle, g_h, gam_h, None, params(it), f_h)
+    barrier()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    n_calls = 0
+    for it in chunks(e_steps):
+        AP.appga_reconstruct_host(ctx.handle, mat.handle, g_h, gam_h, None, params(it), f_h)
+        n_calls += 1
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = replicas.max_over_ranks(e2.elapsed_time(e3), device=dev)
+    e2e_value = replicas.sum_over_ranks(e_steps, device=dev) / (ms_e2e / 1e3)
+
+    # per-kernel device times for the roofline (CUDA events on the launch stream)
+    tp, tf = AP.appga_kernel_times(ctx.handle, mat.handle, g, gamma, params(200), 200)
+    info = mat.info()
+    b_fwd, b_pix = kernel_bytes(geom.m, geom.d, int(info.nnz))
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    dom = ("k_pixel", tp, b_pix) if tp >= tf else ("k_forward", tf, b_fwd)
+    other = ("k_forward", tf, b_fwd) if dom[0] == "k_pixel" else ("k_pixel", tp, b_pix)
+    achieved = dom[2] / (dom[1] * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+        "traffic": committed_traffic(dom[0]), "kernel": dom[0], "peak_source": peak_src,
+        "ms_per_launch": dom[1], "algorithmic_bytes_per_launch": dom[2],
+        "other_kernel": {"kernel": other[0], "ms_per_launch": other[1],
+                         "achieved_gbs": other[2] / (other[1] * 1e-3) / 1e9,
+                         "frac": other[2] / (other[1] * 1e-3) / 1e9 / hbm},
+        "iteration_gbs": (b_fwd + b_pix) / ((tp + tf) * 1e-3) / 1e9,
+    }
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        k, el = oracle_rate(geom, A, sl, args.cpu_seconds)
+        cpu = {"value": k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} FP64 oracle APPGA iterations (with the objective) of the same "
+                         f"256x256 slice from the initial image, {el:.1f} s on one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "geometry": "256x256, 180 x 367",
+                       "nnz": int(info.nnz), "l2": "inputs larger than L2: A + A^T stream "
+                       f"{2 * 8 * int(info.nnz) / 1e6:.0f} MB per iteration (L2 129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * geom.m * n_calls / e_steps,
+                    "d2h_bytes_per_step": 4 * geom.d * n_calls / e_steps},
+            "gpu_launches": launches(args.steps),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    mat.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

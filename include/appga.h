@@ -1,0 +1,258 @@
+/*
+ * appga.h -- C ABI of the GB300 (sm_103a) APPGA reconstruction library.
+ *
+ * The library runs the per-iteration hot path of the accelerated
+ * preconditioned proximal gradient algorithm (APPGA) with generalized
+ * Nesterov (GN) momentum for PET reconstruction under the smoothed
+ * higher-order isotropic TV penalty (SHOITV), arXiv 2409.13344:
+ *
+ *   f~^k     = f^k + theta_k (f^k - f^{k-1})                       (Eq. APPGAiter)
+ *   f^{k+1}  = max(f~^k - P (grad F(f~^k) + B^T grad phi~(B f~^k)), 0)
+ *   grad F   = A^T (1 - g / (A f + gamma))                         (Sec. 2.2)
+ *   theta_k  = (t_{k-1} - 1) / t_k,  t_k = a k^omega + b           (Eq. GNtheta)
+ *   P        = beta diag(f^k / Lambda), Lambda = A^T 1 (1 where 0) (Eq. EM)
+ *
+ * Conventions (all calls):
+ *  - Images are N x N, vectorised row-major: pixel j = r*N + c.  d = N*N.
+ *  - Sinograms have m bins; A is m x d with nonnegative entries.
+ *  - Pointers are DEVICE pointers unless the name ends in _host.  The caller
+ *    owns every input and output buffer; the library owns matrix handles and
+ *    their device workspaces.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered; a call that returns a host value
+ *    (objective, stats) synchronises that stream before returning.
+ *  - Every call returns an appga_status; the library never aborts, traps or
+ *    exits.  appga_last_error() gives a one-line message for the calling
+ *    thread's most recent failure.
+ *  - A context and the matrices created from it may be used by one host
+ *    thread at a time.
+ */
+#ifndef APPGA_H
+#define APPGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  APPGA_OK = 0,
+  APPGA_EINVAL = 1,   /* bad shape, CSR, parameter or null pointer */
+  APPGA_ENOMEM = 2,   /* device or host allocation failed */
+  APPGA_EDOMAIN = 3,  /* non-finite input, g < 0 or gamma <= 0 */
+  APPGA_ETIMEOUT = 4, /* a bounded wait ran out */
+  APPGA_ECUDA = 5,    /* a CUDA runtime call failed */
+  APPGA_ENODEV = 6,   /* no usable CUDA device */
+  APPGA_EBUSY = 7,    /* no free slot / resource in use */
+  APPGA_ENUMERIC = 8  /* the device flagged a non-finite intermediate */
+} appga_status;
+
+typedef struct appga_ctx appga_ctx;
+typedef struct appga_matrix appga_matrix;
+
+/* Matrix-creation flags. */
+#define APPGA_A_BF16_COPY 1u /* also keep a BF16 copy of A's values */
+
+/* Precision of A's values inside the projectors. */
+#define APPGA_PREC_FP32 0
+#define APPGA_PREC_BF16 1
+
+/* Momentum rules. */
+#define APPGA_MOMENTUM_GN 0       /* Eq. GNtheta: t_k = a k^omega + b */
+#define APPGA_MOMENTUM_NONE 1     /* theta_k = 0: PPGA, Eq. PPGAiter */
+#define APPGA_MOMENTUM_NESTEROV 2 /* t_k = (1 + sqrt(1 + 4 t_{k-1}^2)) / 2, Sec. 4.3 */
+
+/* Device sticky flags reported in appga_stats.flags. */
+#define APPGA_FLAG_NONFINITE 1 /* a non-finite value met in a projector */
+
+const char* appga_status_string(appga_status s);
+const char* appga_last_error(void);
+/* Library version, e.g. "0.1.0". */
+const char* appga_version(void);
+
+/* ------------------------------------------------------------------ context
+ * appga_ctx_create: bind the calling thread to CUDA device `device` and
+ * create a context.  Errors: APPGA_ENODEV if the device does not exist,
+ * APPGA_ECUDA on runtime failure. */
+appga_status appga_ctx_create(int32_t device, appga_ctx** out);
+appga_status appga_ctx_destroy(appga_ctx* ctx);
+
+/* ------------------------------------------------------------------ matrix
+ * appga_matrix_create: copy the host CSR of the system matrix A (m x d,
+ * Sec. 2.1 "A in R_+^{m x d}") to the device and build there:
+ *   - A as a row-padded CSR (each row padded with zeros to a multiple of 4
+ *     entries so rows start on 16-byte boundaries),
+ *   - A^T as a row-padded CSR (built on the host by a stable counting sort,
+ *     so the back-projection needs no atomics),
+ *   - 1/Lambda with Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM).
+ * n_side is N (d must equal N*N); n_angles is the number of projection
+ * angles (NPA, used only by the default initial image, Sec. 4.1).
+ * row_ptr_host: int32[m+1], col_host: int32[nnz], val_host: float[nnz]; the
+ * host arrays are only read during the call.  Validation: row_ptr[0] = 0,
+ * nondecreasing, row_ptr[m] = nnz; 0 <= col < d; values finite and >= 0
+ * (EINVAL / EDOMAIN otherwise).  flags: APPGA_A_BF16_COPY. */
+appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n_side,
+                                 int32_t n_angles, const int32_t* row_ptr_host,
+                                 const int32_t* col_host, const float* val_host,
+                                 uint32_t flags, appga_matrix** out);
+appga_status appga_matrix_destroy(appga_matrix* mat);
+
+typedef struct {
+  int32_t m, d, n_side, n_angles;
+  int64_t nnz;          /* entries of A as given */
+  int64_t nnz_padded_a; /* stored entries of A (row padded) */
+  int64_t nnz_padded_t; /* stored entries of A^T (row padded) */
+  int32_t has_bf16;
+  int64_t device_bytes; /* device memory held by the handle */
+} appga_matrix_info;
+appga_status appga_matrix_get_info(const appga_matrix* mat, appga_matrix_info* out);
+
+/* --------------------------------------------------------------- parameters
+ * Model parameters lambda1, lambda2 >= 0, eps > 0 (Sec. 2.1, Eq. def:smoothL2);
+ * momentum a > 0, b, omega in (0, 1] (Eq. GNtheta; the paper uses a = 1/8,
+ * b = 1); step size beta > 0 (Eq. EM).  max_iters >= 0 APPGA maps.
+ * rel_obj_tol > 0 stops once |Phi(f^{k+1}) - Phi(f^k)| <= tol |Phi(f^k)|.
+ * precond_freeze_iter = K_P >= 1 freezes P = beta f^{K_P}/Lambda after
+ * iteration K_P (Sec. 4.1 allows fixing P after early iterations); -1 never
+ * freezes.  track_objective = 1 evaluates Phi(f^k) in FP64 on the device
+ * every iteration (forced on when rel_obj_tol > 0).  graph_iters = number of
+ * iterations captured per CUDA graph replay (0 = library default); the stop
+ * flag is polled once per replay. */
+typedef struct {
+  double lambda1, lambda2, eps;
+  double omega, a, b;
+  double beta;
+  int32_t max_iters;
+  double rel_obj_tol;
+  int32_t precond_freeze_iter;
+  int32_t a_precision; /* APPGA_PREC_FP32 or APPGA_PREC_BF16 */
+  int32_t momentum;    /* APPGA_MOMENTUM_* */
+  int32_t track_objective;
+  int32_t graph_iters;
+} appga_params;
+
+/* Defaults: lambda1 = 0.1, lambda2 = 0.05, eps = 1e-3, omega = 0.5, a = 1/8,
+ * b = 1, beta = 1, max_iters = 100, rel_obj_tol = 0, precond_freeze_iter = -1,
+ * FP32, GN momentum, track_objective = 0, graph_iters = 0. */
+void appga_params_default(appga_params* p);
+/* EINVAL with a message if a field is out of range (see above; also a < 1/2
+ * when omega = 1, the range of the convergence theorem, Thm. 10). */
+appga_status appga_params_validate(const appga_params* p);
+
+/* GN momentum scalar theta_k = (t_{k-1}-1)/t_k, t_k = a k^omega + b, in
+ * FP64 (Eq. GNtheta).  k >= 1.  Host function, for callers and tests. */
+double appga_gn_theta(int32_t k, double a, double b, double omega);
+
+typedef struct {
+  int32_t iters;        /* APPGA maps applied to produce the result */
+  int32_t result_k;     /* iterate index of the result (f^{result_k}) */
+  int32_t stopped_early;/* 1 if rel_obj_tol fired */
+  int32_t flags;        /* APPGA_FLAG_* sticky device flags */
+  int64_t guard_hits;   /* bins where A f~ + gamma < kappa*gamma (guarded) */
+  double phi;           /* Phi(result) in FP64, or NaN if not tracked */
+  double phi_prev;      /* Phi of the iterate before the result, or NaN */
+} appga_stats;
+
+/* ------------------------------------------------- single hot-path steps
+ * Each call below runs exactly the kernel the solver loop runs for that
+ * step, once, with the given inputs.
+ *
+ * appga_forward_ratio (steps a1-a2, Sec. 2.2 grad F): for every bin i
+ *   y_i  = (A f)_i, accumulated in double-float (FP32 pairs) and stored as
+ *          FP64 in y_out[m];
+ *   w_i  = 1 - g_i / den_i with den_i = max(y_i + gamma_i, 1e-3 gamma_i)
+ *          (FP32 in w_out[m]; the gradient uses the ratio only through w);
+ *   data_out (device double[1], may be NULL) = sum_i y_i - g_i ln(y_i + gamma_i)
+ *          in FP64 (the fidelity F, Eq. FidelityTerm, valid for f >= 0).
+ * f: float[d]; g, gamma: float[m]. */
+appga_status appga_forward_ratio(appga_ctx* ctx, const appga_matrix* mat, const float* f,
+                                 const float* g, const float* gamma, double* y_out,
+                                 float* w_out, double* data_out, void* stream);
+
+/* appga_backproject (step a3): out[d] = A^T w via the transposed CSR, one
+ * warp per pixel row, FP32 accumulation, no atomics.  w: float[m]. */
+appga_status appga_backproject(appga_ctx* ctx, const appga_matrix* mat, const float* w,
+                               float* out, void* stream);
+
+/* appga_shoitv_grad (step a4, Sec. 2.1-2.2): out = B^T grad phi~(B f) for an
+ * N x N image f (float[N*N]), with the six difference fields of B1 and B2
+ * and the group norms max(||.||_2, eps), computed by a shared-memory
+ * halo-tiled stencil in FP32. */
+appga_status appga_shoitv_grad(appga_ctx* ctx, int32_t n_side, const float* f, double lambda1,
+                               double lambda2, double eps, float* out, void* stream);
+
+/* appga_pixel_update (steps a0, a3, a4, a5 fused, Eq. APPGAiter + Eq. EM):
+ *   f~ = f_cur + theta (f_cur - f_prev),
+ *   f_next = max(f~ - beta f_cur / Lambda * (A^T w + B^T grad phi~(B f~)), 0)
+ * with w the back-projection weight from appga_forward_ratio evaluated at f~.
+ * Uses lambda1, lambda2, eps, beta from params. */
+appga_status appga_pixel_update(appga_ctx* ctx, const appga_matrix* mat, const float* f_prev,
+                                const float* f_cur, const float* w, double theta,
+                                const appga_params* params, float* f_next, void* stream);
+
+/* appga_objective (step a6): Phi(f) = F(f) + phi~(B f) in FP64 (Eq. def:phi,
+ * no constant terms) for f >= 0, written to *phi_out_host.  Synchronises. */
+appga_status appga_objective(appga_ctx* ctx, const appga_matrix* mat, const float* f,
+                             const float* g, const float* gamma, const appga_params* params,
+                             double* phi_out_host, void* stream);
+
+/* appga_initial_image: f_out = TMC * 1_disk (Sec. 4.1), TMC = ACTc/(NPFOV*NPA),
+ * ACTc = sum g - sum gamma (FP64 on the device), disk = pixel centres with
+ * x^2 + y^2 <= (N/2)^2. */
+appga_status appga_initial_image(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                                 const float* gamma, float* f_out, void* stream);
+
+/* ------------------------------------------------------------------ solver
+ * appga_reconstruct: run APPGA from f^0 = f^1 = f_init (NULL: the initial
+ * image above) for params->max_iters maps or until the stopping test fires,
+ * and write the result to f_out (float[d]).  g: float[m] (counts, >= 0),
+ * gamma: float[m] (> 0).  stats_host may be NULL.  The iteration runs as
+ * captured CUDA graphs on `stream`; the call returns once the result is in
+ * f_out (it synchronises the stream).  Inputs are validated on the device
+ * (EDOMAIN for negative or non-finite g, non-positive or non-finite gamma). */
+appga_status appga_reconstruct(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                               const float* gamma, const float* f_init,
+                               const appga_params* params, float* f_out,
+                               appga_stats* stats_host, void* stream);
+
+/* appga_resume: continue APPGA from the state (f^{k0-1}, f^{k0}) at iteration
+ * index k0 >= 1 (theta_{k0} is the first momentum used).  Writes f^{r-1} to
+ * f_out_prev (may be NULL) and the result f^{r} to f_out.  Resuming from a
+ * snapshot gives the same result as running uninterrupted (theta_k depends
+ * only on k). */
+appga_status appga_resume(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                          const float* gamma, const float* f_prev, const float* f_cur,
+                          int32_t k0, const appga_params* params, float* f_out_prev,
+                          float* f_out, appga_stats* stats_host, void* stream);
+
+/* appga_reconstruct_host: appga_reconstruct with HOST buffers (g_host,
+ * gamma_host: float[m]; f_init_host: float[d] or NULL; f_out_host: float[d]).
+ * Copies in and out through the library's pinned staging buffers. */
+appga_status appga_reconstruct_host(appga_ctx* ctx, const appga_matrix* mat, const float* g_host,
+                                    const float* gamma_host, const float* f_init_host,
+                                    const appga_params* params, float* f_out_host,
+                                    appga_stats* stats_host, void* stream);
+
+/* appga_validate_csr_host: the host-side check appga_matrix_create runs on a
+ * CSR (row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz, 0 <= col < d, values
+ * finite and >= 0).  Host only; needs no device.  EINVAL / EDOMAIN with a
+ * message from appga_last_error(). */
+appga_status appga_validate_csr_host(int32_t m, int32_t d, const int32_t* row_ptr_host,
+                                     const int32_t* col_host, const float* val_host);
+
+/* appga_kernel_times: per-launch device time of the two iteration kernels.
+ * Sets up a run exactly as appga_reconstruct does (f_init NULL: the initial
+ * image), then launches n_iters iterations of (pixel phase, forward phase)
+ * back to back on the library stream with CUDA events around every launch,
+ * and returns the mean duration of each kernel in milliseconds.  The
+ * iterate ring of the matrix workspace is overwritten.  Synchronises. */
+appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                                const float* gamma, const appga_params* params, int32_t n_iters,
+                                double* ms_pixel_host, double* ms_forward_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APPGA_H */

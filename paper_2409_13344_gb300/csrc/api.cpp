@@ -1,0 +1,921 @@
+// C ABI of the APPGA library: contexts, matrix handles, parameter checks,
+// single-step entry points and the graph-driven single-slice solver.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+
+#include "appga.h"
+#include "appga_internal.h"
+
+using appga::DevCSR;
+using appga::SolverState;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kDefaultGraphIters = 16;
+
+struct Workspace {
+  bool ready = false;
+  int m = 0, d = 0;
+  float* f[3] = {nullptr, nullptr, nullptr};
+  double* y[2] = {nullptr, nullptr};
+  float* w = nullptr;
+  float* pfreeze = nullptr;
+  double* partial_p = nullptr;
+  double* partial_r = nullptr;
+  double* partial_aux = nullptr;
+  double* scalars = nullptr;  // device doubles for standalone results
+  SolverState* st = nullptr;
+  SolverState* st_scratch = nullptr;
+  SolverState* st_host = nullptr;  // pinned
+  int* flag = nullptr;
+  int* flag_host = nullptr;        // pinned
+  double* scalars_host = nullptr;  // pinned
+  // device staging for the host-buffer entry point
+  float* d_g = nullptr;
+  float* d_gamma = nullptr;
+  float* d_finit = nullptr;
+  float* d_fout = nullptr;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  int graph_iters = 0;
+};
+
+}  // namespace
+
+struct appga_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+struct appga_matrix {
+  appga_ctx* ctx = nullptr;
+  int32_t m = 0, d = 0, n = 0, na = 0;
+  int64_t nnz = 0;
+  DevCSR A, At;
+  float* inv_lambda = nullptr;
+  int32_t has_bf16 = 0;
+  int64_t bytes = 0;
+  Workspace ws;
+};
+
+namespace appga {
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace appga
+
+namespace {
+
+appga_status fail(appga_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+appga_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return APPGA_ENOMEM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInvalidDevice || e == cudaErrorInsufficientDriver)
+    return APPGA_ENODEV;
+  return APPGA_ECUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, int64_t* bytes = nullptr) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  const size_t b = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, b);
+  if (e == cudaSuccess && bytes) *bytes += (int64_t)b;
+  return e;
+}
+
+void free_csr(DevCSR& c) {
+  cudaFree(c.row_ptr);
+  cudaFree(c.col);
+  cudaFree(c.val);
+  cudaFree(c.val_bf16);
+  c = DevCSR();
+}
+
+void free_workspace(Workspace& ws) {
+  if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
+  for (auto& p : ws.f) cudaFree(p);
+  for (auto& p : ws.y) cudaFree(p);
+  cudaFree(ws.w);
+  cudaFree(ws.pfreeze);
+  cudaFree(ws.partial_p);
+  cudaFree(ws.partial_r);
+  cudaFree(ws.partial_aux);
+  cudaFree(ws.scalars);
+  cudaFree(ws.st);
+  cudaFree(ws.st_scratch);
+  cudaFree(ws.flag);
+  cudaFree(ws.d_g);
+  cudaFree(ws.d_gamma);
+  cudaFree(ws.d_finit);
+  cudaFree(ws.d_fout);
+  cudaFreeHost(ws.st_host);
+  cudaFreeHost(ws.flag_host);
+  cudaFreeHost(ws.scalars_host);
+  ws = Workspace();
+}
+
+appga_status upload_csr(const appga::HostCSR& h, bool bf16, DevCSR* out, int64_t* bytes) {
+  DevCSR c;
+  c.rows = h.rows;
+  c.cols = h.cols;
+  c.nnz_padded = (int64_t)h.col.size();
+  cudaError_t e;
+  if ((e = dalloc(&c.row_ptr, h.row_ptr.size(), bytes)) != cudaSuccess ||
+      (e = dalloc(&c.col, h.col.size(), bytes)) != cudaSuccess ||
+      (e = dalloc(&c.val, h.val.size(), bytes)) != cudaSuccess) {
+    free_csr(c);
+    return cuda_fail(e, "cudaMalloc(matrix)");
+  }
+  if (bf16) {
+    if ((e = dalloc(&c.val_bf16, h.val.size(), bytes)) != cudaSuccess) {
+      free_csr(c);
+      return cuda_fail(e, "cudaMalloc(matrix bf16)");
+    }
+  }
+  e = cudaMemcpy(c.row_ptr, h.row_ptr.data(), h.row_ptr.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !h.col.empty())
+    e = cudaMemcpy(c.col, h.col.data(), h.col.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !h.val.empty())
+    e = cudaMemcpy(c.val, h.val.data(), h.val.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bf16 && !h.val.empty()) {
+    std::vector<uint16_t> b(h.val.size());
+    for (size_t i = 0; i < b.size(); ++i) b[i] = appga::float_to_bf16(h.val[i]);
+    e = cudaMemcpy(c.val_bf16, b.data(), b.size() * 2, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    free_csr(c);
+    return cuda_fail(e, "cudaMemcpy(matrix)");
+  }
+  *out = c;
+  return APPGA_OK;
+}
+
+appga_status ensure_workspace(appga_matrix* M) {
+  Workspace& ws = M->ws;
+  if (ws.ready) return APPGA_OK;
+  const int m = M->m, d = M->d;
+  const int np = appga::max_partials(m, M->n);
+  cudaError_t e = cudaSuccess;
+  int64_t* b = &M->bytes;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(&ws.f[i], (size_t)d, b);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(&ws.y[i], (size_t)m, b);
+  if (e == cudaSuccess) e = dalloc(&ws.w, (size_t)m, b);
+  if (e == cudaSuccess) e = dalloc(&ws.pfreeze, (size_t)d, b);
+  if (e == cudaSuccess) e = dalloc(&ws.partial_p, (size_t)np, b);
+  if (e == cudaSuccess) e = dalloc(&ws.partial_r, (size_t)np, b);
+  if (e == cudaSuccess) e = dalloc(&ws.partial_aux, (size_t)np, b);
+  if (e == cudaSuccess) e = dalloc(&ws.scalars, 8, b);
+  if (e == cudaSuccess) e = dalloc(&ws.st, 1, b);
+  if (e == cudaSuccess) e = dalloc(&ws.st_scratch, 1, b);
+  if (e == cudaSuccess) e = dalloc(&ws.flag, 1, b);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ws.st_host, sizeof(SolverState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ws.flag_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ws.scalars_host, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(ws.st, 0, sizeof(SolverState));
+  if (e == cudaSuccess) e = cudaMemset(ws.st_scratch, 0, sizeof(SolverState));
+  if (e != cudaSuccess) {
+    free_workspace(ws);
+    return cuda_fail(e, "workspace allocation");
+  }
+  ws.m = m;
+  ws.d = d;
+  ws.ready = true;
+  return APPGA_OK;
+}
+
+appga::IterParams iter_params(const appga_params* p, bool track) {
+  appga::IterParams ip{};
+  ip.lambda1 = (float)p->lambda1;
+  ip.lambda2 = (float)p->lambda2;
+  ip.eps = (float)p->eps;
+  ip.beta = (float)p->beta;
+  ip.omega = p->omega;
+  ip.a = p->a;
+  ip.b = p->b;
+  ip.rel_tol = p->rel_obj_tol;
+  ip.momentum = p->momentum;
+  ip.freeze_iter = p->precond_freeze_iter;
+  ip.track = track ? 1 : 0;
+  return ip;
+}
+
+bool bf16_requested(const appga_matrix* M, const appga_params* p) {
+  return p->a_precision == APPGA_PREC_BF16 && M->has_bf16;
+}
+
+appga::FwdArgs fwd_args(appga_matrix* M, bool bf16) {
+  appga::FwdArgs a{};
+  a.A = M->A;
+  a.use_bf16 = bf16 ? 1 : 0;
+  return a;
+}
+
+std::string graph_key(const appga_params* p, bool track, bool bf16, int S) {
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d",
+                (int)track, (int)bf16, S, p->lambda1, p->lambda2, p->eps, p->beta, p->omega, p->a,
+                p->b, p->rel_obj_tol, p->momentum, p->precond_freeze_iter);
+  return buf;
+}
+
+// Prepares a run on the workspace ring whose slots (k0-1)%3 and k0%3 hold
+// f^{k0-1} and f^{k0}: the device state, theta_{k0}, y^{k0-1}, y^{k0},
+// w^{k0} and F(f^{k0}); fills the kernel argument blocks of the loop.
+appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int32_t k0,
+                       const appga_params* p, appga::FwdArgs* fa_out, appga::PixArgs* pa_out) {
+  Workspace& ws = M->ws;
+  cudaStream_t s = M->ctx->stream;
+  const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
+  const bool bf16 = bf16_requested(M, p);
+  SolverState h{};
+  h.k = k0;
+  h.k0 = k0;
+  h.k_last = k0 + p->max_iters - 1;
+  h.done = p->max_iters == 0 ? 1 : 0;
+  h.result_k = k0;
+  h.phi_cur = std::numeric_limits<double>::quiet_NaN();
+  h.phi_prev = h.phi_cur;
+  CK(cudaMemcpyAsync(ws.st, &h, sizeof h, cudaMemcpyHostToDevice, s));
+  CK(appga::launch_init_momentum(ws.st, k0, p->momentum, p->a, p->b, p->omega, s));
+
+  // y^{k0-1} = A f^{k0-1}
+  appga::FwdArgs init = fwd_args(M, bf16);
+  init.f[0] = ws.f[(k0 + 2) % 3];
+  init.y[0] = ws.y[(k0 + 1) & 1];
+  init.g = g;
+  init.gamma = gamma;
+  init.st = ws.st_scratch;
+  init.partial = ws.partial_aux;
+  init.loop = 0;
+  CK(appga::launch_forward(init, 0, s));
+
+  appga::FwdArgs fa = fwd_args(M, bf16);
+  for (int i = 0; i < 3; ++i) fa.f[i] = ws.f[i];
+  fa.y[0] = ws.y[0];
+  fa.y[1] = ws.y[1];
+  fa.w = ws.w;
+  fa.g = g;
+  fa.gamma = gamma;
+  fa.st = ws.st;
+  fa.partial = ws.partial_r;
+  fa.loop = 1;
+  fa.want_data = track ? 1 : 0;
+
+  appga::PixArgs pa{};
+  pa.At = M->At;
+  pa.n = M->n;
+  for (int i = 0; i < 3; ++i) pa.f[i] = ws.f[i];
+  pa.w = ws.w;
+  pa.inv_lambda = M->inv_lambda;
+  pa.pfreeze = ws.pfreeze;
+  pa.st = ws.st;
+  pa.partial = ws.partial_p;
+  pa.ip = iter_params(p, track);
+  pa.use_bf16 = bf16 ? 1 : 0;
+
+  // w^{k0}, y^{k0} and F(f^{k0})
+  CK(appga::launch_forward(fa, track, s));
+  *fa_out = fa;
+  *pa_out = pa;
+  return APPGA_OK;
+}
+
+// Runs APPGA on the workspace ring whose slots (k0-1)%3 and k0%3 already
+// hold f^{k0-1} and f^{k0}.  Everything is ordered on ctx->stream.
+appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int32_t k0,
+                        const appga_params* p, appga_stats* stats, int32_t* result_k_out) {
+  appga_ctx* ctx = M->ctx;
+  Workspace& ws = M->ws;
+  cudaStream_t s = ctx->stream;
+  const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
+  const bool bf16 = bf16_requested(M, p);
+  const int S = p->graph_iters > 0 ? p->graph_iters : kDefaultGraphIters;
+
+  appga::FwdArgs fa;
+  appga::PixArgs pa;
+  appga_status rc0 = setup_run(M, g, gamma, k0, p, &fa, &pa);
+  if (rc0 != APPGA_OK) return rc0;
+
+  if (p->max_iters > 0) {
+    // the captured kernel arguments hold the g / gamma addresses
+    const std::string key = graph_key(p, track, bf16, S) + "|" +
+                            std::to_string((uintptr_t)g) + "|" + std::to_string((uintptr_t)gamma);
+    if (ws.gexec == nullptr || ws.gkey != key) {
+      if (ws.gexec) {
+        cudaGraphExecDestroy(ws.gexec);
+        ws.gexec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < S && e == cudaSuccess; ++i) {
+        e = appga::launch_pixel(pa, s);
+        if (e == cudaSuccess) e = appga::launch_forward(fa, track, s);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+      if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "graph capture");
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&ws.gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      ws.gkey = key;
+      ws.graph_iters = S;
+    }
+    const int reps = (p->max_iters + S - 1) / S;
+    if (p->rel_obj_tol > 0.0) {
+      // poll the stop flag one replay behind so the device never idles
+      cudaEvent_t ev[2];
+      CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+      SolverState* hs = ws.st_host;
+      appga_status rc = APPGA_OK;
+      for (int r = 0; r < reps; ++r) {
+        cudaError_t e = cudaGraphLaunch(ws.gexec, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(&hs->done, &ws.st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[r & 1], s);
+        if (e != cudaSuccess) {
+          rc = cuda_fail(e, "graph replay");
+          break;
+        }
+        if (r >= 1) {
+          e = cudaEventSynchronize(ev[(r - 1) & 1]);
+          if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaEventSynchronize");
+            break;
+          }
+          if (hs->done) break;
+        }
+      }
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+      if (rc != APPGA_OK) return rc;
+    } else {
+      for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ws.gexec, s));
+    }
+  }
+  CK(cudaMemcpyAsync(ws.st_host, ws.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const SolverState fin = *ws.st_host;
+  *result_k_out = fin.result_k;
+  if (stats) {
+    stats->iters = fin.result_k - k0;
+    stats->result_k = fin.result_k;
+    stats->stopped_early = fin.stopped_early;
+    stats->flags = fin.flags;
+    stats->guard_hits = (int64_t)fin.guard_hits;
+    stats->phi = std::numeric_limits<double>::quiet_NaN();
+    stats->phi_prev = std::numeric_limits<double>::quiet_NaN();
+    if (track) {
+      if (fin.stopped_early) {
+        stats->phi = fin.phi_cur;
+        stats->phi_prev = fin.phi_prev;
+      } else {
+        stats->phi_prev = p->max_iters > 0 ? fin.phi_cur : std::numeric_limits<double>::quiet_NaN();
+      }
+    }
+  }
+  if (fin.flags & APPGA_FLAG_NONFINITE)
+    return fail(APPGA_ENUMERIC, "a non-finite value appeared in the iteration");
+  return APPGA_OK;
+}
+
+appga_status check_params_and_mat(appga_ctx* ctx, const appga_matrix* M, const appga_params* p) {
+  if (ctx == nullptr || M == nullptr || p == nullptr)
+    return fail(APPGA_EINVAL, "null context, matrix or params");
+  if (M->ctx != ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
+  return appga_params_validate(p);
+}
+
+appga_status validate_inputs(appga_matrix* M, const float* g, const float* gamma, const float* f,
+                             cudaStream_t s) {
+  Workspace& ws = M->ws;
+  CK(cudaMemsetAsync(ws.flag, 0, sizeof(int), s));
+  CK(appga::launch_validate_inputs(g, gamma, M->m, f, M->d, ws.flag, s));
+  CK(cudaMemcpyAsync(ws.flag_host, ws.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*ws.flag_host)
+    return fail(APPGA_EDOMAIN,
+                "inputs must satisfy: g finite and >= 0, gamma finite and > 0, f finite and >= 0");
+  return APPGA_OK;
+}
+
+// Orders ctx->stream after the caller's stream.
+appga_status enter(appga_ctx* ctx, void* stream) {
+  cudaStream_t us = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaEventRecord(ctx->ev_in, us));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  return APPGA_OK;
+}
+// Orders the caller's stream after ctx->stream.
+appga_status leave(appga_ctx* ctx, void* stream) {
+  cudaStream_t us = (cudaStream_t)stream;
+  CK(cudaEventRecord(ctx->ev_out, ctx->stream));
+  CK(cudaStreamWaitEvent(us, ctx->ev_out, 0));
+  return APPGA_OK;
+}
+
+appga_status objective_on(appga_matrix* M, const float* f, const float* g, const float* gamma,
+                          const appga_params* p, double* phi, cudaStream_t s) {
+  Workspace& ws = M->ws;
+  appga::FwdArgs a = fwd_args(M, bf16_requested(M, p));
+  a.f[0] = f;
+  a.y[0] = ws.y[0];
+  a.g = g;
+  a.gamma = gamma;
+  a.st = ws.st_scratch;
+  a.partial = ws.partial_aux;
+  a.data_out = ws.scalars;
+  a.loop = 0;
+  a.want_data = 1;
+  CK(appga::launch_forward(a, 1, s));
+  CK(appga::launch_reg_term(M->n, f, (float)p->lambda1, (float)p->lambda2, (float)p->eps,
+                            ws.partial_aux, ws.st_scratch, ws.scalars + 1, s));
+  CK(cudaMemcpyAsync(ws.scalars_host, ws.scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *phi = ws.scalars_host[0] + ws.scalars_host[1];
+  return APPGA_OK;
+}
+
+appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const float* gamma,
+                          const float* f_prev, const float* f_cur, int32_t k0,
+                          const appga_params* p, float* f_out_prev, float* f_out,
+                          appga_stats* stats, void* stream, bool fresh) {
+  appga_status rc = check_params_and_mat(ctx, M, p);
+  if (rc != APPGA_OK) return rc;
+  if (g == nullptr || gamma == nullptr || f_out == nullptr)
+    return fail(APPGA_EINVAL, "g, gamma and f_out must be non-NULL");
+  if (!fresh && (f_prev == nullptr || f_cur == nullptr))
+    return fail(APPGA_EINVAL, "resume needs f_prev and f_cur");
+  if (k0 < 1) return fail(APPGA_EINVAL, "k0 must be >= 1");
+  if (p->precond_freeze_iter >= 0 && k0 > p->precond_freeze_iter)
+    return fail(APPGA_EINVAL, "resume past the preconditioner freeze iteration is not supported");
+  if ((rc = ensure_workspace(M)) != APPGA_OK) return rc;
+  if ((rc = enter(ctx, stream)) != APPGA_OK) return rc;
+  cudaStream_t s = ctx->stream;
+  Workspace& ws = M->ws;
+  if ((rc = validate_inputs(M, g, gamma, fresh ? f_cur : f_prev, s)) != APPGA_OK) return rc;
+  if (!fresh && (rc = validate_inputs(M, g, gamma, f_cur, s)) != APPGA_OK) return rc;
+  const size_t fb = (size_t)M->d * sizeof(float);
+  float* slot_cur = ws.f[k0 % 3];
+  float* slot_prev = ws.f[(k0 + 2) % 3];
+  if (fresh) {
+    if (f_cur) {
+      CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, ws.partial_aux, ws.st_scratch,
+                                     slot_cur, s));
+    }
+    CK(cudaMemcpyAsync(slot_prev, slot_cur, fb, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(slot_prev, f_prev, fb, cudaMemcpyDeviceToDevice, s));
+  }
+  int32_t rk = k0;
+  rc = run_solver(M, g, gamma, k0, p, stats, &rk);
+  if (rc != APPGA_OK && rc != APPGA_ENUMERIC) return rc;
+  CK(cudaMemcpyAsync(f_out, ws.f[rk % 3], fb, cudaMemcpyDeviceToDevice, s));
+  if (f_out_prev) CK(cudaMemcpyAsync(f_out_prev, ws.f[(rk + 2) % 3], fb, cudaMemcpyDeviceToDevice, s));
+  const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
+  if (stats && track && !stats->stopped_early && rc == APPGA_OK) {
+    double phi = 0.0;
+    appga_status r2 = objective_on(M, ws.f[rk % 3], g, gamma, p, &phi, s);
+    if (r2 != APPGA_OK) return r2;
+    stats->phi = phi;
+  }
+  appga_status r3 = leave(ctx, stream);
+  if (r3 != APPGA_OK) return r3;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* appga_status_string(appga_status s) {
+  switch (s) {
+    case APPGA_OK: return "ok";
+    case APPGA_EINVAL: return "invalid argument";
+    case APPGA_ENOMEM: return "out of memory";
+    case APPGA_EDOMAIN: return "input outside the model's domain";
+    case APPGA_ETIMEOUT: return "timed out";
+    case APPGA_ECUDA: return "CUDA runtime error";
+    case APPGA_ENODEV: return "no usable CUDA device";
+    case APPGA_EBUSY: return "resource busy";
+    case APPGA_ENUMERIC: return "non-finite intermediate";
+  }
+  return "unknown status";
+}
+
+const char* appga_last_error(void) { return g_last_error.c_str(); }
+
+const char* appga_version(void) { return "0.1.0"; }
+
+void appga_params_default(appga_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->lambda1 = 0.1;
+  p->lambda2 = 0.05;
+  p->eps = 1e-3;
+  p->omega = 0.5;
+  p->a = 0.125;
+  p->b = 1.0;
+  p->beta = 1.0;
+  p->max_iters = 100;
+  p->rel_obj_tol = 0.0;
+  p->precond_freeze_iter = -1;
+  p->a_precision = APPGA_PREC_FP32;
+  p->momentum = APPGA_MOMENTUM_GN;
+  p->track_objective = 0;
+  p->graph_iters = 0;
+}
+
+appga_status appga_params_validate(const appga_params* p) {
+  if (!p) return fail(APPGA_EINVAL, "params is NULL");
+  auto fin = [](double x) { return std::isfinite(x); };
+  if (!fin(p->lambda1) || p->lambda1 < 0 || !fin(p->lambda2) || p->lambda2 < 0)
+    return fail(APPGA_EINVAL, "lambda1 and lambda2 must be finite and >= 0");
+  if (!fin(p->eps) || !(p->eps > 0)) return fail(APPGA_EINVAL, "eps must be finite and > 0");
+  if (!fin(p->beta) || !(p->beta > 0)) return fail(APPGA_EINVAL, "beta must be finite and > 0");
+  if (p->max_iters < 0) return fail(APPGA_EINVAL, "max_iters must be >= 0");
+  if (!fin(p->rel_obj_tol) || p->rel_obj_tol < 0)
+    return fail(APPGA_EINVAL, "rel_obj_tol must be finite and >= 0");
+  if (p->precond_freeze_iter < -1 || p->precond_freeze_iter == 0)
+    return fail(APPGA_EINVAL, "precond_freeze_iter must be -1 or >= 1");
+  if (p->a_precision != APPGA_PREC_FP32 && p->a_precision != APPGA_PREC_BF16)
+    return fail(APPGA_EINVAL, "a_precision must be APPGA_PREC_FP32 or APPGA_PREC_BF16");
+  if (p->graph_iters < 0 || p->graph_iters > 4096)
+    return fail(APPGA_EINVAL, "graph_iters must be in [0, 4096]");
+  if (p->momentum == APPGA_MOMENTUM_GN) {
+    if (!fin(p->omega) || !(p->omega > 0) || p->omega > 1)
+      return fail(APPGA_EINVAL, "omega must be in (0, 1]");
+    if (!fin(p->a) || !(p->a > 0)) return fail(APPGA_EINVAL, "a must be > 0");
+    if (p->omega == 1.0 && !(p->a < 0.5))
+      return fail(APPGA_EINVAL, "a must be < 1/2 when omega = 1 (Thm. 10)");
+    if (!fin(p->b)) return fail(APPGA_EINVAL, "b must be finite");
+    if (p->b <= 0 && p->b > -p->a * 1e12) {
+      // b must keep t_k = a k^omega + b away from zero for every k >= 1
+      // (Lemma on t_k): reject b equal to -a k^omega for some k.
+      const double q = std::pow(-p->b / p->a, 1.0 / p->omega);
+      if (std::fabs(q - std::round(q)) < 1e-12 && std::round(q) >= 1.0)
+        return fail(APPGA_EINVAL, "b = -a k^omega for some k makes t_k vanish");
+    }
+  } else if (p->momentum != APPGA_MOMENTUM_NONE && p->momentum != APPGA_MOMENTUM_NESTEROV) {
+    return fail(APPGA_EINVAL, "unknown momentum rule");
+  }
+  return APPGA_OK;
+}
+
+double appga_gn_theta(int32_t k, double a, double b, double omega) {
+  const double t_prev = a * std::pow((double)(k - 1), omega) + b;
+  const double t = a * std::pow((double)k, omega) + b;
+  return (t_prev - 1.0) / t;
+}
+
+appga_status appga_ctx_create(int32_t device, appga_ctx** out) {
+  if (!out) return fail(APPGA_EINVAL, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) return fail(APPGA_ENODEV, "no CUDA device is visible");
+  if (device < 0 || device >= count) return fail(APPGA_ENODEV, "device index out of range");
+  CK(cudaSetDevice(device));
+  auto* ctx = new appga_ctx();
+  ctx->device = device;
+  e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    appga_ctx_destroy(ctx);
+    return cuda_fail(e, "context setup");
+  }
+  *out = ctx;
+  return APPGA_OK;
+}
+
+appga_status appga_ctx_destroy(appga_ctx* ctx) {
+  if (!ctx) return APPGA_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  delete ctx;
+  return APPGA_OK;
+}
+
+appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n_side,
+                                 int32_t n_angles, const int32_t* row_ptr_host,
+                                 const int32_t* col_host, const float* val_host, uint32_t flags,
+                                 appga_matrix** out) {
+  if (!ctx || !out) return fail(APPGA_EINVAL, "null context or out");
+  *out = nullptr;
+  if (n_side <= 0 || (int64_t)n_side * n_side != d)
+    return fail(APPGA_EINVAL, "d must equal n_side * n_side");
+  if (n_angles <= 0) return fail(APPGA_EINVAL, "n_angles must be > 0");
+  if (m <= 0) return fail(APPGA_EINVAL, "m must be > 0");
+  if ((flags & ~APPGA_A_BF16_COPY) != 0) return fail(APPGA_EINVAL, "unknown flags");
+  std::string why;
+  appga_status rc = appga::validate_csr(m, d, row_ptr_host, col_host, val_host, &why);
+  if (rc != APPGA_OK) return fail(rc, why);
+  const int64_t nnz = row_ptr_host[m];
+  // padded sizes must stay below 2^31 for int32 offsets
+  if (nnz + 4ll * (m > d ? m : d) >= (1ll << 31))
+    return fail(APPGA_EINVAL, "nnz too large for int32 row offsets");
+  CK(cudaSetDevice(ctx->device));
+  appga::HostCSR at, pa, pt;
+  appga::transpose_csr(m, d, row_ptr_host, col_host, val_host, &at);
+  appga::pad_rows(m, d, row_ptr_host, col_host, val_host, 4, &pa);
+  appga::pad_rows(d, m, at.row_ptr.data(), at.col.data(), at.val.data(), 4, &pt);
+  // Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM); summed in FP64
+  std::vector<float> inv(d);
+  for (int32_t j = 0; j < d; ++j) {
+    double sum = 0.0;
+    for (int32_t p = at.row_ptr[j]; p < at.row_ptr[j + 1]; ++p) sum += (double)at.val[p];
+    inv[j] = (float)(1.0 / (sum > 0.0 ? sum : 1.0));
+  }
+  auto* M = new appga_matrix();
+  M->ctx = ctx;
+  M->m = m;
+  M->d = d;
+  M->n = n_side;
+  M->na = n_angles;
+  M->nnz = nnz;
+  M->has_bf16 = (flags & APPGA_A_BF16_COPY) ? 1 : 0;
+  rc = upload_csr(pa, M->has_bf16, &M->A, &M->bytes);
+  if (rc == APPGA_OK) rc = upload_csr(pt, M->has_bf16, &M->At, &M->bytes);
+  if (rc == APPGA_OK) {
+    cudaError_t e = dalloc(&M->inv_lambda, (size_t)d, &M->bytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(M->inv_lambda, inv.data(), (size_t)d * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(e, "inv_lambda");
+  }
+  if (rc != APPGA_OK) {
+    appga_matrix_destroy(M);
+    return rc;
+  }
+  *out = M;
+  return APPGA_OK;
+}
+
+appga_status appga_matrix_destroy(appga_matrix* M) {
+  if (!M) return APPGA_OK;
+  if (M->ctx) cudaSetDevice(M->ctx->device);
+  free_csr(M->A);
+  free_csr(M->At);
+  cudaFree(M->inv_lambda);
+  free_workspace(M->ws);
+  delete M;
+  return APPGA_OK;
+}
+
+appga_status appga_matrix_get_info(const appga_matrix* M, appga_matrix_info* out) {
+  if (!M || !out) return fail(APPGA_EINVAL, "null matrix or out");
+  out->m = M->m;
+  out->d = M->d;
+  out->n_side = M->n;
+  out->n_angles = M->na;
+  out->nnz = M->nnz;
+  out->nnz_padded_a = M->A.nnz_padded;
+  out->nnz_padded_t = M->At.nnz_padded;
+  out->has_bf16 = M->has_bf16;
+  out->device_bytes = M->bytes;
+  return APPGA_OK;
+}
+
+appga_status appga_forward_ratio(appga_ctx* ctx, const appga_matrix* mat, const float* f,
+                                 const float* g, const float* gamma, double* y_out, float* w_out,
+                                 double* data_out, void* stream) {
+  if (!ctx || !mat || !f || !g || !gamma || !y_out)
+    return fail(APPGA_EINVAL, "null argument");
+  auto* M = const_cast<appga_matrix*>(mat);
+  appga_status rc = ensure_workspace(M);
+  if (rc != APPGA_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  appga::FwdArgs a = fwd_args(M, false);
+  a.f[0] = f;
+  a.y[0] = y_out;
+  a.w = w_out;
+  a.g = g;
+  a.gamma = gamma;
+  a.st = M->ws.st_scratch;
+  a.partial = M->ws.partial_aux;
+  a.data_out = data_out;
+  a.loop = 0;
+  a.want_data = data_out != nullptr ? 1 : 0;
+  CK(appga::launch_forward(a, 0, (cudaStream_t)stream));
+  return APPGA_OK;
+}
+
+appga_status appga_backproject(appga_ctx* ctx, const appga_matrix* mat, const float* w,
+                               float* out, void* stream) {
+  if (!ctx || !mat || !w || !out) return fail(APPGA_EINVAL, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  CK(appga::launch_backproject(mat->At, w, out, 0, (cudaStream_t)stream));
+  return APPGA_OK;
+}
+
+appga_status appga_shoitv_grad(appga_ctx* ctx, int32_t n_side, const float* f, double lambda1,
+                               double lambda2, double eps, float* out, void* stream) {
+  if (!ctx || !f || !out) return fail(APPGA_EINVAL, "null argument");
+  if (n_side <= 0) return fail(APPGA_EINVAL, "n_side must be > 0");
+  if (!(lambda1 >= 0) || !(lambda2 >= 0) || !(eps > 0))
+    return fail(APPGA_EINVAL, "need lambda1, lambda2 >= 0 and eps > 0");
+  CK(cudaSetDevice(ctx->device));
+  CK(appga::launch_shoitv_grad(n_side, f, (float)lambda1, (float)lambda2, (float)eps, out,
+                               (cudaStream_t)stream));
+  return APPGA_OK;
+}
+
+appga_status appga_pixel_update(appga_ctx* ctx, const appga_matrix* mat, const float* f_prev,
+                                const float* f_cur, const float* w, double theta,
+                                const appga_params* params, float* f_next, void* stream) {
+  if (!ctx || !mat || !f_prev || !f_cur || !w || !params || !f_next)
+    return fail(APPGA_EINVAL, "null argument");
+  appga_status rc = appga_params_validate(params);
+  if (rc != APPGA_OK) return rc;
+  auto* M = const_cast<appga_matrix*>(mat);
+  if ((rc = ensure_workspace(M)) != APPGA_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  SolverState h{};
+  h.k = 1;
+  h.k0 = 1;
+  h.k_last = 1 << 30;
+  h.theta = theta;
+  h.t_cur = 1.0;
+  CK(cudaMemcpyAsync(M->ws.st_scratch, &h, sizeof h, cudaMemcpyHostToDevice, s));
+  appga::PixArgs pa{};
+  pa.At = M->At;
+  pa.n = M->n;
+  pa.f[0] = const_cast<float*>(f_prev);
+  pa.f[1] = const_cast<float*>(f_cur);
+  pa.f[2] = f_next;
+  pa.w = w;
+  pa.inv_lambda = M->inv_lambda;
+  pa.pfreeze = M->ws.pfreeze;
+  pa.st = M->ws.st_scratch;
+  pa.partial = M->ws.partial_aux;
+  appga_params q = *params;
+  q.precond_freeze_iter = -1;
+  pa.ip = iter_params(&q, false);
+  pa.use_bf16 = bf16_requested(M, params) ? 1 : 0;
+  CK(appga::launch_pixel(pa, s));
+  return APPGA_OK;
+}
+
+appga_status appga_objective(appga_ctx* ctx, const appga_matrix* mat, const float* f,
+                             const float* g, const float* gamma, const appga_params* params,
+                             double* phi_out_host, void* stream) {
+  if (!ctx || !mat || !f || !g || !gamma || !params || !phi_out_host)
+    return fail(APPGA_EINVAL, "null argument");
+  appga_status rc = appga_params_validate(params);
+  if (rc != APPGA_OK) return rc;
+  auto* M = const_cast<appga_matrix*>(mat);
+  if ((rc = ensure_workspace(M)) != APPGA_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  return objective_on(M, f, g, gamma, params, phi_out_host, (cudaStream_t)stream);
+}
+
+appga_status appga_initial_image(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                                 const float* gamma, float* f_out, void* stream) {
+  if (!ctx || !mat || !g || !gamma || !f_out) return fail(APPGA_EINVAL, "null argument");
+  auto* M = const_cast<appga_matrix*>(mat);
+  appga_status rc = ensure_workspace(M);
+  if (rc != APPGA_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->ws.partial_aux,
+                                 M->ws.st_scratch, f_out, (cudaStream_t)stream));
+  return APPGA_OK;
+}
+
+appga_status appga_reconstruct(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                               const float* gamma, const float* f_init,
+                               const appga_params* params, float* f_out,
+                               appga_stats* stats_host, void* stream) {
+  return solve_common(ctx, const_cast<appga_matrix*>(mat), g, gamma, nullptr, f_init, 1, params,
+                      nullptr, f_out, stats_host, stream, true);
+}
+
+appga_status appga_resume(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                          const float* gamma, const float* f_prev, const float* f_cur,
+                          int32_t k0, const appga_params* params, float* f_out_prev,
+                          float* f_out, appga_stats* stats_host, void* stream) {
+  return solve_common(ctx, const_cast<appga_matrix*>(mat), g, gamma, f_prev, f_cur, k0, params,
+                      f_out_prev, f_out, stats_host, stream, false);
+}
+
+appga_status appga_validate_csr_host(int32_t m, int32_t d, const int32_t* row_ptr_host,
+                                     const int32_t* col_host, const float* val_host) {
+  std::string why;
+  appga_status rc = appga::validate_csr(m, d, row_ptr_host, col_host, val_host, &why);
+  if (rc != APPGA_OK) return fail(rc, why);
+  return APPGA_OK;
+}
+
+appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                                const float* gamma, const appga_params* params, int32_t n_iters,
+                                double* ms_pixel_host, double* ms_forward_host) {
+  if (!ms_pixel_host || !ms_forward_host) return fail(APPGA_EINVAL, "null output");
+  if (n_iters < 1 || n_iters > 4096) return fail(APPGA_EINVAL, "n_iters must be in [1, 4096]");
+  auto* M = const_cast<appga_matrix*>(mat);
+  appga_status rc = check_params_and_mat(ctx, M, params);
+  if (rc != APPGA_OK) return rc;
+  if (!g || !gamma) return fail(APPGA_EINVAL, "null argument");
+  if ((rc = ensure_workspace(M)) != APPGA_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Workspace& ws = M->ws;
+  appga_params q = *params;
+  q.max_iters = n_iters;
+  q.rel_obj_tol = 0.0;
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, ws.partial_aux, ws.st_scratch,
+                                 ws.f[1], s));
+  CK(cudaMemcpyAsync(ws.f[0], ws.f[1], (size_t)M->d * 4, cudaMemcpyDeviceToDevice, s));
+  appga::FwdArgs fa;
+  appga::PixArgs pa;
+  if ((rc = setup_run(M, g, gamma, 1, &q, &fa, &pa)) != APPGA_OK) return rc;
+  const bool track = q.track_objective != 0;
+  std::vector<cudaEvent_t> ev((size_t)2 * n_iters + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  for (int i = 0; i < n_iters && e == cudaSuccess; ++i) {
+    e = appga::launch_pixel(pa, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], s);
+    if (e == cudaSuccess) e = appga::launch_forward(fa, track, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 2], s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  double tp = 0.0, tf = 0.0;
+  for (int i = 0; i < n_iters && e == cudaSuccess; ++i) {
+    float a = 0.f, b = 0.f;
+    e = cudaEventElapsedTime(&a, ev[2 * i], ev[2 * i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2 * i + 1], ev[2 * i + 2]);
+    tp += a;
+    tf += b;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel timing");
+  *ms_pixel_host = tp / n_iters;
+  *ms_forward_host = tf / n_iters;
+  return APPGA_OK;
+}
+
+appga_status appga_reconstruct_host(appga_ctx* ctx, const appga_matrix* mat, const float* g_host,
+                                    const float* gamma_host, const float* f_init_host,
+                                    const appga_params* params, float* f_out_host,
+                                    appga_stats* stats_host, void* stream) {
+  if (!ctx || !mat || !g_host || !gamma_host || !params || !f_out_host)
+    return fail(APPGA_EINVAL, "null argument");
+  auto* M = const_cast<appga_matrix*>(mat);
+  appga_status rc = ensure_workspace(M);
+  if (rc != APPGA_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  Workspace& ws = M->ws;
+  int64_t* b = &M->bytes;
+  if (ws.d_g == nullptr) {
+    cudaError_t e = dalloc(&ws.d_g, (size_t)M->m, b);
+    if (e == cudaSuccess) e = dalloc(&ws.d_gamma, (size_t)M->m, b);
+    if (e == cudaSuccess) e = dalloc(&ws.d_finit, (size_t)M->d, b);
+    if (e == cudaSuccess) e = dalloc(&ws.d_fout, (size_t)M->d, b);
+    if (e != cudaSuccess) return cuda_fail(e, "host-path staging buffers");
+  }
+  cudaStream_t us = (cudaStream_t)stream;
+  const size_t mb = (size_t)M->m * 4, db = (size_t)M->d * 4;
+  CK(cudaMemcpyAsync(ws.d_g, g_host, mb, cudaMemcpyHostToDevice, us));
+  CK(cudaMemcpyAsync(ws.d_gamma, gamma_host, mb, cudaMemcpyHostToDevice, us));
+  if (f_init_host) CK(cudaMemcpyAsync(ws.d_finit, f_init_host, db, cudaMemcpyHostToDevice, us));
+  rc = appga_reconstruct(ctx, mat, ws.d_g, ws.d_gamma, f_init_host ? ws.d_finit : nullptr, params,
+                         ws.d_fout, stats_host, stream);
+  if (rc != APPGA_OK && rc != APPGA_ENUMERIC) return rc;
+  CK(cudaMemcpyAsync(f_out_host, ws.d_fout, db, cudaMemcpyDeviceToHost, us));
+  CK(cudaStreamSynchronize(us));
+  return rc;
+}
+
+}  // extern "C"

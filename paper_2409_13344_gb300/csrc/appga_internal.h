@@ -1,0 +1,136 @@
+// Internal declarations shared by the host API and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "appga.h"
+
+namespace appga {
+
+// Poisson-ratio denominator guard: den = max(y + gamma, KAPPA * gamma).
+constexpr double KAPPA = 1e-3;
+
+// Rows of a CSR stored on the device, each row padded with (col = last
+// column of the row, val = 0) to a multiple of 4 entries so every row starts
+// on a 16-byte boundary and can be streamed with 128-bit loads.
+struct DevCSR {
+  int32_t rows = 0, cols = 0;
+  int64_t nnz_padded = 0;
+  int32_t* row_ptr = nullptr;    // rows + 1 padded offsets
+  int32_t* col = nullptr;        // nnz_padded
+  float* val = nullptr;          // nnz_padded
+  uint16_t* val_bf16 = nullptr;  // nnz_padded (optional BF16 copy)
+};
+
+// Device-resident iteration state of one solve.  Kernels derive buffer
+// indices and the momentum scalar from it, so captured graphs replay
+// unchanged from one iteration to the next.
+struct SolverState {
+  int32_t k;          // index of the current iterate f^k
+  int32_t k_last;     // last pixel-phase index to run
+  int32_t k0;         // first index of this run
+  int32_t done;       // set once the run is finished
+  int32_t result_k;   // index of the returned iterate
+  int32_t stopped_early;
+  int32_t flags;      // APPGA_FLAG_* (sticky)
+  int32_t pad0;
+  double theta;       // theta_k for the current k (FP64)
+  double t_cur;       // t_k (Nesterov recursion)
+  double data_term;   // F(f^k) = sum y - g ln(y + gamma)
+  double phi_cur;     // Phi(f^k)
+  double phi_prev;    // Phi(f^{k-1})
+  unsigned long long guard_hits;
+  unsigned int ticket_p;
+  unsigned int ticket_r;
+  unsigned int ticket_aux;
+  unsigned int pad1;
+};
+
+struct IterParams {
+  float lambda1, lambda2, eps, beta;
+  double omega, a, b, rel_tol;
+  int32_t momentum;
+  int32_t freeze_iter;
+  int32_t track;  // evaluate Phi on the device each iteration
+  int32_t pad;
+};
+
+// Forward-projection kernel arguments (steps a1, a2 and the data term).
+struct FwdArgs {
+  DevCSR A;
+  const float* f[3];   // iterate ring (loop) / f in slot 0 (standalone)
+  double* y[2];        // projection ring (loop) / y_out in slot 0
+  float* w;            // back-projection weight 1 - g/den (may be null)
+  const float* g;
+  const float* gamma;
+  SolverState* st;
+  double* partial;     // one double per block
+  double* data_out;    // standalone: where the data term goes (may be null)
+  int32_t loop;        // 1: solver loop mode, 0: standalone
+  int32_t want_data;   // evaluate sum y - g ln(y + gamma)
+  int32_t use_bf16;
+  int32_t pad;
+};
+
+// Fused pixel-phase arguments (steps a0, a3, a4, a5).
+struct PixArgs {
+  DevCSR At;
+  int32_t n;           // image side
+  float* f[3];         // iterate ring: f^{k-1}, f^k read; f^{k+1} written
+  const float* w;      // back-projection weight
+  const float* inv_lambda;
+  float* pfreeze;      // frozen f^{K_P} (may be null)
+  SolverState* st;
+  double* partial;
+  IterParams ip;
+  int32_t use_bf16;
+  int32_t pad;
+};
+
+// ---- launchers (kernels.cu) ----
+int fwd_grid(int m);
+int pix_grid_x(int n);
+int pix_grid_y(int n);
+int max_partials(int m, int n);
+
+cudaError_t launch_forward(const FwdArgs& a, int track, cudaStream_t s);
+cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s);
+cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
+                               cudaStream_t s);
+cudaError_t launch_shoitv_grad(int n, const float* f, float lam1, float lam2, float eps,
+                               float* out, cudaStream_t s);
+cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float eps,
+                            double* partial, SolverState* st, double* out, cudaStream_t s);
+cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, const float* f,
+                                   int d, int* flag, cudaStream_t s);
+cudaError_t launch_init_momentum(SolverState* st, int k0, int momentum, double a, double b,
+                                 double omega, cudaStream_t s);
+cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
+                                 double* partial, SolverState* st, float* f_out, cudaStream_t s);
+
+// ---- host CSR helpers (csr_host.cpp) ----
+struct HostCSR {
+  int32_t rows = 0, cols = 0;
+  std::vector<int32_t> row_ptr, col;
+  std::vector<float> val;
+};
+// Checks a CSR and returns APPGA_OK or EINVAL/EDOMAIN with a message.
+appga_status validate_csr(int32_t m, int32_t d, const int32_t* row_ptr, const int32_t* col,
+                          const float* val, std::string* why);
+// Stable transpose (counting sort by column): rows of the result keep the
+// original row order.
+void transpose_csr(int32_t m, int32_t d, const int32_t* row_ptr, const int32_t* col,
+                   const float* val, HostCSR* out);
+// Pads each row to a multiple of `mult` entries (col = last col, val = 0).
+void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t* col,
+              const float* val, int mult, HostCSR* out);
+// Round-to-nearest-even FP32 -> BF16 bits.
+uint16_t float_to_bf16(float x);
+
+void set_error(const std::string& msg);
+
+}  // namespace appga

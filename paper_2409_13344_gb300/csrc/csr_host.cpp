@@ -1,0 +1,109 @@
+// Host-side CSR utilities: validation, stable transpose, row padding and the
+// FP32 -> BF16 rounding of A's values.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "appga_internal.h"
+
+namespace appga {
+
+appga_status validate_csr(int32_t m, int32_t d, const int32_t* row_ptr, const int32_t* col,
+                          const float* val, std::string* why) {
+  if (m < 0 || d <= 0) {
+    *why = "matrix shape must have m >= 0 and d > 0";
+    return APPGA_EINVAL;
+  }
+  if (row_ptr == nullptr) {
+    *why = "row_ptr is NULL";
+    return APPGA_EINVAL;
+  }
+  if (row_ptr[0] != 0) {
+    *why = "row_ptr[0] must be 0";
+    return APPGA_EINVAL;
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) {
+      *why = "row_ptr must be nondecreasing (row " + std::to_string(i) + ")";
+      return APPGA_EINVAL;
+    }
+  }
+  const int64_t nnz = row_ptr[m];
+  if (nnz > 0 && (col == nullptr || val == nullptr)) {
+    *why = "col or val is NULL";
+    return APPGA_EINVAL;
+  }
+  for (int64_t p = 0; p < nnz; ++p) {
+    if (col[p] < 0 || col[p] >= d) {
+      *why = "column index out of range at entry " + std::to_string(p);
+      return APPGA_EINVAL;
+    }
+    const float v = val[p];
+    if (!std::isfinite(v) || v < 0.f) {
+      *why = "A must have finite nonnegative entries (entry " + std::to_string(p) + ")";
+      return APPGA_EDOMAIN;
+    }
+  }
+  return APPGA_OK;
+}
+
+void transpose_csr(int32_t m, int32_t d, const int32_t* row_ptr, const int32_t* col,
+                   const float* val, HostCSR* out) {
+  const int64_t nnz = row_ptr[m];
+  out->rows = d;
+  out->cols = m;
+  out->row_ptr.assign((size_t)d + 1, 0);
+  out->col.resize((size_t)nnz);
+  out->val.resize((size_t)nnz);
+  for (int64_t p = 0; p < nnz; ++p) out->row_ptr[(size_t)col[p] + 1]++;
+  for (int32_t j = 0; j < d; ++j) out->row_ptr[j + 1] += out->row_ptr[j];
+  std::vector<int32_t> next(out->row_ptr.begin(), out->row_ptr.end() - 1);
+  // rows visited in order -> each transposed row lists ray indices ascending
+  for (int32_t i = 0; i < m; ++i) {
+    for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+      const int32_t q = next[col[p]]++;
+      out->col[q] = i;
+      out->val[q] = val[p];
+    }
+  }
+}
+
+void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t* col,
+              const float* val, int mult, HostCSR* out) {
+  out->rows = rows;
+  out->cols = cols;
+  out->row_ptr.assign((size_t)rows + 1, 0);
+  int64_t total = 0;
+  for (int32_t i = 0; i < rows; ++i) {
+    const int32_t len = row_ptr[i + 1] - row_ptr[i];
+    const int32_t plen = (len + mult - 1) / mult * mult;
+    total += plen;
+    out->row_ptr[i + 1] = (int32_t)total;
+  }
+  out->col.assign((size_t)total, 0);
+  out->val.assign((size_t)total, 0.f);
+  for (int32_t i = 0; i < rows; ++i) {
+    const int32_t s = row_ptr[i], e = row_ptr[i + 1];
+    int32_t q = out->row_ptr[i];
+    for (int32_t p = s; p < e; ++p, ++q) {
+      out->col[q] = col[p];
+      out->val[q] = val[p];
+    }
+    const int32_t last = e > s ? col[e - 1] : 0;
+    for (; q < out->row_ptr[i + 1]; ++q) {
+      out->col[q] = last;  // same cache line as the row's last gather
+      out->val[q] = 0.f;
+    }
+  }
+}
+
+uint16_t float_to_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan (not expected)
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;  // round to nearest, ties to even
+  return (uint16_t)(u >> 16);
+}
+
+}  // namespace appga

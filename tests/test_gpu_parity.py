@@ -1,0 +1,465 @@
+"""GPU parity of every hot-path step and of the solver against the FP64
+oracle, through the C ABI (sm_103a library).
+
+Tolerances (derived in the design notes):
+  y = A f (double-float accumulation)        rel 1e-11 per bin
+  w = 1 - g/den (FP32 output)                rel 5e-7 per bin
+  A^T w (FP32 accumulation)                  |err| <= 2e-6 * (A^T |w|)_j
+  B^T grad phi~(B f) (FP32 stencil)          |err| <= 2e-6 (lam1 + lam2) + 1e-5 |ref|
+  one fused APPGA map                        rel L2 1e-6
+  Phi (FP64 objective on identical images)   rel 1e-9
+  APPGA trajectories, FP32 images            rel L2 1e-5
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import appga_oracle as O
+from paper_2409_13344_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2409_13344_gb300 import build
+    build.build()
+    from paper_2409_13344_gb300 import appga
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA device")
+    return appga
+
+
+@pytest.fixture(scope="module")
+def ctx(A):
+    c = A.Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+# a ragged geometry: N not a multiple of the 32-pixel tile, odd bin count
+RAGGED = W.Geometry(40, 48, 59)
+SPARSE = W.Geometry(16, 10, 8)      # many empty rows and never-hit pixels
+TINY = W.Geometry(1, 3, 3)          # d = 1: B = 0
+
+
+_cache = {}
+
+
+def problem(name_or_geom, counts=1e5, seed=None, phantom="ellipses"):
+    if isinstance(name_or_geom, str):
+        geom = W.GEOMETRIES[name_or_geom]
+        Amat = W.system_matrix(name_or_geom)
+    else:
+        geom = name_or_geom
+        key = (geom.n, geom.n_angles, geom.n_bins)
+        if key not in _cache:
+            _cache[key] = W.siddon_matrix(geom)
+        Amat = _cache[key]
+    seed = W.seed_for(1) if seed is None else seed
+    sl = W.make_slice(Amat, geom, counts, seed, phantom=phantom)
+    return geom, Amat, sl
+
+
+def to_dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.asarray(x), dtype=dtype).to(DEV)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def bf16_round(x):
+    """FP32 -> BF16 (round to nearest even) -> FP32, in NumPy."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def mats(A, ctx):
+    out = {}
+    for key in ("64", RAGGED, SPARSE, TINY):
+        geom, Amat, _ = problem(key)
+        out[key if isinstance(key, str) else (key.n, key.n_angles, key.n_bins)] = \
+            A.Matrix(ctx, Amat, geom.n, geom.n_angles, bf16=True)
+    yield out
+    for m in out.values():
+        m.close()
+
+
+def mkey(k):
+    return k if isinstance(k, str) else (k.n, k.n_angles, k.n_bins)
+
+
+GEOMS = ["64", RAGGED, SPARSE, TINY]
+
+
+# ------------------------------------------------------------- step a1-a2
+
+@pytest.mark.parametrize("gk", GEOMS, ids=["64", "ragged40", "sparse16", "tiny1"])
+def test_forward_ratio(A, ctx, mats, gk):
+    geom, Amat, sl = problem(gk)
+    mat = mats[mkey(gk)]
+    rng = np.random.default_rng(7)
+    f = (sl.f_true * rng.uniform(0.5, 1.5, geom.d)).astype(np.float32)
+    f[rng.uniform(size=geom.d) < 0.1] *= -40.0  # drive some bins into the guard
+    y = torch.empty(geom.m, dtype=torch.float64, device=DEV)
+    w = torch.empty(geom.m, dtype=torch.float32, device=DEV)
+    A.appga_forward_ratio(ctx.handle, mat.handle, to_dev(f), to_dev(sl.g), to_dev(sl.gamma), y, w)
+    torch.cuda.synchronize()
+    A64 = Amat.astype(np.float64)
+    y_ref = A64 @ f.astype(np.float64)
+    gam = sl.gamma.astype(np.float64)
+    den = np.maximum(y_ref + gam, O.KAPPA * gam)
+    w_ref = 1.0 - sl.g / den
+    yg = y.cpu().numpy()
+    np.testing.assert_allclose(yg, y_ref, rtol=1e-11, atol=1e-300)
+    np.testing.assert_allclose(w.cpu().numpy(), w_ref, rtol=5e-7, atol=1e-30)
+    assert np.any(y_ref + gam < O.KAPPA * gam) or gk is TINY or gk is SPARSE
+
+
+@pytest.mark.parametrize("gk", ["64", RAGGED], ids=["64", "ragged40"])
+def test_data_term(A, ctx, mats, gk):
+    geom, Amat, sl = problem(gk)
+    f = sl.f_true.astype(np.float32)
+    y = torch.empty(geom.m, dtype=torch.float64, device=DEV)
+    data = torch.zeros(1, dtype=torch.float64, device=DEV)
+    A.appga_forward_ratio(ctx.handle, mats[mkey(gk)].handle, to_dev(f), to_dev(sl.g),
+                          to_dev(sl.gamma), y, None, data)
+    torch.cuda.synchronize()
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    ref = prob.fidelity(f.astype(np.float64))
+    assert abs(float(data.item()) - ref) <= 1e-11 * abs(ref)
+
+
+# ------------------------------------------------------------------ step a3
+
+@pytest.mark.parametrize("gk", GEOMS, ids=["64", "ragged40", "sparse16", "tiny1"])
+def test_backproject(A, ctx, mats, gk):
+    geom, Amat, _ = problem(gk)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(-1, 1, geom.m).astype(np.float32)
+    out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    A.appga_backproject(ctx.handle, mats[mkey(gk)].handle, to_dev(w), out)
+    torch.cuda.synchronize()
+    At = Amat.astype(np.float64).T.tocsr()
+    ref = At @ w.astype(np.float64)
+    scale = At @ np.abs(w.astype(np.float64))
+    err = np.abs(out.cpu().numpy() - ref)
+    assert np.all(err <= 2e-6 * scale + 1e-30)
+
+
+def test_adjoint_identity_device(A, ctx, mats):
+    # <A x, z> = <x, A^T z> with both products from the device kernels
+    geom, Amat, sl = problem("64")
+    mat = mats["64"]
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 1, geom.d).astype(np.float32)
+    z = rng.uniform(-1, 1, geom.m).astype(np.float32)
+    y = torch.empty(geom.m, dtype=torch.float64, device=DEV)
+    A.appga_forward_ratio(ctx.handle, mat.handle, to_dev(x), to_dev(sl.g), to_dev(sl.gamma), y)
+    bt = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    A.appga_backproject(ctx.handle, mat.handle, to_dev(z), bt)
+    torch.cuda.synchronize()
+    lhs = float(np.dot(y.cpu().numpy(), z.astype(np.float64)))
+    rhs = float(np.dot(x.astype(np.float64), bt.cpu().numpy().astype(np.float64)))
+    assert abs(lhs - rhs) <= 1e-5 * np.sum(np.abs(z)) * np.max(y.cpu().numpy())
+
+
+# ------------------------------------------------------------------ step a4
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 33, 64, 100])
+@pytest.mark.parametrize("eps", [1e-3, 0.3])
+def test_shoitv_grad(A, ctx, n, eps):
+    rng = np.random.default_rng(n)
+    F = rng.uniform(0, 1, (n, n))
+    F[: n // 2, : n // 3] = 0.25          # flat block: quadratic branch of s_eps
+    F = F.astype(np.float32)
+    lam1, lam2 = 0.1, 0.05
+    out = torch.empty(n * n, dtype=torch.float32, device=DEV)
+    A.appga_shoitv_grad(ctx.handle, n, to_dev(F.reshape(-1)), lam1, lam2, eps, out)
+    torch.cuda.synchronize()
+    B = O.b_matrix(n)
+    ref = B.T @ O.grad_phi_tilde(B @ F.reshape(-1).astype(np.float64), n * n, lam1, lam2, eps)
+    err = np.abs(out.cpu().numpy() - ref)
+    assert np.all(err <= 2e-6 * (lam1 + lam2) + 1e-5 * np.abs(ref)), float(err.max())
+
+
+def test_shoitv_adjoint_symmetry(A, ctx):
+    # transposing the image transposes B^T grad phi~(B f) (block swap 3<->5, 4<->6)
+    n = 48
+    rng = np.random.default_rng(5)
+    F = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    outs = []
+    for X in (F, np.ascontiguousarray(F.T)):
+        o = torch.empty(n * n, dtype=torch.float32, device=DEV)
+        A.appga_shoitv_grad(ctx.handle, n, to_dev(X.reshape(-1)), 0.2, 0.1, 1e-2, o)
+        outs.append(o.cpu().numpy().reshape(n, n))
+    np.testing.assert_allclose(outs[0], outs[1].T, atol=2e-6)
+
+
+# ----------------------------------------------------- fused map a0+a3+a4+a5
+
+@pytest.mark.parametrize("gk", ["64", RAGGED, SPARSE], ids=["64", "ragged40", "sparse16"])
+def test_pixel_update(A, ctx, mats, gk):
+    geom, Amat, sl = problem(gk)
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    rng = np.random.default_rng(2)
+    f_cur = (sl.f_true * rng.uniform(0.8, 1.2, geom.d) + 1e-3).astype(np.float32)
+    f_prev = (sl.f_true * rng.uniform(0.8, 1.2, geom.d) + 1e-3).astype(np.float32)
+    theta = 0.7
+    f_tl = f_cur.astype(np.float64) + theta * (f_cur.astype(np.float64) - f_prev)
+    y = prob.A @ f_tl
+    den = np.maximum(y + prob.gamma, O.KAPPA * prob.gamma)
+    w = (1.0 - prob.g / den).astype(np.float32)
+    p = A.default_params(lambda1=0.1, lambda2=0.05, eps=1e-3, beta=1.0)
+    out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    A.appga_pixel_update(ctx.handle, mats[mkey(gk)].handle, to_dev(f_prev), to_dev(f_cur),
+                         to_dev(w), theta, p, out)
+    torch.cuda.synchronize()
+    grad = prob.At @ w.astype(np.float64) + prob.Bt @ O.grad_phi_tilde(
+        prob.B @ f_tl, prob.d, 0.1, 0.05, 1e-3)
+    ref = np.maximum(f_tl - 1.0 * f_cur / prob.em_lambda() * grad, 0.0)
+    assert rel_l2(out.cpu().numpy(), ref) <= 1e-6
+
+
+# ------------------------------------------------------------------ step a6
+
+@pytest.mark.parametrize("gk", ["64", RAGGED, "256"], ids=["64", "ragged40", "256"])
+def test_objective(A, ctx, gk):
+    geom, Amat, sl = problem(gk, counts=1e6 if gk == "256" else 1e5)
+    mat = A.Matrix(ctx, Amat, geom.n, geom.n_angles)
+    rng = np.random.default_rng(9)
+    f = (sl.f_true * rng.uniform(0.9, 1.1, geom.d)).astype(np.float32)
+    p = A.default_params(lambda1=0.1, lambda2=0.05, eps=1e-3)
+    phi = A.appga_objective(ctx.handle, mat.handle, to_dev(f), to_dev(sl.g), to_dev(sl.gamma), p)
+    ref = O.Problem(Amat, sl.g, sl.gamma, geom.n).objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(phi - ref) <= 1e-9 * abs(ref), (phi, ref)
+    mat.close()
+
+
+def test_initial_image(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    A.appga_initial_image(ctx.handle, mats["64"].handle, to_dev(sl.g), to_dev(sl.gamma), out)
+    torch.cuda.synchronize()
+    ref = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(got > 0, ref > 0)
+    np.testing.assert_allclose(got, ref, rtol=1e-7)
+
+
+# ---------------------------------------------------------------- solver
+
+def run_gpu(A, ctx, mat, sl, **kw):
+    p = A.default_params(**kw)
+    f = torch.empty(mat.d, dtype=torch.float32, device=DEV)
+    st = A.appga_reconstruct(ctx.handle, mat.handle, to_dev(sl.g), to_dev(sl.gamma), None, p, f)
+    return f.cpu().numpy(), st
+
+
+def run_oracle(geom, Amat, sl, **kw):
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    par = O.Params(**kw)
+    return prob, O.appga(prob, par, n_angles=geom.n_angles, track_phi=par.rel_obj_tol > 0)
+
+
+@pytest.mark.parametrize("omega", [0.25, 0.5, 1.0])
+def test_trajectory_64_short(A, ctx, mats, omega):
+    geom, Amat, sl = problem("64")
+    f, st = run_gpu(A, ctx, mats["64"], sl, max_iters=30, omega=omega, track_objective=1)
+    prob, ref = run_oracle(geom, Amat, sl, max_iters=30, omega=omega)
+    assert st.iters == 30 and st.result_k == 31
+    assert rel_l2(f, ref.f) <= 1e-5
+    phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+
+
+@pytest.mark.parametrize("gk", ["64", RAGGED, SPARSE], ids=["64", "ragged40", "sparse16"])
+def test_trajectory_long_small_step(A, ctx, mats, gk):
+    # beta = 0.1 keeps p_max within the step-size condition on the small grids
+    geom, Amat, sl = problem(gk)
+    f, st = run_gpu(A, ctx, mats[mkey(gk)], sl, max_iters=150, beta=0.1, omega=1.0)
+    _, ref = run_oracle(geom, Amat, sl, max_iters=150, beta=0.1, omega=1.0)
+    assert rel_l2(f, ref.f) <= 1e-5
+
+
+def test_trajectory_tiny(A, ctx, mats):
+    geom, Amat, sl = problem(TINY)
+    f, st = run_gpu(A, ctx, mats[mkey(TINY)], sl, max_iters=20)
+    _, ref = run_oracle(geom, Amat, sl, max_iters=20)
+    assert rel_l2(f, ref.f) <= 1e-6
+
+
+@pytest.mark.parametrize("momentum,mname", [(1, "none"), (2, "nesterov")])
+def test_momentum_variants(A, ctx, mats, momentum, mname):
+    geom, Amat, sl = problem("64")
+    f, _ = run_gpu(A, ctx, mats["64"], sl, max_iters=40, momentum=momentum)
+    _, ref = run_oracle(geom, Amat, sl, max_iters=40, momentum=mname)
+    assert rel_l2(f, ref.f) <= 1e-5
+
+
+def test_preconditioner_freeze(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    f, _ = run_gpu(A, ctx, mats["64"], sl, max_iters=40, precond_freeze_iter=6)
+    _, ref = run_oracle(geom, Amat, sl, max_iters=40, precond_freeze_iter=6)
+    assert rel_l2(f, ref.f) <= 1e-5
+
+
+def test_stopping_rule(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    tol = 1e-6
+    f, st = run_gpu(A, ctx, mats["64"], sl, max_iters=400, beta=0.1, omega=1.0, rel_obj_tol=tol,
+                    graph_iters=8)
+    prob, ref = run_oracle(geom, Amat, sl, max_iters=400, beta=0.1, omega=1.0, rel_obj_tol=tol)
+    assert st.stopped_early == 1 and ref.iters < 400
+    assert abs(st.iters - ref.iters) <= 1
+    if st.iters == ref.iters:
+        assert rel_l2(f, ref.f) <= 1e-5
+    phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+
+
+def test_guard_hits_counted(A, ctx, mats):
+    # resume from a state whose extrapolation f~ is strongly negative somewhere
+    geom, Amat, sl = problem("64")
+    rng = np.random.default_rng(4)
+    f_cur = np.maximum(sl.f_true, 1e-3).astype(np.float32)
+    f_prev = f_cur.copy()
+    hot = rng.uniform(size=geom.d) < 0.05
+    f_prev[hot] += 60.0 * f_cur.max()
+    p = A.default_params(max_iters=1, omega=1.0)
+    out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    k0 = 50
+    st = A.appga_resume(ctx.handle, mats["64"].handle, to_dev(sl.g), to_dev(sl.gamma),
+                        to_dev(f_prev), to_dev(f_cur), k0, p, None, out)
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    th = O.gn_theta(k0, 0.125, 1.0, 1.0)
+    f_next, hits = O.appga_step(prob, f_cur.astype(np.float64), f_prev.astype(np.float64), th,
+                                O.Params(), prob.em_lambda())
+    assert hits > 0 and st.guard_hits == hits
+    assert rel_l2(out.cpu().numpy(), f_next) <= 1e-5
+
+
+def test_resume_is_bitwise_continuation(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    mat = mats["64"]
+    g, gamma = to_dev(sl.g), to_dev(sl.gamma)
+    p40 = A.default_params(max_iters=40)
+    full = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    A.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, p40, full)
+    p20 = A.default_params(max_iters=20)
+    a_prev = torch.empty_like(full)
+    a_cur = torch.empty_like(full)
+    # first half from the initial image
+    f_init = torch.empty_like(full)
+    A.appga_initial_image(ctx.handle, mat.handle, g, gamma, f_init)
+    st1 = A.appga_resume(ctx.handle, mat.handle, g, gamma, f_init, f_init, 1, p20, a_prev, a_cur)
+    assert st1.result_k == 21
+    out = torch.empty_like(full)
+    st2 = A.appga_resume(ctx.handle, mat.handle, g, gamma, a_prev, a_cur, 21, p20, None, out)
+    assert st2.result_k == 41
+    assert torch.equal(out, full)
+
+
+def test_deterministic_and_host_entry(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    mat = mats["64"]
+    p = A.default_params(max_iters=25, track_objective=1)
+    f1, s1 = run_gpu(A, ctx, mat, sl, max_iters=25, track_objective=1)
+    f2, s2 = run_gpu(A, ctx, mat, sl, max_iters=25, track_objective=1)
+    np.testing.assert_array_equal(f1, f2)
+    assert s1.phi == s2.phi
+    out = np.empty(geom.d, np.float32)
+    s3 = A.appga_reconstruct_host(ctx.handle, mat.handle, sl.g, sl.gamma, None, p, out)
+    np.testing.assert_array_equal(out, f1)
+    assert s3.phi == s1.phi
+
+
+@pytest.mark.parametrize("what", ["g_nan", "g_neg", "gamma_zero", "f_neg"])
+def test_invalid_inputs_rejected(A, ctx, mats, what):
+    geom, Amat, sl = problem("64")
+    g = sl.g.copy()
+    gamma = sl.gamma.copy()
+    f_init = None
+    if what == "g_nan":
+        g[5] = np.nan
+    elif what == "g_neg":
+        g[5] = -1.0
+    elif what == "gamma_zero":
+        gamma[7] = 0.0
+    else:
+        f_init = to_dev(np.full(geom.d, -1.0, np.float32))
+    p = A.default_params(max_iters=5)
+    out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    with pytest.raises(A.AppgaError) as ei:
+        A.appga_reconstruct(ctx.handle, mats["64"].handle, to_dev(g), to_dev(gamma), f_init, p, out)
+    assert ei.value.status == A.APPGA_EDOMAIN
+    # the context stays usable
+    f, st = run_gpu(A, ctx, mats["64"], sl, max_iters=3)
+    assert np.all(np.isfinite(f))
+
+
+def test_bf16_matrix(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    f, _ = run_gpu(A, ctx, mats["64"], sl, max_iters=30, a_precision=1)
+    _, ref32 = run_oracle(geom, Amat, sl, max_iters=30)
+    Ab = sp.csr_matrix((bf16_round(Amat.data), Amat.indices, Amat.indptr), shape=Amat.shape)
+    _, refb = run_oracle(geom, Ab, sl, max_iters=30)
+    assert rel_l2(f, refb.f) <= 1e-5
+    assert rel_l2(f, ref32.f) <= 1e-3
+
+
+def test_kernel_times(A, ctx, mats):
+    geom, Amat, sl = problem("64")
+    p = A.default_params(track_objective=1)
+    tp, tf = A.appga_kernel_times(ctx.handle, mats["64"].handle, to_dev(sl.g), to_dev(sl.gamma),
+                                  p, 20)
+    assert tp > 0 and tf > 0
+
+
+# ------------------------------------------------- full-size (256^2) parity
+
+@pytest.fixture(scope="module")
+def m256(A, ctx):
+    geom, Amat, _ = problem("256", counts=1e6)
+    mat = A.Matrix(ctx, Amat, geom.n, geom.n_angles, bf16=True)
+    yield mat
+    mat.close()
+
+
+def test_full_size_forward_and_backproject(A, ctx, m256):
+    geom, Amat, sl = problem("256", counts=1e6, phantom="lesions")
+    f = sl.f_true.astype(np.float32)
+    y = torch.empty(geom.m, dtype=torch.float64, device=DEV)
+    w = torch.empty(geom.m, dtype=torch.float32, device=DEV)
+    A.appga_forward_ratio(ctx.handle, m256.handle, to_dev(f), to_dev(sl.g), to_dev(sl.gamma), y, w)
+    bp = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    A.appga_backproject(ctx.handle, m256.handle, w, bp)
+    torch.cuda.synchronize()
+    A64 = Amat.astype(np.float64)
+    y_ref = A64 @ f.astype(np.float64)
+    np.testing.assert_allclose(y.cpu().numpy(), y_ref, rtol=1e-11, atol=1e-300)
+    wv = w.cpu().numpy().astype(np.float64)
+    ref = A64.T @ wv
+    assert np.all(np.abs(bp.cpu().numpy() - ref) <= 2e-6 * (A64.T @ np.abs(wv)) + 1e-30)
+
+
+@pytest.mark.parametrize("counts,omega,iters", [(1e6, 0.5, 500), (5e6, 1.0, 100), (1e6, 0.25, 100)])
+def test_full_size_trajectory(A, ctx, m256, counts, omega, iters):
+    # the benchmarked configuration: 256^2, 180 x 367, lesion phantom, objective tracked
+    geom, Amat, sl = problem("256", counts=counts, phantom="lesions")
+    f, st = run_gpu(A, ctx, m256, sl, max_iters=iters, omega=omega, track_objective=1)
+    prob, ref = run_oracle(geom, Amat, sl, max_iters=iters, omega=omega)
+    assert st.iters == iters
+    assert rel_l2(f, ref.f) <= 1e-5
+    phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)

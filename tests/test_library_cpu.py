@@ -1,0 +1,115 @@
+"""CPU-side checks of the C ABI library: it builds, loads, exports every
+function declared in include/appga.h, and its host-only logic (parameter
+validation, CSR validation, momentum scalar, status strings) behaves.  No
+call here touches a GPU."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_13344_gb300 import build
+    build.build()
+    from paper_2409_13344_gb300 import appga
+    return appga.load_library()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(appga_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header(lib):
+    from paper_2409_13344_gb300 import appga
+    assert set(_declared_functions()) <= set(appga.SIGNATURES)
+    for name in _declared_functions():
+        assert callable(getattr(appga, name, None)) or name in (
+            "appga_status_string", "appga_last_error", "appga_version", "appga_params_default"), name
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_2409_13344_gb300 import appga
+    assert ctypes.sizeof(appga.appga_params) == 96
+    assert ctypes.sizeof(appga.appga_stats) == 40
+    assert ctypes.sizeof(appga.appga_matrix_info) == 56
+
+
+def test_params_default_and_validate(lib):
+    from paper_2409_13344_gb300 import appga as A
+    p = A.default_params()
+    assert (p.lambda1, p.lambda2, p.eps, p.omega, p.a, p.b, p.beta) == (0.1, 0.05, 1e-3, 0.5, 0.125, 1.0, 1.0)
+    assert A.appga_params_validate(p) == A.APPGA_OK
+    bad = [dict(eps=0.0), dict(lambda1=-1.0), dict(beta=0.0), dict(omega=1.5), dict(omega=0.0),
+           dict(a=0.0), dict(omega=1.0, a=0.5), dict(max_iters=-1), dict(precond_freeze_iter=0),
+           dict(a_precision=7), dict(momentum=9), dict(rel_obj_tol=-1.0), dict(eps=math.nan),
+           dict(b=-0.125, omega=1.0)]  # b = -a*1 makes t_1 = 0
+    for kw in bad:
+        q = A.default_params(**kw)
+        assert A.appga_params_validate(q) == A.APPGA_EINVAL, kw
+        assert lib.appga_last_error()
+
+
+def test_gn_theta_host(lib):
+    from paper_2409_13344_gb300 import appga as A
+    for k in range(1, 50):
+        assert A.appga_gn_theta(k, 0.125, 1.0, 1.0) == pytest.approx((k - 1) / (k + 8), abs=1e-15)
+        assert A.appga_gn_theta(k, 0.125, 1.0, 0.5) == pytest.approx(
+            math.sqrt(k - 1) / (math.sqrt(k) + 8), abs=1e-15)
+
+
+def _csr_call(lib, m, d, rp, col, val):
+    rp = np.ascontiguousarray(rp, np.int32)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float32)
+    return lib.appga_validate_csr_host(m, d, rp.ctypes.data, col.ctypes.data, val.ctypes.data)
+
+
+def test_csr_validator_rejects_corruption(lib):
+    ok = ([0, 2, 2, 3], [0, 3, 1], [1.0, 0.5, 2.0])
+    assert _csr_call(lib, 3, 4, *ok) == 0
+    assert _csr_call(lib, 3, 4, [1, 2, 2, 3], ok[1], ok[2]) == 1          # row_ptr[0] != 0
+    assert _csr_call(lib, 3, 4, [0, 2, 1, 3], ok[1], ok[2]) == 1          # decreasing
+    assert _csr_call(lib, 3, 4, ok[0], [0, 4, 1], ok[2]) == 1             # col out of range
+    assert _csr_call(lib, 3, 4, ok[0], [0, -1, 1], ok[2]) == 1
+    assert _csr_call(lib, 3, 4, ok[0], ok[1], [1.0, -0.5, 2.0]) == 3      # negative entry
+    assert _csr_call(lib, 3, 4, ok[0], ok[1], [1.0, math.nan, 2.0]) == 3  # NaN entry
+    assert _csr_call(lib, 3, 4, ok[0], ok[1], [1.0, math.inf, 2.0]) == 3
+    assert "range" in lib.appga_last_error().decode() or lib.appga_last_error()
+
+
+def test_status_strings(lib):
+    lib.appga_status_string.restype = ctypes.c_char_p
+    for s in range(0, 9):
+        assert lib.appga_status_string(s)
+    assert lib.appga_status_string(3) == b"input outside the model's domain"
+
+
+def test_no_device_is_reported_not_crashed(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2409_13344_gb300 import appga as A
+    with pytest.raises(A.AppgaError) as ei:
+        A.appga_ctx_create(0)
+    assert ei.value.status == A.APPGA_ENODEV
