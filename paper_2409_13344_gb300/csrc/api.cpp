@@ -62,9 +62,11 @@ struct appga_matrix {
   int32_t m = 0, d = 0, n = 0, na = 0;
   int64_t nnz = 0;
   DevCSR A, At;
-  float* inv_lambda = nullptr;
+  float* inv_lambda = nullptr;       // 1/Lambda of the FP32 values
+  float* inv_lambda_bf16 = nullptr;  // 1/Lambda of the BF16-rounded values
   int32_t has_bf16 = 0;
   int64_t bytes = 0;
+  long long npfov = 0;  // pixels of the initial-image disk
   Workspace ws;
 };
 
@@ -286,7 +288,7 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.n = M->n;
   for (int i = 0; i < 3; ++i) pa.f[i] = ws.f[i];
   pa.w = ws.w;
-  pa.inv_lambda = M->inv_lambda;
+  pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = ws.pfreeze;
   pa.st = ws.st;
   pa.partial = ws.partial_p;
@@ -487,7 +489,7 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
     if (f_cur) {
       CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
     } else {
-      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, ws.partial_aux, ws.st_scratch,
+      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.st_scratch,
                                      slot_cur, s));
     }
     CK(cudaMemcpyAsync(slot_prev, slot_cur, fb, cudaMemcpyDeviceToDevice, s));
@@ -652,12 +654,24 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
   appga::transpose_csr(m, d, row_ptr_host, col_host, val_host, &at);
   appga::pad_rows(m, d, row_ptr_host, col_host, val_host, 4, &pa);
   appga::pad_rows(d, m, at.row_ptr.data(), at.col.data(), at.val.data(), 4, &pt);
-  // Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM); summed in FP64
-  std::vector<float> inv(d);
+  // Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM); summed in FP64, once
+  // for the FP32 values and once for their BF16 rounding (the BF16 run is the
+  // method applied to the rounded matrix, preconditioner included)
+  const bool want_bf16 = (flags & APPGA_A_BF16_COPY) != 0;
+  std::vector<float> inv(d), inv_b(want_bf16 ? d : 0);
   for (int32_t j = 0; j < d; ++j) {
-    double sum = 0.0;
-    for (int32_t p = at.row_ptr[j]; p < at.row_ptr[j + 1]; ++p) sum += (double)at.val[p];
+    double sum = 0.0, sum_b = 0.0;
+    for (int32_t p = at.row_ptr[j]; p < at.row_ptr[j + 1]; ++p) {
+      sum += (double)at.val[p];
+      if (want_bf16) {
+        const uint32_t bits = (uint32_t)appga::float_to_bf16(at.val[p]) << 16;
+        float vb;
+        std::memcpy(&vb, &bits, 4);
+        sum_b += (double)vb;
+      }
+    }
     inv[j] = (float)(1.0 / (sum > 0.0 ? sum : 1.0));
+    if (want_bf16) inv_b[j] = (float)(1.0 / (sum_b > 0.0 ? sum_b : 1.0));
   }
   auto* M = new appga_matrix();
   M->ctx = ctx;
@@ -667,12 +681,16 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
   M->na = n_angles;
   M->nnz = nnz;
   M->has_bf16 = (flags & APPGA_A_BF16_COPY) ? 1 : 0;
+  M->npfov = appga::disk_pixels(n_side);
   rc = upload_csr(pa, M->has_bf16, &M->A, &M->bytes);
   if (rc == APPGA_OK) rc = upload_csr(pt, M->has_bf16, &M->At, &M->bytes);
   if (rc == APPGA_OK) {
     cudaError_t e = dalloc(&M->inv_lambda, (size_t)d, &M->bytes);
     if (e == cudaSuccess)
       e = cudaMemcpy(M->inv_lambda, inv.data(), (size_t)d * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && want_bf16) e = dalloc(&M->inv_lambda_bf16, (size_t)d, &M->bytes);
+    if (e == cudaSuccess && want_bf16)
+      e = cudaMemcpy(M->inv_lambda_bf16, inv_b.data(), (size_t)d * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) rc = cuda_fail(e, "inv_lambda");
   }
   if (rc != APPGA_OK) {
@@ -689,6 +707,7 @@ appga_status appga_matrix_destroy(appga_matrix* M) {
   free_csr(M->A);
   free_csr(M->At);
   cudaFree(M->inv_lambda);
+  cudaFree(M->inv_lambda_bf16);
   free_workspace(M->ws);
   delete M;
   return APPGA_OK;
@@ -777,7 +796,7 @@ appga_status appga_pixel_update(appga_ctx* ctx, const appga_matrix* mat, const f
   pa.f[1] = const_cast<float*>(f_cur);
   pa.f[2] = f_next;
   pa.w = w;
-  pa.inv_lambda = M->inv_lambda;
+  pa.inv_lambda = bf16_requested(M, params) ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = M->ws.pfreeze;
   pa.st = M->ws.st_scratch;
   pa.partial = M->ws.partial_aux;
@@ -809,7 +828,7 @@ appga_status appga_initial_image(appga_ctx* ctx, const appga_matrix* mat, const 
   appga_status rc = ensure_workspace(M);
   if (rc != APPGA_OK) return rc;
   CK(cudaSetDevice(ctx->device));
-  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->ws.partial_aux,
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, M->ws.partial_aux,
                                  M->ws.st_scratch, f_out, (cudaStream_t)stream));
   return APPGA_OK;
 }
@@ -854,7 +873,7 @@ appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const f
   appga_params q = *params;
   q.max_iters = n_iters;
   q.rel_obj_tol = 0.0;
-  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, ws.partial_aux, ws.st_scratch,
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.st_scratch,
                                  ws.f[1], s));
   CK(cudaMemcpyAsync(ws.f[0], ws.f[1], (size_t)M->d * 4, cudaMemcpyDeviceToDevice, s));
   appga::FwdArgs fa;

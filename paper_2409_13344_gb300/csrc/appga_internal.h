@@ -109,8 +109,10 @@ cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, co
                                    int d, int* flag, cudaStream_t s);
 cudaError_t launch_init_momentum(SolverState* st, int k0, int momentum, double a, double b,
                                  double omega, cudaStream_t s);
+long long disk_pixels(int n);
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
-                                 double* partial, SolverState* st, float* f_out, cudaStream_t s);
+                                 long long npfov, double* partial, SolverState* st, float* f_out,
+                                 cudaStream_t s);
 
 // ---- host CSR helpers (csr_host.cpp) ----
 struct HostCSR {

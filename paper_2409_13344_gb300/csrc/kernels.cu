@@ -179,49 +179,168 @@ __device__ double sum_partials(const double* partial) {
 }
 
 // ------------------------------------------------------------ projectors
+//
+// A warp owns R consecutive CSR rows, whose (row-padded) entries form one
+// contiguous range.  It streams that range linearly in 128-entry chunks
+// (one 4-entry pack per lane; row padding keeps every pack inside a single
+// row), loading chunk t+1 while it gathers and accumulates chunk t.  Each
+// lane accumulates into its current row and, when its row changes, parks the
+// partial in a per-warp shared-memory slot [row][lane]; lane q then sums the
+// 32 slots of row q in a fixed order.  No per-row shuffle reductions and no
+// idle lanes on short rows; deterministic.
 
-// One CSR row times a gathered vector, double-float accumulation; the
-// result is returned in every lane.
-template <bool BF16>
-__device__ __forceinline__ void row_dot_df(const DevCSR& M, int row, const float* __restrict__ x,
-                                           int lane, float& hi, float& lo) {
-  const int s = M.row_ptr[row], e = M.row_ptr[row + 1];
-  const uint64_t pol = evict_first_policy();
-  hi = 0.f;
-  lo = 0.f;
-  for (int p = s + lane * 4; p < e; p += 128) {
-    const int4 c = ld_stream_i4(M.col + p, pol);
-    const float4 v = ld_vals<BF16>(M, p, pol);
-    const float x0 = __ldg(x + c.x), x1 = __ldg(x + c.y), x2 = __ldg(x + c.z), x3 = __ldg(x + c.w);
-    df_fma(hi, lo, v.x, x0);
-    df_fma(hi, lo, v.y, x1);
-    df_fma(hi, lo, v.z, x2);
-    df_fma(hi, lo, v.w, x3);
-  }
-  warp_sum_df(hi, lo);
+// Shared-memory slot row stride (33: the per-row sums read without bank conflicts).
+constexpr int SLOT_W = 33;
+
+// Row of entry p among rows q = 0..nrows-1 with starts bnd[0..nrows-1]
+// (the last row starting at or before p; empty rows are skipped).
+template <int R>
+__device__ __forceinline__ int row_of(int p, const int (&bnd)[R + 1], int nrows) {
+  int q = 0;
+#pragma unroll
+  for (int k = 1; k < R; ++k) q += (k < nrows && bnd[k] <= p) ? 1 : 0;
+  return q;
 }
 
-// One CSR row times a gathered vector, FP32 accumulation.
-template <bool BF16>
-__device__ __forceinline__ float row_dot_f(const DevCSR& M, int row, const float* __restrict__ x,
-                                           int lane) {
-  const int s = M.row_ptr[row], e = M.row_ptr[row + 1];
-  const uint64_t pol = evict_first_policy();
-  float acc = 0.f;
-  for (int p = s + lane * 4; p < e; p += 128) {
-    const int4 c = ld_stream_i4(M.col + p, pol);
-    const float4 v = ld_vals<BF16>(M, p, pol);
-    const float x0 = __ldg(x + c.x), x1 = __ldg(x + c.y), x2 = __ldg(x + c.z), x3 = __ldg(x + c.w);
-    acc = fmaf(v.x, x0, acc);
-    acc = fmaf(v.y, x1, acc);
-    acc = fmaf(v.z, x2, acc);
-    acc = fmaf(v.w, x3, acc);
+template <int R>
+__device__ __forceinline__ void load_bounds(const DevCSR& M, int row0, int nrows, int lane,
+                                            int (&bnd)[R + 1]) {
+  const int b = lane <= nrows ? M.row_ptr[row0 + lane] : 0;
+#pragma unroll
+  for (int k = 0; k <= R; ++k) bnd[k] = __shfl_sync(0xffffffffu, b, k <= nrows ? k : nrows);
+}
+
+// Double-float rows: returns row (lane) sums in lanes 0..nrows-1.
+// slot_hi / slot_lo: this warp's R*32 floats each of shared memory.
+template <bool BF16, int R>
+__device__ __forceinline__ void warp_rows_dot_df(const DevCSR& M, int row0, int nrows,
+                                                 const float* __restrict__ x, int lane,
+                                                 float* slot_hi, float* slot_lo, float& out_hi,
+                                                 float& out_lo) {
+  out_hi = 0.f;
+  out_lo = 0.f;
+  if (nrows <= 0) return;
+  int bnd[R + 1];
+  load_bounds<R>(M, row0, nrows, lane, bnd);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    slot_hi[q * SLOT_W + lane] = 0.f;
+    slot_lo[q * SLOT_W + lane] = 0.f;
   }
-  return warp_sum_f(acc);
+  const uint64_t pol = evict_first_policy();
+  const int P1 = bnd[nrows];
+  int p = bnd[0] + lane * 4;
+  int4 c = make_int4(0, 0, 0, 0);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (p < P1) {
+    c = ld_stream_i4(M.col + p, pol);
+    v = ld_vals<BF16>(M, p, pol);
+  }
+  float hi = 0.f, lo = 0.f;
+  int cur = -1;
+  for (int base = bnd[0]; base < P1; base += 128, p += 128) {
+    const int pn = p + 128;
+    int4 cn = make_int4(0, 0, 0, 0);
+    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pn < P1) {
+      cn = ld_stream_i4(M.col + pn, pol);
+      vn = ld_vals<BF16>(M, pn, pol);
+    }
+    if (p < P1) {
+      const int q = row_of<R>(p, bnd, nrows);
+      if (q != cur) {
+        if (cur >= 0) {
+          slot_hi[cur * SLOT_W + lane] = hi;
+          slot_lo[cur * SLOT_W + lane] = lo;
+        }
+        cur = q;
+        hi = 0.f;
+        lo = 0.f;
+      }
+      const float x0 = __ldg(x + c.x), x1 = __ldg(x + c.y), x2 = __ldg(x + c.z), x3 = __ldg(x + c.w);
+      df_fma(hi, lo, v.x, x0);
+      df_fma(hi, lo, v.y, x1);
+      df_fma(hi, lo, v.z, x2);
+      df_fma(hi, lo, v.w, x3);
+    }
+    c = cn;
+    v = vn;
+  }
+  if (cur >= 0) {
+    slot_hi[cur * SLOT_W + lane] = hi;
+    slot_lo[cur * SLOT_W + lane] = lo;
+  }
+  __syncwarp();
+  if (lane < nrows) {
+    float h = 0.f, l = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) df_add(h, l, slot_hi[lane * SLOT_W + i], slot_lo[lane * SLOT_W + i]);
+    out_hi = h;
+    out_lo = l;
+  }
+  __syncwarp();
+}
+
+// FP32 rows: returns row (lane) sums in lanes 0..nrows-1.
+template <bool BF16, int R>
+__device__ __forceinline__ float warp_rows_dot_f(const DevCSR& M, int row0, int nrows,
+                                                 const float* __restrict__ x, int lane,
+                                                 float* slot) {
+  if (nrows <= 0) return 0.f;
+  int bnd[R + 1];
+  load_bounds<R>(M, row0, nrows, lane, bnd);
+#pragma unroll
+  for (int q = 0; q < R; ++q) slot[q * SLOT_W + lane] = 0.f;
+  const uint64_t pol = evict_first_policy();
+  const int P1 = bnd[nrows];
+  int p = bnd[0] + lane * 4;
+  int4 c = make_int4(0, 0, 0, 0);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (p < P1) {
+    c = ld_stream_i4(M.col + p, pol);
+    v = ld_vals<BF16>(M, p, pol);
+  }
+  float acc = 0.f;
+  int cur = -1;
+  for (int base = bnd[0]; base < P1; base += 128, p += 128) {
+    const int pn = p + 128;
+    int4 cn = make_int4(0, 0, 0, 0);
+    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pn < P1) {
+      cn = ld_stream_i4(M.col + pn, pol);
+      vn = ld_vals<BF16>(M, pn, pol);
+    }
+    if (p < P1) {
+      const int q = row_of<R>(p, bnd, nrows);
+      if (q != cur) {
+        if (cur >= 0) slot[cur * SLOT_W + lane] = acc;
+        cur = q;
+        acc = 0.f;
+      }
+      const float x0 = __ldg(x + c.x), x1 = __ldg(x + c.y), x2 = __ldg(x + c.z), x3 = __ldg(x + c.w);
+      acc = fmaf(v.x, x0, acc);
+      acc = fmaf(v.y, x1, acc);
+      acc = fmaf(v.z, x2, acc);
+      acc = fmaf(v.w, x3, acc);
+    }
+    c = cn;
+    v = vn;
+  }
+  if (cur >= 0) slot[cur * SLOT_W + lane] = acc;
+  __syncwarp();
+  float out = 0.f;
+  if (lane < nrows) {
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) out += slot[lane * SLOT_W + i];
+  }
+  __syncwarp();
+  return out;
 }
 
 // Forward projection with the Poisson-ratio epilogue (steps a1, a2) and the
-// FP64 data term of the objective.
+// FP64 data term of the objective.  Each warp projects ROWS_PER_WARP rows;
+// the epilogue runs once per block on 64 consecutive rows with full warps
+// (FP64 is scarce on this part, so it is issued as few times as possible).
 template <bool BF16, bool DATA>
 __global__ void __launch_bounds__(THREADS) k_forward(FwdArgs a) {
   SolverState* st = a.st;
@@ -241,25 +360,26 @@ __global__ void __launch_bounds__(THREADS) k_forward(FwdArgs a) {
     f = a.f[0];
     y_out = a.y[0];
   }
+  __shared__ float s_hi[WARPS][ROWS_PER_WARP * SLOT_W];
+  __shared__ float s_lo[WARPS][ROWS_PER_WARP * SLOT_W];
+  __shared__ float r_hi[WARPS * ROWS_PER_WARP], r_lo[WARPS * ROWS_PER_WARP];
   const int m = a.A.rows;
-  const int row0 = (blockIdx.x * WARPS + warp) * ROWS_PER_WARP;
-  float keep_hi = 0.f, keep_lo = 0.f;
-#pragma unroll 1
-  for (int q = 0; q < ROWS_PER_WARP; ++q) {
-    const int row = row0 + q;
-    if (row >= m) break;
-    float hi, lo;
-    row_dot_df<BF16>(a.A, row, f, lane, hi, lo);
-    if (lane == q) {
-      keep_hi = hi;
-      keep_lo = lo;
-    }
+  const int block_row0 = blockIdx.x * WARPS * ROWS_PER_WARP;
+  const int row0 = block_row0 + warp * ROWS_PER_WARP;
+  const int nrows = max(0, min(ROWS_PER_WARP, m - row0));
+  float hi, lo;
+  warp_rows_dot_df<BF16, ROWS_PER_WARP>(a.A, row0, nrows, f, lane, s_hi[warp], s_lo[warp], hi, lo);
+  if (lane < ROWS_PER_WARP) {
+    r_hi[warp * ROWS_PER_WARP + lane] = hi;
+    r_lo[warp * ROWS_PER_WARP + lane] = lo;
   }
+  __syncthreads();
   double data = 0.0;
   int hits = 0, bad = 0;
-  const int row = row0 + lane;
-  if (lane < ROWS_PER_WARP && row < m) {
-    const double y = (double)keep_hi + (double)keep_lo;
+  const int t = threadIdx.x;
+  const int row = block_row0 + t;
+  if (t < WARPS * ROWS_PER_WARP && row < m) {
+    const double y = (double)r_hi[t] + (double)r_lo[t];
     y_out[row] = y;
     const double gam = (double)a.gamma[row];
     const double gg = (double)a.g[row];
@@ -469,7 +589,19 @@ __global__ void __launch_bounds__(THREADS) k_pixel(PixArgs a) {
   const int r0 = blockIdx.y * TILE_R, c0 = blockIdx.x * TILE_C;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ StencilSmem S;
+  __shared__ float s_slot[WARPS][PIX_PER_WARP * SLOT_W];
   const float th = (float)theta;
+
+  // a3: grad F = A^T w for this warp's PIX_PER_WARP consecutive pixels (their
+  // rows of the transposed CSR are contiguous); issued first so the stream
+  // starts at once
+  float keep = 0.f;
+  {
+    const int t0 = warp * PIX_PER_WARP;
+    const int r = r0 + t0 / TILE_C, c = c0 + t0 % TILE_C;
+    const int np = r < n ? max(0, min(PIX_PER_WARP, n - c)) : 0;
+    keep = warp_rows_dot_f<BF16, PIX_PER_WARP>(a.At, r * n + c, np, a.w, lane, s_slot[warp]);
+  }
 
   // a0: f~ = f^k + theta (f^k - f^{k-1}) on the tile with halo 2
   for (int t = threadIdx.x; t < (TILE_R + 4) * TW; t += THREADS) {
@@ -498,17 +630,6 @@ __global__ void __launch_bounds__(THREADS) k_pixel(PixArgs a) {
       if (TRACK) reg += reg_at(S.K, ii + 2, jj + 2, r, c, n, a.ip.lambda1, a.ip.lambda2, a.ip.eps);
     }
     S.G[t] = gr;
-  }
-  // a3: grad F = A^T w, one warp per pixel row of the transposed CSR
-  float keep = 0.f;
-#pragma unroll 1
-  for (int q = 0; q < PIX_PER_WARP; ++q) {
-    const int t = warp * PIX_PER_WARP + q;
-    const int r = r0 + t / TILE_C, c = c0 + t % TILE_C;
-    if (r < n && c < n) {
-      const float s = row_dot_f<BF16>(a.At, r * n + c, a.w, lane);
-      if (lane == q) keep = s;
-    }
   }
   __syncthreads();  // S.G complete
   // a5: f^{k+1} = max(f~ - beta (f^k / Lambda) (grad F + grad R), 0)
@@ -586,16 +707,11 @@ template <bool BF16>
 __global__ void __launch_bounds__(THREADS) k_backproject(DevCSR At, const float* __restrict__ w,
                                                          float* __restrict__ out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float s_slot[WARPS][ROWS_PER_WARP * SLOT_W];
   const int row0 = (blockIdx.x * WARPS + warp) * ROWS_PER_WARP;
-  float keep = 0.f;
-#pragma unroll 1
-  for (int q = 0; q < ROWS_PER_WARP; ++q) {
-    const int row = row0 + q;
-    if (row >= At.rows) break;
-    const float s = row_dot_f<BF16>(At, row, w, lane);
-    if (lane == q) keep = s;
-  }
-  if (lane < ROWS_PER_WARP && row0 + lane < At.rows) out[row0 + lane] = keep;
+  const int nrows = max(0, min(ROWS_PER_WARP, At.rows - row0));
+  const float s = warp_rows_dot_f<BF16, ROWS_PER_WARP>(At, row0, nrows, w, lane, s_slot[warp]);
+  if (lane < nrows) out[row0 + lane] = s;
 }
 
 // Standalone SHOITV gradient (step a4): out = B^T grad phi~(B f).
@@ -680,21 +796,14 @@ __global__ void __launch_bounds__(THREADS) k_actc(const float* __restrict__ g,
     }
   }
 }
+// Pixel centre (c + 1/2 - N/2, r + 1/2 - N/2) inside x^2 + y^2 <= (N/2)^2, in
+// exact integer arithmetic (both sides scaled by 4).
 __device__ __forceinline__ bool in_disk(int r, int c, int n) {
-  const double h = 0.5 * n;
-  const double x = c + 0.5 - h, y = r + 0.5 - h;
-  return x * x + y * y <= h * h;
+  const long long dx = 2ll * c + 1 - n, dy = 2ll * r + 1 - n;
+  return dx * dx + dy * dy <= (long long)n * n;
 }
-__global__ void k_fill_disk(int n, int n_angles, const double* actc, float* f_out) {
-  // NPFOV by a block-local count over all pixels (small; every block recomputes it)
-  __shared__ int s_cnt;
-  if (threadIdx.x == 0) s_cnt = 0;
-  __syncthreads();
-  int cnt = 0;
-  for (int j = threadIdx.x; j < n * n; j += blockDim.x) cnt += in_disk(j / n, j % n, n);
-  atomicAdd(&s_cnt, cnt);
-  __syncthreads();
-  const double tmc = *actc / ((double)s_cnt * (double)n_angles);
+__global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, float* f_out) {
+  const double tmc = *actc / ((double)npfov * (double)n_angles);
   const float v = (float)tmc;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n * n; j += gridDim.x * blockDim.x)
     f_out[j] = in_disk(j / n, j % n, n) ? v : 0.f;
@@ -783,14 +892,26 @@ cudaError_t launch_init_momentum(SolverState* st, int k0, int momentum, double a
   return cudaGetLastError();
 }
 
+long long disk_pixels(int n) {
+  // pixels with centres in the inscribed disk (same integer test as in_disk)
+  long long npfov = 0;
+  for (long long r = 0; r < n; ++r)
+    for (long long c = 0; c < n; ++c) {
+      const long long dx = 2 * c + 1 - n, dy = 2 * r + 1 - n;
+      npfov += (dx * dx + dy * dy <= (long long)n * n) ? 1 : 0;
+    }
+  return npfov;
+}
+
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
-                                 double* partial, SolverState* st, float* f_out, cudaStream_t s) {
+                                 long long npfov, double* partial, SolverState* st, float* f_out,
+                                 cudaStream_t s) {
   // the ACTc scalar is parked in the last partial slot
   double* actc = partial + 1023;
   k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, st, actc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_fill_disk<<<64, 256, 0, s>>>(n, n_angles, actc, f_out);
+  k_fill_disk<<<pix_grid_x(n) * 8, 256, 0, s>>>(n, n_angles, (int)npfov, actc, f_out);
   return cudaGetLastError();
 }
 

@@ -342,6 +342,27 @@ def test_rate_and_omega_ordering():
         assert gaps[1.0][kk] < gaps[0.5][kk] < gaps[0.25][kk]
 
 
+def test_trajectory_sensitivity_depends_on_step():
+    # The EM step p = beta f/Lambda is not bounded by 1/L_phi (Thm. 10): on the
+    # 64^2 grid with 1e5 counts and beta = 1 the FP64 iteration amplifies a
+    # 1e-8 relative perturbation of f^1 by > 100 within 200 iterations, while
+    # beta = 0.1 damps it.  This is why long small-grid parity runs use beta = 0.1.
+    A = W.system_matrix("64")
+    geom = W.GEOMETRIES["64"]
+    sl = W.make_slice(A, geom, 1e5, W.seed_for(1))
+    prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+    f0 = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    pert = f0 * (1 + 1e-8 * np.random.default_rng(0).standard_normal(prob.d))
+    amp = {}
+    for beta in (1.0, 0.1):
+        par = O.Params(beta=beta, omega=1.0, max_iters=200)
+        a = O.appga(prob, par, f_init=f0, track_phi=False).f
+        b = O.appga(prob, par, f_init=pert, track_phi=False).f
+        amp[beta] = np.linalg.norm(a - b) / np.linalg.norm(a) / 1e-8
+    assert amp[1.0] > 100.0
+    assert amp[0.1] < 1.0
+
+
 def test_ppga_is_monotone_with_small_fixed_step():
     # With theta = 0 and p_max <= 1/L, Lemma 5 gives Phi(T f) <= Phi(f).
     prob, lam1, lam2, eps = _kkt_setup()
