@@ -24,12 +24,14 @@ struct Workspace {
   bool ready = false;
   int m = 0, d = 0;
   float* f[3] = {nullptr, nullptr, nullptr};
-  double* y[2] = {nullptr, nullptr};
+  float2* y[2] = {nullptr, nullptr};  // A f^k as double-float pairs
   float* w = nullptr;
+  float* gR = nullptr;  // B^T grad phi~(B f~) of the current iterate
   float* pfreeze = nullptr;
-  double* partial_p = nullptr;
-  double* partial_r = nullptr;
-  double* partial_aux = nullptr;
+  float2* partial_p = nullptr;
+  float2* partial_r = nullptr;
+  float2* partial_aux = nullptr;
+  unsigned int* gtick = nullptr;  // group tickets of the grid reductions
   double* scalars = nullptr;  // device doubles for standalone results
   SolverState* st = nullptr;
   SolverState* st_scratch = nullptr;
@@ -118,10 +120,12 @@ void free_workspace(Workspace& ws) {
   for (auto& p : ws.f) cudaFree(p);
   for (auto& p : ws.y) cudaFree(p);
   cudaFree(ws.w);
+  cudaFree(ws.gR);
   cudaFree(ws.pfreeze);
   cudaFree(ws.partial_p);
   cudaFree(ws.partial_r);
   cudaFree(ws.partial_aux);
+  cudaFree(ws.gtick);
   cudaFree(ws.scalars);
   cudaFree(ws.st);
   cudaFree(ws.st_scratch);
@@ -182,10 +186,14 @@ appga_status ensure_workspace(appga_matrix* M) {
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(&ws.f[i], (size_t)d, b);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(&ws.y[i], (size_t)m, b);
   if (e == cudaSuccess) e = dalloc(&ws.w, (size_t)m, b);
+  if (e == cudaSuccess) e = dalloc(&ws.gR, (size_t)d, b);
   if (e == cudaSuccess) e = dalloc(&ws.pfreeze, (size_t)d, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_p, (size_t)np, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_r, (size_t)np, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_aux, (size_t)np, b);
+  const int ng = appga::max_group_tickets(m, M->n);
+  if (e == cudaSuccess) e = dalloc(&ws.gtick, (size_t)ng, b);
+  if (e == cudaSuccess) e = cudaMemset(ws.gtick, 0, (size_t)ng * sizeof(unsigned int));
   if (e == cudaSuccess) e = dalloc(&ws.scalars, 8, b);
   if (e == cudaSuccess) e = dalloc(&ws.st, 1, b);
   if (e == cudaSuccess) e = dalloc(&ws.st_scratch, 1, b);
@@ -264,12 +272,15 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   appga::FwdArgs init = fwd_args(M, bf16);
   init.f[0] = ws.f[(k0 + 2) % 3];
   init.y[0] = ws.y[(k0 + 1) & 1];
+  init.y_out = nullptr;
   init.g = g;
   init.gamma = gamma;
   init.st = ws.st_scratch;
   init.partial = ws.partial_aux;
+  init.gtick = ws.gtick;
   init.loop = 0;
-  CK(appga::launch_forward(init, 0, s));
+  init.n = M->n;
+  CK(appga::launch_forward(init, s));
 
   appga::FwdArgs fa = fwd_args(M, bf16);
   for (int i = 0; i < 3; ++i) fa.f[i] = ws.f[i];
@@ -280,23 +291,29 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   fa.gamma = gamma;
   fa.st = ws.st;
   fa.partial = ws.partial_r;
+  fa.gtick = ws.gtick;
   fa.loop = 1;
   fa.want_data = track ? 1 : 0;
+  fa.gR = ws.gR;
+  fa.n = M->n;
+  fa.ip = iter_params(p, track);
 
   appga::PixArgs pa{};
   pa.At = M->At;
   pa.n = M->n;
   for (int i = 0; i < 3; ++i) pa.f[i] = ws.f[i];
   pa.w = ws.w;
+  pa.gR = ws.gR;
   pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = ws.pfreeze;
   pa.st = ws.st;
   pa.partial = ws.partial_p;
+  pa.gtick = ws.gtick;
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
 
-  // w^{k0}, y^{k0} and F(f^{k0})
-  CK(appga::launch_forward(fa, track, s));
+  // w^{k0}, y^{k0}, B^T grad phi~(B f~^{k0}) and Phi(f^{k0})
+  CK(appga::launch_forward(fa, s));
   *fa_out = fa;
   *pa_out = pa;
   return APPGA_OK;
@@ -332,7 +349,7 @@ appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int
       cudaError_t e = cudaSuccess;
       for (int i = 0; i < S && e == cudaSuccess; ++i) {
         e = appga::launch_pixel(pa, s);
-        if (e == cudaSuccess) e = appga::launch_forward(fa, track, s);
+        if (e == cudaSuccess) e = appga::launch_forward(fa, s);
       }
       cudaError_t e2 = cudaStreamEndCapture(s, &graph);
       if (e != cudaSuccess) {
@@ -446,17 +463,20 @@ appga_status objective_on(appga_matrix* M, const float* f, const float* g, const
   Workspace& ws = M->ws;
   appga::FwdArgs a = fwd_args(M, bf16_requested(M, p));
   a.f[0] = f;
-  a.y[0] = ws.y[0];
+  a.y[0] = nullptr;
+  a.y_out = nullptr;
   a.g = g;
   a.gamma = gamma;
   a.st = ws.st_scratch;
   a.partial = ws.partial_aux;
+  a.gtick = ws.gtick;
   a.data_out = ws.scalars;
   a.loop = 0;
   a.want_data = 1;
-  CK(appga::launch_forward(a, 1, s));
+  a.n = M->n;
+  CK(appga::launch_forward(a, s));
   CK(appga::launch_reg_term(M->n, f, (float)p->lambda1, (float)p->lambda2, (float)p->eps,
-                            ws.partial_aux, ws.st_scratch, ws.scalars + 1, s));
+                            ws.partial_aux, ws.gtick, ws.st_scratch, ws.scalars + 1, s));
   CK(cudaMemcpyAsync(ws.scalars_host, ws.scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *phi = ws.scalars_host[0] + ws.scalars_host[1];
@@ -489,7 +509,7 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
     if (f_cur) {
       CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
     } else {
-      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.st_scratch,
+      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.gtick, ws.st_scratch,
                                      slot_cur, s));
     }
     CK(cudaMemcpyAsync(slot_prev, slot_cur, fb, cudaMemcpyDeviceToDevice, s));
@@ -652,8 +672,8 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
   CK(cudaSetDevice(ctx->device));
   appga::HostCSR at, pa, pt;
   appga::transpose_csr(m, d, row_ptr_host, col_host, val_host, &at);
-  appga::pad_rows(m, d, row_ptr_host, col_host, val_host, 4, &pa);
-  appga::pad_rows(d, m, at.row_ptr.data(), at.col.data(), at.val.data(), 4, &pt);
+  appga::pad_rows(m, d, row_ptr_host, col_host, val_host, appga::ROW_PAD, &pa);
+  appga::pad_rows(d, m, at.row_ptr.data(), at.col.data(), at.val.data(), appga::ROW_PAD, &pt);
   // Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM); summed in FP64, once
   // for the FP32 values and once for their BF16 rounding (the BF16 run is the
   // method applied to the rounded matrix, preconditioner included)
@@ -738,22 +758,28 @@ appga_status appga_forward_ratio(appga_ctx* ctx, const appga_matrix* mat, const 
   CK(cudaSetDevice(ctx->device));
   appga::FwdArgs a = fwd_args(M, false);
   a.f[0] = f;
-  a.y[0] = y_out;
+  a.y[0] = nullptr;
+  a.y_out = y_out;
   a.w = w_out;
   a.g = g;
   a.gamma = gamma;
   a.st = M->ws.st_scratch;
   a.partial = M->ws.partial_aux;
+  a.gtick = M->ws.gtick;
   a.data_out = data_out;
   a.loop = 0;
   a.want_data = data_out != nullptr ? 1 : 0;
-  CK(appga::launch_forward(a, 0, (cudaStream_t)stream));
+  a.n = M->n;
+  CK(appga::launch_forward(a, (cudaStream_t)stream));
   return APPGA_OK;
 }
 
 appga_status appga_backproject(appga_ctx* ctx, const appga_matrix* mat, const float* w,
                                float* out, void* stream) {
   if (!ctx || !mat || !w || !out) return fail(APPGA_EINVAL, "null argument");
+  auto* M = const_cast<appga_matrix*>(mat);
+  appga_status rc = ensure_workspace(M);
+  if (rc != APPGA_OK) return rc;
   CK(cudaSetDevice(ctx->device));
   CK(appga::launch_backproject(mat->At, w, out, 0, (cudaStream_t)stream));
   return APPGA_OK;
@@ -766,8 +792,8 @@ appga_status appga_shoitv_grad(appga_ctx* ctx, int32_t n_side, const float* f, d
   if (!(lambda1 >= 0) || !(lambda2 >= 0) || !(eps > 0))
     return fail(APPGA_EINVAL, "need lambda1, lambda2 >= 0 and eps > 0");
   CK(cudaSetDevice(ctx->device));
-  CK(appga::launch_shoitv_grad(n_side, f, (float)lambda1, (float)lambda2, (float)eps, out,
-                               (cudaStream_t)stream));
+  CK(appga::launch_stencil(n_side, f, f, 0.f, (float)lambda1, (float)lambda2, (float)eps, out,
+                           (cudaStream_t)stream));
   return APPGA_OK;
 }
 
@@ -787,8 +813,13 @@ appga_status appga_pixel_update(appga_ctx* ctx, const appga_matrix* mat, const f
   h.k0 = 1;
   h.k_last = 1 << 30;
   h.theta = theta;
+  h.theta_hi = (float)theta;
+  h.theta_lo = (float)(theta - (double)h.theta_hi);
   h.t_cur = 1.0;
   CK(cudaMemcpyAsync(M->ws.st_scratch, &h, sizeof h, cudaMemcpyHostToDevice, s));
+  // B^T grad phi~(B f~) of f~ = f_cur + theta (f_cur - f_prev)
+  CK(appga::launch_stencil(M->n, f_cur, f_prev, (float)theta, (float)params->lambda1,
+                           (float)params->lambda2, (float)params->eps, M->ws.gR, s));
   appga::PixArgs pa{};
   pa.At = M->At;
   pa.n = M->n;
@@ -796,10 +827,12 @@ appga_status appga_pixel_update(appga_ctx* ctx, const appga_matrix* mat, const f
   pa.f[1] = const_cast<float*>(f_cur);
   pa.f[2] = f_next;
   pa.w = w;
+  pa.gR = M->ws.gR;
   pa.inv_lambda = bf16_requested(M, params) ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = M->ws.pfreeze;
   pa.st = M->ws.st_scratch;
   pa.partial = M->ws.partial_aux;
+  pa.gtick = M->ws.gtick;
   appga_params q = *params;
   q.precond_freeze_iter = -1;
   pa.ip = iter_params(&q, false);
@@ -828,7 +861,7 @@ appga_status appga_initial_image(appga_ctx* ctx, const appga_matrix* mat, const 
   appga_status rc = ensure_workspace(M);
   if (rc != APPGA_OK) return rc;
   CK(cudaSetDevice(ctx->device));
-  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, M->ws.partial_aux,
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, M->ws.partial_aux, M->ws.gtick,
                                  M->ws.st_scratch, f_out, (cudaStream_t)stream));
   return APPGA_OK;
 }
@@ -873,7 +906,7 @@ appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const f
   appga_params q = *params;
   q.max_iters = n_iters;
   q.rel_obj_tol = 0.0;
-  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.st_scratch,
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.gtick, ws.st_scratch,
                                  ws.f[1], s));
   CK(cudaMemcpyAsync(ws.f[0], ws.f[1], (size_t)M->d * 4, cudaMemcpyDeviceToDevice, s));
   appga::FwdArgs fa;
@@ -886,7 +919,7 @@ appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const f
   for (int i = 0; i < n_iters && e == cudaSuccess; ++i) {
     e = appga::launch_pixel(pa, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], s);
-    if (e == cudaSuccess) e = appga::launch_forward(fa, track, s);
+    if (e == cudaSuccess) e = appga::launch_forward(fa, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 2], s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -15,8 +15,10 @@ namespace appga {
 constexpr double KAPPA = 1e-3;
 
 // Rows of a CSR stored on the device, each row padded with (col = last
-// column of the row, val = 0) to a multiple of 4 entries so every row starts
-// on a 16-byte boundary and can be streamed with 128-bit loads.
+// column of the row, val = 0) to a multiple of ROW_PAD entries so every row
+// starts on a 16-byte boundary and streams as 4-entry packs.
+constexpr int ROW_PAD = 4;
+
 struct DevCSR {
   int32_t rows = 0, cols = 0;
   int64_t nnz_padded = 0;
@@ -39,6 +41,8 @@ struct SolverState {
   int32_t flags;      // APPGA_FLAG_* (sticky)
   int32_t pad0;
   double theta;       // theta_k for the current k (FP64)
+  float theta_hi;     // theta_k as a double-float pair (for FP32-pipe arithmetic)
+  float theta_lo;
   double t_cur;       // t_k (Nesterov recursion)
   double data_term;   // F(f^k) = sum y - g ln(y + gamma)
   double phi_cur;     // Phi(f^k)
@@ -59,21 +63,25 @@ struct IterParams {
   int32_t pad;
 };
 
-// Forward-projection kernel arguments (steps a1, a2 and the data term).
+// Forward-phase kernel arguments (steps a1, a2, a4 and the objective).
 struct FwdArgs {
   DevCSR A;
   const float* f[3];   // iterate ring (loop) / f in slot 0 (standalone)
-  double* y[2];        // projection ring (loop) / y_out in slot 0
+  float2* y[2];        // loop: projection ring A f^k as double-float pairs (hi, lo)
+  double* y_out;       // standalone: A f in FP64
   float* w;            // back-projection weight 1 - g/den (may be null)
   const float* g;
   const float* gamma;
+  float* gR;           // loop: B^T grad phi~(B f~) of the current iterate
   SolverState* st;
-  double* partial;     // one double per block
+  float2* partial;     // one double-float partial per block (+ group results)
+  unsigned int* gtick; // group tickets of the grid reduction (zero between launches)
   double* data_out;    // standalone: where the data term goes (may be null)
+  IterParams ip;       // loop: lambda, eps, stopping tolerance
+  int32_t n;           // image side
   int32_t loop;        // 1: solver loop mode, 0: standalone
-  int32_t want_data;   // evaluate sum y - g ln(y + gamma)
+  int32_t want_data;   // evaluate the objective (data term; in the loop also the regulariser)
   int32_t use_bf16;
-  int32_t pad;
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).
@@ -82,37 +90,39 @@ struct PixArgs {
   int32_t n;           // image side
   float* f[3];         // iterate ring: f^{k-1}, f^k read; f^{k+1} written
   const float* w;      // back-projection weight
+  const float* gR;     // B^T grad phi~(B f~^k)
   const float* inv_lambda;
   float* pfreeze;      // frozen f^{K_P} (may be null)
   SolverState* st;
-  double* partial;
+  float2* partial;
+  unsigned int* gtick;
   IterParams ip;
   int32_t use_bf16;
   int32_t pad;
 };
 
 // ---- launchers (kernels.cu) ----
-int fwd_grid(int m);
-int pix_grid_x(int n);
-int pix_grid_y(int n);
+int stencil_tiles(int n);
 int max_partials(int m, int n);
+int max_group_tickets(int m, int n);
 
-cudaError_t launch_forward(const FwdArgs& a, int track, cudaStream_t s);
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s);
 cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
                                cudaStream_t s);
-cudaError_t launch_shoitv_grad(int n, const float* f, float lam1, float lam2, float eps,
-                               float* out, cudaStream_t s);
+cudaError_t launch_stencil(int n, const float* f_cur, const float* f_prev, float theta,
+                           float lam1, float lam2, float eps, float* out, cudaStream_t s);
 cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float eps,
-                            double* partial, SolverState* st, double* out, cudaStream_t s);
+                            float2* partial, unsigned int* gtick, SolverState* st, double* out,
+                            cudaStream_t s);
 cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, const float* f,
                                    int d, int* flag, cudaStream_t s);
 cudaError_t launch_init_momentum(SolverState* st, int k0, int momentum, double a, double b,
                                  double omega, cudaStream_t s);
 long long disk_pixels(int n);
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
-                                 long long npfov, double* partial, SolverState* st, float* f_out,
-                                 cudaStream_t s);
+                                 long long npfov, float2* partial, unsigned int* gtick,
+                                 SolverState* st, float* f_out, cudaStream_t s);
 
 // ---- host CSR helpers (csr_host.cpp) ----
 struct HostCSR {
@@ -130,6 +140,7 @@ void transpose_csr(int32_t m, int32_t d, const int32_t* row_ptr, const int32_t* 
 // Pads each row to a multiple of `mult` entries (col = last col, val = 0).
 void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t* col,
               const float* val, int mult, HostCSR* out);
+
 // Round-to-nearest-even FP32 -> BF16 bits.
 uint16_t float_to_bf16(float x);
 

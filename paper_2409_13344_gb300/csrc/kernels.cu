@@ -1,41 +1,68 @@
 // Single-slice CUDA kernels of the APPGA hot path (sm_103a).
 //
-//   k_forward  : y = A f (double-float accumulation), y~ = y + theta (y - y_prev),
-//                w = 1 - g / max(y~ + gamma, kappa gamma), FP64 data term
-//                (steps a1, a2, a6-data; Sec. 2.2 grad F, Eq. FidelityTerm)
-//   k_pixel    : f~ = f^k + theta (f^k - f^{k-1}); B^T grad phi~(B f~) by a
-//                shared-memory halo-tiled stencil; A^T w through the
-//                transposed CSR (no atomics); EM-preconditioned projected
-//                update; FP64 regulariser term of Phi(f^k); momentum scalar
-//                for the next iteration (steps a0, a3, a4, a5, a6-reg;
-//                Eq. APPGAiter, Eq. EM, Eq. GNtheta)
+//   k_forward : y = A f^k (double-float accumulation), y~ = y + theta_k (y - y^{k-1})
+//               (the projection of f~^k by linearity), w = 1 - g / max(y~ + gamma,
+//               kappa gamma), data term of the objective; in the solver loop
+//               the same launch also runs the SHOITV stencil of
+//               f~^k = f^k + theta_k (f^k - f^{k-1}) (B^T grad phi~(B f~^k)), the
+//               regulariser term of Phi(f^k) and the stopping test
+//               (steps a0, a1, a2, a4, a6; Sec. 2.2, Eq. FidelityTerm,
+//               Eq. gradenvL2, Eq. def:phi)
+//   k_pixel   : grad F = A^T w through the transposed CSR (no atomics) and the
+//               EM-preconditioned projected update f^{k+1} = max(f~ - beta
+//               (f^k / Lambda)(grad F + B^T grad phi~), 0); next index and FP64
+//               momentum scalar (steps a3, a5; Eq. APPGAiter, Eq. EM, Eq. GNtheta)
 //
-// Both kernels read the iteration index and theta from a device-resident
+// Projector layout: a warp owns 8 consecutive CSR rows, whose row-padded
+// entries form one contiguous range, and streams it linearly in 128-entry
+// chunks (a 16-byte pack of columns and one of values per lane), keeping PF
+// chunks in flight in registers.  Lanes accumulate into their current row and
+// park partials in per-warp shared-memory slots; lane q sums row q.  No
+// block-wide barrier sits on the streaming path.
+//
+// The per-row epilogue runs on the FP32 pipe only: double-float (FP32 pair)
+// arithmetic for y, y~, the guarded denominator, and a double-float natural
+// logarithm for the data term -- this part's FP64 pipe is a small fraction of
+// its FP32 rate, so FP64 is used only for a handful of scalars per launch.
+//
+// Kernels read the iteration index and theta from a device-resident
 // SolverState, so a captured graph of (k_pixel, k_forward) pairs replays
-// without host involvement.  Block partial sums are combined by the last
-// block to finish (ticket counter), in a fixed order, so every reduction is
-// deterministic.
+// without host involvement.  Block partials (double-float pairs) are combined
+// by the last block to finish (ticket counter) in index order: every
+// reduction is deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 
 #include "appga_internal.h"
 
 namespace appga {
 namespace {
 
-constexpr int THREADS = 256;
-constexpr int WARPS = THREADS / 32;
-constexpr int ROWS_PER_WARP = 8;   // forward: rows handled by one warp
-constexpr int TILE_R = 2;          // pixel kernel tile: TILE_R x TILE_C pixels
-constexpr int TILE_C = 32;
-constexpr int PIX_PER_WARP = TILE_R * TILE_C / WARPS;  // 8
-static_assert(PIX_PER_WARP <= 32, "one lane per pixel in the epilogue");
+constexpr int THREADS = 256;  // setup / reduction kernels
+constexpr int MAX_WARPS = 32;
+constexpr int ROWS_PER_WARP = 8;  // projector rows per warp
+constexpr int PW_WARPS = 2;       // warps per projector block
+constexpr int PW_THREADS = PW_WARPS * 32;
+constexpr int PW_ROWS = PW_WARPS * ROWS_PER_WARP;  // rows per projector block
+#ifndef APPGA_PF
+#define APPGA_PF 2
+#endif
+constexpr int PF = APPGA_PF;  // chunks of the nnz stream in flight per warp
+constexpr int SLOT_W = 33;    // slot row stride: per-row sums read without bank conflicts
+
+// Stencil tiles: ST_R x ST_C pixels, one pixel per thread of a projector block
+constexpr int ST_R = 2;
+constexpr int ST_C = 32;
+static_assert(ST_R * ST_C == PW_THREADS, "stencil tile = one pixel per thread");
+constexpr int TW = ST_C + 4;  // f tile width (halo 2)
+constexpr int VW = ST_C + 2;  // v tile width (halo 1)
 
 // ----------------------------------------------------------------- loads
 
 // A and A^T are streamed once per iteration: bypass L1 and tag the lines
-// evict-first in L2 (an L2 cache-policy operand) so the gathered vectors
-// (f, w) stay cached.
+// evict-first in L2 (cache-policy operand) so the gathered vectors stay cached.
 __device__ __forceinline__ uint64_t evict_first_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -68,7 +95,6 @@ __device__ __forceinline__ float4 ld_stream_bf16x4(const uint16_t* p, uint64_t p
   r.w = __uint_as_float(u.y & 0xffff0000u);
   return r;
 }
-
 template <bool BF16>
 __device__ __forceinline__ float4 ld_vals(const DevCSR& M, int p, uint64_t pol) {
   if constexpr (BF16) {
@@ -79,15 +105,51 @@ __device__ __forceinline__ float4 ld_vals(const DevCSR& M, int p, uint64_t pol) 
 }
 
 // ------------------------------------------------- double-float arithmetic
-// Error-free transformations (Knuth TwoSum, FMA-based TwoProduct).  The
-// explicit _rn intrinsics keep the compiler from contracting them.
+// A double-float is an unevaluated sum hi + lo of two floats (about 48
+// significant bits).  Error-free transformations: Knuth's TwoSum and the
+// FMA-based TwoProduct.  The _rn intrinsics keep the compiler from
+// contracting or reassociating them.
+struct df {
+  float hi, lo;
+};
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-// (hi, lo) += a * x with the product and the sum error kept in lo.
-__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float x) {
+__device__ __forceinline__ df quick_renorm(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return quick_renorm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  return quick_renorm(s, __fadd_rn(e, a.lo));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return quick_renorm(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return quick_renorm(p, e);
+}
+__device__ __forceinline__ float df_to_f(df a) { return __fadd_rn(a.hi, a.lo); }
+
+// (hi, lo) += a * x with the product and the sum error kept in lo (dot-product
+// accumulator: the low parts are summed as plain floats).
+__device__ __forceinline__ void acc_fma(float& hi, float& lo, float a, float x) {
   const float p = __fmul_rn(a, x);
   const float pe = __fmaf_rn(a, x, -p);
   float s, e;
@@ -95,102 +157,159 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float x) {
   hi = s;
   lo = __fadd_rn(lo, __fadd_rn(e, pe));
 }
-__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float h2, float l2) {
   float s, e;
   two_sum(hi, h2, s, e);
   hi = s;
   lo = __fadd_rn(__fadd_rn(lo, l2), e);
 }
-// Butterfly reductions: every lane ends with the same (bitwise) value.
-__device__ __forceinline__ void warp_sum_df(float& hi, float& lo) {
+
+// Natural logarithm of a positive normal double-float x = hi + lo.
+// Reduction: hi = 2^e m with m in [1, 2); c = 1 + j/64 the table point
+// nearest m; r = (m + lo 2^-e - c)/c, |r| <= 1/128;
+//   ln x = e ln 2 + ln c + ln(1 + r),
+//   ln(1 + r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 - r^6/6 + r^7/7 (+ O(r^8)),
+// the first three terms in double-float, the rest in FP32 (below 2^-50 of
+// the result).  ln c and ln 2 come as double-float constants computed on the
+// host in extended precision.
+__constant__ float c_logtab_hi[65];
+__constant__ float c_logtab_lo[65];
+__constant__ float c_ln2[2];
+__constant__ float c_third[2];
+__constant__ float c_kappa[2];  // the ratio guard factor kappa as a double-float
+
+__device__ __forceinline__ df df_log(df x) {
+  const int bits = __float_as_int(x.hi);
+  const int e = ((bits >> 23) & 0xff) - 127;
+  const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+  const float ml = __fmul_rn(x.lo, __int_as_float((127 - e) << 23));  // lo * 2^-e, exact
+  const int j = __float2int_rn(__fmul_rn(__fsub_rn(m, 1.f), 64.f));
+  const float c = __fadd_rn(1.f, __fmul_rn((float)j, 0.015625f));
+  const float d = __fsub_rn(m, c);  // exact: |m - c| <= 1/128 within [1, 2]
+  float nh, nl;
+  two_sum(d, ml, nh, nl);
+  // r = (nh + nl) / c as a double-float
+  const float qh = __fdiv_rn(nh, c);
+  const float rem = __fmaf_rn(-qh, c, nh);
+  const float ql = __fdiv_rn(__fadd_rn(rem, nl), c);
+  const df r = quick_renorm(qh, ql);
+  const df r2 = df_mul(r, r);
+  const df r3 = df_mul(r2, r);
+  const df third = {c_third[0], c_third[1]};
+  // tail: -r^4/4 + r^5/5 - r^6/6 + r^7/7 from r^4 (hi only)
+  const float rh = r.hi;
+  const float r4 = __fmul_rn(r2.hi, r2.hi);
+  float t = __fmaf_rn(rh, 1.f / 7.f, -1.f / 6.f);
+  t = __fmaf_rn(rh, t, 0.2f);
+  t = __fmaf_rn(rh, t, -0.25f);
+  t = __fmul_rn(r4, t);
+  df s = df_add(r, df_mul_f(r2, -0.5f));
+  s = df_add(s, df_mul(r3, third));
+  s = df_add_f(s, t);
+  const df ln2 = {c_ln2[0], c_ln2[1]};
+  const df lc = {c_logtab_hi[j], c_logtab_lo[j]};
+  df out = df_add(df_mul_f(ln2, (float)e), lc);
+  return df_add(out, s);
+}
+
+// ----------------------------------------------------------- reductions
+
+__device__ __forceinline__ void warp_sum_acc(float& hi, float& lo) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    df_add(hi, lo, h2, l2);
+    acc_add(hi, lo, h2, l2);
   }
-}
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
 }
 __device__ __forceinline__ int warp_sum_i(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-
-// Deterministic block sum of one double per thread (fixed tree).
-__device__ double block_sum_d(double v) {
-  __shared__ double red[WARPS];
-  v = warp_sum_d(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Deterministic block sum of a double-float accumulator (fixed tree); valid
+// in warp 0.
+__device__ df block_sum_acc(float hi, float lo) {
+  __shared__ float red_hi[MAX_WARPS], red_lo[MAX_WARPS];
+  warp_sum_acc(hi, lo);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (warp == 0) {
-    t = lane < WARPS ? red[lane] : 0.0;
-    t = warp_sum_d(t);
+  if (lane == 0) {
+    red_hi[warp] = hi;
+    red_lo[warp] = lo;
   }
-  return t;  // valid in warp 0
-}
-__device__ int block_sum_i(int v) {
-  __shared__ int redi[WARPS];
-  v = warp_sum_i(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) redi[warp] = v;
-  __syncthreads();
-  int t = 0;
+  float h = 0.f, l = 0.f;
   if (warp == 0) {
-    t = lane < WARPS ? redi[lane] : 0;
-    t = warp_sum_i(t);
+    if (lane < nw) {
+      h = red_hi[lane];
+      l = red_lo[lane];
+    }
+    warp_sum_acc(h, l);
   }
-  return t;
+  return {h, l};
 }
-
-// Publishes this block's partial and returns true in the block that
-// finishes last; that block then sums all partials in index order.
-__device__ bool publish_and_check_last(double* partial, double mine, unsigned int* ticket) {
-  __shared__ bool s_last;
+// Grid-wide deterministic reduction of one double-float per block, in two
+// levels so that no single block sums thousands of partials serially: every
+// block writes partial[b]; the last block to finish in each group of
+// RED_GROUP blocks sums its group (in index order) into partial[nb + g]; the
+// last group leader sums the group results.  Returns true in that final block
+// only, with the total in *total (thread 0).  Group and final tickets are
+// reset by their last user, so the counters start at zero for the next launch.
+constexpr int RED_GROUP = 64;
+__device__ bool grid_reduce(float2* partial, unsigned int* gtick, unsigned int* ftick, df mine,
+                            double* total) {
+  __shared__ int s_flag;
+  const int nb = gridDim.x, b = blockIdx.x, g = b / RED_GROUP;
+  const int ngroups = (nb + RED_GROUP - 1) / RED_GROUP;
+  const int gsize = min(RED_GROUP, nb - g * RED_GROUP);
   if (threadIdx.x == 0) {
-    partial[blockIdx.y * gridDim.x + blockIdx.x] = mine;
+    partial[b] = make_float2(mine.hi, mine.lo);
     __threadfence();
-    const unsigned int nb = gridDim.x * gridDim.y;
-    const unsigned int t = atomicAdd(ticket, 1u);
-    s_last = (t == nb - 1);
+    s_flag = (atomicAdd(&gtick[g], 1u) == (unsigned)(gsize - 1));
   }
   __syncthreads();
-  if (s_last) __threadfence();
-  return s_last;
+  if (!s_flag) return false;
+  __threadfence();
+  float h = 0.f, l = 0.f;
+  for (int i = threadIdx.x; i < gsize; i += blockDim.x) {
+    const float2 v = __ldcg(partial + g * RED_GROUP + i);
+    acc_add(h, l, v.x, v.y);
+  }
+  const df gs = block_sum_acc(h, l);
+  if (threadIdx.x == 0) {
+    gtick[g] = 0;
+    partial[nb + g] = make_float2(gs.hi, gs.lo);
+    __threadfence();
+    s_flag = (atomicAdd(ftick, 1u) == (unsigned)(ngroups - 1));
+  }
+  __syncthreads();
+  if (!s_flag) return false;
+  __threadfence();
+  h = 0.f;
+  l = 0.f;
+  for (int i = threadIdx.x; i < ngroups; i += blockDim.x) {
+    const float2 v = __ldcg(partial + nb + i);
+    acc_add(h, l, v.x, v.y);
+  }
+  const df t = block_sum_acc(h, l);
+  if (threadIdx.x == 0) {
+    *ftick = 0;
+    *total = (double)t.hi + (double)t.lo;
+  }
+  return true;
 }
-__device__ double sum_partials(const double* partial) {
-  const int nb = gridDim.x * gridDim.y;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nb; i += THREADS) v += __ldcg(partial + i);
-  return block_sum_d(v);
+// Per-warp counters folded into a global counter without block barriers.
+__device__ __forceinline__ void warp_count_add(unsigned long long* dst, int v) {
+  v = warp_sum_i(v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, (unsigned long long)v);
+}
+__device__ __forceinline__ void warp_flag_or(int* dst, int flag) {
+  const unsigned any = __ballot_sync(0xffffffffu, flag != 0);
+  if ((threadIdx.x & 31) == 0 && any) atomicOr(dst, flag ? flag : APPGA_FLAG_NONFINITE);
 }
 
 // ------------------------------------------------------------ projectors
-//
-// A warp owns R consecutive CSR rows, whose (row-padded) entries form one
-// contiguous range.  It streams that range linearly in 128-entry chunks
-// (one 4-entry pack per lane; row padding keeps every pack inside a single
-// row), loading chunk t+1 while it gathers and accumulates chunk t.  Each
-// lane accumulates into its current row and, when its row changes, parks the
-// partial in a per-warp shared-memory slot [row][lane]; lane q then sums the
-// 32 slots of row q in a fixed order.  No per-row shuffle reductions and no
-// idle lanes on short rows; deterministic.
-
-// Shared-memory slot row stride (33: the per-row sums read without bank conflicts).
-constexpr int SLOT_W = 33;
 
 // Row of entry p among rows q = 0..nrows-1 with starts bnd[0..nrows-1]
 // (the last row starting at or before p; empty rows are skipped).
@@ -201,226 +320,111 @@ __device__ __forceinline__ int row_of(int p, const int (&bnd)[R + 1], int nrows)
   for (int k = 1; k < R; ++k) q += (k < nrows && bnd[k] <= p) ? 1 : 0;
   return q;
 }
-
+// Row starts of rows row0 .. row0 + nrows (bnd[k] for k > nrows repeats the
+// end); returns the end of the last row.
 template <int R>
-__device__ __forceinline__ void load_bounds(const DevCSR& M, int row0, int nrows, int lane,
-                                            int (&bnd)[R + 1]) {
+__device__ __forceinline__ int load_bounds(const DevCSR& M, int row0, int nrows, int lane,
+                                           int (&bnd)[R + 1]) {
   const int b = lane <= nrows ? M.row_ptr[row0 + lane] : 0;
 #pragma unroll
   for (int k = 0; k <= R; ++k) bnd[k] = __shfl_sync(0xffffffffu, b, k <= nrows ? k : nrows);
+  return __shfl_sync(0xffffffffu, b, nrows);
 }
 
-// Double-float rows: returns row (lane) sums in lanes 0..nrows-1.
-// slot_hi / slot_lo: this warp's R*32 floats each of shared memory.
-template <bool BF16, int R>
-__device__ __forceinline__ void warp_rows_dot_df(const DevCSR& M, int row0, int nrows,
-                                                 const float* __restrict__ x, int lane,
-                                                 float* slot_hi, float* slot_lo, float& out_hi,
-                                                 float& out_lo) {
+// Rows [row0, row0 + nrows) of M times x; returns the sum of row `lane` in
+// lanes 0..nrows-1: an accumulator pair if DF, else an FP32 value in out_hi.
+// slot_hi / slot_lo: this warp's R*SLOT_W floats each of shared memory.
+template <bool BF16, bool DF, int R>
+__device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nrows,
+                                              const float* __restrict__ x, int lane,
+                                              float* slot_hi, float* slot_lo, float& out_hi,
+                                              float& out_lo) {
   out_hi = 0.f;
   out_lo = 0.f;
   if (nrows <= 0) return;
   int bnd[R + 1];
-  load_bounds<R>(M, row0, nrows, lane, bnd);
+  const int P1 = load_bounds<R>(M, row0, nrows, lane, bnd);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     slot_hi[q * SLOT_W + lane] = 0.f;
-    slot_lo[q * SLOT_W + lane] = 0.f;
+    if (DF) slot_lo[q * SLOT_W + lane] = 0.f;
   }
   const uint64_t pol = evict_first_policy();
-  const int P1 = bnd[nrows];
-  int p = bnd[0] + lane * 4;
-  int4 c = make_int4(0, 0, 0, 0);
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (p < P1) {
-    c = ld_stream_i4(M.col + p, pol);
-    v = ld_vals<BF16>(M, p, pol);
+  const int P0 = bnd[0];
+  const int nchunks = (P1 - P0 + 127) >> 7;
+  int4 c[PF];
+  float4 v[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int p = P0 + (u << 7) + lane * 4;
+    c[u] = make_int4(0, 0, 0, 0);
+    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p < P1) {
+      c[u] = ld_stream_i4(M.col + p, pol);
+      v[u] = ld_vals<BF16>(M, p, pol);
+    }
   }
   float hi = 0.f, lo = 0.f;
   int cur = -1;
-  for (int base = bnd[0]; base < P1; base += 128, p += 128) {
-    const int pn = p + 128;
-    int4 cn = make_int4(0, 0, 0, 0);
-    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (pn < P1) {
-      cn = ld_stream_i4(M.col + pn, pol);
-      vn = ld_vals<BF16>(M, pn, pol);
-    }
-    if (p < P1) {
-      const int q = row_of<R>(p, bnd, nrows);
-      if (q != cur) {
-        if (cur >= 0) {
-          slot_hi[cur * SLOT_W + lane] = hi;
-          slot_lo[cur * SLOT_W + lane] = lo;
+  for (int t0 = 0; t0 < nchunks; t0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int t = t0 + u;
+      if (t < nchunks) {
+        const int p = P0 + (t << 7) + lane * 4;
+        const int4 cc = c[u];
+        const float4 vv = v[u];
+        const int pn = p + (PF << 7);
+        if (pn < P1) {  // refill this slot with chunk t + PF before consuming chunk t
+          c[u] = ld_stream_i4(M.col + pn, pol);
+          v[u] = ld_vals<BF16>(M, pn, pol);
         }
-        cur = q;
-        hi = 0.f;
-        lo = 0.f;
+        if (p < P1) {
+          const int q = row_of<R>(p, bnd, nrows);
+          if (q != cur) {
+            if (cur >= 0) {
+              slot_hi[cur * SLOT_W + lane] = hi;
+              if (DF) slot_lo[cur * SLOT_W + lane] = lo;
+            }
+            cur = q;
+            hi = 0.f;
+            lo = 0.f;
+          }
+          const float x0 = __ldg(x + cc.x), x1 = __ldg(x + cc.y);
+          const float x2 = __ldg(x + cc.z), x3 = __ldg(x + cc.w);
+          if (DF) {
+            acc_fma(hi, lo, vv.x, x0);
+            acc_fma(hi, lo, vv.y, x1);
+            acc_fma(hi, lo, vv.z, x2);
+            acc_fma(hi, lo, vv.w, x3);
+          } else {
+            hi = fmaf(vv.x, x0, hi);
+            hi = fmaf(vv.y, x1, hi);
+            hi = fmaf(vv.z, x2, hi);
+            hi = fmaf(vv.w, x3, hi);
+          }
+        }
       }
-      const float x0 = __ldg(x + c.x), x1 = __ldg(x + c.y), x2 = __ldg(x + c.z), x3 = __ldg(x + c.w);
-      df_fma(hi, lo, v.x, x0);
-      df_fma(hi, lo, v.y, x1);
-      df_fma(hi, lo, v.z, x2);
-      df_fma(hi, lo, v.w, x3);
     }
-    c = cn;
-    v = vn;
   }
   if (cur >= 0) {
     slot_hi[cur * SLOT_W + lane] = hi;
-    slot_lo[cur * SLOT_W + lane] = lo;
+    if (DF) slot_lo[cur * SLOT_W + lane] = lo;
   }
   __syncwarp();
   if (lane < nrows) {
     float h = 0.f, l = 0.f;
+    if (DF) {
 #pragma unroll 8
-    for (int i = 0; i < 32; ++i) df_add(h, l, slot_hi[lane * SLOT_W + i], slot_lo[lane * SLOT_W + i]);
+      for (int i = 0; i < 32; ++i) acc_add(h, l, slot_hi[lane * SLOT_W + i], slot_lo[lane * SLOT_W + i]);
+    } else {
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) h += slot_hi[lane * SLOT_W + i];
+    }
     out_hi = h;
     out_lo = l;
   }
   __syncwarp();
-}
-
-// FP32 rows: returns row (lane) sums in lanes 0..nrows-1.
-template <bool BF16, int R>
-__device__ __forceinline__ float warp_rows_dot_f(const DevCSR& M, int row0, int nrows,
-                                                 const float* __restrict__ x, int lane,
-                                                 float* slot) {
-  if (nrows <= 0) return 0.f;
-  int bnd[R + 1];
-  load_bounds<R>(M, row0, nrows, lane, bnd);
-#pragma unroll
-  for (int q = 0; q < R; ++q) slot[q * SLOT_W + lane] = 0.f;
-  const uint64_t pol = evict_first_policy();
-  const int P1 = bnd[nrows];
-  int p = bnd[0] + lane * 4;
-  int4 c = make_int4(0, 0, 0, 0);
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (p < P1) {
-    c = ld_stream_i4(M.col + p, pol);
-    v = ld_vals<BF16>(M, p, pol);
-  }
-  float acc = 0.f;
-  int cur = -1;
-  for (int base = bnd[0]; base < P1; base += 128, p += 128) {
-    const int pn = p + 128;
-    int4 cn = make_int4(0, 0, 0, 0);
-    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (pn < P1) {
-      cn = ld_stream_i4(M.col + pn, pol);
-      vn = ld_vals<BF16>(M, pn, pol);
-    }
-    if (p < P1) {
-      const int q = row_of<R>(p, bnd, nrows);
-      if (q != cur) {
-        if (cur >= 0) slot[cur * SLOT_W + lane] = acc;
-        cur = q;
-        acc = 0.f;
-      }
-      const float x0 = __ldg(x + c.x), x1 = __ldg(x + c.y), x2 = __ldg(x + c.z), x3 = __ldg(x + c.w);
-      acc = fmaf(v.x, x0, acc);
-      acc = fmaf(v.y, x1, acc);
-      acc = fmaf(v.z, x2, acc);
-      acc = fmaf(v.w, x3, acc);
-    }
-    c = cn;
-    v = vn;
-  }
-  if (cur >= 0) slot[cur * SLOT_W + lane] = acc;
-  __syncwarp();
-  float out = 0.f;
-  if (lane < nrows) {
-#pragma unroll 8
-    for (int i = 0; i < 32; ++i) out += slot[lane * SLOT_W + i];
-  }
-  __syncwarp();
-  return out;
-}
-
-// Forward projection with the Poisson-ratio epilogue (steps a1, a2) and the
-// FP64 data term of the objective.  Each warp projects ROWS_PER_WARP rows;
-// the epilogue runs once per block on 64 consecutive rows with full warps
-// (FP64 is scarce on this part, so it is issued as few times as possible).
-template <bool BF16, bool DATA>
-__global__ void __launch_bounds__(THREADS) k_forward(FwdArgs a) {
-  SolverState* st = a.st;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float* f;
-  double* y_out;
-  const double* y_prev = nullptr;
-  double theta = 0.0;
-  if (a.loop) {
-    if (st->done) return;  // uniform over the grid
-    const int kk = st->k;
-    theta = st->theta;
-    f = a.f[kk % 3];
-    y_out = a.y[kk & 1];
-    y_prev = a.y[(kk + 1) & 1];
-  } else {
-    f = a.f[0];
-    y_out = a.y[0];
-  }
-  __shared__ float s_hi[WARPS][ROWS_PER_WARP * SLOT_W];
-  __shared__ float s_lo[WARPS][ROWS_PER_WARP * SLOT_W];
-  __shared__ float r_hi[WARPS * ROWS_PER_WARP], r_lo[WARPS * ROWS_PER_WARP];
-  const int m = a.A.rows;
-  const int block_row0 = blockIdx.x * WARPS * ROWS_PER_WARP;
-  const int row0 = block_row0 + warp * ROWS_PER_WARP;
-  const int nrows = max(0, min(ROWS_PER_WARP, m - row0));
-  float hi, lo;
-  warp_rows_dot_df<BF16, ROWS_PER_WARP>(a.A, row0, nrows, f, lane, s_hi[warp], s_lo[warp], hi, lo);
-  if (lane < ROWS_PER_WARP) {
-    r_hi[warp * ROWS_PER_WARP + lane] = hi;
-    r_lo[warp * ROWS_PER_WARP + lane] = lo;
-  }
-  __syncthreads();
-  double data = 0.0;
-  int hits = 0, bad = 0;
-  const int t = threadIdx.x;
-  const int row = block_row0 + t;
-  if (t < WARPS * ROWS_PER_WARP && row < m) {
-    const double y = (double)r_hi[t] + (double)r_lo[t];
-    y_out[row] = y;
-    const double gam = (double)a.gamma[row];
-    const double gg = (double)a.g[row];
-    if (a.w != nullptr) {
-      double yt = y;
-      if (theta != 0.0) yt = fma(theta, y - y_prev[row], y);
-      double den = yt + gam;
-      const double floor_ = KAPPA * gam;
-      if (den < floor_) {
-        den = floor_;
-        hits = 1;
-      }
-      // w = 1 - g/den = (den - g)/den: the numerator is formed in FP64 so the
-      // weight keeps its relative accuracy when den ~ g.
-      const float wv = __fdiv_rn((float)(den - gg), (float)den);
-      a.w[row] = wv;
-      if (!isfinite(wv)) bad = 1;
-    }
-    if (!isfinite(y)) bad = 1;
-    if (DATA) data = y - gg * log(y + gam);
-  }
-  if (a.loop || a.want_data) {
-    const int bhits = block_sum_i(hits);
-    const int bbad = block_sum_i(bad);
-    double bdata = 0.0;
-    if (DATA) bdata = block_sum_d(data);
-    if (threadIdx.x == 0) {
-      if (bhits) atomicAdd(&st->guard_hits, (unsigned long long)bhits);
-      if (bbad) atomicOr(&st->flags, (int)APPGA_FLAG_NONFINITE);
-    }
-    if (DATA) {
-      if (publish_and_check_last(a.partial, bdata, &st->ticket_r)) {
-        const double tot = sum_partials(a.partial);
-        if (threadIdx.x == 0) {
-          if (a.loop) st->data_term = tot;
-          if (a.data_out) *a.data_out = tot;
-          st->ticket_r = 0;
-        }
-      }
-    }
-  }
 }
 
 // ------------------------------------------------------------- stencil
@@ -487,20 +491,34 @@ __device__ __forceinline__ float s_eps_f(float nrm2, float eps) {
   return nrm > eps ? nrm - 0.5f * eps : nrm2 / (2.f * eps);
 }
 
-constexpr int TW = TILE_C + 4;  // f tile width (halo 2)
-constexpr int VW = TILE_C + 2;  // v tile width (halo 1)
-
 struct StencilSmem {
-  float T[TILE_R + 4][TW];      // f~ (or f) with halo 2
-  float K[TILE_R + 4][TW];      // f^k with halo 2
-  float V[6][TILE_R + 2][VW];   // grad phi~ fields with halo 1
-  float G[TILE_R * TILE_C];     // B^T grad phi~(B f~) at the tile pixels
+  float T[ST_R + 4][TW];     // f~ (or f) with halo 2
+  float K[ST_R + 4][TW];     // f^k with halo 2
+  float V[6][ST_R + 2][VW];  // grad phi~ fields with halo 1
 };
 
-// v = grad phi~(B X) on the (TILE_R+2) x (TILE_C+2) points around the tile.
-__device__ void stencil_v(StencilSmem& S, int r0, int c0, int n, float lam1, float lam2,
-                          float eps) {
-  for (int t = threadIdx.x; t < (TILE_R + 2) * VW; t += THREADS) {
+// One stencil tile at (r0, c0): writes gR = B^T grad phi~(B f~) with
+// f~ = fk + th (fk - fkm) for the tile pixels (if gR != nullptr) and returns
+// this thread's term lam1 s_eps(pair) + lam2 s_eps(quad) of f^k (if want_reg).
+__device__ float stencil_tile(StencilSmem& S, const float* __restrict__ fk,
+                              const float* __restrict__ fkm, float th, int r0, int c0, int n,
+                              float lam1, float lam2, float eps, float* __restrict__ gR,
+                              bool want_reg) {
+  for (int t = threadIdx.x; t < (ST_R + 4) * TW; t += blockDim.x) {
+    const int ii = t / TW, jj = t % TW;
+    const int r = r0 - 2 + ii, c = c0 - 2 + jj;
+    float vk = 0.f, vt = 0.f;
+    if (r >= 0 && r < n && c >= 0 && c < n) {
+      vk = fk[r * n + c];
+      const float vm = fkm[r * n + c];
+      vt = fmaf(th, vk - vm, vk);
+    }
+    S.K[ii][jj] = vk;
+    S.T[ii][jj] = vt;
+  }
+  __syncthreads();
+  // v = grad phi~(B f~) on the (ST_R+2) x (ST_C+2) points around the tile
+  for (int t = threadIdx.x; t < (ST_R + 2) * VW; t += blockDim.x) {
     const int ii = t / VW, jj = t % VW;
     const int r = r0 - 1 + ii, c = c0 - 1 + jj;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -522,37 +540,215 @@ __device__ void stencil_v(StencilSmem& S, int r0, int c0, int n, float lam1, flo
 #pragma unroll
     for (int q = 0; q < 6; ++q) S.V[q][ii][jj] = v[q];
   }
+  __syncthreads();
+  float reg = 0.f;
+  for (int t = threadIdx.x; t < ST_R * ST_C; t += blockDim.x) {
+    const int ii = t / ST_C, jj = t % ST_C;
+    const int r = r0 + ii, c = c0 + jj;
+    if (r < n && c < n) {
+      if (gR) {
+        // B^T v at (r, c), located at (ii + 1, jj + 1) in V
+        const int i = ii + 1, j = jj + 1;
+        const bool r_lo = r >= 1, r_hi = r <= n - 2, c_lo = c >= 1, c_hi = c <= n - 2;
+        float g = 0.f;
+        if (c_lo) g += S.V[0][i][j];
+        if (c_hi) g -= S.V[0][i][j + 1];
+        if (r_lo) g += S.V[1][i][j];
+        if (r_hi) g -= S.V[1][i + 1][j];
+        g += form_u3<VW>(S.V[2], i, j, c_lo, c_hi);
+        g += form_u6<VW>(S.V[3], i, j, r_lo, c_lo, c_hi);
+        g += form_u5<VW>(S.V[4], i, j, r_lo, r_hi);
+        g += form_u4<VW>(S.V[5], i, j, r_lo, r_hi, c_lo);
+        gR[r * n + c] = g;
+      }
+      if (want_reg) {
+        float u[6];
+        diff_fields<TW>(S.K, ii + 2, jj + 2, r, c, n, u);
+        const float n1 = u[0] * u[0] + u[1] * u[1];
+        const float n2 = u[2] * u[2] + u[3] * u[3] + u[4] * u[4] + u[5] * u[5];
+        reg += lam1 * s_eps_f(n1, eps) + lam2 * s_eps_f(n2, eps);
+      }
+    }
+  }
+  return reg;
 }
 
-// B^T v at tile pixel (r, c), located at (i, j) = (ii + 1, jj + 1) in V.
-__device__ __forceinline__ float stencil_adjoint(const StencilSmem& S, int i, int j, int r, int c,
-                                                 int n) {
-  const bool r_lo = r >= 1, r_hi = r <= n - 2, c_lo = c >= 1, c_hi = c <= n - 2;
-  float t = 0.f;
-  if (c_lo) t += S.V[0][i][j];
-  if (c_hi) t -= S.V[0][i][j + 1];
-  if (r_lo) t += S.V[1][i][j];
-  if (r_hi) t -= S.V[1][i + 1][j];
-  t += form_u3<VW>(S.V[2], i, j, c_lo, c_hi);
-  t += form_u6<VW>(S.V[3], i, j, r_lo, c_lo, c_hi);
-  t += form_u5<VW>(S.V[4], i, j, r_lo, r_hi);
-  t += form_u4<VW>(S.V[5], i, j, r_lo, r_hi, c_lo);
-  return t;
+__host__ __device__ __forceinline__ int st_tiles_x(int n) { return (n + ST_C - 1) / ST_C; }
+__host__ __device__ __forceinline__ int st_tiles(int n) {
+  return st_tiles_x(n) * ((n + ST_R - 1) / ST_R);
 }
-
-// lam1 s_eps(pair) + lam2 s_eps(quad) at pixel (r, c) of X (position (i, j)).
-__device__ __forceinline__ float reg_at(const float (*X)[TW], int i, int j, int r, int c, int n,
-                                        float lam1, float lam2, float eps) {
-  float u[6];
-  diff_fields<TW>(X, i, j, r, c, n, u);
-  const float n1 = u[0] * u[0] + u[1] * u[1];
-  const float n2 = u[2] * u[2] + u[3] * u[3] + u[4] * u[4] + u[5] * u[5];
-  return lam1 * s_eps_f(n1, eps) + lam2 * s_eps_f(n2, eps);
+__host__ __device__ __forceinline__ int proj_blocks(int rows) {
+  return (rows + PW_ROWS - 1) / PW_ROWS;
 }
 
 // Momentum scalar for index k (Eq. GNtheta) -- FP64 on the device.
 __device__ double gn_t_dev(int k, double a, double b, double omega) {
   return a * pow((double)k, omega) + b;
+}
+__device__ void set_theta(SolverState* st, double theta) {
+  st->theta = theta;
+  const float h = (float)theta;
+  st->theta_hi = h;
+  st->theta_lo = (float)(theta - (double)h);
+}
+
+// ------------------------------------------------------------ k_forward
+
+// Blocks [0, proj_blocks(m)) project rows; in the solver loop the blocks
+// after them run the stencil tiles.
+template <bool BF16>
+__global__ void __launch_bounds__(PW_THREADS) k_forward(FwdArgs a) {
+  __shared__ union {
+    struct {
+      float hi[PW_WARPS][ROWS_PER_WARP * SLOT_W];
+      float lo[PW_WARPS][ROWS_PER_WARP * SLOT_W];
+    } slot;
+    StencilSmem st;
+  } sm;
+  SolverState* st = a.st;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (a.loop && st->done) return;  // uniform over the grid
+  const int kk = a.loop ? st->k : 0;
+  const int nproj = proj_blocks(a.A.rows);
+  float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
+  int hits = 0, bad = 0;
+  if ((int)blockIdx.x < nproj) {
+    const float* f = a.loop ? a.f[kk % 3] : a.f[0];
+    const int m = a.A.rows;
+    const int row0 = blockIdx.x * PW_ROWS + warp * ROWS_PER_WARP;
+    const int nrows = max(0, min(ROWS_PER_WARP, m - row0));
+    float hi, lo;
+    warp_rows_dot<BF16, true, ROWS_PER_WARP>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
+                                             sm.slot.lo[warp], hi, lo);
+    if (lane < nrows) {
+      const int row = row0 + lane;
+      const df y = quick_renorm(hi, lo);
+      const float gam = a.gamma[row], gg = a.g[row];
+      if (a.loop) {
+        a.y[kk & 1][row] = make_float2(y.hi, y.lo);
+      } else {
+        if (a.y[0]) a.y[0][row] = make_float2(y.hi, y.lo);
+        if (a.y_out) a.y_out[row] = (double)y.hi + (double)y.lo;
+      }
+      if (a.w != nullptr) {
+        df yt = y;
+        if (a.loop) {
+          // y~ = y + theta (y - y^{k-1}): the projection of f~ by linearity
+          const float2 yp = a.y[(kk + 1) & 1][row];
+          const df th = {st->theta_hi, st->theta_lo};
+          const df dy = df_add(y, df_neg({yp.x, yp.y}));
+          yt = df_add(y, df_mul(th, dy));
+        }
+        df den = df_add_f(yt, gam);
+        const df floor_ = df_mul_f({c_kappa[0], c_kappa[1]}, gam);  // kappa * gamma
+        if (df_add(den, df_neg(floor_)).hi < 0.f) {
+          den = floor_;
+          ++hits;
+        }
+        // w = 1 - g/den = (den - g)/den, numerator in double-float so the
+        // weight keeps its relative accuracy when den ~ g
+        const float wv = __fdiv_rn(df_to_f(df_add_f(den, -gg)), df_to_f(den));
+        a.w[row] = wv;
+        if (!isfinite(wv)) bad = 1;
+      }
+      if (!isfinite(y.hi)) bad = 1;
+      if (a.want_data) {
+        // data term y - g ln(y + gamma) (Eq. FidelityTerm), double-float
+        const df term = df_add(y, df_neg(df_mul_f(df_log(df_add_f(y, gam)), gg)));
+        acc_add(acc_hi, acc_lo, term.hi, term.lo);
+      }
+    }
+  } else {
+    // SHOITV gradient at f~^kk and the regulariser of Phi(f^kk)
+    const int b = blockIdx.x - nproj;
+    const int ntx = st_tiles_x(a.n);
+    const float reg = stencil_tile(sm.st, a.f[kk % 3], a.f[(kk + 2) % 3], st->theta_hi,
+                                   (b / ntx) * ST_R, (b % ntx) * ST_C, a.n, a.ip.lambda1,
+                                   a.ip.lambda2, a.ip.eps, a.gR, a.want_data != 0);
+    acc_hi = reg;
+  }
+  warp_count_add(&st->guard_hits, hits);
+  warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
+  if (!a.want_data) return;
+  const df bsum = block_sum_acc(acc_hi, acc_lo);
+  double tot = 0.0;
+  if (grid_reduce(a.partial, a.gtick, &st->ticket_r, bsum, &tot)) {
+    if (threadIdx.x == 0) {
+      if (!a.loop) {
+        if (a.data_out) *a.data_out = tot;
+      } else {
+        // Phi(f^kk) and the stopping test against Phi(f^{kk-1})
+        const double prev = st->phi_cur;
+        st->phi_prev = prev;
+        st->phi_cur = tot;
+        if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(tot - prev) <= a.ip.rel_tol * fabs(prev)) {
+          st->done = 1;
+          st->result_k = kk;
+          st->stopped_early = 1;
+        }
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------------- k_pixel
+
+template <bool BF16>
+__global__ void __launch_bounds__(PW_THREADS) k_pixel(PixArgs a) {
+  __shared__ float slot[PW_WARPS][ROWS_PER_WARP * SLOT_W];
+  SolverState* st = a.st;
+  if (st->done) return;  // uniform over the grid
+  const int kk = st->k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = a.At.rows;
+  const int j0 = blockIdx.x * PW_ROWS + warp * ROWS_PER_WARP;
+  const int np = max(0, min(ROWS_PER_WARP, d - j0));
+  float bp, unused;
+  warp_rows_dot<BF16, false, ROWS_PER_WARP>(a.At, j0, np, a.w, lane, slot[warp], nullptr, bp,
+                                            unused);
+  int bad = 0;
+  if (lane < np) {
+    const int j = j0 + lane;
+    const float* fk = a.f[kk % 3];
+    const float vk = fk[j];
+    const float ft = fmaf(st->theta_hi, vk - a.f[(kk + 2) % 3][j], vk);
+    float pk = vk;
+    if (a.ip.freeze_iter >= 0) {
+      if (kk == a.ip.freeze_iter) {
+        a.pfreeze[j] = vk;
+      } else if (kk > a.ip.freeze_iter) {
+        pk = a.pfreeze[j];
+      }
+    }
+    const float p = a.ip.beta * pk * a.inv_lambda[j];
+    const float grad = bp + a.gR[j];
+    const float xv = __fmaf_rn(-p, grad, ft);
+    if (!isfinite(xv)) bad = 1;
+    a.f[(kk + 1) % 3][j] = fmaxf(xv, 0.f);
+  }
+  warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
+  // Finalise the iteration in the last block: the next index and momentum.
+  double unused_total;
+  if (grid_reduce(a.partial, a.gtick, &st->ticket_p, {0.f, 0.f}, &unused_total)) {
+    if (threadIdx.x == 0) {
+      if (kk >= st->k_last) {
+        st->done = 1;
+        st->result_k = kk + 1;
+      }
+      st->k = kk + 1;
+      double th_next = 0.0;
+      if (a.ip.momentum == APPGA_MOMENTUM_GN) {
+        th_next = (gn_t_dev(kk, a.ip.a, a.ip.b, a.ip.omega) - 1.0) /
+                  gn_t_dev(kk + 1, a.ip.a, a.ip.b, a.ip.omega);
+      } else if (a.ip.momentum == APPGA_MOMENTUM_NESTEROV) {
+        const double t = st->t_cur;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        th_next = (t - 1.0) / tn;
+        st->t_cur = tn;
+      }
+      set_theta(st, th_next);
+    }
+  }
 }
 
 // theta_{k0} and t_{k0} of the first iteration of a run, with the same device
@@ -571,195 +767,48 @@ __global__ void k_init_momentum(SolverState* st, int k0, int momentum, double a,
       t = tn;
     }
   }
-  st->theta = theta;
+  set_theta(st, theta);
   st->t_cur = t;
-}
-
-// Fused pixel phase: steps a0, a3, a4, a5 (+ the regulariser term of Phi(f^k)).
-template <bool BF16, bool TRACK>
-__global__ void __launch_bounds__(THREADS) k_pixel(PixArgs a) {
-  SolverState* st = a.st;
-  if (st->done) return;  // uniform over the grid
-  const int kk = st->k;
-  const double theta = st->theta;
-  const float* __restrict__ fk = a.f[kk % 3];
-  const float* __restrict__ fkm = a.f[(kk + 2) % 3];
-  float* __restrict__ fnext = a.f[(kk + 1) % 3];
-  const int n = a.n;
-  const int r0 = blockIdx.y * TILE_R, c0 = blockIdx.x * TILE_C;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ StencilSmem S;
-  __shared__ float s_slot[WARPS][PIX_PER_WARP * SLOT_W];
-  const float th = (float)theta;
-
-  // a3: grad F = A^T w for this warp's PIX_PER_WARP consecutive pixels (their
-  // rows of the transposed CSR are contiguous); issued first so the stream
-  // starts at once
-  float keep = 0.f;
-  {
-    const int t0 = warp * PIX_PER_WARP;
-    const int r = r0 + t0 / TILE_C, c = c0 + t0 % TILE_C;
-    const int np = r < n ? max(0, min(PIX_PER_WARP, n - c)) : 0;
-    keep = warp_rows_dot_f<BF16, PIX_PER_WARP>(a.At, r * n + c, np, a.w, lane, s_slot[warp]);
-  }
-
-  // a0: f~ = f^k + theta (f^k - f^{k-1}) on the tile with halo 2
-  for (int t = threadIdx.x; t < (TILE_R + 4) * TW; t += THREADS) {
-    const int ii = t / TW, jj = t % TW;
-    const int r = r0 - 2 + ii, c = c0 - 2 + jj;
-    float vk = 0.f, vt = 0.f;
-    if (r >= 0 && r < n && c >= 0 && c < n) {
-      vk = fk[r * n + c];
-      const float vm = fkm[r * n + c];
-      vt = fmaf(th, vk - vm, vk);
-    }
-    S.K[ii][jj] = vk;
-    S.T[ii][jj] = vt;
-  }
-  __syncthreads();
-  // a4: grad phi~(B f~) around the tile, then B^T at the tile pixels
-  stencil_v(S, r0, c0, n, a.ip.lambda1, a.ip.lambda2, a.ip.eps);
-  __syncthreads();
-  float reg = 0.f;
-  for (int t = threadIdx.x; t < TILE_R * TILE_C; t += THREADS) {
-    const int ii = t / TILE_C, jj = t % TILE_C;
-    const int r = r0 + ii, c = c0 + jj;
-    float gr = 0.f;
-    if (r < n && c < n) {
-      gr = stencil_adjoint(S, ii + 1, jj + 1, r, c, n);
-      if (TRACK) reg += reg_at(S.K, ii + 2, jj + 2, r, c, n, a.ip.lambda1, a.ip.lambda2, a.ip.eps);
-    }
-    S.G[t] = gr;
-  }
-  __syncthreads();  // S.G complete
-  // a5: f^{k+1} = max(f~ - beta (f^k / Lambda) (grad F + grad R), 0)
-  int bad = 0;
-  if (lane < PIX_PER_WARP) {
-    const int t = warp * PIX_PER_WARP + lane;
-    const int ii = t / TILE_C, jj = t % TILE_C;
-    const int r = r0 + ii, c = c0 + jj;
-    if (r < n && c < n) {
-      const int j = r * n + c;
-      const float ft = S.T[ii + 2][jj + 2];
-      float pk = S.K[ii + 2][jj + 2];
-      if (a.ip.freeze_iter >= 0) {
-        if (kk == a.ip.freeze_iter) {
-          a.pfreeze[j] = pk;
-        } else if (kk > a.ip.freeze_iter) {
-          pk = a.pfreeze[j];
-        }
-      }
-      const float p = a.ip.beta * pk * a.inv_lambda[j];
-      const float grad = keep + S.G[t];
-      const float x = __fmaf_rn(-p, grad, ft);
-      if (!isfinite(x)) bad = 1;
-      fnext[j] = fmaxf(x, 0.f);
-    }
-  }
-  // Finalise the iteration in the last block: Phi(f^k), the stopping test,
-  // the next index and the next momentum scalar.
-  const int bbad = block_sum_i(bad);
-  if (threadIdx.x == 0 && bbad) atomicOr(&st->flags, (int)APPGA_FLAG_NONFINITE);
-  double breg = 0.0;
-  if (TRACK) breg = block_sum_d((double)reg);
-  if (publish_and_check_last(a.partial, breg, &st->ticket_p)) {
-    double reg_tot = 0.0;
-    if (TRACK) reg_tot = sum_partials(a.partial);
-    if (threadIdx.x == 0) {
-      st->ticket_p = 0;
-      bool stop = false;
-      if (TRACK) {
-        const double phi = st->data_term + reg_tot;
-        const double prev = st->phi_cur;
-        st->phi_prev = prev;
-        st->phi_cur = phi;
-        if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(phi - prev) <= a.ip.rel_tol * fabs(prev)) {
-          stop = true;
-          st->done = 1;
-          st->result_k = kk;
-          st->stopped_early = 1;
-        }
-      }
-      if (!stop) {
-        if (kk >= st->k_last) {
-          st->done = 1;
-          st->result_k = kk + 1;
-        }
-        st->k = kk + 1;
-        double th_next = 0.0;
-        if (a.ip.momentum == APPGA_MOMENTUM_GN) {
-          th_next = (gn_t_dev(kk, a.ip.a, a.ip.b, a.ip.omega) - 1.0) /
-                    gn_t_dev(kk + 1, a.ip.a, a.ip.b, a.ip.omega);
-        } else if (a.ip.momentum == APPGA_MOMENTUM_NESTEROV) {
-          const double t = st->t_cur;
-          const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-          th_next = (t - 1.0) / tn;
-          st->t_cur = tn;
-        }
-        st->theta = th_next;
-      }
-    }
-  }
 }
 
 // Standalone back-projection (step a3): out = A^T w.
 template <bool BF16>
-__global__ void __launch_bounds__(THREADS) k_backproject(DevCSR At, const float* __restrict__ w,
-                                                         float* __restrict__ out) {
+__global__ void __launch_bounds__(PW_THREADS) k_backproject(DevCSR At, const float* __restrict__ w,
+                                                            float* __restrict__ out) {
+  __shared__ float slot[PW_WARPS][ROWS_PER_WARP * SLOT_W];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ float s_slot[WARPS][ROWS_PER_WARP * SLOT_W];
-  const int row0 = (blockIdx.x * WARPS + warp) * ROWS_PER_WARP;
+  const int row0 = blockIdx.x * PW_ROWS + warp * ROWS_PER_WARP;
   const int nrows = max(0, min(ROWS_PER_WARP, At.rows - row0));
-  const float s = warp_rows_dot_f<BF16, ROWS_PER_WARP>(At, row0, nrows, w, lane, s_slot[warp]);
+  float s, unused;
+  warp_rows_dot<BF16, false, ROWS_PER_WARP>(At, row0, nrows, w, lane, slot[warp], nullptr, s,
+                                            unused);
   if (lane < nrows) out[row0 + lane] = s;
 }
 
-// Standalone SHOITV gradient (step a4): out = B^T grad phi~(B f).
-__global__ void __launch_bounds__(THREADS) k_shoitv(int n, const float* __restrict__ f, float lam1,
-                                                    float lam2, float eps, float* __restrict__ out) {
-  const int r0 = blockIdx.y * TILE_R, c0 = blockIdx.x * TILE_C;
+// Stencil kernel: gR = B^T grad phi~(B f~) with f~ = f_cur + theta (f_cur - f_prev)
+// (theta = 0, f_prev = f_cur: the plain SHOITV gradient, step a4).
+__global__ void __launch_bounds__(PW_THREADS) k_stencil(int n, const float* __restrict__ f_cur,
+                                                        const float* __restrict__ f_prev,
+                                                        float theta, float lam1, float lam2,
+                                                        float eps, float* __restrict__ out) {
   __shared__ StencilSmem S;
-  for (int t = threadIdx.x; t < (TILE_R + 4) * TW; t += THREADS) {
-    const int ii = t / TW, jj = t % TW;
-    const int r = r0 - 2 + ii, c = c0 - 2 + jj;
-    S.T[ii][jj] = (r >= 0 && r < n && c >= 0 && c < n) ? f[r * n + c] : 0.f;
-  }
-  __syncthreads();
-  stencil_v(S, r0, c0, n, lam1, lam2, eps);
-  __syncthreads();
-  for (int t = threadIdx.x; t < TILE_R * TILE_C; t += THREADS) {
-    const int ii = t / TILE_C, jj = t % TILE_C;
-    const int r = r0 + ii, c = c0 + jj;
-    if (r < n && c < n) out[r * n + c] = stencil_adjoint(S, ii + 1, jj + 1, r, c, n);
-  }
+  const int ntx = st_tiles_x(n);
+  stencil_tile(S, f_cur, f_prev, theta, (blockIdx.x / ntx) * ST_R, (blockIdx.x % ntx) * ST_C, n,
+               lam1, lam2, eps, out, false);
 }
 
-// Regulariser term phi~(B f) in FP64 (objective, step a6).
-__global__ void __launch_bounds__(THREADS) k_reg_term(int n, const float* __restrict__ f, float lam1,
-                                                      float lam2, float eps, double* partial,
-                                                      SolverState* st, double* out) {
-  const int r0 = blockIdx.y * TILE_R, c0 = blockIdx.x * TILE_C;
-  __shared__ float X[TILE_R + 4][TW];
-  for (int t = threadIdx.x; t < (TILE_R + 4) * TW; t += THREADS) {
-    const int ii = t / TW, jj = t % TW;
-    const int r = r0 - 2 + ii, c = c0 - 2 + jj;
-    X[ii][jj] = (r >= 0 && r < n && c >= 0 && c < n) ? f[r * n + c] : 0.f;
-  }
-  __syncthreads();
-  double reg = 0.0;
-  for (int t = threadIdx.x; t < TILE_R * TILE_C; t += THREADS) {
-    const int ii = t / TILE_C, jj = t % TILE_C;
-    const int r = r0 + ii, c = c0 + jj;
-    if (r < n && c < n) reg += (double)reg_at(X, ii + 2, jj + 2, r, c, n, lam1, lam2, eps);
-  }
-  const double b = block_sum_d(reg);
-  if (publish_and_check_last(partial, b, &st->ticket_aux)) {
-    const double tot = sum_partials(partial);
-    if (threadIdx.x == 0) {
-      *out = tot;
-      st->ticket_aux = 0;
-    }
-  }
+// Regulariser term phi~(B f) (objective, step a6).
+__global__ void __launch_bounds__(PW_THREADS) k_reg_term(int n, const float* __restrict__ f,
+                                                         float lam1, float lam2, float eps,
+                                                         float2* partial, unsigned int* gtick,
+                                                         SolverState* st, double* out) {
+  __shared__ StencilSmem S;
+  const int ntx = st_tiles_x(n);
+  const float reg = stencil_tile(S, f, f, 0.f, (blockIdx.x / ntx) * ST_R,
+                                 (blockIdx.x % ntx) * ST_C, n, lam1, lam2, eps, nullptr, true);
+  const df b = block_sum_acc(reg, 0.f);
+  double tot = 0.0;
+  if (grid_reduce(partial, gtick, &st->ticket_aux, b, &tot) && threadIdx.x == 0) *out = tot;
 }
 
 // Input validation: g finite and >= 0, gamma finite and > 0, f finite and >= 0.
@@ -782,19 +831,16 @@ __global__ void k_validate(const float* __restrict__ g, const float* __restrict_
 // Initial image (Sec. 4.1): TMC * 1_disk, TMC = (sum g - sum gamma)/(NPFOV * NPA).
 __global__ void __launch_bounds__(THREADS) k_actc(const float* __restrict__ g,
                                                   const float* __restrict__ gamma, int m,
-                                                  double* partial, SolverState* st,
-                                                  double* actc_out) {
-  double v = 0.0;
-  for (int i = blockIdx.x * THREADS + threadIdx.x; i < m; i += gridDim.x * THREADS)
-    v += (double)g[i] - (double)gamma[i];
-  const double b = block_sum_d(v);
-  if (publish_and_check_last(partial, b, &st->ticket_aux)) {
-    const double tot = sum_partials(partial);
-    if (threadIdx.x == 0) {
-      *actc_out = tot;
-      st->ticket_aux = 0;
-    }
+                                                  float2* partial, unsigned int* gtick,
+                                                  SolverState* st, double* actc_out) {
+  float h = 0.f, l = 0.f;
+  for (int i = blockIdx.x * THREADS + threadIdx.x; i < m; i += gridDim.x * THREADS) {
+    acc_add(h, l, g[i], 0.f);
+    acc_add(h, l, -gamma[i], 0.f);
   }
+  const df b = block_sum_acc(h, l);
+  double tot = 0.0;
+  if (grid_reduce(partial, gtick, &st->ticket_aux, b, &tot) && threadIdx.x == 0) *actc_out = tot;
 }
 // Pixel centre (c + 1/2 - N/2, r + 1/2 - N/2) inside x^2 + y^2 <= (N/2)^2, in
 // exact integer arithmetic (both sides scaled by 4).
@@ -809,74 +855,90 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
     f_out[j] = in_disk(j / n, j % n, n) ? v : 0.f;
 }
 
+// Double-float constants of df_log, computed once in extended precision.
+struct LogTables {
+  cudaError_t err = cudaSuccess;
+  LogTables() {
+    float th[65], tl[65], l2[2], t3[2], kp[2];
+    for (int j = 0; j <= 64; ++j) {
+      const long double v = logl(1.0L + (long double)j / 64.0L);
+      th[j] = (float)v;
+      tl[j] = (float)(v - (long double)th[j]);
+    }
+    const long double ln2 = logl(2.0L), third = 1.0L / 3.0L;
+    l2[0] = (float)ln2;
+    l2[1] = (float)(ln2 - (long double)l2[0]);
+    t3[0] = (float)third;
+    t3[1] = (float)(third - (long double)t3[0]);
+    const long double kappa = (long double)KAPPA;
+    kp[0] = (float)kappa;
+    kp[1] = (float)(kappa - (long double)kp[0]);
+    err = cudaMemcpyToSymbol(c_logtab_hi, th, sizeof th);
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_logtab_lo, tl, sizeof tl);
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_ln2, l2, sizeof l2);
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_third, t3, sizeof t3);
+    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_kappa, kp, sizeof kp);
+  }
+};
+cudaError_t ensure_tables() {
+  static LogTables t;
+  return t.err;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers
 
-int fwd_grid(int m) { return (m + WARPS * ROWS_PER_WARP - 1) / (WARPS * ROWS_PER_WARP); }
-int pix_grid_x(int n) { return (n + TILE_C - 1) / TILE_C; }
-int pix_grid_y(int n) { return (n + TILE_R - 1) / TILE_R; }
-int max_partials(int m, int n) {
-  const int a = fwd_grid(m), b = pix_grid_x(n) * pix_grid_y(n);
-  return (a > b ? a : b) + 1024;
-}
+int stencil_tiles(int n) { return st_tiles(n); }
 
-cudaError_t launch_forward(const FwdArgs& a, int track, cudaStream_t s) {
-  const int grid = fwd_grid(a.A.rows);
-  if (grid == 0) return cudaSuccess;
-  const bool data = track || a.want_data;
-  if (a.use_bf16) {
-    if (data)
-      k_forward<true, true><<<grid, THREADS, 0, s>>>(a);
-    else
-      k_forward<true, false><<<grid, THREADS, 0, s>>>(a);
-  } else {
-    if (data)
-      k_forward<false, true><<<grid, THREADS, 0, s>>>(a);
-    else
-      k_forward<false, false><<<grid, THREADS, 0, s>>>(a);
-  }
+int max_partials(int m, int n) {
+  const int a = proj_blocks(m) + st_tiles(n);
+  const int b = proj_blocks(n * n);
+  const int nb = a > b ? a : b;
+  return nb + nb / RED_GROUP + 1024;
+}
+int max_group_tickets(int m, int n) { return max_partials(m, n) / RED_GROUP + 1; }
+
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
+  cudaError_t e = ensure_tables();
+  if (e != cudaSuccess) return e;
+  const int grid = proj_blocks(a.A.rows) + (a.loop ? st_tiles(a.n) : 0);
+  if (a.use_bf16)
+    k_forward<true><<<grid, PW_THREADS, 0, s>>>(a);
+  else
+    k_forward<false><<<grid, PW_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
-  dim3 grid(pix_grid_x(a.n), pix_grid_y(a.n));
-  if (a.use_bf16) {
-    if (a.ip.track)
-      k_pixel<true, true><<<grid, THREADS, 0, s>>>(a);
-    else
-      k_pixel<true, false><<<grid, THREADS, 0, s>>>(a);
-  } else {
-    if (a.ip.track)
-      k_pixel<false, true><<<grid, THREADS, 0, s>>>(a);
-    else
-      k_pixel<false, false><<<grid, THREADS, 0, s>>>(a);
-  }
+  const int grid = proj_blocks(a.At.rows);
+  if (a.use_bf16)
+    k_pixel<true><<<grid, PW_THREADS, 0, s>>>(a);
+  else
+    k_pixel<false><<<grid, PW_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
                                cudaStream_t s) {
-  const int grid = fwd_grid(At.rows);
-  if (grid == 0) return cudaSuccess;
+  const int grid = proj_blocks(At.rows);
   if (use_bf16)
-    k_backproject<true><<<grid, THREADS, 0, s>>>(At, w, out);
+    k_backproject<true><<<grid, PW_THREADS, 0, s>>>(At, w, out);
   else
-    k_backproject<false><<<grid, THREADS, 0, s>>>(At, w, out);
+    k_backproject<false><<<grid, PW_THREADS, 0, s>>>(At, w, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_shoitv_grad(int n, const float* f, float lam1, float lam2, float eps,
-                               float* out, cudaStream_t s) {
-  dim3 grid(pix_grid_x(n), pix_grid_y(n));
-  k_shoitv<<<grid, THREADS, 0, s>>>(n, f, lam1, lam2, eps, out);
+cudaError_t launch_stencil(int n, const float* f_cur, const float* f_prev, float theta,
+                           float lam1, float lam2, float eps, float* out, cudaStream_t s) {
+  k_stencil<<<st_tiles(n), PW_THREADS, 0, s>>>(n, f_cur, f_prev, theta, lam1, lam2, eps, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float eps,
-                            double* partial, SolverState* st, double* out, cudaStream_t s) {
-  dim3 grid(pix_grid_x(n), pix_grid_y(n));
-  k_reg_term<<<grid, THREADS, 0, s>>>(n, f, lam1, lam2, eps, partial, st, out);
+                            float2* partial, unsigned int* gtick, SolverState* st, double* out,
+                            cudaStream_t s) {
+  k_reg_term<<<st_tiles(n), PW_THREADS, 0, s>>>(n, f, lam1, lam2, eps, partial, gtick, st, out);
   return cudaGetLastError();
 }
 
@@ -904,14 +966,15 @@ long long disk_pixels(int n) {
 }
 
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
-                                 long long npfov, double* partial, SolverState* st, float* f_out,
-                                 cudaStream_t s) {
-  // the ACTc scalar is parked in the last partial slot
-  double* actc = partial + 1023;
-  k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, st, actc);
+                                 long long npfov, float2* partial, unsigned int* gtick,
+                                 SolverState* st, float* f_out, cudaStream_t s) {
+  // the ACTc scalar is parked in the last partial slot (as raw bytes of a double)
+  double* actc = reinterpret_cast<double*>(partial + max_partials(m, n) - 1);
+  k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, gtick, st, actc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_fill_disk<<<pix_grid_x(n) * 8, 256, 0, s>>>(n, n_angles, (int)npfov, actc, f_out);
+  k_fill_disk<<<(n * n + 255) / 256 < 1024 ? (n * n + 255) / 256 : 1024, 256, 0, s>>>(
+      n, n_angles, (int)npfov, actc, f_out);
   return cudaGetLastError();
 }
 
