@@ -235,6 +235,22 @@ appga_status appga_reconstruct_host(appga_ctx* ctx, const appga_matrix* mat, con
                                     const appga_params* params, float* f_out_host,
                                     appga_stats* stats_host, void* stream);
 
+/* ------------------------------------------------------------------ batched
+ * appga_reconstruct_batched: K independent slices (1 <= K <= 128) that share
+ * this matrix, iterated together so every nonzero of A and A^T is read once
+ * per iteration for all slices (CSR times a K-column block).  g, gamma:
+ * float[K][m] (slice-major); f_init: float[K][d] or NULL (each slice's initial
+ * image, Sec. 4.1); f_out: float[K][d]; stats_host: appga_stats[K] or NULL
+ * (phi is the FP64 objective of each result).  Every slice runs `params`
+ * for max_iters maps or until its own stopping test fires; a slice's result
+ * does not depend on the other slices in the batch.  The projector
+ * accumulation is FP32 (the single-slice path accumulates in double-float),
+ * so results agree with appga_reconstruct to FP32 rounding.  Synchronises. */
+appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, int32_t K,
+                                       const float* g, const float* gamma, const float* f_init,
+                                       const appga_params* params, float* f_out,
+                                       appga_stats* stats_host, void* stream);
+
 /* appga_validate_csr_host: the host-side check appga_matrix_create runs on a
  * CSR (row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz, 0 <= col < d, values
  * finite and >= 0).  Host only; needs no device.  EINVAL / EDOMAIN with a

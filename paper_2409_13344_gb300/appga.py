@@ -97,6 +97,9 @@ SIGNATURES = {
     "appga_reconstruct_host": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(appga_params), _P,
                                               ctypes.POINTER(appga_stats), _P]),
     "appga_validate_csr_host": (ctypes.c_int, [_I32, _I32, _P, _P, _P]),
+    "appga_reconstruct_batched": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P,
+                                                 ctypes.POINTER(appga_params), _P,
+                                                 ctypes.POINTER(appga_stats), _P]),
     "appga_kernel_times": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(appga_params), _I32,
                                           ctypes.POINTER(_D), ctypes.POINTER(_D)]),
 }
@@ -274,6 +277,16 @@ def appga_reconstruct_host(ctx, mat, g_host, gamma_host, f_init_host, params, f_
                                                  hp(f_out_host), ctypes.byref(st),
                                                  _stream(stream)), "appga_reconstruct_host")
     return st
+
+
+def appga_reconstruct_batched(ctx, mat, K, g, gamma, f_init, params, f_out, stream=None):
+    """g, gamma: [K][m] device arrays; f_out: [K][d]; returns a list of K stats."""
+    st = (appga_stats * K)()
+    _check(load_library().appga_reconstruct_batched(ctx, mat, K, _ptr(g), _ptr(gamma),
+                                                    _ptr(f_init), ctypes.byref(params), _ptr(f_out),
+                                                    st, _stream(stream)),
+           "appga_reconstruct_batched")
+    return list(st)
 
 
 def appga_validate_csr_host(m, d, row_ptr, col, val) -> int:

@@ -10,73 +10,22 @@
 
 #include "appga.h"
 #include "appga_internal.h"
+#include "handles.h"
 
+using appga::cuda_fail;
+using appga::dalloc;
 using appga::DevCSR;
+using appga::fail;
 using appga::SolverState;
+using appga::Workspace;
 
 namespace {
-
 thread_local std::string g_last_error;
-
 constexpr int kDefaultGraphIters = 16;
-
-struct Workspace {
-  bool ready = false;
-  int m = 0, d = 0;
-  float* f[3] = {nullptr, nullptr, nullptr};
-  float2* y[2] = {nullptr, nullptr};  // A f^k as double-float pairs
-  float* w = nullptr;
-  float* gR = nullptr;  // B^T grad phi~(B f~) of the current iterate
-  float* pfreeze = nullptr;
-  float2* partial_p = nullptr;
-  float2* partial_r = nullptr;
-  float2* partial_aux = nullptr;
-  unsigned int* gtick = nullptr;  // group tickets of the grid reductions
-  double* scalars = nullptr;  // device doubles for standalone results
-  SolverState* st = nullptr;
-  SolverState* st_scratch = nullptr;
-  SolverState* st_host = nullptr;  // pinned
-  int* flag = nullptr;
-  int* flag_host = nullptr;        // pinned
-  double* scalars_host = nullptr;  // pinned
-  // device staging for the host-buffer entry point
-  float* d_g = nullptr;
-  float* d_gamma = nullptr;
-  float* d_finit = nullptr;
-  float* d_fout = nullptr;
-  // graph cache
-  cudaGraphExec_t gexec = nullptr;
-  std::string gkey;
-  int graph_iters = 0;
-};
-
 }  // namespace
-
-struct appga_ctx {
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-};
-
-struct appga_matrix {
-  appga_ctx* ctx = nullptr;
-  int32_t m = 0, d = 0, n = 0, na = 0;
-  int64_t nnz = 0;
-  DevCSR A, At;
-  float* inv_lambda = nullptr;       // 1/Lambda of the FP32 values
-  float* inv_lambda_bf16 = nullptr;  // 1/Lambda of the BF16-rounded values
-  int32_t has_bf16 = 0;
-  int64_t bytes = 0;
-  long long npfov = 0;  // pixels of the initial-image disk
-  Workspace ws;
-};
 
 namespace appga {
 void set_error(const std::string& msg) { g_last_error = msg; }
-}  // namespace appga
-
-namespace {
 
 appga_status fail(appga_status s, const std::string& msg) {
   g_last_error = msg;
@@ -90,22 +39,11 @@ appga_status cuda_fail(cudaError_t e, const char* what) {
     return APPGA_ENODEV;
   return APPGA_ECUDA;
 }
+}  // namespace appga
 
-#define CK(call)                                              \
-  do {                                                        \
-    cudaError_t e_ = (call);                                  \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
-  } while (0)
+namespace {
 
-template <typename T>
-cudaError_t dalloc(T** p, size_t count, int64_t* bytes = nullptr) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  const size_t b = count * sizeof(T);
-  cudaError_t e = cudaMalloc((void**)p, b);
-  if (e == cudaSuccess && bytes) *bytes += (int64_t)b;
-  return e;
-}
+#define CK(call) APPGA_CK(call)
 
 void free_csr(DevCSR& c) {
   cudaFree(c.row_ptr);
@@ -442,8 +380,11 @@ appga_status validate_inputs(appga_matrix* M, const float* g, const float* gamma
   return APPGA_OK;
 }
 
+}  // namespace
+
+namespace appga {
 // Orders ctx->stream after the caller's stream.
-appga_status enter(appga_ctx* ctx, void* stream) {
+appga_status enter_stream(appga_ctx* ctx, void* stream) {
   cudaStream_t us = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device));
   CK(cudaEventRecord(ctx->ev_in, us));
@@ -451,12 +392,17 @@ appga_status enter(appga_ctx* ctx, void* stream) {
   return APPGA_OK;
 }
 // Orders the caller's stream after ctx->stream.
-appga_status leave(appga_ctx* ctx, void* stream) {
+appga_status leave_stream(appga_ctx* ctx, void* stream) {
   cudaStream_t us = (cudaStream_t)stream;
   CK(cudaEventRecord(ctx->ev_out, ctx->stream));
   CK(cudaStreamWaitEvent(us, ctx->ev_out, 0));
   return APPGA_OK;
 }
+}  // namespace appga
+
+namespace {
+using appga::enter_stream;
+using appga::leave_stream;
 
 appga_status objective_on(appga_matrix* M, const float* f, const float* g, const float* gamma,
                           const appga_params* p, double* phi, cudaStream_t s) {
@@ -497,7 +443,7 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
   if (p->precond_freeze_iter >= 0 && k0 > p->precond_freeze_iter)
     return fail(APPGA_EINVAL, "resume past the preconditioner freeze iteration is not supported");
   if ((rc = ensure_workspace(M)) != APPGA_OK) return rc;
-  if ((rc = enter(ctx, stream)) != APPGA_OK) return rc;
+  if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
   cudaStream_t s = ctx->stream;
   Workspace& ws = M->ws;
   if ((rc = validate_inputs(M, g, gamma, fresh ? f_cur : f_prev, s)) != APPGA_OK) return rc;
@@ -529,7 +475,7 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
     if (r2 != APPGA_OK) return r2;
     stats->phi = phi;
   }
-  appga_status r3 = leave(ctx, stream);
+  appga_status r3 = leave_stream(ctx, stream);
   if (r3 != APPGA_OK) return r3;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return rc;
@@ -729,6 +675,10 @@ appga_status appga_matrix_destroy(appga_matrix* M) {
   cudaFree(M->inv_lambda);
   cudaFree(M->inv_lambda_bf16);
   free_workspace(M->ws);
+  if (M->bw) {
+    appga::free_batch_workspace(M->bw);
+    delete M->bw;
+  }
   delete M;
   return APPGA_OK;
 }

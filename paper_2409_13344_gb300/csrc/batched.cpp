@@ -1,0 +1,306 @@
+// Batched C ABI: K slices sharing one matrix, iterated together by the
+// slot-minor SpMM kernels under captured CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "appga.h"
+#include "appga_internal.h"
+#include "batched_internal.h"
+#include "handles.h"
+
+namespace appga {
+
+void free_batch_workspace(BatchWorkspace* bw) {
+  if (!bw) return;
+  if (bw->gexec) cudaGraphExecDestroy(bw->gexec);
+  for (auto& p : bw->f) cudaFree(p);
+  for (auto& p : bw->y) cudaFree(p);
+  cudaFree(bw->w);
+  cudaFree(bw->gR);
+  cudaFree(bw->pfreeze);
+  cudaFree(bw->g);
+  cudaFree(bw->gamma);
+  cudaFree(bw->slots);
+  cudaFree(bw->bst);
+  cudaFree(bw->partial);
+  cudaFree(bw->gtick);
+  cudaFree(bw->flag);
+  cudaFreeHost(bw->slots_host);
+  cudaFreeHost(bw->bst_host);
+  cudaFreeHost(bw->flag_host);
+  *bw = BatchWorkspace();
+}
+
+namespace {
+
+constexpr int kBatchGraphIters = 8;
+
+int padded_width(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
+
+appga_status ensure_batch_workspace(appga_matrix* M, int Kp) {
+  if (M->bw && M->bw->Kp == Kp) return APPGA_OK;
+  if (M->bw) {
+    free_batch_workspace(M->bw);
+  } else {
+    M->bw = new BatchWorkspace();
+  }
+  BatchWorkspace& b = *M->bw;
+  const size_t d = (size_t)M->d * Kp, m = (size_t)M->m * Kp;
+  const int maxb = batch_max_blocks();
+  const int ngroups = maxb / 64 + 2;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(&b.f[i], d);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(&b.y[i], m);
+  if (e == cudaSuccess) e = dalloc(&b.w, m);
+  if (e == cudaSuccess) e = dalloc(&b.gR, d);
+  if (e == cudaSuccess) e = dalloc(&b.pfreeze, d);
+  if (e == cudaSuccess) e = dalloc(&b.g, m);
+  if (e == cudaSuccess) e = dalloc(&b.gamma, m);
+  if (e == cudaSuccess) e = dalloc(&b.slots, (size_t)Kp);
+  if (e == cudaSuccess) e = dalloc(&b.bst, 1);
+  if (e == cudaSuccess) e = dalloc(&b.partial, (size_t)(maxb + ngroups + 2) * Kp);
+  if (e == cudaSuccess) e = dalloc(&b.gtick, (size_t)ngroups);
+  if (e == cudaSuccess) e = dalloc(&b.flag, 1);
+  if (e == cudaSuccess) e = cudaMemset(b.gtick, 0, (size_t)ngroups * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(b.bst, 0, sizeof(BatchState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b.slots_host, Kp * sizeof(SlotState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b.bst_host, sizeof(BatchState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b.flag_host, sizeof(int));
+  if (e != cudaSuccess) {
+    free_batch_workspace(M->bw);
+    delete M->bw;
+    M->bw = nullptr;
+    return cuda_fail(e, "batched workspace allocation");
+  }
+  b.Kp = Kp;
+  b.m = M->m;
+  b.d = M->d;
+  return APPGA_OK;
+}
+
+SlotState slot_from_params(const appga_params* p, int k0, bool active) {
+  SlotState s{};
+  s.active = active ? 1 : 0;
+  s.k = k0;
+  s.k0 = k0;
+  s.k_last = k0 + p->max_iters - 1;
+  s.done = (active && p->max_iters > 0) ? 0 : 1;
+  s.result_k = k0;
+  s.freeze_iter = p->precond_freeze_iter;
+  s.momentum = p->momentum;
+  s.lambda1 = (float)p->lambda1;
+  s.lambda2 = (float)p->lambda2;
+  s.eps = (float)p->eps;
+  s.beta = (float)p->beta;
+  s.omega = p->omega;
+  s.a = p->a;
+  s.b = p->b;
+  s.rel_tol = p->rel_obj_tol;
+  s.phi_cur = std::numeric_limits<double>::quiet_NaN();
+  s.phi_prev = s.phi_cur;
+  return s;
+}
+
+#define CK(call) APPGA_CK(call)
+
+}  // namespace
+}  // namespace appga
+
+using namespace appga;
+
+extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat,
+                                                  int32_t K, const float* g, const float* gamma,
+                                                  const float* f_init, const appga_params* params,
+                                                  float* f_out, appga_stats* stats_host,
+                                                  void* stream) {
+  if (!ctx || !mat || !g || !gamma || !params || !f_out) return fail(APPGA_EINVAL, "null argument");
+  if (mat->ctx != ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
+  if (K < 1 || K > 128) return fail(APPGA_EINVAL, "K must be in [1, 128]");
+  appga_status rc = appga_params_validate(params);
+  if (rc != APPGA_OK) return rc;
+  auto* M = const_cast<appga_matrix*>(mat);
+  const int Kp = padded_width(K);
+  if ((rc = ensure_batch_workspace(M, Kp)) != APPGA_OK) return rc;
+  if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
+  BatchWorkspace& b = *M->bw;
+  cudaStream_t s = ctx->stream;
+  const int m = M->m, d = M->d, n = M->n;
+  const bool track = params->track_objective != 0 || params->rel_obj_tol > 0.0;
+  const bool bf16 = params->a_precision == APPGA_PREC_BF16 && M->has_bf16;
+
+  // input checks (g >= 0, gamma > 0, f_init >= 0, all finite) over every slice
+  CK(cudaMemsetAsync(b.flag, 0, sizeof(int), s));
+  CK(launch_validate_inputs(g, gamma, K * m, f_init, K * d, b.flag, s));
+  CK(cudaMemcpyAsync(b.flag_host, b.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*b.flag_host)
+    return fail(APPGA_EDOMAIN,
+                "inputs must satisfy: g finite and >= 0, gamma finite and > 0, f finite and >= 0");
+
+  // slot-minor copies of the sinograms; padding slots hold harmless data
+  CK(launch_to_slot_minor(g, K, m, b.g, Kp, 0, s));
+  CK(launch_to_slot_minor(gamma, K, m, b.gamma, Kp, 0, s));
+  CK(launch_fill_slots(b.g, m, Kp, K, Kp, 0.f, s));
+  CK(launch_fill_slots(b.gamma, m, Kp, K, Kp, 1.f, s));
+
+  // f^0 = f^1 = f_init (or the per-slice initial image) in the ring slots of step G0
+  const int G0 = 1;
+  float* cur = b.f[G0 % 3];
+  if (f_init) {
+    CK(launch_to_slot_minor(f_init, K, d, cur, Kp, 0, s));
+  } else {
+    CK(launch_binit_image(g, gamma, m, n, M->na, M->npfov, K, Kp, 0, cur, s));
+  }
+  CK(launch_fill_slots(cur, d, Kp, K, Kp, 0.f, s));
+  CK(cudaMemcpyAsync(b.f[(G0 + 2) % 3], cur, (size_t)d * Kp * sizeof(float),
+                     cudaMemcpyDeviceToDevice, s));
+
+  for (int i = 0; i < Kp; ++i) b.slots_host[i] = slot_from_params(params, 1, i < K);
+  CK(cudaMemcpyAsync(b.slots, b.slots_host, Kp * sizeof(SlotState), cudaMemcpyHostToDevice, s));
+  CK(launch_binit_momentum(b.slots, Kp, s));
+  BatchState hb{};
+  hb.gstep = G0;
+  hb.remaining = params->max_iters > 0 ? K : 0;
+  *b.bst_host = hb;
+  CK(cudaMemcpyAsync(b.bst, b.bst_host, sizeof(BatchState), cudaMemcpyHostToDevice, s));
+
+  BFwdArgs fa{};
+  fa.A = M->A;
+  fa.n = n;
+  fa.Kp = Kp;
+  fa.track = track ? 1 : 0;
+  fa.use_bf16 = bf16 ? 1 : 0;
+  for (int i = 0; i < 3; ++i) fa.f[i] = b.f[i];
+  fa.y[0] = b.y[0];
+  fa.y[1] = b.y[1];
+  fa.w = b.w;
+  fa.g = b.g;
+  fa.gamma = b.gamma;
+  fa.gR = b.gR;
+  fa.slots = b.slots;
+  fa.bst = b.bst;
+  fa.partial = b.partial;
+  fa.gtick = b.gtick;
+  BPixArgs pa{};
+  pa.At = M->At;
+  pa.n = n;
+  pa.Kp = Kp;
+  pa.use_bf16 = bf16 ? 1 : 0;
+  for (int i = 0; i < 3; ++i) pa.f[i] = b.f[i];
+  pa.w = b.w;
+  pa.gR = b.gR;
+  pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
+  pa.pfreeze = b.pfreeze;
+  pa.slots = b.slots;
+  pa.bst = b.bst;
+  pa.partial = b.partial;
+  pa.gtick = b.gtick;
+
+  // y^{k0-1}, then the first forward phase (w, y, stencil, Phi of f^{k0})
+  BFwdArgs init = fa;
+  init.mode = 1;
+  CK(launch_bforward(init, s));
+  CK(launch_bforward(fa, s));
+
+  if (params->max_iters > 0) {
+    const int S = params->graph_iters > 0 ? params->graph_iters : kBatchGraphIters;
+    char key[256];
+    std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d", Kp, (int)track, (int)bf16, S, K);
+    if (b.gexec == nullptr || b.gkey != key) {
+      if (b.gexec) {
+        cudaGraphExecDestroy(b.gexec);
+        b.gexec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < S && e == cudaSuccess; ++i) {
+        e = launch_bpixel(pa, s);
+        if (e == cudaSuccess) e = launch_bforward(fa, s);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+      if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e, "batched graph capture");
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&b.gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      b.gkey = key;
+    }
+    const int reps = (params->max_iters + S - 1) / S;
+    if (params->rel_obj_tol > 0.0) {
+      cudaEvent_t ev[2];
+      CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+      appga_status prc = APPGA_OK;
+      for (int r = 0; r < reps; ++r) {
+        cudaError_t e = cudaGraphLaunch(b.gexec, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(&b.bst_host->remaining, &b.bst->remaining, sizeof(int),
+                              cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[r & 1], s);
+        if (e != cudaSuccess) {
+          prc = cuda_fail(e, "batched graph replay");
+          break;
+        }
+        if (r >= 1) {
+          e = cudaEventSynchronize(ev[(r - 1) & 1]);
+          if (e != cudaSuccess) {
+            prc = cuda_fail(e, "cudaEventSynchronize");
+            break;
+          }
+          if (b.bst_host->remaining == 0) break;
+        }
+      }
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+      if (prc != APPGA_OK) return prc;
+    } else {
+      for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(b.gexec, s));
+    }
+  }
+  CK(cudaMemcpyAsync(b.bst_host, b.bst, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(b.slots_host, b.slots, Kp * sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int Gf = b.bst_host->gstep;
+  CK(launch_from_slot_minor(b.f[Gf % 3], K, d, Kp, 0, f_out, s));
+  rc = APPGA_OK;
+  if (b.bst_host->flags & APPGA_FLAG_NONFINITE) rc = fail(APPGA_ENUMERIC, "a non-finite value appeared");
+  if (stats_host) {
+    for (int i = 0; i < K; ++i) {
+      const SlotState& sl = b.slots_host[i];
+      appga_stats& st = stats_host[i];
+      st.iters = sl.result_k - sl.k0;
+      st.result_k = sl.result_k;
+      st.stopped_early = sl.stopped_early;
+      st.flags = b.bst_host->flags;
+      st.guard_hits = (int64_t)sl.guard_hits;
+      st.phi = std::numeric_limits<double>::quiet_NaN();
+      st.phi_prev = std::numeric_limits<double>::quiet_NaN();
+      if (track) st.phi_prev = sl.stopped_early ? sl.phi_prev : sl.phi_cur;
+    }
+    if (track) {
+      // Phi of every result image in FP64 (single-slice objective)
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i < K; ++i) {
+        double phi = 0.0;
+        appga_status r2 = appga_objective(ctx, mat, f_out + (size_t)i * d, g + (size_t)i * m,
+                                          gamma + (size_t)i * m, params, &phi, (void*)s);
+        if (r2 != APPGA_OK) return r2;
+        stats_host[i].phi = phi;
+      }
+    }
+  }
+  appga_status r3 = leave_stream(ctx, stream);
+  if (r3 != APPGA_OK) return r3;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return rc;
+}

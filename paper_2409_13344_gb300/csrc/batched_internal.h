@@ -1,0 +1,88 @@
+// Device structures and launchers of the batched (multi-slice) kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "appga_internal.h"
+
+namespace appga {
+
+// Per-slot device state: iteration index, momentum, objective, stop flag and
+// the slot's model parameters.  Slots are independent problems sharing A.
+struct SlotState {
+  int32_t k;          // index of the slot's current iterate
+  int32_t k0;         // first index of the slot's run
+  int32_t k_last;     // last step index to run
+  int32_t done;       // finished (iteration cap or stopping test)
+  int32_t result_k;   // index of the slot's result
+  int32_t stopped_early;
+  int32_t active;     // the slot holds a problem
+  int32_t freeze_iter;
+  int32_t momentum;
+  int32_t pad0;
+  float theta_hi, theta_lo;  // theta_k as a double-float pair
+  float lambda1, lambda2, eps, beta;
+  double theta, t_cur, phi_cur, phi_prev;
+  double omega, a, b, rel_tol;
+  unsigned long long guard_hits;
+};
+
+struct BatchState {
+  int32_t gstep;      // global step: ring slot of the current iterates
+  int32_t remaining;  // live slots
+  int32_t flags;
+  int32_t pad;
+  unsigned int ticket_r, ticket_p, ticket_aux, pad2;
+};
+
+struct BFwdArgs {
+  DevCSR A;
+  int32_t n, Kp;
+  int32_t mode;  // 0: solver step; 1: project the previous iterate only
+  int32_t track;
+  int32_t use_bf16;
+  int32_t n_spmv_blocks;  // set by the launcher
+  float* f[3];
+  float* y[2];
+  float* w;
+  const float* g;
+  const float* gamma;
+  float* gR;
+  SlotState* slots;
+  BatchState* bst;
+  float2* partial;
+  unsigned int* gtick;
+};
+
+struct BPixArgs {
+  DevCSR At;
+  int32_t n, Kp;
+  int32_t use_bf16;
+  int32_t pad;
+  float* f[3];
+  const float* w;
+  const float* gR;
+  const float* inv_lambda;
+  float* pfreeze;
+  SlotState* slots;
+  BatchState* bst;
+  float2* partial;
+  unsigned int* gtick;
+};
+
+int batch_max_blocks();
+cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s);
+cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s);
+cudaError_t launch_binit_momentum(SlotState* slots, int Kp, cudaStream_t s);
+cudaError_t launch_to_slot_minor(const float* in, int K, int len, float* out, int Kp, int s0,
+                                 cudaStream_t s);
+cudaError_t launch_from_slot_minor(const float* in, int K, int len, int Kp, int s0, float* out,
+                                   cudaStream_t s);
+cudaError_t launch_fill_slots(float* out, int len, int Kp, int s0, int s1, float v, cudaStream_t s);
+cudaError_t launch_binit_image(const float* g, const float* gamma, int m, int n, int n_angles,
+                               long long npfov, int K, int Kp, int s0, float* f_out,
+                               cudaStream_t s);
+
+}  // namespace appga

@@ -1,0 +1,119 @@
+// Host-side definitions of the opaque handles and the helpers shared by the
+// translation units of the C ABI (single-slice API, batched API, server).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "appga.h"
+#include "appga_internal.h"
+#include "batched_internal.h"
+
+namespace appga {
+
+// Device workspace of the single-slice solver (per matrix, allocated lazily).
+struct Workspace {
+  bool ready = false;
+  int m = 0, d = 0;
+  float* f[3] = {nullptr, nullptr, nullptr};
+  float2* y[2] = {nullptr, nullptr};  // A f^k as double-float pairs
+  float* w = nullptr;
+  float* gR = nullptr;  // B^T grad phi~(B f~) of the current iterate
+  float* pfreeze = nullptr;
+  float2* partial_p = nullptr;
+  float2* partial_r = nullptr;
+  float2* partial_aux = nullptr;
+  unsigned int* gtick = nullptr;  // group tickets of the grid reductions
+  double* scalars = nullptr;      // device doubles for standalone results
+  SolverState* st = nullptr;
+  SolverState* st_scratch = nullptr;
+  SolverState* st_host = nullptr;  // pinned
+  int* flag = nullptr;
+  int* flag_host = nullptr;        // pinned
+  double* scalars_host = nullptr;  // pinned
+  // device staging for the host-buffer entry point
+  float* d_g = nullptr;
+  float* d_gamma = nullptr;
+  float* d_finit = nullptr;
+  float* d_fout = nullptr;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  int graph_iters = 0;
+};
+
+// Device workspace of the batched solver for one padded batch width Kp.
+struct BatchWorkspace {
+  int Kp = 0, m = 0, d = 0;
+  float* f[3] = {nullptr, nullptr, nullptr};  // [d][Kp]
+  float* y[2] = {nullptr, nullptr};           // [m][Kp]
+  float* w = nullptr;                         // [m][Kp]
+  float* gR = nullptr;                        // [d][Kp]
+  float* pfreeze = nullptr;                   // [d][Kp]
+  float* g = nullptr;                         // [m][Kp]
+  float* gamma = nullptr;                     // [m][Kp]
+  SlotState* slots = nullptr;                 // [Kp]
+  SlotState* slots_host = nullptr;            // pinned [Kp]
+  BatchState* bst = nullptr;
+  BatchState* bst_host = nullptr;             // pinned
+  float2* partial = nullptr;                  // (blocks + groups) x Kp
+  unsigned int* gtick = nullptr;
+  int* flag = nullptr;
+  int* flag_host = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+};
+
+void free_batch_workspace(BatchWorkspace* bw);
+
+}  // namespace appga
+
+struct appga_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+struct appga_matrix {
+  appga_ctx* ctx = nullptr;
+  int32_t m = 0, d = 0, n = 0, na = 0;
+  int64_t nnz = 0;
+  appga::DevCSR A, At;
+  float* inv_lambda = nullptr;       // 1/Lambda of the FP32 values
+  float* inv_lambda_bf16 = nullptr;  // 1/Lambda of the BF16-rounded values
+  int32_t has_bf16 = 0;
+  int64_t bytes = 0;
+  long long npfov = 0;  // pixels of the initial-image disk
+  appga::Workspace ws;
+  appga::BatchWorkspace* bw = nullptr;  // batched workspace (one width at a time)
+};
+
+namespace appga {
+
+appga_status fail(appga_status s, const std::string& msg);
+appga_status cuda_fail(cudaError_t e, const char* what);
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, int64_t* bytes = nullptr) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  const size_t b = count * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, b);
+  if (e == cudaSuccess && bytes) *bytes += (int64_t)b;
+  return e;
+}
+
+// Orders ctx->stream after the caller's stream / the caller's after ctx->stream.
+appga_status enter_stream(appga_ctx* ctx, void* stream);
+appga_status leave_stream(appga_ctx* ctx, void* stream);
+
+}  // namespace appga
+
+#define APPGA_CK(call)                                               \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) return ::appga::cuda_fail(e_, #call);     \
+  } while (0)

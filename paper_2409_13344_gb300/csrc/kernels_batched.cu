@@ -1,0 +1,732 @@
+// Batched CUDA kernels: K independent slices (slots) that share one system
+// matrix run the APPGA iteration together, so every nonzero of A and A^T is
+// read once per iteration for all K right-hand sides (CSR SpMM).
+//
+// Layout (slot-minor): images f[j][s], sinograms y[i][s], w[i][s], g[i][s]
+// with K padded to Kp = 32 V (V = 1, 2 or 4 slots per lane).  One warp owns
+// a CSR row: lanes load 32 (column, value) pairs at a time, then for each
+// nonzero the column is broadcast by shuffle and the warp gathers the Kp-wide
+// image row (one coalesced 4V-byte vector per lane) and accumulates V
+// products per lane in FP32.  The per-(row, slot) epilogues match the
+// single-slice kernels (Eq. APPGAiter, Eq. EM, Sec. 2.2); the SHOITV stencil
+// runs on shared-memory tiles of 2 x 32 pixels x 8 slots.
+//
+// Every slot carries its own device state (iteration index, momentum scalar,
+// objective, stop flag, parameters), so slots may sit at different
+// iterations (continuous batching).  The iterate rings are indexed by a
+// global step counter shared by all slots.  Per-slot objective sums use the
+// deterministic two-level grid reduction, so results do not depend on which
+// other slots are in the batch.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "appga_internal.h"
+#include "batched_internal.h"
+#include "device_common.cuh"
+
+namespace appga {
+namespace {
+
+constexpr int B_THREADS = 256;
+constexpr int B_WARPS = B_THREADS / 32;
+constexpr int MAXK = 128;                    // largest padded batch (V = 4)
+constexpr int BST_R = 2, BST_C = 32, BST_S = 8;  // stencil item: 2 x 32 pixels x 8 slots
+constexpr int BTW = BST_C + 4, BVW = BST_C + 2;
+static_assert(BST_C * BST_S == B_THREADS, "stencil: one thread per (column, slot)");
+
+template <int V>
+__device__ __forceinline__ void vload(const float* p, float (&x)[V]) {
+  if constexpr (V == 1) {
+    x[0] = __ldg(p);
+  } else if constexpr (V == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+  } else {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+  }
+}
+template <int V>
+__device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
+  if constexpr (V == 1) {
+    p[0] = x[0];
+  } else if constexpr (V == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  }
+}
+
+// One CSR row of M times the Kp-wide columns of X ([cols][Kp]): lane holds
+// the V sums of slots lane*V .. lane*V + V - 1.
+template <int V, bool BF16>
+__device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* __restrict__ X,
+                                         int Kp, int lane, uint64_t pol, float (&acc)[V]) {
+#pragma unroll
+  for (int t = 0; t < V; ++t) acc[t] = 0.f;
+  const int s = __ldg(M.row_ptr + row), e = __ldg(M.row_ptr + row + 1);
+  const float* xl = X + lane * V;
+  for (int p0 = s; p0 < e; p0 += 32) {
+    const int p = p0 + lane;
+    int c = 0;
+    float v = 0.f;
+    if (p < e) {
+      c = ld_stream_i1(M.col + p, pol);
+      v = BF16 ? ld_stream_bf16_1(M.val_bf16 + p, pol) : ld_stream_f1(M.val + p, pol);
+    }
+    const int cnt = min(32, e - p0);  // a multiple of 4 (rows are padded)
+    for (int q = 0; q < cnt; q += 4) {
+      int cq[4];
+      float vq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cq[u] = __shfl_sync(0xffffffffu, c, q + u);
+        vq[u] = __shfl_sync(0xffffffffu, v, q + u);
+      }
+      float x[4][V];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vload<V>(xl + (size_t)cq[u] * Kp, x[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc[t] = fmaf(vq[u], x[u][t], acc[t]);
+    }
+  }
+}
+
+// ------------------------------------------------- per-slot grid reduction
+// Two-level deterministic reduction of Kp double-float values per block
+// (p_hi/p_lo in shared memory).  True in the final block, where tot_hi /
+// tot_lo (shared) hold the per-slot totals.  Partial layout: block b at
+// partial[b*Kp .. ), group g result at partial[(nb + g)*Kp .. ).
+__device__ bool grid_reduce_slots(float2* partial, unsigned int* gtick, unsigned int* ftick,
+                                  const float* p_hi, const float* p_lo, int Kp, float* tot_hi,
+                                  float* tot_lo) {
+  __shared__ int s_flag;
+  __shared__ float r_hi[B_THREADS], r_lo[B_THREADS];
+  const int nb = gridDim.x, b = blockIdx.x, g = b / RED_GROUP, tid = threadIdx.x;
+  const int ngroups = (nb + RED_GROUP - 1) / RED_GROUP;
+  const int gsize = min(RED_GROUP, nb - g * RED_GROUP);
+  for (int s = tid; s < Kp; s += blockDim.x) partial[(size_t)b * Kp + s] = make_float2(p_hi[s], p_lo[s]);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_flag = (atomicAdd(&gtick[g], 1u) == (unsigned)(gsize - 1));
+  __syncthreads();
+  if (!s_flag) return false;
+  __threadfence();
+  const int P = blockDim.x / Kp;  // parts per slot
+  auto reduce_rows = [&](const float2* base, int count) {
+    const int s = tid % Kp, part = tid / Kp;
+    float h = 0.f, l = 0.f;
+    if (part < P) {
+      for (int i = part; i < count; i += P) {
+        const float2 v = __ldcg(base + (size_t)i * Kp + s);
+        acc_add(h, l, v.x, v.y);
+      }
+    }
+    r_hi[tid] = h;
+    r_lo[tid] = l;
+    __syncthreads();
+    if (tid < Kp) {
+      float hh = 0.f, ll = 0.f;
+      for (int q = 0; q < P; ++q) acc_add(hh, ll, r_hi[q * Kp + tid], r_lo[q * Kp + tid]);
+      tot_hi[tid] = hh;
+      tot_lo[tid] = ll;
+    }
+    __syncthreads();
+  };
+  reduce_rows(partial + (size_t)g * RED_GROUP * Kp, gsize);
+  for (int s = tid; s < Kp; s += blockDim.x)
+    partial[(size_t)(nb + g) * Kp + s] = make_float2(tot_hi[s], tot_lo[s]);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    gtick[g] = 0;
+    s_flag = (atomicAdd(ftick, 1u) == (unsigned)(ngroups - 1));
+  }
+  __syncthreads();
+  if (!s_flag) return false;
+  __threadfence();
+  reduce_rows(partial + (size_t)nb * Kp, ngroups);
+  if (tid == 0) *ftick = 0;
+  return true;
+}
+
+// --------------------------------------------------------------- stencil
+
+struct BStencilSmem {
+  float T[BST_R + 4][BTW][BST_S];
+  float K[BST_R + 4][BTW][BST_S];
+  float V[6][BST_R + 2][BVW][BST_S];
+};
+
+// One stencil item: tile (r0, c0) for slots s0 .. s0+7.  Thread (col, q) =
+// (tid % 32, tid / 32).  Writes gR and returns this thread's regulariser
+// share of Phi(f^k) for slot s0 + q (both tile rows).
+__device__ float bstencil_item(BStencilSmem& S, const float* __restrict__ fk,
+                               const float* __restrict__ fkm, const SlotState* slots, int Kp,
+                               int r0, int c0, int s0, int n, float* __restrict__ gR,
+                               bool want_reg) {
+  const int tid = threadIdx.x;
+  // load the halo tile, slots fastest (32-byte runs)
+  for (int t = tid; t < (BST_R + 4) * BTW * BST_S; t += blockDim.x) {
+    const int q = t % BST_S, pix = t / BST_S;
+    const int ii = pix / BTW, jj = pix % BTW;
+    const int r = r0 - 2 + ii, c = c0 - 2 + jj;
+    float vk = 0.f, vt = 0.f;
+    if (r >= 0 && r < n && c >= 0 && c < n) {
+      const size_t o = (size_t)(r * n + c) * Kp + s0 + q;
+      vk = fk[o];
+      vt = fmaf(slots[s0 + q].theta_hi, vk - fkm[o], vk);
+    }
+    S.K[ii][jj][q] = vk;
+    S.T[ii][jj][q] = vt;
+  }
+  __syncthreads();
+  for (int t = tid; t < (BST_R + 2) * BVW * BST_S; t += blockDim.x) {
+    const int q = t % BST_S, pix = t / BST_S;
+    const int ii = pix / BVW, jj = pix % BVW;
+    const int r = r0 - 1 + ii, c = c0 - 1 + jj;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r >= 0 && r < n && c >= 0 && c < n) {
+      const SlotState& sl = slots[s0 + q];
+      // the six fields of B at (r, c) of slot s0 + q (same forms as the single-slice stencil)
+      const int i = ii + 1, j = jj + 1;
+      const bool r_lo = r >= 1, r_hi = r <= n - 2, c_lo = c >= 1, c_hi = c <= n - 2;
+      auto X = [&](int a, int b) { return S.T[a][b][q]; };
+      float u[6];
+      u[0] = c_lo ? X(i, j) - X(i, j - 1) : 0.f;
+      u[1] = r_lo ? X(i, j) - X(i - 1, j) : 0.f;
+      u[2] = (c_lo ? -(X(i, j) - X(i, j - 1)) : 0.f) + (c_hi ? X(i, j + 1) - X(i, j) : 0.f);
+      u[3] = c_lo ? ((r_lo ? -(X(i, j) - X(i, j - 1)) : 0.f) +
+                     (r_hi ? X(i + 1, j) - X(i + 1, j - 1) : 0.f))
+                  : 0.f;
+      u[4] = (r_lo ? -(X(i, j) - X(i - 1, j)) : 0.f) + (r_hi ? X(i + 1, j) - X(i, j) : 0.f);
+      u[5] = r_lo ? ((c_lo ? -(X(i, j) - X(i - 1, j)) : 0.f) +
+                     (c_hi ? X(i, j + 1) - X(i - 1, j + 1) : 0.f))
+                  : 0.f;
+      const float n1 = u[0] * u[0] + u[1] * u[1];
+      const float n2 = u[2] * u[2] + u[3] * u[3] + u[4] * u[4] + u[5] * u[5];
+      const float s1 = sl.lambda1 / fmaxf(sqrtf(n1), sl.eps);
+      const float s2 = sl.lambda2 / fmaxf(sqrtf(n2), sl.eps);
+      v[0] = s1 * u[0];
+      v[1] = s1 * u[1];
+      v[2] = s2 * u[2];
+      v[3] = s2 * u[3];
+      v[4] = s2 * u[4];
+      v[5] = s2 * u[5];
+    }
+#pragma unroll
+    for (int f = 0; f < 6; ++f) S.V[f][ii][jj][q] = v[f];
+  }
+  __syncthreads();
+  const int col = tid % BST_C, q = tid / BST_C;
+  const SlotState& sl = slots[s0 + q];
+  float reg = 0.f;
+#pragma unroll
+  for (int ii = 0; ii < BST_R; ++ii) {
+    const int r = r0 + ii, c = c0 + col;
+    if (r < n && c < n) {
+      const int i = ii + 1, j = col + 1;
+      const bool r_lo = r >= 1, r_hi = r <= n - 2, c_lo = c >= 1, c_hi = c <= n - 2;
+      auto W = [&](int f, int a, int b) { return S.V[f][a][b][q]; };
+      float gsum = 0.f;
+      if (c_lo) gsum += W(0, i, j);
+      if (c_hi) gsum -= W(0, i, j + 1);
+      if (r_lo) gsum += W(1, i, j);
+      if (r_hi) gsum -= W(1, i + 1, j);
+      // u3-form of v3, u6-form of v4, u5-form of v5, u4-form of v6
+      gsum += (c_lo ? -(W(2, i, j) - W(2, i, j - 1)) : 0.f) + (c_hi ? W(2, i, j + 1) - W(2, i, j) : 0.f);
+      gsum += r_lo ? ((c_lo ? -(W(3, i, j) - W(3, i - 1, j)) : 0.f) +
+                      (c_hi ? W(3, i, j + 1) - W(3, i - 1, j + 1) : 0.f))
+                   : 0.f;
+      gsum += (r_lo ? -(W(4, i, j) - W(4, i - 1, j)) : 0.f) + (r_hi ? W(4, i + 1, j) - W(4, i, j) : 0.f);
+      gsum += c_lo ? ((r_lo ? -(W(5, i, j) - W(5, i, j - 1)) : 0.f) +
+                      (r_hi ? W(5, i + 1, j) - W(5, i + 1, j - 1) : 0.f))
+                   : 0.f;
+      gR[(size_t)(r * n + c) * Kp + s0 + q] = gsum;
+      if (want_reg) {
+        auto Kf = [&](int a, int b) { return S.K[a][b][q]; };
+        const int a = ii + 2, b = col + 2;
+        float u[6];
+        u[0] = c_lo ? Kf(a, b) - Kf(a, b - 1) : 0.f;
+        u[1] = r_lo ? Kf(a, b) - Kf(a - 1, b) : 0.f;
+        u[2] = (c_lo ? -(Kf(a, b) - Kf(a, b - 1)) : 0.f) + (c_hi ? Kf(a, b + 1) - Kf(a, b) : 0.f);
+        u[3] = c_lo ? ((r_lo ? -(Kf(a, b) - Kf(a, b - 1)) : 0.f) +
+                       (r_hi ? Kf(a + 1, b) - Kf(a + 1, b - 1) : 0.f))
+                    : 0.f;
+        u[4] = (r_lo ? -(Kf(a, b) - Kf(a - 1, b)) : 0.f) + (r_hi ? Kf(a + 1, b) - Kf(a, b) : 0.f);
+        u[5] = r_lo ? ((c_lo ? -(Kf(a, b) - Kf(a - 1, b)) : 0.f) +
+                       (c_hi ? Kf(a, b + 1) - Kf(a - 1, b + 1) : 0.f))
+                    : 0.f;
+        const float n1 = u[0] * u[0] + u[1] * u[1];
+        const float n2 = u[2] * u[2] + u[3] * u[3] + u[4] * u[4] + u[5] * u[5];
+        reg += sl.lambda1 * s_eps_f(n1, sl.eps) + sl.lambda2 * s_eps_f(n2, sl.eps);
+      }
+    }
+  }
+  __syncthreads();  // the tile buffers are reused by the next item
+  return reg;
+}
+
+__device__ double bgn_t(int k, double a, double b, double omega) {
+  return a * pow((double)k, omega) + b;
+}
+__device__ void bset_theta(SlotState& s, double theta) {
+  s.theta = theta;
+  const float h = (float)theta;
+  s.theta_hi = h;
+  s.theta_lo = (float)(theta - (double)h);
+}
+
+// -------------------------------------------------------------- k_bforward
+
+template <int V, bool BF16>
+__global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
+  __shared__ union {
+    struct {
+      float dhi[B_WARPS][MAXK];
+      float dlo[B_WARPS][MAXK];
+      float bhi[MAXK], blo[MAXK];
+      float thi[MAXK], tlo[MAXK];
+    } e;
+    BStencilSmem st;
+  } sm;
+  BatchState* bs = a.bst;
+  if (a.mode == 0 && bs->remaining == 0) return;  // uniform over the grid
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Kp = a.Kp, n = a.n;
+  const int G = bs->gstep;
+  const float* f = a.mode == 0 ? a.f[G % 3] : a.f[(G + 2) % 3];
+  float* y_out = a.mode == 0 ? a.y[G & 1] : a.y[(G + 1) & 1];
+  const float* y_prev = a.y[(G + 1) & 1];
+  const bool loop = a.mode == 0;
+  const bool want = loop && a.track;
+  // per-slot data-term accumulators of this lane
+  float dh[V], dl[V];
+  int hits[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    dh[t] = 0.f;
+    dl[t] = 0.f;
+    hits[t] = 0;
+  }
+  float th_h[V], gam_k[V];
+  if (loop) {
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      th_h[t] = a.slots[lane * V + t].theta_hi;
+      gam_k[t] = 0.f;
+    }
+  }
+  if ((int)blockIdx.x < a.n_spmv_blocks) {
+    const uint64_t pol = evict_first_policy();
+    const int stride = a.n_spmv_blocks * B_WARPS;
+    for (int row = blockIdx.x * B_WARPS + warp; row < a.A.rows; row += stride) {
+      float acc[V];
+      brow_dot<V, BF16>(a.A, row, f, Kp, lane, pol, acc);
+      const size_t o = (size_t)row * Kp + lane * V;
+      vstore<V>(y_out + o, acc);
+      if (!loop) continue;
+      float yp[V], gg[V], gm[V], wv[V];
+      vload<V>(y_prev + o, yp);
+      vload<V>(a.g + o, gg);
+      vload<V>(a.gamma + o, gm);
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        // y~ = y + theta (y - y_prev); den = max(y~ + gamma, kappa gamma); w = (den - g)/den
+        const float yt = fmaf(th_h[t], acc[t] - yp[t], acc[t]);
+        float den = yt + gm[t];
+        const float fl = 1e-3f * gm[t];
+        if (den < fl) {
+          den = fl;
+          ++hits[t];
+        }
+        wv[t] = __fdiv_rn(den - gg[t], den);
+        if (want) {
+          // data term y - g ln(y + gamma) in double-float
+          df yg;
+          two_sum(acc[t], gm[t], yg.hi, yg.lo);
+          const df term = df_add_f(df_neg(df_mul_f(df_log(yg), gg[t])), acc[t]);
+          acc_add(dh[t], dl[t], term.hi, term.lo);
+        }
+      }
+      vstore<V>(a.w + o, wv);
+    }
+  } else if (loop) {
+    // stencil items: (tile, 8-slot chunk) pairs, persistent over the stencil blocks
+    const int nsb = gridDim.x - a.n_spmv_blocks;
+    const int ntx = (n + BST_C - 1) / BST_C, nty = (n + BST_R - 1) / BST_R;
+    const int nchunks = Kp / BST_S;
+    const int nitems = ntx * nty * nchunks;
+    __shared__ float sreg_hi[MAXK], sreg_lo[MAXK];  // per-slot regulariser sums
+    for (int s = tid; s < MAXK; s += blockDim.x) {
+      sreg_hi[s] = 0.f;
+      sreg_lo[s] = 0.f;
+    }
+    __syncthreads();
+    for (int it = blockIdx.x - a.n_spmv_blocks; it < nitems; it += nsb) {
+      const int chunk = it % nchunks, tile = it / nchunks;
+      const int r0 = (tile / ntx) * BST_R, c0 = (tile % ntx) * BST_C;
+      const float reg = bstencil_item(sm.st, f, a.f[(G + 2) % 3], a.slots, Kp, r0, c0,
+                                      chunk * BST_S, n, a.gR, want);
+      if (want) {
+        // warp q holds slot chunk*8 + q: fold the warp's 32 columns
+        float h = reg, l = 0.f;
+        warp_sum_acc(h, l);
+        if (lane == 0) {
+          const int s = chunk * BST_S + warp;
+          acc_add(sreg_hi[s], sreg_lo[s], h, l);
+        }
+      }
+    }
+    __syncthreads();
+    if (want) {
+      // hand the per-slot sums to the lanes that own the slots in warp 0
+      if (warp == 0) {
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          dh[t] = sreg_hi[lane * V + t];
+          dl[t] = sreg_lo[lane * V + t];
+        }
+      }
+    }
+  }
+  // guard hits per slot
+  if (loop) {
+#pragma unroll
+    for (int t = 0; t < V; ++t)
+      if (hits[t]) atomicAdd(&a.slots[lane * V + t].guard_hits, (unsigned long long)hits[t]);
+  }
+  if (!want) return;
+  // block partial per slot (fixed order over warps)
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    sm.e.dhi[warp][lane * V + t] = dh[t];
+    sm.e.dlo[warp][lane * V + t] = dl[t];
+  }
+  __syncthreads();
+  for (int s = tid; s < Kp; s += blockDim.x) {
+    float h = 0.f, l = 0.f;
+    for (int w = 0; w < B_WARPS; ++w) acc_add(h, l, sm.e.dhi[w][s], sm.e.dlo[w][s]);
+    sm.e.bhi[s] = h;
+    sm.e.blo[s] = l;
+  }
+  __syncthreads();
+  if (grid_reduce_slots(a.partial, a.gtick, &bs->ticket_r, sm.e.bhi, sm.e.blo, Kp, sm.e.thi,
+                        sm.e.tlo)) {
+    // Phi(f^k) of every slot and its stopping test
+    for (int s = tid; s < Kp; s += blockDim.x) {
+      SlotState& sl = a.slots[s];
+      if (!sl.active || sl.done) continue;
+      const double phi = (double)sm.e.thi[s] + (double)sm.e.tlo[s];
+      const double prev = sl.phi_cur;
+      sl.phi_prev = prev;
+      sl.phi_cur = phi;
+      if (sl.rel_tol > 0.0 && sl.k > sl.k0 && fabs(phi - prev) <= sl.rel_tol * fabs(prev)) {
+        sl.done = 1;
+        sl.result_k = sl.k;
+        sl.stopped_early = 1;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- k_bpixel
+
+template <int V, bool BF16>
+__global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
+  BatchState* bs = a.bst;
+  if (bs->remaining == 0) return;  // uniform over the grid
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Kp = a.Kp;
+  const int G = bs->gstep;
+  const float* fk = a.f[G % 3];
+  const float* fkm = a.f[(G + 2) % 3];
+  float* fn = a.f[(G + 1) % 3];
+  // this lane's slot parameters
+  float th[V], beta[V];
+  int live[V], kk[V], frz[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const SlotState& sl = a.slots[lane * V + t];
+    th[t] = sl.theta_hi;
+    beta[t] = sl.beta;
+    live[t] = sl.active && !sl.done;
+    kk[t] = sl.k;
+    frz[t] = sl.freeze_iter;
+  }
+  const uint64_t pol = evict_first_policy();
+  const int stride = gridDim.x * B_WARPS;
+  int bad = 0;
+  for (int j = blockIdx.x * B_WARPS + warp; j < a.At.rows; j += stride) {
+    float bp[V];
+    brow_dot<V, BF16>(a.At, j, a.w, Kp, lane, pol, bp);
+    const size_t o = (size_t)j * Kp + lane * V;
+    float vk[V], vm[V], gr[V], out[V];
+    vload<V>(fk + o, vk);
+    vload<V>(fkm + o, vm);
+    vload<V>(a.gR + o, gr);
+    const float il = __ldg(a.inv_lambda + j);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      if (!live[t]) {
+        out[t] = vk[t];  // finished or empty slot: carry the image
+        continue;
+      }
+      const float ft = fmaf(th[t], vk[t] - vm[t], vk[t]);
+      float pk = vk[t];
+      if (frz[t] >= 0) {
+        if (kk[t] == frz[t]) {
+          a.pfreeze[o + t] = vk[t];
+        } else if (kk[t] > frz[t]) {
+          pk = a.pfreeze[o + t];
+        }
+      }
+      const float p = beta[t] * pk * il;
+      const float xv = __fmaf_rn(-p, bp[t] + gr[t], ft);
+      if (!isfinite(xv)) bad = 1;
+      out[t] = fmaxf(xv, 0.f);
+    }
+    vstore<V>(fn + o, out);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&bs->flags, APPGA_FLAG_NONFINITE);
+  // Finalise the step in the last block: every live slot advances its index
+  // and momentum; the global step advances.
+  __syncthreads();
+  double unused;
+  if (grid_reduce(a.partial, a.gtick, &bs->ticket_p, {0.f, 0.f}, &unused)) {
+    __shared__ int s_rem[B_THREADS];
+    int rem = 0;
+    for (int s = tid; s < Kp; s += blockDim.x) {
+      SlotState& sl = a.slots[s];
+      if (!sl.active || sl.done) continue;
+      if (sl.k >= sl.k_last) {
+        sl.done = 1;
+        sl.result_k = sl.k + 1;
+      } else {
+        ++rem;
+      }
+      const int k = sl.k;
+      sl.k = k + 1;
+      double th_next = 0.0;
+      if (sl.momentum == APPGA_MOMENTUM_GN) {
+        th_next = (bgn_t(k, sl.a, sl.b, sl.omega) - 1.0) / bgn_t(k + 1, sl.a, sl.b, sl.omega);
+      } else if (sl.momentum == APPGA_MOMENTUM_NESTEROV) {
+        const double t = sl.t_cur;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        th_next = (t - 1.0) / tn;
+        sl.t_cur = tn;
+      }
+      bset_theta(sl, th_next);
+    }
+    s_rem[tid] = rem;
+    __syncthreads();
+    if (tid == 0) {
+      int tot = 0;
+      for (int i = 0; i < (int)blockDim.x; ++i) tot += s_rem[i];
+      bs->gstep = G + 1;
+      bs->remaining = tot;
+    }
+  }
+}
+
+// ----------------------------------------------------------- setup kernels
+
+// theta_{k0} of every live slot (same device arithmetic as the step kernel).
+__global__ void k_binit_momentum(SlotState* slots, int Kp) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Kp) return;
+  SlotState& sl = slots[s];
+  double theta = 0.0, t = 1.0;
+  if (sl.momentum == APPGA_MOMENTUM_GN) {
+    theta = (bgn_t(sl.k - 1, sl.a, sl.b, sl.omega) - 1.0) / bgn_t(sl.k, sl.a, sl.b, sl.omega);
+  } else if (sl.momentum == APPGA_MOMENTUM_NESTEROV) {
+    for (int k = 1; k <= sl.k; ++k) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      theta = (t - 1.0) / tn;
+      t = tn;
+    }
+  }
+  bset_theta(sl, theta);
+  sl.t_cur = t;
+}
+
+// [rows][ld] slice-major -> [rows_out = ld][Kp] slot-minor for slots [s0, s0+K):
+// out[i*Kp + s0 + s] = in[s*ld + i].  Padding slots are written separately.
+__global__ void k_to_slot_minor(const float* __restrict__ in, int K, int len, float* __restrict__ out,
+                                int Kp, int s0) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, i = i0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && i < len) ? in[(size_t)k * len + i] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, k = k0 + threadIdx.x;
+    if (i < len && k < K) out[(size_t)i * Kp + s0 + k] = tile[threadIdx.x][r];
+  }
+}
+// out[s*len + i] = in[i*Kp + s0 + s] for s < K.
+__global__ void k_from_slot_minor(const float* __restrict__ in, int K, int len, int Kp, int s0,
+                                  float* __restrict__ out) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, k = k0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < len && k < K) ? in[(size_t)i * Kp + s0 + k] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, i = i0 + threadIdx.x;
+    if (k < K && i < len) out[(size_t)k * len + i] = tile[threadIdx.x][r];
+  }
+}
+// Sets column s of a [len][Kp] array to v for s in [s0, s1).
+__global__ void k_fill_slots(float* out, int len, int Kp, int s0, int s1, float v) {
+  const int w = s1 - s0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)len * w;
+       t += (size_t)gridDim.x * blockDim.x)
+    out[(t / w) * Kp + s0 + t % w] = v;
+}
+
+// Per-slot initial image TMC_s * 1_disk (Sec. 4.1) for slots [s0, s0+K) from
+// slice-major g, gamma ([K][m]): one block per slot.
+__global__ void __launch_bounds__(256) k_binit_image(const float* __restrict__ g,
+                                                     const float* __restrict__ gamma, int m, int n,
+                                                     int n_angles, long long npfov, int Kp, int s0,
+                                                     float* __restrict__ f_out) {
+  const int k = blockIdx.x;
+  float h = 0.f, l = 0.f;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    acc_add(h, l, g[(size_t)k * m + i], 0.f);
+    acc_add(h, l, -gamma[(size_t)k * m + i], 0.f);
+  }
+  const df t = block_sum_acc(h, l);
+  __shared__ float s_tmc;
+  if (threadIdx.x == 0)
+    s_tmc = (float)(((double)t.hi + (double)t.lo) / ((double)npfov * (double)n_angles));
+  __syncthreads();
+  const float v = s_tmc;
+  for (int j = threadIdx.x; j < n * n; j += blockDim.x) {
+    const int r = j / n, c = j % n;
+    const long long dx = 2ll * c + 1 - n, dy = 2ll * r + 1 - n;
+    f_out[(size_t)j * Kp + s0 + k] = (dx * dx + dy * dy <= (long long)n * n) ? v : 0.f;
+  }
+}
+
+template <int V, bool BF16>
+int bf_blocks(int per_sm_cap, int sms) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bforward<V, BF16>, B_THREADS, 0);
+  if (per_sm <= 0) per_sm = 1;
+  return (per_sm < per_sm_cap ? per_sm : per_sm_cap) * sms;
+}
+
+int sm_count() {
+  static int sms = [] {
+    int dev = 0, s = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    return s > 0 ? s : 1;
+  }();
+  return sms;
+}
+
+template <int V>
+cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
+  BFwdArgs a = a0;
+  const int sms = sm_count();
+  const int rows_per_block = B_WARPS;
+  int nsp = (a.A.rows + rows_per_block - 1) / rows_per_block;
+  const int cap = sms * 8;
+  if (nsp > cap) nsp = cap;
+  a.n_spmv_blocks = nsp;
+  int nst = 0;
+  if (a.mode == 0) {
+    const int items = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R) * (a.Kp / BST_S);
+    nst = items < sms * 4 ? items : sms * 4;
+  }
+  const int grid = nsp + nst;
+  if (a.use_bf16)
+    k_bforward<V, true><<<grid, B_THREADS, 0, s>>>(a);
+  else
+    k_bforward<V, false><<<grid, B_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <int V>
+cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
+  const int sms = sm_count();
+  int nb = (a.At.rows + B_WARPS - 1) / B_WARPS;
+  if (nb > sms * 8) nb = sms * 8;
+  if (a.use_bf16)
+    k_bpixel<V, true><<<nb, B_THREADS, 0, s>>>(a);
+  else
+    k_bpixel<V, false><<<nb, B_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int batch_max_blocks() { return sm_count() * 12 + 64; }
+
+cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s) {
+  cudaError_t e = ensure_tables();
+  if (e != cudaSuccess) return e;
+  switch (a.Kp / 32) {
+    case 1: return bforward_v<1>(a, s);
+    case 2: return bforward_v<2>(a, s);
+    case 4: return bforward_v<4>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s) {
+  switch (a.Kp / 32) {
+    case 1: return bpixel_v<1>(a, s);
+    case 2: return bpixel_v<2>(a, s);
+    case 4: return bpixel_v<4>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_binit_momentum(SlotState* slots, int Kp, cudaStream_t s) {
+  k_binit_momentum<<<(Kp + 127) / 128, 128, 0, s>>>(slots, Kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_slot_minor(const float* in, int K, int len, float* out, int Kp, int s0,
+                                 cudaStream_t s) {
+  dim3 grid((len + 31) / 32, (K + 31) / 32), block(32, 8);
+  k_to_slot_minor<<<grid, block, 0, s>>>(in, K, len, out, Kp, s0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_slot_minor(const float* in, int K, int len, int Kp, int s0, float* out,
+                                   cudaStream_t s) {
+  dim3 grid((len + 31) / 32, (K + 31) / 32), block(32, 8);
+  k_from_slot_minor<<<grid, block, 0, s>>>(in, K, len, Kp, s0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_slots(float* out, int len, int Kp, int s0, int s1, float v,
+                              cudaStream_t s) {
+  if (s1 <= s0) return cudaSuccess;
+  k_fill_slots<<<256, 256, 0, s>>>(out, len, Kp, s0, s1, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_binit_image(const float* g, const float* gamma, int m, int n, int n_angles,
+                               long long npfov, int K, int Kp, int s0, float* f_out,
+                               cudaStream_t s) {
+  k_binit_image<<<K, 256, 0, s>>>(g, gamma, m, n, n_angles, npfov, Kp, s0, f_out);
+  return cudaGetLastError();
+}
+
+}  // namespace appga

@@ -1,0 +1,172 @@
+"""GPU parity of the batched (K slices, one matrix) solver through the C ABI:
+every slice against the FP64 oracle, against the single-slice GPU path, and
+independence of a slice's result from the rest of the batch."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import appga_oracle as O
+from paper_2409_13344_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2409_13344_gb300 import build
+    build.build()
+    from paper_2409_13344_gb300 import appga
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA device")
+    return appga
+
+
+@pytest.fixture(scope="module")
+def ctx(A):
+    c = A.Context(0)
+    yield c
+    c.close()
+
+
+_mats = {}
+
+
+def matrix(A, ctx, name):
+    if name not in _mats:
+        geom = W.GEOMETRIES[name] if isinstance(name, str) else name
+        Amat = W.system_matrix(name) if isinstance(name, str) else W.siddon_matrix(geom)
+        _mats[name] = (geom, Amat, A.Matrix(ctx, Amat, geom.n, geom.n_angles, bf16=True))
+    return _mats[name]
+
+
+def slices(geom, Amat, K, counts=None, config=3, phantom="ellipses"):
+    rng = np.random.default_rng(99)
+    if counts is None:
+        counts = W.log_uniform_counts(rng, 5e4, 5e5, K)
+    return [W.make_slice(Amat, geom, float(c), W.seed_for(config, i), phantom=phantom)
+            for i, c in enumerate(counts)]
+
+
+def run_batched(A, ctx, mat, sls, **kw):
+    K = len(sls)
+    g = torch.from_numpy(np.stack([s.g for s in sls])).to(DEV)
+    gam = torch.from_numpy(np.stack([s.gamma for s in sls])).to(DEV)
+    f = torch.empty((K, mat.d), dtype=torch.float32, device=DEV)
+    p = A.default_params(**kw)
+    st = A.appga_reconstruct_batched(ctx.handle, mat.handle, K, g, gam, None, p, f)
+    return f.cpu().numpy(), st
+
+
+def oracle(geom, Amat, sl, **kw):
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    par = O.Params(**kw)
+    return prob, O.appga(prob, par, n_angles=geom.n_angles, track_phi=par.rel_obj_tol > 0)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("K", [1, 3, 33, 100])
+def test_batched_vs_oracle_64(A, ctx, K):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = slices(geom, Amat, K)
+    f, st = run_batched(A, ctx, mat, sls, max_iters=30, omega=0.5, track_objective=1)
+    check = range(K) if K <= 3 else [0, K // 2, K - 1]
+    for i in check:
+        prob, ref = oracle(geom, Amat, sls[i], max_iters=30, omega=0.5)
+        assert st[i].iters == 30
+        assert rel(f[i], ref.f) <= 1e-5, (i, rel(f[i], ref.f))
+        phi_same = prob.objective(f[i].astype(np.float64), 0.1, 0.05, 1e-3)
+        assert abs(st[i].phi - phi_same) <= 1e-9 * abs(phi_same)
+
+
+def test_batched_matches_single_slice_path(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = slices(geom, Amat, 4)
+    fb, _ = run_batched(A, ctx, mat, sls, max_iters=40, beta=0.1, omega=1.0)
+    for i, sl in enumerate(sls):
+        p = A.default_params(max_iters=40, beta=0.1, omega=1.0)
+        out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+        A.appga_reconstruct(ctx.handle, mat.handle, torch.from_numpy(sl.g).to(DEV),
+                            torch.from_numpy(sl.gamma).to(DEV), None, p, out)
+        assert rel(fb[i], out.cpu().numpy().astype(np.float64)) <= 2e-6
+
+
+def test_slice_result_independent_of_batch_mates(A, ctx):
+    # the same slice, alone among different batch mates, gives the same image
+    geom, Amat, mat = matrix(A, ctx, "64")
+    base = slices(geom, Amat, 6)
+    other = slices(geom, Amat, 6, config=7)
+    mix = [base[0], other[1], base[2], other[3], other[4], base[5]]
+    f1, s1 = run_batched(A, ctx, mat, base, max_iters=25, track_objective=1)
+    f2, s2 = run_batched(A, ctx, mat, mix, max_iters=25, track_objective=1)
+    for i in (0, 2, 5):
+        np.testing.assert_array_equal(f1[i], f2[i])
+        assert s1[i].phi == s2[i].phi
+
+
+def test_batched_ragged_geometry(A, ctx):
+    geom = W.Geometry(40, 48, 59)
+    geom, Amat, mat = matrix(A, ctx, geom)
+    sls = slices(geom, Amat, 5, counts=[2e4, 3e4, 5e4, 1e4, 4e4])
+    f, st = run_batched(A, ctx, mat, sls, max_iters=100, beta=0.03, omega=1.0)
+    for i in range(5):
+        _, ref = oracle(geom, Amat, sls[i], max_iters=100, beta=0.03, omega=1.0)
+        assert rel(f[i], ref.f) <= 1e-5
+
+
+def test_batched_per_slice_stopping(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = slices(geom, Amat, 4)
+    f, st = run_batched(A, ctx, mat, sls, max_iters=400, beta=0.1, omega=1.0, rel_obj_tol=1e-6)
+    iters = []
+    for i in range(4):
+        prob, ref = oracle(geom, Amat, sls[i], max_iters=400, beta=0.1, omega=1.0,
+                           rel_obj_tol=1e-6)
+        assert st[i].stopped_early == 1
+        assert abs(st[i].iters - ref.iters) <= 1, (i, st[i].iters, ref.iters)
+        if st[i].iters == ref.iters:
+            assert rel(f[i], ref.f) <= 1e-5
+        iters.append(st[i].iters)
+    assert len(set(iters)) > 1  # slices really stop at different iterations
+
+
+def test_batched_bf16(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = slices(geom, Amat, 3)
+    f, _ = run_batched(A, ctx, mat, sls, max_iters=30, a_precision=1)
+    u = Amat.data.view(np.uint32).astype(np.uint64)
+    ub = (((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)).view(np.float32)
+    Ab = sp.csr_matrix((ub, Amat.indices, Amat.indptr), shape=Amat.shape)
+    for i in range(3):
+        _, refb = oracle(geom, Ab, sls[i], max_iters=30)
+        _, ref32 = oracle(geom, Amat, sls[i], max_iters=30)
+        assert rel(f[i], refb.f) <= 1e-5
+        assert rel(f[i], ref32.f) <= 1e-3
+
+
+def test_batched_full_size_256(A, ctx):
+    # 64 slices of 256^2 sharing one A, per-slice counts log-uniform 1e5..1e7
+    geom, Amat, mat = matrix(A, ctx, "256")
+    rng = np.random.default_rng(3)
+    counts = W.log_uniform_counts(rng, 1e5, 1e7, 64)
+    sls = slices(geom, Amat, 64, counts=counts, phantom="lesions")
+    f, st = run_batched(A, ctx, mat, sls, max_iters=60, beta=0.1, omega=1.0, track_objective=1)
+    for i in (0, 31, 63):
+        prob, ref = oracle(geom, Amat, sls[i], max_iters=60, beta=0.1, omega=1.0)
+        assert rel(f[i], ref.f) <= 1e-5, (i, rel(f[i], ref.f))
+        phi_same = prob.objective(f[i].astype(np.float64), 0.1, 0.05, 1e-3)
+        assert abs(st[i].phi - phi_same) <= 1e-9 * abs(phi_same)
+
+
+def test_batched_rejects_bad_input(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = slices(geom, Amat, 2)
+    sls[1].g[3] = np.nan
+    with pytest.raises(A.AppgaError) as ei:
+        run_batched(A, ctx, mat, sls, max_iters=5)
+    assert ei.value.status == A.APPGA_EDOMAIN
