@@ -251,6 +251,30 @@ appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, 
                                        const appga_params* params, float* f_out,
                                        appga_stats* stats_host, void* stream);
 
+/* appga_objective_noalloc: appga_objective without any memory allocation.
+ * The paper has no counterpart; this is a library-side convenience.
+ * Some callers cannot let a library allocate device memory after start-up:
+ * processes that give all device memory to their own pool at launch (a
+ * serving process or a framework allocator that owns every byte) and
+ * real-time reconstruction loops that forbid allocation once running
+ * (cudaMalloc/cudaFree can synchronise the device).  This call computes the
+ * same Phi(f) as appga_objective but keeps its scratch (reduction partials,
+ * tickets, a scratch state) in one fixed 256 KiB device array inside the
+ * library, and writes the FP64 result to the DEVICE pointer phi_out
+ * (double[1]) on `stream` without synchronising.  It allocates nothing; the
+ * caller passes f, g, gamma, phi_out and a matrix created beforehand.
+ * Limits: matrices whose scratch needs more than 256 KiB (images larger than
+ * 512 x 512 or sinograms beyond about 263 K bins) are rejected with
+ * APPGA_EINVAL.  Every GPU that loads the library holds the array until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps
+ * on the GPU (different streams, or concurrent host threads) race and give
+ * wrong results; serialise them. */
+appga_status appga_objective_noalloc(appga_ctx* ctx, const appga_matrix* mat, const float* f,
+                                     const float* g, const float* gamma,
+                                     const appga_params* params, double* phi_out, void* stream);
+
 /* appga_validate_csr_host: the host-side check appga_matrix_create runs on a
  * CSR (row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz, 0 <= col < d, values
  * finite and >= 0).  Host only; needs no device.  EINVAL / EDOMAIN with a

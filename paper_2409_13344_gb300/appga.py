@@ -97,6 +97,8 @@ SIGNATURES = {
     "appga_reconstruct_host": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(appga_params), _P,
                                               ctypes.POINTER(appga_stats), _P]),
     "appga_validate_csr_host": (ctypes.c_int, [_I32, _I32, _P, _P, _P]),
+    "appga_objective_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(appga_params),
+                                               _P, _P]),
     "appga_reconstruct_batched": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P,
                                                  ctypes.POINTER(appga_params), _P,
                                                  ctypes.POINTER(appga_stats), _P]),
@@ -287,6 +289,13 @@ def appga_reconstruct_batched(ctx, mat, K, g, gamma, f_init, params, f_out, stre
                                                     st, _stream(stream)),
            "appga_reconstruct_batched")
     return list(st)
+
+
+def appga_objective_noalloc(ctx, mat, f, g, gamma, params, phi_out, stream=None):
+    """Phi(f) into the device double phi_out[0]; allocates nothing (see appga.h)."""
+    _check(load_library().appga_objective_noalloc(ctx, mat, _ptr(f), _ptr(g), _ptr(gamma),
+                                                  ctypes.byref(params), _ptr(phi_out),
+                                                  _stream(stream)), "appga_objective_noalloc")
 
 
 def appga_validate_csr_host(m, d, row_ptr, col, val) -> int:
