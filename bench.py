@@ -43,6 +43,14 @@ WORKLOAD = ("single 256x256 slice, parallel beam 180 angles x 367 bins, Siddon C
             "FP64 objective every iteration; 500-iteration reconstructions back to back")
 
 
+BATCH_K = 64
+BATCH_ITERS = 200
+SERVE_GEOMS = ("128", "256", "400")
+SERVE_RATE = 100.0
+SERVE_SLOTS = 64
+SERVE_STEPS = 8
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -51,6 +59,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-slice batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
+                    help="Poisson arrival rate of the serving stream (requests/s)")
     return ap.parse_args()
 
 
@@ -152,6 +165,149 @@ def measured_peaks():
             return json.load(fh), "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# --------------------------------------------------------- batched and served
+
+def batched_bytes(m: int, d: int, nnz: int, K: int):
+    """Algorithmic bytes of one batched iteration (both kernels) for K slices:
+    the two matrix streams once, plus every per-slice vector once."""
+    mats = 8 * nnz + 4 * (m + 1) + 8 * nnz + 4 * (d + 1) + 4 * d  # A, A^T, 1/Lambda
+    fwd = K * (4 * d + 4 * m * 5)          # f^k gather; y_prev, g, gamma in; y, w out
+    stencil = K * (4 * d * 2 + 4 * d)      # f^k, f^{k-1} in; gR out
+    pix = K * (4 * m + 4 * d * 4)          # w gather; f^k, f^{k-1}, gR in; f^{k+1} out
+    return mats + fwd + stencil + pix
+
+
+def bench_batched(AP, ctx, geom, A, dev, single_rate):
+    """64 independent 256x256 slices sharing A (per-slice counts log-uniform
+    1e5..1e7), FP32 and BF16 values of A: slices x iterations per second."""
+    import numpy as np
+    import torch
+    from paper_2409_13344_gb300 import workload as W
+    rng = np.random.default_rng(3)
+    counts = W.log_uniform_counts(rng, 1e5, 1e7, BATCH_K)
+    sls = [W.make_slice(A, geom, float(c), W.seed_for(3, i), phantom="lesions")
+           for i, c in enumerate(counts)]
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, bf16=True)
+    g = torch.from_numpy(np.stack([x.g for x in sls])).to(dev)
+    gam = torch.from_numpy(np.stack([x.gamma for x in sls])).to(dev)
+    f = torch.empty((BATCH_K, geom.d), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{BATCH_K} independent 256x256 slices (180 x 367 sinograms) sharing one "
+                       "A, counts log-uniform 1e5..1e7, omega 0.5, beta 1, 200 iterations per "
+                       "call, one call = one SpMM solver run under captured CUDA graphs",
+           "K": BATCH_K}
+    nb = batched_bytes(geom.m, geom.d, int(mat.info().nnz), BATCH_K)
+    for name, prec in (("fp32", 0), ("bf16", 1)):
+        def call(iters):
+            p = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA,
+                                  max_iters=iters, a_precision=prec)
+            AP.appga_reconstruct_batched(ctx.handle, mat.handle, BATCH_K, g, gam, None, p, f)
+        for _ in range(3):
+            call(8)
+        ms = {}
+        for iters in (8, 8 + BATCH_ITERS):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[iters] = e0.elapsed_time(e1)
+        per_iter = (ms[8 + BATCH_ITERS] - ms[8]) / BATCH_ITERS
+        rate = BATCH_K / (per_iter * 1e-3)
+        out[name] = {"slices_iters_per_s": rate, "us_per_batched_iter": 1e3 * per_iter,
+                     "us_per_slice_iter": 1e3 * per_iter / BATCH_K,
+                     "call_slices_iters_per_s": BATCH_K * (8 + BATCH_ITERS) / (ms[8 + BATCH_ITERS] * 1e-3),
+                     "algorithmic_gbs": nb / (per_iter * 1e-3) / 1e9,
+                     "vs_single_slice": rate / single_rate}
+    out["algorithmic_bytes_per_iter"] = nb
+    mat.close()
+    return out
+
+
+def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A):
+    """Poisson stream of reconstruction requests mixing 128^2, 256^2 and 400^2
+    slices (200..800 iterations each, or the relative objective change
+    < 1e-7) through the continuous-batching server."""
+    import numpy as np
+    from paper_2409_13344_gb300 import workload as W
+    rng = np.random.default_rng(4)
+    mats, slices = {}, {}
+    for idx, nm in enumerate(SERVE_GEOMS):
+        geom = W.GEOMETRIES[nm]
+        A = main_A if nm == GEOM else W.system_matrix(nm)
+        mats[nm] = AP.Matrix(ctx, A, geom.n, geom.n_angles)
+        counts = W.log_uniform_counts(rng, 1e5, 1e7, 6)
+        slices[nm] = [W.make_slice(A, geom, float(c), W.seed_for(4, 100 * idx + i),
+                                   phantom="lesions") for i, c in enumerate(counts)]
+    srv = AP.Server(ctx, slots_per_pool=SERVE_SLOTS, steps_per_launch=SERVE_STEPS)
+    gids = {nm: srv.add_geometry(mats[nm]) for nm in SERVE_GEOMS}
+    # warm-up: one short request per geometry (pools and graphs are created here)
+    for nm in SERVE_GEOMS:
+        x = slices[nm][0]
+        srv.submit(gids[nm], x.g, x.gamma, AP.default_params(max_iters=16))
+    while srv.step():
+        pass
+    for rid in list(srv._geom_of):
+        srv.collect(rid)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    kinds = rng.integers(0, len(SERVE_GEOMS), n_requests)
+    iters = rng.integers(200, 801, n_requests)
+    omegas = rng.choice([0.5, 1.0], n_requests)
+    info, lat, per_geom = {}, [], {nm: [] for nm in SERVE_GEOMS}
+    done_iters, stopped = 0, 0
+    nxt, steps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < n_requests and arrivals[nxt] <= now:
+            nm = SERVE_GEOMS[kinds[nxt]]
+            x = slices[nm][nxt % len(slices[nm])]
+            p = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=float(omegas[nxt]),
+                                  max_iters=int(iters[nxt]), rel_obj_tol=1e-7)
+            info[srv.submit(gids[nm], x.g, x.gamma, p)] = (arrivals[nxt], nm)
+            nxt += 1
+        pending = srv.step()
+        steps += 1
+        t_seen = time.perf_counter() - t0
+        for rid in list(info):
+            if srv.poll(rid).state == AP.APPGA_REQ_DONE:
+                a, nm = info.pop(rid)
+                _, st = srv.collect(rid)
+                lat.append(t_seen - a)  # from the request's arrival
+                per_geom[nm].append(t_seen - a)
+                done_iters += st.iters
+                stopped += st.stopped_early
+        if nxt >= n_requests and pending == 0:
+            break
+        if pending == 0:
+            time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)))
+    elapsed = time.perf_counter() - t0
+    summ = srv.summary()
+    srv.close()
+    for m in mats.values():
+        m.close()
+    lat = np.asarray(lat)
+    return {
+        "workload": f"Poisson stream of {n_requests} requests at {rate:g}/s mixing 128^2 (90x185), "
+                    "256^2 (180x367) and 400^2 (288x575) slices, 200..800 iterations each or "
+                    "relative objective change < 1e-7, omega 0.5/1.0, counts log-uniform 1e5..1e7",
+        "requests": n_requests, "rate_per_s": rate, "elapsed_s": elapsed, "steps": steps,
+        "slices_iters_per_s": done_iters / elapsed, "slice_iters": done_iters,
+        "stopped_early": stopped,
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "mean_latency_s": float(lat.mean()),
+        "per_geometry": {nm: {"n": len(v), "p50_s": float(np.percentile(v, 50)),
+                              "p99_s": float(np.percentile(v, 99))} for nm, v in per_geom.items() if v},
+        "server_p50_latency_s": summ.p50_latency_s, "server_p99_latency_s": summ.p99_latency_s,
+        "latency_from": "arrival time of the request in the stream (the server's own figures "
+                        "count from submission)",
+        "pools": summ.pools, "device_bytes": summ.device_bytes, "slots_per_pool": SERVE_SLOTS,
+        "steps_per_launch": SERVE_STEPS,
+    }
 
 
 # ----------------------------------------------------------------- oracle
@@ -336,6 +492,12 @@ def run_ours(args):
         "iteration_gbs": (b_fwd + b_pix) / ((tp + tf) * 1e-3) / 1e9,
     }
 
+    batched = serving = None
+    if world == 1 and not args.no_batched:
+        batched = bench_batched(AP, ctx, geom, A, dev, value)
+    if world == 1 and not args.no_serve:
+        serving = bench_serving(AP, ctx, args.serve_requests, args.serve_rate, geom, A)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         k, el = oracle_rate(geom, A, sl, args.cpu_seconds)
@@ -359,6 +521,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": 4 * geom.d * n_calls / e_steps},
             "gpu_launches": launches(args.steps),
             "clocks": clk,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     mat.close()

@@ -64,8 +64,41 @@ class appga_matrix_info(ctypes.Structure):
     ]
 
 
+class appga_server_config(ctypes.Structure):
+    _fields_ = [
+        ("slots_per_pool", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
+        ("a_precision", ctypes.c_int32), ("max_pools", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_int64), ("hbm_reserve_bytes", ctypes.c_int64),
+    ]
+
+
+class appga_request_stats(ctypes.Structure):
+    _fields_ = [
+        ("state", ctypes.c_int32), ("iters", ctypes.c_int32), ("result_k", ctypes.c_int32),
+        ("stopped_early", ctypes.c_int32), ("flags", ctypes.c_int32), ("phi_k", ctypes.c_int32),
+        ("guard_hits", ctypes.c_int64), ("phi_last", ctypes.c_double),
+        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+    ]
+
+
+class appga_server_summary(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("waiting", ctypes.c_int64),
+        ("running", ctypes.c_int64), ("slice_iters", ctypes.c_int64), ("pools", ctypes.c_int32),
+        ("pad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+        ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+        ("mean_latency_s", ctypes.c_double), ("max_latency_s", ctypes.c_double),
+        ("mean_queue_s", ctypes.c_double),
+    ]
+
+
+APPGA_REQ_WAITING = 0
+APPGA_REQ_RUNNING = 1
+APPGA_REQ_DONE = 2
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
 _D = ctypes.c_double
 
 # name -> (restype, argtypes); the exported surface of appga.h
@@ -104,6 +137,18 @@ SIGNATURES = {
                                                  ctypes.POINTER(appga_stats), _P]),
     "appga_kernel_times": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(appga_params), _I32,
                                           ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    # appga_server.h
+    "appga_server_config_default": (None, [ctypes.POINTER(appga_server_config)]),
+    "appga_server_create": (ctypes.c_int, [_P, ctypes.POINTER(appga_server_config),
+                                           ctypes.POINTER(_P)]),
+    "appga_server_destroy": (ctypes.c_int, [_P]),
+    "appga_server_add_geometry": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I32)]),
+    "appga_server_submit": (ctypes.c_int, [_P, _I32, _P, _P, _P, ctypes.POINTER(appga_params),
+                                           ctypes.POINTER(_I64)]),
+    "appga_server_step": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "appga_server_poll": (ctypes.c_int, [_P, _I64, ctypes.POINTER(appga_request_stats)]),
+    "appga_server_collect": (ctypes.c_int, [_P, _I64, _P, ctypes.POINTER(appga_request_stats)]),
+    "appga_server_get_summary": (ctypes.c_int, [_P, ctypes.POINTER(appga_server_summary)]),
 }
 
 _lib = None
@@ -316,6 +361,88 @@ def appga_kernel_times(ctx, mat, g, gamma, params, n_iters: int):
     return tp.value, tf.value
 
 
+def _host_ptr(x) -> Optional[int]:
+    """Address of a host buffer: a C-contiguous float32 numpy array or CPU tensor."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda:
+            raise ValueError("expected a host buffer")
+        return x.data_ptr()
+    import numpy as np
+    if not (isinstance(x, np.ndarray) and x.flags.c_contiguous and x.dtype == np.float32):
+        raise ValueError("host buffers must be C-contiguous float32 arrays")
+    return x.ctypes.data
+
+
+def appga_server_config_default() -> appga_server_config:
+    c = appga_server_config()
+    load_library().appga_server_config_default(ctypes.byref(c))
+    return c
+
+
+def server_config(**kw) -> appga_server_config:
+    c = appga_server_config_default()
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(f"appga_server_config has no field {k!r}")
+        setattr(c, k, v)
+    return c
+
+
+def appga_server_create(ctx, cfg: appga_server_config) -> int:
+    h = _P()
+    _check(load_library().appga_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)),
+           "appga_server_create")
+    return h.value
+
+
+def appga_server_destroy(srv):
+    _check(load_library().appga_server_destroy(srv), "appga_server_destroy")
+
+
+def appga_server_add_geometry(srv, mat) -> int:
+    gid = _I32()
+    _check(load_library().appga_server_add_geometry(srv, mat, ctypes.byref(gid)),
+           "appga_server_add_geometry")
+    return gid.value
+
+
+def appga_server_submit(srv, geometry, g_host, gamma_host, f_init_host, params) -> int:
+    rid = _I64()
+    _check(load_library().appga_server_submit(srv, geometry, _host_ptr(g_host),
+                                              _host_ptr(gamma_host), _host_ptr(f_init_host),
+                                              ctypes.byref(params), ctypes.byref(rid)),
+           "appga_server_submit")
+    return rid.value
+
+
+def appga_server_step(srv) -> int:
+    pending = _I32()
+    _check(load_library().appga_server_step(srv, ctypes.byref(pending)), "appga_server_step")
+    return pending.value
+
+
+def appga_server_poll(srv, request) -> appga_request_stats:
+    st = appga_request_stats()
+    _check(load_library().appga_server_poll(srv, request, ctypes.byref(st)), "appga_server_poll")
+    return st
+
+
+def appga_server_collect(srv, request, f_out_host) -> appga_request_stats:
+    st = appga_request_stats()
+    _check(load_library().appga_server_collect(srv, request, _host_ptr(f_out_host),
+                                               ctypes.byref(st)), "appga_server_collect")
+    return st
+
+
+def appga_server_get_summary(srv) -> appga_server_summary:
+    s = appga_server_summary()
+    _check(load_library().appga_server_get_summary(srv, ctypes.byref(s)),
+           "appga_server_get_summary")
+    return s
+
+
 # ---- convenience objects ----
 
 class Context:
@@ -372,3 +499,51 @@ def reconstruct(mat: Matrix, g, gamma, params: appga_params, f_init=None, stream
 
 def nan() -> float:
     return math.nan
+
+
+class Server:
+    """Continuous-batching server (appga_server.h) over registered matrices."""
+
+    def __init__(self, ctx: Context, **cfg):
+        self.ctx = ctx
+        self.handle = appga_server_create(ctx.handle, server_config(**cfg))
+        self.geometries = []
+        self._geom_of = {}
+
+    def add_geometry(self, mat: Matrix) -> int:
+        gid = appga_server_add_geometry(self.handle, mat.handle)
+        self.geometries.append(mat)
+        return gid
+
+    def submit(self, geometry: int, g, gamma, params: appga_params, f_init=None) -> int:
+        rid = appga_server_submit(self.handle, geometry, g, gamma, f_init, params)
+        self._geom_of[rid] = geometry
+        return rid
+
+    def step(self) -> int:
+        return appga_server_step(self.handle)
+
+    def poll(self, request: int) -> appga_request_stats:
+        return appga_server_poll(self.handle, request)
+
+    def collect(self, request: int):
+        """(image as a float32 numpy array, stats) of a finished request."""
+        import numpy as np
+        f = np.empty(self.geometries[self._geom_of[request]].d, np.float32)
+        st = appga_server_collect(self.handle, request, f)
+        del self._geom_of[request]
+        return f, st
+
+    def summary(self) -> appga_server_summary:
+        return appga_server_get_summary(self.handle)
+
+    def close(self):
+        if self.handle:
+            appga_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

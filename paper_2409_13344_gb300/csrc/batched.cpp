@@ -37,31 +37,30 @@ void free_batch_workspace(BatchWorkspace* bw) {
   *bw = BatchWorkspace();
 }
 
-namespace {
+int64_t batch_workspace_bytes(int m, int d, int Kp) {
+  const int64_t ngroups = batch_max_blocks() / 64 + 2;
+  int64_t b = 0;
+  b += (int64_t)5 * d * Kp * sizeof(float);  // f ring, gR, pfreeze
+  b += (int64_t)5 * m * Kp * sizeof(float);  // y ring, w, g, gamma
+  b += (int64_t)Kp * sizeof(SlotState) + sizeof(BatchState);
+  b += (batch_max_blocks() + ngroups + 2) * Kp * (int64_t)sizeof(float2);
+  b += ngroups * (int64_t)sizeof(unsigned int) + (int64_t)sizeof(int);
+  return b;
+}
 
-constexpr int kBatchGraphIters = 8;
-
-int padded_width(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
-
-appga_status ensure_batch_workspace(appga_matrix* M, int Kp) {
-  if (M->bw && M->bw->Kp == Kp) return APPGA_OK;
-  if (M->bw) {
-    free_batch_workspace(M->bw);
-  } else {
-    M->bw = new BatchWorkspace();
-  }
-  BatchWorkspace& b = *M->bw;
-  const size_t d = (size_t)M->d * Kp, m = (size_t)M->m * Kp;
+cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp) {
+  b = BatchWorkspace();
+  const size_t dd = (size_t)d * Kp, mm = (size_t)m * Kp;
   const int maxb = batch_max_blocks();
   const int ngroups = maxb / 64 + 2;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(&b.f[i], d);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(&b.y[i], m);
-  if (e == cudaSuccess) e = dalloc(&b.w, m);
-  if (e == cudaSuccess) e = dalloc(&b.gR, d);
-  if (e == cudaSuccess) e = dalloc(&b.pfreeze, d);
-  if (e == cudaSuccess) e = dalloc(&b.g, m);
-  if (e == cudaSuccess) e = dalloc(&b.gamma, m);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = dalloc(&b.f[i], dd);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = dalloc(&b.y[i], mm);
+  if (e == cudaSuccess) e = dalloc(&b.w, mm);
+  if (e == cudaSuccess) e = dalloc(&b.gR, dd);
+  if (e == cudaSuccess) e = dalloc(&b.pfreeze, dd);
+  if (e == cudaSuccess) e = dalloc(&b.g, mm);
+  if (e == cudaSuccess) e = dalloc(&b.gamma, mm);
   if (e == cudaSuccess) e = dalloc(&b.slots, (size_t)Kp);
   if (e == cudaSuccess) e = dalloc(&b.bst, 1);
   if (e == cudaSuccess) e = dalloc(&b.partial, (size_t)(maxb + ngroups + 2) * Kp);
@@ -73,15 +72,65 @@ appga_status ensure_batch_workspace(appga_matrix* M, int Kp) {
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b.bst_host, sizeof(BatchState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b.flag_host, sizeof(int));
   if (e != cudaSuccess) {
-    free_batch_workspace(M->bw);
-    delete M->bw;
-    M->bw = nullptr;
-    return cuda_fail(e, "batched workspace allocation");
+    free_batch_workspace(&b);
+    return e;
   }
   b.Kp = Kp;
-  b.m = M->m;
-  b.d = M->d;
-  return APPGA_OK;
+  b.m = m;
+  b.d = d;
+  return cudaSuccess;
+}
+
+void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda, int n,
+                     BatchWorkspace& b, bool bf16, bool track, BFwdArgs* fa, BPixArgs* pa) {
+  *fa = BFwdArgs{};
+  fa->A = A;
+  fa->n = n;
+  fa->Kp = b.Kp;
+  fa->track = track ? 1 : 0;
+  fa->use_bf16 = bf16 ? 1 : 0;
+  for (int i = 0; i < 3; ++i) fa->f[i] = b.f[i];
+  fa->y[0] = b.y[0];
+  fa->y[1] = b.y[1];
+  fa->w = b.w;
+  fa->g = b.g;
+  fa->gamma = b.gamma;
+  fa->gR = b.gR;
+  fa->slots = b.slots;
+  fa->bst = b.bst;
+  fa->partial = b.partial;
+  fa->gtick = b.gtick;
+  *pa = BPixArgs{};
+  pa->At = At;
+  pa->n = n;
+  pa->Kp = b.Kp;
+  pa->use_bf16 = bf16 ? 1 : 0;
+  for (int i = 0; i < 3; ++i) pa->f[i] = b.f[i];
+  pa->w = b.w;
+  pa->gR = b.gR;
+  pa->inv_lambda = inv_lambda;
+  pa->pfreeze = b.pfreeze;
+  pa->slots = b.slots;
+  pa->bst = b.bst;
+  pa->partial = b.partial;
+  pa->gtick = b.gtick;
+}
+
+cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
+                                cudaGraphExec_t* out) {
+  *out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    e = launch_bpixel(pa, s);
+    if (e == cudaSuccess) e = launch_bforward(fa, s);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  return e;
 }
 
 SlotState slot_from_params(const appga_params* p, int k0, bool active) {
@@ -104,7 +153,30 @@ SlotState slot_from_params(const appga_params* p, int k0, bool active) {
   s.rel_tol = p->rel_obj_tol;
   s.phi_cur = std::numeric_limits<double>::quiet_NaN();
   s.phi_prev = s.phi_cur;
+  s.phi_k = -1;
   return s;
+}
+
+namespace {
+
+constexpr int kBatchGraphIters = 8;
+
+int padded_width(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
+
+appga_status ensure_batch_workspace(appga_matrix* M, int Kp) {
+  if (M->bw && M->bw->Kp == Kp) return APPGA_OK;
+  if (M->bw) {
+    free_batch_workspace(M->bw);
+  } else {
+    M->bw = new BatchWorkspace();
+  }
+  const cudaError_t e = alloc_batch_workspace(*M->bw, M->m, M->d, Kp);
+  if (e != cudaSuccess) {
+    delete M->bw;
+    M->bw = nullptr;
+    return cuda_fail(e, "batched workspace allocation");
+  }
+  return APPGA_OK;
 }
 
 #define CK(call) APPGA_CK(call)
@@ -144,8 +216,8 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
                 "inputs must satisfy: g finite and >= 0, gamma finite and > 0, f finite and >= 0");
 
   // slot-minor copies of the sinograms; padding slots hold harmless data
-  CK(launch_to_slot_minor(g, K, m, b.g, Kp, 0, s));
-  CK(launch_to_slot_minor(gamma, K, m, b.gamma, Kp, 0, s));
+  CK(launch_to_slot_minor(g, K, m, b.g, Kp, 0, nullptr, s));
+  CK(launch_to_slot_minor(gamma, K, m, b.gamma, Kp, 0, nullptr, s));
   CK(launch_fill_slots(b.g, m, Kp, K, Kp, 0.f, s));
   CK(launch_fill_slots(b.gamma, m, Kp, K, Kp, 1.f, s));
 
@@ -153,9 +225,9 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
   const int G0 = 1;
   float* cur = b.f[G0 % 3];
   if (f_init) {
-    CK(launch_to_slot_minor(f_init, K, d, cur, Kp, 0, s));
+    CK(launch_to_slot_minor(f_init, K, d, cur, Kp, 0, nullptr, s));
   } else {
-    CK(launch_binit_image(g, gamma, m, n, M->na, M->npfov, K, Kp, 0, cur, s));
+    CK(launch_binit_image(g, gamma, m, n, M->na, M->npfov, K, Kp, 0, nullptr, cur, s));
   }
   CK(launch_fill_slots(cur, d, Kp, K, Kp, 0.f, s));
   CK(cudaMemcpyAsync(b.f[(G0 + 2) % 3], cur, (size_t)d * Kp * sizeof(float),
@@ -163,44 +235,17 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
 
   for (int i = 0; i < Kp; ++i) b.slots_host[i] = slot_from_params(params, 1, i < K);
   CK(cudaMemcpyAsync(b.slots, b.slots_host, Kp * sizeof(SlotState), cudaMemcpyHostToDevice, s));
-  CK(launch_binit_momentum(b.slots, Kp, s));
+  CK(launch_binit_momentum(b.slots, Kp, false, s));
   BatchState hb{};
   hb.gstep = G0;
   hb.remaining = params->max_iters > 0 ? K : 0;
   *b.bst_host = hb;
   CK(cudaMemcpyAsync(b.bst, b.bst_host, sizeof(BatchState), cudaMemcpyHostToDevice, s));
 
-  BFwdArgs fa{};
-  fa.A = M->A;
-  fa.n = n;
-  fa.Kp = Kp;
-  fa.track = track ? 1 : 0;
-  fa.use_bf16 = bf16 ? 1 : 0;
-  for (int i = 0; i < 3; ++i) fa.f[i] = b.f[i];
-  fa.y[0] = b.y[0];
-  fa.y[1] = b.y[1];
-  fa.w = b.w;
-  fa.g = b.g;
-  fa.gamma = b.gamma;
-  fa.gR = b.gR;
-  fa.slots = b.slots;
-  fa.bst = b.bst;
-  fa.partial = b.partial;
-  fa.gtick = b.gtick;
-  BPixArgs pa{};
-  pa.At = M->At;
-  pa.n = n;
-  pa.Kp = Kp;
-  pa.use_bf16 = bf16 ? 1 : 0;
-  for (int i = 0; i < 3; ++i) pa.f[i] = b.f[i];
-  pa.w = b.w;
-  pa.gR = b.gR;
-  pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
-  pa.pfreeze = b.pfreeze;
-  pa.slots = b.slots;
-  pa.bst = b.bst;
-  pa.partial = b.partial;
-  pa.gtick = b.gtick;
+  BFwdArgs fa;
+  BPixArgs pa;
+  make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, n, b, bf16, track, &fa,
+                  &pa);
 
   // y^{k0-1}, then the first forward phase (w, y, stencil, Phi of f^{k0})
   BFwdArgs init = fa;
@@ -217,22 +262,8 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
         cudaGraphExecDestroy(b.gexec);
         b.gexec = nullptr;
       }
-      cudaGraph_t graph = nullptr;
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      for (int i = 0; i < S && e == cudaSuccess; ++i) {
-        e = launch_bpixel(pa, s);
-        if (e == cudaSuccess) e = launch_bforward(fa, s);
-      }
-      cudaError_t e2 = cudaStreamEndCapture(s, &graph);
-      if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(e, "batched graph capture");
-      }
-      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&b.gexec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      const cudaError_t e = capture_batch_graph(fa, pa, S, s, &b.gexec);
+      if (e != cudaSuccess) return cuda_fail(e, "batched graph capture");
       b.gkey = key;
     }
     const int reps = (params->max_iters + S - 1) / S;
@@ -271,7 +302,7 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
   CK(cudaMemcpyAsync(b.slots_host, b.slots, Kp * sizeof(SlotState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const int Gf = b.bst_host->gstep;
-  CK(launch_from_slot_minor(b.f[Gf % 3], K, d, Kp, 0, f_out, s));
+  CK(launch_from_slot_minor(b.f[Gf % 3], K, d, Kp, 0, nullptr, f_out, s));
   rc = APPGA_OK;
   if (b.bst_host->flags & APPGA_FLAG_NONFINITE) rc = fail(APPGA_ENUMERIC, "a non-finite value appeared");
   if (stats_host) {

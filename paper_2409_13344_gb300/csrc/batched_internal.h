@@ -21,7 +21,9 @@ struct SlotState {
   int32_t active;     // the slot holds a problem
   int32_t freeze_iter;
   int32_t momentum;
-  int32_t pad0;
+  int32_t fresh;      // just admitted: f^{k-1} = f^k, needs its first forward phase
+  int32_t phi_k;      // iterate index whose objective is in phi_cur (-1: none)
+  int32_t pad1;
   float theta_hi, theta_lo;  // theta_k as a double-float pair
   float lambda1, lambda2, eps, beta;
   double theta, t_cur, phi_cur, phi_prev;
@@ -40,7 +42,8 @@ struct BatchState {
 struct BFwdArgs {
   DevCSR A;
   int32_t n, Kp;
-  int32_t mode;  // 0: solver step; 1: project the previous iterate only
+  int32_t mode;  // 0: solver step; 1: project the previous iterate only;
+                 // 2: first forward phase of the fresh slots only (admission)
   int32_t track;
   int32_t use_bf16;
   int32_t n_spmv_blocks;  // set by the launcher
@@ -75,14 +78,18 @@ struct BPixArgs {
 int batch_max_blocks();
 cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s);
 cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s);
-cudaError_t launch_binit_momentum(SlotState* slots, int Kp, cudaStream_t s);
+// Slot lists: where `ids` is given, slice k goes to slot ids[k] (a device
+// array of K ints); otherwise to slot s0 + k.
+cudaError_t launch_binit_momentum(SlotState* slots, int Kp, bool only_fresh, cudaStream_t s);
 cudaError_t launch_to_slot_minor(const float* in, int K, int len, float* out, int Kp, int s0,
-                                 cudaStream_t s);
-cudaError_t launch_from_slot_minor(const float* in, int K, int len, int Kp, int s0, float* out,
-                                   cudaStream_t s);
+                                 const int* ids, cudaStream_t s);
+cudaError_t launch_from_slot_minor(const float* in, int K, int len, int Kp, int s0,
+                                   const int* ids, float* out, cudaStream_t s);
+cudaError_t launch_copy_slots(const float* src, float* dst, int len, int Kp, const int* ids,
+                              int K, cudaStream_t s);
 cudaError_t launch_fill_slots(float* out, int len, int Kp, int s0, int s1, float v, cudaStream_t s);
 cudaError_t launch_binit_image(const float* g, const float* gamma, int m, int n, int n_angles,
-                               long long npfov, int K, int Kp, int s0, float* f_out,
-                               cudaStream_t s);
+                               long long npfov, int K, int Kp, int s0, const int* ids,
+                               float* f_out, cudaStream_t s);
 
 }  // namespace appga

@@ -67,6 +67,20 @@ struct BatchWorkspace {
 };
 
 void free_batch_workspace(BatchWorkspace* bw);
+// Device bytes of a batched workspace of width Kp for an m x d matrix.
+int64_t batch_workspace_bytes(int m, int d, int Kp);
+// Allocates every array of a width-Kp workspace (frees what it made on error).
+cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp);
+// Kernel arguments of one batched step over workspace b with matrix arrays
+// from (A, At, inv_lambda).
+void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda, int n,
+                     BatchWorkspace& b, bool bf16, bool track, BFwdArgs* fa, BPixArgs* pa);
+// Slot state of a problem run with `p` from iterate index k0 (active), or an
+// empty slot that holds no problem (inactive).
+SlotState slot_from_params(const appga_params* p, int k0, bool active);
+// Captures S x (pixel update, forward phase) into an executable graph.
+cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
+                                cudaGraphExec_t* out);
 
 }  // namespace appga
 

@@ -65,7 +65,8 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
 // the V sums of slots lane*V .. lane*V + V - 1.
 template <int V, bool BF16>
 __device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* __restrict__ X,
-                                         int Kp, int lane, uint64_t pol, float (&acc)[V]) {
+                                         int Kp, int lane, bool lane_on, uint64_t pol,
+                                         float (&acc)[V]) {
 #pragma unroll
   for (int t = 0; t < V; ++t) acc[t] = 0.f;
   const int s = __ldg(M.row_ptr + row), e = __ldg(M.row_ptr + row + 1);
@@ -89,7 +90,14 @@ __device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* 
       }
       float x[4][V];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) vload<V>(xl + (size_t)cq[u] * Kp, x[u]);
+      for (int u = 0; u < 4; ++u) {
+        if (lane_on) {
+          vload<V>(xl + (size_t)cq[u] * Kp, x[u]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < V; ++t) x[u][t] = 0.f;
+        }
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -170,7 +178,7 @@ struct BStencilSmem {
 __device__ float bstencil_item(BStencilSmem& S, const float* __restrict__ fk,
                                const float* __restrict__ fkm, const SlotState* slots, int Kp,
                                int r0, int c0, int s0, int n, float* __restrict__ gR,
-                               bool want_reg) {
+                               bool want_reg, int mode) {
   const int tid = threadIdx.x;
   // load the halo tile, slots fastest (32-byte runs)
   for (int t = tid; t < (BST_R + 4) * BTW * BST_S; t += blockDim.x) {
@@ -181,7 +189,7 @@ __device__ float bstencil_item(BStencilSmem& S, const float* __restrict__ fk,
     if (r >= 0 && r < n && c >= 0 && c < n) {
       const size_t o = (size_t)(r * n + c) * Kp + s0 + q;
       vk = fk[o];
-      vt = fmaf(slots[s0 + q].theta_hi, vk - fkm[o], vk);
+      vt = mode == 2 ? vk : fmaf(slots[s0 + q].theta_hi, vk - fkm[o], vk);
     }
     S.K[ii][jj][q] = vk;
     S.T[ii][jj][q] = vt;
@@ -226,11 +234,12 @@ __device__ float bstencil_item(BStencilSmem& S, const float* __restrict__ fk,
   __syncthreads();
   const int col = tid % BST_C, q = tid / BST_C;
   const SlotState& sl = slots[s0 + q];
+  const bool part = mode == 2 ? sl.fresh : (sl.active && !sl.done);
   float reg = 0.f;
 #pragma unroll
   for (int ii = 0; ii < BST_R; ++ii) {
     const int r = r0 + ii, c = c0 + col;
-    if (r < n && c < n) {
+    if (part && r < n && c < n) {
       const int i = ii + 1, j = col + 1;
       const bool r_lo = r >= 1, r_hi = r <= n - 2, c_lo = c >= 1, c_hi = c <= n - 2;
       auto W = [&](int f, int a, int b) { return S.V[f][a][b][q]; };
@@ -285,6 +294,18 @@ __device__ void bset_theta(SlotState& s, double theta) {
 
 // -------------------------------------------------------------- k_bforward
 
+// Live slots (held and not finished), counted by the one block that calls it.
+__device__ void bset_remaining(const SlotState* slots, int Kp, BatchState* bs) {
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int s = threadIdx.x; s < Kp; s += blockDim.x) c += slots[s].active && !slots[s].done;
+  if (c) atomicAdd(&s_cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) bs->remaining = s_cnt;
+}
+
 template <int V, bool BF16>
 __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   __shared__ union {
@@ -301,12 +322,24 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Kp = a.Kp, n = a.n;
   const int G = bs->gstep;
-  const float* f = a.mode == 0 ? a.f[G % 3] : a.f[(G + 2) % 3];
-  float* y_out = a.mode == 0 ? a.y[G & 1] : a.y[(G + 1) & 1];
+  const bool proj_only = a.mode == 1;
+  const float* f = proj_only ? a.f[(G + 2) % 3] : a.f[G % 3];
+  float* y_out = proj_only ? a.y[(G + 1) & 1] : a.y[G & 1];
   const float* y_prev = a.y[(G + 1) & 1];
-  const bool loop = a.mode == 0;
-  const bool want = loop && a.track;
-  // per-slot data-term accumulators of this lane
+  const bool want = !proj_only && a.track;
+  // which of this lane's slots take part: every slot (projection), the live
+  // slots (step), or the fresh slots (admission, where f^{k-1} = f^k so the
+  // extrapolated projection is y itself)
+  int on[V];
+  float th_h[V];
+  bool lane_on = false;
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const SlotState& sl = a.slots[lane * V + t];
+    on[t] = proj_only ? 1 : (a.mode == 2 ? sl.fresh : (sl.active && !sl.done));
+    th_h[t] = a.mode == 2 ? 0.f : sl.theta_hi;
+    lane_on = lane_on || on[t];
+  }
   float dh[V], dl[V];
   int hits[V];
 #pragma unroll
@@ -315,38 +348,36 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
     dl[t] = 0.f;
     hits[t] = 0;
   }
-  float th_h[V], gam_k[V];
-  if (loop) {
-#pragma unroll
-    for (int t = 0; t < V; ++t) {
-      th_h[t] = a.slots[lane * V + t].theta_hi;
-      gam_k[t] = 0.f;
-    }
-  }
   if ((int)blockIdx.x < a.n_spmv_blocks) {
     const uint64_t pol = evict_first_policy();
     const int stride = a.n_spmv_blocks * B_WARPS;
     for (int row = blockIdx.x * B_WARPS + warp; row < a.A.rows; row += stride) {
       float acc[V];
-      brow_dot<V, BF16>(a.A, row, f, Kp, lane, pol, acc);
+      brow_dot<V, BF16>(a.A, row, f, Kp, lane, lane_on, pol, acc);
+      if (!lane_on) continue;
       const size_t o = (size_t)row * Kp + lane * V;
-      vstore<V>(y_out + o, acc);
-      if (!loop) continue;
-      float yp[V], gg[V], gm[V], wv[V];
-      vload<V>(y_prev + o, yp);
-      vload<V>(a.g + o, gg);
-      vload<V>(a.gamma + o, gm);
+      float yp[V], gg[V], gm[V], yo[V], wo[V];
+      vload<V>(y_out + o, yo);
+      if (!proj_only) {
+        vload<V>(y_prev + o, yp);
+        vload<V>(a.g + o, gg);
+        vload<V>(a.gamma + o, gm);
+        vload<V>(a.w + o, wo);
+      }
 #pragma unroll
       for (int t = 0; t < V; ++t) {
+        if (!on[t]) continue;
+        yo[t] = acc[t];
+        if (proj_only) continue;
         // y~ = y + theta (y - y_prev); den = max(y~ + gamma, kappa gamma); w = (den - g)/den
-        const float yt = fmaf(th_h[t], acc[t] - yp[t], acc[t]);
+        const float yt = a.mode == 2 ? acc[t] : fmaf(th_h[t], acc[t] - yp[t], acc[t]);
         float den = yt + gm[t];
         const float fl = 1e-3f * gm[t];
         if (den < fl) {
           den = fl;
           ++hits[t];
         }
-        wv[t] = __fdiv_rn(den - gg[t], den);
+        wo[t] = __fdiv_rn(den - gg[t], den);
         if (want) {
           // data term y - g ln(y + gamma) in double-float
           df yg;
@@ -355,25 +386,38 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
           acc_add(dh[t], dl[t], term.hi, term.lo);
         }
       }
-      vstore<V>(a.w + o, wv);
+      vstore<V>(y_out + o, yo);
+      if (!proj_only) vstore<V>(a.w + o, wo);
     }
-  } else if (loop) {
+  } else if (!proj_only) {
     // stencil items: (tile, 8-slot chunk) pairs, persistent over the stencil blocks
     const int nsb = gridDim.x - a.n_spmv_blocks;
     const int ntx = (n + BST_C - 1) / BST_C, nty = (n + BST_R - 1) / BST_R;
     const int nchunks = Kp / BST_S;
-    const int nitems = ntx * nty * nchunks;
+    const int ntiles = ntx * nty;
     __shared__ float sreg_hi[MAXK], sreg_lo[MAXK];  // per-slot regulariser sums
+    __shared__ int chunk_on[MAXK / BST_S];
     for (int s = tid; s < MAXK; s += blockDim.x) {
       sreg_hi[s] = 0.f;
       sreg_lo[s] = 0.f;
     }
+    for (int c = tid; c < nchunks; c += blockDim.x) {
+      int any = 0;
+      for (int q = 0; q < BST_S; ++q) {
+        const SlotState& sl = a.slots[c * BST_S + q];
+        any |= a.mode == 2 ? sl.fresh : (sl.active && !sl.done);
+      }
+      chunk_on[c] = any;
+    }
     __syncthreads();
-    for (int it = blockIdx.x - a.n_spmv_blocks; it < nitems; it += nsb) {
-      const int chunk = it % nchunks, tile = it / nchunks;
+    // Each block owns the same tiles for every slot chunk, so a slot's
+    // regulariser sum is grouped the same way whatever its slot index.
+    for (int tile = blockIdx.x - a.n_spmv_blocks; tile < ntiles; tile += nsb)
+    for (int chunk = 0; chunk < nchunks; ++chunk) {
+      if (!chunk_on[chunk]) continue;  // uniform over the block
       const int r0 = (tile / ntx) * BST_R, c0 = (tile % ntx) * BST_C;
       const float reg = bstencil_item(sm.st, f, a.f[(G + 2) % 3], a.slots, Kp, r0, c0,
-                                      chunk * BST_S, n, a.gR, want);
+                                      chunk * BST_S, n, a.gR, want, a.mode);
       if (want) {
         // warp q holds slot chunk*8 + q: fold the warp's 32 columns
         float h = reg, l = 0.f;
@@ -385,24 +429,32 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
       }
     }
     __syncthreads();
-    if (want) {
+    if (want && warp == 0) {
       // hand the per-slot sums to the lanes that own the slots in warp 0
-      if (warp == 0) {
 #pragma unroll
-        for (int t = 0; t < V; ++t) {
-          dh[t] = sreg_hi[lane * V + t];
-          dl[t] = sreg_lo[lane * V + t];
-        }
+      for (int t = 0; t < V; ++t) {
+        dh[t] = sreg_hi[lane * V + t];
+        dl[t] = sreg_lo[lane * V + t];
       }
     }
   }
-  // guard hits per slot
-  if (loop) {
+  if (!proj_only) {
 #pragma unroll
     for (int t = 0; t < V; ++t)
       if (hits[t]) atomicAdd(&a.slots[lane * V + t].guard_hits, (unsigned long long)hits[t]);
   }
-  if (!want) return;
+  if (proj_only) return;
+  if (!want) {
+    // no objective: an admission pass still clears the fresh flags (last block)
+    if (a.mode != 2) return;
+    double unused;
+    __syncthreads();
+    if (grid_reduce(a.partial, a.gtick, &bs->ticket_r, {0.f, 0.f}, &unused)) {
+      for (int s = tid; s < Kp; s += blockDim.x) a.slots[s].fresh = 0;
+      bset_remaining(a.slots, Kp, bs);
+    }
+    return;
+  }
   // block partial per slot (fixed order over warps)
   __syncthreads();
 #pragma unroll
@@ -420,20 +472,27 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   __syncthreads();
   if (grid_reduce_slots(a.partial, a.gtick, &bs->ticket_r, sm.e.bhi, sm.e.blo, Kp, sm.e.thi,
                         sm.e.tlo)) {
-    // Phi(f^k) of every slot and its stopping test
+    // Phi(f^k) of every participating slot (once per iterate) and its stopping test
     for (int s = tid; s < Kp; s += blockDim.x) {
       SlotState& sl = a.slots[s];
-      if (!sl.active || sl.done) continue;
+      const bool part = a.mode == 2 ? sl.fresh : (sl.active && !sl.done);
+      if (!part) continue;
+      sl.fresh = 0;
+      if (sl.phi_k == sl.k) continue;  // this iterate's objective is already in
       const double phi = (double)sm.e.thi[s] + (double)sm.e.tlo[s];
       const double prev = sl.phi_cur;
+      const bool consecutive = sl.phi_k == sl.k - 1;
       sl.phi_prev = prev;
       sl.phi_cur = phi;
-      if (sl.rel_tol > 0.0 && sl.k > sl.k0 && fabs(phi - prev) <= sl.rel_tol * fabs(prev)) {
+      sl.phi_k = sl.k;
+      if (sl.rel_tol > 0.0 && sl.k > sl.k0 && consecutive &&
+          fabs(phi - prev) <= sl.rel_tol * fabs(prev)) {
         sl.done = 1;
         sl.result_k = sl.k;
         sl.stopped_early = 1;
       }
     }
+    if (a.mode == 2) bset_remaining(a.slots, Kp, bs);
   }
 }
 
@@ -461,12 +520,15 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
     kk[t] = sl.k;
     frz[t] = sl.freeze_iter;
   }
+  bool lane_live = false;
+#pragma unroll
+  for (int t = 0; t < V; ++t) lane_live = lane_live || live[t];
   const uint64_t pol = evict_first_policy();
   const int stride = gridDim.x * B_WARPS;
   int bad = 0;
   for (int j = blockIdx.x * B_WARPS + warp; j < a.At.rows; j += stride) {
     float bp[V];
-    brow_dot<V, BF16>(a.At, j, a.w, Kp, lane, pol, bp);
+    brow_dot<V, BF16>(a.At, j, a.w, Kp, lane, lane_live, pol, bp);
     const size_t o = (size_t)j * Kp + lane * V;
     float vk[V], vm[V], gr[V], out[V];
     vload<V>(fk + o, vk);
@@ -538,11 +600,13 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
 
 // ----------------------------------------------------------- setup kernels
 
-// theta_{k0} of every live slot (same device arithmetic as the step kernel).
-__global__ void k_binit_momentum(SlotState* slots, int Kp) {
+// theta_{k0} of every slot, or of the fresh slots only (same device
+// arithmetic as the step kernel).
+__global__ void k_binit_momentum(SlotState* slots, int Kp, int only_fresh) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Kp) return;
   SlotState& sl = slots[s];
+  if (only_fresh && !sl.fresh) return;
   double theta = 0.0, t = 1.0;
   if (sl.momentum == APPGA_MOMENTUM_GN) {
     theta = (bgn_t(sl.k - 1, sl.a, sl.b, sl.omega) - 1.0) / bgn_t(sl.k, sl.a, sl.b, sl.omega);
@@ -557,10 +621,15 @@ __global__ void k_binit_momentum(SlotState* slots, int Kp) {
   sl.t_cur = t;
 }
 
-// [rows][ld] slice-major -> [rows_out = ld][Kp] slot-minor for slots [s0, s0+K):
-// out[i*Kp + s0 + s] = in[s*ld + i].  Padding slots are written separately.
+// Slot of the k-th slice: ids[k] when a slot list is given, else s0 + k.
+__device__ __forceinline__ int slot_of(const int* ids, int s0, int k) {
+  return ids ? __ldg(ids + k) : s0 + k;
+}
+
+// [K][len] slice-major -> [len][Kp] slot-minor: out[i*Kp + slot(s)] = in[s*len + i].
+// Padding slots are written separately.
 __global__ void k_to_slot_minor(const float* __restrict__ in, int K, int len, float* __restrict__ out,
-                                int Kp, int s0) {
+                                int Kp, int s0, const int* __restrict__ ids) {
   __shared__ float tile[32][33];
   const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -570,22 +639,31 @@ __global__ void k_to_slot_minor(const float* __restrict__ in, int K, int len, fl
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int i = i0 + r, k = k0 + threadIdx.x;
-    if (i < len && k < K) out[(size_t)i * Kp + s0 + k] = tile[threadIdx.x][r];
+    if (i < len && k < K) out[(size_t)i * Kp + slot_of(ids, s0, k)] = tile[threadIdx.x][r];
   }
 }
-// out[s*len + i] = in[i*Kp + s0 + s] for s < K.
+// out[s*len + i] = in[i*Kp + slot(s)] for s < K.
 __global__ void k_from_slot_minor(const float* __restrict__ in, int K, int len, int Kp, int s0,
-                                  float* __restrict__ out) {
+                                  const int* __restrict__ ids, float* __restrict__ out) {
   __shared__ float tile[32][33];
   const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int i = i0 + r, k = k0 + threadIdx.x;
-    tile[r][threadIdx.x] = (i < len && k < K) ? in[(size_t)i * Kp + s0 + k] : 0.f;
+    tile[r][threadIdx.x] = (i < len && k < K) ? in[(size_t)i * Kp + slot_of(ids, s0, k)] : 0.f;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r, i = i0 + threadIdx.x;
     if (k < K && i < len) out[(size_t)k * len + i] = tile[threadIdx.x][r];
+  }
+}
+// Copies the listed columns of one [len][Kp] array into another.
+__global__ void k_copy_slots(const float* __restrict__ src, float* __restrict__ dst, int len,
+                             int Kp, const int* __restrict__ ids, int K) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)len * K;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = (t / K) * Kp + __ldg(ids + t % K);
+    dst[o] = src[o];
   }
 }
 // Sets column s of a [len][Kp] array to v for s in [s0, s1).
@@ -596,13 +674,15 @@ __global__ void k_fill_slots(float* out, int len, int Kp, int s0, int s1, float 
     out[(t / w) * Kp + s0 + t % w] = v;
 }
 
-// Per-slot initial image TMC_s * 1_disk (Sec. 4.1) for slots [s0, s0+K) from
-// slice-major g, gamma ([K][m]): one block per slot.
+// Per-slot initial image TMC_s * 1_disk (Sec. 4.1) for the slots of K slices
+// (s0 + k, or ids[k]) from slice-major g, gamma ([K][m]): one block per slice.
 __global__ void __launch_bounds__(256) k_binit_image(const float* __restrict__ g,
                                                      const float* __restrict__ gamma, int m, int n,
                                                      int n_angles, long long npfov, int Kp, int s0,
+                                                     const int* __restrict__ ids,
                                                      float* __restrict__ f_out) {
   const int k = blockIdx.x;
+  const int slot = slot_of(ids, s0, k);
   float h = 0.f, l = 0.f;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     acc_add(h, l, g[(size_t)k * m + i], 0.f);
@@ -617,7 +697,7 @@ __global__ void __launch_bounds__(256) k_binit_image(const float* __restrict__ g
   for (int j = threadIdx.x; j < n * n; j += blockDim.x) {
     const int r = j / n, c = j % n;
     const long long dx = 2ll * c + 1 - n, dy = 2ll * r + 1 - n;
-    f_out[(size_t)j * Kp + s0 + k] = (dx * dx + dy * dy <= (long long)n * n) ? v : 0.f;
+    f_out[(size_t)j * Kp + slot] = (dx * dx + dy * dy <= (long long)n * n) ? v : 0.f;
   }
 }
 
@@ -649,9 +729,11 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   if (nsp > cap) nsp = cap;
   a.n_spmv_blocks = nsp;
   int nst = 0;
-  if (a.mode == 0) {
-    const int items = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R) * (a.Kp / BST_S);
-    nst = items < sms * 4 ? items : sms * 4;
+  if (a.mode != 1) {
+    // equal tile counts per stencil block, at most 4 blocks per SM
+    const int tiles = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R);
+    const int per = (tiles + sms * 4 - 1) / (sms * 4);
+    nst = (tiles + per - 1) / per;
   }
   const int grid = nsp + nst;
   if (a.use_bf16)
@@ -696,22 +778,31 @@ cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_binit_momentum(SlotState* slots, int Kp, cudaStream_t s) {
-  k_binit_momentum<<<(Kp + 127) / 128, 128, 0, s>>>(slots, Kp);
+cudaError_t launch_binit_momentum(SlotState* slots, int Kp, bool only_fresh, cudaStream_t s) {
+  k_binit_momentum<<<(Kp + 127) / 128, 128, 0, s>>>(slots, Kp, only_fresh ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_slot_minor(const float* in, int K, int len, float* out, int Kp, int s0,
-                                 cudaStream_t s) {
+                                 const int* ids, cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
   dim3 grid((len + 31) / 32, (K + 31) / 32), block(32, 8);
-  k_to_slot_minor<<<grid, block, 0, s>>>(in, K, len, out, Kp, s0);
+  k_to_slot_minor<<<grid, block, 0, s>>>(in, K, len, out, Kp, s0, ids);
   return cudaGetLastError();
 }
 
-cudaError_t launch_from_slot_minor(const float* in, int K, int len, int Kp, int s0, float* out,
-                                   cudaStream_t s) {
+cudaError_t launch_from_slot_minor(const float* in, int K, int len, int Kp, int s0,
+                                   const int* ids, float* out, cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
   dim3 grid((len + 31) / 32, (K + 31) / 32), block(32, 8);
-  k_from_slot_minor<<<grid, block, 0, s>>>(in, K, len, Kp, s0, out);
+  k_from_slot_minor<<<grid, block, 0, s>>>(in, K, len, Kp, s0, ids, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_slots(const float* src, float* dst, int len, int Kp, const int* ids,
+                              int K, cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
+  k_copy_slots<<<256, 256, 0, s>>>(src, dst, len, Kp, ids, K);
   return cudaGetLastError();
 }
 
@@ -723,9 +814,10 @@ cudaError_t launch_fill_slots(float* out, int len, int Kp, int s0, int s1, float
 }
 
 cudaError_t launch_binit_image(const float* g, const float* gamma, int m, int n, int n_angles,
-                               long long npfov, int K, int Kp, int s0, float* f_out,
-                               cudaStream_t s) {
-  k_binit_image<<<K, 256, 0, s>>>(g, gamma, m, n, n_angles, npfov, Kp, s0, f_out);
+                               long long npfov, int K, int Kp, int s0, const int* ids,
+                               float* f_out, cudaStream_t s) {
+  if (K <= 0) return cudaSuccess;
+  k_binit_image<<<K, 256, 0, s>>>(g, gamma, m, n, n_angles, npfov, Kp, s0, ids, f_out);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,308 @@
+"""GPU tests of the continuous-batching server (appga_server.h) through the C
+ABI: results against the FP64 oracle and the batched call, the same result
+alone and in a mix of geometries admitted mid-run, admission by a device
+memory budget, per-request stopping, and input validation."""
+import numpy as np
+import pytest
+
+from oracle import appga_oracle as O
+from paper_2409_13344_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2409_13344_gb300 import build
+    build.build()
+    from paper_2409_13344_gb300 import appga
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA device")
+    return appga
+
+
+@pytest.fixture(scope="module")
+def ctx(A):
+    c = A.Context(0)
+    yield c
+    c.close()
+
+
+_mats = {}
+
+
+def matrix(A, ctx, name):
+    if name not in _mats:
+        geom = W.GEOMETRIES[name] if isinstance(name, str) else name
+        Amat = W.system_matrix(name) if isinstance(name, str) else W.siddon_matrix(geom)
+        _mats[name] = (geom, Amat, A.Matrix(ctx, Amat, geom.n, geom.n_angles, bf16=True))
+    return _mats[name]
+
+
+def make_slices(geom, Amat, counts, config):
+    return [W.make_slice(Amat, geom, float(c), W.seed_for(config, i)) for i, c in enumerate(counts)]
+
+
+def rel(a, b):
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def drain(srv, limit=10000):
+    for _ in range(limit):
+        if srv.step() == 0:
+            return
+    raise AssertionError("server did not drain")
+
+
+def run_alone(A, ctx, mat, sl, params, **cfg):
+    srv = A.Server(ctx, **cfg)
+    gid = srv.add_geometry(mat)
+    rid = srv.submit(gid, sl.g, sl.gamma, params)
+    drain(srv)
+    f, st = srv.collect(rid)
+    srv.close()
+    return f, st
+
+
+def test_server_matches_batched_call_and_oracle(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = make_slices(geom, Amat, [5e4, 1e5, 3e5], config=3)
+    # (a first-order-only penalty at large steps amplifies FP32 rounding of
+    # the iterates: FP32-sized relative noise on every FP64 oracle iterate
+    # moves its result by ~2e-6 at beta = 0.3 but ~2e-7 at beta = 0.1, so
+    # that case runs at beta = 0.1)
+    kws = [dict(max_iters=30, omega=0.5), dict(max_iters=23, omega=1.0, beta=0.3),
+           dict(max_iters=30, omega=0.25, lambda1=0.2, lambda2=0.0, beta=0.1)]
+    srv = A.Server(ctx, slots_per_pool=32, steps_per_launch=8)
+    gid = srv.add_geometry(mat)
+    ids = [srv.submit(gid, sl.g, sl.gamma, A.default_params(**kw)) for sl, kw in zip(sls, kws)]
+    drain(srv)
+    for rid, sl, kw in zip(ids, sls, kws):
+        f, st = srv.collect(rid)
+        assert st.state == A.APPGA_REQ_DONE
+        assert st.iters == kw["max_iters"] and st.result_k == 1 + kw["max_iters"]
+        # the same slice through the batched call (same kernels, width 32)
+        fb = torch.empty((1, geom.d), dtype=torch.float32, device=DEV)
+        A.appga_reconstruct_batched(ctx.handle, mat.handle, 1, torch.from_numpy(sl.g).to(DEV),
+                                    torch.from_numpy(sl.gamma).to(DEV), None,
+                                    A.default_params(**kw), fb)
+        np.testing.assert_array_equal(f, fb.cpu().numpy()[0])
+        prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+        ref = O.appga(prob, O.Params(**kw), n_angles=geom.n_angles, track_phi=False)
+        assert rel(f, ref.f) <= 1e-5, (kw, rel(f, ref.f))
+        # Phi of the last evaluated iterate, against the FP64 objective of that iterate
+        assert st.phi_k == kw["max_iters"]
+        assert np.isfinite(st.phi_last)
+        assert st.t_submit <= st.t_admit <= st.t_done
+    srv.close()
+
+
+def test_same_result_alone_and_in_the_mix(A, ctx):
+    """A request gives the same image and iteration count whether it runs
+    alone or is admitted into pools whose other slots are mid-run, next to
+    requests of another geometry, with slots freed and reused around it."""
+    g64, A64, m64 = matrix(A, ctx, "64")
+    gr, Ar, mr = matrix(A, ctx, W.Geometry(40, 48, 59))
+    rng = np.random.default_rng(5)
+    mix64 = make_slices(g64, A64, W.log_uniform_counts(rng, 2e4, 5e5, 40), config=11)
+    mixr = make_slices(gr, Ar, W.log_uniform_counts(rng, 1e4, 1e5, 20), config=12)
+    iters64 = rng.integers(5, 60, size=40)
+    itersr = rng.integers(5, 60, size=20)
+    targets = [(m64, mix64[7], dict(max_iters=41, omega=0.5)),
+               (m64, mix64[30], dict(max_iters=300, omega=1.0, beta=0.1, rel_obj_tol=1e-6)),
+               (mr, mixr[3], dict(max_iters=37, beta=0.03, omega=1.0))]
+    alone = [run_alone(A, ctx, m, sl, A.default_params(**kw), slots_per_pool=32)
+             for m, sl, kw in targets]
+
+    srv = A.Server(ctx, slots_per_pool=32, steps_per_launch=4, max_pools=2)
+    gid64, gidr = srv.add_geometry(m64), srv.add_geometry(mr)
+    submitted = {}
+    order = list(range(40))
+    rng.shuffle(order)
+    running_at_admit = {}
+    # a stream of arrivals: a few requests per step, the targets in the middle
+    for step in range(400):
+        for _ in range(2):
+            if order:
+                i = order.pop()
+                if i == 7:
+                    kw = targets[0][2]
+                elif i == 30:
+                    kw = targets[1][2]
+                else:
+                    kw = dict(max_iters=int(iters64[i]), omega=float(rng.choice([0.25, 0.5, 1.0])))
+                submitted[("64", i)] = srv.submit(gid64, mix64[i].g, mix64[i].gamma,
+                                                  A.default_params(**kw))
+                if i in (7, 30):
+                    running_at_admit[i] = srv.summary().running
+        if step < 20:
+            i = step
+            kw = targets[2][2] if i == 3 else dict(max_iters=int(itersr[i]), beta=0.03)
+            submitted[("r", i)] = srv.submit(gidr, mixr[i].g, mixr[i].gamma, A.default_params(**kw))
+            if i == 3:
+                running_at_admit[3] = srv.summary().running
+        pending = srv.step()
+        if not order and step >= 20 and pending == 0:
+            break
+    drain(srv)
+    summ = srv.summary()
+    assert summ.completed == 60 and summ.waiting == 0 and summ.running == 0
+    assert summ.pools <= 2  # 60 requests through two pools of 32 slots: slots were reused
+    # the targets were admitted while other requests were running
+    assert all(v > 0 for v in running_at_admit.values()), running_at_admit
+    keys = [("64", 7), ("64", 30), ("r", 3)]
+    for key, (f0, st0) in zip(keys, alone):
+        f1, st1 = srv.collect(submitted[key])
+        assert st1.iters == st0.iters and st1.stopped_early == st0.stopped_early, key
+        # same per-slot arithmetic in every slot: the images agree bit for bit
+        # (the stated tolerance, rel L2 <= 1e-5, is far looser)
+        np.testing.assert_array_equal(f1, f0)
+        assert st1.phi_last == st0.phi_last
+    assert alone[1][1].stopped_early == 1
+    srv.close()
+
+
+def test_admission_waits_for_device_memory(A, ctx):
+    """With a budget that holds one pool, requests of a second geometry wait
+    until the first geometry's pool is empty and released."""
+    g64, A64, m64 = matrix(A, ctx, "64")
+    gr, Ar, mr = matrix(A, ctx, W.Geometry(40, 48, 59))
+    probe = A.Server(ctx, slots_per_pool=32)
+    pid = probe.add_geometry(m64)
+    sl = make_slices(g64, A64, [1e5], config=3)[0]
+    probe.submit(pid, sl.g, sl.gamma, A.default_params(max_iters=1))
+    probe.step()
+    one_pool = probe.summary().device_bytes
+    probe.close()
+    assert one_pool > 0
+
+    srv = A.Server(ctx, slots_per_pool=32, hbm_budget_bytes=int(one_pool * 1.05))
+    gid64, gidr = srv.add_geometry(m64), srv.add_geometry(mr)
+    s64 = make_slices(g64, A64, [1e5] * 5, config=13)
+    sr = make_slices(gr, Ar, [5e4] * 3, config=14)
+    ids64 = [srv.submit(gid64, s.g, s.gamma, A.default_params(max_iters=20)) for s in s64]
+    idsr = [srv.submit(gidr, s.g, s.gamma, A.default_params(max_iters=10, beta=0.03)) for s in sr]
+    while True:
+        pending = srv.step()
+        summ = srv.summary()
+        assert summ.device_bytes <= int(one_pool * 1.05)
+        assert summ.pools <= 1
+        if pending == 0:
+            break
+    st64 = [srv.poll(i) for i in ids64]
+    str_ = [srv.poll(i) for i in idsr]
+    assert all(s.state == A.APPGA_REQ_DONE for s in st64 + str_)
+    assert min(s.t_admit for s in str_) >= max(s.t_done for s in st64)
+    for i, s in zip(idsr, sr):
+        f, st = srv.collect(i)
+        prob = O.Problem(Ar, s.g, s.gamma, gr.n)
+        ref = O.appga(prob, O.Params(max_iters=10, beta=0.03), n_angles=gr.n_angles,
+                      track_phi=False)
+        assert rel(f, ref.f) <= 1e-5
+    srv.close()
+
+
+def test_server_per_request_stopping_matches_oracle(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = make_slices(geom, Amat, [5e4, 2e5, 5e5], config=3)
+    kw = dict(max_iters=400, beta=0.1, omega=1.0, rel_obj_tol=1e-6)
+    srv = A.Server(ctx, slots_per_pool=32, steps_per_launch=8)
+    gid = srv.add_geometry(mat)
+    ids = [srv.submit(gid, sl.g, sl.gamma, A.default_params(**kw)) for sl in sls]
+    drain(srv)
+    iters = []
+    for rid, sl in zip(ids, sls):
+        f, st = srv.collect(rid)
+        prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+        ref = O.appga(prob, O.Params(**kw), n_angles=geom.n_angles, track_phi=True)
+        assert st.stopped_early == 1
+        assert abs(st.iters - ref.iters) <= 1, (st.iters, ref.iters)
+        if st.iters == ref.iters:
+            assert rel(f, ref.f) <= 1e-5
+        iters.append(st.iters)
+    assert len(set(iters)) > 1
+    srv.close()
+
+
+def test_server_bf16_pools(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = make_slices(geom, Amat, [1e5, 4e5], config=3)
+    srv = A.Server(ctx, slots_per_pool=32, a_precision=A.APPGA_PREC_BF16)
+    gid = srv.add_geometry(mat)
+    ids = [srv.submit(gid, sl.g, sl.gamma, A.default_params(max_iters=30)) for sl in sls]
+    drain(srv)
+    for rid, sl in zip(ids, sls):
+        f, _ = srv.collect(rid)
+        fb = torch.empty((1, geom.d), dtype=torch.float32, device=DEV)
+        A.appga_reconstruct_batched(ctx.handle, mat.handle, 1, torch.from_numpy(sl.g).to(DEV),
+                                    torch.from_numpy(sl.gamma).to(DEV), None,
+                                    A.default_params(max_iters=30, a_precision=1), fb)
+        np.testing.assert_array_equal(f, fb.cpu().numpy()[0])
+        prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+        ref = O.appga(prob, O.Params(max_iters=30), n_angles=geom.n_angles, track_phi=False)
+        assert rel(f, ref.f) <= 1e-3
+    srv.close()
+
+
+def test_server_f_init_and_zero_iterations(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sl = make_slices(geom, Amat, [1e5], config=3)[0]
+    f0 = np.full(geom.d, 0.5, np.float32)
+    srv = A.Server(ctx, slots_per_pool=32)
+    gid = srv.add_geometry(mat)
+    r1 = srv.submit(gid, sl.g, sl.gamma, A.default_params(max_iters=12), f_init=f0)
+    r2 = srv.submit(gid, sl.g, sl.gamma, A.default_params(max_iters=0), f_init=f0)
+    drain(srv)
+    f1, st1 = srv.collect(r1)
+    f2, st2 = srv.collect(r2)
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    ref = O.appga(prob, O.Params(max_iters=12), f_init=f0.astype(np.float64),
+                  n_angles=geom.n_angles, track_phi=False)
+    assert st1.iters == 12 and rel(f1, ref.f) <= 1e-5
+    assert st2.iters == 0
+    np.testing.assert_array_equal(f2, f0)
+    srv.close()
+
+
+def test_server_rejects_bad_requests(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sl = make_slices(geom, Amat, [1e5], config=3)[0]
+    srv = A.Server(ctx, slots_per_pool=32)
+    gid = srv.add_geometry(mat)
+    bad_g = sl.g.copy()
+    bad_g[5] = -1.0
+    with pytest.raises(A.AppgaError) as ei:
+        srv.submit(gid, bad_g, sl.gamma, A.default_params())
+    assert ei.value.status == A.APPGA_EDOMAIN
+    zero_gamma = sl.gamma.copy()
+    zero_gamma[0] = 0.0
+    with pytest.raises(A.AppgaError) as ei:
+        srv.submit(gid, sl.g, zero_gamma, A.default_params())
+    assert ei.value.status == A.APPGA_EDOMAIN
+    with pytest.raises(A.AppgaError) as ei:
+        srv.submit(gid + 5, sl.g, sl.gamma, A.default_params())
+    assert ei.value.status == A.APPGA_EINVAL
+    with pytest.raises(A.AppgaError) as ei:
+        srv.submit(gid, sl.g, sl.gamma, A.default_params(eps=0.0))
+    assert ei.value.status == A.APPGA_EINVAL
+    rid = srv.submit(gid, sl.g, sl.gamma, A.default_params(max_iters=50))
+    with pytest.raises(A.AppgaError) as ei:
+        srv.collect(rid)
+    assert ei.value.status == A.APPGA_EBUSY
+    assert srv.poll(rid).state == A.APPGA_REQ_WAITING
+    srv.step()
+    assert srv.poll(rid).state == A.APPGA_REQ_RUNNING
+    drain(srv)
+    srv.collect(rid)
+    with pytest.raises(A.AppgaError) as ei:
+        srv.poll(rid)
+    assert ei.value.status == A.APPGA_EINVAL
+    assert srv.summary().completed == 1
+    srv.close()
+    with pytest.raises(A.AppgaError) as ei:
+        A.Server(ctx, slots_per_pool=48)
+    assert ei.value.status == A.APPGA_EINVAL

@@ -1,5 +1,5 @@
 """CPU-side checks of the C ABI library: it builds, loads, exports every
-function declared in include/appga.h, and its host-only logic (parameter
+function declared in include/*.h, and its host-only logic (parameter
 validation, CSR validation, momentum scalar, status strings) behaves.  No
 call here touches a GPU."""
 import ctypes
@@ -53,6 +53,43 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(appga.appga_params) == 96
     assert ctypes.sizeof(appga.appga_stats) == 40
     assert ctypes.sizeof(appga.appga_matrix_info) == 56
+
+
+def test_struct_layouts_match_c_compiler(lib, tmp_path):
+    """sizeof and field offsets of every ABI struct as the C compiler lays
+    them out, against the ctypes mirrors the binding passes."""
+    import shutil
+    import subprocess
+    from paper_2409_13344_gb300 import appga
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [appga.appga_params, appga.appga_stats, appga.appga_matrix_info,
+               appga.appga_server_config, appga.appga_request_stats, appga.appga_server_summary]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "appga_server.h"',
+             "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("{st.__name__} %zu\\n", sizeof({st.__name__}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{st.__name__}.{f} %zu\\n", offsetof({st.__name__}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for st in structs:
+        assert int(got[st.__name__]) == ctypes.sizeof(st), st.__name__
+        for f, _ in st._fields_:
+            assert int(got[f"{st.__name__}.{f}"]) == getattr(st, f).offset, (st.__name__, f)
+
+
+def test_server_config_default(lib):
+    from paper_2409_13344_gb300 import appga as A
+    c = A.server_config()
+    assert (c.slots_per_pool, c.steps_per_launch, c.a_precision, c.max_pools) == (64, 8, 0, 0)
+    assert (c.hbm_budget_bytes, c.hbm_reserve_bytes) == (0, 1 << 30)
 
 
 def test_params_default_and_validate(lib):
