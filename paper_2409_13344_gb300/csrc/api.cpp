@@ -247,6 +247,8 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.st = ws.st;
   pa.partial = ws.partial_p;
   pa.gtick = ws.gtick;
+  pa.fwd_partial = ws.partial_r;
+  pa.n_fwd_partial = appga::forward_blocks(M->m, M->n);
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
 

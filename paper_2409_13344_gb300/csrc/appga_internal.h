@@ -96,6 +96,10 @@ struct PixArgs {
   SolverState* st;
   float2* partial;
   unsigned int* gtick;
+  // block partials of Phi(f^k) left by the forward phase of the same step
+  // (ip.track): reduced here, where the stopping test runs
+  const float2* fwd_partial;
+  int32_t n_fwd_partial;
   IterParams ip;
   int32_t use_bf16;
   int32_t pad;
@@ -103,6 +107,7 @@ struct PixArgs {
 
 // ---- launchers (kernels.cu) ----
 int stencil_tiles(int n);
+int forward_blocks(int m, int n);  // grid of the solver-loop forward phase
 int max_partials(int m, int n);
 int max_group_tickets(int m, int n);
 

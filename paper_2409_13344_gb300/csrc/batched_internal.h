@@ -47,6 +47,8 @@ struct BFwdArgs {
   int32_t track;
   int32_t use_bf16;
   int32_t n_spmv_blocks;  // set by the launcher
+  int32_t spmv_per_sm;    // SpMV blocks per SM (0: default); tuned by the autotuner
+  int32_t stencil_per_sm; // stencil blocks per SM (0: default)
   float* f[3];
   float* y[2];
   float* w;
@@ -63,7 +65,7 @@ struct BPixArgs {
   DevCSR At;
   int32_t n, Kp;
   int32_t use_bf16;
-  int32_t pad;
+  int32_t blocks_per_sm;  // 0: default; tuned by the autotuner
   float* f[3];
   const float* w;
   const float* gR;

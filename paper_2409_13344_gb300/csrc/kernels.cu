@@ -42,20 +42,56 @@ namespace appga {
 namespace {
 
 constexpr int THREADS = 256;  // setup / reduction kernels
-constexpr int ROWS_PER_WARP = 8;  // projector rows per warp
-constexpr int PW_WARPS = 2;       // warps per projector block
-constexpr int PW_THREADS = PW_WARPS * 32;
-constexpr int PW_ROWS = PW_WARPS * ROWS_PER_WARP;  // rows per projector block
-#ifndef APPGA_PF
-#define APPGA_PF 2
+
+// Projector launch shapes: warps per block (W), consecutive CSR rows per warp
+// (R) and 128-entry chunks of the nnz stream in flight per warp (PF), for the
+// forward projection (whose grid also runs the stencil tiles) and for the
+// transposed one.  Chosen by timing on GB300 (256^2 workload).
+template <int W_, int R_, int PF_>
+struct Shape {
+  static constexpr int W = W_, R = R_, PF = PF_;
+  static constexpr int THREADS = W_ * 32;
+  static constexpr int ROWS = W_ * R_;  // rows per block
+};
+#ifndef APPGA_FW_W
+#define APPGA_FW_W 4
 #endif
-constexpr int PF = APPGA_PF;  // chunks of the nnz stream in flight per warp
+#ifndef APPGA_FW_RPW
+#define APPGA_FW_RPW 6
+#endif
+#ifndef APPGA_FW_PF
+#define APPGA_FW_PF 3
+#endif
+#ifndef APPGA_PX_W
+#define APPGA_PX_W 4
+#endif
+#ifndef APPGA_PX_RPW
+#define APPGA_PX_RPW 8
+#endif
+#ifndef APPGA_PX_PF
+#define APPGA_PX_PF 3
+#endif
+using FW = Shape<APPGA_FW_W, APPGA_FW_RPW, APPGA_FW_PF>;
+using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
+// minimum resident blocks per SM asked of the compiler (register budget)
+#ifndef APPGA_FW_MINB
+#define APPGA_FW_MINB 1
+#endif
+#ifndef APPGA_PX_MINB
+#define APPGA_PX_MINB 1
+#endif
+#ifndef APPGA_GPIPE
+#define APPGA_GPIPE 1
+#endif
+#ifndef APPGA_SFIRST
+#define APPGA_SFIRST 0
+#endif
 constexpr int SLOT_W = 33;    // slot row stride: per-row sums read without bank conflicts
 
 // Stencil tiles: ST_R x ST_C pixels, one pixel per thread of a projector block
-constexpr int ST_R = 2;
+constexpr int ST_R = FW::W;
 constexpr int ST_C = 32;
-static_assert(ST_R * ST_C == PW_THREADS, "stencil tile = one pixel per thread");
+static_assert(ST_R * ST_C == FW::THREADS, "stencil tile = one pixel per thread");
 constexpr int TW = ST_C + 4;  // f tile width (halo 2)
 constexpr int VW = ST_C + 2;  // v tile width (halo 1)
 
@@ -81,10 +117,14 @@ __device__ __forceinline__ int load_bounds(const DevCSR& M, int row0, int nrows,
   return __shfl_sync(0xffffffffu, b, nrows);
 }
 
+__device__ __forceinline__ float4 gather4(const float* __restrict__ x, int4 c) {
+  return make_float4(__ldg(x + c.x), __ldg(x + c.y), __ldg(x + c.z), __ldg(x + c.w));
+}
+
 // Rows [row0, row0 + nrows) of M times x; returns the sum of row `lane` in
 // lanes 0..nrows-1: an accumulator pair if DF, else an FP32 value in out_hi.
 // slot_hi / slot_lo: this warp's R*SLOT_W floats each of shared memory.
-template <bool BF16, bool DF, int R>
+template <bool BF16, bool DF, int R, int PF>
 __device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nrows,
                                               const float* __restrict__ x, int lane,
                                               float* slot_hi, float* slot_lo, float& out_hi,
@@ -116,6 +156,12 @@ __device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nro
   }
   float hi = 0.f, lo = 0.f;
   int cur = -1;
+#if APPGA_GPIPE
+  // x values of the next chunk are gathered one chunk ahead, so the gather
+  // latency overlaps the arithmetic of the current chunk
+  float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (P0 + lane * 4 < P1) xg = gather4(x, c[0]);
+#endif
   for (int t0 = 0; t0 < nchunks; t0 += PF) {
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
@@ -129,6 +175,11 @@ __device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nro
           c[u] = ld_stream_i4(M.col + pn, pol);
           v[u] = ld_vals<BF16>(M, pn, pol);
         }
+#if APPGA_GPIPE
+        const float4 xx = xg;
+        // chunk t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
+        if (p + 128 < P1) xg = gather4(x, c[(u + 1) % PF]);
+#endif
         if (p < P1) {
           const int q = row_of<R>(p, bnd, nrows);
           if (q != cur) {
@@ -140,8 +191,13 @@ __device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nro
             hi = 0.f;
             lo = 0.f;
           }
+#if APPGA_GPIPE
+          const float x0 = xx.x, x1 = xx.y, x2 = xx.z, x3 = xx.w;
+          (void)cc;
+#else
           const float x0 = __ldg(x + cc.x), x1 = __ldg(x + cc.y);
           const float x2 = __ldg(x + cc.z), x3 = __ldg(x + cc.w);
+#endif
           if (DF) {
             acc_fma(hi, lo, vv.x, x0);
             acc_fma(hi, lo, vv.y, x1);
@@ -263,8 +319,9 @@ __host__ __device__ __forceinline__ int st_tiles_x(int n) { return (n + ST_C - 1
 __host__ __device__ __forceinline__ int st_tiles(int n) {
   return st_tiles_x(n) * ((n + ST_R - 1) / ST_R);
 }
+template <class SH>
 __host__ __device__ __forceinline__ int proj_blocks(int rows) {
-  return (rows + PW_ROWS - 1) / PW_ROWS;
+  return (rows + SH::ROWS - 1) / SH::ROWS;
 }
 
 // Momentum scalar for index k (Eq. GNtheta) -- FP64 on the device.
@@ -280,14 +337,14 @@ __device__ void set_theta(SolverState* st, double theta) {
 
 // ------------------------------------------------------------ k_forward
 
-// Blocks [0, proj_blocks(m)) project rows; in the solver loop the blocks
+// Blocks [0, proj_blocks<FW>(m)) project rows; in the solver loop the blocks
 // after them run the stencil tiles.
 template <bool BF16>
-__global__ void __launch_bounds__(PW_THREADS) k_forward(FwdArgs a) {
+__global__ void __launch_bounds__(FW::THREADS, APPGA_FW_MINB) k_forward(FwdArgs a) {
   __shared__ union {
     struct {
-      float hi[PW_WARPS][ROWS_PER_WARP * SLOT_W];
-      float lo[PW_WARPS][ROWS_PER_WARP * SLOT_W];
+      float hi[FW::W][FW::R * SLOT_W];
+      float lo[FW::W][FW::R * SLOT_W];
     } slot;
     StencilSmem st;
   } sm;
@@ -295,16 +352,24 @@ __global__ void __launch_bounds__(PW_THREADS) k_forward(FwdArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (a.loop && st->done) return;  // uniform over the grid
   const int kk = a.loop ? st->k : 0;
-  const int nproj = proj_blocks(a.A.rows);
+  const int nproj = proj_blocks<FW>(a.A.rows);
   float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
   int hits = 0, bad = 0;
-  if ((int)blockIdx.x < nproj) {
+#if APPGA_SFIRST
+  // stencil tiles take the first blocks, so the projector blocks end the grid
+  const int pb = (int)blockIdx.x - ((int)gridDim.x - nproj);
+  const int sb = blockIdx.x;
+#else
+  const int pb = blockIdx.x;
+  const int sb = (int)blockIdx.x - nproj;
+#endif
+  if (pb >= 0 && pb < nproj) {
     const float* f = a.loop ? a.f[kk % 3] : a.f[0];
     const int m = a.A.rows;
-    const int row0 = blockIdx.x * PW_ROWS + warp * ROWS_PER_WARP;
-    const int nrows = max(0, min(ROWS_PER_WARP, m - row0));
+    const int row0 = pb * FW::ROWS + warp * FW::R;
+    const int nrows = max(0, min(FW::R, m - row0));
     float hi, lo;
-    warp_rows_dot<BF16, true, ROWS_PER_WARP>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
+    warp_rows_dot<BF16, true, FW::R, FW::PF>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
                                              sm.slot.lo[warp], hi, lo);
     if (lane < nrows) {
       const int row = row0 + lane;
@@ -346,7 +411,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_forward(FwdArgs a) {
     }
   } else {
     // SHOITV gradient at f~^kk and the regulariser of Phi(f^kk)
-    const int b = blockIdx.x - nproj;
+    const int b = sb;
     const int ntx = st_tiles_x(a.n);
     const float reg = stencil_tile(sm.st, a.f[kk % 3], a.f[(kk + 2) % 3], st->theta_hi,
                                    (b / ntx) * ST_R, (b % ntx) * ST_C, a.n, a.ip.lambda1,
@@ -357,22 +422,16 @@ __global__ void __launch_bounds__(PW_THREADS) k_forward(FwdArgs a) {
   warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
   if (!a.want_data) return;
   const df bsum = block_sum_acc(acc_hi, acc_lo);
+  if (a.loop) {
+    // the pixel phase of this step reduces the block partials and runs the
+    // stopping test, so no grid-wide ordering is needed here
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = make_float2(bsum.hi, bsum.lo);
+    return;
+  }
   double tot = 0.0;
   if (grid_reduce(a.partial, a.gtick, &st->ticket_r, bsum, &tot)) {
     if (threadIdx.x == 0) {
-      if (!a.loop) {
-        if (a.data_out) *a.data_out = tot;
-      } else {
-        // Phi(f^kk) and the stopping test against Phi(f^{kk-1})
-        const double prev = st->phi_cur;
-        st->phi_prev = prev;
-        st->phi_cur = tot;
-        if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(tot - prev) <= a.ip.rel_tol * fabs(prev)) {
-          st->done = 1;
-          st->result_k = kk;
-          st->stopped_early = 1;
-        }
-      }
+      if (a.data_out) *a.data_out = tot;
     }
   }
 }
@@ -380,17 +439,17 @@ __global__ void __launch_bounds__(PW_THREADS) k_forward(FwdArgs a) {
 // -------------------------------------------------------------- k_pixel
 
 template <bool BF16>
-__global__ void __launch_bounds__(PW_THREADS) k_pixel(PixArgs a) {
-  __shared__ float slot[PW_WARPS][ROWS_PER_WARP * SLOT_W];
+__global__ void __launch_bounds__(PX::THREADS, APPGA_PX_MINB) k_pixel(PixArgs a) {
+  __shared__ float slot[PX::W][PX::R * SLOT_W];
   SolverState* st = a.st;
   if (st->done) return;  // uniform over the grid
   const int kk = st->k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = a.At.rows;
-  const int j0 = blockIdx.x * PW_ROWS + warp * ROWS_PER_WARP;
-  const int np = max(0, min(ROWS_PER_WARP, d - j0));
+  const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
+  const int np = max(0, min(PX::R, d - j0));
   float bp, unused;
-  warp_rows_dot<BF16, false, ROWS_PER_WARP>(a.At, j0, np, a.w, lane, slot[warp], nullptr, bp,
+  warp_rows_dot<BF16, false, PX::R, PX::PF>(a.At, j0, np, a.w, lane, slot[warp], nullptr, bp,
                                             unused);
   int bad = 0;
   if (lane < np) {
@@ -413,10 +472,30 @@ __global__ void __launch_bounds__(PW_THREADS) k_pixel(PixArgs a) {
     a.f[(kk + 1) % 3][j] = fmaxf(xv, 0.f);
   }
   warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
-  // Finalise the iteration in the last block: the next index and momentum.
-  double unused_total;
-  if (grid_reduce(a.partial, a.gtick, &st->ticket_p, {0.f, 0.f}, &unused_total)) {
+  // This block's share of Phi(f^kk): the forward blocks' partials b, b + G, ...
+  float ph = 0.f, pl = 0.f;
+  if (a.ip.track && threadIdx.x == 0)
+    for (int i = blockIdx.x; i < a.n_fwd_partial; i += gridDim.x) {
+      const float2 v = a.fwd_partial[i];
+      acc_add(ph, pl, v.x, v.y);
+    }
+  // Finalise the iteration in the last block: Phi(f^kk) and the stopping
+  // test, then the next index and momentum.
+  double phi = 0.0;
+  if (grid_reduce(a.partial, a.gtick, &st->ticket_p, {ph, pl}, &phi)) {
     if (threadIdx.x == 0) {
+      if (a.ip.track) {
+        const double prev = st->phi_cur;
+        st->phi_prev = prev;
+        st->phi_cur = phi;
+        if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(phi - prev) <= a.ip.rel_tol * fabs(prev)) {
+          // f^kk is the result; the f^{kk+1} written above is not used
+          st->done = 1;
+          st->result_k = kk;
+          st->stopped_early = 1;
+          return;
+        }
+      }
       if (kk >= st->k_last) {
         st->done = 1;
         st->result_k = kk + 1;
@@ -459,21 +538,21 @@ __global__ void k_init_momentum(SolverState* st, int k0, int momentum, double a,
 
 // Standalone back-projection (step a3): out = A^T w.
 template <bool BF16>
-__global__ void __launch_bounds__(PW_THREADS) k_backproject(DevCSR At, const float* __restrict__ w,
+__global__ void __launch_bounds__(PX::THREADS) k_backproject(DevCSR At, const float* __restrict__ w,
                                                             float* __restrict__ out) {
-  __shared__ float slot[PW_WARPS][ROWS_PER_WARP * SLOT_W];
+  __shared__ float slot[PX::W][PX::R * SLOT_W];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int row0 = blockIdx.x * PW_ROWS + warp * ROWS_PER_WARP;
-  const int nrows = max(0, min(ROWS_PER_WARP, At.rows - row0));
+  const int row0 = blockIdx.x * PX::ROWS + warp * PX::R;
+  const int nrows = max(0, min(PX::R, At.rows - row0));
   float s, unused;
-  warp_rows_dot<BF16, false, ROWS_PER_WARP>(At, row0, nrows, w, lane, slot[warp], nullptr, s,
+  warp_rows_dot<BF16, false, PX::R, PX::PF>(At, row0, nrows, w, lane, slot[warp], nullptr, s,
                                             unused);
   if (lane < nrows) out[row0 + lane] = s;
 }
 
 // Stencil kernel: gR = B^T grad phi~(B f~) with f~ = f_cur + theta (f_cur - f_prev)
 // (theta = 0, f_prev = f_cur: the plain SHOITV gradient, step a4).
-__global__ void __launch_bounds__(PW_THREADS) k_stencil(int n, const float* __restrict__ f_cur,
+__global__ void __launch_bounds__(FW::THREADS) k_stencil(int n, const float* __restrict__ f_cur,
                                                         const float* __restrict__ f_prev,
                                                         float theta, float lam1, float lam2,
                                                         float eps, float* __restrict__ out) {
@@ -484,7 +563,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_stencil(int n, const float* __re
 }
 
 // Regulariser term phi~(B f) (objective, step a6).
-__global__ void __launch_bounds__(PW_THREADS) k_reg_term(int n, const float* __restrict__ f,
+__global__ void __launch_bounds__(FW::THREADS) k_reg_term(int n, const float* __restrict__ f,
                                                          float lam1, float lam2, float eps,
                                                          float2* partial, unsigned int* gtick,
                                                          SolverState* st, double* out) {
@@ -546,10 +625,11 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
 // ------------------------------------------------------------- launchers
 
 int stencil_tiles(int n) { return st_tiles(n); }
+int forward_blocks(int m, int n) { return proj_blocks<FW>(m) + st_tiles(n); }
 
 int max_partials(int m, int n) {
-  const int a = proj_blocks(m) + st_tiles(n);
-  const int b = proj_blocks(n * n);
+  const int a = proj_blocks<FW>(m) + st_tiles(n);
+  const int b = proj_blocks<PX>(n * n);
   const int nb = a > b ? a : b;
   return nb + nb / RED_GROUP + 1024;
 }
@@ -558,43 +638,43 @@ int max_group_tickets(int m, int n) { return max_partials(m, n) / RED_GROUP + 1;
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
-  const int grid = proj_blocks(a.A.rows) + (a.loop ? st_tiles(a.n) : 0);
+  const int grid = proj_blocks<FW>(a.A.rows) + (a.loop ? st_tiles(a.n) : 0);
   if (a.use_bf16)
-    k_forward<true><<<grid, PW_THREADS, 0, s>>>(a);
+    k_forward<true><<<grid, FW::THREADS, 0, s>>>(a);
   else
-    k_forward<false><<<grid, PW_THREADS, 0, s>>>(a);
+    k_forward<false><<<grid, FW::THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
-  const int grid = proj_blocks(a.At.rows);
+  const int grid = proj_blocks<PX>(a.At.rows);
   if (a.use_bf16)
-    k_pixel<true><<<grid, PW_THREADS, 0, s>>>(a);
+    k_pixel<true><<<grid, PX::THREADS, 0, s>>>(a);
   else
-    k_pixel<false><<<grid, PW_THREADS, 0, s>>>(a);
+    k_pixel<false><<<grid, PX::THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
                                cudaStream_t s) {
-  const int grid = proj_blocks(At.rows);
+  const int grid = proj_blocks<PX>(At.rows);
   if (use_bf16)
-    k_backproject<true><<<grid, PW_THREADS, 0, s>>>(At, w, out);
+    k_backproject<true><<<grid, PX::THREADS, 0, s>>>(At, w, out);
   else
-    k_backproject<false><<<grid, PW_THREADS, 0, s>>>(At, w, out);
+    k_backproject<false><<<grid, PX::THREADS, 0, s>>>(At, w, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stencil(int n, const float* f_cur, const float* f_prev, float theta,
                            float lam1, float lam2, float eps, float* out, cudaStream_t s) {
-  k_stencil<<<st_tiles(n), PW_THREADS, 0, s>>>(n, f_cur, f_prev, theta, lam1, lam2, eps, out);
+  k_stencil<<<st_tiles(n), FW::THREADS, 0, s>>>(n, f_cur, f_prev, theta, lam1, lam2, eps, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float eps,
                             float2* partial, unsigned int* gtick, SolverState* st, double* out,
                             cudaStream_t s) {
-  k_reg_term<<<st_tiles(n), PW_THREADS, 0, s>>>(n, f, lam1, lam2, eps, partial, gtick, st, out);
+  k_reg_term<<<st_tiles(n), FW::THREADS, 0, s>>>(n, f, lam1, lam2, eps, partial, gtick, st, out);
   return cudaGetLastError();
 }
 

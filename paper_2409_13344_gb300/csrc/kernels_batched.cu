@@ -30,6 +30,12 @@ namespace {
 constexpr int B_THREADS = 256;
 constexpr int B_WARPS = B_THREADS / 32;
 constexpr int MAXK = 128;                    // largest padded batch (V = 4)
+constexpr int kSpmvPerSm = 8;                // default persistent SpMV blocks per SM
+constexpr int kStencilPerSm = 4;             // default stencil blocks per SM
+constexpr int kMaxPerSm = 16;                // upper bound of either tuned value
+__host__ __forceinline__ int clamp_per_sm(int v, int dflt) {
+  return v <= 0 ? dflt : (v > kMaxPerSm ? kMaxPerSm : v);
+}
 constexpr int BST_R = 2, BST_C = 32, BST_S = 8;  // stencil item: 2 x 32 pixels x 8 slots
 constexpr int BTW = BST_C + 4, BVW = BST_C + 2;
 static_assert(BST_C * BST_S == B_THREADS, "stencil: one thread per (column, slot)");
@@ -61,12 +67,86 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
   }
 }
 
+#ifndef APPGA_BDOT
+#define APPGA_BDOT 2
+#endif
+#ifndef APPGA_BCONTIG
+#define APPGA_BCONTIG 1
+#endif
+
 // One CSR row of M times the Kp-wide columns of X ([cols][Kp]): lane holds
-// the V sums of slots lane*V .. lane*V + V - 1.
+// the V sums of slots lane*V .. lane*V + V - 1.  Each lane loads one of 32
+// (column, value) pairs; the warp stages them in shared memory (the column
+// as an element offset col * Kp) and every lane reads them back four at a
+// time with broadcast loads, gathering 8 image rows per step.  The next 32
+// pairs are loaded while the current ones are consumed.  Products are
+// accumulated in the row's entry order.
 template <int V, bool BF16>
 __device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* __restrict__ X,
                                          int Kp, int lane, bool lane_on, uint64_t pol,
-                                         float (&acc)[V]) {
+                                         int* s_off, float* s_val, float (&acc)[V]) {
+#if APPGA_BDOT == 2
+#pragma unroll
+  for (int t = 0; t < V; ++t) acc[t] = 0.f;
+  const int s = __ldg(M.row_ptr + row), e = __ldg(M.row_ptr + row + 1);
+  const float* xl = X + lane * V;
+  int c = 0;
+  float v = 0.f;
+  if (s + lane < e) {
+    c = ld_stream_i1(M.col + s + lane, pol);
+    v = BF16 ? ld_stream_bf16_1(M.val_bf16 + s + lane, pol) : ld_stream_f1(M.val + s + lane, pol);
+  }
+  for (int p0 = s; p0 < e; p0 += 32) {
+    const int cnt = min(32, e - p0);  // a multiple of 4 (rows are padded)
+    __syncwarp();
+    s_off[lane] = c * Kp;
+    s_val[lane] = v;
+    __syncwarp();
+    const int pn = p0 + 32 + lane;
+    if (pn < e) {
+      c = ld_stream_i1(M.col + pn, pol);
+      v = BF16 ? ld_stream_bf16_1(M.val_bf16 + pn, pol) : ld_stream_f1(M.val + pn, pol);
+    }
+    if (!lane_on) continue;
+    int q = 0;
+    for (; q + 8 <= cnt; q += 8) {
+      const int4 o0 = *reinterpret_cast<const int4*>(s_off + q);
+      const int4 o1 = *reinterpret_cast<const int4*>(s_off + q + 4);
+      const float4 w0 = *reinterpret_cast<const float4*>(s_val + q);
+      const float4 w1 = *reinterpret_cast<const float4*>(s_val + q + 4);
+      float x[8][V];
+      vload<V>(xl + o0.x, x[0]);
+      vload<V>(xl + o0.y, x[1]);
+      vload<V>(xl + o0.z, x[2]);
+      vload<V>(xl + o0.w, x[3]);
+      vload<V>(xl + o1.x, x[4]);
+      vload<V>(xl + o1.y, x[5]);
+      vload<V>(xl + o1.z, x[6]);
+      vload<V>(xl + o1.w, x[7]);
+      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc[t] = fmaf(w[u], x[u][t], acc[t]);
+    }
+    if (q < cnt) {
+      const int4 o0 = *reinterpret_cast<const int4*>(s_off + q);
+      const float4 w0 = *reinterpret_cast<const float4*>(s_val + q);
+      float x[4][V];
+      vload<V>(xl + o0.x, x[0]);
+      vload<V>(xl + o0.y, x[1]);
+      vload<V>(xl + o0.z, x[2]);
+      vload<V>(xl + o0.w, x[3]);
+      const float w[4] = {w0.x, w0.y, w0.z, w0.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc[t] = fmaf(w[u], x[u][t], acc[t]);
+    }
+  }
+#else
+  (void)s_off;
+  (void)s_val;
 #pragma unroll
   for (int t = 0; t < V; ++t) acc[t] = 0.f;
   const int s = __ldg(M.row_ptr + row), e = __ldg(M.row_ptr + row + 1);
@@ -104,6 +184,7 @@ __device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* 
         for (int t = 0; t < V; ++t) acc[t] = fmaf(vq[u], x[u][t], acc[t]);
     }
   }
+#endif
 }
 
 // ------------------------------------------------- per-slot grid reduction
@@ -308,6 +389,8 @@ __device__ void bset_remaining(const SlotState* slots, int Kp, BatchState* bs) {
 
 template <int V, bool BF16>
 __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
+  __shared__ __align__(16) int s_off[B_WARPS][32];
+  __shared__ __align__(16) float s_val[B_WARPS][32];
   __shared__ union {
     struct {
       float dhi[B_WARPS][MAXK];
@@ -350,10 +433,18 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   }
   if ((int)blockIdx.x < a.n_spmv_blocks) {
     const uint64_t pol = evict_first_policy();
+#if APPGA_BCONTIG
+    // each block owns a contiguous run of rows (neighbouring rays share
+    // pixels, so the gathered image rows are reused from L1)
+    const int per = (a.A.rows + a.n_spmv_blocks - 1) / a.n_spmv_blocks;
+    const int r0 = blockIdx.x * per, r1 = min(a.A.rows, r0 + per);
+    for (int row = r0 + warp; row < r1; row += B_WARPS) {
+#else
     const int stride = a.n_spmv_blocks * B_WARPS;
     for (int row = blockIdx.x * B_WARPS + warp; row < a.A.rows; row += stride) {
+#endif
       float acc[V];
-      brow_dot<V, BF16>(a.A, row, f, Kp, lane, lane_on, pol, acc);
+      brow_dot<V, BF16>(a.A, row, f, Kp, lane, lane_on, pol, s_off[warp], s_val[warp], acc);
       if (!lane_on) continue;
       const size_t o = (size_t)row * Kp + lane * V;
       float yp[V], gg[V], gm[V], yo[V], wo[V];
@@ -500,6 +591,8 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
 
 template <int V, bool BF16>
 __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
+  __shared__ __align__(16) int s_off[B_WARPS][32];
+  __shared__ __align__(16) float s_val[B_WARPS][32];
   BatchState* bs = a.bst;
   if (bs->remaining == 0) return;  // uniform over the grid
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -524,11 +617,19 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
 #pragma unroll
   for (int t = 0; t < V; ++t) lane_live = lane_live || live[t];
   const uint64_t pol = evict_first_policy();
-  const int stride = gridDim.x * B_WARPS;
   int bad = 0;
+#if APPGA_BCONTIG
+  // each block owns a contiguous run of pixels (neighbouring pixels lie on
+  // the same rays, so the gathered weight rows are reused from L1)
+  const int per = (a.At.rows + gridDim.x - 1) / gridDim.x;
+  const int j0 = blockIdx.x * per, j1 = min(a.At.rows, j0 + per);
+  for (int j = j0 + warp; j < j1; j += B_WARPS) {
+#else
+  const int stride = gridDim.x * B_WARPS;
   for (int j = blockIdx.x * B_WARPS + warp; j < a.At.rows; j += stride) {
+#endif
     float bp[V];
-    brow_dot<V, BF16>(a.At, j, a.w, Kp, lane, lane_live, pol, bp);
+    brow_dot<V, BF16>(a.At, j, a.w, Kp, lane, lane_live, pol, s_off[warp], s_val[warp], bp);
     const size_t o = (size_t)j * Kp + lane * V;
     float vk[V], vm[V], gr[V], out[V];
     vload<V>(fk + o, vk);
@@ -725,14 +826,15 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   const int sms = sm_count();
   const int rows_per_block = B_WARPS;
   int nsp = (a.A.rows + rows_per_block - 1) / rows_per_block;
-  const int cap = sms * 8;
+  const int cap = sms * clamp_per_sm(a.spmv_per_sm, kSpmvPerSm);
   if (nsp > cap) nsp = cap;
   a.n_spmv_blocks = nsp;
   int nst = 0;
   if (a.mode != 1) {
-    // equal tile counts per stencil block, at most 4 blocks per SM
+    // equal tile counts per stencil block
     const int tiles = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R);
-    const int per = (tiles + sms * 4 - 1) / (sms * 4);
+    const int scap = sms * clamp_per_sm(a.stencil_per_sm, kStencilPerSm);
+    const int per = (tiles + scap - 1) / scap;
     nst = (tiles + per - 1) / per;
   }
   const int grid = nsp + nst;
@@ -746,7 +848,8 @@ template <int V>
 cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
   const int sms = sm_count();
   int nb = (a.At.rows + B_WARPS - 1) / B_WARPS;
-  if (nb > sms * 8) nb = sms * 8;
+  const int cap = sms * clamp_per_sm(a.blocks_per_sm, kSpmvPerSm);
+  if (nb > cap) nb = cap;
   if (a.use_bf16)
     k_bpixel<V, true><<<nb, B_THREADS, 0, s>>>(a);
   else
@@ -756,7 +859,9 @@ cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-int batch_max_blocks() { return sm_count() * 12 + 64; }
+// Largest grid of the batched kernels: at most kMaxPerSm SpMV and kMaxPerSm
+// stencil blocks per SM (the launchers clamp the tuned values).
+int batch_max_blocks() { return sm_count() * 2 * kMaxPerSm + 64; }
 
 cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s) {
   cudaError_t e = ensure_tables();
