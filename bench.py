@@ -199,7 +199,8 @@ def bench_batched(AP, ctx, geom, A, dev, single_rate):
                        "call, one call = one SpMM solver run under captured CUDA graphs",
            "K": BATCH_K}
     nb = batched_bytes(geom.m, geom.d, int(mat.info().nnz), BATCH_K)
-    for name, prec in (("fp32", 0), ("bf16", 1)):
+
+    def measure(prec):
         def call(iters):
             p = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA,
                                   max_iters=iters, a_precision=prec)
@@ -218,11 +219,25 @@ def bench_batched(AP, ctx, geom, A, dev, single_rate):
             ms[iters] = e0.elapsed_time(e1)
         per_iter = (ms[8 + BATCH_ITERS] - ms[8]) / BATCH_ITERS
         rate = BATCH_K / (per_iter * 1e-3)
-        out[name] = {"slices_iters_per_s": rate, "us_per_batched_iter": 1e3 * per_iter,
-                     "us_per_slice_iter": 1e3 * per_iter / BATCH_K,
-                     "call_slices_iters_per_s": BATCH_K * (8 + BATCH_ITERS) / (ms[8 + BATCH_ITERS] * 1e-3),
-                     "algorithmic_gbs": nb / (per_iter * 1e-3) / 1e9,
-                     "vs_single_slice": rate / single_rate}
+        return {"slices_iters_per_s": rate, "us_per_batched_iter": 1e3 * per_iter,
+                "us_per_slice_iter": 1e3 * per_iter / BATCH_K,
+                "call_slices_iters_per_s": BATCH_K * (8 + BATCH_ITERS) / (ms[8 + BATCH_ITERS] * 1e-3),
+                "algorithmic_gbs": nb / (per_iter * 1e-3) / 1e9,
+                "vs_single_slice": rate / single_rate}
+
+    for name, prec in (("fp32", 0), ("bf16", 1)):
+        out[name] = measure(prec)
+        # the library's autotuner picks the launch schedule for this width and
+        # precision on these slices; the tuned schedule is then measured the same way
+        t = AP.appga_autotune_batched(ctx.handle, mat.handle, BATCH_K, g, gam,
+                                      AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS,
+                                                        omega=OMEGA, a_precision=prec))
+        tuned = measure(prec)
+        tuned["schedule"] = {"spmv_per_sm": t.spmv_per_sm, "pixel_per_sm": t.pixel_per_sm,
+                             "stencil_per_sm": t.stencil_per_sm, "chunk": t.chunk,
+                             "trial_us_per_slice_iter": t.us_per_slice_iter,
+                             "trial_us_default": t.us_per_slice_iter_default}
+        out[name + "_autotuned"] = tuned
     out["algorithmic_bytes_per_iter"] = nb
     mat.close()
     return out

@@ -251,6 +251,45 @@ appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, 
                                        const appga_params* params, float* f_out,
                                        appga_stats* stats_host, void* stream);
 
+/* appga_autotune_batched: picks the launch schedule of the batched kernels
+ * for this matrix, batch width and precision by timing the solver itself on
+ * the caller's K slices (g, gamma: float[K][m] device; params as for
+ * appga_reconstruct_batched; a_precision selects FP32 or BF16 values).  The
+ * paper has no counterpart; the schedule changes only speed, never results.
+ * Each trial runs 4 + 16 APPGA maps of every slice (after 4 warm-up maps)
+ * and is timed with CUDA events on the library stream.  Tunables, searched
+ * one after another from the kernels' defaults: the sub-batch width (run K
+ * slices as several batches of 32 or 64), SpMV blocks per SM of the forward
+ * phase, blocks per SM of the back-projection, stencil blocks per SM.  The
+ * best schedule is kept in the matrix handle and used by later
+ * appga_reconstruct_batched calls (and server pools) with the same padded
+ * width (32, 64 or 128) and precision.  out_host (may be NULL) receives the
+ * choice and the measured times.  Synchronises; allocates a K x d scratch
+ * image block for the trials.  A schedule never changes the image of a run
+ * with a fixed number of maps (every slot's arithmetic is the same); the
+ * FP64 objective is summed in a schedule-dependent grouping, so it and a
+ * relative-objective stop may differ in the last bits. */
+typedef struct {
+  int32_t K;
+  int32_t a_precision;
+  int32_t spmv_per_sm;    /* 0 = kernel default */
+  int32_t stencil_per_sm; /* 0 = kernel default */
+  int32_t pixel_per_sm;   /* 0 = kernel default */
+  int32_t chunk;          /* slices per sub-batch; 0 = the whole batch */
+  double us_per_slice_iter;         /* chosen schedule, microseconds per slice-iteration */
+  double us_per_slice_iter_default; /* the default schedule */
+} appga_batch_tuning;
+appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matrix* mat, int32_t K,
+                                    const float* g, const float* gamma,
+                                    const appga_params* params, appga_batch_tuning* out_host);
+/* Reads / sets the schedule kept for (tuning->K's padded width,
+ * tuning->a_precision), e.g. to reuse a tuning saved by an earlier process;
+ * only K, a_precision and the four schedule fields are used (values per SM
+ * in [0, 16], 0 = default; chunk 0, 32 or 64).  get fills the schedule
+ * fields (zeros if none is kept).  EINVAL for values out of range. */
+appga_status appga_batch_schedule_get(const appga_matrix* mat, appga_batch_tuning* tuning_host);
+appga_status appga_batch_schedule_set(appga_matrix* mat, const appga_batch_tuning* tuning_host);
+
 /* appga_objective_noalloc: appga_objective without any memory allocation.
  * The paper has no counterpart; this is a library-side convenience.
  * Some callers cannot let a library allocate device memory after start-up:

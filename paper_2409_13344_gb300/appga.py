@@ -64,6 +64,15 @@ class appga_matrix_info(ctypes.Structure):
     ]
 
 
+class appga_batch_tuning(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_int32), ("a_precision", ctypes.c_int32), ("spmv_per_sm", ctypes.c_int32),
+        ("stencil_per_sm", ctypes.c_int32), ("pixel_per_sm", ctypes.c_int32),
+        ("chunk", ctypes.c_int32), ("us_per_slice_iter", ctypes.c_double),
+        ("us_per_slice_iter_default", ctypes.c_double),
+    ]
+
+
 class appga_server_config(ctypes.Structure):
     _fields_ = [
         ("slots_per_pool", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
@@ -137,6 +146,10 @@ SIGNATURES = {
                                                  ctypes.POINTER(appga_stats), _P]),
     "appga_kernel_times": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(appga_params), _I32,
                                           ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "appga_autotune_batched": (ctypes.c_int, [_P, _P, _I32, _P, _P, ctypes.POINTER(appga_params),
+                                              ctypes.POINTER(appga_batch_tuning)]),
+    "appga_batch_schedule_get": (ctypes.c_int, [_P, ctypes.POINTER(appga_batch_tuning)]),
+    "appga_batch_schedule_set": (ctypes.c_int, [_P, ctypes.POINTER(appga_batch_tuning)]),
     # appga_server.h
     "appga_server_config_default": (None, [ctypes.POINTER(appga_server_config)]),
     "appga_server_create": (ctypes.c_int, [_P, ctypes.POINTER(appga_server_config),
@@ -334,6 +347,28 @@ def appga_reconstruct_batched(ctx, mat, K, g, gamma, f_init, params, f_out, stre
                                                     st, _stream(stream)),
            "appga_reconstruct_batched")
     return list(st)
+
+
+def appga_autotune_batched(ctx, mat, K, g, gamma, params) -> appga_batch_tuning:
+    """Times launch schedules of the batched kernels on these K slices and
+    keeps the best in the matrix handle (see appga.h)."""
+    t = appga_batch_tuning()
+    _check(load_library().appga_autotune_batched(ctx, mat, K, _ptr(g), _ptr(gamma),
+                                                 ctypes.byref(params), ctypes.byref(t)),
+           "appga_autotune_batched")
+    return t
+
+
+def appga_batch_schedule_get(mat, K: int, a_precision: int = 0) -> appga_batch_tuning:
+    t = appga_batch_tuning(K=K, a_precision=a_precision)
+    _check(load_library().appga_batch_schedule_get(mat, ctypes.byref(t)),
+           "appga_batch_schedule_get")
+    return t
+
+
+def appga_batch_schedule_set(mat, tuning: appga_batch_tuning):
+    _check(load_library().appga_batch_schedule_set(mat, ctypes.byref(tuning)),
+           "appga_batch_schedule_set")
 
 
 def appga_objective_noalloc(ctx, mat, f, g, gamma, params, phi_out, stream=None):

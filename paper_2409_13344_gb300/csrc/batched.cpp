@@ -2,6 +2,7 @@
 // slot-minor SpMM kernels under captured CUDA graphs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -81,9 +82,17 @@ cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp) {
   return cudaSuccess;
 }
 
+BatchSchedule tuned_schedule(const appga_matrix* M, int Kp, bool bf16) {
+  auto it = M->tuned.find(Kp * 2 + (bf16 ? 1 : 0));
+  return it == M->tuned.end() ? BatchSchedule() : it->second;
+}
+
 void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda, int n,
-                     BatchWorkspace& b, bool bf16, bool track, BFwdArgs* fa, BPixArgs* pa) {
+                     BatchWorkspace& b, bool bf16, bool track, const BatchSchedule& sch,
+                     BFwdArgs* fa, BPixArgs* pa) {
   *fa = BFwdArgs{};
+  fa->spmv_per_sm = sch.spmv_per_sm;
+  fa->stencil_per_sm = sch.stencil_per_sm;
   fa->A = A;
   fa->n = n;
   fa->Kp = b.Kp;
@@ -101,6 +110,7 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
   fa->partial = b.partial;
   fa->gtick = b.gtick;
   *pa = BPixArgs{};
+  pa->blocks_per_sm = sch.pixel_per_sm;
   pa->At = At;
   pa->n = n;
   pa->Kp = b.Kp;
@@ -186,18 +196,19 @@ appga_status ensure_batch_workspace(appga_matrix* M, int Kp) {
 
 using namespace appga;
 
-extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat,
-                                                  int32_t K, const float* g, const float* gamma,
-                                                  const float* f_init, const appga_params* params,
-                                                  float* f_out, appga_stats* stats_host,
-                                                  void* stream) {
-  if (!ctx || !mat || !g || !gamma || !params || !f_out) return fail(APPGA_EINVAL, "null argument");
-  if (mat->ctx != ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
-  if (K < 1 || K > 128) return fail(APPGA_EINVAL, "K must be in [1, 128]");
-  appga_status rc = appga_params_validate(params);
-  if (rc != APPGA_OK) return rc;
-  auto* M = const_cast<appga_matrix*>(mat);
-  const int Kp = padded_width(K);
+namespace appga {
+namespace {
+
+// One batched run of K <= 128 slices with launch schedule `sch` (its chunk
+// field is ignored here) in a workspace at least min_width slots wide.
+// Inputs are validated by the caller.
+appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
+                           const float* gamma, const float* f_init, const appga_params* params,
+                           float* f_out, appga_stats* stats_host, const BatchSchedule& sch,
+                           void* stream, int min_width = 0) {
+  appga_status rc = APPGA_OK;
+  const appga_matrix* mat = M;
+  const int Kp = std::max(padded_width(K), min_width);
   if ((rc = ensure_batch_workspace(M, Kp)) != APPGA_OK) return rc;
   if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
   BatchWorkspace& b = *M->bw;
@@ -244,8 +255,8 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
 
   BFwdArgs fa;
   BPixArgs pa;
-  make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, n, b, bf16, track, &fa,
-                  &pa);
+  make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, n, b, bf16, track, sch,
+                  &fa, &pa);
 
   // y^{k0-1}, then the first forward phase (w, y, stencil, Phi of f^{k0})
   BFwdArgs init = fa;
@@ -256,7 +267,9 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
   if (params->max_iters > 0) {
     const int S = params->graph_iters > 0 ? params->graph_iters : kBatchGraphIters;
     char key[256];
-    std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d", Kp, (int)track, (int)bf16, S, K);
+    // the graph's kernels see only the workspace, never K or the caller's buffers
+    std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%d|%d", Kp, (int)track, (int)bf16, S,
+                  sch.spmv_per_sm, sch.stencil_per_sm, sch.pixel_per_sm);
     if (b.gexec == nullptr || b.gkey != key) {
       if (b.gexec) {
         cudaGraphExecDestroy(b.gexec);
@@ -334,4 +347,181 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
   if (r3 != APPGA_OK) return r3;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return rc;
+}
+
+appga_status check_batched_args(appga_ctx* ctx, const appga_matrix* mat, int32_t K,
+                                const float* g, const float* gamma, const appga_params* params) {
+  if (!ctx || !mat || !g || !gamma || !params) return fail(APPGA_EINVAL, "null argument");
+  if (mat->ctx != ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
+  if (K < 1 || K > 128) return fail(APPGA_EINVAL, "K must be in [1, 128]");
+  return appga_params_validate(params);
+}
+
+// K slices with schedule `sch`: as one batch, or as sub-batches of sch.chunk
+// slices run one after another (each with the schedule tuned for its width).
+appga_status batched_run(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
+                         const float* gamma, const float* f_init, const appga_params* params,
+                         float* f_out, appga_stats* stats_host, const BatchSchedule& sch,
+                         void* stream) {
+  if (sch.chunk <= 0 || sch.chunk >= K)
+    return batched_solve(ctx, M, K, g, gamma, f_init, params, f_out, stats_host, sch, stream);
+  // every sub-batch (the last one too) runs at the chunk's width, so the
+  // workspace and its captured graph are reused
+  for (int c0 = 0; c0 < K; c0 += sch.chunk) {
+    const int kc = std::min(sch.chunk, K - c0);
+    appga_status rc = batched_solve(
+        ctx, M, kc, g + (size_t)c0 * M->m, gamma + (size_t)c0 * M->m,
+        f_init ? f_init + (size_t)c0 * M->d : nullptr, params, f_out + (size_t)c0 * M->d,
+        stats_host ? stats_host + c0 : nullptr, sch, stream, sch.chunk);
+    if (rc != APPGA_OK) return rc;
+  }
+  return APPGA_OK;
+}
+
+}  // namespace
+}  // namespace appga
+
+extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat,
+                                                  int32_t K, const float* g, const float* gamma,
+                                                  const float* f_init, const appga_params* params,
+                                                  float* f_out, appga_stats* stats_host,
+                                                  void* stream) {
+  if (!f_out) return fail(APPGA_EINVAL, "null argument");
+  appga_status rc = check_batched_args(ctx, mat, K, g, gamma, params);
+  if (rc != APPGA_OK) return rc;
+  auto* M = const_cast<appga_matrix*>(mat);
+  const bool bf16 = params->a_precision == APPGA_PREC_BF16 && M->has_bf16;
+  return batched_run(ctx, M, K, g, gamma, f_init, params, f_out, stats_host,
+                     tuned_schedule(M, padded_width(K), bf16), stream);
+}
+
+extern "C" appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matrix* mat,
+                                               int32_t K, const float* g, const float* gamma,
+                                               const appga_params* params,
+                                               appga_batch_tuning* out_host) {
+  float* f_scratch = nullptr;
+  appga_status rc = check_batched_args(ctx, mat, K, g, gamma, params);
+  if (rc != APPGA_OK) return rc;
+  auto* M = const_cast<appga_matrix*>(mat);
+  const bool bf16 = params->a_precision == APPGA_PREC_BF16 && M->has_bf16;
+  const int Kp = padded_width(K);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(APPGA_ENODEV, "cudaSetDevice failed");
+  CK(cudaMalloc((void**)&f_scratch, (size_t)K * M->d * sizeof(float)));
+  cudaEvent_t ev[3];
+  for (auto& e : ev) e = nullptr;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaFree(f_scratch);
+      return fail(APPGA_ECUDA, "cudaEventCreate failed");
+    }
+  cudaStream_t s = ctx->stream;
+  // Trials run the solver itself on the caller's slices: kWarm maps (graph
+  // capture, caches), then kWarm and kWarm + kTimed maps timed with events;
+  // the difference is the cost of kTimed maps.
+  constexpr int kWarm = 4, kTimed = 16;
+  appga_params p = *params;
+  p.rel_obj_tol = 0.0;
+  auto trial = [&](const BatchSchedule& sch, double* us) -> appga_status {
+    float ms[2] = {0.f, 0.f};
+    for (int r = 0; r < 3; ++r) {
+      p.max_iters = r == 2 ? kWarm + kTimed : kWarm;
+      if (r > 0 && cudaEventRecord(ev[0], s) != cudaSuccess) return fail(APPGA_ECUDA, "event");
+      appga_status st = batched_run(ctx, M, K, g, gamma, nullptr, &p, f_scratch, nullptr, sch, s);
+      if (st != APPGA_OK) return st;
+      if (r > 0) {
+        if (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess)
+          return fail(APPGA_ECUDA, "event");
+        cudaEventElapsedTime(&ms[r - 1], ev[0], ev[1]);
+      }
+    }
+    *us = 1e3 * (double)(ms[1] - ms[0]) / ((double)kTimed * K);
+    return APPGA_OK;
+  };
+  BatchSchedule best;  // kernel defaults, whole batch
+  double best_us = 0.0, default_us = 0.0;
+  rc = trial(best, &best_us);
+  default_us = best_us;
+  // coordinate descent: sub-batch width, then SpMV, back-projection and stencil grids
+  auto consider = [&](BatchSchedule cand) -> appga_status {
+    if (cand == best) return APPGA_OK;
+    double us = 0.0;
+    appga_status st = trial(cand, &us);
+    if (st != APPGA_OK) return st;
+    if (us < best_us) {
+      best = cand;
+      best_us = us;
+    }
+    return APPGA_OK;
+  };
+  for (int c : {32, 64}) {
+    if (rc != APPGA_OK || c >= Kp) break;
+    BatchSchedule cand = best;
+    cand.chunk = c;
+    rc = consider(cand);
+  }
+  for (int v : {4, 6, 12, 16}) {
+    if (rc != APPGA_OK) break;
+    BatchSchedule cand = best;
+    cand.spmv_per_sm = v;
+    rc = consider(cand);
+  }
+  for (int v : {4, 6, 12, 16}) {
+    if (rc != APPGA_OK) break;
+    BatchSchedule cand = best;
+    cand.pixel_per_sm = v;
+    rc = consider(cand);
+  }
+  for (int v : {2, 8}) {
+    if (rc != APPGA_OK) break;
+    BatchSchedule cand = best;
+    cand.stencil_per_sm = v;
+    rc = consider(cand);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaFree(f_scratch);
+  if (rc != APPGA_OK) return rc;
+  M->tuned[Kp * 2 + (bf16 ? 1 : 0)] = best;
+  if (out_host) {
+    std::memset(out_host, 0, sizeof *out_host);
+    out_host->K = K;
+    out_host->a_precision = bf16 ? APPGA_PREC_BF16 : APPGA_PREC_FP32;
+    out_host->spmv_per_sm = best.spmv_per_sm;
+    out_host->stencil_per_sm = best.stencil_per_sm;
+    out_host->pixel_per_sm = best.pixel_per_sm;
+    out_host->chunk = best.chunk;
+    out_host->us_per_slice_iter = best_us;
+    out_host->us_per_slice_iter_default = default_us;
+  }
+  return APPGA_OK;
+}
+
+extern "C" appga_status appga_batch_schedule_get(const appga_matrix* mat,
+                                                 appga_batch_tuning* t) {
+  if (!mat || !t) return fail(APPGA_EINVAL, "null argument");
+  if (t->K < 1 || t->K > 128) return fail(APPGA_EINVAL, "K must be in [1, 128]");
+  const BatchSchedule sch =
+      tuned_schedule(mat, padded_width(t->K), t->a_precision == APPGA_PREC_BF16);
+  t->spmv_per_sm = sch.spmv_per_sm;
+  t->stencil_per_sm = sch.stencil_per_sm;
+  t->pixel_per_sm = sch.pixel_per_sm;
+  t->chunk = sch.chunk;
+  return APPGA_OK;
+}
+
+extern "C" appga_status appga_batch_schedule_set(appga_matrix* mat, const appga_batch_tuning* t) {
+  if (!mat || !t) return fail(APPGA_EINVAL, "null argument");
+  if (t->K < 1 || t->K > 128) return fail(APPGA_EINVAL, "K must be in [1, 128]");
+  if (t->a_precision != APPGA_PREC_FP32 && t->a_precision != APPGA_PREC_BF16)
+    return fail(APPGA_EINVAL, "a_precision must be APPGA_PREC_FP32 or APPGA_PREC_BF16");
+  for (int v : {t->spmv_per_sm, t->stencil_per_sm, t->pixel_per_sm})
+    if (v < 0 || v > 16) return fail(APPGA_EINVAL, "blocks per SM must be in [0, 16]");
+  if (t->chunk != 0 && t->chunk != 32 && t->chunk != 64)
+    return fail(APPGA_EINVAL, "chunk must be 0, 32 or 64");
+  BatchSchedule sch;
+  sch.spmv_per_sm = t->spmv_per_sm;
+  sch.stencil_per_sm = t->stencil_per_sm;
+  sch.pixel_per_sm = t->pixel_per_sm;
+  sch.chunk = t->chunk;
+  mat->tuned[padded_width(t->K) * 2 + (t->a_precision == APPGA_PREC_BF16 ? 1 : 0)] = sch;
+  return APPGA_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 
 #include "appga.h"
@@ -44,6 +45,19 @@ struct Workspace {
   int graph_iters = 0;
 };
 
+// Launch schedule of the batched kernels (0 = the kernels' defaults), as
+// picked by appga_autotune_batched for one padded width and precision.
+struct BatchSchedule {
+  int spmv_per_sm = 0;     // forward-phase SpMV blocks per SM
+  int stencil_per_sm = 0;  // stencil blocks per SM
+  int pixel_per_sm = 0;    // back-projection blocks per SM
+  int chunk = 0;           // slices per sub-batch (0: the whole batch at once)
+  bool operator==(const BatchSchedule& o) const {
+    return spmv_per_sm == o.spmv_per_sm && stencil_per_sm == o.stencil_per_sm &&
+           pixel_per_sm == o.pixel_per_sm && chunk == o.chunk;
+  }
+};
+
 // Device workspace of the batched solver for one padded batch width Kp.
 struct BatchWorkspace {
   int Kp = 0, m = 0, d = 0;
@@ -74,7 +88,10 @@ cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp);
 // Kernel arguments of one batched step over workspace b with matrix arrays
 // from (A, At, inv_lambda).
 void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda, int n,
-                     BatchWorkspace& b, bool bf16, bool track, BFwdArgs* fa, BPixArgs* pa);
+                     BatchWorkspace& b, bool bf16, bool track, const BatchSchedule& sch,
+                     BFwdArgs* fa, BPixArgs* pa);
+// Tuned schedule of matrix M for padded width Kp and precision (defaults if none).
+BatchSchedule tuned_schedule(const appga_matrix* M, int Kp, bool bf16);
 // Slot state of a problem run with `p` from iterate index k0 (active), or an
 // empty slot that holds no problem (inactive).
 SlotState slot_from_params(const appga_params* p, int k0, bool active);
@@ -103,6 +120,7 @@ struct appga_matrix {
   long long npfov = 0;  // pixels of the initial-image disk
   appga::Workspace ws;
   appga::BatchWorkspace* bw = nullptr;  // batched workspace (one width at a time)
+  std::map<int, appga::BatchSchedule> tuned;  // key: padded width * 2 + BF16
 };
 
 namespace appga {

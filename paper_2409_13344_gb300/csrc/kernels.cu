@@ -73,12 +73,23 @@ struct Shape {
 #endif
 using FW = Shape<APPGA_FW_W, APPGA_FW_RPW, APPGA_FW_PF>;
 using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
-// minimum resident blocks per SM asked of the compiler (register budget)
+// Minimum resident blocks per SM asked of the compiler (a register budget);
+// 0 leaves the choice to the compiler, which measured fastest.
 #ifndef APPGA_FW_MINB
-#define APPGA_FW_MINB 1
+#define APPGA_FW_MINB 0
 #endif
 #ifndef APPGA_PX_MINB
-#define APPGA_PX_MINB 1
+#define APPGA_PX_MINB 0
+#endif
+#if APPGA_FW_MINB > 0
+#define FW_BOUNDS __launch_bounds__(FW::THREADS, APPGA_FW_MINB)
+#else
+#define FW_BOUNDS __launch_bounds__(FW::THREADS)
+#endif
+#if APPGA_PX_MINB > 0
+#define PX_BOUNDS __launch_bounds__(PX::THREADS, APPGA_PX_MINB)
+#else
+#define PX_BOUNDS __launch_bounds__(PX::THREADS)
 #endif
 #ifndef APPGA_GPIPE
 #define APPGA_GPIPE 1
@@ -340,7 +351,7 @@ __device__ void set_theta(SolverState* st, double theta) {
 // Blocks [0, proj_blocks<FW>(m)) project rows; in the solver loop the blocks
 // after them run the stencil tiles.
 template <bool BF16>
-__global__ void __launch_bounds__(FW::THREADS, APPGA_FW_MINB) k_forward(FwdArgs a) {
+__global__ void FW_BOUNDS k_forward(FwdArgs a) {
   __shared__ union {
     struct {
       float hi[FW::W][FW::R * SLOT_W];
@@ -439,7 +450,7 @@ __global__ void __launch_bounds__(FW::THREADS, APPGA_FW_MINB) k_forward(FwdArgs 
 // -------------------------------------------------------------- k_pixel
 
 template <bool BF16>
-__global__ void __launch_bounds__(PX::THREADS, APPGA_PX_MINB) k_pixel(PixArgs a) {
+__global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
   SolverState* st = a.st;
   if (st->done) return;  // uniform over the grid

@@ -150,7 +150,7 @@ appga_status create_pool(appga_server* S, int geom, Pool** out) {
   }
   const bool bf16 = S->cfg.a_precision == APPGA_PREC_BF16;
   make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, M->n, P->b, bf16,
-                  true, &P->fa, &P->pa);
+                  true, tuned_schedule(M, Kp, bf16), &P->fa, &P->pa);
   cudaStream_t s = S->ctx->stream;
   // every slot starts empty; the ring starts at step 1
   appga_params def;

@@ -170,3 +170,51 @@ def test_batched_rejects_bad_input(A, ctx):
     with pytest.raises(A.AppgaError) as ei:
         run_batched(A, ctx, mat, sls, max_iters=5)
     assert ei.value.status == A.APPGA_EDOMAIN
+
+
+def _reset_schedule(A, mat, K, prec=0):
+    A.appga_batch_schedule_set(mat.handle, A.appga_batch_tuning(K=K, a_precision=prec))
+
+
+def test_launch_schedule_never_changes_images(A, ctx):
+    # sub-batches, SpMV / back-projection / stencil grids: the same images bit for bit
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = slices(geom, Amat, 40)
+    f0, _ = run_batched(A, ctx, mat, sls, max_iters=20, omega=1.0)
+    try:
+        for sch in (dict(chunk=32), dict(spmv_per_sm=3, pixel_per_sm=5, stencil_per_sm=1),
+                    dict(chunk=32, spmv_per_sm=16, pixel_per_sm=16, stencil_per_sm=16)):
+            A.appga_batch_schedule_set(mat.handle, A.appga_batch_tuning(K=40, a_precision=0, **sch))
+            got = A.appga_batch_schedule_get(mat.handle, 40)
+            assert (got.chunk, got.spmv_per_sm) == (sch.get("chunk", 0), sch.get("spmv_per_sm", 0))
+            f1, _ = run_batched(A, ctx, mat, sls, max_iters=20, omega=1.0)
+            np.testing.assert_array_equal(f1, f0)
+    finally:
+        _reset_schedule(A, mat, 40)
+
+
+def test_autotune_batched(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "128")
+    sls = slices(geom, Amat, 64)
+    g = torch.from_numpy(np.stack([s.g for s in sls])).to(DEV)
+    gam = torch.from_numpy(np.stack([s.gamma for s in sls])).to(DEV)
+    f0, _ = run_batched(A, ctx, mat, sls, max_iters=12)
+    try:
+        t = A.appga_autotune_batched(ctx.handle, mat.handle, 64, g, gam, A.default_params())
+        assert t.K == 64 and 0 < t.us_per_slice_iter <= t.us_per_slice_iter_default
+        kept = A.appga_batch_schedule_get(mat.handle, 64)
+        assert (kept.spmv_per_sm, kept.stencil_per_sm, kept.pixel_per_sm, kept.chunk) == (
+            t.spmv_per_sm, t.stencil_per_sm, t.pixel_per_sm, t.chunk)
+        f1, _ = run_batched(A, ctx, mat, sls, max_iters=12)
+        np.testing.assert_array_equal(f1, f0)
+    finally:
+        _reset_schedule(A, mat, 64)
+
+
+def test_batch_schedule_rejects_bad_values(A, ctx):
+    geom, Amat, mat = matrix(A, ctx, "64")
+    for bad in (dict(K=0), dict(K=129), dict(K=8, chunk=48), dict(K=8, spmv_per_sm=17),
+                dict(K=8, pixel_per_sm=-1), dict(K=8, a_precision=3)):
+        with pytest.raises(A.AppgaError) as ei:
+            A.appga_batch_schedule_set(mat.handle, A.appga_batch_tuning(**bad))
+        assert ei.value.status == A.APPGA_EINVAL
