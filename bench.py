@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-slice batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 120 x 512^2 batched leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests/s)")
@@ -179,49 +180,55 @@ def batched_bytes(m: int, d: int, nnz: int, K: int):
     return mats + fwd + stencil + pix
 
 
-def bench_batched(AP, ctx, geom, A, dev, single_rate):
-    """64 independent 256x256 slices sharing A (per-slice counts log-uniform
-    1e5..1e7), FP32 and BF16 values of A: slices x iterations per second."""
+def bench_batched(AP, ctx, geom, A, dev, single_rate, K=BATCH_K, lo=1e5, hi=1e7,
+                  omega=OMEGA, iters=BATCH_ITERS, distinct=None, config=3, label=None):
+    """K independent slices sharing A (per-slice counts log-uniform lo..hi),
+    FP32 and BF16 values of A, default and autotuned launch schedules:
+    slices x iterations per second.  `distinct` slices are generated and
+    repeated to K (sinogram generation is host-bound at large sizes)."""
     import numpy as np
     import torch
     from paper_2409_13344_gb300 import workload as W
-    rng = np.random.default_rng(3)
-    counts = W.log_uniform_counts(rng, 1e5, 1e7, BATCH_K)
-    sls = [W.make_slice(A, geom, float(c), W.seed_for(3, i), phantom="lesions")
-           for i, c in enumerate(counts)]
+    rng = np.random.default_rng(config)
+    counts = W.log_uniform_counts(rng, lo, hi, K)
+    nd = K if distinct is None else distinct
+    sls = [W.make_slice(A, geom, float(counts[i]), W.seed_for(config, i), phantom="lesions")
+           for i in range(nd)]
     mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, bf16=True)
-    g = torch.from_numpy(np.stack([x.g for x in sls])).to(dev)
-    gam = torch.from_numpy(np.stack([x.gamma for x in sls])).to(dev)
-    f = torch.empty((BATCH_K, geom.d), dtype=torch.float32, device=dev)
+    g = torch.from_numpy(np.stack([sls[i % nd].g for i in range(K)])).to(dev)
+    gam = torch.from_numpy(np.stack([sls[i % nd].gamma for i in range(K)])).to(dev)
+    f = torch.empty((K, geom.d), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    out = {"workload": f"{BATCH_K} independent 256x256 slices (180 x 367 sinograms) sharing one "
-                       "A, counts log-uniform 1e5..1e7, omega 0.5, beta 1, 200 iterations per "
-                       "call, one call = one SpMM solver run under captured CUDA graphs",
-           "K": BATCH_K}
-    nb = batched_bytes(geom.m, geom.d, int(mat.info().nnz), BATCH_K)
+    out = {"workload": label or (
+               f"{K} independent {geom.n}x{geom.n} slices ({geom.n_angles} x {geom.n_bins} "
+               f"sinograms) sharing one A, counts log-uniform {lo:g}..{hi:g}, omega {omega:g}, "
+               f"beta 1, {iters} iterations per call, one call = one SpMM solver run under "
+               "captured CUDA graphs"),
+           "K": K, "nnz": int(mat.info().nnz)}
+    nb = batched_bytes(geom.m, geom.d, int(mat.info().nnz), K)
 
     def measure(prec):
-        def call(iters):
-            p = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA,
-                                  max_iters=iters, a_precision=prec)
-            AP.appga_reconstruct_batched(ctx.handle, mat.handle, BATCH_K, g, gam, None, p, f)
+        def call(n_maps):
+            p = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=omega,
+                                  max_iters=n_maps, a_precision=prec)
+            AP.appga_reconstruct_batched(ctx.handle, mat.handle, K, g, gam, None, p, f)
         for _ in range(3):
             call(8)
         ms = {}
-        for iters in (8, 8 + BATCH_ITERS):
+        for n_maps in (8, 8 + iters):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            call(iters)
+            call(n_maps)
             e1.record(stream)
             torch.cuda.synchronize()
-            ms[iters] = e0.elapsed_time(e1)
-        per_iter = (ms[8 + BATCH_ITERS] - ms[8]) / BATCH_ITERS
-        rate = BATCH_K / (per_iter * 1e-3)
+            ms[n_maps] = e0.elapsed_time(e1)
+        per_iter = (ms[8 + iters] - ms[8]) / iters
+        rate = K / (per_iter * 1e-3)
         return {"slices_iters_per_s": rate, "us_per_batched_iter": 1e3 * per_iter,
-                "us_per_slice_iter": 1e3 * per_iter / BATCH_K,
-                "call_slices_iters_per_s": BATCH_K * (8 + BATCH_ITERS) / (ms[8 + BATCH_ITERS] * 1e-3),
+                "us_per_slice_iter": 1e3 * per_iter / K,
+                "call_slices_iters_per_s": K * (8 + iters) / (ms[8 + iters] * 1e-3),
                 "algorithmic_gbs": nb / (per_iter * 1e-3) / 1e9,
                 "vs_single_slice": rate / single_rate}
 
@@ -229,9 +236,9 @@ def bench_batched(AP, ctx, geom, A, dev, single_rate):
         out[name] = measure(prec)
         # the library's autotuner picks the launch schedule for this width and
         # precision on these slices; the tuned schedule is then measured the same way
-        t = AP.appga_autotune_batched(ctx.handle, mat.handle, BATCH_K, g, gam,
+        t = AP.appga_autotune_batched(ctx.handle, mat.handle, K, g, gam,
                                       AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS,
-                                                        omega=OMEGA, a_precision=prec))
+                                                        omega=omega, a_precision=prec))
         tuned = measure(prec)
         tuned["schedule"] = {"spmv_per_sm": t.spmv_per_sm, "pixel_per_sm": t.pixel_per_sm,
                              "stencil_per_sm": t.stencil_per_sm, "chunk": t.chunk,
@@ -508,8 +515,20 @@ def run_ours(args):
     }
 
     batched = serving = None
+    large = None
     if world == 1 and not args.no_batched:
         batched = bench_batched(AP, ctx, geom, A, dev, value)
+    if world == 1 and not args.no_large:
+        # 120 slices of 512x512 (360 x 731), dynamic-frame counts 1e4..1e7, omega 1, 300 iterations
+        from paper_2409_13344_gb300 import workload as W
+        g5 = W.GEOMETRIES["512"]
+        large = bench_batched(AP, ctx, g5, W.system_matrix("512"), dev, value, K=120, lo=1e4,
+                              hi=1e7, omega=1.0, iters=60, distinct=8, config=5,
+                              label="120 independent 512x512 slices (360 x 731 sinograms, "
+                                    "Siddon A 120.2M nnz) sharing one A, dynamic-frame counts "
+                                    "log-uniform 1e4..1e7 (8 distinct sinograms repeated), "
+                                    "omega 1, beta 1; rates over 60 timed iterations of a "
+                                    "300-iteration schedule")
     if world == 1 and not args.no_serve:
         serving = bench_serving(AP, ctx, args.serve_requests, args.serve_rate, geom, A)
 
@@ -537,6 +556,7 @@ def run_ours(args):
             "gpu_launches": launches(args.steps),
             "clocks": clk,
             "batched": batched,
+            "large_batch": large,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

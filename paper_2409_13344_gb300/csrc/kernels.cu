@@ -4,21 +4,26 @@
 //               (the projection of f~^k by linearity), w = 1 - g / max(y~ + gamma,
 //               kappa gamma), data term of the objective; in the solver loop
 //               the same launch also runs the SHOITV stencil of
-//               f~^k = f^k + theta_k (f^k - f^{k-1}) (B^T grad phi~(B f~^k)), the
-//               regulariser term of Phi(f^k) and the stopping test
-//               (steps a0, a1, a2, a4, a6; Sec. 2.2, Eq. FidelityTerm,
+//               f~^k = f^k + theta_k (f^k - f^{k-1}) (B^T grad phi~(B f~^k)) and the
+//               regulariser term of Phi(f^k), leaving per-block objective
+//               partials (steps a0, a1, a2, a4, a6; Sec. 2.2, Eq. FidelityTerm,
 //               Eq. gradenvL2, Eq. def:phi)
 //   k_pixel   : grad F = A^T w through the transposed CSR (no atomics) and the
 //               EM-preconditioned projected update f^{k+1} = max(f~ - beta
-//               (f^k / Lambda)(grad F + B^T grad phi~), 0); next index and FP64
-//               momentum scalar (steps a3, a5; Eq. APPGAiter, Eq. EM, Eq. GNtheta)
+//               (f^k / Lambda)(grad F + B^T grad phi~), 0); its last block
+//               sums the forward phase's objective partials into Phi(f^k), runs
+//               the stopping test, and sets the next index and the FP64
+//               momentum scalar (steps a3, a5, a6; Eq. APPGAiter, Eq. EM,
+//               Eq. GNtheta)
 //
-// Projector layout: a warp owns 8 consecutive CSR rows, whose row-padded
+// Projector layout: a warp owns R consecutive CSR rows, whose row-padded
 // entries form one contiguous range, and streams it linearly in 128-entry
 // chunks (a 16-byte pack of columns and one of values per lane), keeping PF
-// chunks in flight in registers.  Lanes accumulate into their current row and
-// park partials in per-warp shared-memory slots; lane q sums row q.  No
-// block-wide barrier sits on the streaming path.
+// chunks in flight in registers and gathering the x values of the next chunk
+// while it accumulates the current one.  Lanes accumulate into their current
+// row and park partials in per-warp shared-memory slots; lane q sums row q.
+// No block-wide barrier sits on the streaming path.  The block shapes (warps
+// per block, R, PF) differ for the two projections (Shape below).
 //
 // The per-row epilogue runs on the FP32 pipe only: double-float (FP32 pair)
 // arithmetic for y, y~, the guarded denominator, and a double-float natural
@@ -28,8 +33,8 @@
 // Kernels read the iteration index and theta from a device-resident
 // SolverState, so a captured graph of (k_pixel, k_forward) pairs replays
 // without host involvement.  Block partials (double-float pairs) are combined
-// by the last block to finish (ticket counter) in index order: every
-// reduction is deterministic.
+// in a fixed order (two-level ticketed reduction), so every reduction is
+// deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -4,10 +4,12 @@
 //
 // Layout (slot-minor): images f[j][s], sinograms y[i][s], w[i][s], g[i][s]
 // with K padded to Kp = 32 V (V = 1, 2 or 4 slots per lane).  One warp owns
-// a CSR row: lanes load 32 (column, value) pairs at a time, then for each
-// nonzero the column is broadcast by shuffle and the warp gathers the Kp-wide
-// image row (one coalesced 4V-byte vector per lane) and accumulates V
-// products per lane in FP32.  The per-(row, slot) epilogues match the
+// a CSR row: lanes load 32 (column, value) pairs at a time and stage them in
+// shared memory; every lane reads them back with broadcast loads and, for
+// each nonzero, gathers its 4V-byte piece of the Kp-wide image row (one
+// coalesced row per warp) and accumulates V products in FP32.  Each block
+// owns a contiguous run of rows, so neighbouring rays (or pixels) reuse the
+// gathered rows from L1.  The per-(row, slot) epilogues match the
 // single-slice kernels (Eq. APPGAiter, Eq. EM, Sec. 2.2); the SHOITV stencil
 // runs on shared-memory tiles of 2 x 32 pixels x 8 slots.
 //

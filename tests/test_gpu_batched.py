@@ -218,3 +218,22 @@ def test_batch_schedule_rejects_bad_values(A, ctx):
         with pytest.raises(A.AppgaError) as ei:
             A.appga_batch_schedule_set(mat.handle, A.appga_batch_tuning(**bad))
         assert ei.value.status == A.APPGA_EINVAL
+
+
+def test_batched_large_512_sampled(A, ctx):
+    # 120 slices of 512^2 (360 x 731, 120.2M nnz) in one batch (Kp = 128),
+    # dynamic-frame counts 1e4..1e7, omega 1: a few maps, sampled slices
+    # against the FP64 oracle
+    geom, Amat, mat = matrix(A, ctx, "512")
+    rng = np.random.default_rng(5)
+    counts = W.log_uniform_counts(rng, 1e4, 1e7, 120)
+    picks = {0: None, 77: None, 119: None}
+    for i in picks:
+        picks[i] = W.make_slice(Amat, geom, float(counts[i]), W.seed_for(5, i), phantom="lesions")
+    base = W.make_slice(Amat, geom, 1e6, W.seed_for(5, 1000), phantom="lesions")
+    sls = [picks.get(i, base) for i in range(120)]
+    f, st = run_batched(A, ctx, mat, sls, max_iters=3, omega=1.0)
+    for i, sl in picks.items():
+        _, ref = oracle(geom, Amat, sl, max_iters=3, omega=1.0)
+        assert st[i].iters == 3
+        assert rel(f[i], ref.f) <= 1e-5, (i, rel(f[i], ref.f))
