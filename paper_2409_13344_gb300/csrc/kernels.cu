@@ -102,12 +102,18 @@ using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
 #ifndef APPGA_SFIRST
 #define APPGA_SFIRST 0
 #endif
+// row starts of a warp's group kept in shared memory instead of registers
+#ifndef APPGA_SBND
+#define APPGA_SBND 1
+#endif
+
 constexpr int SLOT_W = 33;    // slot row stride: per-row sums read without bank conflicts
 
 // Stencil tiles: ST_R x ST_C pixels, one pixel per thread of a projector block
 constexpr int ST_R = FW::W;
 constexpr int ST_C = 32;
 static_assert(ST_R * ST_C == FW::THREADS, "stencil tile = one pixel per thread");
+static_assert(FW::R <= 16 && PX::R <= 16, "row starts of a group: at most 16 in shared memory");
 constexpr int TW = ST_C + 4;  // f tile width (halo 2)
 constexpr int VW = ST_C + 2;  // v tile width (halo 1)
 
@@ -122,118 +128,164 @@ __device__ __forceinline__ int row_of(int p, const int (&bnd)[R + 1], int nrows)
   for (int k = 1; k < R; ++k) q += (k < nrows && bnd[k] <= p) ? 1 : 0;
   return q;
 }
-// Row starts of rows row0 .. row0 + nrows (bnd[k] for k > nrows repeats the
-// end); returns the end of the last row.
-template <int R>
-__device__ __forceinline__ int load_bounds(const DevCSR& M, int row0, int nrows, int lane,
-                                           int (&bnd)[R + 1]) {
-  const int b = lane <= nrows ? M.row_ptr[row0 + lane] : 0;
-#pragma unroll
-  for (int k = 0; k <= R; ++k) bnd[k] = __shfl_sync(0xffffffffu, b, k <= nrows ? k : nrows);
-  return __shfl_sync(0xffffffffu, b, nrows);
-}
-
 __device__ __forceinline__ float4 gather4(const float* __restrict__ x, int4 c) {
   return make_float4(__ldg(x + c.x), __ldg(x + c.y), __ldg(x + c.z), __ldg(x + c.w));
 }
 
-// Rows [row0, row0 + nrows) of M times x; returns the sum of row `lane` in
-// lanes 0..nrows-1: an accumulator pair if DF, else an FP32 value in out_hi.
-// slot_hi / slot_lo: this warp's R*SLOT_W floats each of shared memory.
+// Row starts of rows row0 .. row0 + nrows held one per lane (lane q <= nrows).
+__device__ __forceinline__ int load_raw_bound(const DevCSR& M, int row0, int nrows, int lane) {
+  return lane <= nrows ? M.row_ptr[row0 + lane] : 0;
+}
+
+// One group of R consecutive CSR rows of M streamed by one warp: the row
+// starts, the group's entry range [P0, P1), and PF chunks of the stream in
+// flight.  set_bounds + prologue issue the loads; stream() accumulates the
+// products into per-lane row partials parked in the warp's shared-memory
+// slots; slot_reduce() then sums row q in lane q.
 template <bool BF16, bool DF, int R, int PF>
-__device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nrows,
-                                              const float* __restrict__ x, int lane,
-                                              float* slot_hi, float* slot_lo, float& out_hi,
-                                              float& out_lo) {
-  out_hi = 0.f;
-  out_lo = 0.f;
-  if (nrows <= 0) return;
+struct RowGroup {
+#if APPGA_SBND
+  int* sb;  // the warp's row starts in shared memory (INT_MAX past the last row)
+#else
   int bnd[R + 1];
-  const int P1 = load_bounds<R>(M, row0, nrows, lane, bnd);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    slot_hi[q * SLOT_W + lane] = 0.f;
-    if (DF) slot_lo[q * SLOT_W + lane] = 0.f;
-  }
-  const uint64_t pol = evict_first_policy();
-  const int P0 = bnd[0];
-  const int nchunks = (P1 - P0 + 127) >> 7;
+#endif
+  int nrows, P0, P1;
   int4 c[PF];
   float4 v[PF];
+
+  __device__ __forceinline__ void set_bounds(int braw, int nr) {
+    nrows = nr;
+#if APPGA_SBND
+    const int lane = threadIdx.x & 31;
+    if (lane < 4 * ((R + 3) / 4)) sb[lane] = lane < nr ? braw : 0x7fffffff;
+    __syncwarp();
+    P0 = __shfl_sync(0xffffffffu, braw, 0);
+#else
 #pragma unroll
-  for (int u = 0; u < PF; ++u) {
-    const int p = P0 + (u << 7) + lane * 4;
-    c[u] = make_int4(0, 0, 0, 0);
-    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (p < P1) {
-      c[u] = ld_stream_i4(M.col + p, pol);
-      v[u] = ld_vals<BF16>(M, p, pol);
-    }
-  }
-  float hi = 0.f, lo = 0.f;
-  int cur = -1;
-#if APPGA_GPIPE
-  // x values of the next chunk are gathered one chunk ahead, so the gather
-  // latency overlaps the arithmetic of the current chunk
-  float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (P0 + lane * 4 < P1) xg = gather4(x, c[0]);
+    for (int k = 0; k <= R; ++k) bnd[k] = __shfl_sync(0xffffffffu, braw, k <= nr ? k : nr);
+    P0 = bnd[0];
 #endif
-  for (int t0 = 0; t0 < nchunks; t0 += PF) {
+    P1 = __shfl_sync(0xffffffffu, braw, nr);
+  }
+
+  // row (within the group) of entry p
+  __device__ __forceinline__ int row(int p) const {
+#if APPGA_SBND
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < (R + 3) / 4; ++i) {
+      const int4 b = reinterpret_cast<const int4*>(sb)[i];
+      if (i > 0 && 4 * i < R) q += b.x <= p;
+      if (4 * i + 1 < R) q += b.y <= p;
+      if (4 * i + 2 < R) q += b.z <= p;
+      if (4 * i + 3 < R) q += b.w <= p;
+    }
+    return q;
+#else
+    return row_of<R>(p, bnd, nrows);
+#endif
+  }
+
+  __device__ __forceinline__ void prologue(const DevCSR& M, int lane, uint64_t pol) {
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
-      const int t = t0 + u;
-      if (t < nchunks) {
-        const int p = P0 + (t << 7) + lane * 4;
-        const int4 cc = c[u];
-        const float4 vv = v[u];
-        const int pn = p + (PF << 7);
-        if (pn < P1) {  // refill this slot with chunk t + PF before consuming chunk t
-          c[u] = ld_stream_i4(M.col + pn, pol);
-          v[u] = ld_vals<BF16>(M, pn, pol);
-        }
+      const int p = P0 + (u << 7) + lane * 4;
+      c[u] = make_int4(0, 0, 0, 0);
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < P1) {
+        c[u] = ld_stream_i4(M.col + p, pol);
+        v[u] = ld_vals<BF16>(M, p, pol);
+      }
+    }
+  }
+
+  // clears this lane's row slots (before a group is streamed into them)
+  __device__ __forceinline__ static void clear_slots(int lane, float* slot_hi, float* slot_lo) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      slot_hi[q * SLOT_W + lane] = 0.f;
+      if (DF) slot_lo[q * SLOT_W + lane] = 0.f;
+    }
+  }
+
+  __device__ __forceinline__ void stream(const DevCSR& M, const float* __restrict__ x, int lane,
+                                         uint64_t pol, float* slot_hi, float* slot_lo) {
+    const int nchunks = (P1 - P0 + 127) >> 7;
+    float hi = 0.f, lo = 0.f;
+    int cur = -1;
 #if APPGA_GPIPE
-        const float4 xx = xg;
-        // chunk t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
-        if (p + 128 < P1) xg = gather4(x, c[(u + 1) % PF]);
+    // x values of the next chunk are gathered one chunk ahead, so the gather
+    // latency overlaps the arithmetic of the current chunk
+    float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P0 + lane * 4 < P1) xg = gather4(x, c[0]);
 #endif
-        if (p < P1) {
-          const int q = row_of<R>(p, bnd, nrows);
-          if (q != cur) {
-            if (cur >= 0) {
-              slot_hi[cur * SLOT_W + lane] = hi;
-              if (DF) slot_lo[cur * SLOT_W + lane] = lo;
-            }
-            cur = q;
-            hi = 0.f;
-            lo = 0.f;
+    for (int t0 = 0; t0 < nchunks; t0 += PF) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + u;
+        if (t < nchunks) {
+          const int p = P0 + (t << 7) + lane * 4;
+          const int4 cc = c[u];
+          const float4 vv = v[u];
+          const int pn = p + (PF << 7);
+          if (pn < P1) {  // refill this slot with chunk t + PF before consuming chunk t
+            c[u] = ld_stream_i4(M.col + pn, pol);
+            v[u] = ld_vals<BF16>(M, pn, pol);
           }
 #if APPGA_GPIPE
-          const float x0 = xx.x, x1 = xx.y, x2 = xx.z, x3 = xx.w;
-          (void)cc;
-#else
-          const float x0 = __ldg(x + cc.x), x1 = __ldg(x + cc.y);
-          const float x2 = __ldg(x + cc.z), x3 = __ldg(x + cc.w);
+          const float4 xx = xg;
+          // chunk t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
+          if (p + 128 < P1) xg = gather4(x, c[(u + 1) % PF]);
 #endif
-          if (DF) {
-            acc_fma(hi, lo, vv.x, x0);
-            acc_fma(hi, lo, vv.y, x1);
-            acc_fma(hi, lo, vv.z, x2);
-            acc_fma(hi, lo, vv.w, x3);
-          } else {
-            hi = fmaf(vv.x, x0, hi);
-            hi = fmaf(vv.y, x1, hi);
-            hi = fmaf(vv.z, x2, hi);
-            hi = fmaf(vv.w, x3, hi);
+          if (p < P1) {
+            const int q = row(p);
+            if (q != cur) {
+              if (cur >= 0) {
+                slot_hi[cur * SLOT_W + lane] = hi;
+                if (DF) slot_lo[cur * SLOT_W + lane] = lo;
+              }
+              cur = q;
+              hi = 0.f;
+              lo = 0.f;
+            }
+#if APPGA_GPIPE
+            const float x0 = xx.x, x1 = xx.y, x2 = xx.z, x3 = xx.w;
+            (void)cc;
+#else
+            const float x0 = __ldg(x + cc.x), x1 = __ldg(x + cc.y);
+            const float x2 = __ldg(x + cc.z), x3 = __ldg(x + cc.w);
+#endif
+            if (DF) {
+              acc_fma(hi, lo, vv.x, x0);
+              acc_fma(hi, lo, vv.y, x1);
+              acc_fma(hi, lo, vv.z, x2);
+              acc_fma(hi, lo, vv.w, x3);
+            } else {
+              hi = fmaf(vv.x, x0, hi);
+              hi = fmaf(vv.y, x1, hi);
+              hi = fmaf(vv.z, x2, hi);
+              hi = fmaf(vv.w, x3, hi);
+            }
           }
         }
       }
     }
+    if (cur >= 0) {
+      slot_hi[cur * SLOT_W + lane] = hi;
+      if (DF) slot_lo[cur * SLOT_W + lane] = lo;
+    }
+    __syncwarp();
   }
-  if (cur >= 0) {
-    slot_hi[cur * SLOT_W + lane] = hi;
-    if (DF) slot_lo[cur * SLOT_W + lane] = lo;
-  }
-  __syncwarp();
+
+};
+
+// Sum of row `lane` of a streamed group in lanes 0..nrows-1 from the warp's
+// slots (an accumulator pair if DF).
+template <bool DF>
+__device__ __forceinline__ void slot_reduce(int lane, int nrows, const float* slot_hi,
+                                            const float* slot_lo, float& out_hi, float& out_lo) {
+  out_hi = 0.f;
+  out_lo = 0.f;
   if (lane < nrows) {
     float h = 0.f, l = 0.f;
     if (DF) {
@@ -247,6 +299,31 @@ __device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nro
     out_lo = l;
   }
   __syncwarp();
+}
+
+// Rows [row0, row0 + nrows) of M times x; returns the sum of row `lane` in
+// lanes 0..nrows-1: an accumulator pair if DF, else an FP32 value in out_hi.
+// slot_hi / slot_lo: this warp's R*SLOT_W floats each of shared memory.
+template <bool BF16, bool DF, int R, int PF>
+__device__ __forceinline__ void warp_rows_dot(const DevCSR& M, int row0, int nrows,
+                                              const float* __restrict__ x, int lane,
+                                              float* slot_hi, float* slot_lo, float& out_hi,
+                                              float& out_lo, int* sbnd) {
+  out_hi = 0.f;
+  out_lo = 0.f;
+  if (nrows <= 0) return;
+  RowGroup<BF16, DF, R, PF> rg;
+#if APPGA_SBND
+  rg.sb = sbnd;
+#else
+  (void)sbnd;
+#endif
+  rg.set_bounds(load_raw_bound(M, row0, nrows, lane), nrows);
+  RowGroup<BF16, DF, R, PF>::clear_slots(lane, slot_hi, slot_lo);
+  const uint64_t pol = evict_first_policy();
+  rg.prologue(M, lane, pol);
+  rg.stream(M, x, lane, pol, slot_hi, slot_lo);
+  slot_reduce<DF>(lane, nrows, slot_hi, slot_lo, out_hi, out_lo);
 }
 
 struct StencilSmem {
@@ -361,6 +438,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     struct {
       float hi[FW::W][FW::R * SLOT_W];
       float lo[FW::W][FW::R * SLOT_W];
+      int4 bnd[FW::W][4];
     } slot;
     StencilSmem st;
   } sm;
@@ -386,7 +464,8 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     const int nrows = max(0, min(FW::R, m - row0));
     float hi, lo;
     warp_rows_dot<BF16, true, FW::R, FW::PF>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
-                                             sm.slot.lo[warp], hi, lo);
+                                             sm.slot.lo[warp], hi, lo,
+                                             reinterpret_cast<int*>(sm.slot.bnd[warp]));
     if (lane < nrows) {
       const int row = row0 + lane;
       const df y = quick_renorm(hi, lo);
@@ -454,39 +533,44 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
 
 // -------------------------------------------------------------- k_pixel
 
+// EM-preconditioned projected update of pixel j (Eq. EM, Eq. cloformproiota)
+// given the back-projection bp = (A^T w)_j.
+__device__ __forceinline__ void pixel_update(const PixArgs& a, int kk, int j, float bp,
+                                             int& bad) {
+  const float* fk = a.f[kk % 3];
+  const float vk = fk[j];
+  const float ft = fmaf(a.st->theta_hi, vk - a.f[(kk + 2) % 3][j], vk);
+  float pk = vk;
+  if (a.ip.freeze_iter >= 0) {
+    if (kk == a.ip.freeze_iter) {
+      a.pfreeze[j] = vk;
+    } else if (kk > a.ip.freeze_iter) {
+      pk = a.pfreeze[j];
+    }
+  }
+  const float p = a.ip.beta * pk * a.inv_lambda[j];
+  const float grad = bp + a.gR[j];
+  const float xv = __fmaf_rn(-p, grad, ft);
+  if (!isfinite(xv)) bad = 1;
+  a.f[(kk + 1) % 3][j] = fmaxf(xv, 0.f);
+}
+
 template <bool BF16>
 __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
+  __shared__ int4 sbnd[PX::W][4];
   SolverState* st = a.st;
   if (st->done) return;  // uniform over the grid
   const int kk = st->k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = a.At.rows;
+  int bad = 0;
   const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
   const int np = max(0, min(PX::R, d - j0));
   float bp, unused;
   warp_rows_dot<BF16, false, PX::R, PX::PF>(a.At, j0, np, a.w, lane, slot[warp], nullptr, bp,
-                                            unused);
-  int bad = 0;
-  if (lane < np) {
-    const int j = j0 + lane;
-    const float* fk = a.f[kk % 3];
-    const float vk = fk[j];
-    const float ft = fmaf(st->theta_hi, vk - a.f[(kk + 2) % 3][j], vk);
-    float pk = vk;
-    if (a.ip.freeze_iter >= 0) {
-      if (kk == a.ip.freeze_iter) {
-        a.pfreeze[j] = vk;
-      } else if (kk > a.ip.freeze_iter) {
-        pk = a.pfreeze[j];
-      }
-    }
-    const float p = a.ip.beta * pk * a.inv_lambda[j];
-    const float grad = bp + a.gR[j];
-    const float xv = __fmaf_rn(-p, grad, ft);
-    if (!isfinite(xv)) bad = 1;
-    a.f[(kk + 1) % 3][j] = fmaxf(xv, 0.f);
-  }
+                                            unused, reinterpret_cast<int*>(sbnd[warp]));
+  if (lane < np) pixel_update(a, kk, j0 + lane, bp, bad);
   warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
   // This block's share of Phi(f^kk): the forward blocks' partials b, b + G, ...
   float ph = 0.f, pl = 0.f;
@@ -557,12 +641,13 @@ template <bool BF16>
 __global__ void __launch_bounds__(PX::THREADS) k_backproject(DevCSR At, const float* __restrict__ w,
                                                             float* __restrict__ out) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
+  __shared__ int4 sbnd[PX::W][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row0 = blockIdx.x * PX::ROWS + warp * PX::R;
   const int nrows = max(0, min(PX::R, At.rows - row0));
   float s, unused;
   warp_rows_dot<BF16, false, PX::R, PX::PF>(At, row0, nrows, w, lane, slot[warp], nullptr, s,
-                                            unused);
+                                            unused, reinterpret_cast<int*>(sbnd[warp]));
   if (lane < nrows) out[row0 + lane] = s;
 }
 
