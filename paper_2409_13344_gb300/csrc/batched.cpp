@@ -459,19 +459,19 @@ extern "C" appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matri
     cand.chunk = c;
     rc = consider(cand);
   }
-  for (int v : {4, 6, 12, 16}) {
+  for (int v : {1, 2, 3, 4, 5, 6, 8, 12}) {
     if (rc != APPGA_OK) break;
     BatchSchedule cand = best;
     cand.spmv_per_sm = v;
     rc = consider(cand);
   }
-  for (int v : {4, 6, 12, 16}) {
+  for (int v : {2, 3, 4, 5, 6, 8, 12}) {
     if (rc != APPGA_OK) break;
     BatchSchedule cand = best;
     cand.pixel_per_sm = v;
     rc = consider(cand);
   }
-  for (int v : {2, 8}) {
+  for (int v : {1, 2, 3, 4, 8}) {
     if (rc != APPGA_OK) break;
     BatchSchedule cand = best;
     cand.stencil_per_sm = v;

@@ -32,8 +32,6 @@ namespace {
 constexpr int B_THREADS = 256;
 constexpr int B_WARPS = B_THREADS / 32;
 constexpr int MAXK = 128;                    // largest padded batch (V = 4)
-constexpr int kSpmvPerSm = 8;                // default persistent SpMV blocks per SM
-constexpr int kStencilPerSm = 4;             // default stencil blocks per SM
 constexpr int kMaxPerSm = 16;                // upper bound of either tuned value
 __host__ __forceinline__ int clamp_per_sm(int v, int dflt) {
   return v <= 0 ? dflt : (v > kMaxPerSm ? kMaxPerSm : v);
@@ -804,12 +802,25 @@ __global__ void __launch_bounds__(256) k_binit_image(const float* __restrict__ g
   }
 }
 
+// Resident blocks per SM of each kernel (the defaults keep the whole grid
+// resident: the SpMV loops are persistent).
 template <int V, bool BF16>
-int bf_blocks(int per_sm_cap, int sms) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bforward<V, BF16>, B_THREADS, 0);
-  if (per_sm <= 0) per_sm = 1;
-  return (per_sm < per_sm_cap ? per_sm : per_sm_cap) * sms;
+int bforward_resident() {
+  static const int r = [] {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bforward<V, BF16>, B_THREADS, 0);
+    return per_sm > 0 ? per_sm : 1;
+  }();
+  return r;
+}
+template <int V, bool BF16>
+int bpixel_resident() {
+  static const int r = [] {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bpixel<V, BF16>, B_THREADS, 0);
+    return per_sm > 0 ? per_sm : 1;
+  }();
+  return r;
 }
 
 int sm_count() {
@@ -828,14 +839,16 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   const int sms = sm_count();
   const int rows_per_block = B_WARPS;
   int nsp = (a.A.rows + rows_per_block - 1) / rows_per_block;
-  const int cap = sms * clamp_per_sm(a.spmv_per_sm, kSpmvPerSm);
+  // default: one stencil block per SM and SpMV blocks filling the rest
+  const int res = a.use_bf16 ? bforward_resident<V, true>() : bforward_resident<V, false>();
+  const int cap = sms * clamp_per_sm(a.spmv_per_sm, res > 1 ? res - 1 : 1);
   if (nsp > cap) nsp = cap;
   a.n_spmv_blocks = nsp;
   int nst = 0;
   if (a.mode != 1) {
     // equal tile counts per stencil block
     const int tiles = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R);
-    const int scap = sms * clamp_per_sm(a.stencil_per_sm, kStencilPerSm);
+    const int scap = sms * clamp_per_sm(a.stencil_per_sm, 1);
     const int per = (tiles + scap - 1) / scap;
     nst = (tiles + per - 1) / per;
   }
@@ -850,7 +863,8 @@ template <int V>
 cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
   const int sms = sm_count();
   int nb = (a.At.rows + B_WARPS - 1) / B_WARPS;
-  const int cap = sms * clamp_per_sm(a.blocks_per_sm, kSpmvPerSm);
+  const int res = a.use_bf16 ? bpixel_resident<V, true>() : bpixel_resident<V, false>();
+  const int cap = sms * clamp_per_sm(a.blocks_per_sm, res);
   if (nb > cap) nb = cap;
   if (a.use_bf16)
     k_bpixel<V, true><<<nb, B_THREADS, 0, s>>>(a);
