@@ -32,6 +32,11 @@ namespace {
 constexpr int B_THREADS = 256;
 constexpr int B_WARPS = B_THREADS / 32;
 constexpr int MAXK = 128;                    // largest padded batch (V = 4)
+// Default grids: more blocks than fit at once (measured faster on GB300 than
+// grids that are all resident: blocks own contiguous row ranges, and the
+// block scheduler balances the tail).
+constexpr int kSpmvPerSm = 8;                // SpMV / back-projection blocks per SM
+constexpr int kStencilPerSm = 4;             // stencil blocks per SM
 constexpr int kMaxPerSm = 16;                // upper bound of either tuned value
 __host__ __forceinline__ int clamp_per_sm(int v, int dflt) {
   return v <= 0 ? dflt : (v > kMaxPerSm ? kMaxPerSm : v);
@@ -802,26 +807,6 @@ __global__ void __launch_bounds__(256) k_binit_image(const float* __restrict__ g
   }
 }
 
-// Resident blocks per SM of each kernel (the defaults keep the whole grid
-// resident: the SpMV loops are persistent).
-template <int V, bool BF16>
-int bforward_resident() {
-  static const int r = [] {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bforward<V, BF16>, B_THREADS, 0);
-    return per_sm > 0 ? per_sm : 1;
-  }();
-  return r;
-}
-template <int V, bool BF16>
-int bpixel_resident() {
-  static const int r = [] {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bpixel<V, BF16>, B_THREADS, 0);
-    return per_sm > 0 ? per_sm : 1;
-  }();
-  return r;
-}
 
 int sm_count() {
   static int sms = [] {
@@ -839,16 +824,14 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   const int sms = sm_count();
   const int rows_per_block = B_WARPS;
   int nsp = (a.A.rows + rows_per_block - 1) / rows_per_block;
-  // default: one stencil block per SM and SpMV blocks filling the rest
-  const int res = a.use_bf16 ? bforward_resident<V, true>() : bforward_resident<V, false>();
-  const int cap = sms * clamp_per_sm(a.spmv_per_sm, res > 1 ? res - 1 : 1);
+  const int cap = sms * clamp_per_sm(a.spmv_per_sm, kSpmvPerSm);
   if (nsp > cap) nsp = cap;
   a.n_spmv_blocks = nsp;
   int nst = 0;
   if (a.mode != 1) {
     // equal tile counts per stencil block
     const int tiles = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R);
-    const int scap = sms * clamp_per_sm(a.stencil_per_sm, 1);
+    const int scap = sms * clamp_per_sm(a.stencil_per_sm, kStencilPerSm);
     const int per = (tiles + scap - 1) / scap;
     nst = (tiles + per - 1) / per;
   }
@@ -863,8 +846,7 @@ template <int V>
 cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
   const int sms = sm_count();
   int nb = (a.At.rows + B_WARPS - 1) / B_WARPS;
-  const int res = a.use_bf16 ? bpixel_resident<V, true>() : bpixel_resident<V, false>();
-  const int cap = sms * clamp_per_sm(a.blocks_per_sm, res);
+  const int cap = sms * clamp_per_sm(a.blocks_per_sm, kSpmvPerSm);
   if (nb > cap) nb = cap;
   if (a.use_bf16)
     k_bpixel<V, true><<<nb, B_THREADS, 0, s>>>(a);
