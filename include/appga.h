@@ -314,6 +314,34 @@ appga_status appga_objective_noalloc(appga_ctx* ctx, const appga_matrix* mat, co
                                      const float* g, const float* gamma,
                                      const appga_params* params, double* phi_out, void* stream);
 
+/* ------------------------------------------------------- figures of merit
+ * The comparison metrics of Sec. 4.1, for evaluating reconstructions.
+ * appga_figures_of_merit: f, f_true: float[d] device images; roi_h, roi_b:
+ * uint8[d] device masks of the hot region and the background region (both
+ * NULL to skip the contrast figures); max_value: MAX, the largest possible
+ * pixel value.  Computes in FP64-accurate arithmetic (double-float sums):
+ *   mse  = ||f - f_true||^2 / d,   psnr = 10 log10(MAX^2 / mse),
+ *   rc   = |E_H(f) - E_B(f)| / E_B(f) with E the region means,
+ *   rc_true the same for f_true,   nrc = rc / rc_true.
+ * Contrast fields are NaN when a region is empty or not given.  Allocates a
+ * small scratch and synchronises.  EINVAL for d < 1, max_value <= 0, one
+ * mask without the other. */
+typedef struct {
+  double mse, psnr, rc, rc_true, nrc;
+  int64_t n_roi_h, n_roi_b;  /* pixels in each region */
+} appga_fom;
+appga_status appga_figures_of_merit(appga_ctx* ctx, int32_t d, const float* f,
+                                    const float* f_true, const uint8_t* roi_h,
+                                    const uint8_t* roi_b, double max_value, appga_fom* out_host,
+                                    void* stream);
+/* NOFV(f^k) = (Phi(f^k) - Phi_ref) / (Phi_0 - Phi_ref), Phi_0 the objective of
+ * the initial image and Phi_ref a reference value (Sec. 4.1).  Host function. */
+double appga_nofv(double phi_k, double phi_0, double phi_ref);
+/* Central line profile: out[c] = f[(n_side/2) * n_side + c], c < n_side (row
+ * n_side/2 of the row-major image), device to device on `stream`. */
+appga_status appga_central_line_profile(appga_ctx* ctx, int32_t n_side, const float* f,
+                                        float* out, void* stream);
+
 /* appga_validate_csr_host: the host-side check appga_matrix_create runs on a
  * CSR (row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz, 0 <= col < d, values
  * finite and >= 0).  Host only; needs no device.  EINVAL / EDOMAIN with a

@@ -73,6 +73,14 @@ class appga_batch_tuning(ctypes.Structure):
     ]
 
 
+class appga_fom(ctypes.Structure):
+    _fields_ = [
+        ("mse", ctypes.c_double), ("psnr", ctypes.c_double), ("rc", ctypes.c_double),
+        ("rc_true", ctypes.c_double), ("nrc", ctypes.c_double), ("n_roi_h", ctypes.c_int64),
+        ("n_roi_b", ctypes.c_int64),
+    ]
+
+
 class appga_server_config(ctypes.Structure):
     _fields_ = [
         ("slots_per_pool", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
@@ -150,6 +158,10 @@ SIGNATURES = {
                                               ctypes.POINTER(appga_batch_tuning)]),
     "appga_batch_schedule_get": (ctypes.c_int, [_P, ctypes.POINTER(appga_batch_tuning)]),
     "appga_batch_schedule_set": (ctypes.c_int, [_P, ctypes.POINTER(appga_batch_tuning)]),
+    "appga_figures_of_merit": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _D,
+                                              ctypes.POINTER(appga_fom), _P]),
+    "appga_nofv": (_D, [_D, _D, _D]),
+    "appga_central_line_profile": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     # appga_server.h
     "appga_server_config_default": (None, [ctypes.POINTER(appga_server_config)]),
     "appga_server_create": (ctypes.c_int, [_P, ctypes.POINTER(appga_server_config),
@@ -369,6 +381,26 @@ def appga_batch_schedule_get(mat, K: int, a_precision: int = 0) -> appga_batch_t
 def appga_batch_schedule_set(mat, tuning: appga_batch_tuning):
     _check(load_library().appga_batch_schedule_set(mat, ctypes.byref(tuning)),
            "appga_batch_schedule_set")
+
+
+def appga_figures_of_merit(ctx, d, f, f_true, roi_h, roi_b, max_value, stream=None) -> appga_fom:
+    """MSE, PSNR, RC and NRC of a device image against the ground truth
+    (roi_h / roi_b: uint8 device masks, or None for both)."""
+    out = appga_fom()
+    _check(load_library().appga_figures_of_merit(ctx, d, _ptr(f), _ptr(f_true), _ptr(roi_h),
+                                                 _ptr(roi_b), float(max_value), ctypes.byref(out),
+                                                 _stream(stream)), "appga_figures_of_merit")
+    return out
+
+
+def appga_nofv(phi_k, phi_0, phi_ref) -> float:
+    return load_library().appga_nofv(phi_k, phi_0, phi_ref)
+
+
+def appga_central_line_profile(ctx, n_side, f, out, stream=None):
+    _check(load_library().appga_central_line_profile(ctx, n_side, _ptr(f), _ptr(out),
+                                                     _stream(stream)),
+           "appga_central_line_profile")
 
 
 def appga_objective_noalloc(ctx, mat, f, g, gamma, params, phi_out, stream=None):

@@ -30,6 +30,7 @@ void free_batch_workspace(BatchWorkspace* bw) {
   cudaFree(bw->slots);
   cudaFree(bw->bst);
   cudaFree(bw->partial);
+  cudaFree(bw->fpartial);
   cudaFree(bw->gtick);
   cudaFree(bw->flag);
   cudaFreeHost(bw->slots_host);
@@ -44,7 +45,7 @@ int64_t batch_workspace_bytes(int m, int d, int Kp) {
   b += (int64_t)5 * d * Kp * sizeof(float);  // f ring, gR, pfreeze
   b += (int64_t)5 * m * Kp * sizeof(float);  // y ring, w, g, gamma
   b += (int64_t)Kp * sizeof(SlotState) + sizeof(BatchState);
-  b += (batch_max_blocks() + ngroups + 2) * Kp * (int64_t)sizeof(float2);
+  b += (2 * batch_max_blocks() + ngroups + 2) * Kp * (int64_t)sizeof(float2);
   b += ngroups * (int64_t)sizeof(unsigned int) + (int64_t)sizeof(int);
   return b;
 }
@@ -65,6 +66,7 @@ cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp) {
   if (e == cudaSuccess) e = dalloc(&b.slots, (size_t)Kp);
   if (e == cudaSuccess) e = dalloc(&b.bst, 1);
   if (e == cudaSuccess) e = dalloc(&b.partial, (size_t)(maxb + ngroups + 2) * Kp);
+  if (e == cudaSuccess) e = dalloc(&b.fpartial, (size_t)maxb * Kp);
   if (e == cudaSuccess) e = dalloc(&b.gtick, (size_t)ngroups);
   if (e == cudaSuccess) e = dalloc(&b.flag, 1);
   if (e == cudaSuccess) e = cudaMemset(b.gtick, 0, (size_t)ngroups * sizeof(unsigned int));
@@ -107,8 +109,7 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
   fa->gR = b.gR;
   fa->slots = b.slots;
   fa->bst = b.bst;
-  fa->partial = b.partial;
-  fa->gtick = b.gtick;
+  fa->fpartial = b.fpartial;
   *pa = BPixArgs{};
   pa->blocks_per_sm = sch.pixel_per_sm;
   pa->At = At;
@@ -124,6 +125,9 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
   pa->bst = b.bst;
   pa->partial = b.partial;
   pa->gtick = b.gtick;
+  pa->fpartial = b.fpartial;
+  pa->n_fpartial = bforward_grid(*fa);
+  pa->track = track ? 1 : 0;
 }
 
 cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
@@ -311,6 +315,9 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
       for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(b.gexec, s));
     }
   }
+  // a slot stopped by the test in the last pixel phase has its result one
+  // ring entry back: move it into the current entry first
+  CK(launch_resolve_rollback(fa, s));
   CK(cudaMemcpyAsync(b.bst_host, b.bst, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(b.slots_host, b.slots, Kp * sizeof(SlotState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

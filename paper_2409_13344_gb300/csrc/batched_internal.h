@@ -23,7 +23,7 @@ struct SlotState {
   int32_t momentum;
   int32_t fresh;      // just admitted: f^{k-1} = f^k, needs its first forward phase
   int32_t phi_k;      // iterate index whose objective is in phi_cur (-1: none)
-  int32_t pad1;
+  int32_t rollback;   // stopped one step back: the result is the previous ring entry
   float theta_hi, theta_lo;  // theta_k as a double-float pair
   float lambda1, lambda2, eps, beta;
   double theta, t_cur, phi_cur, phi_prev;
@@ -57,8 +57,7 @@ struct BFwdArgs {
   float* gR;
   SlotState* slots;
   BatchState* bst;
-  float2* partial;
-  unsigned int* gtick;
+  float2* fpartial;  // per-slot objective partials, one row of Kp per block
 };
 
 struct BPixArgs {
@@ -75,9 +74,19 @@ struct BPixArgs {
   BatchState* bst;
   float2* partial;
   unsigned int* gtick;
+  // objective partials left by the forward phase of the same step (track):
+  // reduced here, where the stopping test runs
+  const float2* fpartial;
+  int32_t n_fpartial;
+  int32_t track;
 };
 
 int batch_max_blocks();
+// Grid of the forward phase for these arguments (the launcher's own choice).
+int bforward_grid(const BFwdArgs& a);
+// Slots whose result sits one ring entry back (stopped by the test in the
+// last pixel phase): copy it into the current entry and clear the mark.
+cudaError_t launch_resolve_rollback(const BFwdArgs& a, cudaStream_t s);
 cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s);
 cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s);
 // Slot lists: where `ids` is given, slice k goes to slot ids[k] (a device

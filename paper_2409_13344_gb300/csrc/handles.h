@@ -73,6 +73,7 @@ struct BatchWorkspace {
   BatchState* bst = nullptr;
   BatchState* bst_host = nullptr;             // pinned
   float2* partial = nullptr;                  // (blocks + groups) x Kp
+  float2* fpartial = nullptr;                 // forward-phase objective partials, blocks x Kp
   unsigned int* gtick = nullptr;
   int* flag = nullptr;
   int* flag_host = nullptr;

@@ -380,18 +380,6 @@ __device__ void bset_theta(SlotState& s, double theta) {
 
 // -------------------------------------------------------------- k_bforward
 
-// Live slots (held and not finished), counted by the one block that calls it.
-__device__ void bset_remaining(const SlotState* slots, int Kp, BatchState* bs) {
-  __shared__ int s_cnt;
-  if (threadIdx.x == 0) s_cnt = 0;
-  __syncthreads();
-  int c = 0;
-  for (int s = threadIdx.x; s < Kp; s += blockDim.x) c += slots[s].active && !slots[s].done;
-  if (c) atomicAdd(&s_cnt, c);
-  __syncthreads();
-  if (threadIdx.x == 0) bs->remaining = s_cnt;
-}
-
 template <int V, bool BF16>
 __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   __shared__ __align__(16) int s_off[B_WARPS][32];
@@ -400,8 +388,6 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
     struct {
       float dhi[B_WARPS][MAXK];
       float dlo[B_WARPS][MAXK];
-      float bhi[MAXK], blo[MAXK];
-      float thi[MAXK], tlo[MAXK];
     } e;
     BStencilSmem st;
   } sm;
@@ -539,19 +525,9 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
     for (int t = 0; t < V; ++t)
       if (hits[t]) atomicAdd(&a.slots[lane * V + t].guard_hits, (unsigned long long)hits[t]);
   }
-  if (proj_only) return;
-  if (!want) {
-    // no objective: an admission pass still clears the fresh flags (last block)
-    if (a.mode != 2) return;
-    double unused;
-    __syncthreads();
-    if (grid_reduce(a.partial, a.gtick, &bs->ticket_r, {0.f, 0.f}, &unused)) {
-      for (int s = tid; s < Kp; s += blockDim.x) a.slots[s].fresh = 0;
-      bset_remaining(a.slots, Kp, bs);
-    }
-    return;
-  }
-  // block partial per slot (fixed order over warps)
+  if (!want) return;
+  // block partial per slot (fixed order over warps), left for the pixel
+  // phase of this step; an admission pass writes only the fresh slots' columns
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < V; ++t) {
@@ -560,35 +536,11 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   }
   __syncthreads();
   for (int s = tid; s < Kp; s += blockDim.x) {
+    const SlotState& sl = a.slots[s];
+    if (a.mode == 2 ? !sl.fresh : !(sl.active && !sl.done)) continue;
     float h = 0.f, l = 0.f;
     for (int w = 0; w < B_WARPS; ++w) acc_add(h, l, sm.e.dhi[w][s], sm.e.dlo[w][s]);
-    sm.e.bhi[s] = h;
-    sm.e.blo[s] = l;
-  }
-  __syncthreads();
-  if (grid_reduce_slots(a.partial, a.gtick, &bs->ticket_r, sm.e.bhi, sm.e.blo, Kp, sm.e.thi,
-                        sm.e.tlo)) {
-    // Phi(f^k) of every participating slot (once per iterate) and its stopping test
-    for (int s = tid; s < Kp; s += blockDim.x) {
-      SlotState& sl = a.slots[s];
-      const bool part = a.mode == 2 ? sl.fresh : (sl.active && !sl.done);
-      if (!part) continue;
-      sl.fresh = 0;
-      if (sl.phi_k == sl.k) continue;  // this iterate's objective is already in
-      const double phi = (double)sm.e.thi[s] + (double)sm.e.tlo[s];
-      const double prev = sl.phi_cur;
-      const bool consecutive = sl.phi_k == sl.k - 1;
-      sl.phi_prev = prev;
-      sl.phi_cur = phi;
-      sl.phi_k = sl.k;
-      if (sl.rel_tol > 0.0 && sl.k > sl.k0 && consecutive &&
-          fabs(phi - prev) <= sl.rel_tol * fabs(prev)) {
-        sl.done = 1;
-        sl.result_k = sl.k;
-        sl.stopped_early = 1;
-      }
-    }
-    if (a.mode == 2) bset_remaining(a.slots, Kp, bs);
+    a.fpartial[(size_t)blockIdx.x * Kp + s] = make_float2(h, l);
   }
 }
 
@@ -598,6 +550,7 @@ template <int V, bool BF16>
 __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
   __shared__ __align__(16) int s_off[B_WARPS][32];
   __shared__ __align__(16) float s_val[B_WARPS][32];
+  __shared__ float r_hi[MAXK], r_lo[MAXK], t_hi[MAXK], t_lo[MAXK];
   BatchState* bs = a.bst;
   if (bs->remaining == 0) return;  // uniform over the grid
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -608,7 +561,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
   float* fn = a.f[(G + 1) % 3];
   // this lane's slot parameters
   float th[V], beta[V];
-  int live[V], kk[V], frz[V];
+  int live[V], kk[V], frz[V], back[V];
 #pragma unroll
   for (int t = 0; t < V; ++t) {
     const SlotState& sl = a.slots[lane * V + t];
@@ -617,6 +570,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
     live[t] = sl.active && !sl.done;
     kk[t] = sl.k;
     frz[t] = sl.freeze_iter;
+    back[t] = sl.rollback;
   }
   bool lane_live = false;
 #pragma unroll
@@ -644,7 +598,9 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       if (!live[t]) {
-        out[t] = vk[t];  // finished or empty slot: carry the image
+        // finished or empty slot: carry the image (the previous entry when
+        // the slot stopped one step back)
+        out[t] = back[t] ? vm[t] : vk[t];
         continue;
       }
       const float ft = fmaf(th[t], vk[t] - vm[t], vk[t]);
@@ -664,16 +620,48 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
     vstore<V>(fn + o, out);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&bs->flags, APPGA_FLAG_NONFINITE);
-  // Finalise the step in the last block: every live slot advances its index
-  // and momentum; the global step advances.
+  // This block's share of every slot's Phi(f^k): forward partial rows
+  // b, b + G, ... (fixed order).
+  for (int s = tid; s < Kp; s += blockDim.x) {
+    float h = 0.f, l = 0.f;
+    if (a.track)
+      for (int i = blockIdx.x; i < a.n_fpartial; i += gridDim.x) {
+        const float2 v = a.fpartial[(size_t)i * Kp + s];
+        acc_add(h, l, v.x, v.y);
+      }
+    r_hi[s] = h;
+    r_lo[s] = l;
+  }
+  // Finalise the step in the last block: Phi and the stopping test of every
+  // live slot, then its next index and momentum; the global step advances.
   __syncthreads();
-  double unused;
-  if (grid_reduce(a.partial, a.gtick, &bs->ticket_p, {0.f, 0.f}, &unused)) {
+  if (grid_reduce_slots(a.partial, a.gtick, &bs->ticket_p, r_hi, r_lo, Kp, t_hi, t_lo)) {
     __shared__ int s_rem[B_THREADS];
     int rem = 0;
     for (int s = tid; s < Kp; s += blockDim.x) {
       SlotState& sl = a.slots[s];
-      if (!sl.active || sl.done) continue;
+      sl.fresh = 0;
+      if (!sl.active || sl.done) {
+        sl.rollback = 0;  // its carry above used the previous entry
+        continue;
+      }
+      if (a.track && sl.phi_k != sl.k) {
+        const double phi = (double)t_hi[s] + (double)t_lo[s];
+        const double prev = sl.phi_cur;
+        const bool consecutive = sl.phi_k == sl.k - 1;
+        sl.phi_prev = prev;
+        sl.phi_cur = phi;
+        sl.phi_k = sl.k;
+        if (sl.rel_tol > 0.0 && sl.k > sl.k0 && consecutive &&
+            fabs(phi - prev) <= sl.rel_tol * fabs(prev)) {
+          // f^k is the result; the f^{k+1} written above is not used
+          sl.done = 1;
+          sl.result_k = sl.k;
+          sl.stopped_early = 1;
+          sl.rollback = 1;
+          continue;
+        }
+      }
       if (sl.k >= sl.k_last) {
         sl.done = 1;
         sl.result_k = sl.k + 1;
@@ -705,6 +693,24 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
 }
 
 // ----------------------------------------------------------- setup kernels
+
+// Slots marked rollback: copy the previous ring entry into the current one
+// (the ring entries of the current global step, read on the device).
+__global__ void k_resolve_rollback(const SlotState* slots, const BatchState* bs, float* f0,
+                                   float* f1, float* f2, int len, int Kp) {
+  const int s = blockIdx.y;
+  if (!slots[s].rollback) return;  // uniform over the block
+  float* ring[3] = {f0, f1, f2};
+  const int G = bs->gstep;
+  const float* prev = ring[(G + 2) % 3];
+  float* cur = ring[G % 3];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x)
+    cur[(size_t)i * Kp + s] = prev[(size_t)i * Kp + s];
+}
+__global__ void k_clear_rollback(SlotState* slots, int Kp) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < Kp) slots[s].rollback = 0;
+}
 
 // theta_{k0} of every slot, or of the fresh slots only (same device
 // arithmetic as the step kernel).
@@ -818,15 +824,11 @@ int sm_count() {
   return sms;
 }
 
-template <int V>
-cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
-  BFwdArgs a = a0;
+int bforward_grid_n(const BFwdArgs& a, int* n_spmv) {
   const int sms = sm_count();
-  const int rows_per_block = B_WARPS;
-  int nsp = (a.A.rows + rows_per_block - 1) / rows_per_block;
+  int nsp = (a.A.rows + B_WARPS - 1) / B_WARPS;
   const int cap = sms * clamp_per_sm(a.spmv_per_sm, kSpmvPerSm);
   if (nsp > cap) nsp = cap;
-  a.n_spmv_blocks = nsp;
   int nst = 0;
   if (a.mode != 1) {
     // equal tile counts per stencil block
@@ -835,7 +837,18 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
     const int per = (tiles + scap - 1) / scap;
     nst = (tiles + per - 1) / per;
   }
-  const int grid = nsp + nst;
+  if (n_spmv) *n_spmv = nsp;
+  return nsp + nst;
+}
+
+template <int V>
+cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
+  BFwdArgs a = a0;
+  const int sms = sm_count();
+  (void)sms;
+  int nsp = 0;
+  const int grid = bforward_grid_n(a, &nsp);
+  a.n_spmv_blocks = nsp;
   if (a.use_bf16)
     k_bforward<V, true><<<grid, B_THREADS, 0, s>>>(a);
   else
@@ -860,6 +873,19 @@ cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
 // Largest grid of the batched kernels: at most kMaxPerSm SpMV and kMaxPerSm
 // stencil blocks per SM (the launchers clamp the tuned values).
 int batch_max_blocks() { return sm_count() * 2 * kMaxPerSm + 64; }
+
+int bforward_grid(const BFwdArgs& a) { return bforward_grid_n(a, nullptr); }
+
+cudaError_t launch_resolve_rollback(const BFwdArgs& a, cudaStream_t s) {
+  const int len = a.n * a.n;
+  dim3 grid((len + 255) / 256 < 64 ? (len + 255) / 256 : 64, a.Kp);
+  k_resolve_rollback<<<grid, 256, 0, s>>>(a.slots, a.bst, a.f[0], a.f[1], a.f[2], len, a.Kp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // cleared by a second launch: every block above has read the mark first
+  k_clear_rollback<<<(a.Kp + 127) / 128, 128, 0, s>>>(a.slots, a.Kp);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s) {
   cudaError_t e = ensure_tables();

@@ -286,6 +286,10 @@ appga_status admit(appga_server* S, Pool* P, int count) {
   BFwdArgs a = P->fa;
   a.mode = 2;
   CK(launch_bforward(a, s));
+  // every held slot is live at a step boundary (finished ones were retired)
+  P->b.bst_host->remaining = P->used + K;
+  CK(cudaMemcpyAsync(&P->b.bst->remaining, &P->b.bst_host->remaining, sizeof(int),
+                     cudaMemcpyHostToDevice, s));
   const double t = S->now();
   for (int64_t id : ids) {
     Request& R = S->reqs[id];
@@ -341,6 +345,9 @@ appga_status retire(appga_server* S, Pool* P) {
   }
   const int K = (int)slots.size();
   if (K == 0) return APPGA_OK;
+  // a slot stopped by the test in the last pixel phase has its result one
+  // ring entry back: move it into the current entry first
+  CK(launch_resolve_rollback(P->fa, s));
   for (int k = 0; k < K; ++k) P->h_ids[2 * Kp + k] = slots[k];
   CK(cudaMemcpyAsync(P->d_ids + 2 * Kp, P->h_ids + 2 * Kp, K * sizeof(int),
                      cudaMemcpyHostToDevice, s));

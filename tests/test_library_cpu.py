@@ -65,7 +65,8 @@ def test_struct_layouts_match_c_compiler(lib, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = [appga.appga_params, appga.appga_stats, appga.appga_matrix_info,
-               appga.appga_batch_tuning, appga.appga_server_config, appga.appga_request_stats,
+               appga.appga_batch_tuning, appga.appga_fom, appga.appga_server_config,
+               appga.appga_request_stats,
                appga.appga_server_summary]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "appga_server.h"',
              "int main(void) {"]
@@ -84,6 +85,13 @@ def test_struct_layouts_match_c_compiler(lib, tmp_path):
         assert int(got[st.__name__]) == ctypes.sizeof(st), st.__name__
         for f, _ in st._fields_:
             assert int(got[f"{st.__name__}.{f}"]) == getattr(st, f).offset, (st.__name__, f)
+
+
+def test_nofv_host(lib):
+    from paper_2409_13344_gb300 import appga as A
+    assert A.appga_nofv(5.0, 5.0, 1.0) == 1.0
+    assert A.appga_nofv(1.0, 5.0, 1.0) == 0.0
+    assert A.appga_nofv(3.0, 5.0, 1.0) == 0.5
 
 
 def test_server_config_default(lib):
