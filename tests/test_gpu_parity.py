@@ -490,3 +490,20 @@ def test_full_size_5e6_beta1_objective(A, ctx, m256, omega):
     phi_ref = prob.objective(ref.f, 0.1, 0.05, 1e-3)
     assert abs(st.phi - phi_ref) <= 1e-9 * abs(phi_ref)
     assert rel_l2(f, ref.f) <= 1e-3
+
+
+def test_largest_geometry_single_slice_sampled(A, ctx):
+    # 512^2, 360 x 731 (120.2M nnz): the largest workload geometry through the
+    # single-slice solver; a few maps against the FP64 oracle, with the
+    # objective tracked
+    geom, Amat, sl = problem("512", counts=1e6, phantom="lesions")
+    mat = A.Matrix(ctx, Amat, geom.n, geom.n_angles)
+    try:
+        f, st = run_gpu(A, ctx, mat, sl, max_iters=4, omega=1.0, track_objective=1)
+        prob, ref = run_oracle(geom, Amat, sl, max_iters=4, omega=1.0)
+        assert st.iters == 4
+        assert rel_l2(f, ref.f) <= 1e-5
+        phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+        assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+    finally:
+        mat.close()
