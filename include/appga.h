@@ -314,6 +314,37 @@ appga_status appga_objective_noalloc(appga_ctx* ctx, const appga_matrix* mat, co
                                      const float* g, const float* gamma,
                                      const appga_params* params, double* phi_out, void* stream);
 
+/* ------------------------------------------------------------------ AFPPA
+ * appga_afppa_reconstruct: the accelerated fixed-point proximity algorithm
+ * for the non-smooth HOITV model F(f) + lam1 sum ||(B1 f)_i|| + lam2 sum
+ * ||(B2 f)_i|| + iota(f) (Eq. model:HOTV), the paper's extension of the GN
+ * momentum (Sec. 4.4):
+ *   f~ = f^k + theta_k (f^k - f^{k-1}), b~, c~ likewise,
+ *   f^{k+1} = max(f~ - P (grad F(f~) + B1^T b~ + B2^T c~), 0),
+ *   b^{k+1} = rho1 (I - prox_{(lam1/rho1)||.||})(b~/rho1 + B1 (2 f^{k+1} - f~)),
+ *   c^{k+1} = rho2 (I - prox_{(lam2/rho2)||.||})(c~/rho2 + B2 (2 f^{k+1} - f~)),
+ * with P = beta diag(f^k / Lambda) (Eq. EM), rho1 = 1/(2*8*p_max),
+ * rho2 = 1/(2*64*p_max) from the largest entry of P each step, duals starting
+ * at zero, and f^0 = f^1 = f_init (NULL: TMC * 1_disk).  params: lambda1,
+ * lambda2, beta, omega, a, b, momentum (APPGA_MOMENTUM_NONE gives FPPA),
+ * max_iters, precond_freeze_iter and a_precision are used; eps and
+ * track_objective are not; rel_obj_tol must be 0 (the run makes max_iters
+ * maps).  f_out: float[d]; b_out: float[2][d] and c_out: float[4][d] (field-
+ * major, each may be NULL) receive the last duals; stats_host (may be NULL)
+ * the number of maps, RE = ||f^{K+1} - f^K|| / ||f^{K+1}|| in FP64, the last
+ * rho1/rho2 and the guarded-bin count.  Synchronises. */
+typedef struct {
+  int32_t iters;
+  int32_t flags;          /* APPGA_FLAG_* sticky device flags */
+  int64_t guard_hits;
+  double re;              /* relative change of the last map */
+  double rho1, rho2;      /* dual step sizes of the last step */
+} appga_afppa_stats;
+appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matrix* mat, const float* g,
+                                     const float* gamma, const float* f_init,
+                                     const appga_params* params, float* f_out, float* b_out,
+                                     float* c_out, appga_afppa_stats* stats_host, void* stream);
+
 /* ------------------------------------------------------- figures of merit
  * The comparison metrics of Sec. 4.1, for evaluating reconstructions.
  * appga_figures_of_merit: f, f_true: float[d] device images; roi_h, roi_b:

@@ -73,6 +73,13 @@ class appga_batch_tuning(ctypes.Structure):
     ]
 
 
+class appga_afppa_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32), ("flags", ctypes.c_int32), ("guard_hits", ctypes.c_int64),
+        ("re", ctypes.c_double), ("rho1", ctypes.c_double), ("rho2", ctypes.c_double),
+    ]
+
+
 class appga_fom(ctypes.Structure):
     _fields_ = [
         ("mse", ctypes.c_double), ("psnr", ctypes.c_double), ("rc", ctypes.c_double),
@@ -158,6 +165,8 @@ SIGNATURES = {
                                               ctypes.POINTER(appga_batch_tuning)]),
     "appga_batch_schedule_get": (ctypes.c_int, [_P, ctypes.POINTER(appga_batch_tuning)]),
     "appga_batch_schedule_set": (ctypes.c_int, [_P, ctypes.POINTER(appga_batch_tuning)]),
+    "appga_afppa_reconstruct": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(appga_params),
+                                               _P, _P, _P, ctypes.POINTER(appga_afppa_stats), _P]),
     "appga_figures_of_merit": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _D,
                                               ctypes.POINTER(appga_fom), _P]),
     "appga_nofv": (_D, [_D, _D, _D]),
@@ -381,6 +390,17 @@ def appga_batch_schedule_get(mat, K: int, a_precision: int = 0) -> appga_batch_t
 def appga_batch_schedule_set(mat, tuning: appga_batch_tuning):
     _check(load_library().appga_batch_schedule_set(mat, ctypes.byref(tuning)),
            "appga_batch_schedule_set")
+
+
+def appga_afppa_reconstruct(ctx, mat, g, gamma, f_init, params, f_out, b_out=None, c_out=None,
+                            stream=None) -> appga_afppa_stats:
+    """AFPPA for the non-smooth HOITV model (see appga.h); device buffers."""
+    st = appga_afppa_stats()
+    _check(load_library().appga_afppa_reconstruct(ctx, mat, _ptr(g), _ptr(gamma), _ptr(f_init),
+                                                  ctypes.byref(params), _ptr(f_out), _ptr(b_out),
+                                                  _ptr(c_out), ctypes.byref(st), _stream(stream)),
+           "appga_afppa_reconstruct")
+    return st
 
 
 def appga_figures_of_merit(ctx, d, f, f_true, roi_h, roi_b, max_value, stream=None) -> appga_fom:

@@ -41,7 +41,7 @@ appga_status cuda_fail(cudaError_t e, const char* what) {
 }
 }  // namespace appga
 
-namespace {
+namespace appga {
 
 #define CK(call) APPGA_CK(call)
 
@@ -382,7 +382,9 @@ appga_status validate_inputs(appga_matrix* M, const float* g, const float* gamma
   return APPGA_OK;
 }
 
-}  // namespace
+}  // namespace appga
+
+using namespace appga;
 
 namespace appga {
 // Orders ctx->stream after the caller's stream.
@@ -677,6 +679,10 @@ appga_status appga_matrix_destroy(appga_matrix* M) {
   cudaFree(M->inv_lambda);
   cudaFree(M->inv_lambda_bf16);
   free_workspace(M->ws);
+  if (M->aw) {
+    appga::free_afppa_workspace(M->aw);
+    delete M->aw;
+  }
   if (M->bw) {
     appga::free_batch_workspace(M->bw);
     delete M->bw;

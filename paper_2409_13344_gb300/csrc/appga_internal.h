@@ -52,6 +52,12 @@ struct SolverState {
   unsigned int ticket_r;
   unsigned int ticket_aux;
   unsigned int pad1;
+  // fixed-point proximity iteration (AFPPA): theta of the step just taken,
+  // the dual step sizes from the largest preconditioner entry of that step,
+  // and that largest entry as bits (positive floats order as integers)
+  float theta_prev;
+  float rho1, rho2;
+  unsigned int pmax_bits;
 };
 
 struct IterParams {
@@ -82,6 +88,8 @@ struct FwdArgs {
   int32_t loop;        // 1: solver loop mode, 0: standalone
   int32_t want_data;   // evaluate the objective (data term; in the loop also the regulariser)
   int32_t use_bf16;
+  int32_t no_stencil;  // solver loop without the SHOITV stencil blocks (AFPPA)
+  int32_t pad_f;
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).
@@ -102,7 +110,7 @@ struct PixArgs {
   int32_t n_fwd_partial;
   IterParams ip;
   int32_t use_bf16;
-  int32_t pad;
+  int32_t want_pmax;  // also reduce the largest preconditioner entry (AFPPA step sizes)
 };
 
 // ---- launchers (kernels.cu) ----

@@ -58,6 +58,14 @@ struct BatchSchedule {
   }
 };
 
+// Dual fields of the AFPPA solver (per matrix, allocated lazily).
+struct AfppaWorkspace {
+  float* b[3] = {nullptr, nullptr, nullptr};  // [2][d] first-order duals, iterate ring
+  float* c[3] = {nullptr, nullptr, nullptr};  // [4][d] second-order duals
+  double* norms = nullptr;                    // device [2]
+  double* norms_host = nullptr;               // pinned [2]
+};
+
 // Device workspace of the batched solver for one padded batch width Kp.
 struct BatchWorkspace {
   int Kp = 0, m = 0, d = 0;
@@ -121,6 +129,7 @@ struct appga_matrix {
   long long npfov = 0;  // pixels of the initial-image disk
   appga::Workspace ws;
   appga::BatchWorkspace* bw = nullptr;  // batched workspace (one width at a time)
+  appga::AfppaWorkspace* aw = nullptr;  // AFPPA dual fields
   std::map<int, appga::BatchSchedule> tuned;  // key: padded width * 2 + BF16
 };
 
@@ -138,6 +147,15 @@ cudaError_t dalloc(T** p, size_t count, int64_t* bytes = nullptr) {
   if (e == cudaSuccess && bytes) *bytes += (int64_t)b;
   return e;
 }
+
+// Single-slice helpers shared by the solvers (api.cpp).
+appga_status ensure_workspace(appga_matrix* M);
+IterParams iter_params(const appga_params* p, bool track);
+bool bf16_requested(const appga_matrix* M, const appga_params* p);
+appga_status check_params_and_mat(appga_ctx* ctx, const appga_matrix* M, const appga_params* p);
+appga_status validate_inputs(appga_matrix* M, const float* g, const float* gamma, const float* f,
+                             cudaStream_t s);
+void free_afppa_workspace(AfppaWorkspace* aw);
 
 // Orders ctx->stream after the caller's stream / the caller's after ctx->stream.
 appga_status enter_stream(appga_ctx* ctx, void* stream);

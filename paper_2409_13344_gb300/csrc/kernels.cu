@@ -534,9 +534,9 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
 // -------------------------------------------------------------- k_pixel
 
 // EM-preconditioned projected update of pixel j (Eq. EM, Eq. cloformproiota)
-// given the back-projection bp = (A^T w)_j.
-__device__ __forceinline__ void pixel_update(const PixArgs& a, int kk, int j, float bp,
-                                             int& bad) {
+// given the back-projection bp = (A^T w)_j; returns the preconditioner entry.
+__device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, float bp,
+                                              int& bad) {
   const float* fk = a.f[kk % 3];
   const float vk = fk[j];
   const float ft = fmaf(a.st->theta_hi, vk - a.f[(kk + 2) % 3][j], vk);
@@ -553,6 +553,7 @@ __device__ __forceinline__ void pixel_update(const PixArgs& a, int kk, int j, fl
   const float xv = __fmaf_rn(-p, grad, ft);
   if (!isfinite(xv)) bad = 1;
   a.f[(kk + 1) % 3][j] = fmaxf(xv, 0.f);
+  return p;
 }
 
 template <bool BF16>
@@ -570,7 +571,13 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   float bp, unused;
   warp_rows_dot<BF16, false, PX::R, PX::PF>(a.At, j0, np, a.w, lane, slot[warp], nullptr, bp,
                                             unused, reinterpret_cast<int*>(sbnd[warp]));
-  if (lane < np) pixel_update(a, kk, j0 + lane, bp, bad);
+  float pj = 0.f;
+  if (lane < np) pj = pixel_update(a, kk, j0 + lane, bp, bad);
+  if (a.want_pmax) {
+    // largest preconditioner entry of this step (order-independent)
+    const unsigned pm = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(pj, 0.f)));
+    if (lane == 0 && pm > 0u) atomicMax(&st->pmax_bits, pm);
+  }
   warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
   // This block's share of Phi(f^kk): the forward blocks' partials b, b + G, ...
   float ph = 0.f, pl = 0.f;
@@ -596,6 +603,17 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
           return;
         }
       }
+      if (a.want_pmax) {
+        // dual step sizes of this step: rho1 = 1/(2*8*p_max), rho2 = 1/(2*64*p_max)
+        // (kept when every entry is zero: the all-zero iterate is absorbing)
+        const float pm = __uint_as_float(st->pmax_bits);
+        if (pm > 0.f) {
+          st->rho1 = (float)(1.0 / (16.0 * (double)pm));
+          st->rho2 = (float)(1.0 / (128.0 * (double)pm));
+        }
+        st->pmax_bits = 0u;
+      }
+      st->theta_prev = st->theta_hi;
       if (kk >= st->k_last) {
         st->done = 1;
         st->result_k = kk + 1;
@@ -739,7 +757,7 @@ int max_group_tickets(int m, int n) { return max_partials(m, n) / RED_GROUP + 1;
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
-  const int grid = proj_blocks<FW>(a.A.rows) + (a.loop ? st_tiles(a.n) : 0);
+  const int grid = proj_blocks<FW>(a.A.rows) + (a.loop && !a.no_stencil ? st_tiles(a.n) : 0);
   if (a.use_bf16)
     k_forward<true><<<grid, FW::THREADS, 0, s>>>(a);
   else

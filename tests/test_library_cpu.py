@@ -65,7 +65,8 @@ def test_struct_layouts_match_c_compiler(lib, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = [appga.appga_params, appga.appga_stats, appga.appga_matrix_info,
-               appga.appga_batch_tuning, appga.appga_fom, appga.appga_server_config,
+               appga.appga_batch_tuning, appga.appga_fom, appga.appga_afppa_stats,
+               appga.appga_server_config,
                appga.appga_request_stats,
                appga.appga_server_summary]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "appga_server.h"',
