@@ -447,9 +447,11 @@ def run_ours(args):
     S = 16  # library default iterations per graph replay
 
     def launches(total):
+        # per run: 8 setup launches, then per iteration the pixel kernel, its
+        # one-block finalisation and the forward kernel (whole graph replays)
         n = 0
         for it in chunks(total):
-            n += 8 + 2 * S * math.ceil(it / S)
+            n += 8 + 3 * S * math.ceil(it / S)
         return n
 
     # warm-up

@@ -380,11 +380,12 @@ appga_status appga_central_line_profile(appga_ctx* ctx, int32_t n_side, const fl
 appga_status appga_validate_csr_host(int32_t m, int32_t d, const int32_t* row_ptr_host,
                                      const int32_t* col_host, const float* val_host);
 
-/* appga_kernel_times: per-launch device time of the two iteration kernels.
+/* appga_kernel_times: device time of the two phases of an iteration.
  * Sets up a run exactly as appga_reconstruct does (f_init NULL: the initial
  * image), then launches n_iters iterations of (pixel phase, forward phase)
- * back to back on the library stream with CUDA events around every launch,
- * and returns the mean duration of each kernel in milliseconds.  The
+ * back to back on the library stream with CUDA events around every phase,
+ * and returns the mean duration of each in milliseconds (the pixel phase is
+ * the back-projection/update kernel and its one-block step finalisation).  The
  * iterate ring of the matrix workspace is overwritten.  Synchronises. */
 appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const float* g,
                                 const float* gamma, const appga_params* params, int32_t n_iters,

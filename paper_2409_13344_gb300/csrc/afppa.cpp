@@ -95,7 +95,7 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   h.done = p->max_iters == 0 ? 1 : 0;
   h.result_k = k0;
   CK(cudaMemcpyAsync(ws.st, &h, sizeof h, cudaMemcpyHostToDevice, s));
-  CK(launch_init_momentum(ws.st, k0, p->momentum, p->a, p->b, p->omega, s));
+  if ((rc = momentum_table(M, ws.st, k0, p, s)) != APPGA_OK) return rc;
 
   // y^{k0-1} = A f^{k0-1}, then the first forward phase (y^{k0}, w^{k0})
   FwdArgs init{};
@@ -143,6 +143,7 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   pa.ip = iter_params(p, false);
   pa.use_bf16 = bf16 ? 1 : 0;
   pa.want_pmax = 1;
+  pa.theta_tab = ws.theta_tab;
   DualArgs da{};
   da.n = M->n;
   da.lambda1 = (float)p->lambda1;

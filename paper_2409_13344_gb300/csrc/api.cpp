@@ -65,6 +65,7 @@ void free_workspace(Workspace& ws) {
   cudaFree(ws.partial_aux);
   cudaFree(ws.gtick);
   cudaFree(ws.scalars);
+  cudaFree(ws.theta_tab);
   cudaFree(ws.st);
   cudaFree(ws.st_scratch);
   cudaFree(ws.flag);
@@ -204,7 +205,8 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   h.phi_cur = std::numeric_limits<double>::quiet_NaN();
   h.phi_prev = h.phi_cur;
   CK(cudaMemcpyAsync(ws.st, &h, sizeof h, cudaMemcpyHostToDevice, s));
-  CK(appga::launch_init_momentum(ws.st, k0, p->momentum, p->a, p->b, p->omega, s));
+  const appga_status rc_t = momentum_table(M, ws.st, k0, p, s);
+  if (rc_t != APPGA_OK) return rc_t;
 
   // y^{k0-1} = A f^{k0-1}
   appga::FwdArgs init = fwd_args(M, bf16);
@@ -249,6 +251,7 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.gtick = ws.gtick;
   pa.fwd_partial = ws.partial_r;
   pa.n_fwd_partial = appga::forward_blocks(M->m, M->n);
+  pa.theta_tab = ws.theta_tab;
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
 
@@ -278,7 +281,8 @@ appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int
   if (p->max_iters > 0) {
     // the captured kernel arguments hold the g / gamma addresses
     const std::string key = graph_key(p, track, bf16, S) + "|" +
-                            std::to_string((uintptr_t)g) + "|" + std::to_string((uintptr_t)gamma);
+                            std::to_string((uintptr_t)g) + "|" + std::to_string((uintptr_t)gamma) +
+                            "|" + std::to_string((uintptr_t)ws.theta_tab);
     if (ws.gexec == nullptr || ws.gkey != key) {
       if (ws.gexec) {
         cudaGraphExecDestroy(ws.gexec);
@@ -359,6 +363,23 @@ appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int
   }
   if (fin.flags & APPGA_FLAG_NONFINITE)
     return fail(APPGA_ENUMERIC, "a non-finite value appeared in the iteration");
+  return APPGA_OK;
+}
+
+appga_status momentum_table(appga_matrix* M, SolverState* st, int k0, const appga_params* p,
+                            cudaStream_t s) {
+  Workspace& ws = M->ws;
+  const int need = p->max_iters + 1;
+  if (ws.theta_cap < need) {
+    cudaFree(ws.theta_tab);
+    ws.theta_tab = nullptr;
+    ws.theta_cap = 0;
+    const int cap = need < 1024 ? 1024 : need;
+    const cudaError_t e = cudaMalloc((void**)&ws.theta_tab, (size_t)cap * sizeof(ThetaEntry));
+    if (e != cudaSuccess) return cuda_fail(e, "momentum table");
+    ws.theta_cap = cap;
+  }
+  CK(launch_theta_table(st, ws.theta_tab, k0, p->max_iters, p->momentum, p->a, p->b, p->omega, s));
   return APPGA_OK;
 }
 

@@ -60,6 +60,12 @@ struct SolverState {
   unsigned int pmax_bits;
 };
 
+// One momentum scalar of a run: the FP64 value and its double-float split.
+struct ThetaEntry {
+  double v;
+  float hi, lo;
+};
+
 struct IterParams {
   float lambda1, lambda2, eps, beta;
   double omega, a, b, rel_tol;
@@ -108,6 +114,9 @@ struct PixArgs {
   // (ip.track): reduced here, where the stopping test runs
   const float2* fwd_partial;
   int32_t n_fwd_partial;
+  // theta_{k0+i} of the run (launch_theta_table); NULL for a standalone
+  // update, which then has no step to finalise
+  const ThetaEntry* theta_tab;
   IterParams ip;
   int32_t use_bf16;
   int32_t want_pmax;  // also reduce the largest preconditioner entry (AFPPA step sizes)
@@ -130,8 +139,9 @@ cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float
                             cudaStream_t s);
 cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, const float* f,
                                    int d, int* flag, cudaStream_t s);
-cudaError_t launch_init_momentum(SolverState* st, int k0, int momentum, double a, double b,
-                                 double omega, cudaStream_t s);
+// theta_{k0+i}, i = 0..n, into tab and theta_{k0} into the state
+cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
+                               double a, double b, double omega, cudaStream_t s);
 long long disk_pixels(int n);
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
                                  long long npfov, float2* partial, unsigned int* gtick,

@@ -28,6 +28,8 @@ struct Workspace {
   float2* partial_aux = nullptr;
   unsigned int* gtick = nullptr;  // group tickets of the grid reductions
   double* scalars = nullptr;      // device doubles for standalone results
+  ThetaEntry* theta_tab = nullptr;  // momentum scalars of the current run
+  int theta_cap = 0;                // entries of theta_tab
   SolverState* st = nullptr;
   SolverState* st_scratch = nullptr;
   SolverState* st_host = nullptr;  // pinned
@@ -150,6 +152,10 @@ cudaError_t dalloc(T** p, size_t count, int64_t* bytes = nullptr) {
 
 // Single-slice helpers shared by the solvers (api.cpp).
 appga_status ensure_workspace(appga_matrix* M);
+// theta_{k0+i}, i <= max_iters, of a run into ws.theta_tab (grown as needed)
+// and theta_{k0} into the state st.
+appga_status momentum_table(appga_matrix* M, SolverState* st, int k0, const appga_params* p,
+                            cudaStream_t s);
 IterParams iter_params(const appga_params* p, bool track);
 bool bf16_requested(const appga_matrix* M, const appga_params* p);
 appga_status check_params_and_mat(appga_ctx* ctx, const appga_matrix* M, const appga_params* p);

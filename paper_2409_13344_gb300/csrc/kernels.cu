@@ -421,11 +421,15 @@ __host__ __device__ __forceinline__ int proj_blocks(int rows) {
 __device__ double gn_t_dev(int k, double a, double b, double omega) {
   return a * pow((double)k, omega) + b;
 }
-__device__ void set_theta(SolverState* st, double theta) {
-  st->theta = theta;
-  const float h = (float)theta;
-  st->theta_hi = h;
-  st->theta_lo = (float)(theta - (double)h);
+__device__ __forceinline__ void put_theta(ThetaEntry* e, double theta) {
+  e->v = theta;
+  e->hi = (float)theta;
+  e->lo = (float)(theta - (double)e->hi);
+}
+__device__ __forceinline__ void load_theta(SolverState* st, const ThetaEntry& e) {
+  st->theta = e.v;
+  st->theta_hi = e.hi;
+  st->theta_lo = e.lo;
 }
 
 // ------------------------------------------------------------ k_forward
@@ -579,79 +583,90 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
     if (lane == 0 && pm > 0u) atomicMax(&st->pmax_bits, pm);
   }
   warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
-  // This block's share of Phi(f^kk): the forward blocks' partials b, b + G, ...
-  float ph = 0.f, pl = 0.f;
-  if (a.ip.track && threadIdx.x == 0)
-    for (int i = blockIdx.x; i < a.n_fwd_partial; i += gridDim.x) {
-      const float2 v = a.fwd_partial[i];
-      acc_add(ph, pl, v.x, v.y);
-    }
-  // Finalise the iteration in the last block: Phi(f^kk) and the stopping
-  // test, then the next index and momentum.
-  double phi = 0.0;
-  if (grid_reduce(a.partial, a.gtick, &st->ticket_p, {ph, pl}, &phi)) {
-    if (threadIdx.x == 0) {
-      if (a.ip.track) {
-        const double prev = st->phi_cur;
-        st->phi_prev = prev;
-        st->phi_cur = phi;
-        if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(phi - prev) <= a.ip.rel_tol * fabs(prev)) {
-          // f^kk is the result; the f^{kk+1} written above is not used
-          st->done = 1;
-          st->result_k = kk;
-          st->stopped_early = 1;
-          return;
-        }
-      }
-      if (a.want_pmax) {
-        // dual step sizes of this step: rho1 = 1/(2*8*p_max), rho2 = 1/(2*64*p_max)
-        // (kept when every entry is zero: the all-zero iterate is absorbing)
-        const float pm = __uint_as_float(st->pmax_bits);
-        if (pm > 0.f) {
-          st->rho1 = (float)(1.0 / (16.0 * (double)pm));
-          st->rho2 = (float)(1.0 / (128.0 * (double)pm));
-        }
-        st->pmax_bits = 0u;
-      }
-      st->theta_prev = st->theta_hi;
-      if (kk >= st->k_last) {
-        st->done = 1;
-        st->result_k = kk + 1;
-      }
-      st->k = kk + 1;
-      double th_next = 0.0;
-      if (a.ip.momentum == APPGA_MOMENTUM_GN) {
-        th_next = (gn_t_dev(kk, a.ip.a, a.ip.b, a.ip.omega) - 1.0) /
-                  gn_t_dev(kk + 1, a.ip.a, a.ip.b, a.ip.omega);
-      } else if (a.ip.momentum == APPGA_MOMENTUM_NESTEROV) {
-        const double t = st->t_cur;
-        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        th_next = (t - 1.0) / tn;
-        st->t_cur = tn;
-      }
-      set_theta(st, th_next);
-    }
-  }
 }
 
-// theta_{k0} and t_{k0} of the first iteration of a run, with the same device
-// arithmetic the pixel kernel uses for later indices (so a resumed run
-// replays an uninterrupted one bit for bit).
-__global__ void k_init_momentum(SolverState* st, int k0, int momentum, double a, double b,
-                                double omega) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double theta = 0.0, t = 1.0;
-  if (momentum == APPGA_MOMENTUM_GN) {
-    theta = (gn_t_dev(k0 - 1, a, b, omega) - 1.0) / gn_t_dev(k0, a, b, omega);
-  } else if (momentum == APPGA_MOMENTUM_NESTEROV) {
-    for (int k = 1; k <= k0; ++k) {  // t_0 = 1
-      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-      theta = (t - 1.0) / tn;
-      t = tn;
+// Finalises a step after the pixel phase, in one block (so the pixel blocks
+// end without a grid-wide ticket): Phi(f^kk) from the forward phase's block
+// partials in a fixed order and the stopping test, the AFPPA dual step sizes,
+// then the next index and its momentum scalar from the run's table.
+constexpr int FIN_THREADS = 512;
+constexpr int FIN_BATCH = 8;  // independent loads in flight per thread
+__global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
+  SolverState* st = a.st;
+  if (st->done) return;  // uniform over the block
+  const int kk = st->k;
+  df phi = {0.f, 0.f};
+  if (a.ip.track) {
+    float h = 0.f, l = 0.f;
+    for (int i0 = 0; i0 < a.n_fwd_partial; i0 += FIN_THREADS * FIN_BATCH) {
+      float2 v[FIN_BATCH];
+#pragma unroll
+      for (int u = 0; u < FIN_BATCH; ++u) {
+        const int i = i0 + u * FIN_THREADS + threadIdx.x;
+        v[u] = i < a.n_fwd_partial ? a.fwd_partial[i] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < FIN_BATCH; ++u) acc_add(h, l, v[u].x, v[u].y);
+    }
+    phi = block_sum_acc(h, l);
+  }
+  if (threadIdx.x != 0) return;
+  if (a.ip.track) {
+    const double cur = (double)phi.hi + (double)phi.lo;
+    const double prev = st->phi_cur;
+    st->phi_prev = prev;
+    st->phi_cur = cur;
+    if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(cur - prev) <= a.ip.rel_tol * fabs(prev)) {
+      // f^kk is the result; the f^{kk+1} the pixel phase wrote is not used
+      st->done = 1;
+      st->result_k = kk;
+      st->stopped_early = 1;
+      return;
     }
   }
-  set_theta(st, theta);
-  st->t_cur = t;
+  if (a.want_pmax) {
+    // dual step sizes of this step: rho1 = 1/(2*8*p_max), rho2 = 1/(2*64*p_max)
+    // (kept when every entry is zero: the all-zero iterate is absorbing)
+    const float pm = __uint_as_float(st->pmax_bits);
+    if (pm > 0.f) {
+      st->rho1 = (float)(1.0 / (16.0 * (double)pm));
+      st->rho2 = (float)(1.0 / (128.0 * (double)pm));
+    }
+    st->pmax_bits = 0u;
+  }
+  st->theta_prev = st->theta_hi;
+  if (kk >= st->k_last) {
+    st->done = 1;
+    st->result_k = kk + 1;
+  }
+  st->k = kk + 1;
+  load_theta(st, a.theta_tab[kk + 1 - st->k0]);  // kk + 1 <= k_last + 1
+}
+
+// Momentum scalars of a whole run, tab[i] = theta_{k0+i} for i <= n, in
+// FP64: Eq. GNtheta with one thread per index, or Nesterov's recursion
+// t_k = (1 + sqrt(1 + 4 t_{k-1}^2)) / 2 from t_0 = 1 in one thread; and
+// theta_{k0} into the state.  Precomputed because an FP64 pow() in the
+// per-step finalisation costs several microseconds on this part.  A resumed
+// run computes the same values, so it replays an uninterrupted one bit for bit.
+__global__ void k_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
+                              double a, double b, double omega) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (momentum == APPGA_MOMENTUM_NESTEROV) {
+    if (i != 0) return;
+    double t = 1.0;
+    for (int k = 1; k <= k0 + n; ++k) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+      if (k >= k0) put_theta(&tab[k - k0], (t - 1.0) / tn);
+      t = tn;
+    }
+  } else if (i <= n) {
+    const int k = k0 + i;
+    put_theta(&tab[i], momentum == APPGA_MOMENTUM_GN
+                           ? (gn_t_dev(k - 1, a, b, omega) - 1.0) / gn_t_dev(k, a, b, omega)
+                           : 0.0);
+  }
+  if (i == 0) load_theta(st, tab[0]);
 }
 
 // Standalone back-projection (step a3): out = A^T w.
@@ -771,6 +786,9 @@ cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
     k_pixel<true><<<grid, PX::THREADS, 0, s>>>(a);
   else
     k_pixel<false><<<grid, PX::THREADS, 0, s>>>(a);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.theta_tab == nullptr) return e;
+  k_finalize<<<1, FIN_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -803,9 +821,10 @@ cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_momentum(SolverState* st, int k0, int momentum, double a, double b,
-                                 double omega, cudaStream_t s) {
-  k_init_momentum<<<1, 32, 0, s>>>(st, k0, momentum, a, b, omega);
+cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
+                               double a, double b, double omega, cudaStream_t s) {
+  const int threads = 256, blocks = (n + 1 + threads - 1) / threads;
+  k_theta_table<<<blocks, threads, 0, s>>>(st, tab, k0, n, momentum, a, b, omega);
   return cudaGetLastError();
 }
 
