@@ -108,6 +108,7 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   init.st = ws.st_scratch;
   init.partial = ws.partial_aux;
   init.gtick = ws.gtick;
+  init.solver_acc = 1;
   init.n = M->n;
   CK(launch_forward(init, s));
   FwdArgs fa{};

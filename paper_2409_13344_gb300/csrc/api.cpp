@@ -219,6 +219,7 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   init.partial = ws.partial_aux;
   init.gtick = ws.gtick;
   init.loop = 0;
+  init.solver_acc = 1;
   init.n = M->n;
   CK(appga::launch_forward(init, s));
 

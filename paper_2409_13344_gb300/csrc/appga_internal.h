@@ -95,7 +95,7 @@ struct FwdArgs {
   int32_t want_data;   // evaluate the objective (data term; in the loop also the regulariser)
   int32_t use_bf16;
   int32_t no_stencil;  // solver loop without the SHOITV stencil blocks (AFPPA)
-  int32_t pad_f;
+  int32_t solver_acc;  // 1: accumulate y as the solver loop does, also when loop == 0
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).

@@ -1,20 +1,23 @@
 // Single-slice CUDA kernels of the APPGA hot path (sm_103a).
 //
-//   k_forward : y = A f^k (double-float accumulation), y~ = y + theta_k (y - y^{k-1})
-//               (the projection of f~^k by linearity), w = 1 - g / max(y~ + gamma,
-//               kappa gamma), data term of the objective; in the solver loop
-//               the same launch also runs the SHOITV stencil of
-//               f~^k = f^k + theta_k (f^k - f^{k-1}) (B^T grad phi~(B f~^k)) and the
-//               regulariser term of Phi(f^k), leaving per-block objective
-//               partials (steps a0, a1, a2, a4, a6; Sec. 2.2, Eq. FidelityTerm,
-//               Eq. gradenvL2, Eq. def:phi)
-//   k_pixel   : grad F = A^T w through the transposed CSR (no atomics) and the
-//               EM-preconditioned projected update f^{k+1} = max(f~ - beta
-//               (f^k / Lambda)(grad F + B^T grad phi~), 0); its last block
-//               sums the forward phase's objective partials into Phi(f^k), runs
-//               the stopping test, and sets the next index and the FP64
-//               momentum scalar (steps a3, a5, a6; Eq. APPGAiter, Eq. EM,
-//               Eq. GNtheta)
+//   k_forward  : y = A f^k, y~ = y + theta_k (y - y^{k-1}) (the projection of
+//                f~^k by linearity), w = 1 - g / max(y~ + gamma, kappa gamma),
+//                data term of the objective; in the solver loop the same launch
+//                also runs the SHOITV stencil of f~^k = f^k + theta_k (f^k -
+//                f^{k-1}) (B^T grad phi~(B f~^k)) and the regulariser term of
+//                Phi(f^k), leaving per-block objective partials (steps a0, a1,
+//                a2, a4, a6; Sec. 2.2, Eq. FidelityTerm, Eq. gradenvL2,
+//                Eq. def:phi).  y is accumulated in FP32 in the solver loop and
+//                in double-float by the stand-alone projection and objective.
+//   k_pixel    : grad F = A^T w through the transposed CSR (no atomics) and the
+//                EM-preconditioned projected update f^{k+1} = max(f~ - beta
+//                (f^k / Lambda)(grad F + B^T grad phi~), 0) (steps a3, a5;
+//                Eq. APPGAiter, Eq. EM)
+//   k_finalize : one block: sums the forward phase's objective partials into
+//                Phi(f^k) in a fixed order, runs the stopping test, advances
+//                the iteration index and loads the next momentum scalar from
+//                the FP64 table k_theta_table fills once per run (step a6;
+//                Eq. GNtheta)
 //
 // Projector layout: a warp owns R consecutive CSR rows, whose row-padded
 // entries form one contiguous range, and streams it linearly in 128-entry
@@ -31,10 +34,10 @@
 // its FP32 rate, so FP64 is used only for a handful of scalars per launch.
 //
 // Kernels read the iteration index and theta from a device-resident
-// SolverState, so a captured graph of (k_pixel, k_forward) pairs replays
-// without host involvement.  Block partials (double-float pairs) are combined
-// in a fixed order (two-level ticketed reduction), so every reduction is
-// deterministic.
+// SolverState, so a captured graph of (k_pixel, k_finalize, k_forward)
+// triples replays without host involvement.  Block partials (double-float
+// pairs) are combined in a fixed order (k_finalize, or a two-level ticketed
+// reduction in the stand-alone calls), so every reduction is deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -51,7 +54,9 @@ constexpr int THREADS = 256;  // setup / reduction kernels
 // Projector launch shapes: warps per block (W), consecutive CSR rows per warp
 // (R) and 128-entry chunks of the nnz stream in flight per warp (PF), for the
 // forward projection (whose grid also runs the stencil tiles) and for the
-// transposed one.  Chosen by timing on GB300 (256^2 workload).
+// transposed one.  Chosen by timing on GB300 (256^2 workload): the forward
+// with 4 rows and 2 chunks per warp fits in 56 registers (36 warps per SM),
+// the transposed one with 8 rows and 3 chunks in 72 (28 warps per SM).
 template <int W_, int R_, int PF_>
 struct Shape {
   static constexpr int W = W_, R = R_, PF = PF_;
@@ -62,10 +67,10 @@ struct Shape {
 #define APPGA_FW_W 4
 #endif
 #ifndef APPGA_FW_RPW
-#define APPGA_FW_RPW 6
+#define APPGA_FW_RPW 4
 #endif
 #ifndef APPGA_FW_PF
-#define APPGA_FW_PF 3
+#define APPGA_FW_PF 2
 #endif
 #ifndef APPGA_PX_W
 #define APPGA_PX_W 4
@@ -102,9 +107,23 @@ using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
 #ifndef APPGA_SFIRST
 #define APPGA_SFIRST 0
 #endif
+// forward epilogue once per block (1) or once per warp (0)
+#ifndef APPGA_FEPI
+#define APPGA_FEPI 1
+#endif
+// a lane finds the row of its entry by advancing from its previous row (1)
+// or by comparing against every row start of the group (0)
+#ifndef APPGA_ROWINC
+#define APPGA_ROWINC 1
+#endif
 // row starts of a warp's group kept in shared memory instead of registers
 #ifndef APPGA_SBND
 #define APPGA_SBND 1
+#endif
+// accumulation of y = A f in the solver loop: 0 = FP32 (as the back-projection),
+// 1 = double-float per product
+#ifndef APPGA_LOOP_DF
+#define APPGA_LOOP_DF 0
 #endif
 
 constexpr int SLOT_W = 33;    // slot row stride: per-row sums read without bank conflicts
@@ -168,6 +187,15 @@ struct RowGroup {
     P1 = __shfl_sync(0xffffffffu, braw, nr);
   }
 
+  // first entry of row q of the group (q < nrows)
+  __device__ __forceinline__ int row_start(int q) const {
+#if APPGA_SBND
+    return sb[q];
+#else
+    return bnd[q];
+#endif
+  }
+
   // row (within the group) of entry p
   __device__ __forceinline__ int row(int p) const {
 #if APPGA_SBND
@@ -213,6 +241,9 @@ struct RowGroup {
     const int nchunks = (P1 - P0 + 127) >> 7;
     float hi = 0.f, lo = 0.f;
     int cur = -1;
+#if APPGA_ROWINC
+    int q = 0;  // row of this lane's current entry (entries only move forward)
+#endif
 #if APPGA_GPIPE
     // x values of the next chunk are gathered one chunk ahead, so the gather
     // latency overlaps the arithmetic of the current chunk
@@ -238,7 +269,11 @@ struct RowGroup {
           if (p + 128 < P1) xg = gather4(x, c[(u + 1) % PF]);
 #endif
           if (p < P1) {
+#if APPGA_ROWINC
+            while (q + 1 < nrows && row_start(q + 1) <= p) ++q;
+#else
             const int q = row(p);
+#endif
             if (q != cur) {
               if (cur >= 0) {
                 slot_hi[cur * SLOT_W + lane] = hi;
@@ -434,9 +469,52 @@ __device__ __forceinline__ void load_theta(SolverState* st, const ThetaEntry& e)
 
 // ------------------------------------------------------------ k_forward
 
+// Per-row epilogue of the forward phase (steps a1, a2, a6): stores y (and in
+// the loop y~ by linearity), the guarded weight w = 1 - g/den, and adds the
+// data term y - g ln(y + gamma) of the objective to (acc_hi, acc_lo).
+__device__ __forceinline__ void forward_row(const FwdArgs& a, const SolverState* st, int kk,
+                                            int row, float hi, float lo, int& hits, int& bad,
+                                            float& acc_hi, float& acc_lo) {
+  const df y = quick_renorm(hi, lo);
+  const float gam = a.gamma[row], gg = a.g[row];
+  if (a.loop) {
+    a.y[kk & 1][row] = make_float2(y.hi, y.lo);
+  } else {
+    if (a.y[0]) a.y[0][row] = make_float2(y.hi, y.lo);
+    if (a.y_out) a.y_out[row] = (double)y.hi + (double)y.lo;
+  }
+  if (a.w != nullptr) {
+    df yt = y;
+    if (a.loop) {
+      // y~ = y + theta (y - y^{k-1}): the projection of f~ by linearity
+      const float2 yp = a.y[(kk + 1) & 1][row];
+      const df th = {st->theta_hi, st->theta_lo};
+      const df dy = df_add(y, df_neg({yp.x, yp.y}));
+      yt = df_add(y, df_mul(th, dy));
+    }
+    df den = df_add_f(yt, gam);
+    const df floor_ = df_mul_f({c_kappa[0], c_kappa[1]}, gam);  // kappa * gamma
+    if (df_add(den, df_neg(floor_)).hi < 0.f) {
+      den = floor_;
+      ++hits;
+    }
+    // w = 1 - g/den = (den - g)/den, numerator in double-float so the
+    // weight keeps its relative accuracy when den ~ g
+    const float wv = __fdiv_rn(df_to_f(df_add_f(den, -gg)), df_to_f(den));
+    a.w[row] = wv;
+    if (!isfinite(wv)) bad = 1;
+  }
+  if (!isfinite(y.hi)) bad = 1;
+  if (a.want_data) {
+    // data term y - g ln(y + gamma) (Eq. FidelityTerm), double-float
+    const df term = df_add(y, df_neg(df_mul_f(df_log(df_add_f(y, gam)), gg)));
+    acc_add(acc_hi, acc_lo, term.hi, term.lo);
+  }
+}
+
 // Blocks [0, proj_blocks<FW>(m)) project rows; in the solver loop the blocks
 // after them run the stencil tiles.
-template <bool BF16>
+template <bool BF16, bool DFA>
 __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   __shared__ union {
     struct {
@@ -467,47 +545,25 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     const int row0 = pb * FW::ROWS + warp * FW::R;
     const int nrows = max(0, min(FW::R, m - row0));
     float hi, lo;
-    warp_rows_dot<BF16, true, FW::R, FW::PF>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
+    warp_rows_dot<BF16, DFA, FW::R, FW::PF>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
                                              sm.slot.lo[warp], hi, lo,
                                              reinterpret_cast<int*>(sm.slot.bnd[warp]));
-    if (lane < nrows) {
-      const int row = row0 + lane;
-      const df y = quick_renorm(hi, lo);
-      const float gam = a.gamma[row], gg = a.g[row];
-      if (a.loop) {
-        a.y[kk & 1][row] = make_float2(y.hi, y.lo);
-      } else {
-        if (a.y[0]) a.y[0][row] = make_float2(y.hi, y.lo);
-        if (a.y_out) a.y_out[row] = (double)y.hi + (double)y.lo;
-      }
-      if (a.w != nullptr) {
-        df yt = y;
-        if (a.loop) {
-          // y~ = y + theta (y - y^{k-1}): the projection of f~ by linearity
-          const float2 yp = a.y[(kk + 1) & 1][row];
-          const df th = {st->theta_hi, st->theta_lo};
-          const df dy = df_add(y, df_neg({yp.x, yp.y}));
-          yt = df_add(y, df_mul(th, dy));
-        }
-        df den = df_add_f(yt, gam);
-        const df floor_ = df_mul_f({c_kappa[0], c_kappa[1]}, gam);  // kappa * gamma
-        if (df_add(den, df_neg(floor_)).hi < 0.f) {
-          den = floor_;
-          ++hits;
-        }
-        // w = 1 - g/den = (den - g)/den, numerator in double-float so the
-        // weight keeps its relative accuracy when den ~ g
-        const float wv = __fdiv_rn(df_to_f(df_add_f(den, -gg)), df_to_f(den));
-        a.w[row] = wv;
-        if (!isfinite(wv)) bad = 1;
-      }
-      if (!isfinite(y.hi)) bad = 1;
-      if (a.want_data) {
-        // data term y - g ln(y + gamma) (Eq. FidelityTerm), double-float
-        const df term = df_add(y, df_neg(df_mul_f(df_log(df_add_f(y, gam)), gg)));
-        acc_add(acc_hi, acc_lo, term.hi, term.lo);
+#if APPGA_FEPI
+    // the block's row sums go to warp 0, so the double-float epilogue (with
+    // the logarithm of the data term) runs once per block, not once per warp
+    __shared__ float2 ysum[FW::ROWS];
+    if (lane < nrows) ysum[warp * FW::R + lane] = make_float2(hi, lo);
+    __syncthreads();
+    if (warp == 0) {
+      const int brow0 = pb * FW::ROWS, bn = min(FW::ROWS, m - brow0);
+      for (int q = lane; q < bn; q += 32) {
+        const float2 v = ysum[q];
+        forward_row(a, st, kk, brow0 + q, v.x, v.y, hits, bad, acc_hi, acc_lo);
       }
     }
+#else
+    if (lane < nrows) forward_row(a, st, kk, row0 + lane, hi, lo, hits, bad, acc_hi, acc_lo);
+#endif
   } else {
     // SHOITV gradient at f~^kk and the regulariser of Phi(f^kk)
     const int b = sb;
@@ -590,7 +646,10 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
 // partials in a fixed order and the stopping test, the AFPPA dual step sizes,
 // then the next index and its momentum scalar from the run's table.
 constexpr int FIN_THREADS = 512;
-constexpr int FIN_BATCH = 8;  // independent loads in flight per thread
+#ifndef APPGA_FIN_BATCH
+#define APPGA_FIN_BATCH 12
+#endif
+constexpr int FIN_BATCH = APPGA_FIN_BATCH;  // independent loads in flight per thread
 __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
   SolverState* st = a.st;
   if (st->done) return;  // uniform over the block
@@ -773,10 +832,21 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   cudaError_t e = ensure_tables();
   if (e != cudaSuccess) return e;
   const int grid = proj_blocks<FW>(a.A.rows) + (a.loop && !a.no_stencil ? st_tiles(a.n) : 0);
-  if (a.use_bf16)
-    k_forward<true><<<grid, FW::THREADS, 0, s>>>(a);
-  else
-    k_forward<false><<<grid, FW::THREADS, 0, s>>>(a);
+  // the solver (its loop and its projection of the previous iterate)
+  // accumulates y in FP32; the stand-alone projection and objective calls
+  // in double-float
+  const bool dfa = (a.loop || a.solver_acc) ? APPGA_LOOP_DF != 0 : true;
+  if (a.use_bf16) {
+    if (dfa)
+      k_forward<true, true><<<grid, FW::THREADS, 0, s>>>(a);
+    else
+      k_forward<true, false><<<grid, FW::THREADS, 0, s>>>(a);
+  } else {
+    if (dfa)
+      k_forward<false, true><<<grid, FW::THREADS, 0, s>>>(a);
+    else
+      k_forward<false, false><<<grid, FW::THREADS, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
