@@ -244,12 +244,50 @@ appga_status appga_reconstruct_host(appga_ctx* ctx, const appga_matrix* mat, con
  * (phi is the FP64 objective of each result).  Every slice runs `params`
  * for max_iters maps or until its own stopping test fires; a slice's result
  * does not depend on the other slices in the batch.  The projector
- * accumulation is FP32 (the single-slice path accumulates in double-float),
- * so results agree with appga_reconstruct to FP32 rounding.  Synchronises. */
+ * accumulation is FP32 in a different order from the single-slice path, so
+ * results agree with appga_reconstruct to FP32 rounding.  Synchronises. */
 appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, int32_t K,
                                        const float* g, const float* gamma, const float* f_init,
                                        const appga_params* params, float* f_out,
                                        appga_stats* stats_host, void* stream);
+
+/* ------------------------------------------------------------ 3-D SHOITV
+ * The paper states HOITV in 2-D (Sec. 2.1) and refers to other work for 3-D.
+ * These calls use its Kronecker generalisation: for a volume of nz slices of
+ * n x n pixels (voxel (z, r, c) at z*n*n + r*n + c, slice-major), D the
+ * paper's backward difference (zero first row) along each axis,
+ *   B1 = [Dc; Dr; Dz]  (3 components per voxel),
+ *   B2 = [-Dc^T Dc; -Dr^T Dc; -Dr^T Dr; -Dr Dc^T;          (the 2-D blocks)
+ *         -Dz^T Dz; -Dz^T Dc; -Dz Dc^T; -Dz^T Dr; -Dz Dr^T] (9 components),
+ * and phi~ = lambda1 sum s_eps(3-vector) + lambda2 sum s_eps(9-vector)
+ * (Eq. def:smoothL2).  With nz = 1 this is the 2-D SHOITV of the slice.
+ *
+ * appga_shoitv3d_grad: out = B^T grad phi~(B f) (Eq. gradenvL2 on the 3-D
+ * groups) for the volume f; f, out: float[nz][n*n] device (distinct
+ * buffers); 1 <= nz <= 128.  reg_out (device double, may be NULL): phi~(B f)
+ * in FP64 (double-float sums).  Allocates a small stream-ordered scratch
+ * when reg_out is given.  EINVAL for bad sizes or parameters (lambda >= 0,
+ * eps > 0, all finite). */
+appga_status appga_shoitv3d_grad(appga_ctx* ctx, int32_t n_side, int32_t nz, const float* f,
+                                 double lambda1, double lambda2, double eps, float* out,
+                                 double* reg_out, void* stream);
+
+/* appga_reconstruct_volume: APPGA (Eq. APPGAiter, EM preconditioner Eq. EM)
+ * on a volume of nz slices (1 <= nz <= 128) whose slices share this matrix
+ * and have their own sinograms: Phi(f) = sum_z F(f_z) + phi~(B f) with the
+ * 3-D B above.  g, gamma: float[nz][m] device; f_init: float[nz][d] or NULL
+ * (each slice's TMC * 1_disk, Sec. 4.1); f_out: float[nz][d].  One momentum
+ * sequence and one stopping test (params->rel_obj_tol on the volume's Phi)
+ * serve the whole volume.  Runs the batched SpMM kernels on the nz slices
+ * plus the 3-D stencil, under captured CUDA graphs.  stats_host (one
+ * appga_stats, may be NULL): iterations, stop flag, flags, guard hits summed
+ * over the slices, phi = the volume's FP64 Phi of the result when the
+ * objective is tracked.  EINVAL / EDOMAIN as appga_reconstruct_batched.
+ * Synchronises. */
+appga_status appga_reconstruct_volume(appga_ctx* ctx, const appga_matrix* mat, int32_t nz,
+                                      const float* g, const float* gamma, const float* f_init,
+                                      const appga_params* params, float* f_out,
+                                      appga_stats* stats_host, void* stream);
 
 /* appga_autotune_batched: picks the launch schedule of the batched kernels
  * for this matrix, batch width and precision by timing the solver itself on

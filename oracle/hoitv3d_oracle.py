@@ -52,36 +52,36 @@ N1, N2 = 3, 9  # components of the first- and second-order groups
 # 3-D difference operators
 # --------------------------------------------------------------------------
 
-def axis_differences(nz: int, n: int):
-    """Dc, Dr, Dz for a volume of nz slices of n x n pixels."""
-    Dn = difference_matrix(n)
-    Dz1 = difference_matrix(nz)
-    In = sp.identity(n, format="csr", dtype=np.float64)
-    Iz = sp.identity(nz, format="csr", dtype=np.float64)
-    Dc = sp.kron(sp.kron(Iz, In), Dn).tocsr()
-    Dr = sp.kron(sp.kron(Iz, Dn), In).tocsr()
-    Dz = sp.kron(sp.kron(Dz1, In), In).tocsr()
+def axis_differences(nz: int, nr: int, nc: Optional[int] = None):
+    """Dc, Dr, Dz for a volume of nz slices of nr x nc pixels (nc = nr when
+    not given; the solver's volumes are square in-plane, rectangular boxes
+    serve the sampled checks)."""
+    nc = nr if nc is None else nc
+    I = lambda k: sp.identity(k, format="csr", dtype=np.float64)
+    Dc = sp.kron(sp.kron(I(nz), I(nr)), difference_matrix(nc)).tocsr()
+    Dr = sp.kron(sp.kron(I(nz), difference_matrix(nr)), I(nc)).tocsr()
+    Dz = sp.kron(sp.kron(difference_matrix(nz), I(nr)), I(nc)).tocsr()
     return Dc, Dr, Dz
 
 
-def b1_matrix3(nz: int, n: int) -> sp.csr_matrix:
+def b1_matrix3(nz: int, nr: int, nc: Optional[int] = None) -> sp.csr_matrix:
     """B1 = [Dc ; Dr ; Dz]  (3 dv x dv)."""
-    Dc, Dr, Dz = axis_differences(nz, n)
+    Dc, Dr, Dz = axis_differences(nz, nr, nc)
     return sp.vstack([Dc, Dr, Dz]).tocsr()
 
 
-def b2_matrix3(nz: int, n: int) -> sp.csr_matrix:
+def b2_matrix3(nz: int, nr: int, nc: Optional[int] = None) -> sp.csr_matrix:
     """The nine second-order blocks (9 dv x dv), in the order listed above."""
-    Dc, Dr, Dz = axis_differences(nz, n)
+    Dc, Dr, Dz = axis_differences(nz, nr, nc)
     Dct, Drt, Dzt = Dc.T.tocsr(), Dr.T.tocsr(), Dz.T.tocsr()
     blocks = [-(Dct @ Dc), -(Drt @ Dc), -(Drt @ Dr), -(Dr @ Dct),
               -(Dzt @ Dz), -(Dzt @ Dc), -(Dz @ Dct), -(Dzt @ Dr), -(Dz @ Drt)]
     return sp.vstack(blocks).tocsr()
 
 
-def b_matrix3(nz: int, n: int) -> sp.csr_matrix:
+def b_matrix3(nz: int, nr: int, nc: Optional[int] = None) -> sp.csr_matrix:
     """B = [B1 ; B2]  (12 dv x dv)."""
-    return sp.vstack([b1_matrix3(nz, n), b2_matrix3(nz, n)]).tocsr()
+    return sp.vstack([b1_matrix3(nz, nr, nc), b2_matrix3(nz, nr, nc)]).tocsr()
 
 
 # --------------------------------------------------------------------------
@@ -109,12 +109,14 @@ def grad_phi_tilde3(u: np.ndarray, dv: int, lam1: float, lam2: float, eps: float
 
 
 class Regulariser3D:
-    """phi~(B f) and B^T grad phi~(B f) for volumes of nz x n x n."""
+    """phi~(B f) and B^T grad phi~(B f) for volumes of nz x nr x nc
+    (nc = nr when not given)."""
 
-    def __init__(self, nz: int, n: int):
-        self.nz, self.n = int(nz), int(n)
-        self.dv = self.nz * self.n * self.n
-        self.B = b_matrix3(self.nz, self.n)
+    def __init__(self, nz: int, nr: int, nc: Optional[int] = None):
+        self.nz, self.nr = int(nz), int(nr)
+        self.nc = self.nr if nc is None else int(nc)
+        self.dv = self.nz * self.nr * self.nc
+        self.B = b_matrix3(self.nz, self.nr, self.nc)
         self.Bt = self.B.T.tocsr()
 
     def value(self, f, lam1, lam2, eps) -> float:

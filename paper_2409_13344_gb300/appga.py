@@ -159,6 +159,10 @@ SIGNATURES = {
     "appga_reconstruct_batched": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P,
                                                  ctypes.POINTER(appga_params), _P,
                                                  ctypes.POINTER(appga_stats), _P]),
+    "appga_shoitv3d_grad": (ctypes.c_int, [_P, _I32, _I32, _P, _D, _D, _D, _P, _P, _P]),
+    "appga_reconstruct_volume": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P,
+                                                ctypes.POINTER(appga_params), _P,
+                                                ctypes.POINTER(appga_stats), _P]),
     "appga_kernel_times": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(appga_params), _I32,
                                           ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "appga_autotune_batched": (ctypes.c_int, [_P, _P, _I32, _P, _P, ctypes.POINTER(appga_params),
@@ -368,6 +372,28 @@ def appga_reconstruct_batched(ctx, mat, K, g, gamma, f_init, params, f_out, stre
                                                     st, _stream(stream)),
            "appga_reconstruct_batched")
     return list(st)
+
+
+def appga_shoitv3d_grad(ctx, n_side, nz, f, lambda1, lambda2, eps, out, reg_out=None,
+                        stream=None):
+    """3-D SHOITV gradient of the slice-major volume f ([nz][n*n]) into out;
+    reg_out (a device float64 scalar, optional) receives the regulariser."""
+    _check(load_library().appga_shoitv3d_grad(ctx, n_side, nz, _ptr(f), lambda1, lambda2, eps,
+                                              _ptr(out), _ptr(reg_out), _stream(stream)),
+           "appga_shoitv3d_grad")
+
+
+def appga_reconstruct_volume(ctx, mat, nz, g, gamma, f_init, params, f_out, stream=None):
+    """APPGA on a volume of nz slices sharing the matrix: g, gamma [nz][m],
+    f_init [nz][d] or None, f_out [nz][d] (device arrays).  Returns the
+    volume's stats."""
+    st = appga_stats()
+    _check(load_library().appga_reconstruct_volume(ctx, mat, nz, _ptr(g), _ptr(gamma),
+                                                   _ptr(f_init), ctypes.byref(params),
+                                                   _ptr(f_out), ctypes.byref(st),
+                                                   _stream(stream)),
+           "appga_reconstruct_volume")
+    return st
 
 
 def appga_autotune_batched(ctx, mat, K, g, gamma, params) -> appga_batch_tuning:

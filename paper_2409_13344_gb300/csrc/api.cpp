@@ -424,6 +424,28 @@ appga_status leave_stream(appga_ctx* ctx, void* stream) {
   CK(cudaStreamWaitEvent(us, ctx->ev_out, 0));
   return APPGA_OK;
 }
+
+appga_status data_term_on(appga_matrix* M, const float* f, const float* g, const float* gamma,
+                          bool bf16, double* dev_out, cudaStream_t s) {
+  appga_status rc = ensure_workspace(M);
+  if (rc != APPGA_OK) return rc;
+  Workspace& ws = M->ws;
+  appga::FwdArgs a = fwd_args(M, bf16);
+  a.f[0] = f;
+  a.y[0] = nullptr;
+  a.y_out = nullptr;
+  a.g = g;
+  a.gamma = gamma;
+  a.st = ws.st_scratch;
+  a.partial = ws.partial_aux;
+  a.gtick = ws.gtick;
+  a.data_out = dev_out;
+  a.loop = 0;
+  a.want_data = 1;
+  a.n = M->n;
+  CK(appga::launch_forward(a, s));
+  return APPGA_OK;
+}
 }  // namespace appga
 
 namespace {

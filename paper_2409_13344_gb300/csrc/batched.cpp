@@ -33,6 +33,8 @@ void free_batch_workspace(BatchWorkspace* bw) {
   cudaFree(bw->fpartial);
   cudaFree(bw->gtick);
   cudaFree(bw->flag);
+  cudaFree(bw->vscal);
+  cudaFreeHost(bw->vscal_host);
   cudaFreeHost(bw->slots_host);
   cudaFreeHost(bw->bst_host);
   cudaFreeHost(bw->flag_host);
@@ -47,6 +49,7 @@ int64_t batch_workspace_bytes(int m, int d, int Kp) {
   b += (int64_t)Kp * sizeof(SlotState) + sizeof(BatchState);
   b += (2 * batch_max_blocks() + ngroups + 2) * Kp * (int64_t)sizeof(float2);
   b += ngroups * (int64_t)sizeof(unsigned int) + (int64_t)sizeof(int);
+  b += (int64_t)(Kp + 2) * sizeof(double);
   return b;
 }
 
@@ -69,6 +72,8 @@ cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp) {
   if (e == cudaSuccess) e = dalloc(&b.fpartial, (size_t)maxb * Kp);
   if (e == cudaSuccess) e = dalloc(&b.gtick, (size_t)ngroups);
   if (e == cudaSuccess) e = dalloc(&b.flag, 1);
+  if (e == cudaSuccess) e = dalloc(&b.vscal, (size_t)Kp + 2);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b.vscal_host, (Kp + 2) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(b.gtick, 0, (size_t)ngroups * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(b.bst, 0, sizeof(BatchState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b.slots_host, Kp * sizeof(SlotState));
@@ -131,7 +136,7 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
 }
 
 cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
-                                cudaGraphExec_t* out) {
+                                cudaGraphExec_t* out, const Vol3Args* va) {
   *out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -139,6 +144,7 @@ cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, c
   for (int i = 0; i < S && e == cudaSuccess; ++i) {
     e = launch_bpixel(pa, s);
     if (e == cudaSuccess) e = launch_bforward(fa, s);
+    if (e == cudaSuccess && va) e = launch_stencil3d(*va, s);
   }
   const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   if (e == cudaSuccess) e = e2;
@@ -209,7 +215,7 @@ namespace {
 appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
                            const float* gamma, const float* f_init, const appga_params* params,
                            float* f_out, appga_stats* stats_host, const BatchSchedule& sch,
-                           void* stream, int min_width = 0) {
+                           void* stream, int min_width = 0, bool volume = false) {
   appga_status rc = APPGA_OK;
   const appga_matrix* mat = M;
   const int Kp = std::max(padded_width(K), min_width);
@@ -254,6 +260,7 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
   BatchState hb{};
   hb.gstep = G0;
   hb.remaining = params->max_iters > 0 ? K : 0;
+  hb.phi_tot_k = -1;
   *b.bst_host = hb;
   CK(cudaMemcpyAsync(b.bst, b.bst_host, sizeof(BatchState), cudaMemcpyHostToDevice, s));
 
@@ -261,25 +268,48 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
   BPixArgs pa;
   make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, n, b, bf16, track, sch,
                   &fa, &pa);
+  // volume: the K slots are the slices of one volume; the 3-D stencil runs
+  // in its own kernel after the forward phase and leaves its per-slice
+  // regulariser sums after the forward phase's rows; one stopping test
+  Vol3Args va{};
+  if (volume) {
+    fa.no_stencil = 1;
+    pa.joint = 1;
+    const int nfw = bforward_grid(fa);
+    va.n = n;
+    va.nz = K;
+    va.ps = Kp;
+    va.zs = 1;
+    for (int i = 0; i < 3; ++i) va.f[i] = b.f[i];
+    va.slots = b.slots;
+    va.bst = b.bst;
+    va.want_reg = track ? 1 : 0;
+    va.pstride = Kp;
+    va.gR = b.gR;
+    va.partial = b.fpartial + (size_t)nfw * Kp;
+    pa.n_fpartial = nfw + (track ? stencil3d_grid(n, K) : 0);
+  }
 
   // y^{k0-1}, then the first forward phase (w, y, stencil, Phi of f^{k0})
   BFwdArgs init = fa;
   init.mode = 1;
   CK(launch_bforward(init, s));
   CK(launch_bforward(fa, s));
+  if (volume) CK(launch_stencil3d(va, s));
 
   if (params->max_iters > 0) {
     const int S = params->graph_iters > 0 ? params->graph_iters : kBatchGraphIters;
     char key[256];
     // the graph's kernels see only the workspace, never K or the caller's buffers
-    std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%d|%d", Kp, (int)track, (int)bf16, S,
-                  sch.spmv_per_sm, sch.stencil_per_sm, sch.pixel_per_sm);
+    std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d|%d|%d|%d|%d", Kp, (int)track, (int)bf16, S,
+                  sch.spmv_per_sm, sch.stencil_per_sm, sch.pixel_per_sm, (int)volume,
+                  volume ? K : 0);
     if (b.gexec == nullptr || b.gkey != key) {
       if (b.gexec) {
         cudaGraphExecDestroy(b.gexec);
         b.gexec = nullptr;
       }
-      const cudaError_t e = capture_batch_graph(fa, pa, S, s, &b.gexec);
+      const cudaError_t e = capture_batch_graph(fa, pa, S, s, &b.gexec, volume ? &va : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "batched graph capture");
       b.gkey = key;
     }
@@ -386,6 +416,16 @@ appga_status batched_run(appga_ctx* ctx, appga_matrix* M, int32_t K, const float
 }
 
 }  // namespace
+
+appga_status volume_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
+                          const float* gamma, const float* f_init, const appga_params* params,
+                          float* f_out, void* stream) {
+  const bool bf16 = params->a_precision == APPGA_PREC_BF16 && M->has_bf16;
+  const int Kp = padded_width(K);
+  return batched_solve(ctx, M, K, g, gamma, f_init, params, f_out, nullptr,
+                       tuned_schedule(M, Kp, bf16), stream, 0, true);
+}
+
 }  // namespace appga
 
 extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat,

@@ -35,8 +35,9 @@ struct BatchState {
   int32_t gstep;      // global step: ring slot of the current iterates
   int32_t remaining;  // live slots
   int32_t flags;
-  int32_t pad;
+  int32_t phi_tot_k;  // volume mode: iterate index of phi_tot_cur (-1: none)
   unsigned int ticket_r, ticket_p, ticket_aux, pad2;
+  double phi_tot_cur, phi_tot_prev;  // volume mode: objective of the whole volume
 };
 
 struct BFwdArgs {
@@ -49,6 +50,8 @@ struct BFwdArgs {
   int32_t n_spmv_blocks;  // set by the launcher
   int32_t spmv_per_sm;    // SpMV blocks per SM (0: default); tuned by the autotuner
   int32_t stencil_per_sm; // stencil blocks per SM (0: default)
+  int32_t no_stencil;     // volume mode: the 3-D stencil runs in its own kernel
+  int32_t pad;
   float* f[3];
   float* y[2];
   float* w;
@@ -79,7 +82,32 @@ struct BPixArgs {
   const float2* fpartial;
   int32_t n_fpartial;
   int32_t track;
+  int32_t joint;  // volume mode: one stopping test on the sum of the slots' objectives
 };
+
+// 3-D SHOITV stencil (kernels_vol.cu).  Voxel (z, r, c) of a volume is at
+// (r n + c) ps + z zs.  Solver mode (bst != null): f^k and f^{k-1} are the
+// ring entries of the current step, theta, lambda and eps come from slot z;
+// stand-alone mode: f[0] is the volume, f~ = f, lam1/lam2/eps as given.
+struct Vol3Args {
+  int32_t n, nz;
+  int64_t ps, zs;
+  const float* f[3];
+  const SlotState* slots;
+  const BatchState* bst;
+  float lam1, lam2, eps;
+  int32_t want_reg;       // also the regulariser at f^k: one row of pstride
+  int32_t pstride;        // per-slice double-float sums per block in partial
+  int32_t pad;
+  float* gR;              // out: B^T grad phi~(B f~), same layout as f
+  float2* partial;        // out (want_reg): stencil3d_grid rows of pstride
+};
+int stencil3d_max_slices();
+int stencil3d_grid(int n, int nz);
+cudaError_t launch_stencil3d(const Vol3Args& a, cudaStream_t s);
+// *out = sum of rows x cols double-float pairs (row stride pstride), in FP64
+cudaError_t launch_sum_pairs(const float2* p, int rows, int cols, int pstride, double* out,
+                             cudaStream_t s);
 
 int batch_max_blocks();
 // Grid of the forward phase for these arguments (the launcher's own choice).

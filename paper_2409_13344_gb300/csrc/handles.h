@@ -87,6 +87,8 @@ struct BatchWorkspace {
   unsigned int* gtick = nullptr;
   int* flag = nullptr;
   int* flag_host = nullptr;
+  double* vscal = nullptr;       // volume objective terms: [Kp] data terms, regulariser
+  double* vscal_host = nullptr;  // pinned mirror
   cudaGraphExec_t gexec = nullptr;
   std::string gkey;
 };
@@ -106,9 +108,20 @@ BatchSchedule tuned_schedule(const appga_matrix* M, int Kp, bool bf16);
 // Slot state of a problem run with `p` from iterate index k0 (active), or an
 // empty slot that holds no problem (inactive).
 SlotState slot_from_params(const appga_params* p, int k0, bool active);
-// Captures S x (pixel update, forward phase) into an executable graph.
+// Captures S x (pixel update, forward phase[, 3-D stencil]) into an
+// executable graph; va (volume mode) adds the 3-D stencil after each forward.
 cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
-                                cudaGraphExec_t* out);
+                                cudaGraphExec_t* out, const Vol3Args* va = nullptr);
+// APPGA on a volume of K <= 128 slices sharing the matrix (the batched solver
+// in volume mode): device buffers as in appga_reconstruct_batched; on return
+// the workspace's pinned slot and batch states hold the final states.
+appga_status volume_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
+                          const float* gamma, const float* f_init, const appga_params* params,
+                          float* f_out, void* stream);
+// Data term sum_i (A f)_i - g_i ln((A f)_i + gamma_i) of one slice in FP64
+// (double-float accumulation) into the device double *dev_out.
+appga_status data_term_on(appga_matrix* M, const float* f, const float* g, const float* gamma,
+                          bool bf16, double* dev_out, cudaStream_t s);
 
 }  // namespace appga
 

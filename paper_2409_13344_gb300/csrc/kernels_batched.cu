@@ -637,6 +637,35 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
   __syncthreads();
   if (grid_reduce_slots(a.partial, a.gtick, &bs->ticket_p, r_hi, r_lo, Kp, t_hi, t_lo)) {
     __shared__ int s_rem[B_THREADS];
+    __shared__ int s_jstop;
+    if (a.joint) {
+      // volume: the slices are one problem; its objective is the sum of the
+      // slots' shares, summed in FP64 in slot order, and one test stops all
+      if (tid == 0) {
+        double tot = 0.0;
+        int kk = -1, k0 = 0;
+        double tol = 0.0;
+        for (int s = 0; s < Kp; ++s) {
+          const SlotState& sl = a.slots[s];
+          if (!sl.active || sl.done) continue;
+          tot += (double)t_hi[s] + (double)t_lo[s];
+          kk = sl.k;
+          k0 = sl.k0;
+          tol = sl.rel_tol;
+        }
+        int stop = 0;
+        if (kk >= 0 && a.track && bs->phi_tot_k != kk) {
+          const double prev = bs->phi_tot_cur;
+          const bool consecutive = bs->phi_tot_k == kk - 1;
+          bs->phi_tot_prev = prev;
+          bs->phi_tot_cur = tot;
+          bs->phi_tot_k = kk;
+          stop = tol > 0.0 && kk > k0 && consecutive && fabs(tot - prev) <= tol * fabs(prev);
+        }
+        s_jstop = stop;
+      }
+      __syncthreads();
+    }
     int rem = 0;
     for (int s = tid; s < Kp; s += blockDim.x) {
       SlotState& sl = a.slots[s];
@@ -652,7 +681,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
         sl.phi_prev = prev;
         sl.phi_cur = phi;
         sl.phi_k = sl.k;
-        if (sl.rel_tol > 0.0 && sl.k > sl.k0 && consecutive &&
+        if (!a.joint && sl.rel_tol > 0.0 && sl.k > sl.k0 && consecutive &&
             fabs(phi - prev) <= sl.rel_tol * fabs(prev)) {
           // f^k is the result; the f^{k+1} written above is not used
           sl.done = 1;
@@ -661,6 +690,14 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
           sl.rollback = 1;
           continue;
         }
+      }
+      if (a.joint && s_jstop) {
+        // the volume's test fired: f^k of every slice is the result
+        sl.done = 1;
+        sl.result_k = sl.k;
+        sl.stopped_early = 1;
+        sl.rollback = 1;
+        continue;
       }
       if (sl.k >= sl.k_last) {
         sl.done = 1;
@@ -830,7 +867,7 @@ int bforward_grid_n(const BFwdArgs& a, int* n_spmv) {
   const int cap = sms * clamp_per_sm(a.spmv_per_sm, kSpmvPerSm);
   if (nsp > cap) nsp = cap;
   int nst = 0;
-  if (a.mode != 1) {
+  if (a.mode != 1 && !a.no_stencil) {
     // equal tile counts per stencil block
     const int tiles = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R);
     const int scap = sms * clamp_per_sm(a.stencil_per_sm, kStencilPerSm);

@@ -278,6 +278,59 @@ def make_slice(A: sp.csr_matrix, geom: Geometry, counts: float, seed: int,
     return Slice(f_true=f, g=g, gamma=gamma.astype(np.float32), counts=float(counts))
 
 
+def ellipsoid_volume(n: int, nz: int, rng: np.random.Generator) -> np.ndarray:
+    """Random-ellipsoid volume, FP64 [nz, N*N], unscaled (body activity 1):
+    a body ellipsoid that every slice cuts (z semi-axis longer than half the
+    stack), 5-10 inner ellipsoids with activity U(0, 4), slice thickness one
+    pixel."""
+    x, y = _pixel_centres(n)
+    R = n / 2.0
+    zc = np.arange(nz, dtype=np.float64) + 0.5 - nz / 2.0
+    vol = np.zeros((nz, n, n))
+
+    def ellipsoid(cx, cy, cz, ax, ay, az, ang):
+        ca, sa = math.cos(ang), math.sin(ang)
+        xr = (x - cx) * ca + (y - cy) * sa
+        yr = -(x - cx) * sa + (y - cy) * ca
+        inplane = (xr / ax) ** 2 + (yr / ay) ** 2
+        return inplane[None, :, :] + ((zc - cz) / az)[:, None, None] ** 2 <= 1.0
+
+    body = ellipsoid(0.0, 0.0, 0.0, rng.uniform(0.80, 0.95) * R, rng.uniform(0.60, 0.85) * R,
+                     rng.uniform(0.6, 1.0) * nz + 1.0, rng.uniform(0.0, math.pi))
+    vol[body] = 1.0
+    for _ in range(int(rng.integers(5, 11))):
+        rad = 0.7 * R * math.sqrt(rng.uniform())
+        th = rng.uniform(0.0, 2 * math.pi)
+        m = ellipsoid(rad * math.cos(th), rad * math.sin(th), rng.uniform(-0.4, 0.4) * nz,
+                      rng.uniform(0.05, 0.4) * R, rng.uniform(0.05, 0.4) * R,
+                      rng.uniform(0.1, 0.5) * nz + 1.0, rng.uniform(0.0, math.pi)) & body
+        vol[m] = rng.uniform(0.0, 4.0)
+    return vol.reshape(nz, n * n)
+
+
+@dataclasses.dataclass
+class Volume:
+    f_true: np.ndarray   # FP64 [nz, d]
+    g: np.ndarray        # FP32 [nz, m] Poisson counts, slice by slice
+    gamma: np.ndarray    # FP32 [nz, m] background mean (uniform over the volume)
+    counts: float        # total expected counts over the volume
+
+
+def make_volume(A: sp.csr_matrix, geom: Geometry, nz: int, counts: float, seed: int) -> Volume:
+    """One seeded volume of nz slices sharing A: ellipsoid phantom scaled so
+    the volume's expected counts are `counts`, gamma = 10 % of the mean
+    projection over the volume, g_z ~ Poisson(A f_z + gamma) per slice."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = ellipsoid_volume(geom.n, nz, rng)
+    A64 = A.astype(np.float64)
+    proj = (A64 @ f.T).T
+    f = f * (counts / (1.1 * proj.sum()))
+    proj = (A64 @ f.T).T
+    gamma = np.full((nz, geom.m), 0.1 * proj.mean())
+    g = rng.poisson(proj + gamma).astype(np.float32)
+    return Volume(f_true=f, g=g, gamma=gamma.astype(np.float32), counts=float(counts))
+
+
 def log_uniform_counts(rng: np.random.Generator, lo: float, hi: float, k: int) -> np.ndarray:
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size=k))
 

@@ -184,3 +184,13 @@ def test_volume_objective_decreases_and_stops():
     prev = abs(res.phi[-2] - res.phi[-3]) / abs(res.phi[-3])
     assert last <= 1e-6 < prev
     assert res.phi[-1] < res.phi[0]
+
+
+def test_rectangular_boxes_match_voxelwise_definition():
+    # the same twelve fields on a non-square box (used for sampled checks)
+    rng = np.random.default_rng(12)
+    V = rng.standard_normal((3, 4, 6))
+    u = H.b_matrix3(3, 4, 6) @ V.reshape(-1)
+    ref = _fields_by_loops(V)
+    for q in range(12):
+        np.testing.assert_allclose(u[q * V.size:(q + 1) * V.size], ref[q], rtol=0, atol=1e-12)

@@ -69,3 +69,17 @@ def test_phantoms():
     assert f.shape == (4096,) and f.min() >= 0 and f.max() > 0
     u = W.uniform_phantom(256).reshape(256, 256)
     assert set(np.unique(u)) == {0.0, 1.0, 4.0}
+
+
+def test_make_volume_seeded_and_positive():
+    geom = W.GEOMETRIES["64"]
+    A = W.system_matrix("64")
+    v1 = W.make_volume(A, geom, 7, 5e5, W.seed_for(6, 0))
+    v2 = W.make_volume(A, geom, 7, 5e5, W.seed_for(6, 0))
+    assert np.array_equal(v1.g, v2.g) and np.array_equal(v1.f_true, v2.f_true)
+    assert v1.g.shape == (7, geom.m) and v1.gamma.shape == (7, geom.m)
+    assert np.all(v1.gamma > 0) and np.all(v1.g >= 0)
+    # every slice cuts the body, and the expected counts total the request
+    assert np.all(v1.f_true.sum(axis=1) > 0)
+    expected = (A.astype(np.float64) @ v1.f_true.T).sum() + v1.gamma.astype(np.float64).sum()
+    assert abs(expected - 5e5) <= 1e-3 * 5e5
