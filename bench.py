@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-slice batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 120 x 512^2 batched leg")
+    ap.add_argument("--no-volume", action="store_true",
+                    help="skip the 64-slice 3-D SHOITV volume leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests/s)")
@@ -252,6 +254,68 @@ def bench_batched(AP, ctx, geom, A, dev, single_rate, K=BATCH_K, lo=1e5, hi=1e7,
                              "trial_us_default": t.us_per_slice_iter_default}
         out[name + "_autotuned"] = tuned
     out["algorithmic_bytes_per_iter"] = nb
+    mat.close()
+    return out
+
+
+def bench_volume(AP, ctx, geom, A, dev, batched_rate, nz=64, counts=6.4e7, iters=100):
+    """APPGA with the 3-D SHOITV regulariser on one volume of nz slices of
+    the main geometry sharing A (ellipsoid phantom, Poisson counts per
+    slice): slices x iterations per second, and the 3-D stencil kernel alone
+    against the HBM roofline."""
+    import numpy as np
+    import torch
+    from paper_2409_13344_gb300 import workload as W
+    vol = W.make_volume(A, geom, nz, counts, W.seed_for(6, 4))
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, bf16=True)
+    g = torch.from_numpy(vol.g).to(dev)
+    gam = torch.from_numpy(vol.gamma).to(dev)
+    f = torch.empty((nz, geom.d), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"one volume of {nz} slices of {geom.n}x{geom.n} ({geom.n_angles} x "
+                       f"{geom.n_bins} sinograms per slice) sharing one A, ellipsoid phantom, "
+                       f"{counts:g} expected counts over the volume, 3-D SHOITV (3 + 9 "
+                       "components per voxel), omega 0.5, beta 1, objective every iteration; "
+                       "batched SpMM kernels + 3-D stencil under captured CUDA graphs",
+           "nz": nz}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for name, prec in (("fp32", 0), ("bf16", 1)):
+        def call(n_maps):
+            p = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA,
+                                  max_iters=n_maps, a_precision=prec, track_objective=1)
+            AP.appga_reconstruct_volume(ctx.handle, mat.handle, nz, g, gam, None, p, f)
+        for _ in range(2):
+            call(8)
+        reps = sorted((timed(lambda: call(8 + iters)) - timed(lambda: call(8))) / iters
+                      for _ in range(3))
+        per_iter = reps[1]
+        out[name] = {"slices_iters_per_s": nz / (per_iter * 1e-3),
+                     "us_per_volume_iter": 1e3 * per_iter, "us_per_slice_iter": 1e3 * per_iter / nz}
+        if batched_rate and name in batched_rate:
+            out[name]["vs_batched_2d"] = out[name]["slices_iters_per_s"] / batched_rate[name]
+    # the 3-D stencil alone: slice-major volume in, gradient out (8 bytes per voxel)
+    vox = nz * geom.d
+    fin = f.clone()
+    gout = torch.empty_like(fin)
+    run = lambda: AP.appga_shoitv3d_grad(ctx.handle, geom.n, nz, fin, LAM1, LAM2, EPS, gout)
+    for _ in range(5):
+        run()
+    ms = timed(lambda: [run() for _ in range(50)]) / 50
+    peaks, src = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    out["stencil3d"] = {"kernel": "k_stencil3d", "us_per_launch": 1e3 * ms,
+                        "algorithmic_bytes_per_launch": 8 * vox,
+                        "achieved_gbs": 8 * vox / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                        "peak_source": src, "frac": 8 * vox / (ms * 1e-3) / 1e9 / hbm}
     mat.close()
     return out
 
@@ -538,6 +602,12 @@ def run_ours(args):
                                     "log-uniform 1e4..1e7 (8 distinct sinograms repeated), "
                                     "omega 1, beta 1; rates over 60 timed iterations of a "
                                     "300-iteration schedule")
+    volume = None
+    if world == 1 and not args.no_volume:
+        brate = None
+        if batched:  # the volume runs the batched kernels' default schedule
+            brate = {k: batched[k]["slices_iters_per_s"] for k in ("fp32", "bf16")}
+        volume = bench_volume(AP, ctx, geom, A, dev, brate)
     if world == 1 and not args.no_serve:
         serving = bench_serving(AP, ctx, args.serve_requests, args.serve_rate, geom, A)
 
@@ -566,6 +636,7 @@ def run_ours(args):
             "clocks": clk,
             "batched": batched,
             "large_batch": large,
+            "volume": volume,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

@@ -33,6 +33,8 @@ void free_batch_workspace(BatchWorkspace* bw) {
   cudaFree(bw->fpartial);
   cudaFree(bw->gtick);
   cudaFree(bw->flag);
+  for (auto& p : bw->fsm) cudaFree(p);
+  cudaFree(bw->gsm);
   cudaFree(bw->vscal);
   cudaFreeHost(bw->vscal_host);
   cudaFreeHost(bw->slots_host);
@@ -136,15 +138,20 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
 }
 
 cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
-                                cudaGraphExec_t* out, const Vol3Args* va) {
+                                cudaGraphExec_t* out, const VolumeSteps* vb) {
   *out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   for (int i = 0; i < S && e == cudaSuccess; ++i) {
     e = launch_bpixel(pa, s);
+    if (e == cudaSuccess && vb)
+      e = launch_slots_to_slices(vb->slot_ring, vb->slice_ring, vb->d, vb->Kp, vb->nz,
+                                 vb->va.bst, 0, s);
     if (e == cudaSuccess) e = launch_bforward(fa, s);
-    if (e == cudaSuccess && va) e = launch_stencil3d(*va, s);
+    if (e == cudaSuccess && vb) e = launch_stencil3d(vb->va, s);
+    if (e == cudaSuccess && vb)
+      e = launch_slices_to_slots(vb->va.gR, fa.gR, vb->d, vb->Kp, vb->nz, vb->va.bst, s);
   }
   const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   if (e == cudaSuccess) e = e2;
@@ -268,25 +275,35 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
   BPixArgs pa;
   make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, n, b, bf16, track, sch,
                   &fa, &pa);
-  // volume: the K slots are the slices of one volume; the 3-D stencil runs
-  // in its own kernel after the forward phase and leaves its per-slice
-  // regulariser sums after the forward phase's rows; one stopping test
-  Vol3Args va{};
+  // volume: the K slots are the slices of one volume.  The 3-D stencil runs
+  // on slice-major copies of the iterates after the forward phase, leaves
+  // its per-slice regulariser sums after the forward phase's rows, and its
+  // gradient is moved back to the slot-minor gR; one stopping test
+  VolumeSteps vb{};
   if (volume) {
+    for (int i = 0; i < 3; ++i)
+      if (!b.fsm[i]) CK(cudaMalloc((void**)&b.fsm[i], (size_t)d * Kp * sizeof(float)));
+    if (!b.gsm) CK(cudaMalloc((void**)&b.gsm, (size_t)d * Kp * sizeof(float)));
     fa.no_stencil = 1;
     pa.joint = 1;
     const int nfw = bforward_grid(fa);
+    Vol3Args& va = vb.va;
     va.n = n;
     va.nz = K;
-    va.ps = Kp;
-    va.zs = 1;
-    for (int i = 0; i < 3; ++i) va.f[i] = b.f[i];
+    for (int i = 0; i < 3; ++i) {
+      va.f[i] = b.fsm[i];
+      vb.slot_ring[i] = b.f[i];
+      vb.slice_ring[i] = b.fsm[i];
+    }
     va.slots = b.slots;
     va.bst = b.bst;
     va.want_reg = track ? 1 : 0;
     va.pstride = Kp;
-    va.gR = b.gR;
+    va.gR = b.gsm;
     va.partial = b.fpartial + (size_t)nfw * Kp;
+    vb.d = d;
+    vb.Kp = Kp;
+    vb.nz = K;
     pa.n_fpartial = nfw + (track ? stencil3d_grid(n, K) : 0);
   }
 
@@ -295,7 +312,11 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
   init.mode = 1;
   CK(launch_bforward(init, s));
   CK(launch_bforward(fa, s));
-  if (volume) CK(launch_stencil3d(va, s));
+  if (volume) {
+    CK(launch_slots_to_slices(vb.slot_ring, vb.slice_ring, d, Kp, K, b.bst, 1, s));
+    CK(launch_stencil3d(vb.va, s));
+    CK(launch_slices_to_slots(vb.va.gR, b.gR, d, Kp, K, b.bst, s));
+  }
 
   if (params->max_iters > 0) {
     const int S = params->graph_iters > 0 ? params->graph_iters : kBatchGraphIters;
@@ -309,7 +330,7 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
         cudaGraphExecDestroy(b.gexec);
         b.gexec = nullptr;
       }
-      const cudaError_t e = capture_batch_graph(fa, pa, S, s, &b.gexec, volume ? &va : nullptr);
+      const cudaError_t e = capture_batch_graph(fa, pa, S, s, &b.gexec, volume ? &vb : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "batched graph capture");
       b.gkey = key;
     }

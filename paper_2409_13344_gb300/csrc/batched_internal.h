@@ -85,13 +85,13 @@ struct BPixArgs {
   int32_t joint;  // volume mode: one stopping test on the sum of the slots' objectives
 };
 
-// 3-D SHOITV stencil (kernels_vol.cu).  Voxel (z, r, c) of a volume is at
-// (r n + c) ps + z zs.  Solver mode (bst != null): f^k and f^{k-1} are the
-// ring entries of the current step, theta, lambda and eps come from slot z;
-// stand-alone mode: f[0] is the volume, f~ = f, lam1/lam2/eps as given.
+// 3-D SHOITV stencil (kernels_vol.cu) on slice-major volumes: voxel
+// (z, r, c) at z n^2 + r n + c.  Solver mode (bst != null): f^k and f^{k-1}
+// are the slice-major ring entries of the current step (f[G % 3] and
+// f[(G + 2) % 3]), theta, lambda and eps come from slot z; stand-alone mode:
+// f[0] is the volume, f~ = f, lam1/lam2/eps as given.
 struct Vol3Args {
   int32_t n, nz;
-  int64_t ps, zs;
   const float* f[3];
   const SlotState* slots;
   const BatchState* bst;
@@ -99,7 +99,7 @@ struct Vol3Args {
   int32_t want_reg;       // also the regulariser at f^k: one row of pstride
   int32_t pstride;        // per-slice double-float sums per block in partial
   int32_t pad;
-  float* gR;              // out: B^T grad phi~(B f~), same layout as f
+  float* gR;              // out: B^T grad phi~(B f~), slice-major
   float2* partial;        // out (want_reg): stencil3d_grid rows of pstride
 };
 int stencil3d_max_slices();
@@ -108,6 +108,15 @@ cudaError_t launch_stencil3d(const Vol3Args& a, cudaStream_t s);
 // *out = sum of rows x cols double-float pairs (row stride pstride), in FP64
 cudaError_t launch_sum_pairs(const float2* p, int rows, int cols, int pstride, double* out,
                              cudaStream_t s);
+// Volume mode: the current ring entry (bst->gstep) of the slot-minor iterate
+// ring [d][Kp] into the slice-major ring [nz][d] (every entry if all != 0),
+// and a slice-major gradient [nz][d] into the slot-minor [d][Kp].  Both do
+// nothing once no slot is live.
+cudaError_t launch_slots_to_slices(float* const* slot_ring, float* const* slice_ring, int d,
+                                   int Kp, int nz, const BatchState* bst, int all,
+                                   cudaStream_t s);
+cudaError_t launch_slices_to_slots(const float* in, float* out, int d, int Kp, int nz,
+                                   const BatchState* bst, cudaStream_t s);
 
 int batch_max_blocks();
 // Grid of the forward phase for these arguments (the launcher's own choice).

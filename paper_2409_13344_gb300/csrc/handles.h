@@ -87,6 +87,8 @@ struct BatchWorkspace {
   unsigned int* gtick = nullptr;
   int* flag = nullptr;
   int* flag_host = nullptr;
+  float* fsm[3] = {nullptr, nullptr, nullptr};  // volume mode: slice-major iterate ring [Kp][d]
+  float* gsm = nullptr;                         // volume mode: slice-major 3-D gradient
   double* vscal = nullptr;       // volume objective terms: [Kp] data terms, regulariser
   double* vscal_host = nullptr;  // pinned mirror
   cudaGraphExec_t gexec = nullptr;
@@ -108,10 +110,17 @@ BatchSchedule tuned_schedule(const appga_matrix* M, int Kp, bool bf16);
 // Slot state of a problem run with `p` from iterate index k0 (active), or an
 // empty slot that holds no problem (inactive).
 SlotState slot_from_params(const appga_params* p, int k0, bool active);
-// Captures S x (pixel update, forward phase[, 3-D stencil]) into an
-// executable graph; va (volume mode) adds the 3-D stencil after each forward.
+// Captures S x (pixel update, forward phase) into an executable graph; with
+// vb (volume mode) each step is pixel update, transpose of the new iterate to
+// the slice-major ring, forward phase, 3-D stencil, transpose of its gradient.
+struct VolumeSteps {
+  Vol3Args va;
+  float* slot_ring[3];
+  float* slice_ring[3];
+  int d, Kp, nz;
+};
 cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
-                                cudaGraphExec_t* out, const Vol3Args* va = nullptr);
+                                cudaGraphExec_t* out, const VolumeSteps* vb = nullptr);
 // APPGA on a volume of K <= 128 slices sharing the matrix (the batched solver
 // in volume mode): device buffers as in appga_reconstruct_batched; on return
 // the workspace's pinned slot and batch states hold the final states.

@@ -9,15 +9,18 @@
 // row along each axis.  grad phi~ scales the triple by lambda1 / max(||.||,
 // eps) and the 9-vector by lambda2 / max(||.||, eps).
 //
-// Layout: voxel (z, r, c) of a volume sits at (r n + c) ps + z zs, so the
-// same kernel serves the solver's slot-minor blocks (ps = Kp, zs = 1: slice z
-// is slot z) and slice-major volumes (ps = 1, zs = n^2).
+// Volumes are slice-major (voxel (z, r, c) at z n^2 + r n + c), so every
+// plane of a tile is read and written with coalesced rows.  A block owns an
+// 8 x 32 pixel tile and marches along z through a run of slices, keeping
+// three planes of f~ and f^k (2-pixel in-plane halo) and three planes of the
+// twelve gradient fields (1-pixel halo) in rings: each plane is loaded and
+// each field plane computed once per run, so the z-direction costs no halo.
+// Blocks are persistent over (tile, z-run) items and leave one row of
+// per-slice regulariser sums (double-float pairs, fixed order) each.
 //
-// Tiles of 2 x 32 pixels x 8 slices, one thread per (column, slice); f~ and
-// f^k are staged with a 2-voxel halo in every axis, the twelve gradient
-// fields with a 1-voxel halo, so each block writes only its own voxels.
-// Blocks are persistent over the tiles and leave one row of per-slice
-// regulariser sums (double-float pairs) each, in a fixed order.
+// The solver keeps its iterates slot-minor ([d][Kp], one slot per slice) for
+// the SpMM kernels; two transpose kernels move the current iterate to the
+// slice-major ring and the gradient back.
 #include <cuda_runtime.h>
 
 #include "appga_internal.h"
@@ -27,19 +30,28 @@
 namespace appga {
 namespace {
 
-constexpr int VR = 2, VC = 32, VS = 8;  // tile: rows x columns x slices
-constexpr int VT = VC * VS;             // threads: one per (column, slice)
-constexpr int HR = VR + 4, HC = VC + 4, HS = VS + 4;  // f tiles, halo 2
-constexpr int WR = VR + 2, WC = VC + 2, WS = VS + 2;  // gradient fields, halo 1
-constexpr int NF = 12;                                // 3 + 9 components
-constexpr int MAXZ = 128;                             // slices (slots) at most
+constexpr int TR = 8, TC = 32;              // in-plane tile
+constexpr int NT = TR * TC;                   // threads: one per tile pixel
+constexpr int NWARP = NT / 32;
+constexpr int HR = TR + 4, HC = TC + 4;       // f planes, halo 2
+constexpr int WR = TR + 2, WC = TC + 2;       // gradient-field planes, halo 1
+constexpr int NF = 12;                        // 3 + 9 components
+constexpr int MAXZ = 128;                     // slices at most
+#ifndef APPGA_VOL_ZRUN
+#define APPGA_VOL_ZRUN 16
+#endif
+constexpr int ZRUN = APPGA_VOL_ZRUN;          // slices per item
 
+// The field planes use the f planes' row stride (HC), so the in-plane index
+// of a point is the same in both and neighbouring threads hit distinct banks.
 struct Vol3Smem {
-  float T[HR][HC][HS];      // f~
-  float K[HR][HC][HS];      // f^k (regulariser value)
-  float W[NF][WR][WC][WS];  // grad phi~ fields
-  float reg_hi[MAXZ], reg_lo[MAXZ];
+  float T[3][HR][HC];        // f~ ring
+  float K[3][HR][HC];        // f^k ring (regulariser value)
+  float W[3][NF][WR][HC];    // grad phi~ field ring (columns WC.. unused)
+  float reg_hi[NWARP][MAXZ], reg_lo[NWARP][MAXZ];
 };
+
+__device__ __forceinline__ int ring3(int p) { return (p + 6) % 3; }  // p >= -6
 
 struct Edges {
   bool c_lo, c_hi, r_lo, r_hi, z_lo, z_hi;
@@ -112,13 +124,48 @@ __device__ __forceinline__ void norms(const float (&u)[NF], float& n1, float& n2
   for (int q = 3; q < NF; ++q) n2 = fmaf(u[q], u[q], n2);
 }
 
-__global__ void __launch_bounds__(VT) k_stencil3d(Vol3Args a) {
+// The thirteen neighbours of a point that the twelve components read, loaded
+// once into registers from three consecutive planes (m, 0, p) at in-plane
+// offset o; X(dz, dr, dc) resolves at compile time.
+struct Nbr {
+  float v[27];
+  __device__ __forceinline__ void load(const float* m, const float* z, const float* p, int o) {
+    v[13] = z[o];
+    v[12] = z[o - 1];
+    v[14] = z[o + 1];
+    v[10] = z[o - HC];
+    v[16] = z[o + HC];
+    v[15] = z[o + HC - 1];
+    v[11] = z[o - HC + 1];
+    v[4] = m[o];
+    v[22] = p[o];
+    v[21] = p[o - 1];
+    v[5] = m[o + 1];
+    v[19] = p[o - HC];
+    v[7] = m[o + HC];
+  }
+  __device__ __forceinline__ float operator()(int dz, int dr, int dc) const {
+    return v[(dz + 1) * 9 + (dr + 1) * 3 + (dc + 1)];
+  }
+};
+// A field in three consecutive planes (m, 0, p) around in-plane offset o.
+struct Planes3 {
+  const float *m, *z, *p;
+  int o;
+  __device__ __forceinline__ float operator()(int dz, int dr, int dc) const {
+    const float* b = dz < 0 ? m : (dz > 0 ? p : z);
+    return b[o + dr * HC + dc];
+  }
+};
+
+__global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Vol3Smem& S = *reinterpret_cast<Vol3Smem*>(smem_raw);
   if (a.bst != nullptr && a.bst->remaining == 0) return;  // uniform over the grid
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tr = tid / TC, tc = tid % TC;
   const int n = a.n, nz = a.nz;
-  const long long ps = a.ps, zs = a.zs;
+  const long long d = (long long)n * n;
   const float *fk, *fkm;
   if (a.bst != nullptr) {
     const int G = a.bst->gstep;
@@ -128,127 +175,210 @@ __global__ void __launch_bounds__(VT) k_stencil3d(Vol3Args a) {
     fk = a.f[0];
     fkm = nullptr;
   }
-  for (int s = tid; s < MAXZ; s += VT) {
-    S.reg_hi[s] = 0.f;
-    S.reg_lo[s] = 0.f;
+  for (int s = tid; s < NWARP * MAXZ; s += NT) {
+    (&S.reg_hi[0][0])[s] = 0.f;
+    (&S.reg_lo[0][0])[s] = 0.f;
   }
-  const int ntx = (n + VC - 1) / VC, nty = (n + VR - 1) / VR, ntz = (nz + VS - 1) / VS;
-  const int items = ntx * nty * ntz;
+  const int ntx = (n + TC - 1) / TC, nty = (n + TR - 1) / TR, nzr = (nz + ZRUN - 1) / ZRUN;
+  const int items = ntx * nty * nzr;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
-    const int tz = it % ntz, txy = it / ntz;
-    const int z0 = tz * VS, r0 = (txy / ntx) * VR, c0 = (txy % ntx) * VC;
-    __syncthreads();  // the previous item's fields are no longer read
-    // f~ = f^k + theta_z (f^k - f^{k-1}) and f^k on the tile with a 2-voxel halo
-    for (int t = tid; t < HR * HC * HS; t += VT) {
-      int iz, ic, ir;
-      if (a.zs == 1) {  // slices adjacent in memory: slice fastest
-        iz = t % HS;
-        ic = (t / HS) % HC;
-        ir = t / (HS * HC);
-      } else {          // pixels of a row adjacent: column fastest
-        ic = t % HC;
-        iz = (t / HC) % HS;
-        ir = t / (HC * HS);
-      }
-      const int z = z0 - 2 + iz, r = r0 - 2 + ir, c = c0 - 2 + ic;
-      float vk = 0.f, vt = 0.f;
-      if (z >= 0 && z < nz && r >= 0 && r < n && c >= 0 && c < n) {
-        const long long o = (long long)(r * n + c) * ps + (long long)z * zs;
-        vk = fk[o];
-        vt = vk;
-        if (fkm != nullptr) vt = fmaf(a.slots[z].theta_hi, vk - fkm[o], vk);
-      }
-      S.T[ir][ic][iz] = vt;
-      S.K[ir][ic][iz] = vk;
-    }
-    __syncthreads();
-    // grad phi~(B f~) on the tile and a 1-voxel ring around it
-    for (int t = tid; t < WR * WC * WS; t += VT) {
-      const int iz = t % WS, ic = (t / WS) % WC, ir = t / (WS * WC);
-      const int z = z0 - 1 + iz, r = r0 - 1 + ir, c = c0 - 1 + ic;
-      float v[NF];
+    const int zr = it % nzr, txy = it / nzr;
+    const int zb = zr * ZRUN, ze = min(nz, zb + ZRUN);
+    const int r0 = (txy / ntx) * TR, c0 = (txy % ntx) * TC;
+    const int r = r0 + tr, c = c0 + tc;
+    // plane loads are issued one step ahead into registers (each thread
+    // holds at most LPT elements of a plane), so their latency overlaps the
+    // field and gradient work of the current step
+    constexpr int LPT = (HR * HC + NT - 1) / NT;
+    float pk[LPT], pm[LPT];
+    auto fetch = [&](int s) {
+      const bool s_in = s >= 0 && s < nz;
+      const float* fks = fk + (long long)(s_in ? s : 0) * d;
+      const float* fms = fkm != nullptr ? fkm + (long long)(s_in ? s : 0) * d : nullptr;
 #pragma unroll
-      for (int q = 0; q < NF; ++q) v[q] = 0.f;
-      if (z >= 0 && z < nz && r >= 0 && r < n && c >= 0 && c < n) {
-        const Edges e = edges(z, r, c, nz, n);
-        auto X = [&](int dz, int dr, int dc) { return S.T[ir + 1 + dr][ic + 1 + dc][iz + 1 + dz]; };
-        all_comps(X, e, v);
-        float n1, n2;
-        norms(v, n1, n2);
-        const float lam1 = a.slots ? a.slots[z].lambda1 : a.lam1;
-        const float lam2 = a.slots ? a.slots[z].lambda2 : a.lam2;
-        const float eps = a.slots ? a.slots[z].eps : a.eps;
-        const float s1 = lam1 / fmaxf(sqrtf(n1), eps);
-        const float s2 = lam2 / fmaxf(sqrtf(n2), eps);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) v[q] *= s1;
-#pragma unroll
-        for (int q = 3; q < NF; ++q) v[q] *= s2;
-      }
-#pragma unroll
-      for (int q = 0; q < NF; ++q) S.W[q][ir][ic][iz] = v[q];
-    }
-    __syncthreads();
-    // B^T applied to the fields at the tile voxels: D^T for the first-order
-    // fields; each second-order block's transpose is the block of the same
-    // form (symmetric ones) or of its partner (4 <-> 6, 8 <-> 9, 10 <-> 11)
-    const int col = tid % VC, zq = tid / VC;
-    const int z = z0 + zq, c = c0 + col;
-    float reg = 0.f;
-    if (z < nz && c < n) {
-#pragma unroll
-      for (int ii = 0; ii < VR; ++ii) {
-        const int r = r0 + ii;
-        if (r >= n) continue;
-        const Edges e = edges(z, r, c, nz, n);
-        const int wr = ii + 1, wc = col + 1, wz = zq + 1;
-        auto Wf = [&](int q) {
-          return [&, q](int dz, int dr, int dc) { return S.W[q][wr + dr][wc + dc][wz + dz]; };
-        };
-        float g = 0.f;
-        if (e.c_lo) g += S.W[0][wr][wc][wz];
-        if (e.c_hi) g -= S.W[0][wr][wc + 1][wz];
-        if (e.r_lo) g += S.W[1][wr][wc][wz];
-        if (e.r_hi) g -= S.W[1][wr + 1][wc][wz];
-        if (e.z_lo) g += S.W[2][wr][wc][wz];
-        if (e.z_hi) g -= S.W[2][wr][wc][wz + 1];
-        g += comp<3>(Wf(3), e);
-        g += comp<6>(Wf(4), e);
-        g += comp<5>(Wf(5), e);
-        g += comp<4>(Wf(6), e);
-        g += comp<7>(Wf(7), e);
-        g += comp<9>(Wf(8), e);
-        g += comp<8>(Wf(9), e);
-        g += comp<11>(Wf(10), e);
-        g += comp<10>(Wf(11), e);
-        a.gR[(long long)(r * n + c) * ps + (long long)z * zs] = g;
-        if (a.want_reg) {
-          auto Xk = [&](int dz, int dr, int dc) {
-            return S.K[ii + 2 + dr][col + 2 + dc][zq + 2 + dz];
-          };
-          float u[NF];
-          all_comps(Xk, e, u);
-          float n1, n2;
-          norms(u, n1, n2);
-          const float lam1 = a.slots ? a.slots[z].lambda1 : a.lam1;
-          const float lam2 = a.slots ? a.slots[z].lambda2 : a.lam2;
-          const float eps = a.slots ? a.slots[z].eps : a.eps;
-          reg += lam1 * s_eps_f(n1, eps) + lam2 * s_eps_f(n2, eps);
+      for (int u = 0; u < LPT; ++u) {
+        const int t = tid + u * NT;
+        const int i = t / HC, j = t % HC;
+        const int rr = r0 - 2 + i, cc = c0 - 2 + j;
+        pk[u] = 0.f;
+        pm[u] = 0.f;
+        if (t < HR * HC && s_in && rr >= 0 && rr < n && cc >= 0 && cc < n) {
+          const long long o = (long long)rr * n + cc;
+          pk[u] = fks[o];
+          if (fms != nullptr) pm[u] = fms[o];
         }
       }
-    }
-    if (a.want_reg) {
-      // warp zq holds slice z0 + zq: fold its 32 columns in a fixed order
-      float h = reg, l = 0.f;
-      warp_sum_acc(h, l);
-      if (lane == 0 && z0 + warp < nz) acc_add(S.reg_hi[z0 + warp], S.reg_lo[z0 + warp], h, l);
+    };
+    fetch(zb - 2);
+    for (int s = zb - 2; s <= ze + 1; ++s) {
+      // plane s of f~ = f^k + theta_s (f^k - f^{k-1}) and of f^k (zero outside
+      // the volume).  The ring slot it replaces (plane s - 3) was last read
+      // before the previous step's second barrier.
+      {
+        const int ls = ring3(s);
+        const bool s_in = s >= 0 && s < nz;
+        const float th = (s_in && fkm != nullptr) ? a.slots[s].theta_hi : 0.f;
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+          const int t = tid + u * NT;
+          if (t < HR * HC) {
+            const float vk = pk[u];
+            (&S.K[ls][0][0])[t] = vk;
+            (&S.T[ls][0][0])[t] = fkm != nullptr ? fmaf(th, vk - pm[u], vk) : vk;
+          }
+        }
+      }
+      if (s + 1 <= ze + 1) fetch(s + 1);
+      __syncthreads();
+      // field plane P = s - 1 (needs f~ planes P - 1 .. P + 1)
+      const int P = s - 1;
+      if (P >= zb - 1 && P <= ze) {
+        const bool inside = P >= 0 && P < nz;
+        float lam1 = a.lam1, lam2 = a.lam2, eps = a.eps;
+        if (inside && a.slots) {
+          lam1 = a.slots[P].lambda1;
+          lam2 = a.slots[P].lambda2;
+          eps = a.slots[P].eps;
+        }
+        const float inv_eps = 1.f / eps;
+        const float* Tm = &S.T[ring3(P - 1)][0][0];
+        const float* T0 = &S.T[ring3(P)][0][0];
+        const float* Tp = &S.T[ring3(P + 1)][0][0];
+        float* Wo = &S.W[ring3(P)][0][0][0];
+        for (int t = tid; t < WR * HC; t += NT) {
+          const int i = t / HC, j = t % HC;
+          if (j >= WC) continue;  // padding columns of the field planes
+          const int rr = r0 - 1 + i, cc = c0 - 1 + j;
+          float v[NF];
+#pragma unroll
+          for (int q = 0; q < NF; ++q) v[q] = 0.f;
+          if (inside && rr >= 0 && rr < n && cc >= 0 && cc < n) {
+            const Edges e = edges(P, rr, cc, nz, n);
+            Nbr X;
+            X.load(Tm, T0, Tp, (i + 1) * HC + (j + 1));
+            all_comps(X, e, v);
+            float n1, n2;
+            norms(v, n1, n2);
+            // lambda / max(||u||, eps) = lambda * min(rsqrt(||u||^2), 1/eps)
+            const float s1 = lam1 * fminf(rsqrtf(n1), inv_eps);
+            const float s2 = lam2 * fminf(rsqrtf(n2), inv_eps);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v[q] *= s1;
+#pragma unroll
+            for (int q = 3; q < NF; ++q) v[q] *= s2;
+          }
+#pragma unroll
+          for (int q = 0; q < NF; ++q) Wo[q * (WR * HC) + i * HC + j] = v[q];
+        }
+        // the regulariser at plane P from f^k (planes P - 1 .. P + 1)
+        if (a.want_reg && P >= zb && P < ze) {
+          float reg = 0.f;
+          if (r < n && c < n) {
+            const Edges e = edges(P, r, c, nz, n);
+            Nbr Xk;
+            Xk.load(&S.K[ring3(P - 1)][0][0], &S.K[ring3(P)][0][0], &S.K[ring3(P + 1)][0][0],
+                    (tr + 2) * HC + (tc + 2));
+            float u[NF];
+            all_comps(Xk, e, u);
+            float n1, n2;
+            norms(u, n1, n2);
+            reg = lam1 * s_eps_f(n1, eps) + lam2 * s_eps_f(n2, eps);
+          }
+          float h = reg, l = 0.f;
+          warp_sum_acc(h, l);
+          if (lane == 0) acc_add(S.reg_hi[warp][P], S.reg_lo[warp][P], h, l);
+        }
+      }
+      __syncthreads();
+      // gradient at plane O = s - 2 (needs field planes O - 1 .. O + 1):
+      // D^T for the first-order fields; each second-order block's transpose
+      // is the block of the same form (symmetric ones) or of its partner
+      // (4 <-> 6, 8 <-> 9, 10 <-> 11)
+      const int O = s - 2;
+      if (O >= zb && O < ze && r < n && c < n) {
+        const Edges e = edges(O, r, c, nz, n);
+        const float* Wm = &S.W[ring3(O - 1)][0][0][0];
+        const float* W0 = &S.W[ring3(O)][0][0][0];
+        const float* Wp = &S.W[ring3(O + 1)][0][0][0];
+        const int o = (tr + 1) * HC + (tc + 1);
+        constexpr int FS = WR * HC;  // field stride in a plane
+        auto F = [&](int q) { return Planes3{Wm + q * FS, W0 + q * FS, Wp + q * FS, o}; };
+        float g = 0.f;
+        if (e.c_lo) g += W0[o];
+        if (e.c_hi) g -= W0[o + 1];
+        if (e.r_lo) g += W0[FS + o];
+        if (e.r_hi) g -= W0[FS + o + HC];
+        if (e.z_lo) g += W0[2 * FS + o];
+        if (e.z_hi) g -= Wp[2 * FS + o];
+        g += comp<3>(F(3), e);
+        g += comp<6>(F(4), e);
+        g += comp<5>(F(5), e);
+        g += comp<4>(F(6), e);
+        g += comp<7>(F(7), e);
+        g += comp<9>(F(8), e);
+        g += comp<8>(F(9), e);
+        g += comp<11>(F(10), e);
+        g += comp<10>(F(11), e);
+        a.gR[(long long)O * d + (long long)r * n + c] = g;
+      }
     }
   }
   if (!a.want_reg) return;
   __syncthreads();
-  for (int s = tid; s < a.pstride; s += VT)
-    a.partial[(long long)blockIdx.x * a.pstride + s] =
-        s < MAXZ ? make_float2(S.reg_hi[s], S.reg_lo[s]) : make_float2(0.f, 0.f);
+  // the block's per-slice sums: warps in a fixed order
+  for (int s = tid; s < a.pstride; s += NT) {
+    float h = 0.f, l = 0.f;
+    if (s < MAXZ)
+      for (int w = 0; w < NWARP; ++w) acc_add(h, l, S.reg_hi[w][s], S.reg_lo[w][s]);
+    a.partial[(long long)blockIdx.x * a.pstride + s] = make_float2(h, l);
+  }
+}
+
+// slot-minor [d][Kp] -> slice-major [nz][d] of the ring entry of the current
+// step (or every entry), 32 x 32 tiles through shared memory
+__global__ void __launch_bounds__(256) k_slots_to_slices(const float* r0, const float* r1,
+                                                         const float* r2, float* o0, float* o1,
+                                                         float* o2, int d, int Kp, int nz,
+                                                         const BatchState* bst, int all) {
+  __shared__ float tile[32][33];
+  if (bst != nullptr && bst->remaining == 0) return;
+  const float* rin[3] = {r0, r1, r2};
+  float* rout[3] = {o0, o1, o2};
+  const int G = bst != nullptr ? bst->gstep : 0;
+  const int j0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+  for (int e = 0; e < 3; ++e) {
+    if (!all && e != G % 3) continue;  // uniform over the block
+    const float* in = rin[e];
+    float* out = rout[e];
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+      const int j = j0 + k, z = z0 + threadIdx.x;
+      tile[k][threadIdx.x] = (j < d && z < nz) ? in[(long long)j * Kp + z] : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+      const int z = z0 + k, j = j0 + threadIdx.x;
+      if (z < nz && j < d) out[(long long)z * d + j] = tile[threadIdx.x][k];
+    }
+  }
+}
+
+// slice-major [nz][d] -> slot-minor [d][Kp] (slots >= nz untouched)
+__global__ void __launch_bounds__(256) k_slices_to_slots(const float* in, float* out, int d,
+                                                         int Kp, int nz,
+                                                         const BatchState* bst) {
+  __shared__ float tile[32][33];
+  if (bst != nullptr && bst->remaining == 0) return;
+  const int j0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int z = z0 + k, j = j0 + threadIdx.x;
+    tile[k][threadIdx.x] = (z < nz && j < d) ? in[(long long)z * d + j] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int j = j0 + k, z = z0 + threadIdx.x;
+    if (j < d && z < nz) out[(long long)j * Kp + z] = tile[threadIdx.x][k];
+  }
 }
 
 // out = sum of rows x cols double-float pairs (row stride pstride), one block,
@@ -280,8 +410,8 @@ int sm_count_vol() {
 int stencil3d_max_slices() { return MAXZ; }
 
 int stencil3d_grid(int n, int nz) {
-  const int items = ((n + VC - 1) / VC) * ((n + VR - 1) / VR) * ((nz + VS - 1) / VS);
-  const int cap = 2 * sm_count_vol();
+  const int items = ((n + TC - 1) / TC) * ((n + TR - 1) / TR) * ((nz + ZRUN - 1) / ZRUN);
+  const int cap = 3 * sm_count_vol();
   return items < cap ? items : cap;
 }
 
@@ -290,13 +420,30 @@ cudaError_t launch_stencil3d(const Vol3Args& a, cudaStream_t s) {
   static cudaError_t attr = cudaFuncSetAttribute(
       k_stencil3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Vol3Smem));
   if (attr != cudaSuccess) return attr;
-  k_stencil3d<<<stencil3d_grid(a.n, a.nz), VT, sizeof(Vol3Smem), s>>>(a);
+  k_stencil3d<<<stencil3d_grid(a.n, a.nz), NT, sizeof(Vol3Smem), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum_pairs(const float2* p, int rows, int cols, int pstride, double* out,
                              cudaStream_t s) {
   k_sum_pairs<<<1, 256, 0, s>>>(p, rows, cols, pstride, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slots_to_slices(float* const* slot_ring, float* const* slice_ring, int d,
+                                   int Kp, int nz, const BatchState* bst, int all,
+                                   cudaStream_t s) {
+  const dim3 grid((d + 31) / 32, (nz + 31) / 32), block(32, 8);
+  k_slots_to_slices<<<grid, block, 0, s>>>(slot_ring[0], slot_ring[1], slot_ring[2],
+                                           slice_ring[0], slice_ring[1], slice_ring[2], d, Kp,
+                                           nz, bst, all);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slices_to_slots(const float* in, float* out, int d, int Kp, int nz,
+                                   const BatchState* bst, cudaStream_t s) {
+  const dim3 grid((d + 31) / 32, (nz + 31) / 32), block(32, 8);
+  k_slices_to_slots<<<grid, block, 0, s>>>(in, out, d, Kp, nz, bst);
   return cudaGetLastError();
 }
 

@@ -35,8 +35,6 @@ appga_status volume_objective(appga_ctx* ctx, appga_matrix* M, int nz, const flo
   Vol3Args va{};
   va.n = M->n;
   va.nz = nz;
-  va.ps = 1;
-  va.zs = d;
   va.f[0] = f;
   va.lam1 = (float)p->lambda1;
   va.lam2 = (float)p->lambda2;
@@ -76,8 +74,6 @@ extern "C" appga_status appga_shoitv3d_grad(appga_ctx* ctx, int32_t n_side, int3
   Vol3Args va{};
   va.n = n_side;
   va.nz = nz;
-  va.ps = 1;
-  va.zs = (int64_t)n_side * n_side;
   va.f[0] = f;
   va.lam1 = (float)lambda1;
   va.lam2 = (float)lambda2;
