@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 120 x 512^2 batched leg")
     ap.add_argument("--no-volume", action="store_true",
                     help="skip the 64-slice 3-D SHOITV volume leg")
+    ap.add_argument("--volume-only", action="store_true",
+                    help="run only the volume leg and print its JSON (for profiling)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests/s)")
@@ -488,6 +490,10 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     geom, A, sl = make_inputs(rank)
     ctx = AP.Context(dev.index)
+    if args.volume_only:
+        print(json.dumps({"volume": bench_volume(AP, ctx, geom, A, dev, None)}), flush=True)
+        ctx.close()
+        return 0
     mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
     g = torch.from_numpy(sl.g).to(dev)
     gamma = torch.from_numpy(sl.gamma).to(dev)
