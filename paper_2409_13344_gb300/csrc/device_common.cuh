@@ -21,6 +21,18 @@ constexpr int MAX_WARPS = 32;
 
 // A and A^T are streamed once per iteration: bypass L1 and tag the lines
 // evict-first in L2 (cache-policy operand) so the gathered vectors stay cached.
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream is still
+// running: pdl_trigger lets this grid's successor launch once every block of
+// this grid has started (or exited), and pdl_wait blocks until the
+// predecessor grid has completed with its memory visible.  Before pdl_wait a
+// kernel may read only data that no kernel of the stream writes.  Both are
+// no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t evict_first_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));

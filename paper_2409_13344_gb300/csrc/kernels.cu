@@ -524,13 +524,10 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     } slot;
     StencilSmem st;
   } sm;
+  pdl_trigger();
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (a.loop && st->done) return;  // uniform over the grid
-  const int kk = a.loop ? st->k : 0;
   const int nproj = proj_blocks<FW>(a.A.rows);
-  float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
-  int hits = 0, bad = 0;
 #if APPGA_SFIRST
   // stencil tiles take the first blocks, so the projector blocks end the grid
   const int pb = (int)blockIdx.x - ((int)gridDim.x - nproj);
@@ -539,15 +536,35 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   const int pb = blockIdx.x;
   const int sb = (int)blockIdx.x - nproj;
 #endif
-  if (pb >= 0 && pb < nproj) {
+  const bool proj = pb >= 0 && pb < nproj;
+  const int m = a.A.rows;
+  const int row0 = pb * FW::ROWS + warp * FW::R;
+  const int nrows = proj ? max(0, min(FW::R, m - row0)) : 0;
+  // The warp's row bounds and first chunks of A: no kernel writes them, so
+  // they are fetched before waiting for the previous kernel of the stream.
+  RowGroup<BF16, DFA, FW::R, FW::PF> rg;
+  uint64_t pol = 0;
+  if (nrows > 0) {
+#if APPGA_SBND
+    rg.sb = reinterpret_cast<int*>(sm.slot.bnd[warp]);
+#endif
+    rg.set_bounds(load_raw_bound(a.A, row0, nrows, lane), nrows);
+    decltype(rg)::clear_slots(lane, sm.slot.hi[warp], sm.slot.lo[warp]);
+    pol = evict_first_policy();
+    rg.prologue(a.A, lane, pol);
+  }
+  pdl_wait();
+  if (a.loop && st->done) return;  // uniform over the grid
+  const int kk = a.loop ? st->k : 0;
+  float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
+  int hits = 0, bad = 0;
+  if (proj) {
     const float* f = a.loop ? a.f[kk % 3] : a.f[0];
-    const int m = a.A.rows;
-    const int row0 = pb * FW::ROWS + warp * FW::R;
-    const int nrows = max(0, min(FW::R, m - row0));
-    float hi, lo;
-    warp_rows_dot<BF16, DFA, FW::R, FW::PF>(a.A, row0, nrows, f, lane, sm.slot.hi[warp],
-                                             sm.slot.lo[warp], hi, lo,
-                                             reinterpret_cast<int*>(sm.slot.bnd[warp]));
+    float hi = 0.f, lo = 0.f;
+    if (nrows > 0) {
+      rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
+      slot_reduce<DFA>(lane, nrows, sm.slot.hi[warp], sm.slot.lo[warp], hi, lo);
+    }
 #if APPGA_FEPI
     // the block's row sums go to warp 0, so the double-float epilogue (with
     // the logarithm of the data term) runs once per block, not once per warp
@@ -620,17 +637,33 @@ template <bool BF16>
 __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
   __shared__ int4 sbnd[PX::W][4];
+  pdl_trigger();
   SolverState* st = a.st;
-  if (st->done) return;  // uniform over the grid
-  const int kk = st->k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = a.At.rows;
-  int bad = 0;
   const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
   const int np = max(0, min(PX::R, d - j0));
-  float bp, unused;
-  warp_rows_dot<BF16, false, PX::R, PX::PF>(a.At, j0, np, a.w, lane, slot[warp], nullptr, bp,
-                                            unused, reinterpret_cast<int*>(sbnd[warp]));
+  // row bounds and first chunks of A^T before waiting (no kernel writes them)
+  RowGroup<BF16, false, PX::R, PX::PF> rg;
+  uint64_t pol = 0;
+  if (np > 0) {
+#if APPGA_SBND
+    rg.sb = reinterpret_cast<int*>(sbnd[warp]);
+#endif
+    rg.set_bounds(load_raw_bound(a.At, j0, np, lane), np);
+    decltype(rg)::clear_slots(lane, slot[warp], nullptr);
+    pol = evict_first_policy();
+    rg.prologue(a.At, lane, pol);
+  }
+  pdl_wait();
+  if (st->done) return;  // uniform over the grid
+  const int kk = st->k;
+  int bad = 0;
+  float bp = 0.f, unused = 0.f;
+  if (np > 0) {
+    rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
+    slot_reduce<false>(lane, np, slot[warp], nullptr, bp, unused);
+  }
   float pj = 0.f;
   if (lane < np) pj = pixel_update(a, kk, j0 + lane, bp, bad);
   if (a.want_pmax) {
@@ -651,6 +684,8 @@ constexpr int FIN_THREADS = 512;
 #endif
 constexpr int FIN_BATCH = APPGA_FIN_BATCH;  // independent loads in flight per thread
 __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
+  pdl_trigger();
+  pdl_wait();
   SolverState* st = a.st;
   if (st->done) return;  // uniform over the block
   const int kk = st->k;
@@ -817,6 +852,34 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
 
 // ------------------------------------------------------------- launchers
 
+// The solver loop's kernels are launched with programmatic stream
+// serialisation (1), so each may start while its predecessor drains; 0 gives
+// plain stream order.
+#ifndef APPGA_PDL
+#define APPGA_PDL 1
+#endif
+namespace {
+template <class... P, class... Args>
+cudaError_t launch_dep(void (*kern)(P...), int grid, int block, cudaStream_t s, Args... args) {
+#if APPGA_PDL
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr{};
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+#else
+  kern<<<grid, block, 0, s>>>(args...);
+  return cudaGetLastError();
+#endif
+}
+}  // namespace
+
 int stencil_tiles(int n) { return st_tiles(n); }
 int forward_blocks(int m, int n) { return proj_blocks<FW>(m) + st_tiles(n); }
 
@@ -836,30 +899,19 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   // accumulates y in FP32; the stand-alone projection and objective calls
   // in double-float
   const bool dfa = (a.loop || a.solver_acc) ? APPGA_LOOP_DF != 0 : true;
-  if (a.use_bf16) {
-    if (dfa)
-      k_forward<true, true><<<grid, FW::THREADS, 0, s>>>(a);
-    else
-      k_forward<true, false><<<grid, FW::THREADS, 0, s>>>(a);
-  } else {
-    if (dfa)
-      k_forward<false, true><<<grid, FW::THREADS, 0, s>>>(a);
-    else
-      k_forward<false, false><<<grid, FW::THREADS, 0, s>>>(a);
-  }
-  return cudaGetLastError();
+  if (a.use_bf16)
+    return dfa ? launch_dep(k_forward<true, true>, grid, FW::THREADS, s, a)
+               : launch_dep(k_forward<true, false>, grid, FW::THREADS, s, a);
+  return dfa ? launch_dep(k_forward<false, true>, grid, FW::THREADS, s, a)
+             : launch_dep(k_forward<false, false>, grid, FW::THREADS, s, a);
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
   const int grid = proj_blocks<PX>(a.At.rows);
-  if (a.use_bf16)
-    k_pixel<true><<<grid, PX::THREADS, 0, s>>>(a);
-  else
-    k_pixel<false><<<grid, PX::THREADS, 0, s>>>(a);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = a.use_bf16 ? launch_dep(k_pixel<true>, grid, PX::THREADS, s, a)
+                                   : launch_dep(k_pixel<false>, grid, PX::THREADS, s, a);
   if (e != cudaSuccess || a.theta_tab == nullptr) return e;
-  k_finalize<<<1, FIN_THREADS, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
 }
 
 cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
