@@ -128,6 +128,13 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   fa.want_data = 0;
   fa.n = M->n;
   fa.ip = iter_params(p, false);
+  const bool tiled = tiled_gather_enabled();
+  if (tiled) {
+    // the loop's projector gathers f^k from its 8 x 8-tiled copy
+    fa.A.col = M->A_tiled.col;
+    fa.ft = ws.ft;
+    CK(launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
+  }
   CK(launch_forward(fa, s));
 
   PixArgs pa{};
@@ -138,6 +145,7 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   pa.gR = ws.gR;
   pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = ws.pfreeze;
+  pa.ft = tiled ? ws.ft : nullptr;
   pa.st = ws.st;
   pa.partial = ws.partial_p;
   pa.gtick = ws.gtick;

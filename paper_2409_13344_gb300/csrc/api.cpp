@@ -60,6 +60,7 @@ void free_workspace(Workspace& ws) {
   cudaFree(ws.w);
   cudaFree(ws.gR);
   cudaFree(ws.pfreeze);
+  cudaFree(ws.ft);
   cudaFree(ws.partial_p);
   cudaFree(ws.partial_r);
   cudaFree(ws.partial_aux);
@@ -127,6 +128,7 @@ appga_status ensure_workspace(appga_matrix* M) {
   if (e == cudaSuccess) e = dalloc(&ws.w, (size_t)m, b);
   if (e == cudaSuccess) e = dalloc(&ws.gR, (size_t)d, b);
   if (e == cudaSuccess) e = dalloc(&ws.pfreeze, (size_t)d, b);
+  if (e == cudaSuccess) e = dalloc(&ws.ft, (size_t)appga::tiled_size(M->n), b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_p, (size_t)np, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_r, (size_t)np, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_aux, (size_t)np, b);
@@ -255,6 +257,13 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.theta_tab = ws.theta_tab;
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
+  if (appga::tiled_gather_enabled()) {
+    // the loop's projector gathers f^k from its 8 x 8-tiled copy
+    fa.A.col = M->A_tiled.col;
+    fa.ft = ws.ft;
+    pa.ft = ws.ft;
+    CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
+  }
 
   // w^{k0}, y^{k0}, B^T grad phi~(B f~^{k0}) and Phi(f^{k0})
   CK(appga::launch_forward(fa, s));
@@ -699,6 +708,18 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
   rc = upload_csr(pa, M->has_bf16, &M->A, &M->bytes);
   if (rc == APPGA_OK) rc = upload_csr(pt, M->has_bf16, &M->At, &M->bytes);
   if (rc == APPGA_OK) {
+    // A's column indices in the 8 x 8-tiled pixel order (row_ptr and values shared)
+    std::vector<int32_t> ct(pa.col.size());
+    for (size_t q = 0; q < ct.size(); ++q)
+      ct[q] = appga::tiled_index(pa.col[q] / n_side, pa.col[q] % n_side, n_side);
+    M->A_tiled = M->A;
+    M->A_tiled.col = nullptr;
+    cudaError_t e = dalloc(&M->A_tiled.col, ct.size(), &M->bytes);
+    if (e == cudaSuccess && !ct.empty())
+      e = cudaMemcpy(M->A_tiled.col, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(e, "tiled column indices");
+  }
+  if (rc == APPGA_OK) {
     cudaError_t e = dalloc(&M->inv_lambda, (size_t)d, &M->bytes);
     if (e == cudaSuccess)
       e = cudaMemcpy(M->inv_lambda, inv.data(), (size_t)d * 4, cudaMemcpyHostToDevice);
@@ -718,6 +739,7 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
 appga_status appga_matrix_destroy(appga_matrix* M) {
   if (!M) return APPGA_OK;
   if (M->ctx) cudaSetDevice(M->ctx->device);
+  cudaFree(M->A_tiled.col);  // its other arrays belong to A
   free_csr(M->A);
   free_csr(M->At);
   cudaFree(M->inv_lambda);

@@ -95,6 +95,9 @@ struct FwdArgs {
   int32_t want_data;   // evaluate the objective (data term; in the loop also the regulariser)
   int32_t use_bf16;
   int32_t no_stencil;  // solver loop without the SHOITV stencil blocks (AFPPA)
+  // loop: f^k in the 8 x 8-tiled pixel order; then A carries tiled column
+  // indices (its projector gathers from ft, the stencil still reads f[])
+  const float* ft;
   int32_t solver_acc;  // 1: accumulate y as the solver loop does, also when loop == 0
 };
 
@@ -120,6 +123,7 @@ struct PixArgs {
   IterParams ip;
   int32_t use_bf16;
   int32_t want_pmax;  // also reduce the largest preconditioner entry (AFPPA step sizes)
+  float* ft;          // if set: f^{k+1} also written in the 8 x 8-tiled pixel order
 };
 
 // ---- launchers (kernels.cu) ----
@@ -140,6 +144,17 @@ cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float
 cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, const float* f,
                                    int d, int* flag, cudaStream_t s);
 // theta_{k0+i}, i = 0..n, into tab and theta_{k0} into the state
+// Pixel (r, c) of an n x n image in the 8 x 8-tiled order: tiles row-major,
+// pixels row-major inside a tile; tiled_size(n) entries cover the image.
+__host__ __device__ inline int64_t tiled_size(int n) {
+  return (int64_t)((n + 7) / 8) * ((n + 7) / 8) * 64;
+}
+__host__ __device__ inline int32_t tiled_index(int r, int c, int n) {
+  return (((r >> 3) * ((n + 7) / 8) + (c >> 3)) << 6) + ((r & 7) << 3) + (c & 7);
+}
+// ft[tiled_index(j)] = f[j] for the d = n * n pixels
+cudaError_t launch_to_tiled(const float* f, float* ft, int n, cudaStream_t s);
+bool tiled_gather_enabled();  // the solver loop gathers from the tiled copy
 cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
                                double a, double b, double omega, cudaStream_t s);
 long long disk_pixels(int n);

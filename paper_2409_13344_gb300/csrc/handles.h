@@ -28,6 +28,7 @@ struct Workspace {
   float2* partial_aux = nullptr;
   unsigned int* gtick = nullptr;  // group tickets of the grid reductions
   double* scalars = nullptr;      // device doubles for standalone results
+  float* ft = nullptr;  // the current iterate in the 8 x 8-tiled pixel order (loop gathers)
   ThetaEntry* theta_tab = nullptr;  // momentum scalars of the current run
   int theta_cap = 0;                // entries of theta_tab
   SolverState* st = nullptr;
@@ -146,6 +147,8 @@ struct appga_matrix {
   int32_t m = 0, d = 0, n = 0, na = 0;
   int64_t nnz = 0;
   appga::DevCSR A, At;
+  appga::DevCSR A_tiled;  // A with column indices in the 8 x 8-tiled pixel order
+                          // (shares row_ptr and values with A)
   float* inv_lambda = nullptr;       // 1/Lambda of the FP32 values
   float* inv_lambda_bf16 = nullptr;  // 1/Lambda of the BF16-rounded values
   int32_t has_bf16 = 0;

@@ -559,7 +559,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
   int hits = 0, bad = 0;
   if (proj) {
-    const float* f = a.loop ? a.f[kk % 3] : a.f[0];
+    const float* f = a.loop ? (a.ft ? a.ft : a.f[kk % 3]) : a.f[0];
     float hi = 0.f, lo = 0.f;
     if (nrows > 0) {
       rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
@@ -629,7 +629,9 @@ __device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, f
   const float grad = bp + a.gR[j];
   const float xv = __fmaf_rn(-p, grad, ft);
   if (!isfinite(xv)) bad = 1;
-  a.f[(kk + 1) % 3][j] = fmaxf(xv, 0.f);
+  const float fn = fmaxf(xv, 0.f);
+  a.f[(kk + 1) % 3][j] = fn;
+  if (a.ft) a.ft[tiled_index(j / a.n, j % a.n, a.n)] = fn;  // the next forward's gathers
   return p;
 }
 
@@ -850,7 +852,28 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
 
 }  // namespace
 
+__global__ void k_to_tiled(const float* __restrict__ f, float* __restrict__ ft, int n) {
+  const int d = n * n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+    ft[tiled_index(j / n, j % n, n)] = f[j];
+}
+
 // ------------------------------------------------------------- launchers
+
+// The solver loop's forward projection gathers f^k from a copy in the 8 x 8-
+// tiled pixel order (1): a ray crosses image rows, and tiles keep the pixels
+// it meets close in memory; 0 gathers from the row-major iterate.
+#ifndef APPGA_TILED_GATHER
+#define APPGA_TILED_GATHER 1
+#endif
+bool tiled_gather_enabled() { return APPGA_TILED_GATHER != 0; }
+
+cudaError_t launch_to_tiled(const float* f, float* ft, int n, cudaStream_t s) {
+  const int d = n * n;
+  const int grid = (d + 255) / 256 < 1024 ? (d + 255) / 256 : 1024;
+  k_to_tiled<<<grid, 256, 0, s>>>(f, ft, n);
+  return cudaGetLastError();
+}
 
 // The solver loop's kernels are launched with programmatic stream
 // serialisation (1), so each may start while its predecessor drains; 0 gives
@@ -858,7 +881,24 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
 #ifndef APPGA_PDL
 #define APPGA_PDL 1
 #endif
+// Preferred shared-memory carveout of the projector kernels in percent of the
+// unified L1 / shared memory (-1: the driver's choice).  The projectors need
+// little shared memory; the rest serves as L1 for the gathered vectors.
+// Measured on GB300: 31 % for the forward kernel (the 100 KB configuration
+// for its 9 resident blocks) is 2.3 us faster than the driver's choice; the
+// back-projection is fastest with the driver's choice.
+#ifndef APPGA_CARVEOUT_FW
+#define APPGA_CARVEOUT_FW 31
+#endif
+#ifndef APPGA_CARVEOUT_PX
+#define APPGA_CARVEOUT_PX -1
+#endif
 namespace {
+template <class K>
+cudaError_t set_carveout(K kern, int percent) {
+  if (percent < 0) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, percent);
+}
 template <class... P, class... Args>
 cudaError_t launch_dep(void (*kern)(P...), int grid, int block, cudaStream_t s, Args... args) {
 #if APPGA_PDL
@@ -899,6 +939,14 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   // accumulates y in FP32; the stand-alone projection and objective calls
   // in double-float
   const bool dfa = (a.loop || a.solver_acc) ? APPGA_LOOP_DF != 0 : true;
+  static const cudaError_t carve = [] {
+    cudaError_t r = set_carveout(k_forward<true, true>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<true, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, true>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, false>, APPGA_CARVEOUT_FW);
+    return r;
+  }();
+  if (carve != cudaSuccess) return carve;
   if (a.use_bf16)
     return dfa ? launch_dep(k_forward<true, true>, grid, FW::THREADS, s, a)
                : launch_dep(k_forward<true, false>, grid, FW::THREADS, s, a);
@@ -907,6 +955,12 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
+  static const cudaError_t carve = [] {
+    cudaError_t r = set_carveout(k_pixel<true>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<false>, APPGA_CARVEOUT_PX);
+    return r;
+  }();
+  if (carve != cudaSuccess) return carve;
   const int grid = proj_blocks<PX>(a.At.rows);
   const cudaError_t e = a.use_bf16 ? launch_dep(k_pixel<true>, grid, PX::THREADS, s, a)
                                    : launch_dep(k_pixel<false>, grid, PX::THREADS, s, a);
