@@ -380,17 +380,35 @@ __device__ void bset_theta(SlotState& s, double theta) {
 
 // -------------------------------------------------------------- k_bforward
 
-template <int V, bool BF16>
+// Shared memory of the forward phase: the per-slot objective partials of the
+// block, and with stencil blocks in the grid the stencil tiles.  A launch
+// without stencil blocks (the first projection, volume mode) leaves out the
+// stencil's ~40 KB, so more blocks fit per SM and more of the unified L1
+// serves the gathers of image rows.
+struct BFwdEpi {
+  float dhi[B_WARPS][MAXK];
+  float dlo[B_WARPS][MAXK];
+};
+template <bool ST>
+struct BFwdSmem {
+  BFwdEpi e;
+};
+template <>
+struct BFwdSmem<true> {
+  union {
+    BFwdEpi e;
+    BStencilSmem st;
+  };
+};
+
+// ST false: SpMV blocks only (grid n_spmv_blocks); ST true: the SpMV blocks
+// followed by the stencil blocks in one grid, so the stencil blocks fill the
+// SMs as the SpMV blocks finish.
+template <int V, bool BF16, bool ST>
 __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   __shared__ __align__(16) int s_off[B_WARPS][32];
   __shared__ __align__(16) float s_val[B_WARPS][32];
-  __shared__ union {
-    struct {
-      float dhi[B_WARPS][MAXK];
-      float dlo[B_WARPS][MAXK];
-    } e;
-    BStencilSmem st;
-  } sm;
+  __shared__ BFwdSmem<ST> sm;
   BatchState* bs = a.bst;
   if (a.mode == 0 && bs->remaining == 0) return;  // uniform over the grid
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -422,7 +440,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
     dl[t] = 0.f;
     hits[t] = 0;
   }
-  if ((int)blockIdx.x < a.n_spmv_blocks) {
+  if (!ST || (int)blockIdx.x < a.n_spmv_blocks) {
     const uint64_t pol = evict_first_policy();
 #if APPGA_BCONTIG
     // each block owns a contiguous run of rows (neighbouring rays share
@@ -471,52 +489,54 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
       vstore<V>(y_out + o, yo);
       if (!proj_only) vstore<V>(a.w + o, wo);
     }
-  } else if (!proj_only) {
-    // stencil items: (tile, 8-slot chunk) pairs, persistent over the stencil blocks
-    const int nsb = gridDim.x - a.n_spmv_blocks;
-    const int ntx = (n + BST_C - 1) / BST_C, nty = (n + BST_R - 1) / BST_R;
-    const int nchunks = Kp / BST_S;
-    const int ntiles = ntx * nty;
-    __shared__ float sreg_hi[MAXK], sreg_lo[MAXK];  // per-slot regulariser sums
-    __shared__ int chunk_on[MAXK / BST_S];
-    for (int s = tid; s < MAXK; s += blockDim.x) {
-      sreg_hi[s] = 0.f;
-      sreg_lo[s] = 0.f;
-    }
-    for (int c = tid; c < nchunks; c += blockDim.x) {
-      int any = 0;
-      for (int q = 0; q < BST_S; ++q) {
-        const SlotState& sl = a.slots[c * BST_S + q];
-        any |= a.mode == 2 ? sl.fresh : (sl.active && !sl.done);
+  } else if constexpr (ST) {
+    if (!proj_only) {
+      // stencil items: (tile, 8-slot chunk) pairs, persistent over the stencil blocks
+      const int nsb = gridDim.x - a.n_spmv_blocks;
+      const int ntx = (n + BST_C - 1) / BST_C, nty = (n + BST_R - 1) / BST_R;
+      const int nchunks = Kp / BST_S;
+      const int ntiles = ntx * nty;
+      __shared__ float sreg_hi[MAXK], sreg_lo[MAXK];  // per-slot regulariser sums
+      __shared__ int chunk_on[MAXK / BST_S];
+      for (int s = tid; s < MAXK; s += blockDim.x) {
+        sreg_hi[s] = 0.f;
+        sreg_lo[s] = 0.f;
       }
-      chunk_on[c] = any;
-    }
-    __syncthreads();
-    // Each block owns the same tiles for every slot chunk, so a slot's
-    // regulariser sum is grouped the same way whatever its slot index.
-    for (int tile = blockIdx.x - a.n_spmv_blocks; tile < ntiles; tile += nsb)
-    for (int chunk = 0; chunk < nchunks; ++chunk) {
-      if (!chunk_on[chunk]) continue;  // uniform over the block
-      const int r0 = (tile / ntx) * BST_R, c0 = (tile % ntx) * BST_C;
-      const float reg = bstencil_item(sm.st, f, a.f[(G + 2) % 3], a.slots, Kp, r0, c0,
-                                      chunk * BST_S, n, a.gR, want, a.mode);
-      if (want) {
-        // warp q holds slot chunk*8 + q: fold the warp's 32 columns
-        float h = reg, l = 0.f;
-        warp_sum_acc(h, l);
-        if (lane == 0) {
-          const int s = chunk * BST_S + warp;
-          acc_add(sreg_hi[s], sreg_lo[s], h, l);
+      for (int c = tid; c < nchunks; c += blockDim.x) {
+        int any = 0;
+        for (int q = 0; q < BST_S; ++q) {
+          const SlotState& sl = a.slots[c * BST_S + q];
+          any |= a.mode == 2 ? sl.fresh : (sl.active && !sl.done);
+        }
+        chunk_on[c] = any;
+      }
+      __syncthreads();
+      // Each block owns the same tiles for every slot chunk, so a slot's
+      // regulariser sum is grouped the same way whatever its slot index.
+      for (int tile = blockIdx.x - a.n_spmv_blocks; tile < ntiles; tile += nsb)
+      for (int chunk = 0; chunk < nchunks; ++chunk) {
+        if (!chunk_on[chunk]) continue;  // uniform over the block
+        const int r0 = (tile / ntx) * BST_R, c0 = (tile % ntx) * BST_C;
+        const float reg = bstencil_item(sm.st, f, a.f[(G + 2) % 3], a.slots, Kp, r0, c0,
+                                        chunk * BST_S, n, a.gR, want, a.mode);
+        if (want) {
+          // warp q holds slot chunk*8 + q: fold the warp's 32 columns
+          float h = reg, l = 0.f;
+          warp_sum_acc(h, l);
+          if (lane == 0) {
+            const int s = chunk * BST_S + warp;
+            acc_add(sreg_hi[s], sreg_lo[s], h, l);
+          }
         }
       }
-    }
-    __syncthreads();
-    if (want && warp == 0) {
-      // hand the per-slot sums to the lanes that own the slots in warp 0
-#pragma unroll
-      for (int t = 0; t < V; ++t) {
-        dh[t] = sreg_hi[lane * V + t];
-        dl[t] = sreg_lo[lane * V + t];
+      __syncthreads();
+      if (want && warp == 0) {
+        // hand the per-slot sums to the lanes that own the slots in warp 0
+  #pragma unroll
+        for (int t = 0; t < V; ++t) {
+          dh[t] = sreg_hi[lane * V + t];
+          dl[t] = sreg_lo[lane * V + t];
+        }
       }
     }
   }
@@ -886,10 +906,17 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   int nsp = 0;
   const int grid = bforward_grid_n(a, &nsp);
   a.n_spmv_blocks = nsp;
-  if (a.use_bf16)
-    k_bforward<V, true><<<grid, B_THREADS, 0, s>>>(a);
-  else
-    k_bforward<V, false><<<grid, B_THREADS, 0, s>>>(a);
+  if (grid > nsp) {
+    if (a.use_bf16)
+      k_bforward<V, true, true><<<grid, B_THREADS, 0, s>>>(a);
+    else
+      k_bforward<V, false, true><<<grid, B_THREADS, 0, s>>>(a);
+  } else {
+    if (a.use_bf16)
+      k_bforward<V, true, false><<<grid, B_THREADS, 0, s>>>(a);
+    else
+      k_bforward<V, false, false><<<grid, B_THREADS, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 template <int V>
