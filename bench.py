@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 120 x 512^2 batched leg")
     ap.add_argument("--no-volume", action="store_true",
                     help="skip the 64-slice 3-D SHOITV volume leg")
+    ap.add_argument("--no-afppa", action="store_true",
+                    help="skip the AFPPA (non-smooth HOITV) and figures-of-merit legs")
     ap.add_argument("--volume-only", action="store_true",
                     help="run only the volume leg and print its JSON (for profiling)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -318,6 +320,78 @@ def bench_volume(AP, ctx, geom, A, dev, batched_rate, nz=64, counts=6.4e7, iters
                         "algorithmic_bytes_per_launch": 8 * vox,
                         "achieved_gbs": 8 * vox / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
                         "peak_source": src, "frac": 8 * vox / (ms * 1e-3) / 1e9 / hbm}
+    mat.close()
+    return out
+
+
+def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
+    """AFPPA with GN momentum for the non-smooth HOITV model (Sec. 4.4) on the
+    main slice: time per step on the GPU (projectors + dual-update kernel)
+    against one APPGA iteration, the FP64 oracle's step on the host, and the
+    figures of merit of the result (MSE, PSNR, RC / NRC on a lesion mask,
+    central line profile) with their own call time."""
+    import numpy as np
+    import torch
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
+    g = torch.from_numpy(sl.g).to(dev)
+    gam = torch.from_numpy(sl.gamma).to(dev)
+    f = torch.empty(geom.d, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def call(n):
+        p = AP.default_params(lambda1=LAM1, lambda2=LAM2, omega=OMEGA, max_iters=n)
+        AP.appga_afppa_reconstruct(ctx.handle, mat.handle, g, gam, None, p, f)
+    for _ in range(2):
+        call(8)
+    per = sorted((timed(lambda: call(8 + iters)) - timed(lambda: call(8))) / iters
+                 for _ in range(3))[1]
+    out = {"workload": f"AFPPA (GN momentum, omega {OMEGA:g}) for the non-smooth HOITV model on "
+                       f"the main {geom.n}x{geom.n} slice, lambda1/lambda2 {LAM1:g}/{LAM2:g}, "
+                       f"rates over {iters} timed steps",
+           "us_per_step": 1e3 * per, "steps_per_s": 1.0 / (per * 1e-3),
+           "vs_appga_iteration": per / appga_ms}
+    if cpu:
+        from oracle import afppa_oracle as F
+        from oracle import appga_oracle as O
+        prob = O.Problem(A, sl.g, sl.gamma, geom.n)
+        par = O.Params(lambda1=LAM1, lambda2=LAM2, omega=OMEGA, max_iters=3)
+        t0 = time.perf_counter()
+        F.afppa(prob, par, n_angles=geom.n_angles)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 3 / el, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "sample": f"3 FP64 oracle AFPPA steps of the same slice, {el:.1f} s"}
+    # figures of merit of the AFPPA result against the phantom (Sec. 4.1)
+    call(iters)
+    n = geom.n
+    truth = torch.from_numpy(sl.f_true.astype(np.float32)).to(dev)
+    hot = sl.f_true > 1.5 * np.median(sl.f_true[sl.f_true > 0])
+    body = (sl.f_true > 0) & ~hot
+    roi_h = torch.from_numpy(hot.astype(np.uint8)).to(dev)
+    roi_b = torch.from_numpy(body.astype(np.uint8)).to(dev)
+    vmax = float(sl.f_true.max())
+    for _ in range(3):
+        fm = AP.appga_figures_of_merit(ctx.handle, geom.d, f, truth, roi_h, roi_b, vmax)
+    t0 = time.perf_counter()
+    for _ in range(20):
+        fm = AP.appga_figures_of_merit(ctx.handle, geom.d, f, truth, roi_h, roi_b, vmax)
+    us_fom = (time.perf_counter() - t0) / 20 * 1e6
+    prof = torch.empty(n, dtype=torch.float32, device=dev)
+    AP.appga_central_line_profile(ctx.handle, n, f, prof)
+    torch.cuda.synchronize()
+    out["figures_of_merit"] = {"mse": fm.mse, "psnr_db": fm.psnr, "nrc": fm.nrc,
+                               "roi_hot_pixels": int(fm.n_roi_h),
+                               "us_per_call": us_fom,
+                               "note": "one call = MSE, PSNR, RC and NRC reductions in double-float "
+                                       "plus the host read-back (latency-bound at this size)"}
     mat.close()
     return out
 
@@ -610,6 +684,10 @@ def run_ours(args):
                                     "log-uniform 1e4..1e7 (8 distinct sinograms repeated), "
                                     "omega 1, beta 1; rates over 60 timed iterations of a "
                                     "300-iteration schedule")
+    afppa = None
+    if world == 1 and not args.no_afppa:
+        afppa = bench_afppa(AP, ctx, geom, A, sl, dev, ms_max / args.steps,
+                            cpu=rank == 0 and not args.no_cpu_baseline)
     volume = None
     if world == 1 and not args.no_volume:
         brate = None
@@ -645,6 +723,7 @@ def run_ours(args):
             "batched": batched,
             "large_batch": large,
             "volume": volume,
+            "afppa": afppa,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
