@@ -371,6 +371,8 @@ appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int
       }
     }
   }
+  if (fin.flags & APPGA_FLAG_TIMEOUT)
+    return fail(APPGA_ETIMEOUT, "a bounded device wait ran out; the run stopped");
   if (fin.flags & APPGA_FLAG_NONFINITE)
     return fail(APPGA_ENUMERIC, "a non-finite value appeared in the iteration");
   return APPGA_OK;
