@@ -47,7 +47,7 @@ BATCH_K = 64
 BATCH_ITERS = 200
 SERVE_GEOMS = ("128", "256", "400")
 SERVE_RATE = 100.0
-SERVE_SLOTS = 64
+SERVE_SLOTS = 0  # adaptive pool widths (32 / 64 / 128 slots by demand)
 SERVE_STEPS = 8
 
 
@@ -69,6 +69,12 @@ def parse():
     ap.add_argument("--volume-only", action="store_true",
                     help="run only the volume leg and print its JSON (for profiling)")
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS, choices=(0, 32, 64, 128),
+                    help="slots per server pool (0: adaptive widths)")
+    ap.add_argument("--serve-steps", type=int, default=SERVE_STEPS,
+                    help="APPGA maps per graph replay of a server pool")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving leg and print its JSON (for tuning)")
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests/s)")
     return ap.parse_args()
@@ -396,7 +402,8 @@ def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
     return out
 
 
-def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A):
+def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
+                  slots: int = SERVE_SLOTS, steps: int = SERVE_STEPS):
     """Poisson stream of reconstruction requests mixing 128^2, 256^2 and 400^2
     slices (200..800 iterations each, or the relative objective change
     < 1e-7) through the continuous-batching server."""
@@ -411,7 +418,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A):
         counts = W.log_uniform_counts(rng, 1e5, 1e7, 6)
         slices[nm] = [W.make_slice(A, geom, float(c), W.seed_for(4, 100 * idx + i),
                                    phantom="lesions") for i, c in enumerate(counts)]
-    srv = AP.Server(ctx, slots_per_pool=SERVE_SLOTS, steps_per_launch=SERVE_STEPS)
+    srv = AP.Server(ctx, slots_per_pool=slots, steps_per_launch=steps)
     gids = {nm: srv.add_geometry(mats[nm]) for nm in SERVE_GEOMS}
     # warm-up: one short request per geometry (pools and graphs are created here)
     for nm in SERVE_GEOMS:
@@ -473,8 +480,8 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A):
         "server_p50_latency_s": summ.p50_latency_s, "server_p99_latency_s": summ.p99_latency_s,
         "latency_from": "arrival time of the request in the stream (the server's own figures "
                         "count from submission)",
-        "pools": summ.pools, "device_bytes": summ.device_bytes, "slots_per_pool": SERVE_SLOTS,
-        "steps_per_launch": SERVE_STEPS,
+        "pools": summ.pools, "device_bytes": summ.device_bytes, "slots_per_pool": slots,
+        "steps_per_launch": steps,
     }
 
 
@@ -566,6 +573,12 @@ def run_ours(args):
     ctx = AP.Context(dev.index)
     if args.volume_only:
         print(json.dumps({"volume": bench_volume(AP, ctx, geom, A, dev, None)}), flush=True)
+        ctx.close()
+        return 0
+    if args.serve_only:
+        print(json.dumps({"serving": bench_serving(AP, ctx, args.serve_requests, args.serve_rate,
+                                                   geom, A, args.serve_slots,
+                                                   args.serve_steps)}), flush=True)
         ctx.close()
         return 0
     mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
@@ -695,7 +708,8 @@ def run_ours(args):
             brate = {k: batched[k]["slices_iters_per_s"] for k in ("fp32", "bf16")}
         volume = bench_volume(AP, ctx, geom, A, dev, brate)
     if world == 1 and not args.no_serve:
-        serving = bench_serving(AP, ctx, args.serve_requests, args.serve_rate, geom, A)
+        serving = bench_serving(AP, ctx, args.serve_requests, args.serve_rate, geom, A,
+                                args.serve_slots, args.serve_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -11,7 +11,12 @@
  *    (appga_matrix, created by the caller and kept alive until the server is
  *    destroyed).  appga_server_add_geometry registers one and returns its id.
  *  - Pools.  Requests of one geometry run in pools of `slots_per_pool` slots
- *    that share the matrix: one pool is one batched solver (the slot-minor
+ *    (or, with slots_per_pool 0, of 32, 64 or 128 slots: each new pool the
+ *    narrowest that holds the geometry's demand, its waiting requests plus
+ *    those running in its pools, and admission fills
+ *    the narrowest pool with a free slot first -- narrow pools step faster at
+ *    light load, wide pools read the matrix once for more slices under heavy
+ *    load) that share the matrix: one pool is one batched solver (the slot-minor
  *    SpMM kernels of appga_reconstruct_batched) whose iterates, momentum
  *    scalars, objective values and counters stay in device memory for the
  *    whole life of each request.  A pool steps `steps_per_launch` APPGA maps
@@ -33,7 +38,9 @@
  * A request's result does not depend on which slot it runs in, on the other
  * requests of its pool, or on when it was admitted: every slot runs the same
  * per-slot arithmetic, so the same request gives the same image alone and in
- * any mix with the same pool width and precision.
+ * any mix with the same pool width and precision.  (With adaptive widths a
+ * request's pool width depends on the load, and images of the same request
+ * agree to FP32 rounding across widths.)
  *
  * Threading: a server is driven by one host thread at a time; every call
  * below runs on the library stream of the server's context and
@@ -52,7 +59,7 @@ extern "C" {
 typedef struct appga_server appga_server;
 
 typedef struct {
-  int32_t slots_per_pool;    /* 32, 64 or 128 slots per pool */
+  int32_t slots_per_pool;    /* 32, 64 or 128 slots per pool; 0: adaptive (above) */
   int32_t steps_per_launch;  /* APPGA maps per graph replay, >= 1 */
   int32_t a_precision;       /* APPGA_PREC_FP32 or APPGA_PREC_BF16 (the
                                 matrix needs its BF16 copy) for every pool */
@@ -93,8 +100,8 @@ typedef struct {
   double mean_queue_s;   /* admission minus submission, mean over completed */
 } appga_server_summary;
 
-/* appga_server_create: EINVAL for a bad config (slots_per_pool not 32, 64 or
- * 128; steps_per_launch < 1; negative sizes). */
+/* appga_server_create: EINVAL for a bad config (slots_per_pool not 0, 32, 64
+ * or 128; steps_per_launch < 1; negative sizes). */
 appga_status appga_server_create(appga_ctx* ctx, const appga_server_config* cfg,
                                  appga_server** out);
 /* Frees every pool; requests not collected are dropped. */

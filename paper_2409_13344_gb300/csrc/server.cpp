@@ -127,10 +127,9 @@ namespace {
 
 #define CK(call) APPGA_CK(call)
 
-appga_status create_pool(appga_server* S, int geom, Pool** out) {
+appga_status create_pool(appga_server* S, int geom, int Kp, Pool** out) {
   *out = nullptr;
   const appga_matrix* M = S->geoms[geom].M;
-  const int Kp = S->cfg.slots_per_pool;
   auto P = std::make_unique<Pool>();
   P->geom = geom;
   P->bytes = pool_bytes(M, Kp);
@@ -202,10 +201,24 @@ int live_pools(const appga_server* S) {
   return c;
 }
 
-// Whether a new pool of geometry `geom` fits the pool cap and device memory.
-bool pool_fits(appga_server* S, int geom) {
+// Width of a new pool of geometry `geom`: the configured one, or (adaptive,
+// slots_per_pool 0) the narrowest of 32, 64, 128 slots that holds the
+// geometry's demand (its waiting requests plus those running in its pools):
+// narrow pools step faster when few requests are in flight, wide pools read
+// the matrix once for more slices under load.
+int new_pool_width(const appga_server* S, int geom) {
+  if (S->cfg.slots_per_pool > 0) return S->cfg.slots_per_pool;
+  size_t demand = S->geoms[geom].waiting.size();
+  for (const auto& q : S->pools)
+    if (q && q->geom == geom) demand += (size_t)q->used;
+  return demand <= 32 ? 32 : (demand <= 64 ? 64 : 128);
+}
+
+// Whether a new pool of geometry `geom` and width Kp fits the pool cap and
+// device memory.
+bool pool_fits(appga_server* S, int geom, int Kp) {
   if (S->cfg.max_pools > 0 && live_pools(S) >= S->cfg.max_pools) return false;
-  const int64_t need = pool_bytes(S->geoms[geom].M, S->cfg.slots_per_pool);
+  const int64_t need = pool_bytes(S->geoms[geom].M, Kp);
   if (S->cfg.hbm_budget_bytes > 0 && S->bytes + need > S->cfg.hbm_budget_bytes) return false;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
@@ -310,19 +323,18 @@ appga_status admit_all(appga_server* S) {
     Geometry& G = S->geoms[gi];
     bool released = false;
     while (!G.waiting.empty()) {
+      // the narrowest pool of this geometry with a free slot
       Pool* P = nullptr;
       for (auto& q : S->pools)
-        if (q && q->geom == gi && q->free_slots() > 0) {
-          P = q.get();
-          break;
-        }
+        if (q && q->geom == gi && q->free_slots() > 0 && (!P || q->b.Kp < P->b.Kp)) P = q.get();
       if (!P) {
-        if (!pool_fits(S, gi)) {
+        const int width = new_pool_width(S, gi);
+        if (!pool_fits(S, gi, width)) {
           if (released || !release_empty_pools(S, gi)) break;  // waits for memory
           released = true;
-          if (!pool_fits(S, gi)) break;
+          if (!pool_fits(S, gi, width)) break;
         }
-        appga_status rc = create_pool(S, gi, &P);
+        appga_status rc = create_pool(S, gi, width, &P);
         if (rc != APPGA_OK) return rc;
       }
       appga_status rc = admit(S, P, P->free_slots());
@@ -410,9 +422,9 @@ extern "C" appga_status appga_server_create(appga_ctx* ctx, const appga_server_c
                                             appga_server** out) {
   if (!ctx || !cfg || !out) return fail(APPGA_EINVAL, "null argument");
   *out = nullptr;
-  const int kp = cfg->slots_per_pool;
-  if (kp != 32 && kp != 64 && kp != 128)
-    return fail(APPGA_EINVAL, "slots_per_pool must be 32, 64 or 128");
+  const int kp = cfg->slots_per_pool;  // 0: adaptive widths
+  if (kp != 0 && kp != 32 && kp != 64 && kp != 128)
+    return fail(APPGA_EINVAL, "slots_per_pool must be 0 (adaptive), 32, 64 or 128");
   if (cfg->steps_per_launch < 1) return fail(APPGA_EINVAL, "steps_per_launch must be >= 1");
   if (cfg->a_precision != APPGA_PREC_FP32 && cfg->a_precision != APPGA_PREC_BF16)
     return fail(APPGA_EINVAL, "a_precision must be APPGA_PREC_FP32 or APPGA_PREC_BF16");

@@ -306,3 +306,51 @@ def test_server_rejects_bad_requests(A, ctx):
     with pytest.raises(A.AppgaError) as ei:
         A.Server(ctx, slots_per_pool=48)
     assert ei.value.status == A.APPGA_EINVAL
+
+
+def _one_pool_bytes(A, ctx, mat, sl, width):
+    probe = A.Server(ctx, slots_per_pool=width)
+    pid = probe.add_geometry(mat)
+    probe.submit(pid, sl.g, sl.gamma, A.default_params(max_iters=1))
+    probe.step()
+    b = probe.summary().device_bytes
+    probe.close()
+    return b
+
+
+def test_adaptive_pool_widths(A, ctx):
+    """slots_per_pool 0: a lone request gets a 32-slot pool and a burst of 40
+    waiting requests one 64-slot pool (pool sizes read from the device memory
+    the server holds); each image equals, bit for bit, the same request run
+    alone in a fixed-width pool of that width, and the oracle to 1e-5."""
+    geom, Amat, mat = matrix(A, ctx, "64")
+    sls = make_slices(geom, Amat, [1e5 * (1 + i % 5) for i in range(40)], config=15)
+    b32 = _one_pool_bytes(A, ctx, mat, sls[0], 32)
+    b64 = _one_pool_bytes(A, ctx, mat, sls[0], 64)
+    assert b64 > b32
+    p = A.default_params(max_iters=12)
+    srv = A.Server(ctx, slots_per_pool=0)
+    gid = srv.add_geometry(mat)
+    rid = srv.submit(gid, sls[0].g, sls[0].gamma, p)
+    srv.step()
+    assert (srv.summary().pools, srv.summary().device_bytes) == (1, b32)
+    drain(srv)
+    f_lone, _ = srv.collect(rid)
+    srv.close()
+    f32, _ = run_alone(A, ctx, mat, sls[0], p, slots_per_pool=32)
+    assert np.array_equal(f_lone, f32)
+
+    srv = A.Server(ctx, slots_per_pool=0)
+    gid = srv.add_geometry(mat)
+    ids = [srv.submit(gid, s.g, s.gamma, p) for s in sls]
+    srv.step()
+    assert (srv.summary().pools, srv.summary().device_bytes) == (1, b64)
+    drain(srv)
+    f_burst = [srv.collect(i)[0] for i in ids]
+    srv.close()
+    f64, _ = run_alone(A, ctx, mat, sls[7], p, slots_per_pool=64)
+    assert np.array_equal(f_burst[7], f64)
+    for s, f in zip(sls[:4], f_burst[:4]):
+        prob = O.Problem(Amat, s.g, s.gamma, geom.n)
+        ref = O.appga(prob, O.Params(max_iters=12), n_angles=geom.n_angles, track_phi=False)
+        assert rel(f, ref.f) <= 1e-5
