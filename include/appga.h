@@ -156,8 +156,10 @@ typedef struct {
 } appga_stats;
 
 /* ------------------------------------------------- single hot-path steps
- * Each call below runs exactly the kernel the solver loop runs for that
- * step, once, with the given inputs.
+ * Each call below runs the kernel the solver loop runs for that step, once,
+ * with the given inputs (appga_forward_ratio runs the forward kernel's
+ * double-float instance; the solver loop accumulates y in FP32 and gathers
+ * f from a copy in an 8 x 8-tiled pixel order).
  *
  * appga_forward_ratio (steps a1-a2, Sec. 2.2 grad F): for every bin i
  *   y_i  = (A f)_i, accumulated in double-float (FP32 pairs) and stored as
@@ -211,7 +213,11 @@ appga_status appga_initial_image(appga_ctx* ctx, const appga_matrix* mat, const 
  * gamma: float[m] (> 0).  stats_host may be NULL.  The iteration runs as
  * captured CUDA graphs on `stream`; the call returns once the result is in
  * f_out (it synchronises the stream).  Inputs are validated on the device
- * (EDOMAIN for negative or non-finite g, non-positive or non-finite gamma). */
+ * (EDOMAIN for negative or non-finite g, non-positive or non-finite gamma).
+ * Arithmetic: FP32 projections and updates, y = A f accumulated in FP32,
+ * the objective's logarithm and sums in double-float, the momentum scalars,
+ * Phi and the stopping test in FP64.  ETIMEOUT if a bounded device wait ran
+ * out; ENUMERIC if a non-finite value appeared. */
 appga_status appga_reconstruct(appga_ctx* ctx, const appga_matrix* mat, const float* g,
                                const float* gamma, const float* f_init,
                                const appga_params* params, float* f_out,
