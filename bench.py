@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="wall-time bound of the reference arm's timed oracle steps")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-slice batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 120 x 512^2 batched leg")
@@ -528,20 +530,30 @@ def run_reference(args):
         prob.objective(fn, LAM1, LAM2, EPS)
         fm, f = f, fn
 
+    # One oracle iteration takes tens of milliseconds on one host core, so the
+    # run is bounded in wall time: at most 3 warm-up steps, then steps until
+    # --steps are done or --ref-seconds have passed (at least one).
     k = 0
-    for _ in range(args.warmup):
+    warm = min(args.warmup, 3)
+    for _ in range(warm):
         k += 1
         step(k)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    done, el = 0, 0.0
+    while done < max(args.steps, 1):
         k += 1
         step(k)
-    el = time.perf_counter() - t0
-    val = args.steps / el
-    sample = f"{args.steps} APPGA iterations of the 256x256 slice (after {args.warmup} warm-up)"
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= args.ref_seconds:
+            break
+    val = done / el
+    sample = (f"{done} FP64 oracle APPGA iterations of the 256x256 slice (of {args.steps} "
+              f"requested; bounded to {args.ref_seconds:g} s) after {warm} warm-up")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": done, "requested_steps": args.steps, "warmup": warm,
+        "ms_per_step": 1e3 * el / done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "reference": "FP64 NumPy/SciPy oracle on the host"},
