@@ -265,6 +265,28 @@ def bench_batched(AP, ctx, geom, A, dev, single_rate, K=BATCH_K, lo=1e5, hi=1e7,
                              "trial_us_per_slice_iter": t.us_per_slice_iter,
                              "trial_us_default": t.us_per_slice_iter_default}
         out[name + "_autotuned"] = tuned
+    # the second ceiling of the batched kernels: their gather loop alone
+    # (L1/L2-bound), timed by the library's probe on this matrix
+    sch = out["fp32_autotuned"]["schedule"]
+    k_eff = sch["chunk"] if 0 < sch["chunk"] < K else K
+    width = 32 if k_eff <= 32 else (64 if k_eff <= 64 else 128)
+    p_fwd, p_bwd = AP.appga_gather_probe(ctx.handle, mat.handle, width, 20)
+    info = mat.info()
+    b_fwd = int(info.nnz_padded_a) * 4 * width  # gathered bytes per (sub-)batch projection
+    b_bwd = int(info.nnz_padded_t) * 4 * width
+    # the iteration's gather ceiling: both projections at their probed rates
+    t_ceil = b_fwd / (p_fwd * 1e9) + b_bwd / (p_bwd * 1e9)
+    t_iter = k_eff / out["fp32_autotuned"]["slices_iters_per_s"]  # per (sub-)batch iteration
+    out["fp32_autotuned"]["gather_roofline"] = {
+        "bound": "l1/l2 gathers", "unit": "GB/s", "width": width,
+        "probe_fwd_gbs": p_fwd, "probe_bwd_gbs": p_bwd,
+        "achieved_gbs": (b_fwd + b_bwd) / t_iter / 1e9,
+        "peak": (b_fwd + b_bwd) / t_ceil / 1e9, "frac": t_ceil / t_iter,
+        "note": "bytes = Kp-wide rows gathered by both projections per (sub-)batch iteration; "
+                "peak = those bytes at the rates appga_gather_probe measures for the projectors' "
+                "inner loop alone (column/value stream + gathers, no epilogue, stencil or pixel "
+                "update; fastest grid size) on this matrix, so frac is the share of the "
+                "iteration's time that is projector gathers"}
     out["algorithmic_bytes_per_iter"] = nb
     mat.close()
     return out

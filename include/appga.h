@@ -257,6 +257,21 @@ appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, 
                                        const appga_params* params, float* f_out,
                                        appga_stats* stats_host, void* stream);
 
+/* appga_gather_probe: the rate of the batched projectors' inner loop alone on
+ * this matrix (a measurement utility; the paper has no counterpart).  It
+ * times `launches` runs of a kernel that runs only that loop: every row
+ * reduced against the width-float rows of a slot-minor block named by its
+ * columns (the column/value stream and the gathers), in the projectors' row
+ * order, with no epilogue, stencil or pixel update, for several grid sizes
+ * (blocks per SM), and keeps the fastest.  *gbs_fwd: A's rows against an
+ * image block [d][width] (the forward projection); *gbs_bwd: A^T's rows
+ * against a weight block [m][width] (the back-projection); both host doubles,
+ * gathered bytes (padded entries x width x 4) per second / 1e9.  width: 32,
+ * 64 or 128; launches >= 1 per grid size.  Uses the matrix's batched
+ * workspace; synchronises. */
+appga_status appga_gather_probe(appga_ctx* ctx, const appga_matrix* mat, int32_t width,
+                                int32_t launches, double* gbs_fwd, double* gbs_bwd);
+
 /* ------------------------------------------------------------ 3-D SHOITV
  * The paper states HOITV in 2-D (Sec. 2.1) and refers to other work for 3-D.
  * These calls use its Kronecker generalisation: for a volume of nz slices of

@@ -159,6 +159,8 @@ SIGNATURES = {
     "appga_reconstruct_batched": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P,
                                                  ctypes.POINTER(appga_params), _P,
                                                  ctypes.POINTER(appga_stats), _P]),
+    "appga_gather_probe": (ctypes.c_int, [_P, _P, _I32, _I32, ctypes.POINTER(_D),
+                                          ctypes.POINTER(_D)]),
     "appga_shoitv3d_grad": (ctypes.c_int, [_P, _I32, _I32, _P, _D, _D, _D, _P, _P, _P]),
     "appga_reconstruct_volume": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P,
                                                 ctypes.POINTER(appga_params), _P,
@@ -372,6 +374,16 @@ def appga_reconstruct_batched(ctx, mat, K, g, gamma, f_init, params, f_out, stre
                                                     st, _stream(stream)),
            "appga_reconstruct_batched")
     return list(st)
+
+
+def appga_gather_probe(ctx, mat, width: int = 64, launches: int = 20):
+    """Rate (gathered GB/s) of the batched projectors' inner loop alone on
+    this matrix, forward projection and back-projection (see appga.h):
+    (fwd, bwd)."""
+    fwd, bwd = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().appga_gather_probe(ctx, mat, width, launches, ctypes.byref(fwd),
+                                             ctypes.byref(bwd)), "appga_gather_probe")
+    return fwd.value, bwd.value
 
 
 def appga_shoitv3d_grad(ctx, n_side, nz, f, lambda1, lambda2, eps, out, reg_out=None,

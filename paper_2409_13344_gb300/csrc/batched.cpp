@@ -463,6 +463,63 @@ extern "C" appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_ma
                      tuned_schedule(M, padded_width(K), bf16), stream);
 }
 
+namespace appga {
+namespace {
+// best gathered GB/s over launch shapes for the column stream `col` (nnz
+// entries) into the slot-minor block x of `width` floats per row
+appga_status probe_best(const DevCSR& M, bool forward, const float* x, int width, float* sink,
+                        int launches, cudaStream_t s, double* best) {
+  const long long nnz = M.nnz_padded;
+  *best = 0.0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  CK(cudaEventCreate(&ev[0]));
+  cudaError_t e = cudaEventCreate(&ev[1]);
+  for (const int per_sm : {3, 4, 5, 6, 8}) {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+      e = launch_gather_probe(M, forward, x, width, sink, per_sm, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    for (int i = 0; i < launches && e == cudaSuccess; ++i)
+      e = launch_gather_probe(M, forward, x, width, sink, per_sm, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (e != cudaSuccess) break;
+    const double gbs = (double)launches * (double)nnz * width * sizeof(float) / (ms * 1e-3) / 1e9;
+    if (gbs > *best) *best = gbs;
+  }
+  cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "appga_gather_probe");
+  return APPGA_OK;
+}
+}  // namespace
+}  // namespace appga
+
+extern "C" appga_status appga_gather_probe(appga_ctx* ctx, const appga_matrix* mat,
+                                           int32_t width, int32_t launches, double* gbs_fwd,
+                                           double* gbs_bwd) {
+  if (!ctx || !mat || !gbs_fwd || !gbs_bwd) return fail(APPGA_EINVAL, "null argument");
+  if (mat->ctx != ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
+  if (width != 32 && width != 64 && width != 128)
+    return fail(APPGA_EINVAL, "width must be 32, 64 or 128");
+  if (launches < 1) return fail(APPGA_EINVAL, "launches must be >= 1");
+  auto* M = const_cast<appga_matrix*>(mat);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(APPGA_ENODEV, "cudaSetDevice failed");
+  appga_status rc = ensure_batch_workspace(M, width);
+  if (rc != APPGA_OK) return rc;
+  BatchWorkspace& b = *M->bw;
+  cudaStream_t s = ctx->stream;
+  float* sink = reinterpret_cast<float*>(b.partial);
+  // forward projection: A's columns into the image block [d][width];
+  // back-projection: A^T's columns into the weight block [m][width]
+  CK(cudaMemsetAsync(b.f[0], 0, (size_t)M->d * width * sizeof(float), s));
+  CK(cudaMemsetAsync(b.w, 0, (size_t)M->m * width * sizeof(float), s));
+  rc = probe_best(M->A, true, b.f[0], width, sink, launches, s, gbs_fwd);
+  if (rc == APPGA_OK) rc = probe_best(M->At, false, b.w, width, sink, launches, s, gbs_bwd);
+  return rc;
+}
+
 extern "C" appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matrix* mat,
                                                int32_t K, const float* g, const float* gamma,
                                                const appga_params* params,

@@ -125,6 +125,13 @@ int bforward_grid(const BFwdArgs& a);
 // last pixel phase): copy it into the current entry and clear the mark.
 cudaError_t launch_resolve_rollback(const BFwdArgs& a, cudaStream_t s);
 cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s);
+// The batched projectors' inner loop alone over M (rows reduced against the
+// Kp-wide rows of x, [cols][Kp]; no epilogue) in the row order of the forward
+// projection (forward) or of the back-projection, with blocks_per_sm (1..16)
+// blocks per SM; sink: at least (SMs x 16) floats, written only in a case
+// that does not arise.
+cudaError_t launch_gather_probe(const DevCSR& M, bool forward, const float* x, int Kp,
+                                float* sink, int blocks_per_sm, cudaStream_t s);
 cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s);
 // Slot lists: where `ids` is given, slice k goes to slot ids[k] (a device
 // array of K ints); otherwise to slot s0 + k.

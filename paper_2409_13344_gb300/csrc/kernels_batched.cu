@@ -78,6 +78,18 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
 #ifndef APPGA_BCONTIG
 #define APPGA_BCONTIG 1
 #endif
+// Row order of each projection: a contiguous run of rows per block (1) or
+// rows dealt to the warps of the whole grid in turn (0).  The forward
+// projection gathers image rows faster dealt in turn (the whole grid works
+// on neighbouring rays at once, so the rows it gathers stay in L2); the
+// back-projection keeps contiguous runs of pixels (their weight rows are
+// reused from L1).
+#ifndef APPGA_BCONTIG_FW
+#define APPGA_BCONTIG_FW 0
+#endif
+#ifndef APPGA_BCONTIG_PX
+#define APPGA_BCONTIG_PX APPGA_BCONTIG
+#endif
 
 // One CSR row of M times the Kp-wide columns of X ([cols][Kp]): lane holds
 // the V sums of slots lane*V .. lane*V + V - 1.  Each lane loads one of 32
@@ -442,7 +454,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   }
   if (!ST || (int)blockIdx.x < a.n_spmv_blocks) {
     const uint64_t pol = evict_first_policy();
-#if APPGA_BCONTIG
+#if APPGA_BCONTIG_FW
     // each block owns a contiguous run of rows (neighbouring rays share
     // pixels, so the gathered image rows are reused from L1)
     const int per = (a.A.rows + a.n_spmv_blocks - 1) / a.n_spmv_blocks;
@@ -597,7 +609,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
   for (int t = 0; t < V; ++t) lane_live = lane_live || live[t];
   const uint64_t pol = evict_first_policy();
   int bad = 0;
-#if APPGA_BCONTIG
+#if APPGA_BCONTIG_PX
   // each block owns a contiguous run of pixels (neighbouring pixels lie on
   // the same rays, so the gathered weight rows are reused from L1)
   const int per = (a.At.rows + gridDim.x - 1) / gridDim.x;
@@ -898,6 +910,34 @@ int bforward_grid_n(const BFwdArgs& a, int* n_spmv) {
   return nsp + nst;
 }
 
+// Gather probe: the batched projectors' inner loop alone.  Every row of M
+// is reduced against the Kp-wide slot-minor rows of x by brow_dot, in the
+// row order of the projection it stands for (contig: a contiguous run of
+// rows per block, else rows dealt to the grid's warps in turn), with no
+// epilogue, stencil or pixel update: the time of the column/value stream and
+// the gathers by themselves.
+template <int V>
+__global__ void __launch_bounds__(B_THREADS) k_gather_probe(DevCSR M, const float* __restrict__ x,
+                                                            int Kp, int contig,
+                                                            float* __restrict__ sink) {
+  __shared__ __align__(16) int s_off[B_WARPS][32];
+  __shared__ __align__(16) float s_val[B_WARPS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t pol = evict_first_policy();
+  const int per = (M.rows + gridDim.x - 1) / gridDim.x;
+  const int r0 = contig ? blockIdx.x * per : blockIdx.x * B_WARPS;
+  const int r1 = contig ? min(M.rows, r0 + per) : M.rows;
+  const int step = contig ? B_WARPS : gridDim.x * B_WARPS;
+  float s = 0.f;
+  for (int row = r0 + warp; row < r1; row += step) {
+    float acc[V];
+    brow_dot<V, false>(M, row, x, Kp, lane, true, pol, s_off[warp], s_val[warp], acc);
+#pragma unroll
+    for (int t = 0; t < V; ++t) s += acc[t];
+  }
+  if (s == 1.0e38f) sink[blockIdx.x] = s;  // keeps the loads; the value is never used
+}
+
 template <int V>
 cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   BFwdArgs a = a0;
@@ -960,6 +1000,20 @@ cudaError_t launch_bforward(const BFwdArgs& a, cudaStream_t s) {
     case 4: return bforward_v<4>(a, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gather_probe(const DevCSR& M, bool forward, const float* x, int Kp,
+                                float* sink, int blocks_per_sm, cudaStream_t s) {
+  if (blocks_per_sm < 1 || blocks_per_sm > kMaxPerSm) return cudaErrorInvalidValue;
+  const int grid = sm_count() * blocks_per_sm;
+  const int contig = forward ? APPGA_BCONTIG_FW : APPGA_BCONTIG_PX;
+  switch (Kp / 32) {
+    case 1: k_gather_probe<1><<<grid, B_THREADS, 0, s>>>(M, x, Kp, contig, sink); break;
+    case 2: k_gather_probe<2><<<grid, B_THREADS, 0, s>>>(M, x, Kp, contig, sink); break;
+    case 4: k_gather_probe<4><<<grid, B_THREADS, 0, s>>>(M, x, Kp, contig, sink); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bpixel(const BPixArgs& a, cudaStream_t s) {

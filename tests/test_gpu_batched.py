@@ -237,3 +237,15 @@ def test_batched_large_512_sampled(A, ctx):
         _, ref = oracle(geom, Amat, sl, max_iters=3, omega=1.0)
         assert st[i].iters == 3
         assert rel(f[i], ref.f) <= 1e-5, (i, rel(f[i], ref.f))
+
+
+def test_gather_probe(A, ctx):
+    """The gather-bandwidth probe runs for every width and rejects others."""
+    geom, Amat, mat = matrix(A, ctx, "64")
+    for w in (32, 64, 128):
+        fwd, bwd = A.appga_gather_probe(ctx.handle, mat.handle, w, 3)
+        assert np.isfinite(fwd) and fwd > 0 and np.isfinite(bwd) and bwd > 0
+    with pytest.raises(A.AppgaError):
+        A.appga_gather_probe(ctx.handle, mat.handle, 48, 3)
+    with pytest.raises(A.AppgaError):
+        A.appga_gather_probe(ctx.handle, mat.handle, 64, 0)
