@@ -1,0 +1,201 @@
+"""Host-side matrix setup of the library, checked on the CPU.
+
+``tests/host/csr_host_check.cpp`` is compiled against the library's own
+host source (``csrc/csr_host.cpp`` and the internal header) and run on
+seeded matrices.  What it computes is checked against definitions and
+independent implementations:
+
+* the transposed CSR that the back-projection streams (A^T w of Sec. 2.2,
+  formed without atomics) equals A^T entry by entry, built here by brute
+  force, and SciPy's CSC form of the Siddon matrix; each transposed row lists
+  its rays in ascending order;
+* rows padded to a multiple of 4 entries keep every entry in place and only
+  add zero values on the row's last column, so every product is unchanged;
+* the FP32 -> BF16 rounding of A's values is round-to-nearest-even, as
+  PyTorch's conversion;
+* the 8 x 8 tiled pixel order maps the n x n pixels one to one into
+  tiled_size(n) entries, each 8 x 8 block onto one aligned run of 64, blocks
+  and pixels within a block in raster order.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2409_13344_gb300", "csrc")
+CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+ROW_PAD = 4
+SIDES = (1, 5, 8, 9, 16, 63, 64, 100)
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are missing")
+    exe = str(tmp_path_factory.mktemp("host") / "csr_host_check")
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                    "-I", CUDA_INC, os.path.join(ROOT, "tests", "host", "csr_host_check.cpp"),
+                    os.path.join(CSRC, "csr_host.cpp"), "-o", exe], check=True)
+    return exe
+
+
+def _run(exe, tmp_path, m, d, row_ptr, col, val, bf_in):
+    inp, out = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    with open(inp, "wb") as f:
+        np.array([m, d, len(col), len(bf_in)], np.int32).tofile(f)
+        np.asarray(row_ptr, np.int32).tofile(f)
+        np.asarray(col, np.int32).tofile(f)
+        np.asarray(val, np.float32).tofile(f)
+        np.asarray(bf_in, np.float32).tofile(f)
+        np.array([len(SIDES)] + list(SIDES), np.int32).tofile(f)
+    subprocess.run([exe, inp, out], check=True)
+    raw = open(out, "rb").read()
+    pos = 0
+
+    def take(dtype, n):
+        nonlocal pos
+        a = np.frombuffer(raw, dtype=dtype, count=n, offset=pos)
+        pos += a.nbytes
+        return a
+
+    res = {}
+    for key in ("at", "pa", "pt"):
+        rows, nnz = take(np.int32, 2)
+        res[key] = (take(np.int32, rows + 1), take(np.int32, nnz), take(np.float32, nnz))
+    res["bf"] = take(np.uint16, len(bf_in))
+    res["status"] = int(take(np.int32, 1)[0])
+    res["tiled"] = {}
+    for n in SIDES:
+        size = int(take(np.int64, 1)[0])
+        res["tiled"][n] = (size, take(np.int32, n * n).reshape(n, n))
+    assert pos == len(raw)
+    return res
+
+
+def _random_csr(rng, m, d):
+    """Rows of varied length (a share of them empty), columns unsorted within
+    a row and occasionally repeated, positive values."""
+    lens = rng.integers(0, 23, m)
+    lens[rng.random(m) < 0.15] = 0
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    col = rng.integers(0, d, int(row_ptr[-1])).astype(np.int32)
+    val = rng.uniform(0.01, 2.0, int(row_ptr[-1])).astype(np.float32)
+    return row_ptr, col, val
+
+
+def _brute_transpose(m, d, row_ptr, col, val):
+    rows = [[] for _ in range(d)]
+    for i in range(m):
+        for p in range(row_ptr[i], row_ptr[i + 1]):
+            rows[col[p]].append((i, val[p]))
+    t_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])])
+    t_col = np.array([i for r in rows for i, _ in r], np.int32)
+    t_val = np.array([v for r in rows for _, v in r], np.float32)
+    return t_ptr, t_col, t_val
+
+
+def _check_padding(src, padded):
+    s_ptr, s_col, s_val = src
+    p_ptr, p_col, p_val = padded
+    for i in range(len(s_ptr) - 1):
+        n, pn = s_ptr[i + 1] - s_ptr[i], p_ptr[i + 1] - p_ptr[i]
+        assert pn % ROW_PAD == 0 and n <= pn < n + ROW_PAD
+        a, b = s_ptr[i], p_ptr[i]
+        np.testing.assert_array_equal(p_col[b:b + n], s_col[a:a + n])
+        np.testing.assert_array_equal(p_val[b:b + n], s_val[a:a + n])
+        assert np.all(p_val[b + n:b + pn] == 0.0)
+        if pn > n:
+            assert np.all(p_col[b + n:b + pn] == s_col[a + n - 1])
+
+
+def test_transpose_and_padding_random(harness, tmp_path):
+    rng = np.random.default_rng(20240913)
+    m, d = 300, 211
+    row_ptr, col, val = _random_csr(rng, m, d)
+    res = _run(harness, tmp_path, m, d, row_ptr, col, val, [])
+    assert res["status"] == 0
+    t_ptr, t_col, t_val = res["at"]
+    e_ptr, e_col, e_val = _brute_transpose(m, d, row_ptr, col, val)
+    np.testing.assert_array_equal(t_ptr, e_ptr)
+    np.testing.assert_array_equal(t_col, e_col)
+    np.testing.assert_array_equal(t_val, e_val)
+    _check_padding((row_ptr, col, val), res["pa"])
+    _check_padding(res["at"], res["pt"])
+    # padded forms give the same products bit for bit (the added terms are +0)
+    x = rng.uniform(0.0, 3.0, d).astype(np.float64)
+    w = rng.uniform(-1.0, 1.0, m).astype(np.float64)
+    A = sp.csr_matrix((val.astype(np.float64), col, row_ptr), shape=(m, d))
+    pa_ptr, pa_col, pa_val = res["pa"]
+    Ap = sp.csr_matrix((pa_val.astype(np.float64), pa_col, pa_ptr), shape=(m, d))
+    pt_ptr, pt_col, pt_val = res["pt"]
+    Atp = sp.csr_matrix((pt_val.astype(np.float64), pt_col, pt_ptr), shape=(d, m))
+    for i in range(m):
+        a = sum(float(val[p]) * x[col[p]] for p in range(row_ptr[i], row_ptr[i + 1]))
+        b = sum(float(pa_val[p]) * x[pa_col[p]] for p in range(pa_ptr[i], pa_ptr[i + 1]))
+        assert a == b
+    np.testing.assert_allclose(Ap @ x, A @ x, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(Atp @ w, A.T @ w, rtol=1e-12, atol=1e-12)
+
+
+def test_transpose_of_siddon_matrix_matches_scipy(harness, tmp_path):
+    from paper_2409_13344_gb300 import workload as W
+    A = W.system_matrix("64").tocsr()
+    A.sort_indices()
+    m, d = A.shape
+    res = _run(harness, tmp_path, m, d, A.indptr, A.indices, A.data.astype(np.float32), [])
+    assert res["status"] == 0
+    C = A.tocsc()
+    C.sort_indices()
+    t_ptr, t_col, t_val = res["at"]
+    np.testing.assert_array_equal(t_ptr, C.indptr)
+    np.testing.assert_array_equal(t_col, C.indices)
+    np.testing.assert_array_equal(t_val, C.data.astype(np.float32))
+    _check_padding((A.indptr, A.indices, A.data.astype(np.float32)), res["pa"])
+
+
+def test_bf16_rounding_is_nearest_even(harness, tmp_path):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    vals = [rng.standard_normal(4000) * 10.0 ** rng.integers(-30, 30, 4000)]
+    # exact ties (low half 0x8000) with even and odd kept parts, neighbours of
+    # ties, carries into the exponent, subnormals, the largest finite float
+    hi = rng.integers(0x0001, 0x7f7f, 500, dtype=np.uint32)
+    for low in (0x8000, 0x7fff, 0x8001, 0xffff, 0x0000, 0x0001):
+        vals.append(((hi << 16) | low).view(np.float32))
+    vals.append(np.array([0.0, -0.0, 1e-45, -1e-45, 1e-40, 3.4028235e38, -3.4028235e38,
+                          np.float32(1.0) + np.float32(2.0 ** -8), 1.0 + 3 * 2.0 ** -8,
+                          np.inf, -np.inf], np.float32))
+    x = np.concatenate([np.asarray(v, np.float32) for v in vals])
+    x = x[np.isfinite(x) | np.isinf(x)]
+    res = _run(harness, tmp_path, 0, 1, [0], [], [], x)
+    ref = torch.from_numpy(x.copy()).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    np.testing.assert_array_equal(res["bf"], ref)
+
+
+def test_tiled_pixel_order(harness, tmp_path):
+    res = _run(harness, tmp_path, 0, 1, [0], [], [], [])
+    for n in SIDES:
+        size, idx = res["tiled"][n]
+        nb = -(-n // 8)
+        assert size == nb * nb * 64
+        flat = idx.reshape(-1)
+        assert flat.min() >= 0 and flat.max() < size
+        assert len(np.unique(flat)) == n * n  # one to one
+        chunks = idx // 64
+        prev_chunk = -1
+        for br in range(nb):
+            for bc in range(nb):
+                blk = idx[8 * br:8 * br + 8, 8 * bc:8 * bc + 8]
+                cb = chunks[8 * br:8 * br + 8, 8 * bc:8 * bc + 8]
+                assert np.all(cb == cb.flat[0])  # the block sits in one aligned run of 64
+                assert cb.flat[0] > prev_chunk   # blocks in raster order
+                prev_chunk = cb.flat[0]
+                assert np.all(np.diff(blk.reshape(-1)) > 0)  # raster order inside the block
+                # a full block fills its run exactly
+                if blk.shape == (8, 8):
+                    np.testing.assert_array_equal(np.sort(blk.reshape(-1) % 64), np.arange(64))
