@@ -251,7 +251,11 @@ appga_status appga_reconstruct_host(appga_ctx* ctx, const appga_matrix* mat, con
  * for max_iters maps or until its own stopping test fires; a slice's result
  * does not depend on the other slices in the batch.  The projector
  * accumulation is FP32 in a different order from the single-slice path, so
- * results agree with appga_reconstruct to FP32 rounding.  Synchronises. */
+ * results agree with appga_reconstruct to FP32 rounding.  Slices are held in
+ * blocks of Kp = 32, 64 or 128 slots (the smallest that holds K); the
+ * kernels index them with 32-bit offsets, so max(m, d) * Kp must stay below
+ * 2^31 (else EINVAL).  EINVAL also for K outside [1, 128] or bad params;
+ * EDOMAIN for non-finite or negative g or f_init, or gamma <= 0.  Synchronises. */
 appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, int32_t K,
                                        const float* g, const float* gamma, const float* f_init,
                                        const appga_params* params, float* f_out,
@@ -267,7 +271,8 @@ appga_status appga_reconstruct_batched(appga_ctx* ctx, const appga_matrix* mat, 
  * image block [d][width] (the forward projection); *gbs_bwd: A^T's rows
  * against a weight block [m][width] (the back-projection); both host doubles,
  * gathered bytes (padded entries x width x 4) per second / 1e9.  width: 32,
- * 64 or 128; launches >= 1 per grid size.  Uses the matrix's batched
+ * 64 or 128 (max(m, d) * width below 2^31, else EINVAL); launches >= 1 per
+ * grid size.  Uses the matrix's batched
  * workspace; synchronises. */
 appga_status appga_gather_probe(appga_ctx* ctx, const appga_matrix* mat, int32_t width,
                                 int32_t launches, double* gbs_fwd, double* gbs_bwd);

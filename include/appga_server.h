@@ -108,8 +108,10 @@ appga_status appga_server_create(appga_ctx* ctx, const appga_server_config* cfg,
 appga_status appga_server_destroy(appga_server* srv);
 
 /* Registers a geometry (its matrix must come from the server's context and
- * outlive the server).  EINVAL if it belongs to another context, or if the
- * config asks for BF16 and the matrix has no BF16 copy. */
+ * outlive the server).  EINVAL if it belongs to another context, if the
+ * config asks for BF16 and the matrix has no BF16 copy, or if max(m, d)
+ * times the widest pool the server may create (slots_per_pool, or 128 when
+ * widths are adaptive) reaches 2^31 (the batched kernels' 32-bit offsets). */
 appga_status appga_server_add_geometry(appga_server* srv, const appga_matrix* mat,
                                        int32_t* geometry_out);
 

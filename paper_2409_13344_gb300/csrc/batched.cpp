@@ -412,6 +412,8 @@ appga_status check_batched_args(appga_ctx* ctx, const appga_matrix* mat, int32_t
   if (!ctx || !mat || !g || !gamma || !params) return fail(APPGA_EINVAL, "null argument");
   if (mat->ctx != ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
   if (K < 1 || K > 128) return fail(APPGA_EINVAL, "K must be in [1, 128]");
+  appga_status rc = check_slot_width(mat, padded_width(K));
+  if (rc != APPGA_OK) return rc;
   return appga_params_validate(params);
 }
 
@@ -438,11 +440,20 @@ appga_status batched_run(appga_ctx* ctx, appga_matrix* M, int32_t K, const float
 
 }  // namespace
 
+appga_status check_slot_width(const appga_matrix* M, int Kp) {
+  if ((int64_t)std::max(M->m, M->d) * Kp > (int64_t)INT32_MAX)
+    return fail(APPGA_EINVAL, "matrix too large for this batch width: max(m, d) * " +
+                                  std::to_string(Kp) + " must stay below 2^31");
+  return APPGA_OK;
+}
+
 appga_status volume_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
                           const float* gamma, const float* f_init, const appga_params* params,
                           float* f_out, void* stream) {
   const bool bf16 = params->a_precision == APPGA_PREC_BF16 && M->has_bf16;
   const int Kp = padded_width(K);
+  const appga_status rc = check_slot_width(M, Kp);
+  if (rc != APPGA_OK) return rc;
   return batched_solve(ctx, M, K, g, gamma, f_init, params, f_out, nullptr,
                        tuned_schedule(M, Kp, bf16), stream, 0, true);
 }
@@ -504,9 +515,11 @@ extern "C" appga_status appga_gather_probe(appga_ctx* ctx, const appga_matrix* m
   if (width != 32 && width != 64 && width != 128)
     return fail(APPGA_EINVAL, "width must be 32, 64 or 128");
   if (launches < 1) return fail(APPGA_EINVAL, "launches must be >= 1");
+  appga_status rc = check_slot_width(mat, width);
+  if (rc != APPGA_OK) return rc;
   auto* M = const_cast<appga_matrix*>(mat);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(APPGA_ENODEV, "cudaSetDevice failed");
-  appga_status rc = ensure_batch_workspace(M, width);
+  rc = ensure_batch_workspace(M, width);
   if (rc != APPGA_OK) return rc;
   BatchWorkspace& b = *M->bw;
   cudaStream_t s = ctx->stream;

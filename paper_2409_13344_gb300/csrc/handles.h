@@ -128,6 +128,10 @@ cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, c
 appga_status volume_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const float* g,
                           const float* gamma, const float* f_init, const appga_params* params,
                           float* f_out, void* stream);
+// The batched kernels stage the offset col * Kp of every gathered slot-minor
+// row in 32 bits: APPGA_OK when max(m, d) * Kp stays below 2^31, else
+// APPGA_EINVAL (with the library's error message set).
+appga_status check_slot_width(const appga_matrix* M, int Kp);
 // Data term sum_i (A f)_i - g_i ln((A f)_i + gamma_i) of one slice in FP64
 // (double-float accumulation) into the device double *dev_out.
 appga_status data_term_on(appga_matrix* M, const float* f, const float* g, const float* gamma,

@@ -459,6 +459,10 @@ extern "C" appga_status appga_server_add_geometry(appga_server* S, const appga_m
   if (mat->ctx != S->ctx) return fail(APPGA_EINVAL, "matrix belongs to another context");
   if (S->cfg.a_precision == APPGA_PREC_BF16 && !mat->has_bf16)
     return fail(APPGA_EINVAL, "BF16 pools need a matrix created with APPGA_A_BF16_COPY");
+  // the widest pool the server may create for this geometry
+  const int widest = S->cfg.slots_per_pool > 0 ? S->cfg.slots_per_pool : 128;
+  const appga_status rc = check_slot_width(mat, widest);
+  if (rc != APPGA_OK) return rc;
   Geometry G;
   G.M = mat;
   S->geoms.push_back(G);
