@@ -1,6 +1,7 @@
-"""The benchmark's reference arm (the FP64 oracle on the host) and its
-argument handling, on the CPU: one JSON line with the contract's keys,
-bounded in wall time whatever --steps asks for."""
+"""The benchmark on the CPU: its reference arm (the FP64 oracle on the host)
+prints one JSON line with the contract's keys, bounded in wall time whatever
+--steps asks for; its roofline bookkeeping (algorithmic bytes, and ncu
+traffic only for the kernel source it was captured on) holds."""
 import json
 import os
 import subprocess
@@ -37,3 +38,47 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--steps", "1", "--warmup", "0"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0 and not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_algorithmic_bytes_match_the_committed_record():
+    """Per-launch algorithmic bytes of the two iteration kernels at 256x256
+    (m 66 060 rays, d 65 536 pixels, 15 017 956 stored entries): the A or A^T
+    stream at 8 B per entry plus each vector once, as the ncu record states."""
+    b = _bench_module()
+    rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    fwd, pix = b.kernel_bytes(66060, 65536, 15017956)
+    assert fwd == rec["kernels"]["k_forward"]["algorithmic_bytes_per_launch"]
+    assert pix == rec["kernels"]["k_pixel"]["algorithmic_bytes_per_launch"]
+    # both streams dominate: 16 B per entry is 98 % of an iteration's bytes
+    assert 0.98 < 16 * 15017956 / (fwd + pix) < 0.99
+    # a batched iteration of 64 slices reads the matrix once: far below 64 iterations
+    kb = b.batched_bytes(66060, 65536, 15017956, 64)
+    assert 16 * 15017956 < kb < 3 * (fwd + pix)
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
+    """ncu traffic is attached to the roofline only while kernels.cu is the
+    source the capture was taken on (its SHA-256 is in the record)."""
+    import hashlib
+    b = _bench_module()
+    src = tmp_path / "paper_2409_13344_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    code = b"// kernel source\n"
+    (src / "kernels.cu").write_bytes(code)
+    rec = {"kernels_cu_sha256": hashlib.sha256(code).hexdigest(),
+           "kernels": {"k_pixel": {"dram_bytes_per_launch": 123}}}
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.committed_traffic("k_pixel") == 123
+    assert b.committed_traffic("k_forward") is None
+    (src / "kernels.cu").write_bytes(code + b"// changed\n")
+    assert b.committed_traffic("k_pixel") is None
