@@ -75,9 +75,6 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
 #ifndef APPGA_BDOT
 #define APPGA_BDOT 2
 #endif
-#ifndef APPGA_BCONTIG
-#define APPGA_BCONTIG 1
-#endif
 // Row order of each projection: a contiguous run of rows per block (1) or
 // rows dealt to the warps of the whole grid in turn (0).  The forward
 // projection gathers image rows faster dealt in turn (the whole grid works
@@ -88,7 +85,7 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
 #define APPGA_BCONTIG_FW 0
 #endif
 #ifndef APPGA_BCONTIG_PX
-#define APPGA_BCONTIG_PX APPGA_BCONTIG
+#define APPGA_BCONTIG_PX 1
 #endif
 
 // One CSR row of M times the Kp-wide columns of X ([cols][Kp]): lane holds
