@@ -33,6 +33,14 @@ Readings where the paper is silent (each also listed in the design notes):
   x^2 + y^2 <= (N/2)^2; ACTc = sum(g) - sum(gamma); NPA = number of angles.
 * The "K iterations" of a run are K applications of the APPGA map, starting
   from f^0 = f^1 = f_init, so the result is f^{K+1}.
+
+Pins (tests/test_oracle.py, tests/golden/): the difference operators against
+hand-written matrices and a pixel-loop definition; phi~ and its gradient on a
+hand-worked 3 x 3 image with lambda1 != lambda2 and both s_eps branches; the
+Lambda_j = 1 branch of Eq. EM, the preconditioner freeze and the relative-
+objective stop on hand-solved one- and four-pixel problems in exact rational
+arithmetic; MLEM as the unregularised momentum-free step; finite
+differences; KKT against L-BFGS-B; the momentum closed forms.
 """
 from __future__ import annotations
 
@@ -319,9 +327,18 @@ def appga(prob: Problem, params: Params, f_init: Optional[np.ndarray] = None,
 
 def mlem_step(prob: Problem, f: np.ndarray) -> np.ndarray:
     """Classical MLEM update (f / A^T 1) * A^T (g / (A f + gamma)), used as an
-    independent closed form for the unregularised, momentum-free step."""
+    independent closed form for the unregularised, momentum-free step.
+
+    A pixel that no ray sees, (A^T 1)_j = 0, has no data: the update there is
+    0/0, and such a pixel keeps its value (the sensitivity-zero convention;
+    the EM-preconditioned step does the same, since its fidelity gradient is
+    zero there and Lambda_j = 1 by Eq. EM)."""
     s = prob.At @ prob.ones_m
-    return f / s * (prob.At @ (prob.g / (prob.A @ f + prob.gamma)))
+    back = prob.At @ (prob.g / (prob.A @ f + prob.gamma))
+    seen = s > 0
+    out = f.copy()
+    out[seen] = f[seen] / s[seen] * back[seen]
+    return out
 
 
 def lipschitz_bound(prob: Problem, lam1: float, lam2: float, eps: float) -> float:

@@ -371,3 +371,190 @@ def test_ppga_is_monotone_with_small_fixed_step():
     par = O.Params(lambda1=lam1, lambda2=lam2, eps=eps, momentum="none", max_iters=200)
     res = O.appga(prob, par, f_init=x0, p_fixed=np.full(prob.d, 1.0 / L))
     assert all(b <= a + 1e-12 * abs(a) for a, b in zip(res.phi, res.phi[1:]))
+
+
+# ------------------------------------- hand-worked SHOITV case (3 x 3 image)
+
+def _read_sections(name):
+    """Sections '[key]' of a golden file, each a float array."""
+    out, key, rows = {}, None, []
+    with open(f"{GOLDEN}/{name}") as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            if line.startswith("["):
+                if key is not None:
+                    out[key] = np.array(rows, dtype=np.float64)
+                key, rows = line.strip("[]"), []
+            else:
+                rows.append([float(v) for v in line.split()])
+    out[key] = np.array(rows, dtype=np.float64)
+    return out
+
+
+SHOITV = _read_sections("shoitv_3x3.txt")
+LAM1_H, LAM2_H, EPS_H = 0.3, 0.7, 1.5
+
+
+def _hand_fields():
+    return np.concatenate([SHOITV[f"u{q}"].reshape(-1) for q in range(1, 7)])
+
+
+def test_hand_fields_match_operator_b():
+    # Sec. 2.1: B = [B1; B2] applied to the 3 x 3 image gives the six hand fields.
+    F = SHOITV["image"].reshape(-1)
+    np.testing.assert_array_equal(O.b_matrix(3) @ F, _hand_fields())
+
+
+def test_phi_tilde_hand_value_weights_and_groups():
+    # phi~ = lambda1 sum s_eps(pairs) + lambda2 sum s_eps(quads), worked by hand
+    # (tests/golden/shoitv_3x3.txt): both branches of s_eps occur in both kinds
+    # of group, and lambda1 != lambda2, so a swapped weight, a wrong grouping
+    # or a wrong branch changes the value.
+    s = math.sqrt
+    pairs = 21.0 / 4.0 + 2.0 * s(13)
+    quads = (2.0 / 3.0 - 6.0 + s(5) + s(17) + s(10) + s(30) + s(66) + s(14) + s(26)
+             + 4.0 * s(2))
+    want = LAM1_H * pairs + LAM2_H * quads
+    got = O.phi_tilde(_hand_fields(), 9, LAM1_H, LAM2_H, EPS_H)
+    assert got == pytest.approx(want, rel=1e-14)
+    swapped = LAM2_H * pairs + LAM1_H * quads
+    assert abs(swapped - want) > 1.0
+    # the hand norms listed beside the fields are those of the groups
+    u = SHOITV
+    np.testing.assert_array_equal((u["u1"] ** 2 + u["u2"] ** 2).reshape(-1),
+                                  SHOITV["pair_norm2"].reshape(-1))
+    np.testing.assert_array_equal(
+        (u["u3"] ** 2 + u["u4"] ** 2 + u["u5"] ** 2 + u["u6"] ** 2).reshape(-1),
+        SHOITV["quad_norm2"].reshape(-1))
+
+
+def test_grad_phi_tilde_hand_entries():
+    # Eq. gradenvL2: the gradient of phi~ at u is lambda x / max(||x||, eps) per
+    # group; entries of four pixels worked by hand.  Pixel j's pair sits at u[j],
+    # u[d + j] and its quadruple at u[2d + j], ..., u[5d + j] (d = 9).
+    d = 9
+    gr = O.grad_phi_tilde(_hand_fields(), d, LAM1_H, LAM2_H, EPS_H)
+    s = math.sqrt
+
+    def at(j):
+        return [gr[q * d + j] for q in range(6)]
+
+    # j = 0, pixel (0,0): pair (0,0) -> 0; quad (1,0,2,0), norm sqrt5 > eps
+    np.testing.assert_allclose(at(0), [0, 0, 0.7 / s(5), 0, 1.4 / s(5), 0], rtol=1e-14, atol=0)
+    # j = 1, pixel (0,1): pair (1,0) and quad (1,0,1,0) on the quadratic branch
+    # (norms 1 and sqrt2 <= 3/2): lambda x / eps
+    np.testing.assert_allclose(at(1), [0.2, 0, 0.7 / 1.5, 0, 0.7 / 1.5, 0], rtol=1e-14, atol=0)
+    # j = 5, pixel (1,2): pair (-2,-3), quad (2,2,7,3)
+    np.testing.assert_allclose(
+        at(5), [-0.6 / s(13), -0.9 / s(13), 1.4 / s(66), 1.4 / s(66), 4.9 / s(66), 2.1 / s(66)],
+        rtol=1e-14, atol=0)
+    # j = 8, pixel (2,2): pair (0,4), norm 4; quad (0,0,-4,-4), norm sqrt32
+    np.testing.assert_allclose(at(8), [0, 0.3, 0, 0, -2.8 / s(32), -2.8 / s(32)],
+                               rtol=1e-14, atol=0)
+
+
+def test_regulariser_gradient_fd_at_hand_image():
+    # B^T grad phi~(B f) against central differences of phi~(B f), at the hand
+    # image where groups sit on both branches of s_eps.
+    F = SHOITV["image"].reshape(-1)
+    B = O.b_matrix(3)
+    gr = B.T @ O.grad_phi_tilde(B @ F, 9, LAM1_H, LAM2_H, EPS_H)
+    h = 1e-6
+    for j in range(9):
+        e = np.zeros(9); e[j] = h
+        fd = (O.phi_tilde(B @ (F + e), 9, LAM1_H, LAM2_H, EPS_H)
+              - O.phi_tilde(B @ (F - e), 9, LAM1_H, LAM2_H, EPS_H)) / (2 * h)
+        assert gr[j] == pytest.approx(fd, rel=1e-7, abs=1e-8)
+
+
+# ------------------- Eq. EM branches, preconditioner freeze, stopping rule
+
+def test_em_lambda_unseen_pixel_is_one_and_steps_with_it():
+    # Eq. EM: Lambda_j = (A^T 1)_j if positive, else 1.  Column 2 of A is zero
+    # (a pixel no ray sees).  2 x 2 image [[1, 2], [3, 1/2]], lambda2 = 0 and
+    # eps = 100 (every pair on the quadratic branch), so the regulariser
+    # gradient is (lambda1/eps) B1^T B1 f; at pixel 2 = (r 1, c 0) it is
+    # (lambda1/eps)((3 - 1/2) + (3 - 1)) = 4.5 lambda1/eps = 0.09 for
+    # lambda1 = 2, and the fidelity gradient is zero there.  With theta = 0 and
+    # beta = 1: f_2 <- 3 - (3 / Lambda_2) 0.09 = 2.73 exactly when Lambda_2 = 1.
+    A = np.array([[1.0, 2.0, 0.0, 0.0], [0.0, 3.0, 0.0, 4.0]])
+    prob = O.Problem(A, np.array([3.0, 5.0]), np.array([0.5, 0.5]), 2)
+    lam = prob.em_lambda()
+    np.testing.assert_array_equal(lam, [1.0, 5.0, 1.0, 4.0])
+    f = np.array([1.0, 2.0, 3.0, 0.5])
+    p = O.Params(lambda1=2.0, lambda2=0.0, eps=100.0, beta=1.0)
+    f_next, _ = O.appga_step(prob, f, f, 0.0, p, lam)
+    assert f_next[2] == pytest.approx(2.73, rel=1e-14)
+
+
+def _one_pixel():
+    # N = 1 (B = 0), A = [[2]], g = 5, gamma = 1: Lambda = 2 and
+    # Phi(f) = 2 f - 5 ln(2 f + 1).  From f^1 = 1 with beta = 1/2, no momentum:
+    #   k = 1: P = 1/4, grad = 2 (1 - 5/3) = -4/3          -> f^2 = 4/3
+    #   k = 2: P = 1/3 (recomputed), grad = -8/11          -> f^3 = 52/33
+    #          P = 1/4 (frozen at k = 1)                    -> f^3 = 50/33
+    #   k = 3: P = 13/33 (recomputed), grad = -56/137      -> f^4 = 7852/4521
+    #          P = 1/3 (frozen at k = 2)                    -> f^4 = 2580/1507
+    prob = O.Problem(np.array([[2.0]]), np.array([5.0]), np.array([1.0]), 1)
+    return prob
+
+
+@pytest.mark.parametrize("freeze,iters,want", [
+    (-1, 2, Fraction(52, 33)),
+    (1, 2, Fraction(50, 33)),
+    (-1, 3, Fraction(7852, 4521)),
+    (2, 3, Fraction(2580, 1507)),
+    (3, 3, Fraction(7852, 4521)),   # frozen only after the last map: no effect
+])
+def test_preconditioner_freeze_hand_case(freeze, iters, want):
+    # Sec. 4.1 allows updating P in the first K_P iterations and fixing it
+    # afterwards: P is recomputed from f^k for k <= K_P and kept at P_{K_P} later.
+    prob = _one_pixel()
+    p = O.Params(lambda1=0.0, lambda2=0.0, beta=0.5, momentum="none", max_iters=iters,
+                 precond_freeze_iter=freeze)
+    res = O.appga(prob, p, f_init=np.array([1.0]), track_phi=False)
+    assert res.iters == iters
+    assert res.f[0] == pytest.approx(float(want), rel=1e-15)
+
+
+def test_relative_objective_stop_hand_case():
+    # Stop after map k when |Phi(f^{k+1}) - Phi(f^k)| <= tol |Phi(f^k)|; the
+    # result is f^{k+1}.  On the one-pixel problem the relative changes are
+    # 0.096... (map 1) and 0.035... (map 2), so tol = 0.05 stops after map 2
+    # with f^3 = 52/33, and tol = 0.1 already after map 1 with f^2 = 4/3.
+    # The change is measured against |Phi(f^k)|, the earlier value: at
+    # tol = 0.035 map 2 changes Phi by 0.03554 |Phi(f^2)| (= 0.03432 |Phi(f^3)|),
+    # so the run goes on to map 3 (change 0.0130) and returns f^4 = 7852/4521.
+    prob = _one_pixel()
+    phi = lambda f: 2.0 * f - 5.0 * math.log(2.0 * f + 1.0)
+    seq = [1.0, 4.0 / 3.0, 52.0 / 33.0, 7852.0 / 4521.0]
+    vals = [phi(v) for v in seq]
+    rel = [abs(vals[i] - vals[i - 1]) / abs(vals[i - 1]) for i in (1, 2, 3)]
+    assert 0.1 >= rel[0] > 0.09 and 0.05 >= rel[1] > 0.035 >= rel[2]
+    assert abs(vals[2] - vals[1]) / abs(vals[2]) < 0.035
+    for tol, n_maps in ((0.05, 2), (0.1, 1), (0.035, 3)):
+        p = O.Params(lambda1=0.0, lambda2=0.0, beta=0.5, momentum="none", max_iters=50,
+                     rel_obj_tol=tol)
+        res = O.appga(prob, p, f_init=np.array([1.0]))
+        assert res.iters == n_maps
+        assert res.f[0] == pytest.approx(seq[n_maps], rel=1e-15)
+        np.testing.assert_allclose(res.phi, vals[:n_maps + 1], rtol=1e-14)
+
+
+def test_mlem_closed_form_with_an_unseen_pixel():
+    # A column of A set to zero (a pixel no ray sees): the unregularised,
+    # momentum-free EM step is MLEM on the seen pixels and leaves the unseen one.
+    A, f, g, gamma = W.dense_problem(8, 96, seed=5)
+    A = np.array(A, dtype=np.float64)
+    A[:, 19] = 0.0
+    prob = O.Problem(A, g, gamma, 8)
+    f0 = np.full(prob.d, 1.5)
+    p = O.Params(lambda1=0.0, lambda2=0.0, beta=1.0, momentum="none", max_iters=3)
+    res = O.appga(prob, p, f_init=f0, track_phi=False)
+    ref = f0.copy()
+    for _ in range(3):
+        ref = O.mlem_step(prob, ref)
+    assert res.f[19] == 1.5 and ref[19] == 1.5
+    assert np.max(np.abs(res.f - ref)) <= 1e-13 * np.max(np.abs(ref))
