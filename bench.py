@@ -397,7 +397,8 @@ def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
         t0 = time.perf_counter()
         F.afppa(prob, par, n_angles=geom.n_angles)
         el = time.perf_counter() - t0
-        out["cpu_baseline"] = {"value": 3 / el, "unit": "steps/s", "cores": 1, "kind": "oracle",
+        out["cpu_baseline"] = {"value": 3 / el, "unit": "steps/s", "cores": 1,
+                               "host_cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"3 FP64 oracle AFPPA steps of the same slice, {el:.1f} s"}
     # figures of merit of the AFPPA result against the phantom (Sec. 4.1)
     call(iters)
@@ -579,7 +580,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "reference": "FP64 NumPy/SciPy oracle on the host"},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -635,14 +637,15 @@ def run_ours(args):
         for it in chunks(total):
             AP.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, params(it), f_out)
 
-    S = 16  # library default iterations per graph replay
-
     def launches(total):
-        # per run: 8 setup launches, then per iteration the pixel kernel, its
-        # one-block finalisation and the forward kernel (whole graph replays)
+        # per run: the start-state/momentum kernel, the initial image (two
+        # kernels, with the input check), the first forward phase, then per
+        # iteration the pixel kernel, its one-block finalisation and the
+        # forward kernel (exactly `it` maps), the last finalisation (objective
+        # of the result) and the result copy
         n = 0
         for it in chunks(total):
-            n += 8 + 3 * S * math.ceil(it / S)
+            n += 6 + 3 * it
         return n
 
     # warm-up
@@ -748,7 +751,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         k, el = oracle_rate(geom, A, sl, args.cpu_seconds)
-        cpu = {"value": k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": k / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+               "kind": "oracle",
                "sample": f"{k} FP64 oracle APPGA iterations (with the objective) of the same "
                          f"256x256 slice from the initial image, {el:.1f} s on one host core"}
 

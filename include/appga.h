@@ -66,6 +66,7 @@ typedef struct appga_matrix appga_matrix;
 /* Device sticky flags reported in appga_stats.flags. */
 #define APPGA_FLAG_NONFINITE 1 /* a non-finite value met in a projector */
 #define APPGA_FLAG_TIMEOUT 2   /* a bounded device wait ran out; the run stopped */
+#define APPGA_FLAG_DOMAIN 4    /* an input failed the device-side check; no map ran */
 
 const char* appga_status_string(appga_status s);
 const char* appga_last_error(void);

@@ -34,6 +34,8 @@ APPGA_MOMENTUM_GN = 0
 APPGA_MOMENTUM_NONE = 1
 APPGA_MOMENTUM_NESTEROV = 2
 APPGA_FLAG_NONFINITE = 1
+APPGA_FLAG_TIMEOUT = 2
+APPGA_FLAG_DOMAIN = 4
 
 
 class appga_params(ctypes.Structure):

@@ -54,7 +54,8 @@ void free_csr(DevCSR& c) {
 }
 
 void free_workspace(Workspace& ws) {
-  if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
+  for (auto& kv : ws.gexec) cudaGraphExecDestroy(kv.second);
+  ws.gexec.clear();
   for (auto& p : ws.f) cudaFree(p);
   for (auto& p : ws.y) cudaFree(p);
   cudaFree(ws.w);
@@ -189,41 +190,51 @@ std::string graph_key(const appga_params* p, bool track, bool bf16, int S) {
   return buf;
 }
 
-// Prepares a run on the workspace ring whose slots (k0-1)%3 and k0%3 hold
-// f^{k0-1} and f^{k0}: the device state, theta_{k0}, y^{k0-1}, y^{k0},
-// w^{k0} and F(f^{k0}); fills the kernel argument blocks of the loop.
-appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int32_t k0,
-                       const appga_params* p, appga::FwdArgs* fa_out, appga::PixArgs* pa_out) {
-  Workspace& ws = M->ws;
-  cudaStream_t s = M->ctx->stream;
+// Device state of a run at its start (iteration index k0).  A run of zero
+// maps with the objective tracked starts at done = 2: its one forward phase
+// and the last finalisation still evaluate Phi(f^{k0}).
+SolverState start_state(int32_t k0, const appga_params* p) {
   const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
-  const bool bf16 = bf16_requested(M, p);
   SolverState h{};
   h.k = k0;
   h.k0 = k0;
   h.k_last = k0 + p->max_iters - 1;
-  h.done = p->max_iters == 0 ? 1 : 0;
+  h.done = p->max_iters == 0 ? (track ? 2 : 1) : 0;
   h.result_k = k0;
   h.phi_cur = std::numeric_limits<double>::quiet_NaN();
   h.phi_prev = h.phi_cur;
-  CK(cudaMemcpyAsync(ws.st, &h, sizeof h, cudaMemcpyHostToDevice, s));
-  const appga_status rc_t = momentum_table(M, ws.st, k0, p, s);
-  if (rc_t != APPGA_OK) return rc_t;
+  return h;
+}
 
-  // y^{k0-1} = A f^{k0-1}
-  appga::FwdArgs init = fwd_args(M, bf16);
-  init.f[0] = ws.f[(k0 + 2) % 3];
-  init.y[0] = ws.y[(k0 + 1) & 1];
-  init.y_out = nullptr;
-  init.g = g;
-  init.gamma = gamma;
-  init.st = ws.st_scratch;
-  init.partial = ws.partial_aux;
-  init.gtick = ws.gtick;
-  init.loop = 0;
-  init.solver_acc = 1;
-  init.n = M->n;
-  CK(appga::launch_forward(init, s));
+// Prepares a run on the workspace ring whose slots (k0-1)%3 and k0%3 hold
+// f^{k0-1} and f^{k0} (and, if tiled_ready, whose tiled copy holds f^{k0}),
+// with the device state already started: y^{k0-1} (a resumed run only; a
+// fresh run has f^{k0-1} = f^{k0}), y^{k0}, w^{k0} and F(f^{k0}); fills the
+// kernel argument blocks of the loop.
+appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int32_t k0,
+                       const appga_params* p, bool fresh, bool tiled_ready,
+                       appga::FwdArgs* fa_out, appga::PixArgs* pa_out) {
+  Workspace& ws = M->ws;
+  cudaStream_t s = M->ctx->stream;
+  const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
+  const bool bf16 = bf16_requested(M, p);
+
+  if (!fresh) {
+    // y^{k0-1} = A f^{k0-1}
+    appga::FwdArgs init = fwd_args(M, bf16);
+    init.f[0] = ws.f[(k0 + 2) % 3];
+    init.y[0] = ws.y[(k0 + 1) & 1];
+    init.y_out = nullptr;
+    init.g = g;
+    init.gamma = gamma;
+    init.st = ws.st_scratch;
+    init.partial = ws.partial_aux;
+    init.gtick = ws.gtick;
+    init.loop = 0;
+    init.solver_acc = 1;
+    init.n = M->n;
+    CK(appga::launch_forward(init, s));
+  }
 
   appga::FwdArgs fa = fwd_args(M, bf16);
   for (int i = 0; i < 3; ++i) fa.f[i] = ws.f[i];
@@ -262,71 +273,96 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
     fa.A.col = M->A_tiled.col;
     fa.ft = ws.ft;
     pa.ft = ws.ft;
-    CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
+    if (!tiled_ready) CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
   }
 
   // w^{k0}, y^{k0}, B^T grad phi~(B f~^{k0}) and Phi(f^{k0})
-  CK(appga::launch_forward(fa, s));
+  appga::FwdArgs first = fa;
+  first.fresh_first = fresh ? 1 : 0;
+  CK(appga::launch_forward(first, s));
   *fa_out = fa;
   *pa_out = pa;
   return APPGA_OK;
 }
 
-// Runs APPGA on the workspace ring whose slots (k0-1)%3 and k0%3 already
-// hold f^{k0-1} and f^{k0}.  Everything is ordered on ctx->stream.
-appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int32_t k0,
-                        const appga_params* p, appga_stats* stats, int32_t* result_k_out) {
+// Executable graph of `maps` solver maps (pixel phase, finalisation, forward
+// phase) for the loop arguments of `key`, captured on first use.
+appga_status loop_graph(Workspace& ws, const std::string& key, int maps,
+                        const appga::FwdArgs& fa, const appga::PixArgs& pa, cudaStream_t s,
+                        cudaGraphExec_t* out) {
+  if (ws.gkey != key) {
+    for (auto& kv : ws.gexec) cudaGraphExecDestroy(kv.second);
+    ws.gexec.clear();
+    ws.gkey = key;
+  }
+  auto it = ws.gexec.find(maps);
+  if (it != ws.gexec.end()) {
+    *out = it->second;
+    return APPGA_OK;
+  }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < maps && e == cudaSuccess; ++i) {
+    e = appga::launch_pixel(pa, s);
+    if (e == cudaSuccess) e = appga::launch_forward(fa, s);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "graph capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  ws.gexec[maps] = exec;
+  *out = exec;
+  return APPGA_OK;
+}
+
+// Graph replays of a run of `total` maps: whole replays of S maps, then the
+// remainder as replays of its binary digits (so exactly `total` maps run).
+std::vector<int> replay_plan(int total, int S) {
+  std::vector<int> plan((size_t)(total / S), S);
+  const int rem = total % S;
+  for (int b = 1 << 30; b > 0; b >>= 1)
+    if (rem & b) plan.push_back(b);
+  return plan;
+}
+
+// Runs the maps of a prepared run (setup_run) on ctx->stream, then the last
+// finalisation of a tracked run.  With a stopping tolerance the stop flag is
+// polled one replay behind, so the device never idles on the host.
+appga_status run_maps(appga_matrix* M, const float* g, const float* gamma,
+                      const appga_params* p, const appga::FwdArgs& fa, const appga::PixArgs& pa) {
   appga_ctx* ctx = M->ctx;
   Workspace& ws = M->ws;
   cudaStream_t s = ctx->stream;
   const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
   const bool bf16 = bf16_requested(M, p);
   const int S = p->graph_iters > 0 ? p->graph_iters : kDefaultGraphIters;
-
-  appga::FwdArgs fa;
-  appga::PixArgs pa;
-  appga_status rc0 = setup_run(M, g, gamma, k0, p, &fa, &pa);
-  if (rc0 != APPGA_OK) return rc0;
-
   if (p->max_iters > 0) {
     // the captured kernel arguments hold the g / gamma addresses
     const std::string key = graph_key(p, track, bf16, S) + "|" +
                             std::to_string((uintptr_t)g) + "|" + std::to_string((uintptr_t)gamma) +
                             "|" + std::to_string((uintptr_t)ws.theta_tab);
-    if (ws.gexec == nullptr || ws.gkey != key) {
-      if (ws.gexec) {
-        cudaGraphExecDestroy(ws.gexec);
-        ws.gexec = nullptr;
-      }
-      cudaGraph_t graph = nullptr;
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      for (int i = 0; i < S && e == cudaSuccess; ++i) {
-        e = appga::launch_pixel(pa, s);
-        if (e == cudaSuccess) e = appga::launch_forward(fa, s);
-      }
-      cudaError_t e2 = cudaStreamEndCapture(s, &graph);
-      if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return cuda_fail(e, "graph capture");
-      }
-      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&ws.gexec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-      ws.gkey = key;
-      ws.graph_iters = S;
+    const std::vector<int> plan = replay_plan(p->max_iters, S);
+    std::vector<cudaGraphExec_t> execs(plan.size());
+    for (size_t r = 0; r < plan.size(); ++r) {
+      const appga_status rc = loop_graph(ws, key, plan[r], fa, pa, s, &execs[r]);
+      if (rc != APPGA_OK) return rc;
     }
-    const int reps = (p->max_iters + S - 1) / S;
     if (p->rel_obj_tol > 0.0) {
-      // poll the stop flag one replay behind so the device never idles
       cudaEvent_t ev[2];
       CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
       SolverState* hs = ws.st_host;
+      hs->done = 0;
       appga_status rc = APPGA_OK;
-      for (int r = 0; r < reps; ++r) {
-        cudaError_t e = cudaGraphLaunch(ws.gexec, s);
+      for (size_t r = 0; r < execs.size(); ++r) {
+        cudaError_t e = cudaGraphLaunch(execs[r], s);
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(&hs->done, &ws.st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[r & 1], s);
@@ -347,30 +383,29 @@ appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int
       cudaEventDestroy(ev[1]);
       if (rc != APPGA_OK) return rc;
     } else {
-      for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ws.gexec, s));
+      for (cudaGraphExec_t x : execs) CK(cudaGraphLaunch(x, s));
     }
   }
-  CK(cudaMemcpyAsync(ws.st_host, ws.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const SolverState fin = *ws.st_host;
-  *result_k_out = fin.result_k;
+  if (track) CK(appga::launch_finalize(pa, s));
+  return APPGA_OK;
+}
+
+// Statistics of a finished run from its final device state.
+appga_status finish_stats(const SolverState& fin, int32_t k0, const appga_params* p,
+                          appga_stats* stats) {
+  const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
   if (stats) {
     stats->iters = fin.result_k - k0;
     stats->result_k = fin.result_k;
     stats->stopped_early = fin.stopped_early;
     stats->flags = fin.flags;
     stats->guard_hits = (int64_t)fin.guard_hits;
-    stats->phi = std::numeric_limits<double>::quiet_NaN();
-    stats->phi_prev = std::numeric_limits<double>::quiet_NaN();
-    if (track) {
-      if (fin.stopped_early) {
-        stats->phi = fin.phi_cur;
-        stats->phi_prev = fin.phi_prev;
-      } else {
-        stats->phi_prev = p->max_iters > 0 ? fin.phi_cur : std::numeric_limits<double>::quiet_NaN();
-      }
-    }
+    stats->phi = track ? fin.phi_cur : std::numeric_limits<double>::quiet_NaN();
+    stats->phi_prev = track ? fin.phi_prev : std::numeric_limits<double>::quiet_NaN();
   }
+  if (fin.flags & APPGA_FLAG_DOMAIN)
+    return fail(APPGA_EDOMAIN,
+                "inputs must satisfy: g finite and >= 0, gamma finite and > 0, f finite and >= 0");
   if (fin.flags & APPGA_FLAG_TIMEOUT)
     return fail(APPGA_ETIMEOUT, "a bounded device wait ran out; the run stopped");
   if (fin.flags & APPGA_FLAG_NONFINITE)
@@ -379,7 +414,7 @@ appga_status run_solver(appga_matrix* M, const float* g, const float* gamma, int
 }
 
 appga_status momentum_table(appga_matrix* M, SolverState* st, int k0, const appga_params* p,
-                            cudaStream_t s) {
+                            cudaStream_t s, const SolverState* init) {
   Workspace& ws = M->ws;
   const int need = p->max_iters + 1;
   if (ws.theta_cap < need) {
@@ -391,7 +426,8 @@ appga_status momentum_table(appga_matrix* M, SolverState* st, int k0, const appg
     if (e != cudaSuccess) return cuda_fail(e, "momentum table");
     ws.theta_cap = cap;
   }
-  CK(launch_theta_table(st, ws.theta_tab, k0, p->max_iters, p->momentum, p->a, p->b, p->omega, s));
+  CK(launch_theta_table(st, ws.theta_tab, k0, p->max_iters, p->momentum, p->a, p->b, p->omega, s,
+                        init));
   return APPGA_OK;
 }
 
@@ -488,10 +524,15 @@ appga_status objective_on(appga_matrix* M, const float* f, const float* g, const
   return APPGA_OK;
 }
 
+// One solver call on ctx->stream after the caller's stream: start state and
+// momentum table, input check (on the device: no host round trip), f^{k0-1}
+// and f^{k0}, the first forward phase, exactly max_iters maps, the result
+// copied out on the device (and to f_out_host if given), one synchronisation.
 appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const float* gamma,
                           const float* f_prev, const float* f_cur, int32_t k0,
                           const appga_params* p, float* f_out_prev, float* f_out,
-                          appga_stats* stats, void* stream, bool fresh) {
+                          appga_stats* stats, void* stream, bool fresh,
+                          float* f_out_host = nullptr) {
   appga_status rc = check_params_and_mat(ctx, M, p);
   if (rc != APPGA_OK) return rc;
   if (g == nullptr || gamma == nullptr || f_out == nullptr)
@@ -505,39 +546,37 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
   if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
   cudaStream_t s = ctx->stream;
   Workspace& ws = M->ws;
-  if ((rc = validate_inputs(M, g, gamma, fresh ? f_cur : f_prev, s)) != APPGA_OK) return rc;
-  if (!fresh && (rc = validate_inputs(M, g, gamma, f_cur, s)) != APPGA_OK) return rc;
+  const SolverState h = start_state(k0, p);
+  if ((rc = momentum_table(M, ws.st, k0, p, s, &h)) != APPGA_OK) return rc;
   const size_t fb = (size_t)M->d * sizeof(float);
   float* slot_cur = ws.f[k0 % 3];
   float* slot_prev = ws.f[(k0 + 2) % 3];
-  if (fresh) {
-    if (f_cur) {
-      CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
-    } else {
-      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.gtick, ws.st_scratch,
-                                     slot_cur, s));
-    }
-    CK(cudaMemcpyAsync(slot_prev, slot_cur, fb, cudaMemcpyDeviceToDevice, s));
+  const bool tiled = appga::tiled_gather_enabled();
+  bool tiled_ready = false;
+  if (fresh && f_cur == nullptr) {
+    // TMC * 1_disk into f^{k0}, f^{k0-1} and the tiled copy; g and gamma are
+    // checked in the same pass
+    CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux,
+                                   ws.gtick, ws.st_scratch, slot_cur, s, slot_prev,
+                                   tiled ? ws.ft : nullptr, ws.st));
+    tiled_ready = tiled;
   } else {
+    CK(appga::launch_check_inputs(g, gamma, M->m, f_cur, fresh ? nullptr : f_prev, M->d, ws.st,
+                                  s));
     CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(slot_prev, f_prev, fb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(slot_prev, fresh ? f_cur : f_prev, fb, cudaMemcpyDeviceToDevice, s));
   }
-  int32_t rk = k0;
-  rc = run_solver(M, g, gamma, k0, p, stats, &rk);
-  if (rc != APPGA_OK && rc != APPGA_ENUMERIC) return rc;
-  CK(cudaMemcpyAsync(f_out, ws.f[rk % 3], fb, cudaMemcpyDeviceToDevice, s));
-  if (f_out_prev) CK(cudaMemcpyAsync(f_out_prev, ws.f[(rk + 2) % 3], fb, cudaMemcpyDeviceToDevice, s));
-  const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
-  if (stats && track && !stats->stopped_early && rc == APPGA_OK) {
-    double phi = 0.0;
-    appga_status r2 = objective_on(M, ws.f[rk % 3], g, gamma, p, &phi, s);
-    if (r2 != APPGA_OK) return r2;
-    stats->phi = phi;
-  }
-  appga_status r3 = leave_stream(ctx, stream);
-  if (r3 != APPGA_OK) return r3;
+  appga::FwdArgs fa;
+  appga::PixArgs pa;
+  if ((rc = setup_run(M, g, gamma, k0, p, fresh, tiled_ready, &fa, &pa)) != APPGA_OK) return rc;
+  if ((rc = run_maps(M, g, gamma, p, fa, pa)) != APPGA_OK) return rc;
+  CK(appga::launch_copy_result(ws.st, ws.f, f_out, f_out_prev, M->d, s));
+  if (f_out_host) CK(cudaMemcpyAsync(f_out_host, f_out, fb, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ws.st_host, ws.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  if ((rc = leave_stream(ctx, stream)) != APPGA_OK) return rc;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
-  return rc;
+  const SolverState fin = *ws.st_host;
+  return finish_stats(fin, k0, p, stats);
 }
 
 }  // namespace
@@ -932,12 +971,13 @@ appga_status appga_kernel_times(appga_ctx* ctx, const appga_matrix* mat, const f
   appga_params q = *params;
   q.max_iters = n_iters;
   q.rel_obj_tol = 0.0;
-  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.gtick, ws.st_scratch,
-                                 ws.f[1], s));
-  CK(cudaMemcpyAsync(ws.f[0], ws.f[1], (size_t)M->d * 4, cudaMemcpyDeviceToDevice, s));
+  const SolverState h = start_state(1, &q);
+  if ((rc = momentum_table(M, ws.st, 1, &q, s, &h)) != APPGA_OK) return rc;
+  CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux, ws.gtick,
+                                 ws.st_scratch, ws.f[1], s, ws.f[0]));
   appga::FwdArgs fa;
   appga::PixArgs pa;
-  if ((rc = setup_run(M, g, gamma, 1, &q, &fa, &pa)) != APPGA_OK) return rc;
+  if ((rc = setup_run(M, g, gamma, 1, &q, true, false, &fa, &pa)) != APPGA_OK) return rc;
   const bool track = q.track_objective != 0;
   std::vector<cudaEvent_t> ev((size_t)2 * n_iters + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -988,12 +1028,10 @@ appga_status appga_reconstruct_host(appga_ctx* ctx, const appga_matrix* mat, con
   CK(cudaMemcpyAsync(ws.d_g, g_host, mb, cudaMemcpyHostToDevice, us));
   CK(cudaMemcpyAsync(ws.d_gamma, gamma_host, mb, cudaMemcpyHostToDevice, us));
   if (f_init_host) CK(cudaMemcpyAsync(ws.d_finit, f_init_host, db, cudaMemcpyHostToDevice, us));
-  rc = appga_reconstruct(ctx, mat, ws.d_g, ws.d_gamma, f_init_host ? ws.d_finit : nullptr, params,
-                         ws.d_fout, stats_host, stream);
-  if (rc != APPGA_OK && rc != APPGA_ENUMERIC) return rc;
-  CK(cudaMemcpyAsync(f_out_host, ws.d_fout, db, cudaMemcpyDeviceToHost, us));
-  CK(cudaStreamSynchronize(us));
-  return rc;
+  // the result comes back to f_out_host inside the solver call, before its
+  // one synchronisation
+  return solve_common(ctx, M, ws.d_g, ws.d_gamma, nullptr, f_init_host ? ws.d_finit : nullptr, 1,
+                      params, nullptr, ws.d_fout, stats_host, stream, true, f_out_host);
 }
 
 }  // extern "C"

@@ -99,6 +99,9 @@ struct FwdArgs {
   // indices (its projector gathers from ft, the stencil still reads f[])
   const float* ft;
   int32_t solver_acc;  // 1: accumulate y as the solver loop does, also when loop == 0
+  // loop: first forward phase of a fresh run (f^{k-1} = f^k, so y~ = y and
+  // the projection of f^{k-1} is not needed)
+  int32_t fresh_first;
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).
@@ -143,6 +146,18 @@ cudaError_t launch_reg_term(int n, const float* f, float lam1, float lam2, float
                             cudaStream_t s);
 cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, const float* f,
                                    int d, int* flag, cudaStream_t s);
+// Solver-run input check without a host round trip: on a bad g, gamma, fa or
+// fb (fa, fb may be NULL) sets APPGA_FLAG_DOMAIN in st->flags and st->done.
+cudaError_t launch_check_inputs(const float* g, const float* gamma, int m, const float* fa,
+                                const float* fb, int d, SolverState* st, cudaStream_t s);
+// One more finalisation of the solver loop: after the last forward phase of a
+// tracked run it turns that phase's partials into Phi of the result.
+cudaError_t launch_finalize(const PixArgs& a, cudaStream_t s);
+// out = f^{result_k}, out_prev = f^{result_k - 1} (may be NULL) from the ring
+// f[3], selected on the device from st; nothing is written if the run's
+// inputs failed the check.
+cudaError_t launch_copy_result(const SolverState* st, float* const f[3], float* out,
+                               float* out_prev, int d, cudaStream_t s);
 // theta_{k0+i}, i = 0..n, into tab and theta_{k0} into the state
 // Pixel (r, c) of an n x n image in the 8 x 8-tiled order: tiles row-major,
 // pixels row-major inside a tile; tiled_size(n) entries cover the image.
@@ -155,12 +170,18 @@ __host__ __device__ inline int32_t tiled_index(int r, int c, int n) {
 // ft[tiled_index(j)] = f[j] for the d = n * n pixels
 cudaError_t launch_to_tiled(const float* f, float* ft, int n, cudaStream_t s);
 bool tiled_gather_enabled();  // the solver loop gathers from the tiled copy
+// (with init: *st = *init first, so one launch starts a run)
 cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
-                               double a, double b, double omega, cudaStream_t s);
+                               double a, double b, double omega, cudaStream_t s,
+                               const SolverState* init = nullptr);
 long long disk_pixels(int n);
+// f_out = TMC * 1_disk; also into f_out2 and (8 x 8-tiled) ft when not NULL;
+// with check_st set, g and gamma are checked as launch_check_inputs does.
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
                                  long long npfov, float2* partial, unsigned int* gtick,
-                                 SolverState* st, float* f_out, cudaStream_t s);
+                                 SolverState* st, float* f_out, cudaStream_t s,
+                                 float* f_out2 = nullptr, float* ft = nullptr,
+                                 SolverState* check_st = nullptr);
 
 // ---- host CSR helpers (csr_host.cpp) ----
 struct HostCSR {

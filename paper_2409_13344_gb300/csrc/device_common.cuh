@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "appga_internal.h"
 
@@ -359,34 +360,73 @@ __device__ __forceinline__ float s_eps_f(float nrm2, float eps) {
 }
 
 
-// Double-float constants of df_log, computed once in extended precision.
-struct LogTables {
-  cudaError_t err = cudaSuccess;
-  LogTables() {
-    float th[65], tl[65], l2[2], t3[2], kp[2];
-    for (int j = 0; j <= 64; ++j) {
-      const long double v = logl(1.0L + (long double)j / 64.0L);
-      th[j] = (float)v;
-      tl[j] = (float)(v - (long double)th[j]);
+// Set-up that a CUDA device needs once (constant tables, function
+// attributes): run() calls init with the calling thread's current device and
+// returns that device's result on every later call.  Each device of the
+// process gets its own set-up.
+constexpr int kMaxDevices = 64;
+struct PerDeviceOnce {
+  std::mutex mu;
+  bool done[kMaxDevices] = {};
+  cudaError_t err[kMaxDevices] = {};
+  template <class F>
+  cudaError_t run(F init) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+      err[dev] = init();
+      done[dev] = true;
     }
-    const long double ln2 = logl(2.0L), third = 1.0L / 3.0L;
-    l2[0] = (float)ln2;
-    l2[1] = (float)(ln2 - (long double)l2[0]);
-    t3[0] = (float)third;
-    t3[1] = (float)(third - (long double)t3[0]);
-    const long double kappa = (long double)KAPPA;
-    kp[0] = (float)kappa;
-    kp[1] = (float)(kappa - (long double)kp[0]);
-    err = cudaMemcpyToSymbol(c_logtab_hi, th, sizeof th);
-    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_logtab_lo, tl, sizeof tl);
-    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_ln2, l2, sizeof l2);
-    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_third, t3, sizeof t3);
-    if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_kappa, kp, sizeof kp);
+    return err[dev];
   }
 };
+
+// Streaming multiprocessors of the current device (looked up once per device).
+inline int current_sm_count() {
+  static std::mutex mu;
+  static int sms[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (sms[dev] == 0) {
+    int s = 0;
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = s > 0 ? s : 1;
+  }
+  return sms[dev];
+}
+
+// Double-float constants of df_log, computed in extended precision and
+// uploaded to the constant banks of the current device.
+cudaError_t upload_log_tables() {
+  float th[65], tl[65], l2[2], t3[2], kp[2];
+  for (int j = 0; j <= 64; ++j) {
+    const long double v = logl(1.0L + (long double)j / 64.0L);
+    th[j] = (float)v;
+    tl[j] = (float)(v - (long double)th[j]);
+  }
+  const long double ln2 = logl(2.0L), third = 1.0L / 3.0L;
+  l2[0] = (float)ln2;
+  l2[1] = (float)(ln2 - (long double)l2[0]);
+  t3[0] = (float)third;
+  t3[1] = (float)(third - (long double)t3[0]);
+  const long double kappa = (long double)KAPPA;
+  kp[0] = (float)kappa;
+  kp[1] = (float)(kappa - (long double)kp[0]);
+  cudaError_t err = cudaMemcpyToSymbol(c_logtab_hi, th, sizeof th);
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_logtab_lo, tl, sizeof tl);
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_ln2, l2, sizeof l2);
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_third, t3, sizeof t3);
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_kappa, kp, sizeof kp);
+  return err;
+}
+// The tables of the current device, uploaded on its first use.
 cudaError_t ensure_tables() {
-  static LogTables t;
-  return t.err;
+  static PerDeviceOnce once;
+  return once.run(upload_log_tables);
 }
 
 

@@ -42,10 +42,10 @@ struct Workspace {
   float* d_gamma = nullptr;
   float* d_finit = nullptr;
   float* d_fout = nullptr;
-  // graph cache
-  cudaGraphExec_t gexec = nullptr;
+  // graph cache: executable graphs of n maps (n = the replay length and the
+  // powers of two below it) for the parameters in gkey
+  std::map<int, cudaGraphExec_t> gexec;
   std::string gkey;
-  int graph_iters = 0;
 };
 
 // Launch schedule of the batched kernels (0 = the kernels' defaults), as
@@ -184,7 +184,7 @@ appga_status ensure_workspace(appga_matrix* M);
 // theta_{k0+i}, i <= max_iters, of a run into ws.theta_tab (grown as needed)
 // and theta_{k0} into the state st.
 appga_status momentum_table(appga_matrix* M, SolverState* st, int k0, const appga_params* p,
-                            cudaStream_t s);
+                            cudaStream_t s, const SolverState* init = nullptr);
 IterParams iter_params(const appga_params* p, bool track);
 bool bf16_requested(const appga_matrix* M, const appga_params* p);
 appga_status check_params_and_mat(appga_ctx* ctx, const appga_matrix* M, const appga_params* p);

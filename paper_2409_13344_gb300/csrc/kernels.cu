@@ -485,8 +485,9 @@ __device__ __forceinline__ void forward_row(const FwdArgs& a, const SolverState*
   }
   if (a.w != nullptr) {
     df yt = y;
-    if (a.loop) {
-      // y~ = y + theta (y - y^{k-1}): the projection of f~ by linearity
+    if (a.loop && !a.fresh_first) {
+      // y~ = y + theta (y - y^{k-1}): the projection of f~ by linearity (the
+      // first step of a fresh run has f^{k-1} = f^k, so there y~ = y)
       const float2 yp = a.y[(kk + 1) & 1][row];
       const df th = {st->theta_hi, st->theta_lo};
       const df dy = df_add(y, df_neg({yp.x, yp.y}));
@@ -554,7 +555,9 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     rg.prologue(a.A, lane, pol);
   }
   pdl_wait();
-  if (a.loop && st->done) return;  // uniform over the grid
+  // done == 2: the last pixel phase has run and this forward phase only
+  // evaluates the objective of the result (uniform over the grid)
+  if (a.loop && st->done == 1) return;
   const int kk = a.loop ? st->k : 0;
   float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
   int hits = 0, bad = 0;
@@ -689,7 +692,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
   pdl_trigger();
   pdl_wait();
   SolverState* st = a.st;
-  if (st->done) return;  // uniform over the block
+  const int state = st->done;  // uniform over the block
+  if (state == 1) return;
   const int kk = st->k;
   df phi = {0.f, 0.f};
   if (a.ip.track) {
@@ -707,6 +711,13 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
     phi = block_sum_acc(h, l);
   }
   if (threadIdx.x != 0) return;
+  if (state == 2) {
+    // after the run's last forward phase: Phi of the result, f^{result_k}
+    st->phi_prev = st->phi_cur;
+    st->phi_cur = (double)phi.hi + (double)phi.lo;
+    st->done = 1;
+    return;
+  }
   if (a.ip.track) {
     const double cur = (double)phi.hi + (double)phi.lo;
     const double prev = st->phi_cur;
@@ -732,7 +743,9 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
   }
   st->theta_prev = st->theta_hi;
   if (kk >= st->k_last) {
-    st->done = 1;
+    // with the objective tracked, the forward phase of f^{kk+1} still runs
+    // and a last finalisation turns its partials into Phi(f^{kk+1})
+    st->done = a.ip.track ? 2 : 1;
     st->result_k = kk + 1;
   }
   st->k = kk + 1;
@@ -746,8 +759,9 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
 // per-step finalisation costs several microseconds on this part.  A resumed
 // run computes the same values, so it replays an uninterrupted one bit for bit.
 __global__ void k_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
-                              double a, double b, double omega) {
+                              double a, double b, double omega, SolverState init, int set_state) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && set_state) *st = init;
   if (momentum == APPGA_MOMENTUM_NESTEROV) {
     if (i != 0) return;
     double t = 1.0;
@@ -823,16 +837,53 @@ __global__ void k_validate(const float* __restrict__ g, const float* __restrict_
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// Input check of a solver run: marks the run state with APPGA_FLAG_DOMAIN and
+// ends the run (done = 1) if some g_i is negative or not finite, some gamma_i
+// is not positive or not finite, or an entry of f_a / f_b (may be NULL) is
+// negative or not finite.  No host round trip: the host reads the flag with
+// the final state.
+__device__ __forceinline__ bool bad_counts(float gi, float ci) {
+  return !(isfinite(gi) && gi >= 0.f && isfinite(ci) && ci > 0.f);
+}
+__device__ __forceinline__ void mark_domain(SolverState* st) {
+  atomicOr(&st->flags, APPGA_FLAG_DOMAIN);
+  st->done = 1;
+}
+__global__ void k_check_inputs(const float* __restrict__ g, const float* __restrict__ gamma,
+                               int m, const float* __restrict__ fa,
+                               const float* __restrict__ fb, int d, SolverState* st) {
+  int bad = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    bad |= bad_counts(g[i], gamma[i]) ? 1 : 0;
+  for (int q = 0; q < 2; ++q) {
+    const float* f = q == 0 ? fa : fb;
+    if (f == nullptr) continue;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += stride) {
+      const float x = f[i];
+      if (!(isfinite(x) && x >= 0.f)) bad = 1;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) mark_domain(st);
+}
+
 // Initial image (Sec. 4.1): TMC * 1_disk, TMC = (sum g - sum gamma)/(NPFOV * NPA).
+// With vst set, the same pass checks g and gamma for a solver run (as
+// k_check_inputs does).
 __global__ void __launch_bounds__(THREADS) k_actc(const float* __restrict__ g,
                                                   const float* __restrict__ gamma, int m,
                                                   float2* partial, unsigned int* gtick,
-                                                  SolverState* st, double* actc_out) {
+                                                  SolverState* st, double* actc_out,
+                                                  SolverState* vst) {
   float h = 0.f, l = 0.f;
+  int bad = 0;
   for (int i = blockIdx.x * THREADS + threadIdx.x; i < m; i += gridDim.x * THREADS) {
-    acc_add(h, l, g[i], 0.f);
-    acc_add(h, l, -gamma[i], 0.f);
+    const float gi = g[i], ci = gamma[i];
+    acc_add(h, l, gi, 0.f);
+    acc_add(h, l, -ci, 0.f);
+    bad |= bad_counts(gi, ci) ? 1 : 0;
   }
+  if (vst != nullptr && __syncthreads_or(bad) && threadIdx.x == 0) mark_domain(vst);
   const df b = block_sum_acc(h, l);
   double tot = 0.0;
   if (grid_reduce(partial, gtick, &st->ticket_aux, b, &tot) && threadIdx.x == 0) *actc_out = tot;
@@ -843,11 +894,34 @@ __device__ __forceinline__ bool in_disk(int r, int c, int n) {
   const long long dx = 2ll * c + 1 - n, dy = 2ll * r + 1 - n;
   return dx * dx + dy * dy <= (long long)n * n;
 }
-__global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, float* f_out) {
+// f_out (and f_out2, ft if not NULL; ft in the 8 x 8-tiled pixel order)
+__global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, float* f_out,
+                            float* f_out2, float* ft) {
   const double tmc = *actc / ((double)npfov * (double)n_angles);
   const float v = (float)tmc;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n * n; j += gridDim.x * blockDim.x)
-    f_out[j] = in_disk(j / n, j % n, n) ? v : 0.f;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n * n; j += gridDim.x * blockDim.x) {
+    const int r = j / n, c = j % n;
+    const float x = in_disk(r, c, n) ? v : 0.f;
+    f_out[j] = x;
+    if (f_out2) f_out2[j] = x;
+    if (ft) ft[tiled_index(r, c, n)] = x;
+  }
+}
+
+// Result of a solver run: out = f^{result_k} and out_prev = f^{result_k - 1}
+// (may be NULL) from the iterate ring, unless the inputs failed the check.
+__global__ void k_copy_result(const SolverState* st, const float* __restrict__ f0,
+                              const float* __restrict__ f1, const float* __restrict__ f2,
+                              float* __restrict__ out, float* __restrict__ out_prev, int d) {
+  if (st->flags & APPGA_FLAG_DOMAIN) return;
+  const int rk = st->result_k;
+  const float* ring[3] = {f0, f1, f2};
+  const float* cur = ring[rk % 3];
+  const float* prv = ring[(rk + 2) % 3];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+    out[j] = cur[j];
+    if (out_prev) out_prev[j] = prv[j];
+  }
 }
 
 }  // namespace
@@ -939,13 +1013,14 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   // accumulates y in FP32; the stand-alone projection and objective calls
   // in double-float
   const bool dfa = (a.loop || a.solver_acc) ? APPGA_LOOP_DF != 0 : true;
-  static const cudaError_t carve = [] {
+  static PerDeviceOnce carve_once;
+  const cudaError_t carve = carve_once.run([] {
     cudaError_t r = set_carveout(k_forward<true, true>, APPGA_CARVEOUT_FW);
     if (r == cudaSuccess) r = set_carveout(k_forward<true, false>, APPGA_CARVEOUT_FW);
     if (r == cudaSuccess) r = set_carveout(k_forward<false, true>, APPGA_CARVEOUT_FW);
     if (r == cudaSuccess) r = set_carveout(k_forward<false, false>, APPGA_CARVEOUT_FW);
     return r;
-  }();
+  });
   if (carve != cudaSuccess) return carve;
   if (a.use_bf16)
     return dfa ? launch_dep(k_forward<true, true>, grid, FW::THREADS, s, a)
@@ -955,17 +1030,35 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
-  static const cudaError_t carve = [] {
+  static PerDeviceOnce carve_once;
+  const cudaError_t carve = carve_once.run([] {
     cudaError_t r = set_carveout(k_pixel<true>, APPGA_CARVEOUT_PX);
     if (r == cudaSuccess) r = set_carveout(k_pixel<false>, APPGA_CARVEOUT_PX);
     return r;
-  }();
+  });
   if (carve != cudaSuccess) return carve;
   const int grid = proj_blocks<PX>(a.At.rows);
   const cudaError_t e = a.use_bf16 ? launch_dep(k_pixel<true>, grid, PX::THREADS, s, a)
                                    : launch_dep(k_pixel<false>, grid, PX::THREADS, s, a);
   if (e != cudaSuccess || a.theta_tab == nullptr) return e;
   return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
+}
+
+cudaError_t launch_finalize(const PixArgs& a, cudaStream_t s) {
+  return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
+}
+
+cudaError_t launch_check_inputs(const float* g, const float* gamma, int m, const float* fa,
+                                const float* fb, int d, SolverState* st, cudaStream_t s) {
+  k_check_inputs<<<256, 256, 0, s>>>(g, gamma, m, fa, fb, d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_result(const SolverState* st, float* const f[3], float* out,
+                               float* out_prev, int d, cudaStream_t s) {
+  const int grid = (d + 255) / 256 < 1024 ? (d + 255) / 256 : 1024;
+  k_copy_result<<<grid, 256, 0, s>>>(st, f[0], f[1], f[2], out, out_prev, d);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
@@ -998,9 +1091,12 @@ cudaError_t launch_validate_inputs(const float* g, const float* gamma, int m, co
 }
 
 cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
-                               double a, double b, double omega, cudaStream_t s) {
+                               double a, double b, double omega, cudaStream_t s,
+                               const SolverState* init) {
   const int threads = 256, blocks = (n + 1 + threads - 1) / threads;
-  k_theta_table<<<blocks, threads, 0, s>>>(st, tab, k0, n, momentum, a, b, omega);
+  SolverState z{};
+  k_theta_table<<<blocks, threads, 0, s>>>(st, tab, k0, n, momentum, a, b, omega,
+                                           init ? *init : z, init ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1017,14 +1113,15 @@ long long disk_pixels(int n) {
 
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
                                  long long npfov, float2* partial, unsigned int* gtick,
-                                 SolverState* st, float* f_out, cudaStream_t s) {
+                                 SolverState* st, float* f_out, cudaStream_t s, float* f_out2,
+                                 float* ft, SolverState* check_st) {
   // the ACTc scalar is parked in the last partial slot (as raw bytes of a double)
   double* actc = reinterpret_cast<double*>(partial + max_partials(m, n) - 1);
-  k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, gtick, st, actc);
+  k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, gtick, st, actc, check_st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_fill_disk<<<(n * n + 255) / 256 < 1024 ? (n * n + 255) / 256 : 1024, 256, 0, s>>>(
-      n, n_angles, (int)npfov, actc, f_out);
+      n, n_angles, (int)npfov, actc, f_out, f_out2, ft);
   return cudaGetLastError();
 }
 

@@ -7,9 +7,12 @@
 // a CSR row: lanes load 32 (column, value) pairs at a time and stage them in
 // shared memory; every lane reads them back with broadcast loads and, for
 // each nonzero, gathers its 4V-byte piece of the Kp-wide image row (one
-// coalesced row per warp) and accumulates V products in FP32.  Each block
-// owns a contiguous run of rows, so neighbouring rays (or pixels) reuse the
-// gathered rows from L1.  The per-(row, slot) epilogues match the
+// coalesced row per warp) and accumulates V products in FP32.  The
+// back-projection's blocks own contiguous runs of pixels, whose rays overlap,
+// so the gathered weight rows are reused from L1; the forward projection
+// deals rays to the warps of the whole grid in turn, so the grid works on
+// neighbouring rays at once and the image rows they gather stay in L2 (each
+// order is a per-projection switch).  The per-(row, slot) epilogues match the
 // single-slice kernels (Eq. APPGAiter, Eq. EM, Sec. 2.2); the SHOITV stencil
 // runs on shared-memory tiles of 2 x 32 pixels x 8 slots.
 //
@@ -880,15 +883,7 @@ __global__ void __launch_bounds__(256) k_binit_image(const float* __restrict__ g
 }
 
 
-int sm_count() {
-  static int sms = [] {
-    int dev = 0, s = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-    return s > 0 ? s : 1;
-  }();
-  return sms;
-}
+int sm_count() { return current_sm_count(); }
 
 int bforward_grid_n(const BFwdArgs& a, int* n_spmv) {
   const int sms = sm_count();

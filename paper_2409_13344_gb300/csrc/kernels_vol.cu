@@ -395,15 +395,7 @@ __global__ void __launch_bounds__(256) k_sum_pairs(const float2* __restrict__ p,
   if (threadIdx.x == 0) *out = (double)s.hi + (double)s.lo;
 }
 
-int sm_count_vol() {
-  static const int sms = [] {
-    int dev = 0, s = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-    return s > 0 ? s : 1;
-  }();
-  return sms;
-}
+int sm_count_vol() { return current_sm_count(); }
 
 }  // namespace
 
@@ -417,8 +409,11 @@ int stencil3d_grid(int n, int nz) {
 
 cudaError_t launch_stencil3d(const Vol3Args& a, cudaStream_t s) {
   if (a.nz < 1 || a.nz > MAXZ || a.n < 1) return cudaErrorInvalidValue;
-  static cudaError_t attr = cudaFuncSetAttribute(
-      k_stencil3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Vol3Smem));
+  static PerDeviceOnce attr_once;
+  const cudaError_t attr = attr_once.run([] {
+    return cudaFuncSetAttribute(k_stencil3d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(Vol3Smem));
+  });
   if (attr != cudaSuccess) return attr;
   k_stencil3d<<<stencil3d_grid(a.n, a.nz), NT, sizeof(Vol3Smem), s>>>(a);
   return cudaGetLastError();

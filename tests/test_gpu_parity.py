@@ -329,10 +329,47 @@ def test_stopping_rule(A, ctx, mats):
     prob, ref = run_oracle(geom, Amat, sl, max_iters=400, beta=0.1, omega=1.0, rel_obj_tol=tol)
     assert st.stopped_early == 1 and ref.iters < 400
     assert abs(st.iters - ref.iters) <= 1
-    if st.iters == ref.iters:
-        assert rel_l2(f, ref.f) <= 1e-5
+    # the test can fire one map apart on FP32 and FP64 objectives; the image
+    # is compared with the oracle's iterate after the GPU's own map count
+    if st.iters != ref.iters:
+        _, ref = run_oracle(geom, Amat, sl, max_iters=st.iters, beta=0.1, omega=1.0)
+    assert rel_l2(f, ref.f) <= 1e-5
     phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
     assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+
+
+@pytest.mark.parametrize("track", [0, 1])
+def test_zero_maps_returns_the_initial_image(A, ctx, mats, track):
+    # max_iters = 0: the result is f^1 = f_init, with Phi(f^1) when tracked
+    geom, Amat, sl = problem("64")
+    f, st = run_gpu(A, ctx, mats["64"], sl, max_iters=0, track_objective=track)
+    f0 = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    assert st.iters == 0 and st.result_k == 1 and st.stopped_early == 0
+    np.testing.assert_allclose(f, f0, rtol=1e-7)
+    if track:
+        prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+        phi0 = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+        assert abs(st.phi - phi0) <= 1e-9 * abs(phi0)
+        assert math.isnan(st.phi_prev)
+    else:
+        assert math.isnan(st.phi)
+
+
+@pytest.mark.parametrize("iters,graph_iters", [(1, 0), (5, 0), (17, 0), (23, 4), (31, 16)])
+def test_exact_map_counts(A, ctx, mats, iters, graph_iters):
+    # a run of K maps replays whole graphs plus power-of-two remainders and
+    # must apply exactly K maps, with Phi of the result and of the map before
+    geom, Amat, sl = problem("64")
+    f, st = run_gpu(A, ctx, mats["64"], sl, max_iters=iters, graph_iters=graph_iters,
+                    track_objective=1)
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    ref = O.appga(prob, O.Params(max_iters=iters), n_angles=geom.n_angles, track_phi=True)
+    assert st.iters == iters and st.result_k == iters + 1
+    assert rel_l2(f, ref.f) <= 1e-5
+    phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+    # Phi of the previous iterate, against the oracle's value at f^K
+    assert abs(st.phi_prev - ref.phi[-2]) <= 1e-8 * abs(ref.phi[-2])
 
 
 def test_guard_hits_counted(A, ctx, mats):
@@ -463,7 +500,7 @@ def test_full_size_forward_and_backproject(A, ctx, m256):
 @pytest.mark.parametrize("counts,omega,iters,beta", [
     (1e6, 0.5, 500, 1.0),    # the benchmarked configuration
     (1e6, 1.0, 500, 1.0),
-    (1e6, 0.25, 200, 1.0),
+    (1e6, 0.25, 500, 1.0),
     (5e6, 1.0, 300, 0.1),
     (5e6, 0.5, 30, 1.0),
 ])
@@ -478,18 +515,72 @@ def test_full_size_trajectory(A, ctx, m256, counts, omega, iters, beta):
     assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
 
 
+def _oracle_fp32_spread(prob, par, f0, seed):
+    """Relative L2 distance after par.max_iters maps between the oracle run
+    and the same run with a relative perturbation of FP32 size (2^-24 N(0,1))
+    applied to every new iterate: how far FP32 rounding alone can move the
+    trajectory of this problem."""
+    lam = prob.em_lambda()
+    th = O.thetas_for(par, par.max_iters)
+    rng = np.random.default_rng(seed)
+    fk, fkm = f0.copy(), f0.copy()
+    for it in range(par.max_iters):
+        fn, _ = O.appga_step(prob, fk, fkm, th[it], par, lam)
+        fn = fn * (1.0 + 2.0 ** -24 * rng.standard_normal(fn.shape[0]))
+        fkm, fk = fk, fn
+    return fk
+
+
 @pytest.mark.parametrize("omega", [0.25, 1.0])
-def test_full_size_5e6_beta1_objective(A, ctx, m256, omega):
-    # With 5e6 counts and beta = 1 the EM step breaks the step-size condition
-    # (Thm. 10 needs p_max <= 1/L) and the FP64 oracle itself amplifies a 1e-9
-    # perturbation of f^1 about 1e4-fold in 100 iterations, so the image is not
-    # determined to 1e-5 by FP32 inputs.  The objective value is: compare it.
+def test_full_size_5e6_beta1_500_maps(A, ctx, m256, omega):
+    # 256^2 at 5e6 counts with beta = 1 over the workload's 500 maps.  The EM
+    # step here breaks the step-size condition of Thm. 10 (p_max <= 1/L) and
+    # the FP64 oracle itself does not fix the image to 1e-5 from FP32-sized
+    # rounding: the oracle-side pin (tests/test_oracle.py) shows a 2^-24
+    # perturbation of f^1 growing past 1e-5.  So the GPU's distance from the
+    # oracle is bounded by a stated multiple (10x) of the oracle's own spread
+    # under FP32-sized noise on every iterate, and the objective is compared.
     geom, Amat, sl = problem("256", counts=5e6, phantom="lesions")
-    f, st = run_gpu(A, ctx, m256, sl, max_iters=100, omega=omega, track_objective=1)
-    prob, ref = run_oracle(geom, Amat, sl, max_iters=100, omega=omega)
+    f, st = run_gpu(A, ctx, m256, sl, max_iters=500, omega=omega, track_objective=1)
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    par = O.Params(max_iters=500, omega=omega)
+    f0 = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
+    ref = O.appga(prob, par, f_init=f0, track_phi=False)
+    noisy = _oracle_fp32_spread(prob, par, f0, seed=1)
+    spread = rel_l2(noisy, ref.f)
+    dist = rel_l2(f, ref.f)
+    assert spread > 1e-6
+    assert dist <= 10.0 * spread, (dist, spread)
     phi_ref = prob.objective(ref.f, 0.1, 0.05, 1e-3)
-    assert abs(st.phi - phi_ref) <= 1e-9 * abs(phi_ref)
-    assert rel_l2(f, ref.f) <= 1e-3
+    phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+    # the objective is flat where the trajectories part
+    assert abs(st.phi - phi_ref) <= 1e-7 * abs(phi_ref)
+
+
+def _bf16_matrix(Amat):
+    return sp.csr_matrix((bf16_round(Amat.data), Amat.indices, Amat.indptr), shape=Amat.shape)
+
+
+def test_full_size_bf16_single_slice(A, ctx, m256):
+    # 256^2 with the BF16 copy of A (FP32 accumulation) over the benchmarked
+    # 500-map run.  Against the FP64 oracle on the BF16-rounded matrix (the
+    # method's arithmetic): 1e-5.  Against the FP64 oracle on the FP32 matrix
+    # the distance includes the matrix rounding itself, which the two FP64
+    # oracles alone already show: about 1.3e-3 after 100 maps and 1.8e-3 after
+    # 500 here, above the 1e-3 that holds on the 64^2 grid over 30 maps.  The
+    # GPU may add no more than the FP32 arithmetic's share to it.
+    geom, Amat, sl = problem("256", counts=1e6, phantom="lesions")
+    f, st = run_gpu(A, ctx, m256, sl, max_iters=500, a_precision=1, track_objective=1)
+    _, ref32 = run_oracle(geom, Amat, sl, max_iters=500)
+    Ab = _bf16_matrix(Amat)
+    probb, refb = run_oracle(geom, Ab, sl, max_iters=500)
+    rounding = rel_l2(refb.f, ref32.f)
+    assert 1e-4 < rounding < 5e-3
+    assert rel_l2(f, refb.f) <= 1e-5
+    assert rel_l2(f, ref32.f) <= rounding + 2e-5
+    phi_same = probb.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
+    assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
 
 
 def test_largest_geometry_single_slice_sampled(A, ctx):
@@ -507,3 +598,27 @@ def test_largest_geometry_single_slice_sampled(A, ctx):
         assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
     finally:
         mat.close()
+
+
+def test_objective_on_every_visible_device(A):
+    # The double-float logarithm's constant tables and the kernels' function
+    # attributes are set up per device on first use there: the objective of
+    # the same inputs is the same on device 0 and on device 1 (where a second
+    # device is visible; a one-GPU machine skips this).
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one CUDA device visible")
+    geom, Amat, sl = problem("64")
+    vals = []
+    for dev in (0, 1):
+        c = A.Context(dev)
+        mat = A.Matrix(c, Amat, geom.n, geom.n_angles)
+        d = f"cuda:{dev}"
+        f = torch.from_numpy(sl.f_true.astype(np.float32)).to(d)
+        vals.append(A.appga_objective(c.handle, mat.handle, f, torch.from_numpy(sl.g).to(d),
+                                      torch.from_numpy(sl.gamma).to(d), A.default_params()))
+        mat.close()
+        c.close()
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    ref = prob.objective(sl.f_true.astype(np.float32).astype(np.float64), 0.1, 0.05, 1e-3)
+    assert vals[0] == vals[1]
+    assert abs(vals[1] - ref) <= 1e-9 * abs(ref)

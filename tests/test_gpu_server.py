@@ -221,8 +221,12 @@ def test_server_per_request_stopping_matches_oracle(A, ctx):
         ref = O.appga(prob, O.Params(**kw), n_angles=geom.n_angles, track_phi=True)
         assert st.stopped_early == 1
         assert abs(st.iters - ref.iters) <= 1, (st.iters, ref.iters)
-        if st.iters == ref.iters:
-            assert rel(f, ref.f) <= 1e-5
+        # FP32 and FP64 objectives can fire the test one map apart: compare
+        # with the oracle's iterate after the request's own map count
+        if st.iters != ref.iters:
+            kw1 = dict(kw, max_iters=st.iters, rel_obj_tol=0.0)
+            ref = O.appga(prob, O.Params(**kw1), n_angles=geom.n_angles, track_phi=False)
+        assert rel(f, ref.f) <= 1e-5
         iters.append(st.iters)
     assert len(set(iters)) > 1
     srv.close()

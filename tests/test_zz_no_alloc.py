@@ -34,7 +34,8 @@ def ctx(lib):
     c.close()
 
 
-@pytest.mark.parametrize("name,counts", [("64", 1e5), ("256", 1e6)])
+# 512 x 512 (360 x 731 bins) is the largest size the fixed scratch serves
+@pytest.mark.parametrize("name,counts", [("64", 1e5), ("256", 1e6), ("512", 1e6)])
 def test_noalloc_objective_matches_allocating_call_twice(lib, ctx, name, counts):
     geom = W.GEOMETRIES[name]
     A = W.system_matrix(name)
