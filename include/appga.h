@@ -107,6 +107,10 @@ typedef struct {
   int64_t nnz_padded_t; /* stored entries of A^T (row padded) */
   int32_t has_bf16;
   int64_t device_bytes; /* device memory held by the handle */
+  int32_t packed_columns; /* 1 if the solver loop streams 2-byte packed column
+                             indices (every column below 2^20 and, within each
+                             4-entry pack of a row, within [-8192, 8191] of the
+                             pack's first column); 0: 4-byte indices */
 } appga_matrix_info;
 appga_status appga_matrix_get_info(const appga_matrix* mat, appga_matrix_info* out);
 

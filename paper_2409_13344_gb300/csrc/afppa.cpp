@@ -93,6 +93,8 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   h.k0 = k0;
   h.k_last = k0 + p->max_iters - 1;
   h.done = p->max_iters == 0 ? 1 : 0;
+  h.k_next = k0;
+  h.done_next = h.done;
   h.result_k = k0;
   CK(cudaMemcpyAsync(ws.st, &h, sizeof h, cudaMemcpyHostToDevice, s));
   if ((rc = momentum_table(M, ws.st, k0, p, s)) != APPGA_OK) return rc;
@@ -128,6 +130,7 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   fa.want_data = 0;
   fa.n = M->n;
   fa.ip = iter_params(p, false);
+  fa.theta_tab = ws.theta_tab;
   const bool tiled = tiled_gather_enabled();
   if (tiled) {
     // the loop's projector gathers f^k from its 8 x 8-tiled copy

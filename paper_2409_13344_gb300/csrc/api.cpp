@@ -24,6 +24,17 @@ thread_local std::string g_last_error;
 constexpr int kDefaultGraphIters = 16;
 }  // namespace
 
+// The solver loop streams 2-byte packed column indices where the matrix
+// allows (1), or 4-byte indices always (0).
+#ifndef APPGA_PACK
+#define APPGA_PACK 1
+#endif
+// The single-slice solver finalises each step in the pixel phase's first
+// blocks (1) or in a separate one-block kernel (0).
+#ifndef APPGA_FUSE_FIN
+#define APPGA_FUSE_FIN 1
+#endif
+
 namespace appga {
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -50,6 +61,7 @@ void free_csr(DevCSR& c) {
   cudaFree(c.col);
   cudaFree(c.val);
   cudaFree(c.val_bf16);
+  cudaFree(c.cpk);
   c = DevCSR();
 }
 
@@ -200,6 +212,8 @@ SolverState start_state(int32_t k0, const appga_params* p) {
   h.k0 = k0;
   h.k_last = k0 + p->max_iters - 1;
   h.done = p->max_iters == 0 ? (track ? 2 : 1) : 0;
+  h.k_next = k0;
+  h.done_next = h.done;
   h.result_k = k0;
   h.phi_cur = std::numeric_limits<double>::quiet_NaN();
   h.phi_prev = h.phi_cur;
@@ -251,6 +265,7 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   fa.gR = ws.gR;
   fa.n = M->n;
   fa.ip = iter_params(p, track);
+  fa.theta_tab = ws.theta_tab;
 
   appga::PixArgs pa{};
   pa.At = M->At;
@@ -268,9 +283,11 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.theta_tab = ws.theta_tab;
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
+  pa.fuse_fin = APPGA_FUSE_FIN;
   if (appga::tiled_gather_enabled()) {
     // the loop's projector gathers f^k from its 8 x 8-tiled copy
     fa.A.col = M->A_tiled.col;
+    fa.A.cpk = M->A_tiled.cpk;
     fa.ft = ws.ft;
     pa.ft = ws.ft;
     if (!tiled_ready) CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
@@ -348,6 +365,13 @@ appga_status run_maps(appga_matrix* M, const float* g, const float* gamma,
     const std::string key = graph_key(p, track, bf16, S) + "|" +
                             std::to_string((uintptr_t)g) + "|" + std::to_string((uintptr_t)gamma) +
                             "|" + std::to_string((uintptr_t)ws.theta_tab);
+    // the whole ladder (S and every power of two below it) is captured on
+    // first use of these arguments, so later calls of any length find their
+    // graphs cached
+    cudaGraphExec_t unused = nullptr;
+    appga_status rc0 = loop_graph(ws, key, S, fa, pa, s, &unused);
+    for (int b = 1; b < S && rc0 == APPGA_OK; b *= 2) rc0 = loop_graph(ws, key, b, fa, pa, s, &unused);
+    if (rc0 != APPGA_OK) return rc0;
     const std::vector<int> plan = replay_plan(p->max_iters, S);
     std::vector<cudaGraphExec_t> execs(plan.size());
     for (size_t r = 0; r < plan.size(); ++r) {
@@ -755,10 +779,23 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
       ct[q] = appga::tiled_index(pa.col[q] / n_side, pa.col[q] % n_side, n_side);
     M->A_tiled = M->A;
     M->A_tiled.col = nullptr;
+    M->A_tiled.cpk = nullptr;
     cudaError_t e = dalloc(&M->A_tiled.col, ct.size(), &M->bytes);
     if (e == cudaSuccess && !ct.empty())
       e = cudaMemcpy(M->A_tiled.col, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) rc = cuda_fail(e, "tiled column indices");
+    // packed columns of the solver loop's two projections (both or neither)
+    std::vector<uint64_t> pk_a, pk_t;
+    if (APPGA_PACK && e == cudaSuccess && !ct.empty() && !pt.col.empty() &&
+        appga::pack_columns(ct, &pk_a) &&
+        appga::pack_columns(pt.col, &pk_t)) {
+      e = dalloc(&M->A_tiled.cpk, pk_a.size(), &M->bytes);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(M->A_tiled.cpk, pk_a.data(), pk_a.size() * 8, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = dalloc(&M->At.cpk, pk_t.size(), &M->bytes);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(M->At.cpk, pk_t.data(), pk_t.size() * 8, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "tiled and packed column indices");
   }
   if (rc == APPGA_OK) {
     cudaError_t e = dalloc(&M->inv_lambda, (size_t)d, &M->bytes);
@@ -780,7 +817,8 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
 appga_status appga_matrix_destroy(appga_matrix* M) {
   if (!M) return APPGA_OK;
   if (M->ctx) cudaSetDevice(M->ctx->device);
-  cudaFree(M->A_tiled.col);  // its other arrays belong to A
+  cudaFree(M->A_tiled.col);  // its other arrays (but the packed columns) belong to A
+  cudaFree(M->A_tiled.cpk);
   free_csr(M->A);
   free_csr(M->At);
   cudaFree(M->inv_lambda);
@@ -809,6 +847,7 @@ appga_status appga_matrix_get_info(const appga_matrix* M, appga_matrix_info* out
   out->nnz_padded_t = M->At.nnz_padded;
   out->has_bf16 = M->has_bf16;
   out->device_bytes = M->bytes;
+  out->packed_columns = M->At.cpk != nullptr ? 1 : 0;
   return APPGA_OK;
 }
 

@@ -19,6 +19,16 @@ constexpr double KAPPA = 1e-3;
 // starts on a 16-byte boundary and streams as 4-entry packs.
 constexpr int ROW_PAD = 4;
 
+// Packed column indices: the four entries of a row-padded 4-entry pack as
+// one 64-bit word, the first column in bits 0-19 and the other three as
+// signed 14-bit offsets from it in bits 20-33, 34-47 and 48-61 (2 bytes per
+// entry instead of 4).  A matrix whose columns do not fit (a column above
+// 2^20 - 1 or an offset outside [-8192, 8191]) keeps 32-bit indices only.
+constexpr int PACK_ENTRIES = ROW_PAD;
+constexpr int PACK_BASE_BITS = 20;
+constexpr int32_t PACK_BASE_MAX = (1 << PACK_BASE_BITS) - 1;
+constexpr int32_t PACK_OFFSET_MAX = 8191;
+
 struct DevCSR {
   int32_t rows = 0, cols = 0;
   int64_t nnz_padded = 0;
@@ -26,20 +36,28 @@ struct DevCSR {
   int32_t* col = nullptr;        // nnz_padded
   float* val = nullptr;          // nnz_padded
   uint16_t* val_bf16 = nullptr;  // nnz_padded (optional BF16 copy)
+  uint2* cpk = nullptr;          // nnz_padded / 4 packed columns (optional, solver loop)
 };
 
 // Device-resident iteration state of one solve.  Kernels derive buffer
 // indices and the momentum scalar from it, so captured graphs replay
 // unchanged from one iteration to the next.
+//
+// Step hand-over in the solver loop: the forward phase of a step reads the
+// step's index and run status from k_next / done_next (its block 0 then
+// publishes them, with theta, as k / done / theta for the pixel phase), and
+// the finalisation of the step -- in the pixel phase's first blocks, or in
+// the one-block k_finalize -- writes the next ones.  So no kernel overwrites
+// a field that blocks of the same kernel may still read.
 struct SolverState {
   int32_t k;          // index of the current iterate f^k
   int32_t k_last;     // last pixel-phase index to run
   int32_t k0;         // first index of this run
-  int32_t done;       // set once the run is finished
+  int32_t done;       // 0 running; 1 finished; 2 finished, objective of the result pending
   int32_t result_k;   // index of the returned iterate
   int32_t stopped_early;
   int32_t flags;      // APPGA_FLAG_* (sticky)
-  int32_t pad0;
+  int32_t k_next;     // index of the next forward phase
   double theta;       // theta_k for the current k (FP64)
   float theta_hi;     // theta_k as a double-float pair (for FP32-pipe arithmetic)
   float theta_lo;
@@ -51,7 +69,7 @@ struct SolverState {
   unsigned int ticket_p;
   unsigned int ticket_r;
   unsigned int ticket_aux;
-  unsigned int pad1;
+  int32_t done_next;  // run status for the next forward phase
   // fixed-point proximity iteration (AFPPA): theta of the step just taken,
   // the dual step sizes from the largest preconditioner entry of that step,
   // and that largest entry as bits (positive floats order as integers)
@@ -102,6 +120,8 @@ struct FwdArgs {
   // loop: first forward phase of a fresh run (f^{k-1} = f^k, so y~ = y and
   // the projection of f^{k-1} is not needed)
   int32_t fresh_first;
+  // loop: theta_{k0+i} of the run (the forward phase takes theta_k from it)
+  const ThetaEntry* theta_tab;
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).
@@ -127,6 +147,9 @@ struct PixArgs {
   int32_t use_bf16;
   int32_t want_pmax;  // also reduce the largest preconditioner entry (AFPPA step sizes)
   float* ft;          // if set: f^{k+1} also written in the 8 x 8-tiled pixel order
+  // 1: the pixel phase's first blocks finalise the step (Phi(f^k) from the
+  // forward phase's partials, stopping test, next index); 0: k_finalize does
+  int32_t fuse_fin;
 };
 
 // ---- launchers (kernels.cu) ----
@@ -202,6 +225,9 @@ void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t*
 
 // Round-to-nearest-even FP32 -> BF16 bits.
 uint16_t float_to_bf16(float x);
+// Packs a row-padded column array (a multiple of PACK_ENTRIES entries) into
+// 64-bit words (layout above); false if some pack does not fit.
+bool pack_columns(const std::vector<int32_t>& col, std::vector<uint64_t>* out);
 
 void set_error(const std::string& msg);
 

@@ -97,6 +97,25 @@ void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t*
   }
 }
 
+bool pack_columns(const std::vector<int32_t>& col, std::vector<uint64_t>* out) {
+  out->clear();
+  if (col.size() % PACK_ENTRIES != 0) return false;
+  const size_t np = col.size() / PACK_ENTRIES;
+  out->resize(np);
+  for (size_t q = 0; q < np; ++q) {
+    const int32_t* c = &col[q * PACK_ENTRIES];
+    if (c[0] < 0 || c[0] > PACK_BASE_MAX) return false;
+    uint64_t w = (uint64_t)c[0];
+    for (int i = 1; i < PACK_ENTRIES; ++i) {
+      const int32_t dlt = c[i] - c[0];
+      if (dlt < -PACK_OFFSET_MAX - 1 || dlt > PACK_OFFSET_MAX) return false;
+      w |= ((uint64_t)(uint32_t)dlt & 0x3fffull) << (PACK_BASE_BITS + 14 * (i - 1));
+    }
+    (*out)[q] = w;
+  }
+  return true;
+}
+
 uint16_t float_to_bf16(float x) {
   uint32_t u;
   std::memcpy(&u, &x, 4);

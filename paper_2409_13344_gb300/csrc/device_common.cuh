@@ -66,6 +66,24 @@ __device__ __forceinline__ float4 ld_stream_bf16x4(const uint16_t* p, uint64_t p
   r.w = __uint_as_float(u.y & 0xffff0000u);
   return r;
 }
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2* p, uint64_t pol) {
+  uint2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+      : "=r"(r.x), "=r"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+// Columns of one packed 4-entry pack (layout at PACK_BASE_BITS): the base in
+// bits 0-19, then three signed 14-bit offsets from it.
+__device__ __forceinline__ int4 unpack_cols(uint2 u) {
+  const int base = (int)(u.x & 0xfffffu);
+  int4 c;
+  c.x = base;
+  c.y = base + (((int)(((u.x >> 20) | (u.y << 12)) << 18)) >> 18);
+  c.z = base + (((int)(u.y << 16)) >> 18);
+  c.w = base + (((int)(u.y << 2)) >> 18);
+  return c;
+}
 __device__ __forceinline__ int ld_stream_i1(const int32_t* p, uint64_t pol) {
   int r;
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));

@@ -151,6 +151,27 @@ __device__ __forceinline__ float4 gather4(const float* __restrict__ x, int4 c) {
   return make_float4(__ldg(x + c.x), __ldg(x + c.y), __ldg(x + c.z), __ldg(x + c.w));
 }
 
+// The column stream of a projection: 32-bit indices (a 16-byte pack of four
+// per lane and chunk) or packed indices (one 8-byte word per four entries).
+template <bool PK>
+struct ColStream {
+  using T = int4;
+  __device__ __forceinline__ static T load(const DevCSR& M, int p, uint64_t pol) {
+    return ld_stream_i4(M.col + p, pol);
+  }
+  __device__ __forceinline__ static int4 cols(T t) { return t; }
+  __device__ __forceinline__ static T zero() { return make_int4(0, 0, 0, 0); }
+};
+template <>
+struct ColStream<true> {
+  using T = uint2;
+  __device__ __forceinline__ static T load(const DevCSR& M, int p, uint64_t pol) {
+    return ld_stream_u2(M.cpk + (p >> 2), pol);  // p is a multiple of 4
+  }
+  __device__ __forceinline__ static int4 cols(T t) { return unpack_cols(t); }
+  __device__ __forceinline__ static T zero() { return make_uint2(0u, 0u); }
+};
+
 // Row starts of rows row0 .. row0 + nrows held one per lane (lane q <= nrows).
 __device__ __forceinline__ int load_raw_bound(const DevCSR& M, int row0, int nrows, int lane) {
   return lane <= nrows ? M.row_ptr[row0 + lane] : 0;
@@ -161,15 +182,16 @@ __device__ __forceinline__ int load_raw_bound(const DevCSR& M, int row0, int nro
 // flight.  set_bounds + prologue issue the loads; stream() accumulates the
 // products into per-lane row partials parked in the warp's shared-memory
 // slots; slot_reduce() then sums row q in lane q.
-template <bool BF16, bool DF, int R, int PF>
+template <bool BF16, bool DF, int R, int PF, bool PK = false>
 struct RowGroup {
+  using CS = ColStream<PK>;
 #if APPGA_SBND
   int* sb;  // the warp's row starts in shared memory (INT_MAX past the last row)
 #else
   int bnd[R + 1];
 #endif
   int nrows, P0, P1;
-  int4 c[PF];
+  typename CS::T c[PF];
   float4 v[PF];
 
   __device__ __forceinline__ void set_bounds(int braw, int nr) {
@@ -218,10 +240,10 @@ struct RowGroup {
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
       const int p = P0 + (u << 7) + lane * 4;
-      c[u] = make_int4(0, 0, 0, 0);
+      c[u] = CS::zero();
       v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (p < P1) {
-        c[u] = ld_stream_i4(M.col + p, pol);
+        c[u] = CS::load(M, p, pol);
         v[u] = ld_vals<BF16>(M, p, pol);
       }
     }
@@ -248,7 +270,7 @@ struct RowGroup {
     // x values of the next chunk are gathered one chunk ahead, so the gather
     // latency overlaps the arithmetic of the current chunk
     float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (P0 + lane * 4 < P1) xg = gather4(x, c[0]);
+    if (P0 + lane * 4 < P1) xg = gather4(x, CS::cols(c[0]));
 #endif
     for (int t0 = 0; t0 < nchunks; t0 += PF) {
 #pragma unroll
@@ -256,17 +278,17 @@ struct RowGroup {
         const int t = t0 + u;
         if (t < nchunks) {
           const int p = P0 + (t << 7) + lane * 4;
-          const int4 cc = c[u];
+          const typename CS::T cc = c[u];
           const float4 vv = v[u];
           const int pn = p + (PF << 7);
           if (pn < P1) {  // refill this slot with chunk t + PF before consuming chunk t
-            c[u] = ld_stream_i4(M.col + pn, pol);
+            c[u] = CS::load(M, pn, pol);
             v[u] = ld_vals<BF16>(M, pn, pol);
           }
 #if APPGA_GPIPE
           const float4 xx = xg;
           // chunk t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
-          if (p + 128 < P1) xg = gather4(x, c[(u + 1) % PF]);
+          if (p + 128 < P1) xg = gather4(x, CS::cols(c[(u + 1) % PF]));
 #endif
           if (p < P1) {
 #if APPGA_ROWINC
@@ -287,8 +309,9 @@ struct RowGroup {
             const float x0 = xx.x, x1 = xx.y, x2 = xx.z, x3 = xx.w;
             (void)cc;
 #else
-            const float x0 = __ldg(x + cc.x), x1 = __ldg(x + cc.y);
-            const float x2 = __ldg(x + cc.z), x3 = __ldg(x + cc.w);
+            const int4 ci = CS::cols(cc);
+            const float x0 = __ldg(x + ci.x), x1 = __ldg(x + ci.y);
+            const float x2 = __ldg(x + ci.z), x3 = __ldg(x + ci.w);
 #endif
             if (DF) {
               acc_fma(hi, lo, vv.x, x0);
@@ -472,9 +495,9 @@ __device__ __forceinline__ void load_theta(SolverState* st, const ThetaEntry& e)
 // Per-row epilogue of the forward phase (steps a1, a2, a6): stores y (and in
 // the loop y~ by linearity), the guarded weight w = 1 - g/den, and adds the
 // data term y - g ln(y + gamma) of the objective to (acc_hi, acc_lo).
-__device__ __forceinline__ void forward_row(const FwdArgs& a, const SolverState* st, int kk,
-                                            int row, float hi, float lo, int& hits, int& bad,
-                                            float& acc_hi, float& acc_lo) {
+__device__ __forceinline__ void forward_row(const FwdArgs& a, df th, int kk, int row, float hi,
+                                            float lo, int& hits, int& bad, float& acc_hi,
+                                            float& acc_lo) {
   const df y = quick_renorm(hi, lo);
   const float gam = a.gamma[row], gg = a.g[row];
   if (a.loop) {
@@ -489,7 +512,6 @@ __device__ __forceinline__ void forward_row(const FwdArgs& a, const SolverState*
       // y~ = y + theta (y - y^{k-1}): the projection of f~ by linearity (the
       // first step of a fresh run has f^{k-1} = f^k, so there y~ = y)
       const float2 yp = a.y[(kk + 1) & 1][row];
-      const df th = {st->theta_hi, st->theta_lo};
       const df dy = df_add(y, df_neg({yp.x, yp.y}));
       yt = df_add(y, df_mul(th, dy));
     }
@@ -515,7 +537,7 @@ __device__ __forceinline__ void forward_row(const FwdArgs& a, const SolverState*
 
 // Blocks [0, proj_blocks<FW>(m)) project rows; in the solver loop the blocks
 // after them run the stencil tiles.
-template <bool BF16, bool DFA>
+template <bool BF16, bool DFA, bool PK>
 __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   __shared__ union {
     struct {
@@ -543,7 +565,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   const int nrows = proj ? max(0, min(FW::R, m - row0)) : 0;
   // The warp's row bounds and first chunks of A: no kernel writes them, so
   // they are fetched before waiting for the previous kernel of the stream.
-  RowGroup<BF16, DFA, FW::R, FW::PF> rg;
+  RowGroup<BF16, DFA, FW::R, FW::PF, PK> rg;
   uint64_t pol = 0;
   if (nrows > 0) {
 #if APPGA_SBND
@@ -555,14 +577,29 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     rg.prologue(a.A, lane, pol);
   }
   pdl_wait();
-  // done == 2: the last pixel phase has run and this forward phase only
-  // evaluates the objective of the result (uniform over the grid)
-  if (a.loop && st->done == 1) return;
-  const int kk = a.loop ? st->k : 0;
+  int kk = 0;
+  df th = {0.f, 0.f};
+  if (a.loop) {
+    // this step's index and status, handed over by the previous step's
+    // finalisation; block 0 publishes them for the pixel phase.  done == 2:
+    // the last pixel phase has run and this forward phase only evaluates the
+    // objective of the result (uniform over the grid)
+    const int dn = st->done_next;
+    kk = st->k_next;
+    const ThetaEntry te = a.theta_tab[kk - st->k0];
+    th = {te.hi, te.lo};
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->done = dn;
+      st->k = kk;
+      load_theta(st, te);
+    }
+    if (dn == 1) return;
+  }
   float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
   int hits = 0, bad = 0;
   if (proj) {
-    const float* f = a.loop ? (a.ft ? a.ft : a.f[kk % 3]) : a.f[0];
+    // the tiled copy when given (the solver's projections), else the image
+    const float* f = a.ft ? a.ft : (a.loop ? a.f[kk % 3] : a.f[0]);
     float hi = 0.f, lo = 0.f;
     if (nrows > 0) {
       rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
@@ -578,17 +615,17 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
       const int brow0 = pb * FW::ROWS, bn = min(FW::ROWS, m - brow0);
       for (int q = lane; q < bn; q += 32) {
         const float2 v = ysum[q];
-        forward_row(a, st, kk, brow0 + q, v.x, v.y, hits, bad, acc_hi, acc_lo);
+        forward_row(a, th, kk, brow0 + q, v.x, v.y, hits, bad, acc_hi, acc_lo);
       }
     }
 #else
-    if (lane < nrows) forward_row(a, st, kk, row0 + lane, hi, lo, hits, bad, acc_hi, acc_lo);
+    if (lane < nrows) forward_row(a, th, kk, row0 + lane, hi, lo, hits, bad, acc_hi, acc_lo);
 #endif
   } else {
     // SHOITV gradient at f~^kk and the regulariser of Phi(f^kk)
     const int b = sb;
     const int ntx = st_tiles_x(a.n);
-    const float reg = stencil_tile(sm.st, a.f[kk % 3], a.f[(kk + 2) % 3], st->theta_hi,
+    const float reg = stencil_tile(sm.st, a.f[kk % 3], a.f[(kk + 2) % 3], th.hi,
                                    (b / ntx) * ST_R, (b % ntx) * ST_C, a.n, a.ip.lambda1,
                                    a.ip.lambda2, a.ip.eps, a.gR, a.want_data != 0);
     acc_hi = reg;
@@ -638,7 +675,78 @@ __device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, f
   return p;
 }
 
-template <bool BF16>
+// Step finalisation (step a6) after the forward phase of step kk, given
+// Phi(f^kk) if tracked: stopping test, then the index and run status of the
+// next forward phase (k_next, done_next).  One thread.
+__device__ void finish_step(const PixArgs& a, SolverState* st, int kk, double phi) {
+  if (a.ip.track) {
+    const double prev = st->phi_cur;
+    st->phi_prev = prev;
+    st->phi_cur = phi;
+    if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(phi - prev) <= a.ip.rel_tol * fabs(prev)) {
+      // f^kk is the result; the f^{kk+1} the pixel phase writes is not used
+      st->done_next = 1;
+      st->result_k = kk;
+      st->stopped_early = 1;
+      return;
+    }
+  }
+  if (kk >= st->k_last) {
+    // with the objective tracked, the forward phase of f^{kk+1} still runs
+    // and a last finalisation turns its partials into Phi(f^{kk+1})
+    st->done_next = a.ip.track ? 2 : 1;
+    st->result_k = kk + 1;
+  }
+  st->k_next = kk + 1;
+}
+
+// The step finalisation inside the pixel phase (PixArgs::fuse_fin): the
+// forward phase's block partials are summed in fixed groups of RED_GROUP by
+// the pixel phase's first blocks (each group in index order), and the last
+// of them to finish sums the group results in order and finalises the step.
+// These blocks run first, so the reduction overlaps the rest of the phase
+// instead of adding a serial tail or a launch.
+__device__ void fused_finalize(const PixArgs& a, SolverState* st, int kk) {
+  if (!a.ip.track) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) finish_step(a, st, kk, 0.0);
+    return;
+  }
+  __shared__ int s_last;
+  const int np = a.n_fwd_partial;
+  const int ng = (np + RED_GROUP - 1) / RED_GROUP;
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {  // uniform over the block
+    float h = 0.f, l = 0.f;
+    const int gsize = min(RED_GROUP, np - g * RED_GROUP);
+    for (int i = threadIdx.x; i < gsize; i += blockDim.x) {
+      const float2 v = __ldcg(a.fwd_partial + g * RED_GROUP + i);
+      acc_add(h, l, v.x, v.y);
+    }
+    const df gs = block_sum_acc(h, l);
+    if (threadIdx.x == 0) {
+      a.partial[g] = make_float2(gs.hi, gs.lo);
+      __threadfence();
+      s_last = (atomicAdd(&st->ticket_p, 1u) == (unsigned)(ng - 1));
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      h = 0.f;
+      l = 0.f;
+      for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        const float2 v = __ldcg(a.partial + i);
+        acc_add(h, l, v.x, v.y);
+      }
+      const df t = block_sum_acc(h, l);
+      if (threadIdx.x == 0) {
+        st->ticket_p = 0u;
+        finish_step(a, st, kk, (double)t.hi + (double)t.lo);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <bool BF16, bool PK>
 __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
   __shared__ int4 sbnd[PX::W][4];
@@ -649,7 +757,7 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
   const int np = max(0, min(PX::R, d - j0));
   // row bounds and first chunks of A^T before waiting (no kernel writes them)
-  RowGroup<BF16, false, PX::R, PX::PF> rg;
+  RowGroup<BF16, false, PX::R, PX::PF, PK> rg;
   uint64_t pol = 0;
   if (np > 0) {
 #if APPGA_SBND
@@ -663,6 +771,7 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   pdl_wait();
   if (st->done) return;  // uniform over the grid
   const int kk = st->k;
+  if (a.fuse_fin) fused_finalize(a, st, kk);
   int bad = 0;
   float bp = 0.f, unused = 0.f;
   if (np > 0) {
@@ -716,6 +825,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
     st->phi_prev = st->phi_cur;
     st->phi_cur = (double)phi.hi + (double)phi.lo;
     st->done = 1;
+    st->done_next = 1;
     return;
   }
   if (a.ip.track) {
@@ -726,6 +836,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
     if (a.ip.rel_tol > 0.0 && kk > st->k0 && fabs(cur - prev) <= a.ip.rel_tol * fabs(prev)) {
       // f^kk is the result; the f^{kk+1} the pixel phase wrote is not used
       st->done = 1;
+      st->done_next = 1;
       st->result_k = kk;
       st->stopped_early = 1;
       return;
@@ -746,9 +857,11 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
     // with the objective tracked, the forward phase of f^{kk+1} still runs
     // and a last finalisation turns its partials into Phi(f^{kk+1})
     st->done = a.ip.track ? 2 : 1;
+    st->done_next = st->done;
     st->result_k = kk + 1;
   }
   st->k = kk + 1;
+  st->k_next = kk + 1;
   load_theta(st, a.theta_tab[kk + 1 - st->k0]);  // kk + 1 <= k_last + 1
 }
 
@@ -848,6 +961,7 @@ __device__ __forceinline__ bool bad_counts(float gi, float ci) {
 __device__ __forceinline__ void mark_domain(SolverState* st) {
   atomicOr(&st->flags, APPGA_FLAG_DOMAIN);
   st->done = 1;
+  st->done_next = 1;
 }
 __global__ void k_check_inputs(const float* __restrict__ g, const float* __restrict__ gamma,
                                int m, const float* __restrict__ fa,
@@ -1015,32 +1129,46 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   const bool dfa = (a.loop || a.solver_acc) ? APPGA_LOOP_DF != 0 : true;
   static PerDeviceOnce carve_once;
   const cudaError_t carve = carve_once.run([] {
-    cudaError_t r = set_carveout(k_forward<true, true>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<true, false>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<false, true>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<false, false>, APPGA_CARVEOUT_FW);
+    cudaError_t r = set_carveout(k_forward<true, true, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, true, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, true>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, true>, APPGA_CARVEOUT_FW);
     return r;
   });
   if (carve != cudaSuccess) return carve;
+  // packed columns serve the solver's FP32-accumulated projections
+  if (a.A.cpk != nullptr && !dfa)
+    return a.use_bf16 ? launch_dep(k_forward<true, false, true>, grid, FW::THREADS, s, a)
+                      : launch_dep(k_forward<false, false, true>, grid, FW::THREADS, s, a);
   if (a.use_bf16)
-    return dfa ? launch_dep(k_forward<true, true>, grid, FW::THREADS, s, a)
-               : launch_dep(k_forward<true, false>, grid, FW::THREADS, s, a);
-  return dfa ? launch_dep(k_forward<false, true>, grid, FW::THREADS, s, a)
-             : launch_dep(k_forward<false, false>, grid, FW::THREADS, s, a);
+    return dfa ? launch_dep(k_forward<true, true, false>, grid, FW::THREADS, s, a)
+               : launch_dep(k_forward<true, false, false>, grid, FW::THREADS, s, a);
+  return dfa ? launch_dep(k_forward<false, true, false>, grid, FW::THREADS, s, a)
+             : launch_dep(k_forward<false, false, false>, grid, FW::THREADS, s, a);
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
   static PerDeviceOnce carve_once;
   const cudaError_t carve = carve_once.run([] {
-    cudaError_t r = set_carveout(k_pixel<true>, APPGA_CARVEOUT_PX);
-    if (r == cudaSuccess) r = set_carveout(k_pixel<false>, APPGA_CARVEOUT_PX);
+    cudaError_t r = set_carveout(k_pixel<true, false>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<false, false>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<true, true>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<false, true>, APPGA_CARVEOUT_PX);
     return r;
   });
   if (carve != cudaSuccess) return carve;
   const int grid = proj_blocks<PX>(a.At.rows);
-  const cudaError_t e = a.use_bf16 ? launch_dep(k_pixel<true>, grid, PX::THREADS, s, a)
-                                   : launch_dep(k_pixel<false>, grid, PX::THREADS, s, a);
-  if (e != cudaSuccess || a.theta_tab == nullptr) return e;
+  const bool pk = a.At.cpk != nullptr;
+  cudaError_t e;
+  if (a.use_bf16)
+    e = pk ? launch_dep(k_pixel<true, true>, grid, PX::THREADS, s, a)
+           : launch_dep(k_pixel<true, false>, grid, PX::THREADS, s, a);
+  else
+    e = pk ? launch_dep(k_pixel<false, true>, grid, PX::THREADS, s, a)
+           : launch_dep(k_pixel<false, false>, grid, PX::THREADS, s, a);
+  if (e != cudaSuccess || a.theta_tab == nullptr || a.fuse_fin) return e;
   return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
 }
 

@@ -315,7 +315,10 @@ def test_batched_slot_width_guard_at_the_limit(A, ctx):
     try:
         g1 = torch.tensor([[2.0e4]], dtype=torch.float32, device=DEV)
         gam1 = torch.tensor([[50.0]], dtype=torch.float32, device=DEV)
-        p = A.default_params(max_iters=2, omega=1.0, beta=0.5)
+        # a small step: one ray against a 13M-pixel initial disk makes the
+        # EM step scale the ray's pixels by ~180 at beta = 1, which would
+        # amplify the FP32 summation-order difference between the two paths
+        p = A.default_params(max_iters=2, omega=1.0, beta=1e-3)
         # a full-size output even for the rejected call (8.6 GB)
         fbuf = torch.empty((128, d), dtype=torch.float32, device=DEV)
         with pytest.raises(A.AppgaError) as ei:
@@ -334,6 +337,7 @@ def test_batched_slot_width_guard_at_the_limit(A, ctx):
             got = f[i].cpu().numpy()
             assert np.all(np.isfinite(got))
             assert rel(got, ref) <= 2e-6
+            assert rel(got.reshape(n, n)[2050], ref.reshape(n, n)[2050]) <= 1e-5
         # the ray's row moved, the pixels far from it and from the disk edge did not
         ray = ref.reshape(n, n)[2050]
         far = ref.reshape(n, n)[1000, 2040:2060]
