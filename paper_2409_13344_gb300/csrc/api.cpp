@@ -99,20 +99,14 @@ appga_status upload_csr(const appga::HostCSR& h, bool bf16, DevCSR* out, int64_t
   c.cols = h.cols;
   c.nnz_padded = (int64_t)h.col.size();
   cudaError_t e;
-  // the streamed arrays carry STREAM_SLACK zero entries past the end: bulk
-  // copies round a row group's range out to 8-entry boundaries
-  const size_t ns = h.col.size() + appga::STREAM_SLACK;
   if ((e = dalloc(&c.row_ptr, h.row_ptr.size(), bytes)) != cudaSuccess ||
-      (e = dalloc(&c.col, ns, bytes)) != cudaSuccess ||
-      (e = dalloc(&c.val, ns, bytes)) != cudaSuccess ||
-      (e = cudaMemset(c.col, 0, ns * 4)) != cudaSuccess ||
-      (e = cudaMemset(c.val, 0, ns * 4)) != cudaSuccess) {
+      (e = dalloc(&c.col, h.col.size(), bytes)) != cudaSuccess ||
+      (e = dalloc(&c.val, h.val.size(), bytes)) != cudaSuccess) {
     free_csr(c);
     return cuda_fail(e, "cudaMalloc(matrix)");
   }
   if (bf16) {
-    if ((e = dalloc(&c.val_bf16, ns, bytes)) != cudaSuccess ||
-        (e = cudaMemset(c.val_bf16, 0, ns * 2)) != cudaSuccess) {
+    if ((e = dalloc(&c.val_bf16, h.val.size(), bytes)) != cudaSuccess) {
       free_csr(c);
       return cuda_fail(e, "cudaMalloc(matrix bf16)");
     }
@@ -786,9 +780,7 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
     M->A_tiled = M->A;
     M->A_tiled.col = nullptr;
     M->A_tiled.cpk = nullptr;
-    cudaError_t e = dalloc(&M->A_tiled.col, ct.size() + appga::STREAM_SLACK, &M->bytes);
-    if (e == cudaSuccess)
-      e = cudaMemset(M->A_tiled.col, 0, (ct.size() + appga::STREAM_SLACK) * 4);
+    cudaError_t e = dalloc(&M->A_tiled.col, ct.size(), &M->bytes);
     if (e == cudaSuccess && !ct.empty())
       e = cudaMemcpy(M->A_tiled.col, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice);
     // packed columns of the solver loop's two projections (both or neither)
@@ -796,9 +788,6 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
     if (APPGA_PACK && e == cudaSuccess && !ct.empty() && !pt.col.empty() &&
         appga::pack_columns(ct, &pk_a) &&
         appga::pack_columns(pt.col, &pk_t)) {
-      // STREAM_SLACK entries of zero words past the end, as for the values
-      pk_a.resize(pk_a.size() + appga::STREAM_SLACK / appga::PACK_ENTRIES, 0ull);
-      pk_t.resize(pk_t.size() + appga::STREAM_SLACK / appga::PACK_ENTRIES, 0ull);
       e = dalloc(&M->A_tiled.cpk, pk_a.size(), &M->bytes);
       if (e == cudaSuccess)
         e = cudaMemcpy(M->A_tiled.cpk, pk_a.data(), pk_a.size() * 8, cudaMemcpyHostToDevice);

@@ -25,8 +25,6 @@ constexpr int ROW_PAD = 4;
 // entry instead of 4).  A matrix whose columns do not fit (a column above
 // 2^20 - 1 or an offset outside [-8192, 8191]) keeps 32-bit indices only.
 constexpr int PACK_ENTRIES = ROW_PAD;
-// zero entries past the end of every streamed matrix array
-constexpr int STREAM_SLACK = 8;
 constexpr int PACK_BASE_BITS = 20;
 constexpr int32_t PACK_BASE_MAX = (1 << PACK_BASE_BITS) - 1;
 constexpr int32_t PACK_OFFSET_MAX = 8191;

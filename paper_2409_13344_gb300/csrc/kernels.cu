@@ -42,7 +42,6 @@
 #include <math.h>
 
 #include <cmath>
-#include <type_traits>
 
 #include "appga_internal.h"
 #include "device_common.cuh"
@@ -120,11 +119,6 @@ using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
 // row starts of a warp's group kept in shared memory instead of registers
 #ifndef APPGA_SBND
 #define APPGA_SBND 1
-#endif
-// the solver loop's packed projections stream the matrix through shared
-// memory with bulk asynchronous copies (1) or through registers (0)
-#ifndef APPGA_BULK
-#define APPGA_BULK 0
 #endif
 // accumulation of y = A f in the solver loop: 0 = FP32 (as the back-projection),
 // 1 = double-float per product
@@ -343,166 +337,6 @@ struct RowGroup {
 
 };
 
-// ----------------------------------------------- bulk-streamed row groups
-// The solver loop's projections with packed columns can stream a warp's row
-// group through shared memory instead of registers: the warp's lane 0 issues
-// one-dimensional bulk asynchronous copies of the group's packed columns and
-// values, BULK_E entries per stage, into a ring of BULK_NS stages in the
-// block's dynamic shared memory, each stage completed on its own mbarrier.
-// The copies of the first stages are issued before the kernel waits for its
-// predecessor (the matrix is never written), so the whole group is usually
-// in flight from the start; no register holds in-flight matrix data.  Each
-// stage is consumed in two passes: every lane first issues the gathers of
-// all its packs in the stage (up to 4 x BULK_E/128 loads in flight per lane)
-// and then accumulates.  Copies start on an 8-entry boundary at or before
-// the group's first entry (16-byte alignment of the packed columns), so the
-// arrays carry 8 entries of slack at the end; entries outside the group are
-// masked.  Waits are bounded (one second); a wait that runs out marks the
-// warp dead (APPGA_FLAG_TIMEOUT), skips the rest of its work and waits
-// boundedly for its copies in flight before the kernel ends.
-#ifndef APPGA_BULK_E
-#define APPGA_BULK_E 512
-#endif
-#ifndef APPGA_BULK_NS
-#define APPGA_BULK_NS 4
-#endif
-constexpr int BULK_E = APPGA_BULK_E;    // entries per stage (a multiple of 128)
-constexpr int BULK_NS = APPGA_BULK_NS;  // stages per warp
-static_assert(BULK_E % 128 == 0 && BULK_E >= 128, "a stage holds whole 128-entry chunks");
-constexpr int BULK_COLB = BULK_E * 2;   // packed columns of a stage (bytes)
-constexpr int BULK_VALB = BULK_E * 4;   // values of a stage (bytes, FP32; BF16 uses half)
-constexpr int BULK_STAGE = BULK_COLB + BULK_VALB;
-constexpr uint64_t BULK_WAIT_NS = 1000000000ull;  // bounded waits: one second
-__host__ __device__ constexpr int bulk_smem_bytes(int warps) {
-  return warps * BULK_NS * (BULK_STAGE + 8);
-}
-
-template <bool BF16, int R>
-struct BulkGroup {
-  int* sb;  // the warp's row starts in shared memory (INT_MAX past the last row)
-  int nrows, P0, P1, S0, S1, nst;
-  int issued;     // stages whose copies have been issued
-  uint32_t ring;  // this warp's stages (shared address)
-  uint32_t bars;  // this warp's mbarriers
-  bool dead;
-
-  __device__ __forceinline__ void set_bounds(int braw, int nr) {
-    nrows = nr;
-    const int lane = threadIdx.x & 31;
-    if (lane < 4 * ((R + 3) / 4)) sb[lane] = lane < nr ? braw : 0x7fffffff;
-    __syncwarp();
-    P0 = __shfl_sync(0xffffffffu, braw, 0);
-    P1 = __shfl_sync(0xffffffffu, braw, nr);
-    S0 = P0 & ~7;
-    S1 = (P1 + 7) & ~7;
-    nst = P1 > P0 ? (S1 - S0 + BULK_E - 1) / BULK_E : 0;
-    dead = false;
-  }
-  __device__ __forceinline__ int row_start(int q) const { return sb[q]; }
-
-  // lane 0: stage s into ring buffer s % BULK_NS
-  __device__ __forceinline__ void issue(const DevCSR& M, int s, uint64_t pol) const {
-    const int e0 = S0 + s * BULK_E;
-    const int ne = min(BULK_E, S1 - e0);  // a multiple of 8
-    const uint32_t buf = ring + (uint32_t)((s % BULK_NS) * BULK_STAGE);
-    const uint32_t bar = bars + (uint32_t)((s % BULK_NS) * 8);
-    const uint32_t cb = (uint32_t)ne * 2u;
-    const uint32_t vb = (uint32_t)ne * (BF16 ? 2u : 4u);
-    mbar_arrive_expect_tx(bar, cb + vb);
-    bulk_copy_g2s(buf, M.cpk + (e0 >> 2), cb, bar, pol);
-    if constexpr (BF16) {
-      bulk_copy_g2s(buf + BULK_COLB, M.val_bf16 + e0, vb, bar, pol);
-    } else {
-      bulk_copy_g2s(buf + BULK_COLB, M.val + e0, vb, bar, pol);
-    }
-  }
-
-  // before the kernel waits for its predecessor: barriers and first stages
-  __device__ __forceinline__ void prologue(const DevCSR& M, int lane, uint64_t pol) {
-    issued = min(nst, BULK_NS);
-    if (lane == 0) {
-      for (int b = 0; b < BULK_NS; ++b) mbar_init(bars + 8u * b, 1u);
-      mbar_init_fence();
-      for (int t = 0; t < issued; ++t) issue(M, t, pol);
-    }
-    __syncwarp();
-  }
-
-  __device__ __forceinline__ void stream(const DevCSR& M, const float* __restrict__ x, int lane,
-                                         uint64_t pol, float* slot_hi) {
-    constexpr int CH = BULK_E / 128;  // chunks (packs per lane) per stage
-    float hi = 0.f;
-    int cur = -1, q = 0, t = 0;
-    for (; t < nst; ++t) {
-      const int buf = t % BULK_NS;
-      const uint32_t sbuf = ring + (uint32_t)(buf * BULK_STAGE);
-      if (!dead && !mbar_wait_bounded(bars + 8u * buf, (uint32_t)((t / BULK_NS) & 1), BULK_WAIT_NS))
-        dead = true;
-      dead = __any_sync(0xffffffffu, dead);
-      if (dead) break;
-      const int e0 = S0 + t * BULK_E;
-      // pass 1: the gathers of every pack of this lane in the stage
-      float4 xg[CH];
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int p = e0 + (c << 7) + lane * 4;
-        xg[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p >= P0 && p < P1) {
-          const int4 ci = unpack_cols(lds_u2(sbuf + (uint32_t)((p - e0) * 2)));
-          xg[c] = gather4(x, ci);
-        }
-      }
-      // pass 2: accumulate into the lane's current row, parking finished rows
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int p = e0 + (c << 7) + lane * 4;
-        if (p >= P0 && p < P1) {
-          float4 vv;
-          if constexpr (BF16) {
-            const uint2 u = lds_u2(sbuf + BULK_COLB + (uint32_t)((p - e0) * 2));
-            vv = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                             __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-          } else {
-            vv = lds_f4(sbuf + BULK_COLB + (uint32_t)((p - e0) * 4));
-          }
-          while (q + 1 < nrows && row_start(q + 1) <= p) ++q;
-          if (q != cur) {
-            if (cur >= 0) slot_hi[cur * SLOT_W + lane] = hi;
-            cur = q;
-            hi = 0.f;
-          }
-          hi = fmaf(vv.x, xg[c].x, hi);
-          hi = fmaf(vv.y, xg[c].y, hi);
-          hi = fmaf(vv.z, xg[c].z, hi);
-          hi = fmaf(vv.w, xg[c].w, hi);
-        }
-      }
-      __syncwarp();
-      if (t + BULK_NS < nst) {
-        if (lane == 0) {
-          fence_proxy_async_smem();
-          issue(M, t + BULK_NS, pol);
-        }
-        issued = t + BULK_NS + 1;
-      }
-    }
-    if (cur >= 0) slot_hi[cur * SLOT_W + lane] = hi;
-    __syncwarp();
-    if (dead) drain(t);
-  }
-
-  // after a wait ran out at stage t0: bounded waits for the copies this warp
-  // issued and has not consumed
-  __device__ __forceinline__ void drain(int t0) const {
-    const uint64_t start = global_ns();
-    for (int t = t0; t < issued; ++t) {
-      const int buf = t % BULK_NS;
-      while (!mbar_try_wait(bars + 8u * buf, (uint32_t)((t / BULK_NS) & 1)))
-        if (global_ns() - start > BULK_WAIT_NS) return;
-    }
-  }
-};
-
 // Sum of row `lane` of a streamed group in lanes 0..nrows-1 from the warp's
 // slots (an accumulator pair if DF).
 template <bool DF>
@@ -713,9 +547,6 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     } slot;
     StencilSmem st;
   } sm;
-  constexpr bool BULK = PK && !DFA && APPGA_BULK;
-  using Grp = std::conditional_t<BULK, BulkGroup<BF16, FW::R>,
-                                 RowGroup<BF16, DFA, FW::R, FW::PF, PK>>;
   pdl_trigger();
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -734,21 +565,14 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   const int nrows = proj ? max(0, min(FW::R, m - row0)) : 0;
   // The warp's row bounds and first chunks of A: no kernel writes them, so
   // they are fetched before waiting for the previous kernel of the stream.
-  Grp rg;
+  RowGroup<BF16, DFA, FW::R, FW::PF, PK> rg;
   uint64_t pol = 0;
   if (nrows > 0) {
 #if APPGA_SBND
     rg.sb = reinterpret_cast<int*>(sm.slot.bnd[warp]);
-#else
-    static_assert(!BULK, "bulk streaming keeps row starts in shared memory");
 #endif
-    if constexpr (BULK) {
-      extern __shared__ __align__(128) unsigned char dyn_fw[];
-      rg.ring = smem_u32(dyn_fw) + (uint32_t)(warp * BULK_NS * BULK_STAGE);
-      rg.bars = smem_u32(dyn_fw) + (uint32_t)(FW::W * BULK_NS * BULK_STAGE + warp * BULK_NS * 8);
-    }
     rg.set_bounds(load_raw_bound(a.A, row0, nrows, lane), nrows);
-    RowGroup<BF16, DFA, FW::R, FW::PF, PK>::clear_slots(lane, sm.slot.hi[warp], sm.slot.lo[warp]);
+    decltype(rg)::clear_slots(lane, sm.slot.hi[warp], sm.slot.lo[warp]);
     pol = evict_first_policy();
     rg.prologue(a.A, lane, pol);
   }
@@ -769,12 +593,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
       st->k = kk;
       load_theta(st, te);
     }
-    if (dn == 1) {
-      if constexpr (BULK) {
-        if (nrows > 0) rg.drain(0);  // no copy may outlive the block
-      }
-      return;
-    }
+    if (dn == 1) return;
   }
   float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
   int hits = 0, bad = 0;
@@ -783,12 +602,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     const float* f = a.ft ? a.ft : (a.loop ? a.f[kk % 3] : a.f[0]);
     float hi = 0.f, lo = 0.f;
     if (nrows > 0) {
-      if constexpr (BULK) {
-        rg.stream(a.A, f, lane, pol, sm.slot.hi[warp]);
-        if (rg.dead && lane == 0) atomicOr(&st->flags, APPGA_FLAG_TIMEOUT);
-      } else {
-        rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
-      }
+      rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
       slot_reduce<DFA>(lane, nrows, sm.slot.hi[warp], sm.slot.lo[warp], hi, lo);
     }
 #if APPGA_FEPI
@@ -936,9 +750,6 @@ template <bool BF16, bool PK>
 __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
   __shared__ int4 sbnd[PX::W][4];
-  constexpr bool BULK = PK && APPGA_BULK;
-  using Grp = std::conditional_t<BULK, BulkGroup<BF16, PX::R>,
-                                 RowGroup<BF16, false, PX::R, PX::PF, PK>>;
   pdl_trigger();
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -946,42 +757,25 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
   const int np = max(0, min(PX::R, d - j0));
   // row bounds and first chunks of A^T before waiting (no kernel writes them)
-  Grp rg;
+  RowGroup<BF16, false, PX::R, PX::PF, PK> rg;
   uint64_t pol = 0;
   if (np > 0) {
 #if APPGA_SBND
     rg.sb = reinterpret_cast<int*>(sbnd[warp]);
-#else
-    static_assert(!BULK, "bulk streaming keeps row starts in shared memory");
 #endif
-    if constexpr (BULK) {
-      extern __shared__ __align__(128) unsigned char dyn_px[];
-      rg.ring = smem_u32(dyn_px) + (uint32_t)(warp * BULK_NS * BULK_STAGE);
-      rg.bars = smem_u32(dyn_px) + (uint32_t)(PX::W * BULK_NS * BULK_STAGE + warp * BULK_NS * 8);
-    }
     rg.set_bounds(load_raw_bound(a.At, j0, np, lane), np);
-    RowGroup<BF16, false, PX::R, PX::PF, PK>::clear_slots(lane, slot[warp], nullptr);
+    decltype(rg)::clear_slots(lane, slot[warp], nullptr);
     pol = evict_first_policy();
     rg.prologue(a.At, lane, pol);
   }
   pdl_wait();
-  if (st->done) {  // uniform over the grid
-    if constexpr (BULK) {
-      if (np > 0) rg.drain(0);  // no copy may outlive the block
-    }
-    return;
-  }
+  if (st->done) return;  // uniform over the grid
   const int kk = st->k;
   if (a.fuse_fin) fused_finalize(a, st, kk);
   int bad = 0;
   float bp = 0.f, unused = 0.f;
   if (np > 0) {
-    if constexpr (BULK) {
-      rg.stream(a.At, a.w, lane, pol, slot[warp]);
-      if (rg.dead && lane == 0) atomicOr(&st->flags, APPGA_FLAG_TIMEOUT);
-    } else {
-      rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
-    }
+    rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
     slot_reduce<false>(lane, np, slot[warp], nullptr, bp, unused);
   }
   float pj = 0.f;
@@ -1294,13 +1088,12 @@ cudaError_t set_carveout(K kern, int percent) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, percent);
 }
 template <class... P, class... Args>
-cudaError_t launch_dep_smem(void (*kern)(P...), int grid, int block, size_t smem,
-                            cudaStream_t s, Args... args) {
+cudaError_t launch_dep(void (*kern)(P...), int grid, int block, cudaStream_t s, Args... args) {
 #if APPGA_PDL
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr{};
   attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1309,21 +1102,10 @@ cudaError_t launch_dep_smem(void (*kern)(P...), int grid, int block, size_t smem
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
 #else
-  kern<<<grid, block, smem, s>>>(args...);
+  kern<<<grid, block, 0, s>>>(args...);
   return cudaGetLastError();
 #endif
 }
-template <class... P, class... Args>
-cudaError_t launch_dep(void (*kern)(P...), int grid, int block, cudaStream_t s, Args... args) {
-  return launch_dep_smem(kern, grid, block, 0, s, args...);
-}
-template <class K>
-cudaError_t allow_dyn_smem(K kern, int bytes) {
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-// dynamic shared memory of the packed loop projections (their bulk stages)
-constexpr int FW_DYN = APPGA_BULK ? bulk_smem_bytes(FW::W) : 0;
-constexpr int PX_DYN = APPGA_BULK ? bulk_smem_bytes(PX::W) : 0;
 }  // namespace
 
 int stencil_tiles(int n) { return st_tiles(n); }
@@ -1353,16 +1135,13 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
     if (r == cudaSuccess) r = set_carveout(k_forward<false, false, false>, APPGA_CARVEOUT_FW);
     if (r == cudaSuccess) r = set_carveout(k_forward<true, false, true>, APPGA_CARVEOUT_FW);
     if (r == cudaSuccess) r = set_carveout(k_forward<false, false, true>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess && FW_DYN > 0) r = allow_dyn_smem(k_forward<true, false, true>, FW_DYN);
-    if (r == cudaSuccess && FW_DYN > 0) r = allow_dyn_smem(k_forward<false, false, true>, FW_DYN);
     return r;
   });
   if (carve != cudaSuccess) return carve;
   // packed columns serve the solver's FP32-accumulated projections
   if (a.A.cpk != nullptr && !dfa)
-    return a.use_bf16
-               ? launch_dep_smem(k_forward<true, false, true>, grid, FW::THREADS, FW_DYN, s, a)
-               : launch_dep_smem(k_forward<false, false, true>, grid, FW::THREADS, FW_DYN, s, a);
+    return a.use_bf16 ? launch_dep(k_forward<true, false, true>, grid, FW::THREADS, s, a)
+                      : launch_dep(k_forward<false, false, true>, grid, FW::THREADS, s, a);
   if (a.use_bf16)
     return dfa ? launch_dep(k_forward<true, true, false>, grid, FW::THREADS, s, a)
                : launch_dep(k_forward<true, false, false>, grid, FW::THREADS, s, a);
@@ -1377,8 +1156,6 @@ cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
     if (r == cudaSuccess) r = set_carveout(k_pixel<false, false>, APPGA_CARVEOUT_PX);
     if (r == cudaSuccess) r = set_carveout(k_pixel<true, true>, APPGA_CARVEOUT_PX);
     if (r == cudaSuccess) r = set_carveout(k_pixel<false, true>, APPGA_CARVEOUT_PX);
-    if (r == cudaSuccess && PX_DYN > 0) r = allow_dyn_smem(k_pixel<true, true>, PX_DYN);
-    if (r == cudaSuccess && PX_DYN > 0) r = allow_dyn_smem(k_pixel<false, true>, PX_DYN);
     return r;
   });
   if (carve != cudaSuccess) return carve;
@@ -1386,10 +1163,10 @@ cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
   const bool pk = a.At.cpk != nullptr;
   cudaError_t e;
   if (a.use_bf16)
-    e = pk ? launch_dep_smem(k_pixel<true, true>, grid, PX::THREADS, PX_DYN, s, a)
+    e = pk ? launch_dep(k_pixel<true, true>, grid, PX::THREADS, s, a)
            : launch_dep(k_pixel<true, false>, grid, PX::THREADS, s, a);
   else
-    e = pk ? launch_dep_smem(k_pixel<false, true>, grid, PX::THREADS, PX_DYN, s, a)
+    e = pk ? launch_dep(k_pixel<false, true>, grid, PX::THREADS, s, a)
            : launch_dep(k_pixel<false, false>, grid, PX::THREADS, s, a);
   if (e != cudaSuccess || a.theta_tab == nullptr || a.fuse_fin) return e;
   return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
