@@ -150,7 +150,6 @@ struct PixArgs {
   // 1: the pixel phase's first blocks finalise the step (Phi(f^k) from the
   // forward phase's partials, stopping test, next index); 0: k_finalize does
   int32_t fuse_fin;
-  int32_t rpw;  // pixel rows per warp (set by launch_pixel)
 };
 
 // ---- launchers (kernels.cu) ----

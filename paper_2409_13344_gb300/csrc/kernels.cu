@@ -42,9 +42,6 @@
 #include <math.h>
 
 #include <cmath>
-#include <map>
-#include <mutex>
-#include <utility>
 
 #include "appga_internal.h"
 #include "device_common.cuh"
@@ -78,19 +75,8 @@ struct Shape {
 #ifndef APPGA_PX_W
 #define APPGA_PX_W 4
 #endif
-// The pixel phase runs as one wave: rows per warp are chosen at launch so
-// that the grid fits on the device at the kernel's occupancy (1), up to
-// APPGA_PX_RPW; 0 keeps APPGA_PX_RPW rows per warp and as many waves as that
-// takes.
-#ifndef APPGA_PX_ONEWAVE
-#define APPGA_PX_ONEWAVE 1
-#endif
 #ifndef APPGA_PX_RPW
-#if APPGA_PX_ONEWAVE
-#define APPGA_PX_RPW 16
-#else
 #define APPGA_PX_RPW 8
-#endif
 #endif
 #ifndef APPGA_PX_PF
 #define APPGA_PX_PF 3
@@ -768,8 +754,8 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = a.At.rows;
-  const int j0 = (blockIdx.x * PX::W + warp) * a.rpw;
-  const int np = max(0, min(a.rpw, d - j0));
+  const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
+  const int np = max(0, min(PX::R, d - j0));
   // row bounds and first chunks of A^T before waiting (no kernel writes them)
   RowGroup<BF16, false, PX::R, PX::PF, PK> rg;
   uint64_t pol = 0;
@@ -1096,24 +1082,6 @@ cudaError_t launch_to_tiled(const float* f, float* ft, int n, cudaStream_t s) {
 #define APPGA_CARVEOUT_PX -1
 #endif
 namespace {
-// Resident blocks per SM of `kern` at `threads` threads per block and no
-// dynamic shared memory (looked up once per device and kernel).
-int resident_blocks(void (*kern)(PixArgs), int threads) {
-  static std::mutex mu;
-  static std::map<std::pair<int, const void*>, int> cache;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-  std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(dev, (const void*)kern);
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0) != cudaSuccess ||
-      nb < 1)
-    nb = 1;
-  cache[key] = nb;
-  return nb;
-}
 template <class K>
 cudaError_t set_carveout(K kern, int percent) {
   if (percent < 0) return cudaSuccess;
@@ -1191,22 +1159,15 @@ cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
     return r;
   });
   if (carve != cudaSuccess) return carve;
+  const int grid = proj_blocks<PX>(a.At.rows);
   const bool pk = a.At.cpk != nullptr;
-  void (*kern)(PixArgs) = a.use_bf16 ? (pk ? k_pixel<true, true> : k_pixel<true, false>)
-                                     : (pk ? k_pixel<false, true> : k_pixel<false, false>);
-  PixArgs b = a;
-  b.rpw = PX::R;
-#if APPGA_PX_ONEWAVE
-  {
-    // the fewest rows per warp (at most PX::R) whose grid fits in one wave
-    const int resident = resident_blocks(kern, PX::THREADS) * current_sm_count();
-    const long long warps = (long long)resident * PX::W;
-    const int want = (int)((a.At.rows + warps - 1) / (warps > 0 ? warps : 1));
-    b.rpw = want < 1 ? 1 : (want > PX::R ? PX::R : want);
-  }
-#endif
-  const int grid = (a.At.rows + b.rpw * PX::W - 1) / (b.rpw * PX::W);
-  cudaError_t e = launch_dep(kern, grid < 1 ? 1 : grid, PX::THREADS, s, b);
+  cudaError_t e;
+  if (a.use_bf16)
+    e = pk ? launch_dep(k_pixel<true, true>, grid, PX::THREADS, s, a)
+           : launch_dep(k_pixel<true, false>, grid, PX::THREADS, s, a);
+  else
+    e = pk ? launch_dep(k_pixel<false, true>, grid, PX::THREADS, s, a)
+           : launch_dep(k_pixel<false, false>, grid, PX::THREADS, s, a);
   if (e != cudaSuccess || a.theta_tab == nullptr || a.fuse_fin) return e;
   return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
 }
