@@ -264,7 +264,10 @@ struct RowGroup {
     float hi = 0.f, lo = 0.f;
     int cur = -1;
 #if APPGA_ROWINC
-    int q = 0;  // row of this lane's current entry (entries only move forward)
+    // row of this lane's current entry (entries only move forward) and the
+    // first entry of the row after it (INT_MAX past the last row)
+    int q = 0;
+    int nxt = nrows > 1 ? row_start(1) : 0x7fffffff;
 #endif
 #if APPGA_GPIPE
     // x values of the next chunk are gathered one chunk ahead, so the gather
@@ -292,7 +295,10 @@ struct RowGroup {
 #endif
           if (p < P1) {
 #if APPGA_ROWINC
-            while (q + 1 < nrows && row_start(q + 1) <= p) ++q;
+            while (p >= nxt) {
+              ++q;
+              nxt = q + 1 < nrows ? row_start(q + 1) : 0x7fffffff;
+            }
 #else
             const int q = row(p);
 #endif

@@ -60,9 +60,10 @@ def test_noalloc_objective_matches_allocating_call_twice(lib, ctx, name, counts)
 
 
 def test_noalloc_rejects_matrices_beyond_the_fixed_scratch(lib, ctx):
-    # a 1024 x 1024 image (a few rays suffice) needs more scratch than the
-    # fixed array holds
-    n, m = 1024, 4
+    # a 2048 x 2048 image (a few rays suffice) needs more scratch than the
+    # fixed array holds: its stencil blocks alone leave more block partials
+    # than fit
+    n, m = 2048, 4
     row_ptr = np.array([0, 2, 3, 3, 4], np.int32)
     col = np.array([0, 5, 7, n * n - 1], np.int32)
     val = np.ones(4, np.float32)
