@@ -61,8 +61,43 @@ void free_csr(DevCSR& c) {
   cudaFree(c.col);
   cudaFree(c.val);
   cudaFree(c.val_bf16);
-  cudaFree(c.cpk);
   c = DevCSR();
+}
+
+void free_sell(DevSell& c) {
+  cudaFree(c.off);
+  cudaFree(c.cols);
+  cudaFree(c.vals);
+  cudaFree(c.vals_bf16);
+  c = DevSell();
+}
+
+appga_status upload_sell(const appga::HostSell& h, bool bf16, DevSell* out, int64_t* bytes) {
+  DevSell c;
+  c.rows = h.rows;
+  c.slices = h.slices;
+  const size_t np = h.cols.size();
+  cudaError_t e = dalloc(&c.off, h.off.size(), bytes);
+  if (e == cudaSuccess) e = dalloc(&c.cols, np, bytes);
+  if (e == cudaSuccess) e = dalloc(&c.vals, np, bytes);
+  if (e == cudaSuccess && bf16) e = dalloc(&c.vals_bf16, np, bytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c.off, h.off.data(), h.off.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && np)
+    e = cudaMemcpy(c.cols, h.cols.data(), np * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && np)
+    e = cudaMemcpy(c.vals, h.vals.data(), np * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bf16 && np) {
+    std::vector<uint16_t> b(h.vals.size());
+    for (size_t i = 0; i < b.size(); ++i) b[i] = appga::float_to_bf16(h.vals[i]);
+    e = cudaMemcpy(c.vals_bf16, b.data(), np * 8, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    free_sell(c);
+    return cuda_fail(e, "sliced matrix upload");
+  }
+  *out = c;
+  return APPGA_OK;
 }
 
 void free_workspace(Workspace& ws) {
@@ -233,8 +268,11 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
   const bool bf16 = bf16_requested(M, p);
 
+  const bool tiled = appga::tiled_gather_enabled();
   if (!fresh) {
-    // y^{k0-1} = A f^{k0-1}
+    // y^{k0-1} = A f^{k0-1}, with the loop's projection (the same matrix
+    // layout, gather order and accumulation), so a resumed run continues an
+    // uninterrupted one bit for bit
     appga::FwdArgs init = fwd_args(M, bf16);
     init.f[0] = ws.f[(k0 + 2) % 3];
     init.y[0] = ws.y[(k0 + 1) & 1];
@@ -247,6 +285,12 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
     init.loop = 0;
     init.solver_acc = 1;
     init.n = M->n;
+    if (tiled) {
+      init.A.col = M->A_tiled.col;
+      init.S = M->sell_a;
+      init.ft = ws.ft;
+      CK(appga::launch_to_tiled(ws.f[(k0 + 2) % 3], ws.ft, M->n, s));
+    }
     CK(appga::launch_forward(init, s));
   }
 
@@ -279,19 +323,20 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.partial = ws.partial_p;
   pa.gtick = ws.gtick;
   pa.fwd_partial = ws.partial_r;
-  pa.n_fwd_partial = appga::forward_blocks(M->m, M->n);
   pa.theta_tab = ws.theta_tab;
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
   pa.fuse_fin = APPGA_FUSE_FIN;
-  if (appga::tiled_gather_enabled()) {
+  if (tiled) {
     // the loop's projector gathers f^k from its 8 x 8-tiled copy
     fa.A.col = M->A_tiled.col;
-    fa.A.cpk = M->A_tiled.cpk;
+    fa.S = M->sell_a;
     fa.ft = ws.ft;
     pa.ft = ws.ft;
+    pa.S = M->sell_t;
     if (!tiled_ready) CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
   }
+  pa.n_fwd_partial = appga::forward_blocks(M->m, M->n, fa.S.cols != nullptr);
 
   // w^{k0}, y^{k0}, B^T grad phi~(B f~^{k0}) and Phi(f^{k0})
   appga::FwdArgs first = fa;
@@ -779,23 +824,20 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
       ct[q] = appga::tiled_index(pa.col[q] / n_side, pa.col[q] % n_side, n_side);
     M->A_tiled = M->A;
     M->A_tiled.col = nullptr;
-    M->A_tiled.cpk = nullptr;
     cudaError_t e = dalloc(&M->A_tiled.col, ct.size(), &M->bytes);
     if (e == cudaSuccess && !ct.empty())
       e = cudaMemcpy(M->A_tiled.col, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice);
-    // packed columns of the solver loop's two projections (both or neither)
-    std::vector<uint64_t> pk_a, pk_t;
-    if (APPGA_PACK && e == cudaSuccess && !ct.empty() && !pt.col.empty() &&
-        appga::pack_columns(ct, &pk_a) &&
-        appga::pack_columns(pt.col, &pk_t)) {
-      e = dalloc(&M->A_tiled.cpk, pk_a.size(), &M->bytes);
-      if (e == cudaSuccess)
-        e = cudaMemcpy(M->A_tiled.cpk, pk_a.data(), pk_a.size() * 8, cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = dalloc(&M->At.cpk, pk_t.size(), &M->bytes);
-      if (e == cudaSuccess)
-        e = cudaMemcpy(M->At.cpk, pk_t.data(), pk_t.size() * 8, cudaMemcpyHostToDevice);
+    // the solver loop's two projections in the sliced layout (both or neither)
+    if (APPGA_PACK && e == cudaSuccess && !ct.empty() && !pt.col.empty()) {
+      appga::HostSell ha, ht;
+      if (appga::build_sell(m, pa.row_ptr, ct, pa.val, &ha) &&
+          appga::build_sell(d, pt.row_ptr, pt.col, pt.val, &ht)) {
+        appga_status r1 = upload_sell(ha, want_bf16, &M->sell_a, &M->bytes);
+        if (r1 == APPGA_OK) r1 = upload_sell(ht, want_bf16, &M->sell_t, &M->bytes);
+        if (r1 != APPGA_OK) e = cudaErrorMemoryAllocation;
+      }
     }
-    if (e != cudaSuccess) rc = cuda_fail(e, "tiled and packed column indices");
+    if (e != cudaSuccess) rc = cuda_fail(e, "tiled column indices and sliced layout");
   }
   if (rc == APPGA_OK) {
     cudaError_t e = dalloc(&M->inv_lambda, (size_t)d, &M->bytes);
@@ -817,8 +859,9 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
 appga_status appga_matrix_destroy(appga_matrix* M) {
   if (!M) return APPGA_OK;
   if (M->ctx) cudaSetDevice(M->ctx->device);
-  cudaFree(M->A_tiled.col);  // its other arrays (but the packed columns) belong to A
-  cudaFree(M->A_tiled.cpk);
+  cudaFree(M->A_tiled.col);  // its other arrays belong to A
+  free_sell(M->sell_a);
+  free_sell(M->sell_t);
   free_csr(M->A);
   free_csr(M->At);
   cudaFree(M->inv_lambda);
@@ -847,7 +890,7 @@ appga_status appga_matrix_get_info(const appga_matrix* M, appga_matrix_info* out
   out->nnz_padded_t = M->At.nnz_padded;
   out->has_bf16 = M->has_bf16;
   out->device_bytes = M->bytes;
-  out->packed_columns = M->At.cpk != nullptr ? 1 : 0;
+  out->packed_columns = M->sell_t.cols != nullptr ? 1 : 0;
   return APPGA_OK;
 }
 

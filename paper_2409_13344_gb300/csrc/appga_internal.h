@@ -29,6 +29,16 @@ constexpr int PACK_BASE_BITS = 20;
 constexpr int32_t PACK_BASE_MAX = (1 << PACK_BASE_BITS) - 1;
 constexpr int32_t PACK_OFFSET_MAX = 8191;
 
+// Device copy of a HostSell (see below), with an optional BF16 copy of the
+// values (4 per pack, 8 bytes).
+struct DevSell {
+  int32_t rows = 0, slices = 0;
+  int32_t* off = nullptr;
+  uint2* cols = nullptr;
+  float4* vals = nullptr;
+  uint2* vals_bf16 = nullptr;
+};
+
 struct DevCSR {
   int32_t rows = 0, cols = 0;
   int64_t nnz_padded = 0;
@@ -36,7 +46,6 @@ struct DevCSR {
   int32_t* col = nullptr;        // nnz_padded
   float* val = nullptr;          // nnz_padded
   uint16_t* val_bf16 = nullptr;  // nnz_padded (optional BF16 copy)
-  uint2* cpk = nullptr;          // nnz_padded / 4 packed columns (optional, solver loop)
 };
 
 // Device-resident iteration state of one solve.  Kernels derive buffer
@@ -122,6 +131,9 @@ struct FwdArgs {
   int32_t fresh_first;
   // loop: theta_{k0+i} of the run (the forward phase takes theta_k from it)
   const ThetaEntry* theta_tab;
+  // the sliced layout of A (solver projections with FP32 accumulation; its
+  // columns index ft); S.cols == NULL: the CSR A
+  DevSell S;
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).
@@ -150,11 +162,14 @@ struct PixArgs {
   // 1: the pixel phase's first blocks finalise the step (Phi(f^k) from the
   // forward phase's partials, stopping test, next index); 0: k_finalize does
   int32_t fuse_fin;
+  // the sliced layout of A^T (S.cols == NULL: the CSR At)
+  DevSell S;
 };
 
 // ---- launchers (kernels.cu) ----
 int stencil_tiles(int n);
-int forward_blocks(int m, int n);  // grid of the solver-loop forward phase
+// grid of the solver-loop forward phase (sliced: A in the sliced layout)
+int forward_blocks(int m, int n, bool sliced);
 int max_partials(int m, int n);
 int max_group_tickets(int m, int n);
 
@@ -228,6 +243,28 @@ uint16_t float_to_bf16(float x);
 // Packs a row-padded column array (a multiple of PACK_ENTRIES entries) into
 // 64-bit words (layout above); false if some pack does not fit.
 bool pack_columns(const std::vector<int32_t>& col, std::vector<uint64_t>* out);
+// One pack of PACK_ENTRIES columns into a word; false if it does not fit.
+bool encode_pack(const int32_t* c, uint64_t* word);
+
+// Sliced layout of a row-padded CSR for the solver loop's projections
+// (sliced ELLPACK over 4-entry packs): rows in slices of SELL_ROWS; each row
+// owns SELL_LANES lanes of a warp, which take its packs in turn (pack k to
+// lane k mod SELL_LANES at step k / SELL_LANES); a slice runs for as many
+// steps as its longest row needs, and every step is one pack per lane, the
+// 32 packs of a step stored consecutively.  Positions are counted in packs;
+// padding packs have value 0 (and column 0).
+constexpr int SELL_LANES = 4;
+constexpr int SELL_ROWS = 32 / SELL_LANES;
+struct HostSell {
+  int32_t rows = 0, slices = 0;
+  std::vector<int32_t> off;    // slices + 1 pack offsets (a multiple of 32 apart)
+  std::vector<uint64_t> cols;  // one packed word per pack
+  std::vector<float> vals;     // PACK_ENTRIES values per pack
+};
+// false if some pack's columns do not fit the packed word or the layout
+// exceeds 2^31 packs
+bool build_sell(int32_t rows, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                const std::vector<float>& val, HostSell* out);
 
 void set_error(const std::string& msg);
 

@@ -1,5 +1,6 @@
 // Host-side CSR utilities: validation, stable transpose, row padding and the
 // FP32 -> BF16 rounding of A's values.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -97,21 +98,61 @@ void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t*
   }
 }
 
+bool encode_pack(const int32_t* c, uint64_t* word) {
+  if (c[0] < 0 || c[0] > PACK_BASE_MAX) return false;
+  uint64_t w = (uint64_t)c[0];
+  for (int i = 1; i < PACK_ENTRIES; ++i) {
+    const int32_t dlt = c[i] - c[0];
+    if (dlt < -PACK_OFFSET_MAX - 1 || dlt > PACK_OFFSET_MAX) return false;
+    w |= ((uint64_t)(uint32_t)dlt & 0x3fffull) << (PACK_BASE_BITS + 14 * (i - 1));
+  }
+  *word = w;
+  return true;
+}
+
 bool pack_columns(const std::vector<int32_t>& col, std::vector<uint64_t>* out) {
   out->clear();
   if (col.size() % PACK_ENTRIES != 0) return false;
   const size_t np = col.size() / PACK_ENTRIES;
   out->resize(np);
-  for (size_t q = 0; q < np; ++q) {
-    const int32_t* c = &col[q * PACK_ENTRIES];
-    if (c[0] < 0 || c[0] > PACK_BASE_MAX) return false;
-    uint64_t w = (uint64_t)c[0];
-    for (int i = 1; i < PACK_ENTRIES; ++i) {
-      const int32_t dlt = c[i] - c[0];
-      if (dlt < -PACK_OFFSET_MAX - 1 || dlt > PACK_OFFSET_MAX) return false;
-      w |= ((uint64_t)(uint32_t)dlt & 0x3fffull) << (PACK_BASE_BITS + 14 * (i - 1));
+  for (size_t q = 0; q < np; ++q)
+    if (!encode_pack(&col[q * PACK_ENTRIES], &(*out)[q])) return false;
+  return true;
+}
+
+bool build_sell(int32_t rows, const std::vector<int32_t>& row_ptr, const std::vector<int32_t>& col,
+                const std::vector<float>& val, HostSell* out) {
+  constexpr int C = SELL_ROWS, L = SELL_LANES;
+  const int32_t ns = (rows + C - 1) / C;
+  out->rows = rows;
+  out->slices = ns;
+  out->off.assign((size_t)ns + 1, 0);
+  // steps of a slice: the most packs of any of its rows, over the L lanes of a row
+  int64_t total = 0;
+  for (int32_t s = 0; s < ns; ++s) {
+    int32_t most = 0;
+    for (int32_t r = s * C; r < std::min(rows, (s + 1) * C); ++r)
+      most = std::max(most, (row_ptr[r + 1] - row_ptr[r]) / PACK_ENTRIES);
+    const int64_t steps = (most + L - 1) / L;
+    total += steps * 32;
+    if (total > (int64_t)INT32_MAX) return false;
+    out->off[(size_t)s + 1] = (int32_t)total;
+  }
+  out->cols.assign((size_t)total, 0ull);
+  out->vals.assign((size_t)total * PACK_ENTRIES, 0.f);
+  for (int32_t s = 0; s < ns; ++s) {
+    const int64_t base = out->off[(size_t)s];
+    for (int32_t rr = 0; rr < C && s * C + rr < rows; ++rr) {
+      const int32_t r = s * C + rr;
+      const int32_t npk = (row_ptr[r + 1] - row_ptr[r]) / PACK_ENTRIES;
+      for (int32_t k = 0; k < npk; ++k) {
+        const int64_t pos = base + (int64_t)(k / L) * 32 + rr * L + (k % L);
+        const int32_t e = row_ptr[r] + k * PACK_ENTRIES;
+        if (!encode_pack(&col[(size_t)e], &out->cols[(size_t)pos])) return false;
+        for (int i = 0; i < PACK_ENTRIES; ++i)
+          out->vals[(size_t)pos * PACK_ENTRIES + i] = val[(size_t)e + i];
+      }
     }
-    (*out)[q] = w;
   }
   return true;
 }

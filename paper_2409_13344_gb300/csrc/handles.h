@@ -153,6 +153,10 @@ struct appga_matrix {
   appga::DevCSR A, At;
   appga::DevCSR A_tiled;  // A with column indices in the 8 x 8-tiled pixel order
                           // (shares row_ptr and values with A)
+  // the solver loop's projections in the sliced layout: A with tiled
+  // columns, and A^T (both or neither, cols == NULL when the matrix's
+  // columns do not fit the packed words)
+  appga::DevSell sell_a, sell_t;
   float* inv_lambda = nullptr;       // 1/Lambda of the FP32 values
   float* inv_lambda_bf16 = nullptr;  // 1/Lambda of the BF16-rounded values
   int32_t has_bf16 = 0;

@@ -151,27 +151,6 @@ __device__ __forceinline__ float4 gather4(const float* __restrict__ x, int4 c) {
   return make_float4(__ldg(x + c.x), __ldg(x + c.y), __ldg(x + c.z), __ldg(x + c.w));
 }
 
-// The column stream of a projection: 32-bit indices (a 16-byte pack of four
-// per lane and chunk) or packed indices (one 8-byte word per four entries).
-template <bool PK>
-struct ColStream {
-  using T = int4;
-  __device__ __forceinline__ static T load(const DevCSR& M, int p, uint64_t pol) {
-    return ld_stream_i4(M.col + p, pol);
-  }
-  __device__ __forceinline__ static int4 cols(T t) { return t; }
-  __device__ __forceinline__ static T zero() { return make_int4(0, 0, 0, 0); }
-};
-template <>
-struct ColStream<true> {
-  using T = uint2;
-  __device__ __forceinline__ static T load(const DevCSR& M, int p, uint64_t pol) {
-    return ld_stream_u2(M.cpk + (p >> 2), pol);  // p is a multiple of 4
-  }
-  __device__ __forceinline__ static int4 cols(T t) { return unpack_cols(t); }
-  __device__ __forceinline__ static T zero() { return make_uint2(0u, 0u); }
-};
-
 // Row starts of rows row0 .. row0 + nrows held one per lane (lane q <= nrows).
 __device__ __forceinline__ int load_raw_bound(const DevCSR& M, int row0, int nrows, int lane) {
   return lane <= nrows ? M.row_ptr[row0 + lane] : 0;
@@ -182,16 +161,15 @@ __device__ __forceinline__ int load_raw_bound(const DevCSR& M, int row0, int nro
 // flight.  set_bounds + prologue issue the loads; stream() accumulates the
 // products into per-lane row partials parked in the warp's shared-memory
 // slots; slot_reduce() then sums row q in lane q.
-template <bool BF16, bool DF, int R, int PF, bool PK = false>
+template <bool BF16, bool DF, int R, int PF>
 struct RowGroup {
-  using CS = ColStream<PK>;
 #if APPGA_SBND
   int* sb;  // the warp's row starts in shared memory (INT_MAX past the last row)
 #else
   int bnd[R + 1];
 #endif
   int nrows, P0, P1;
-  typename CS::T c[PF];
+  int4 c[PF];
   float4 v[PF];
 
   __device__ __forceinline__ void set_bounds(int braw, int nr) {
@@ -240,10 +218,10 @@ struct RowGroup {
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
       const int p = P0 + (u << 7) + lane * 4;
-      c[u] = CS::zero();
+      c[u] = make_int4(0, 0, 0, 0);
       v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (p < P1) {
-        c[u] = CS::load(M, p, pol);
+        c[u] = ld_stream_i4(M.col + p, pol);
         v[u] = ld_vals<BF16>(M, p, pol);
       }
     }
@@ -273,7 +251,7 @@ struct RowGroup {
     // x values of the next chunk are gathered one chunk ahead, so the gather
     // latency overlaps the arithmetic of the current chunk
     float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (P0 + lane * 4 < P1) xg = gather4(x, CS::cols(c[0]));
+    if (P0 + lane * 4 < P1) xg = gather4(x, c[0]);
 #endif
     for (int t0 = 0; t0 < nchunks; t0 += PF) {
 #pragma unroll
@@ -281,17 +259,17 @@ struct RowGroup {
         const int t = t0 + u;
         if (t < nchunks) {
           const int p = P0 + (t << 7) + lane * 4;
-          const typename CS::T cc = c[u];
+          const int4 cc = c[u];
           const float4 vv = v[u];
           const int pn = p + (PF << 7);
           if (pn < P1) {  // refill this slot with chunk t + PF before consuming chunk t
-            c[u] = CS::load(M, pn, pol);
+            c[u] = ld_stream_i4(M.col + pn, pol);
             v[u] = ld_vals<BF16>(M, pn, pol);
           }
 #if APPGA_GPIPE
           const float4 xx = xg;
           // chunk t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
-          if (p + 128 < P1) xg = gather4(x, CS::cols(c[(u + 1) % PF]));
+          if (p + 128 < P1) xg = gather4(x, c[(u + 1) % PF]);
 #endif
           if (p < P1) {
 #if APPGA_ROWINC
@@ -315,9 +293,8 @@ struct RowGroup {
             const float x0 = xx.x, x1 = xx.y, x2 = xx.z, x3 = xx.w;
             (void)cc;
 #else
-            const int4 ci = CS::cols(cc);
-            const float x0 = __ldg(x + ci.x), x1 = __ldg(x + ci.y);
-            const float x2 = __ldg(x + ci.z), x3 = __ldg(x + ci.w);
+            const float x0 = __ldg(x + cc.x), x1 = __ldg(x + cc.y);
+            const float x2 = __ldg(x + cc.z), x3 = __ldg(x + cc.w);
 #endif
             if (DF) {
               acc_fma(hi, lo, vv.x, x0);
@@ -341,6 +318,77 @@ struct RowGroup {
     __syncwarp();
   }
 
+};
+
+// One slice of the sliced layout (DevSell) streamed by one warp: lane l
+// works on row l / SELL_LANES of the slice and takes every SELL_LANES-th pack
+// of it, so each step reads 32 consecutive packs (8-byte packed columns and
+// 16 values bytes per lane) and no lane has to find the row of its entries.
+// PF steps are kept in flight in registers and the gathers of the next step
+// are issued while the current one accumulates (two FP32 accumulators per
+// lane); the SELL_LANES partial sums of a row are combined by a butterfly,
+// which leaves the same row sum in each of its lanes.
+template <bool BF16, int PF>
+struct SellGroup {
+  int q0, steps;
+  uint2 c[PF];
+  float4 v[PF];
+
+  __device__ __forceinline__ static float4 vals(const DevSell& S, int pos, uint64_t pol) {
+    if constexpr (BF16) {
+      const uint2 u = ld_stream_u2(S.vals_bf16 + pos, pol);
+      return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                         __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    } else {
+      return ld_stream_f4(reinterpret_cast<const float*>(S.vals + pos), pol);
+    }
+  }
+
+  // before the kernel waits for its predecessor: the slice's first PF steps
+  __device__ __forceinline__ void prologue(const DevSell& S, int slice, int lane, uint64_t pol) {
+    q0 = S.off[slice] + lane;
+    steps = (S.off[slice + 1] - S.off[slice]) >> 5;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      c[u] = make_uint2(0u, 0u);
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u < steps) {
+        c[u] = ld_stream_u2(S.cols + q0 + (u << 5), pol);
+        v[u] = vals(S, q0 + (u << 5), pol);
+      }
+    }
+  }
+
+  __device__ __forceinline__ float stream(const DevSell& S, const float* __restrict__ x,
+                                          uint64_t pol) {
+    float a0 = 0.f, a1 = 0.f;
+    float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (steps > 0) xg = gather4(x, unpack_cols(c[0]));
+    for (int t0 = 0; t0 < steps; t0 += PF) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + u;
+        if (t < steps) {
+          const float4 vv = v[u];
+          if (t + PF < steps) {  // refill this slot with step t + PF
+            c[u] = ld_stream_u2(S.cols + q0 + ((t + PF) << 5), pol);
+            v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+          }
+          const float4 xx = xg;
+          // step t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
+          if (t + 1 < steps) xg = gather4(x, unpack_cols(c[(u + 1) % PF]));
+          a0 = fmaf(vv.x, xx.x, a0);
+          a1 = fmaf(vv.y, xx.y, a1);
+          a0 = fmaf(vv.z, xx.z, a0);
+          a1 = fmaf(vv.w, xx.w, a1);
+        }
+      }
+    }
+    float r = a0 + a1;
+#pragma unroll
+    for (int o = 1; o < SELL_LANES; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+  }
 };
 
 // Sum of row `lane` of a streamed group in lanes 0..nrows-1 from the warp's
@@ -543,7 +591,17 @@ __device__ __forceinline__ void forward_row(const FwdArgs& a, df th, int kk, int
 
 // Blocks [0, proj_blocks<FW>(m)) project rows; in the solver loop the blocks
 // after them run the stencil tiles.
-template <bool BF16, bool DFA, bool PK>
+// Rows per forward block: FW::W warps of FW::R CSR rows, or of one slice of
+// SELL_ROWS rows in the sliced layout.
+template <bool SL>
+__host__ __device__ __forceinline__ constexpr int fw_block_rows() {
+  return SL ? FW::W * SELL_ROWS : FW::ROWS;
+}
+
+// Blocks [0, nproj) project rows (CSR row groups, or slices of the sliced
+// layout when SL); in the solver loop the blocks after them run the stencil
+// tiles.
+template <bool BF16, bool DFA, bool SL>
 __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   __shared__ union {
     struct {
@@ -553,10 +611,13 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     } slot;
     StencilSmem st;
   } sm;
+  static_assert(!(SL && DFA), "the sliced layout serves the FP32-accumulated projections");
   pdl_trigger();
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nproj = proj_blocks<FW>(a.A.rows);
+  const int m = a.A.rows;
+  constexpr int BROWS = fw_block_rows<SL>();
+  const int nproj = (m + BROWS - 1) / BROWS;
 #if APPGA_SFIRST
   // stencil tiles take the first blocks, so the projector blocks end the grid
   const int pb = (int)blockIdx.x - ((int)gridDim.x - nproj);
@@ -566,21 +627,26 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   const int sb = (int)blockIdx.x - nproj;
 #endif
   const bool proj = pb >= 0 && pb < nproj;
-  const int m = a.A.rows;
-  const int row0 = pb * FW::ROWS + warp * FW::R;
-  const int nrows = proj ? max(0, min(FW::R, m - row0)) : 0;
+  // CSR: this warp's rows; sliced: this warp's slice
+  const int row0 = SL ? (pb * FW::W + warp) * SELL_ROWS : pb * FW::ROWS + warp * FW::R;
+  const int nrows = proj ? max(0, min(SL ? SELL_ROWS : FW::R, m - row0)) : 0;
   // The warp's row bounds and first chunks of A: no kernel writes them, so
   // they are fetched before waiting for the previous kernel of the stream.
-  RowGroup<BF16, DFA, FW::R, FW::PF, PK> rg;
+  RowGroup<BF16, DFA, FW::R, FW::PF> rg;
+  SellGroup<BF16, FW::PF> sg;
   uint64_t pol = 0;
   if (nrows > 0) {
-#if APPGA_SBND
-    rg.sb = reinterpret_cast<int*>(sm.slot.bnd[warp]);
-#endif
-    rg.set_bounds(load_raw_bound(a.A, row0, nrows, lane), nrows);
-    decltype(rg)::clear_slots(lane, sm.slot.hi[warp], sm.slot.lo[warp]);
     pol = evict_first_policy();
-    rg.prologue(a.A, lane, pol);
+    if constexpr (SL) {
+      sg.prologue(a.S, pb * FW::W + warp, lane, pol);
+    } else {
+#if APPGA_SBND
+      rg.sb = reinterpret_cast<int*>(sm.slot.bnd[warp]);
+#endif
+      rg.set_bounds(load_raw_bound(a.A, row0, nrows, lane), nrows);
+      decltype(rg)::clear_slots(lane, sm.slot.hi[warp], sm.slot.lo[warp]);
+      rg.prologue(a.A, lane, pol);
+    }
   }
   pdl_wait();
   int kk = 0;
@@ -607,25 +673,37 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     // the tiled copy when given (the solver's projections), else the image
     const float* f = a.ft ? a.ft : (a.loop ? a.f[kk % 3] : a.f[0]);
     float hi = 0.f, lo = 0.f;
-    if (nrows > 0) {
-      rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
-      slot_reduce<DFA>(lane, nrows, sm.slot.hi[warp], sm.slot.lo[warp], hi, lo);
+    // lanes holding a row sum, and which row of the warp's rows
+    bool has_row;
+    int wrow;
+    if constexpr (SL) {
+      if (nrows > 0) hi = sg.stream(a.S, f, pol);
+      wrow = lane / SELL_LANES;
+      has_row = (lane % SELL_LANES) == 0 && wrow < nrows;
+    } else {
+      if (nrows > 0) {
+        rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
+        slot_reduce<DFA>(lane, nrows, sm.slot.hi[warp], sm.slot.lo[warp], hi, lo);
+      }
+      wrow = lane;
+      has_row = lane < nrows;
     }
+    constexpr int WROWS = SL ? SELL_ROWS : FW::R;
 #if APPGA_FEPI
     // the block's row sums go to warp 0, so the double-float epilogue (with
     // the logarithm of the data term) runs once per block, not once per warp
-    __shared__ float2 ysum[FW::ROWS];
-    if (lane < nrows) ysum[warp * FW::R + lane] = make_float2(hi, lo);
+    __shared__ float2 ysum[BROWS];
+    if (has_row) ysum[warp * WROWS + wrow] = make_float2(hi, lo);
     __syncthreads();
     if (warp == 0) {
-      const int brow0 = pb * FW::ROWS, bn = min(FW::ROWS, m - brow0);
+      const int brow0 = pb * BROWS, bn = min(BROWS, m - brow0);
       for (int q = lane; q < bn; q += 32) {
         const float2 v = ysum[q];
         forward_row(a, th, kk, brow0 + q, v.x, v.y, hits, bad, acc_hi, acc_lo);
       }
     }
 #else
-    if (lane < nrows) forward_row(a, th, kk, row0 + lane, hi, lo, hits, bad, acc_hi, acc_lo);
+    if (has_row) forward_row(a, th, kk, row0 + wrow, hi, lo, hits, bad, acc_hi, acc_lo);
 #endif
   } else {
     // SHOITV gradient at f~^kk and the regulariser of Phi(f^kk)
@@ -752,7 +830,14 @@ __device__ void fused_finalize(const PixArgs& a, SolverState* st, int kk) {
   }
 }
 
-template <bool BF16, bool PK>
+// Pixel rows per block: PX::W warps of PX::R CSR rows of A^T, or of one
+// slice of SELL_ROWS rows in the sliced layout.
+template <bool SL>
+__host__ __device__ __forceinline__ constexpr int px_block_rows() {
+  return SL ? PX::W * SELL_ROWS : PX::ROWS;
+}
+
+template <bool BF16, bool SL>
 __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
   __shared__ int4 sbnd[PX::W][4];
@@ -760,19 +845,25 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int d = a.At.rows;
-  const int j0 = blockIdx.x * PX::ROWS + warp * PX::R;
-  const int np = max(0, min(PX::R, d - j0));
+  // CSR: this warp's pixel rows; sliced: this warp's slice
+  const int j0 = SL ? (blockIdx.x * PX::W + warp) * SELL_ROWS : blockIdx.x * PX::ROWS + warp * PX::R;
+  const int np = max(0, min(SL ? SELL_ROWS : PX::R, d - j0));
   // row bounds and first chunks of A^T before waiting (no kernel writes them)
-  RowGroup<BF16, false, PX::R, PX::PF, PK> rg;
+  RowGroup<BF16, false, PX::R, PX::PF> rg;
+  SellGroup<BF16, PX::PF> sg;
   uint64_t pol = 0;
   if (np > 0) {
-#if APPGA_SBND
-    rg.sb = reinterpret_cast<int*>(sbnd[warp]);
-#endif
-    rg.set_bounds(load_raw_bound(a.At, j0, np, lane), np);
-    decltype(rg)::clear_slots(lane, slot[warp], nullptr);
     pol = evict_first_policy();
-    rg.prologue(a.At, lane, pol);
+    if constexpr (SL) {
+      sg.prologue(a.S, blockIdx.x * PX::W + warp, lane, pol);
+    } else {
+#if APPGA_SBND
+      rg.sb = reinterpret_cast<int*>(sbnd[warp]);
+#endif
+      rg.set_bounds(load_raw_bound(a.At, j0, np, lane), np);
+      decltype(rg)::clear_slots(lane, slot[warp], nullptr);
+      rg.prologue(a.At, lane, pol);
+    }
   }
   pdl_wait();
   if (st->done) return;  // uniform over the grid
@@ -780,12 +871,19 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   if (a.fuse_fin) fused_finalize(a, st, kk);
   int bad = 0;
   float bp = 0.f, unused = 0.f;
-  if (np > 0) {
-    rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
-    slot_reduce<false>(lane, np, slot[warp], nullptr, bp, unused);
+  int j = -1;  // the pixel whose update this lane makes
+  if constexpr (SL) {
+    if (np > 0) bp = sg.stream(a.S, a.w, pol);
+    if ((lane % SELL_LANES) == 0 && lane / SELL_LANES < np) j = j0 + lane / SELL_LANES;
+  } else {
+    if (np > 0) {
+      rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
+      slot_reduce<false>(lane, np, slot[warp], nullptr, bp, unused);
+    }
+    if (lane < np) j = j0 + lane;
   }
   float pj = 0.f;
-  if (lane < np) pj = pixel_update(a, kk, j0 + lane, bp, bad);
+  if (j >= 0) pj = pixel_update(a, kk, j, bp, bad);
   if (a.want_pmax) {
     // largest preconditioner entry of this step (order-independent)
     const unsigned pm = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(pj, 0.f)));
@@ -1115,7 +1213,11 @@ cudaError_t launch_dep(void (*kern)(P...), int grid, int block, cudaStream_t s, 
 }  // namespace
 
 int stencil_tiles(int n) { return st_tiles(n); }
-int forward_blocks(int m, int n) { return proj_blocks<FW>(m) + st_tiles(n); }
+int forward_blocks_of(int m, int n, bool sliced, bool stencil) {
+  const int rows = sliced ? fw_block_rows<true>() : fw_block_rows<false>();
+  return (m + rows - 1) / rows + (stencil ? st_tiles(n) : 0);
+}
+int forward_blocks(int m, int n, bool sliced) { return forward_blocks_of(m, n, sliced, true); }
 
 int max_partials(int m, int n) {
   const int a = proj_blocks<FW>(m) + st_tiles(n);
@@ -1144,10 +1246,12 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
     return r;
   });
   if (carve != cudaSuccess) return carve;
-  // packed columns serve the solver's FP32-accumulated projections
-  if (a.A.cpk != nullptr && !dfa)
-    return a.use_bf16 ? launch_dep(k_forward<true, false, true>, grid, FW::THREADS, s, a)
-                      : launch_dep(k_forward<false, false, true>, grid, FW::THREADS, s, a);
+  // the sliced layout serves the solver's FP32-accumulated projections
+  if (a.S.cols != nullptr && !dfa) {
+    const int sgrid = forward_blocks_of(a.A.rows, a.n, true, a.loop && !a.no_stencil);
+    return a.use_bf16 ? launch_dep(k_forward<true, false, true>, sgrid, FW::THREADS, s, a)
+                      : launch_dep(k_forward<false, false, true>, sgrid, FW::THREADS, s, a);
+  }
   if (a.use_bf16)
     return dfa ? launch_dep(k_forward<true, true, false>, grid, FW::THREADS, s, a)
                : launch_dep(k_forward<true, false, false>, grid, FW::THREADS, s, a);
@@ -1165,14 +1269,15 @@ cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
     return r;
   });
   if (carve != cudaSuccess) return carve;
-  const int grid = proj_blocks<PX>(a.At.rows);
-  const bool pk = a.At.cpk != nullptr;
+  const bool sl = a.S.cols != nullptr;
+  const int rows_pb = sl ? px_block_rows<true>() : px_block_rows<false>();
+  const int grid = (a.At.rows + rows_pb - 1) / rows_pb;
   cudaError_t e;
   if (a.use_bf16)
-    e = pk ? launch_dep(k_pixel<true, true>, grid, PX::THREADS, s, a)
+    e = sl ? launch_dep(k_pixel<true, true>, grid, PX::THREADS, s, a)
            : launch_dep(k_pixel<true, false>, grid, PX::THREADS, s, a);
   else
-    e = pk ? launch_dep(k_pixel<false, true>, grid, PX::THREADS, s, a)
+    e = sl ? launch_dep(k_pixel<false, true>, grid, PX::THREADS, s, a)
            : launch_dep(k_pixel<false, false>, grid, PX::THREADS, s, a);
   if (e != cudaSuccess || a.theta_tab == nullptr || a.fuse_fin) return e;
   return launch_dep(k_finalize, 1, FIN_THREADS, s, a);

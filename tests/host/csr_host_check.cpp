@@ -11,7 +11,10 @@
 //          float val[nnz]; then uint16 bf_out[nbf] (float_to_bf16); then
 //          int32 validate status of the input; then for each side n:
 //          int64 tiled_size(n), int32 tiled_index(r, c, n) for the n x n
-//          pixels in row-major order.
+//          pixels in row-major order; then for A padded and A^T padded the
+//          sliced layout (build_sell): int32 ok, slices, n_packs,
+//          int32 off[slices+1], uint64 cols[n_packs], float vals[4 n_packs]
+//          (only the ok flag when it is 0).
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -78,6 +81,17 @@ int main(int argc, char** argv) {
     for (int32_t r = 0; r < n; ++r)
       for (int32_t c = 0; c < n; ++c) idx[(size_t)r * n + c] = appga::tiled_index(r, c, n);
     std::fwrite(idx.data(), 4, idx.size(), out);
+  }
+  for (const appga::HostCSR* c : {&pa, &pt}) {
+    appga::HostSell sl;
+    const int32_t ok = appga::build_sell(c->rows, c->row_ptr, c->col, c->val, &sl) ? 1 : 0;
+    std::fwrite(&ok, 4, 1, out);
+    if (!ok) continue;
+    const int32_t h2[2] = {sl.slices, (int32_t)sl.cols.size()};
+    std::fwrite(h2, 4, 2, out);
+    std::fwrite(sl.off.data(), 4, sl.off.size(), out);
+    std::fwrite(sl.cols.data(), 8, sl.cols.size(), out);
+    std::fwrite(sl.vals.data(), 4, sl.vals.size(), out);
   }
   std::fclose(out);
   return 0;

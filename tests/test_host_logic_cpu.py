@@ -15,7 +15,10 @@ independent implementations:
   PyTorch's conversion;
 * the 8 x 8 tiled pixel order maps the n x n pixels one to one into
   tiled_size(n) entries, each 8 x 8 block onto one aligned run of 64, blocks
-  and pixels within a block in raster order.
+  and pixels within a block in raster order;
+* the sliced layout of the solver loop's projections, decoded here from its
+  documented word format and position rule, holds every padded row's
+  entries in order and zero values everywhere else.
 """
 import os
 import shutil
@@ -73,6 +76,13 @@ def _run(exe, tmp_path, m, d, row_ptr, col, val, bf_in):
     for n in SIDES:
         size = int(take(np.int64, 1)[0])
         res["tiled"][n] = (size, take(np.int32, n * n).reshape(n, n))
+    for key in ("sell_a", "sell_t"):
+        ok = int(take(np.int32, 1)[0])
+        if not ok:
+            res[key] = None
+            continue
+        slices, npk = take(np.int32, 2)
+        res[key] = (take(np.int32, slices + 1), take(np.uint64, npk), take(np.float32, 4 * npk))
     assert pos == len(raw)
     return res
 
@@ -199,3 +209,61 @@ def test_tiled_pixel_order(harness, tmp_path):
                 # a full block fills its run exactly
                 if blk.shape == (8, 8):
                     np.testing.assert_array_equal(np.sort(blk.reshape(-1) % 64), np.arange(64))
+
+
+SELL_LANES = 4
+SELL_ROWS = 32 // SELL_LANES
+
+
+def _decode_word(w):
+    """Columns of one 64-bit pack word: base in bits 0-19, then three signed
+    14-bit offsets from it."""
+    w = int(w)
+    base = w & 0xFFFFF
+    out = [base]
+    for i in range(3):
+        o = (w >> (20 + 14 * i)) & 0x3FFF
+        if o >= 0x2000:
+            o -= 0x4000
+        out.append(base + o)
+    return out
+
+
+def _check_sell(padded, sell):
+    row_ptr, col, val = padded
+    off, words, vals = sell
+    rows = len(row_ptr) - 1
+    assert len(off) == (rows + SELL_ROWS - 1) // SELL_ROWS + 1 and off[0] == 0
+    assert np.all(np.diff(off) % 32 == 0)
+    seen = np.zeros(len(words), bool)
+    for r in range(rows):
+        s, rr = divmod(r, SELL_ROWS)
+        npk = (row_ptr[r + 1] - row_ptr[r]) // 4
+        # the slice runs for as many steps as its longest row needs
+        assert (off[s + 1] - off[s]) // 32 >= (npk + SELL_LANES - 1) // SELL_LANES
+        for k in range(npk):
+            pos = off[s] + (k // SELL_LANES) * 32 + rr * SELL_LANES + k % SELL_LANES
+            e = row_ptr[r] + 4 * k
+            assert _decode_word(words[pos]) == list(col[e:e + 4])
+            np.testing.assert_array_equal(vals[4 * pos:4 * pos + 4], val[e:e + 4])
+            seen[pos] = True
+    assert np.all(vals.reshape(-1, 4)[~seen] == 0.0)
+
+
+def test_sliced_layout_of_random_and_siddon_matrices(harness, tmp_path):
+    from paper_2409_13344_gb300 import workload as W
+    rng = np.random.default_rng(11)
+    cases = [(37, 53) + _random_csr(rng, 37, 53), (8, 8) + _random_csr(rng, 8, 8)]
+    A = W.siddon_matrix(W.Geometry(16, 10, 8))
+    cases.append((A.shape[0], A.shape[1], A.indptr, A.indices, A.data))
+    for m, d, row_ptr, col, val in cases:
+        res = _run(harness, tmp_path, m, d, row_ptr, col, val, np.zeros(0, np.float32))
+        _check_sell(res["pa"], res["sell_a"])
+        _check_sell(res["pt"], res["sell_t"])
+
+
+def test_sliced_layout_refuses_columns_beyond_the_word(harness, tmp_path):
+    # one row with columns 0 and 9000 in one pack: the offset does not fit 14 bits
+    res = _run(harness, tmp_path, 1, 9001, [0, 2], [0, 9000], [1.0, 2.0],
+               np.zeros(0, np.float32))
+    assert res["sell_a"] is None
