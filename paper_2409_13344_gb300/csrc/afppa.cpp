@@ -133,8 +133,10 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   fa.theta_tab = ws.theta_tab;
   const bool tiled = tiled_gather_enabled();
   if (tiled) {
-    // the loop's projector gathers f^k from its 8 x 8-tiled copy
+    // the loop's projector gathers f^k from its 8 x 8-tiled copy (through
+    // the sliced layout, as the APPGA loop does)
     fa.A.col = M->A_tiled.col;
+    fa.S = M->sell_a;
     fa.ft = ws.ft;
     CK(launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
   }
@@ -149,6 +151,7 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = ws.pfreeze;
   pa.ft = tiled ? ws.ft : nullptr;
+  if (tiled) pa.S = M->sell_t;
   pa.st = ws.st;
   pa.partial = ws.partial_p;
   pa.gtick = ws.gtick;

@@ -253,7 +253,11 @@ bool encode_pack(const int32_t* c, uint64_t* word);
 // steps as its longest row needs, and every step is one pack per lane, the
 // 32 packs of a step stored consecutively.  Positions are counted in packs;
 // padding packs have value 0 (and column 0).
-constexpr int SELL_LANES = 4;
+#ifndef APPGA_SELL_LANES
+#define APPGA_SELL_LANES 4
+#endif
+constexpr int SELL_LANES = APPGA_SELL_LANES;  // 1, 2, 4, 8, 16 or 32
+static_assert(SELL_LANES >= 1 && SELL_LANES <= 32 && 32 % SELL_LANES == 0, "lanes per row");
 constexpr int SELL_ROWS = 32 / SELL_LANES;
 struct HostSell {
   int32_t rows = 0, slices = 0;

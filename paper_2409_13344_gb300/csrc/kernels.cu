@@ -81,6 +81,13 @@ struct Shape {
 #ifndef APPGA_PX_PF
 #define APPGA_PX_PF 3
 #endif
+// steps in flight per warp in the sliced layout's forward and pixel phases
+#ifndef APPGA_SELL_FW_PF
+#define APPGA_SELL_FW_PF 3
+#endif
+#ifndef APPGA_SELL_PX_PF
+#define APPGA_SELL_PX_PF 4
+#endif
 using FW = Shape<APPGA_FW_W, APPGA_FW_RPW, APPGA_FW_PF>;
 using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
 // Minimum resident blocks per SM asked of the compiler (a register budget);
@@ -633,7 +640,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   // The warp's row bounds and first chunks of A: no kernel writes them, so
   // they are fetched before waiting for the previous kernel of the stream.
   RowGroup<BF16, DFA, FW::R, FW::PF> rg;
-  SellGroup<BF16, FW::PF> sg;
+  SellGroup<BF16, APPGA_SELL_FW_PF> sg;
   uint64_t pol = 0;
   if (nrows > 0) {
     pol = evict_first_policy();
@@ -850,7 +857,7 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   const int np = max(0, min(SL ? SELL_ROWS : PX::R, d - j0));
   // row bounds and first chunks of A^T before waiting (no kernel writes them)
   RowGroup<BF16, false, PX::R, PX::PF> rg;
-  SellGroup<BF16, PX::PF> sg;
+  SellGroup<BF16, APPGA_SELL_PX_PF> sg;
   uint64_t pol = 0;
   if (np > 0) {
     pol = evict_first_policy();
