@@ -111,6 +111,8 @@ typedef struct {
                              indices (every column below 2^20 and, within each
                              4-entry pack of a row, within [-8192, 8191] of the
                              pack's first column); 0: 4-byte indices */
+  int32_t sliced_layout;  /* 1 if the solver loop's projections stream A and
+                             A^T in the sliced (ELLPACK-like) layout; 0: CSR */
 } appga_matrix_info;
 appga_status appga_matrix_get_info(const appga_matrix* mat, appga_matrix_info* out);
 

@@ -63,6 +63,7 @@ class appga_matrix_info(ctypes.Structure):
         ("n_angles", ctypes.c_int32), ("nnz", ctypes.c_int64), ("nnz_padded_a", ctypes.c_int64),
         ("nnz_padded_t", ctypes.c_int64), ("has_bf16", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64), ("packed_columns", ctypes.c_int32),
+        ("sliced_layout", ctypes.c_int32),
     ]
 
 

@@ -67,6 +67,7 @@ void free_csr(DevCSR& c) {
 void free_sell(DevSell& c) {
   cudaFree(c.off);
   cudaFree(c.cols);
+  cudaFree(c.cols32);
   cudaFree(c.vals);
   cudaFree(c.vals_bf16);
   c = DevSell();
@@ -76,15 +77,18 @@ appga_status upload_sell(const appga::HostSell& h, bool bf16, DevSell* out, int6
   DevSell c;
   c.rows = h.rows;
   c.slices = h.slices;
-  const size_t np = h.cols.size();
+  const size_t np = h.vals.size() / appga::PACK_ENTRIES;
   cudaError_t e = dalloc(&c.off, h.off.size(), bytes);
-  if (e == cudaSuccess) e = dalloc(&c.cols, np, bytes);
+  if (e == cudaSuccess && !h.cols.empty()) e = dalloc(&c.cols, np, bytes);
+  if (e == cudaSuccess && !h.cols32.empty()) e = dalloc(&c.cols32, np, bytes);
   if (e == cudaSuccess) e = dalloc(&c.vals, np, bytes);
   if (e == cudaSuccess && bf16) e = dalloc(&c.vals_bf16, np, bytes);
   if (e == cudaSuccess)
     e = cudaMemcpy(c.off, h.off.data(), h.off.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && np)
+  if (e == cudaSuccess && !h.cols.empty())
     e = cudaMemcpy(c.cols, h.cols.data(), np * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !h.cols32.empty())
+    e = cudaMemcpy(c.cols32, h.cols32.data(), np * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && np)
     e = cudaMemcpy(c.vals, h.vals.data(), np * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && bf16 && np) {
@@ -336,7 +340,7 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
     pa.S = M->sell_t;
     if (!tiled_ready) CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
   }
-  pa.n_fwd_partial = appga::forward_blocks(M->m, M->n, fa.S.cols != nullptr);
+  pa.n_fwd_partial = appga::forward_blocks(M->m, M->n, fa.S.off != nullptr);
 
   // w^{k0}, y^{k0}, B^T grad phi~(B f~^{k0}) and Phi(f^{k0})
   appga::FwdArgs first = fa;
@@ -891,6 +895,7 @@ appga_status appga_matrix_get_info(const appga_matrix* M, appga_matrix_info* out
   out->has_bf16 = M->has_bf16;
   out->device_bytes = M->bytes;
   out->packed_columns = M->sell_t.cols != nullptr ? 1 : 0;
+  out->sliced_layout = (M->sell_t.cols != nullptr || M->sell_t.cols32 != nullptr) ? 1 : 0;
   return APPGA_OK;
 }
 

@@ -34,7 +34,8 @@ constexpr int32_t PACK_OFFSET_MAX = 8191;
 struct DevSell {
   int32_t rows = 0, slices = 0;
   int32_t* off = nullptr;
-  uint2* cols = nullptr;
+  uint2* cols = nullptr;    // packed words (APPGA_SELL_PACK), or
+  int4* cols32 = nullptr;   // four 32-bit columns per pack
   float4* vals = nullptr;
   uint2* vals_bf16 = nullptr;
 };
@@ -259,10 +260,16 @@ bool encode_pack(const int32_t* c, uint64_t* word);
 constexpr int SELL_LANES = APPGA_SELL_LANES;  // 1, 2, 4, 8, 16 or 32
 static_assert(SELL_LANES >= 1 && SELL_LANES <= 32 && 32 % SELL_LANES == 0, "lanes per row");
 constexpr int SELL_ROWS = 32 / SELL_LANES;
+// Columns of the sliced layout as packed words (1) or as four 32-bit
+// indices per pack (0).
+#ifndef APPGA_SELL_PACK
+#define APPGA_SELL_PACK 1
+#endif
 struct HostSell {
   int32_t rows = 0, slices = 0;
   std::vector<int32_t> off;    // slices + 1 pack offsets (a multiple of 32 apart)
-  std::vector<uint64_t> cols;  // one packed word per pack
+  std::vector<uint64_t> cols;  // one packed word per pack (APPGA_SELL_PACK)
+  std::vector<int32_t> cols32; // PACK_ENTRIES columns per pack (otherwise)
   std::vector<float> vals;     // PACK_ENTRIES values per pack
 };
 // false if some pack's columns do not fit the packed word or the layout

@@ -138,7 +138,10 @@ bool build_sell(int32_t rows, const std::vector<int32_t>& row_ptr, const std::ve
     if (total > (int64_t)INT32_MAX) return false;
     out->off[(size_t)s + 1] = (int32_t)total;
   }
-  out->cols.assign((size_t)total, 0ull);
+  if (APPGA_SELL_PACK)
+    out->cols.assign((size_t)total, 0ull);
+  else
+    out->cols32.assign((size_t)total * PACK_ENTRIES, 0);
   out->vals.assign((size_t)total * PACK_ENTRIES, 0.f);
   for (int32_t s = 0; s < ns; ++s) {
     const int64_t base = out->off[(size_t)s];
@@ -148,9 +151,13 @@ bool build_sell(int32_t rows, const std::vector<int32_t>& row_ptr, const std::ve
       for (int32_t k = 0; k < npk; ++k) {
         const int64_t pos = base + (int64_t)(k / L) * 32 + rr * L + (k % L);
         const int32_t e = row_ptr[r] + k * PACK_ENTRIES;
-        if (!encode_pack(&col[(size_t)e], &out->cols[(size_t)pos])) return false;
-        for (int i = 0; i < PACK_ENTRIES; ++i)
+        if (APPGA_SELL_PACK) {
+          if (!encode_pack(&col[(size_t)e], &out->cols[(size_t)pos])) return false;
+        }
+        for (int i = 0; i < PACK_ENTRIES; ++i) {
           out->vals[(size_t)pos * PACK_ENTRIES + i] = val[(size_t)e + i];
+          if (!APPGA_SELL_PACK) out->cols32[(size_t)pos * PACK_ENTRIES + i] = col[(size_t)e + i];
+        }
       }
     }
   }

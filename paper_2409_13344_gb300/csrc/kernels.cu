@@ -335,10 +335,26 @@ struct RowGroup {
 // are issued while the current one accumulates (two FP32 accumulators per
 // lane); the SELL_LANES partial sums of a row are combined by a butterfly,
 // which leaves the same row sum in each of its lanes.
+#if APPGA_SELL_PACK
+using SellCols = uint2;  // one packed word per pack
+__device__ __forceinline__ SellCols sell_cols_load(const DevSell& S, int pos, uint64_t pol) {
+  return ld_stream_u2(S.cols + pos, pol);
+}
+__device__ __forceinline__ int4 sell_cols(SellCols c) { return unpack_cols(c); }
+__device__ __forceinline__ SellCols sell_cols_zero() { return make_uint2(0u, 0u); }
+#else
+using SellCols = int4;  // four 32-bit columns per pack
+__device__ __forceinline__ SellCols sell_cols_load(const DevSell& S, int pos, uint64_t pol) {
+  return ld_stream_i4(reinterpret_cast<const int32_t*>(S.cols32 + pos), pol);
+}
+__device__ __forceinline__ int4 sell_cols(SellCols c) { return c; }
+__device__ __forceinline__ SellCols sell_cols_zero() { return make_int4(0, 0, 0, 0); }
+#endif
+
 template <bool BF16, int PF>
 struct SellGroup {
   int q0, steps;
-  uint2 c[PF];
+  SellCols c[PF];
   float4 v[PF];
 
   __device__ __forceinline__ static float4 vals(const DevSell& S, int pos, uint64_t pol) {
@@ -357,10 +373,10 @@ struct SellGroup {
     steps = (S.off[slice + 1] - S.off[slice]) >> 5;
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
-      c[u] = make_uint2(0u, 0u);
+      c[u] = sell_cols_zero();
       v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (u < steps) {
-        c[u] = ld_stream_u2(S.cols + q0 + (u << 5), pol);
+        c[u] = sell_cols_load(S, q0 + (u << 5), pol);
         v[u] = vals(S, q0 + (u << 5), pol);
       }
     }
@@ -370,7 +386,7 @@ struct SellGroup {
                                           uint64_t pol) {
     float a0 = 0.f, a1 = 0.f;
     float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (steps > 0) xg = gather4(x, unpack_cols(c[0]));
+    if (steps > 0) xg = gather4(x, sell_cols(c[0]));
     for (int t0 = 0; t0 < steps; t0 += PF) {
 #pragma unroll
       for (int u = 0; u < PF; ++u) {
@@ -378,12 +394,12 @@ struct SellGroup {
         if (t < steps) {
           const float4 vv = v[u];
           if (t + PF < steps) {  // refill this slot with step t + PF
-            c[u] = ld_stream_u2(S.cols + q0 + ((t + PF) << 5), pol);
+            c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
             v[u] = vals(S, q0 + ((t + PF) << 5), pol);
           }
           const float4 xx = xg;
           // step t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
-          if (t + 1 < steps) xg = gather4(x, unpack_cols(c[(u + 1) % PF]));
+          if (t + 1 < steps) xg = gather4(x, sell_cols(c[(u + 1) % PF]));
           a0 = fmaf(vv.x, xx.x, a0);
           a1 = fmaf(vv.y, xx.y, a1);
           a0 = fmaf(vv.z, xx.z, a0);
@@ -1254,7 +1270,7 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   });
   if (carve != cudaSuccess) return carve;
   // the sliced layout serves the solver's FP32-accumulated projections
-  if (a.S.cols != nullptr && !dfa) {
+  if (a.S.off != nullptr && !dfa) {
     const int sgrid = forward_blocks_of(a.A.rows, a.n, true, a.loop && !a.no_stencil);
     return a.use_bf16 ? launch_dep(k_forward<true, false, true>, sgrid, FW::THREADS, s, a)
                       : launch_dep(k_forward<false, false, true>, sgrid, FW::THREADS, s, a);
@@ -1276,7 +1292,7 @@ cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
     return r;
   });
   if (carve != cudaSuccess) return carve;
-  const bool sl = a.S.cols != nullptr;
+  const bool sl = a.S.off != nullptr;
   const int rows_pb = sl ? px_block_rows<true>() : px_block_rows<false>();
   const int grid = (a.At.rows + rows_pb - 1) / rows_pb;
   cudaError_t e;
