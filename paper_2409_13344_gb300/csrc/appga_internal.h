@@ -255,7 +255,7 @@ bool encode_pack(const int32_t* c, uint64_t* word);
 // 32 packs of a step stored consecutively.  Positions are counted in packs;
 // padding packs have value 0 (and column 0).
 #ifndef APPGA_SELL_LANES
-#define APPGA_SELL_LANES 4
+#define APPGA_SELL_LANES 8
 #endif
 constexpr int SELL_LANES = APPGA_SELL_LANES;  // 1, 2, 4, 8, 16 or 32
 static_assert(SELL_LANES >= 1 && SELL_LANES <= 32 && 32 % SELL_LANES == 0, "lanes per row");

@@ -83,10 +83,10 @@ struct Shape {
 #endif
 // steps in flight per warp in the sliced layout's forward and pixel phases
 #ifndef APPGA_SELL_FW_PF
-#define APPGA_SELL_FW_PF 3
+#define APPGA_SELL_FW_PF 2
 #endif
 #ifndef APPGA_SELL_PX_PF
-#define APPGA_SELL_PX_PF 4
+#define APPGA_SELL_PX_PF 3
 #endif
 using FW = Shape<APPGA_FW_W, APPGA_FW_RPW, APPGA_FW_PF>;
 using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;

@@ -50,15 +50,23 @@ def _bench_module():
 
 def test_algorithmic_bytes_match_the_committed_record():
     """Per-launch algorithmic bytes of the two iteration kernels at 256x256
-    (m 66 060 rays, d 65 536 pixels, 15 017 956 stored entries): the A or A^T
-    stream at 8 B per entry plus each vector once, as the ncu record states."""
+    (m 66 060 rays, d 65 536 pixels, 15 017 956 nonzeros): the A or A^T
+    stream at 6 B per nonzero in the sliced, packed layout (8 B for FP32
+    values and 4-byte columns), its offsets, and each vector once, as the
+    ncu record states."""
     b = _bench_module()
+    m, d, nnz = 66060, 65536, 15017956
+    fwd, pix = b.kernel_bytes(m, d, nnz, 6, True)
+    # written out: matrix, offsets (one per 4 rows), f, g, gamma, y_prev, y, w, stencil vectors
+    assert fwd == 6 * nnz + 4 * (m // 4 + 1) + 4 * d + (4 + 4 + 8 + 8 + 4) * m + 12 * d
+    assert pix == 6 * nnz + 4 * (d // 4 + 1) + 4 * m + 20 * d
+    assert b.kernel_bytes(m, d, nnz)[1] == 8 * nnz + 4 * (d + 1) + 4 * m + 20 * d
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    fwd, pix = b.kernel_bytes(66060, 65536, 15017956)
-    assert fwd == rec["kernels"]["k_forward"]["algorithmic_bytes_per_launch"]
-    assert pix == rec["kernels"]["k_pixel"]["algorithmic_bytes_per_launch"]
-    # both streams dominate: 16 B per entry is 98 % of an iteration's bytes
-    assert 0.98 < 16 * 15017956 / (fwd + pix) < 0.99
+    if rec.get("bytes_per_nnz") == 6:
+        assert fwd == rec["kernels"]["k_forward"]["algorithmic_bytes_per_launch"]
+        assert pix == rec["kernels"]["k_pixel"]["algorithmic_bytes_per_launch"]
+    # both streams dominate: 12 B per nonzero is 97-98 % of an iteration's bytes
+    assert 0.97 < 12 * nnz / (fwd + pix) < 0.99
     # a batched iteration of 64 slices reads the matrix once: far below 64 iterations
     kb = b.batched_bytes(66060, 65536, 15017956, 64)
     assert 16 * 15017956 < kb < 3 * (fwd + pix)

@@ -211,7 +211,7 @@ def test_tiled_pixel_order(harness, tmp_path):
                     np.testing.assert_array_equal(np.sort(blk.reshape(-1) % 64), np.arange(64))
 
 
-SELL_LANES = 4
+SELL_LANES = 8
 SELL_ROWS = 32 // SELL_LANES
 
 
