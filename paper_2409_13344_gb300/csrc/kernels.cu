@@ -81,6 +81,11 @@ struct Shape {
 #ifndef APPGA_PX_PF
 #define APPGA_PX_PF 3
 #endif
+// the sliced layout's step loop runs whole groups of steps without per-step
+// tests (1) or tests every step (0)
+#ifndef APPGA_SELL_PEEL
+#define APPGA_SELL_PEEL 1
+#endif
 // steps in flight per warp in the sliced layout's forward and pixel phases
 #ifndef APPGA_SELL_FW_PF
 #define APPGA_SELL_FW_PF 2
@@ -387,7 +392,27 @@ struct SellGroup {
     float a0 = 0.f, a1 = 0.f;
     float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
     if (steps > 0) xg = gather4(x, sell_cols(c[0]));
-    for (int t0 = 0; t0 < steps; t0 += PF) {
+    int t0 = 0;
+#if APPGA_SELL_PEEL
+    // whole groups of PF steps whose refills and next gathers all exist: no
+    // per-step tests
+    for (; t0 + 2 * PF <= steps; t0 += PF) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + u;
+        const float4 vv = v[u];
+        c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+        v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+        const float4 xx = xg;
+        xg = gather4(x, sell_cols(c[(u + 1) % PF]));
+        a0 = fmaf(vv.x, xx.x, a0);
+        a1 = fmaf(vv.y, xx.y, a1);
+        a0 = fmaf(vv.z, xx.z, a0);
+        a1 = fmaf(vv.w, xx.w, a1);
+      }
+    }
+#endif
+    for (; t0 < steps; t0 += PF) {
 #pragma unroll
       for (int u = 0; u < PF; ++u) {
         const int t = t0 + u;
