@@ -467,7 +467,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
     omegas = rng.choice([0.5, 1.0], n_requests)
     info, lat, per_geom = {}, [], {nm: [] for nm in SERVE_GEOMS}
     done_iters, stopped = 0, 0
-    nxt, steps = 0, 0
+    nxt, rounds = 0, 0
     t0 = time.perf_counter()
     while True:
         now = time.perf_counter() - t0
@@ -479,7 +479,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
             info[srv.submit(gids[nm], x.g, x.gamma, p)] = (arrivals[nxt], nm)
             nxt += 1
         pending = srv.step()
-        steps += 1
+        rounds += 1
         t_seen = time.perf_counter() - t0
         for rid in list(info):
             if srv.poll(rid).state == AP.APPGA_REQ_DONE:
@@ -503,7 +503,8 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
         "workload": f"Poisson stream of {n_requests} requests at {rate:g}/s mixing 128^2 (90x185), "
                     "256^2 (180x367) and 400^2 (288x575) slices, 200..800 iterations each or "
                     "relative objective change < 1e-7, omega 0.5/1.0, counts log-uniform 1e5..1e7",
-        "requests": n_requests, "rate_per_s": rate, "elapsed_s": elapsed, "steps": steps,
+        "requests": n_requests, "rate_per_s": rate, "elapsed_s": elapsed,
+        "scheduling_rounds": rounds,
         "slices_iters_per_s": done_iters / elapsed, "slice_iters": done_iters,
         "stopped_early": stopped,
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),

@@ -1,6 +1,15 @@
 // Continuous-batching reconstruction server (appga_server.h): pools of
 // batched solvers per geometry, admission at step boundaries by free device
 // memory, retirement of finished slots, per-request latency.
+//
+// Every pool has its own stream, so the replays of different pools (and of
+// different geometries) overlap on the device.  A scheduling round never
+// waits for a pool that is still running: a pool's replay ends with a copy
+// of its slot states to pinned memory and an event; the round handles the
+// pools whose event has completed (retires their finished slots, admits
+// waiting requests into them, starts their next replay) and leaves the
+// others running.  Retirement copies results out asynchronously and
+// completes in a later round, once that copy has landed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,6 +52,14 @@ struct Pool {
   BFwdArgs fa{};
   BPixArgs pa{};
   cudaGraphExec_t gexec = nullptr;
+  cudaStream_t stream = nullptr;  // all of this pool's work
+  cudaEvent_t ev_snap = nullptr;  // the slot-state copy after a replay has landed
+  cudaEvent_t ev_out = nullptr;   // the retired images have landed in h_out
+  bool inflight = false;          // a replay (and its slot-state copy) is running
+  bool retiring = false;          // retired images on their way to h_out
+  std::vector<int64_t> ret_ids;   // requests of the images on their way
+  std::vector<SlotState> ret_fin; // their final slot states
+  int ret_flags = 0;
   std::vector<int64_t> slot_req;  // request id per slot, -1 = free
   int used = 0;
   int gstep = 0;  // global step of the pool, as last read back
@@ -53,9 +70,9 @@ struct Pool {
   float* h_out = nullptr; // pinned mirror
   int* d_ids = nullptr;   // [3 Kp]: admitted slots | slots with f_init | retired slots
   int* h_ids = nullptr;   // pinned mirror
-  bool ran = false;
 
   int free_slots() const { return (int)slot_req.size() - used; }
+  bool idle() const { return !inflight; }
 };
 
 struct Geometry {
@@ -71,7 +88,13 @@ int64_t pool_bytes(const appga_matrix* M, int Kp) {
 
 void free_pool(Pool* P) {
   if (!P) return;
+  if (P->stream) cudaStreamSynchronize(P->stream);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->ev_snap) cudaEventDestroy(P->ev_snap);
+  if (P->ev_out) cudaEventDestroy(P->ev_out);
+  if (P->stream) cudaStreamDestroy(P->stream);
+  P->stream = nullptr;
+  P->ev_snap = P->ev_out = nullptr;
   free_batch_workspace(&P->b);
   cudaFree(P->d_in);
   cudaFree(P->d_out);
@@ -118,7 +141,6 @@ struct appga_server {
   int64_t submitted = 0, completed = 0, slice_iters = 0, waiting = 0, running = 0;
   std::vector<double> latencies, queue_waits;
   Clock::time_point t0;
-  cudaEvent_t ev = nullptr;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -137,7 +159,10 @@ appga_status create_pool(appga_server* S, int geom, int Kp, Pool** out) {
   if (e != cudaSuccess) return cuda_fail(e, "server pool workspace");
   const size_t in_len = (size_t)Kp * (2 * (size_t)M->m + M->d);
   const size_t out_len = (size_t)Kp * M->d;
-  e = dalloc(&P->d_in, in_len);
+  e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_snap, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = dalloc(&P->d_in, in_len);
   if (e == cudaSuccess) e = dalloc(&P->d_out, out_len);
   if (e == cudaSuccess) e = dalloc(&P->d_ids, (size_t)3 * Kp);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&P->h_in, in_len * sizeof(float));
@@ -150,7 +175,7 @@ appga_status create_pool(appga_server* S, int geom, int Kp, Pool** out) {
   const bool bf16 = S->cfg.a_precision == APPGA_PREC_BF16;
   make_batch_args(M->A, M->At, bf16 ? M->inv_lambda_bf16 : M->inv_lambda, M->n, P->b, bf16,
                   true, tuned_schedule(M, Kp, bf16), &P->fa, &P->pa);
-  cudaStream_t s = S->ctx->stream;
+  cudaStream_t s = P->stream;
   // every slot starts empty; the ring starts at step 1
   appga_params def;
   appga_params_default(&def);
@@ -225,11 +250,12 @@ bool pool_fits(appga_server* S, int geom, int Kp) {
   return (int64_t)free_b - S->cfg.hbm_reserve_bytes >= need;
 }
 
-// Releases every pool that holds no request (other than `keep_geom`'s).
+// Releases every pool that holds no request (other than `keep_geom`'s) and
+// has no work in flight (a replay, or retired images on their way out).
 bool release_empty_pools(appga_server* S, int keep_geom) {
   bool any = false;
   for (auto& q : S->pools) {
-    if (q && q->used == 0 && q->geom != keep_geom) {
+    if (q && q->used == 0 && q->geom != keep_geom && !q->inflight && !q->retiring) {
       S->bytes -= q->bytes;
       free_pool(q.get());
       q.reset();
@@ -241,11 +267,13 @@ bool release_empty_pools(appga_server* S, int keep_geom) {
 
 // Admits up to `count` waiting requests of the pool's geometry into its free
 // slots and runs their first forward phase (mode 2 of the forward kernel).
+// The pool is idle: its last replay's slot states have landed, so P->gstep
+// is its ring position and its staging buffers are free.
 appga_status admit(appga_server* S, Pool* P, int count) {
   Geometry& G = S->geoms[P->geom];
   const appga_matrix* M = G.M;
   const int Kp = P->b.Kp, m = M->m, d = M->d;
-  cudaStream_t s = S->ctx->stream;
+  cudaStream_t s = P->stream;
   std::vector<int64_t> ids;
   ids.reserve(count);
   int slot = 0;
@@ -323,10 +351,19 @@ appga_status admit_all(appga_server* S) {
     Geometry& G = S->geoms[gi];
     bool released = false;
     while (!G.waiting.empty()) {
-      // the narrowest pool of this geometry with a free slot
+      // the narrowest idle pool of this geometry with a free slot; a pool of
+      // the geometry that is running takes the requests once its replay ends
       Pool* P = nullptr;
-      for (auto& q : S->pools)
-        if (q && q->geom == gi && q->free_slots() > 0 && (!P || q->b.Kp < P->b.Kp)) P = q.get();
+      bool busy = false;
+      for (auto& q : S->pools) {
+        if (!q || q->geom != gi || q->free_slots() == 0) continue;
+        if (!q->idle()) {
+          busy = true;
+          continue;
+        }
+        if (!P || q->b.Kp < P->b.Kp) P = q.get();
+      }
+      if (!P && busy) break;
       if (!P) {
         const int width = new_pool_width(S, gi);
         if (!pool_fits(S, gi, width)) {
@@ -344,10 +381,14 @@ appga_status admit_all(appga_server* S) {
   return APPGA_OK;
 }
 
-appga_status retire(appga_server* S, Pool* P) {
+// First half of a retirement, right after the pool's slot states have
+// landed: the finished slots' images are gathered out and copied to pinned
+// memory on the pool's stream, the slots are reset and freed (an admission
+// enqueued after this may reuse them), and the copy's event is recorded.
+appga_status retire_begin(appga_server* S, Pool* P) {
   const appga_matrix* M = S->geoms[P->geom].M;
   const int Kp = P->b.Kp, d = M->d;
-  cudaStream_t s = S->ctx->stream;
+  cudaStream_t s = P->stream;
   const BatchState& bs = *P->b.bst_host;
   P->gstep = bs.gstep;
   std::vector<int> slots;
@@ -369,39 +410,81 @@ appga_status retire(appga_server* S, Pool* P) {
                      s));
   appga_params def;
   appga_params_default(&def);
-  std::vector<SlotState> fin(K);
+  P->ret_ids.resize(K);
+  P->ret_fin.resize(K);
+  P->ret_flags = bs.flags;
   for (int k = 0; k < K; ++k) {
-    fin[k] = P->b.slots_host[slots[k]];
+    P->ret_fin[k] = P->b.slots_host[slots[k]];
+    P->ret_ids[k] = P->slot_req[slots[k]];
     P->b.slots_host[slots[k]] = slot_from_params(&def, 1, false);
     CK(cudaMemcpyAsync(P->b.slots + slots[k], P->b.slots_host + slots[k], sizeof(SlotState),
                        cudaMemcpyHostToDevice, s));
+    P->slot_req[slots[k]] = -1;
   }
-  CK(cudaStreamSynchronize(s));
+  CK(cudaEventRecord(P->ev_out, s));
+  P->used -= K;
+  P->retiring = true;
+  return APPGA_OK;
+}
+
+// Second half, once the images have landed in h_out: results and statistics
+// of the retired requests.
+void retire_finish(appga_server* S, Pool* P) {
+  const int d = S->geoms[P->geom].M->d;
   const double t = S->now();
+  const int K = (int)P->ret_ids.size();
   for (int k = 0; k < K; ++k) {
-    const SlotState& sl = fin[k];
-    const int64_t id = P->slot_req[slots[k]];
-    Request& R = S->reqs[id];
+    const SlotState& sl = P->ret_fin[k];
+    Request& R = S->reqs[P->ret_ids[k]];
     R.f.assign(P->h_out + (size_t)k * d, P->h_out + (size_t)(k + 1) * d);
     R.st.state = APPGA_REQ_DONE;
     R.st.iters = sl.result_k - sl.k0;
     R.st.result_k = sl.result_k;
     R.st.stopped_early = sl.stopped_early;
-    R.st.flags = bs.flags;
+    R.st.flags = P->ret_flags;
     R.st.phi_k = sl.phi_k;
     R.st.phi_last = sl.phi_k >= 0 ? sl.phi_cur : kNaN;
     R.st.guard_hits = (int64_t)sl.guard_hits;
     R.st.t_done = t;
     R.pool = -1;
     R.slot = -1;
-    P->slot_req[slots[k]] = -1;
     S->latencies.push_back(t - R.st.t_submit);
     S->queue_waits.push_back(R.st.t_admit - R.st.t_submit);
     S->slice_iters += R.st.iters;
   }
-  P->used -= K;
   S->running -= K;
   S->completed += K;
+  P->ret_ids.clear();
+  P->ret_fin.clear();
+  P->retiring = false;
+}
+
+// Handles the pools whose work has landed; true if any had.
+appga_status progress(appga_server* S, bool* any) {
+  *any = false;
+  for (auto& q : S->pools) {
+    if (!q) continue;
+    if (q->retiring) {
+      const cudaError_t e = cudaEventQuery(q->ev_out);
+      if (e == cudaSuccess) {
+        retire_finish(S, q.get());
+        *any = true;
+      } else if (e != cudaErrorNotReady) {
+        return cuda_fail(e, "server retirement");
+      }
+    }
+    if (q->inflight && !q->retiring) {
+      const cudaError_t e = cudaEventQuery(q->ev_snap);
+      if (e == cudaSuccess) {
+        q->inflight = false;
+        *any = true;
+        appga_status rc = retire_begin(S, q.get());
+        if (rc != APPGA_OK) return rc;
+      } else if (e != cudaErrorNotReady) {
+        return cuda_fail(e, "server replay");
+      }
+    }
+  }
   return APPGA_OK;
 }
 
@@ -435,10 +518,6 @@ extern "C" appga_status appga_server_create(appga_ctx* ctx, const appga_server_c
   S->ctx = ctx;
   S->cfg = *cfg;
   S->t0 = Clock::now();
-  if (cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) != cudaSuccess) {
-    delete S;
-    return fail(APPGA_ECUDA, "cudaEventCreate failed");
-  }
   *out = S;
   return APPGA_OK;
 }
@@ -448,7 +527,6 @@ extern "C" appga_status appga_server_destroy(appga_server* S) {
   cudaStreamSynchronize(S->ctx->stream);
   for (auto& q : S->pools)
     if (q) free_pool(q.get());
-  if (S->ev) cudaEventDestroy(S->ev);
   delete S;
   return APPGA_OK;
 }
@@ -513,27 +591,42 @@ extern "C" appga_status appga_server_submit(appga_server* S, int32_t geometry,
 extern "C" appga_status appga_server_step(appga_server* S, int32_t* pending_out) {
   if (!S) return fail(APPGA_EINVAL, "null argument");
   if (cudaSetDevice(S->ctx->device) != cudaSuccess) return fail(APPGA_ENODEV, "cudaSetDevice failed");
-  cudaStream_t s = S->ctx->stream;
-  appga_status rc = admit_all(S);
-  if (rc != APPGA_OK) return rc;
-  // one replay per pool that holds requests, back to back on the stream
+  // retirements and replays that have landed
   bool any = false;
+  appga_status rc = progress(S, &any);
+  if (rc != APPGA_OK) return rc;
+  // waiting requests into idle pools (or new pools)
+  if ((rc = admit_all(S)) != APPGA_OK) return rc;
+  // the next replay of every idle pool that holds requests, each on its own
+  // stream, ending with a copy of its slot states and an event
+  bool running = false, launched = false;
   for (auto& q : S->pools) {
     if (!q) continue;
-    q->ran = q->used > 0;
-    if (!q->ran) continue;
-    any = true;
-    CK(cudaGraphLaunch(q->gexec, s));
-    CK(cudaMemcpyAsync(q->b.slots_host, q->b.slots, q->b.Kp * sizeof(SlotState),
-                       cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(q->b.bst_host, q->b.bst, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+    if (q->idle() && q->used > 0) {
+      launched = true;
+      CK(cudaGraphLaunch(q->gexec, q->stream));
+      CK(cudaMemcpyAsync(q->b.slots_host, q->b.slots, q->b.Kp * sizeof(SlotState),
+                         cudaMemcpyDeviceToHost, q->stream));
+      CK(cudaMemcpyAsync(q->b.bst_host, q->b.bst, sizeof(BatchState), cudaMemcpyDeviceToHost,
+                         q->stream));
+      CK(cudaEventRecord(q->ev_snap, q->stream));
+      q->inflight = true;
+    }
+    running |= q->inflight || q->retiring;
   }
-  if (any) {
-    CK(cudaEventRecord(S->ev, s));
-    CK(cudaEventSynchronize(S->ev));
+  // nothing landed or started in this round: wait for the pending work of
+  // one pool instead of returning straight into another poll
+  if (!any && !launched && running) {
     for (auto& q : S->pools) {
-      if (!q || !q->ran) continue;
-      if ((rc = retire(S, q.get())) != APPGA_OK) return rc;
+      if (!q) continue;
+      if (q->retiring) {
+        CK(cudaEventSynchronize(q->ev_out));
+        break;
+      }
+      if (q->inflight) {
+        CK(cudaEventSynchronize(q->ev_snap));
+        break;
+      }
     }
   }
   if (pending_out) *pending_out = (int32_t)(S->waiting + S->running);
