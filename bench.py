@@ -79,6 +79,8 @@ def parse():
                     help="run only the serving leg and print its JSON (for tuning)")
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE,
                     help="Poisson arrival rate of the serving stream (requests/s)")
+    ap.add_argument("--serve-max-pools", type=int, default=0,
+                    help="cap on the server's live pools (0: none)")
     return ap.parse_args()
 
 
@@ -436,7 +438,7 @@ def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
 
 
 def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
-                  slots: int = SERVE_SLOTS, steps: int = SERVE_STEPS):
+                  slots: int = SERVE_SLOTS, steps: int = SERVE_STEPS, max_pools: int = 0):
     """Poisson stream of reconstruction requests mixing 128^2, 256^2 and 400^2
     slices (200..800 iterations each, or the relative objective change
     < 1e-7) through the continuous-batching server."""
@@ -451,7 +453,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
         counts = W.log_uniform_counts(rng, 1e5, 1e7, 6)
         slices[nm] = [W.make_slice(A, geom, float(c), W.seed_for(4, 100 * idx + i),
                                    phantom="lesions") for i, c in enumerate(counts)]
-    srv = AP.Server(ctx, slots_per_pool=slots, steps_per_launch=steps)
+    srv = AP.Server(ctx, slots_per_pool=slots, steps_per_launch=steps, max_pools=max_pools)
     gids = {nm: srv.add_geometry(mats[nm]) for nm in SERVE_GEOMS}
     # warm-up: one short request per geometry (pools and graphs are created here)
     for nm in SERVE_GEOMS:
@@ -515,6 +517,8 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
         "latency_from": "arrival time of the request in the stream (the server's own figures "
                         "count from submission)",
         "pools": summ.pools, "device_bytes": summ.device_bytes, "slots_per_pool": slots,
+        "slot_occupancy": summ.live_slot_steps / max(summ.pool_slot_steps, 1),
+        "replay_seconds_over_elapsed": summ.replay_seconds / elapsed,
         "steps_per_launch": steps,
     }
 
@@ -623,7 +627,8 @@ def run_ours(args):
     if args.serve_only:
         print(json.dumps({"serving": bench_serving(AP, ctx, args.serve_requests, args.serve_rate,
                                                    geom, A, args.serve_slots,
-                                                   args.serve_steps)}), flush=True)
+                                                   args.serve_steps,
+                                                   args.serve_max_pools)}), flush=True)
         ctx.close()
         return 0
     mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)

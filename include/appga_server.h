@@ -42,10 +42,18 @@
  * request's pool width depends on the load, and images of the same request
  * agree to FP32 rounding across widths.)
  *
- * Threading: a server is driven by one host thread at a time; every call
- * below runs on the library stream of the server's context and
- * appga_server_step synchronises with it.  Pointers named *_host are host
- * memory; the server copies what it needs during the call.
+ * Streams: every pool has its own stream, so the replays of different pools
+ * (and geometries) overlap on the device.  A scheduling round
+ * (appga_server_step) handles the pools whose last replay has landed --
+ * retiring their finished slots, admitting waiting requests into them and
+ * starting their next replay -- and leaves running pools alone; it blocks
+ * only when no pool's work landed and none started.  A retirement copies the
+ * finished images out asynchronously and completes (state DONE) in a later
+ * round.
+ *
+ * Threading: a server is driven by one host thread at a time.  Pointers
+ * named *_host are host memory; the server copies what it needs during the
+ * call.
  */
 #ifndef APPGA_SERVER_H
 #define APPGA_SERVER_H
@@ -98,6 +106,13 @@ typedef struct {
   double p50_latency_s, p99_latency_s; /* completion minus submission (nearest rank) */
   double mean_latency_s, max_latency_s;
   double mean_queue_s;   /* admission minus submission, mean over completed */
+  /* occupancy: slot-steps the pools ran (pool width x maps per replay, over
+   * every replay) and, of those, the slot-steps of slots holding a request
+   * when the replay started; device seconds of the replays (each from its
+   * start to its slot-state copy, summed over pools, so overlapping replays
+   * of different pools add up) */
+  int64_t pool_slot_steps, live_slot_steps;
+  double replay_seconds;
 } appga_server_summary;
 
 /* appga_server_create: EINVAL for a bad config (slots_per_pool not 0, 32, 64

@@ -115,7 +115,8 @@ class appga_server_summary(ctypes.Structure):
         ("pad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
         ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
         ("mean_latency_s", ctypes.c_double), ("max_latency_s", ctypes.c_double),
-        ("mean_queue_s", ctypes.c_double),
+        ("mean_queue_s", ctypes.c_double), ("pool_slot_steps", ctypes.c_int64),
+        ("live_slot_steps", ctypes.c_int64), ("replay_seconds", ctypes.c_double),
     ]
 
 

@@ -54,6 +54,7 @@ struct Pool {
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t stream = nullptr;  // all of this pool's work
   cudaEvent_t ev_snap = nullptr;  // the slot-state copy after a replay has landed
+  cudaEvent_t ev_start = nullptr; // start of the replay (timing)
   cudaEvent_t ev_out = nullptr;   // the retired images have landed in h_out
   bool inflight = false;          // a replay (and its slot-state copy) is running
   bool retiring = false;          // retired images on their way to h_out
@@ -91,10 +92,11 @@ void free_pool(Pool* P) {
   if (P->stream) cudaStreamSynchronize(P->stream);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->ev_snap) cudaEventDestroy(P->ev_snap);
+  if (P->ev_start) cudaEventDestroy(P->ev_start);
   if (P->ev_out) cudaEventDestroy(P->ev_out);
   if (P->stream) cudaStreamDestroy(P->stream);
   P->stream = nullptr;
-  P->ev_snap = P->ev_out = nullptr;
+  P->ev_snap = P->ev_out = P->ev_start = nullptr;
   free_batch_workspace(&P->b);
   cudaFree(P->d_in);
   cudaFree(P->d_out);
@@ -139,6 +141,8 @@ struct appga_server {
   int64_t next_id = 1;
   int64_t bytes = 0;
   int64_t submitted = 0, completed = 0, slice_iters = 0, waiting = 0, running = 0;
+  int64_t pool_slot_steps = 0, live_slot_steps = 0;
+  double replay_seconds = 0.0;
   std::vector<double> latencies, queue_waits;
   Clock::time_point t0;
 
@@ -160,7 +164,8 @@ appga_status create_pool(appga_server* S, int geom, int Kp, Pool** out) {
   const size_t in_len = (size_t)Kp * (2 * (size_t)M->m + M->d);
   const size_t out_len = (size_t)Kp * M->d;
   e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_snap, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->ev_snap);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->ev_start);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = dalloc(&P->d_in, in_len);
   if (e == cudaSuccess) e = dalloc(&P->d_out, out_len);
@@ -478,6 +483,9 @@ appga_status progress(appga_server* S, bool* any) {
       if (e == cudaSuccess) {
         q->inflight = false;
         *any = true;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q->ev_start, q->ev_snap) == cudaSuccess)
+          S->replay_seconds += 1e-3 * ms;
         appga_status rc = retire_begin(S, q.get());
         if (rc != APPGA_OK) return rc;
       } else if (e != cudaErrorNotReady) {
@@ -604,6 +612,9 @@ extern "C" appga_status appga_server_step(appga_server* S, int32_t* pending_out)
     if (!q) continue;
     if (q->idle() && q->used > 0) {
       launched = true;
+      S->pool_slot_steps += (int64_t)q->b.Kp * S->cfg.steps_per_launch;
+      S->live_slot_steps += (int64_t)q->used * S->cfg.steps_per_launch;
+      CK(cudaEventRecord(q->ev_start, q->stream));
       CK(cudaGraphLaunch(q->gexec, q->stream));
       CK(cudaMemcpyAsync(q->b.slots_host, q->b.slots, q->b.Kp * sizeof(SlotState),
                          cudaMemcpyDeviceToHost, q->stream));
@@ -677,5 +688,8 @@ extern "C" appga_status appga_server_get_summary(const appga_server* S, appga_se
   out->mean_latency_s = n ? sum / (double)n : kNaN;
   out->max_latency_s = n ? mx : kNaN;
   out->mean_queue_s = n ? qs / (double)n : kNaN;
+  out->pool_slot_steps = S->pool_slot_steps;
+  out->live_slot_steps = S->live_slot_steps;
+  out->replay_seconds = S->replay_seconds;
   return APPGA_OK;
 }
