@@ -49,6 +49,8 @@ SERVE_GEOMS = ("128", "256", "400")
 SERVE_RATE = 100.0
 SERVE_SLOTS = 0  # adaptive pool widths (32 / 64 / 128 slots by demand)
 SERVE_STEPS = 8
+SAT_RATE = 400.0      # requests/s of the saturated serving leg
+SAT_REQUESTS = 1500
 
 
 def parse():
@@ -81,6 +83,8 @@ def parse():
                     help="Poisson arrival rate of the serving stream (requests/s)")
     ap.add_argument("--serve-max-pools", type=int, default=0,
                     help="cap on the server's live pools (0: none)")
+    ap.add_argument("--serve-geom-pools", type=int, default=2,
+                    help="cap on the server's live pools per geometry (0: none)")
     return ap.parse_args()
 
 
@@ -438,7 +442,8 @@ def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
 
 
 def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
-                  slots: int = SERVE_SLOTS, steps: int = SERVE_STEPS, max_pools: int = 0):
+                  slots: int = SERVE_SLOTS, steps: int = SERVE_STEPS, max_pools: int = 0,
+                  geom_pools: int = 2):
     """Poisson stream of reconstruction requests mixing 128^2, 256^2 and 400^2
     slices (200..800 iterations each, or the relative objective change
     < 1e-7) through the continuous-batching server."""
@@ -453,7 +458,8 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
         counts = W.log_uniform_counts(rng, 1e5, 1e7, 6)
         slices[nm] = [W.make_slice(A, geom, float(c), W.seed_for(4, 100 * idx + i),
                                    phantom="lesions") for i, c in enumerate(counts)]
-    srv = AP.Server(ctx, slots_per_pool=slots, steps_per_launch=steps, max_pools=max_pools)
+    srv = AP.Server(ctx, slots_per_pool=slots, steps_per_launch=steps, max_pools=max_pools,
+                    max_pools_per_geometry=geom_pools)
     gids = {nm: srv.add_geometry(mats[nm]) for nm in SERVE_GEOMS}
     # warm-up: one short request per geometry (pools and graphs are created here)
     for nm in SERVE_GEOMS:
@@ -468,6 +474,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
     iters = rng.integers(200, 801, n_requests)
     omegas = rng.choice([0.5, 1.0], n_requests)
     info, lat, per_geom = {}, [], {nm: [] for nm in SERVE_GEOMS}
+    finished = []  # (completion time, iterations) of every request
     done_iters, stopped = 0, 0
     nxt, rounds = 0, 0
     t0 = time.perf_counter()
@@ -489,6 +496,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
                 _, st = srv.collect(rid)
                 lat.append(t_seen - a)  # from the request's arrival
                 per_geom[nm].append(t_seen - a)
+                finished.append((t_seen, st.iters))
                 done_iters += st.iters
                 stopped += st.stopped_early
         if nxt >= n_requests and pending == 0:
@@ -501,6 +509,12 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
     for m in mats.values():
         m.close()
     lat = np.asarray(lat)
+    # steady state: iterations of the requests completed between the arrival
+    # of the first fifth of the stream and the last arrival (the queue is
+    # still being fed there; the drain after the last arrival is left out)
+    w0, w1 = float(arrivals[n_requests // 5]), float(arrivals[-1])
+    in_win = sum(n for t, n in finished if w0 <= t <= w1)
+    steady = in_win / (w1 - w0) if w1 > w0 else float("nan")
     return {
         "workload": f"Poisson stream of {n_requests} requests at {rate:g}/s mixing 128^2 (90x185), "
                     "256^2 (180x367) and 400^2 (288x575) slices, 200..800 iterations each or "
@@ -508,6 +522,8 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
         "requests": n_requests, "rate_per_s": rate, "elapsed_s": elapsed,
         "scheduling_rounds": rounds,
         "slices_iters_per_s": done_iters / elapsed, "slice_iters": done_iters,
+        "steady_slices_iters_per_s": steady,
+        "steady_window_s": [w0, w1],
         "stopped_early": stopped,
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "mean_latency_s": float(lat.mean()),
@@ -517,6 +533,7 @@ def bench_serving(AP, ctx, n_requests: int, rate: float, main_geom, main_A,
         "latency_from": "arrival time of the request in the stream (the server's own figures "
                         "count from submission)",
         "pools": summ.pools, "device_bytes": summ.device_bytes, "slots_per_pool": slots,
+        "max_pools_per_geometry": geom_pools,
         "slot_occupancy": summ.live_slot_steps / max(summ.pool_slot_steps, 1),
         "replay_seconds_over_elapsed": summ.replay_seconds / elapsed,
         "steps_per_launch": steps,
@@ -628,7 +645,8 @@ def run_ours(args):
         print(json.dumps({"serving": bench_serving(AP, ctx, args.serve_requests, args.serve_rate,
                                                    geom, A, args.serve_slots,
                                                    args.serve_steps,
-                                                   args.serve_max_pools)}), flush=True)
+                                                   args.serve_max_pools,
+                                                   args.serve_geom_pools)}), flush=True)
         ctx.close()
         return 0
     mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
@@ -771,9 +789,13 @@ def run_ours(args):
         if batched:  # the volume runs the batched kernels' default schedule
             brate = {k: batched[k]["slices_iters_per_s"] for k in ("fp32", "bf16")}
         volume = bench_volume(AP, ctx, geom, A, dev, brate)
+    serving_sat = None
     if world == 1 and not args.no_serve:
         serving = bench_serving(AP, ctx, args.serve_requests, args.serve_rate, geom, A,
                                 args.serve_slots, args.serve_steps)
+        # an arrival rate above what the server completes: its saturated throughput
+        serving_sat = bench_serving(AP, ctx, SAT_REQUESTS, SAT_RATE, geom, A, args.serve_slots,
+                                    args.serve_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -804,6 +826,7 @@ def run_ours(args):
             "volume": volume,
             "afppa": afppa,
             "serving": serving,
+            "serving_saturated": serving_sat,
         }
         print(json.dumps(line), flush=True)
     mat.close()

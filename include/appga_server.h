@@ -74,10 +74,15 @@ typedef struct {
   int32_t max_pools;         /* cap on live pools over all geometries; 0 = none */
   int64_t hbm_budget_bytes;  /* cap on device bytes held by pools; 0 = none */
   int64_t hbm_reserve_bytes; /* device memory a new pool must leave free */
+  int32_t max_pools_per_geometry; /* cap on live pools of one geometry; 0 = none.
+                                     Under load more pools of a geometry stream its
+                                     matrix more often and contend for the device;
+                                     requests beyond the cap wait for free slots */
+  int32_t pad;
 } appga_server_config;
 
 /* Defaults: 64 slots per pool, 8 maps per launch, FP32, no pool cap, no
- * budget, 1 GiB reserve. */
+ * budget, 1 GiB reserve, 2 pools per geometry. */
 void appga_server_config_default(appga_server_config* cfg);
 
 /* Request states. */

@@ -96,6 +96,7 @@ class appga_server_config(ctypes.Structure):
         ("slots_per_pool", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
         ("a_precision", ctypes.c_int32), ("max_pools", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_int64), ("hbm_reserve_bytes", ctypes.c_int64),
+        ("max_pools_per_geometry", ctypes.c_int32), ("pad", ctypes.c_int32),
     ]
 
 

@@ -248,6 +248,11 @@ int new_pool_width(const appga_server* S, int geom) {
 // device memory.
 bool pool_fits(appga_server* S, int geom, int Kp) {
   if (S->cfg.max_pools > 0 && live_pools(S) >= S->cfg.max_pools) return false;
+  if (S->cfg.max_pools_per_geometry > 0) {
+    int mine = 0;
+    for (const auto& q : S->pools) mine += (q && q->geom == geom) ? 1 : 0;
+    if (mine >= S->cfg.max_pools_per_geometry) return false;
+  }
   const int64_t need = pool_bytes(S->geoms[geom].M, Kp);
   if (S->cfg.hbm_budget_bytes > 0 && S->bytes + need > S->cfg.hbm_budget_bytes) return false;
   size_t free_b = 0, total_b = 0;
@@ -507,6 +512,7 @@ extern "C" void appga_server_config_default(appga_server_config* cfg) {
   cfg->max_pools = 0;
   cfg->hbm_budget_bytes = 0;
   cfg->hbm_reserve_bytes = 1LL << 30;
+  cfg->max_pools_per_geometry = 2;
 }
 
 extern "C" appga_status appga_server_create(appga_ctx* ctx, const appga_server_config* cfg,
@@ -519,7 +525,8 @@ extern "C" appga_status appga_server_create(appga_ctx* ctx, const appga_server_c
   if (cfg->steps_per_launch < 1) return fail(APPGA_EINVAL, "steps_per_launch must be >= 1");
   if (cfg->a_precision != APPGA_PREC_FP32 && cfg->a_precision != APPGA_PREC_BF16)
     return fail(APPGA_EINVAL, "a_precision must be APPGA_PREC_FP32 or APPGA_PREC_BF16");
-  if (cfg->max_pools < 0 || cfg->hbm_budget_bytes < 0 || cfg->hbm_reserve_bytes < 0)
+  if (cfg->max_pools < 0 || cfg->hbm_budget_bytes < 0 || cfg->hbm_reserve_bytes < 0 ||
+      cfg->max_pools_per_geometry < 0)
     return fail(APPGA_EINVAL, "negative pool cap or memory size");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(APPGA_ENODEV, "cudaSetDevice failed");
   auto* S = new appga_server();
