@@ -276,6 +276,8 @@ def bench_batched(AP, ctx, geom, A, dev, single_rate, K=BATCH_K, lo=1e5, hi=1e7,
         tuned = measure(prec)
         tuned["schedule"] = {"spmv_per_sm": t.spmv_per_sm, "pixel_per_sm": t.pixel_per_sm,
                              "stencil_per_sm": t.stencil_per_sm, "chunk": t.chunk,
+                             "gather_rows_fw": t.gather_rows_fw,
+                             "gather_rows_px": t.gather_rows_px,
                              "trial_us_per_slice_iter": t.us_per_slice_iter,
                              "trial_us_default": t.us_per_slice_iter_default}
         out[name + "_autotuned"] = tuned

@@ -331,7 +331,10 @@ appga_status appga_reconstruct_volume(appga_ctx* ctx, const appga_matrix* mat, i
  * and is timed with CUDA events on the library stream.  Tunables, searched
  * one after another from the kernels' defaults: the sub-batch width (run K
  * slices as several batches of 32 or 64), SpMV blocks per SM of the forward
- * phase, blocks per SM of the back-projection, stencil blocks per SM.  The
+ * phase, blocks per SM of the back-projection, stencil blocks per SM, and for
+ * each projection the rows it gathers per step of its staged (column, value)
+ * pairs (8, or 4: fewer loads in flight, fewer registers; separate kernel
+ * instances).  The
  * best schedule is kept in the matrix handle and used by later
  * appga_reconstruct_batched calls (and server pools) with the same padded
  * width (32, 64 or 128) and precision.  out_host (may be NULL) receives the
@@ -347,6 +350,8 @@ typedef struct {
   int32_t stencil_per_sm; /* 0 = kernel default */
   int32_t pixel_per_sm;   /* 0 = kernel default */
   int32_t chunk;          /* slices per sub-batch; 0 = the whole batch */
+  int32_t gather_rows_fw; /* image rows the forward projection gathers per step: 8 or 4 (0 = 8) */
+  int32_t gather_rows_px; /* weight rows the back-projection gathers per step: 8 or 4 (0 = 8) */
   double us_per_slice_iter;         /* chosen schedule, microseconds per slice-iteration */
   double us_per_slice_iter_default; /* the default schedule */
 } appga_batch_tuning;
@@ -355,9 +360,10 @@ appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matrix* mat, int
                                     const appga_params* params, appga_batch_tuning* out_host);
 /* Reads / sets the schedule kept for (tuning->K's padded width,
  * tuning->a_precision), e.g. to reuse a tuning saved by an earlier process;
- * only K, a_precision and the four schedule fields are used (values per SM
- * in [0, 16], 0 = default; chunk 0, 32 or 64).  get fills the schedule
- * fields (zeros if none is kept).  EINVAL for values out of range. */
+ * only K, a_precision and the six schedule fields are used (values per SM
+ * in [0, 16], 0 = default; chunk 0, 32 or 64; gather rows 0, 4 or 8).  get
+ * fills the schedule fields (zeros if none is kept).  EINVAL for values out
+ * of range. */
 appga_status appga_batch_schedule_get(const appga_matrix* mat, appga_batch_tuning* tuning_host);
 appga_status appga_batch_schedule_set(appga_matrix* mat, const appga_batch_tuning* tuning_host);
 

@@ -71,7 +71,8 @@ class appga_batch_tuning(ctypes.Structure):
     _fields_ = [
         ("K", ctypes.c_int32), ("a_precision", ctypes.c_int32), ("spmv_per_sm", ctypes.c_int32),
         ("stencil_per_sm", ctypes.c_int32), ("pixel_per_sm", ctypes.c_int32),
-        ("chunk", ctypes.c_int32), ("us_per_slice_iter", ctypes.c_double),
+        ("chunk", ctypes.c_int32), ("gather_rows_fw", ctypes.c_int32),
+        ("gather_rows_px", ctypes.c_int32), ("us_per_slice_iter", ctypes.c_double),
         ("us_per_slice_iter_default", ctypes.c_double),
     ]
 

@@ -102,6 +102,7 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
   *fa = BFwdArgs{};
   fa->spmv_per_sm = sch.spmv_per_sm;
   fa->stencil_per_sm = sch.stencil_per_sm;
+  fa->gather_rows = sch.gather_rows_fw;
   fa->A = A;
   fa->n = n;
   fa->Kp = b.Kp;
@@ -119,6 +120,7 @@ void make_batch_args(const DevCSR& A, const DevCSR& At, const float* inv_lambda,
   fa->fpartial = b.fpartial;
   *pa = BPixArgs{};
   pa->blocks_per_sm = sch.pixel_per_sm;
+  pa->gather_rows = sch.gather_rows_px;
   pa->At = At;
   pa->n = n;
   pa->Kp = b.Kp;
@@ -615,6 +617,17 @@ extern "C" appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matri
     cand.stencil_per_sm = v;
     rc = consider(cand);
   }
+  // rows gathered per step by each projection (kernel instances)
+  if (rc == APPGA_OK) {
+    BatchSchedule cand = best;
+    cand.gather_rows_fw = 4;
+    rc = consider(cand);
+  }
+  if (rc == APPGA_OK) {
+    BatchSchedule cand = best;
+    cand.gather_rows_px = 4;
+    rc = consider(cand);
+  }
   for (auto& e : ev) cudaEventDestroy(e);
   cudaFree(f_scratch);
   if (rc != APPGA_OK) return rc;
@@ -627,6 +640,8 @@ extern "C" appga_status appga_autotune_batched(appga_ctx* ctx, const appga_matri
     out_host->stencil_per_sm = best.stencil_per_sm;
     out_host->pixel_per_sm = best.pixel_per_sm;
     out_host->chunk = best.chunk;
+    out_host->gather_rows_fw = best.gather_rows_fw == 0 ? 8 : best.gather_rows_fw;
+    out_host->gather_rows_px = best.gather_rows_px == 0 ? 8 : best.gather_rows_px;
     out_host->us_per_slice_iter = best_us;
     out_host->us_per_slice_iter_default = default_us;
   }
@@ -643,6 +658,8 @@ extern "C" appga_status appga_batch_schedule_get(const appga_matrix* mat,
   t->stencil_per_sm = sch.stencil_per_sm;
   t->pixel_per_sm = sch.pixel_per_sm;
   t->chunk = sch.chunk;
+  t->gather_rows_fw = sch.gather_rows_fw;
+  t->gather_rows_px = sch.gather_rows_px;
   return APPGA_OK;
 }
 
@@ -655,11 +672,15 @@ extern "C" appga_status appga_batch_schedule_set(appga_matrix* mat, const appga_
     if (v < 0 || v > 16) return fail(APPGA_EINVAL, "blocks per SM must be in [0, 16]");
   if (t->chunk != 0 && t->chunk != 32 && t->chunk != 64)
     return fail(APPGA_EINVAL, "chunk must be 0, 32 or 64");
+  for (int v : {t->gather_rows_fw, t->gather_rows_px})
+    if (v != 0 && v != 4 && v != 8) return fail(APPGA_EINVAL, "gather rows must be 0, 4 or 8");
   BatchSchedule sch;
   sch.spmv_per_sm = t->spmv_per_sm;
   sch.stencil_per_sm = t->stencil_per_sm;
   sch.pixel_per_sm = t->pixel_per_sm;
   sch.chunk = t->chunk;
+  sch.gather_rows_fw = t->gather_rows_fw == 8 ? 0 : t->gather_rows_fw;
+  sch.gather_rows_px = t->gather_rows_px == 8 ? 0 : t->gather_rows_px;
   mat->tuned[padded_width(t->K) * 2 + (t->a_precision == APPGA_PREC_BF16 ? 1 : 0)] = sch;
   return APPGA_OK;
 }

@@ -51,7 +51,7 @@ struct BFwdArgs {
   int32_t spmv_per_sm;    // SpMV blocks per SM (0: default); tuned by the autotuner
   int32_t stencil_per_sm; // stencil blocks per SM (0: default)
   int32_t no_stencil;     // volume mode: the 3-D stencil runs in its own kernel
-  int32_t pad;
+  int32_t gather_rows;    // image rows gathered per step: 8 (0: default) or 4; tuned
   float* f[3];
   float* y[2];
   float* w;
@@ -68,6 +68,8 @@ struct BPixArgs {
   int32_t n, Kp;
   int32_t use_bf16;
   int32_t blocks_per_sm;  // 0: default; tuned by the autotuner
+  int32_t gather_rows;    // weight rows gathered per step: 8 (0: default) or 4; tuned
+  int32_t pad;
   float* f[3];
   const float* w;
   const float* gR;

@@ -55,9 +55,12 @@ struct BatchSchedule {
   int stencil_per_sm = 0;  // stencil blocks per SM
   int pixel_per_sm = 0;    // back-projection blocks per SM
   int chunk = 0;           // slices per sub-batch (0: the whole batch at once)
+  int gather_rows_fw = 0;  // rows gathered per step by the forward projection (0: 8)
+  int gather_rows_px = 0;  // rows gathered per step by the back-projection (0: 8)
   bool operator==(const BatchSchedule& o) const {
     return spmv_per_sm == o.spmv_per_sm && stencil_per_sm == o.stencil_per_sm &&
-           pixel_per_sm == o.pixel_per_sm && chunk == o.chunk;
+           pixel_per_sm == o.pixel_per_sm && chunk == o.chunk &&
+           gather_rows_fw == o.gather_rows_fw && gather_rows_px == o.gather_rows_px;
   }
 };
 

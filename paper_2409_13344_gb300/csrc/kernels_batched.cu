@@ -95,10 +95,12 @@ __device__ __forceinline__ void vstore(float* p, const float (&x)[V]) {
 // the V sums of slots lane*V .. lane*V + V - 1.  Each lane loads one of 32
 // (column, value) pairs; the warp stages them in shared memory (the column
 // as an element offset col * Kp) and every lane reads them back four at a
-// time with broadcast loads, gathering 8 image rows per step.  The next 32
-// pairs are loaded while the current ones are consumed.  Products are
-// accumulated in the row's entry order.
-template <int V, bool BF16>
+// time with broadcast loads, gathering GR image rows per step (8 or 4: more
+// loads in flight against fewer registers; a launch-schedule choice).  The
+// next 32 pairs are loaded while the current ones are consumed.  Products
+// are accumulated in the row's entry order whatever GR, so the sums do not
+// depend on it.
+template <int V, bool BF16, int GR = 8>
 __device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* __restrict__ X,
                                          int Kp, int lane, bool lane_on, uint64_t pol,
                                          int* s_off, float* s_val, float (&acc)[V]) {
@@ -126,27 +128,30 @@ __device__ __forceinline__ void brow_dot(const DevCSR& M, int row, const float* 
     }
     if (!lane_on) continue;
     int q = 0;
-    for (; q + 8 <= cnt; q += 8) {
-      const int4 o0 = *reinterpret_cast<const int4*>(s_off + q);
-      const int4 o1 = *reinterpret_cast<const int4*>(s_off + q + 4);
-      const float4 w0 = *reinterpret_cast<const float4*>(s_val + q);
-      const float4 w1 = *reinterpret_cast<const float4*>(s_val + q + 4);
-      float x[8][V];
-      vload<V>(xl + o0.x, x[0]);
-      vload<V>(xl + o0.y, x[1]);
-      vload<V>(xl + o0.z, x[2]);
-      vload<V>(xl + o0.w, x[3]);
-      vload<V>(xl + o1.x, x[4]);
-      vload<V>(xl + o1.y, x[5]);
-      vload<V>(xl + o1.z, x[6]);
-      vload<V>(xl + o1.w, x[7]);
-      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    if constexpr (GR == 8) {
+      for (; q + 8 <= cnt; q += 8) {
+        const int4 o0 = *reinterpret_cast<const int4*>(s_off + q);
+        const int4 o1 = *reinterpret_cast<const int4*>(s_off + q + 4);
+        const float4 w0 = *reinterpret_cast<const float4*>(s_val + q);
+        const float4 w1 = *reinterpret_cast<const float4*>(s_val + q + 4);
+        float x[8][V];
+        vload<V>(xl + o0.x, x[0]);
+        vload<V>(xl + o0.y, x[1]);
+        vload<V>(xl + o0.z, x[2]);
+        vload<V>(xl + o0.w, x[3]);
+        vload<V>(xl + o1.x, x[4]);
+        vload<V>(xl + o1.y, x[5]);
+        vload<V>(xl + o1.z, x[6]);
+        vload<V>(xl + o1.w, x[7]);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int t = 0; t < V; ++t) acc[t] = fmaf(w[u], x[u][t], acc[t]);
+          for (int t = 0; t < V; ++t) acc[t] = fmaf(w[u], x[u][t], acc[t]);
+      }
     }
-    if (q < cnt) {
+    static_assert(GR == 8 || GR == 4, "image rows gathered per step");
+    for (; q < cnt; q += 4) {  // cnt is a multiple of 4 (rows are padded)
       const int4 o0 = *reinterpret_cast<const int4*>(s_off + q);
       const float4 w0 = *reinterpret_cast<const float4*>(s_val + q);
       float x[4][V];
@@ -416,7 +421,7 @@ struct BFwdSmem<true> {
 // ST false: SpMV blocks only (grid n_spmv_blocks); ST true: the SpMV blocks
 // followed by the stencil blocks in one grid, so the stencil blocks fill the
 // SMs as the SpMV blocks finish.
-template <int V, bool BF16, bool ST>
+template <int V, bool BF16, bool ST, int GR>
 __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
   __shared__ __align__(16) int s_off[B_WARPS][32];
   __shared__ __align__(16) float s_val[B_WARPS][32];
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
     for (int row = blockIdx.x * B_WARPS + warp; row < a.A.rows; row += stride) {
 #endif
       float acc[V];
-      brow_dot<V, BF16>(a.A, row, f, Kp, lane, lane_on, pol, s_off[warp], s_val[warp], acc);
+      brow_dot<V, BF16, GR>(a.A, row, f, Kp, lane, lane_on, pol, s_off[warp], s_val[warp], acc);
       if (!lane_on) continue;
       const size_t o = (size_t)row * Kp + lane * V;
       float yp[V], gg[V], gm[V], yo[V], wo[V];
@@ -578,7 +583,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bforward(BFwdArgs a) {
 
 // --------------------------------------------------------------- k_bpixel
 
-template <int V, bool BF16>
+template <int V, bool BF16, int GR>
 __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
   __shared__ __align__(16) int s_off[B_WARPS][32];
   __shared__ __align__(16) float s_val[B_WARPS][32];
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(B_THREADS) k_bpixel(BPixArgs a) {
   for (int j = blockIdx.x * B_WARPS + warp; j < a.At.rows; j += stride) {
 #endif
     float bp[V];
-    brow_dot<V, BF16>(a.At, j, a.w, Kp, lane, lane_live, pol, s_off[warp], s_val[warp], bp);
+    brow_dot<V, BF16, GR>(a.At, j, a.w, Kp, lane, lane_live, pol, s_off[warp], s_val[warp], bp);
     const size_t o = (size_t)j * Kp + lane * V;
     float vk[V], vm[V], gr[V], out[V];
     vload<V>(fk + o, vk);
@@ -938,17 +943,15 @@ cudaError_t bforward_v(const BFwdArgs& a0, cudaStream_t s) {
   int nsp = 0;
   const int grid = bforward_grid_n(a, &nsp);
   a.n_spmv_blocks = nsp;
-  if (grid > nsp) {
-    if (a.use_bf16)
-      k_bforward<V, true, true><<<grid, B_THREADS, 0, s>>>(a);
-    else
-      k_bforward<V, false, true><<<grid, B_THREADS, 0, s>>>(a);
-  } else {
-    if (a.use_bf16)
-      k_bforward<V, true, false><<<grid, B_THREADS, 0, s>>>(a);
-    else
-      k_bforward<V, false, false><<<grid, B_THREADS, 0, s>>>(a);
-  }
+  const bool st = grid > nsp, g4 = a.gather_rows == 4;
+  void (*kern)(BFwdArgs);
+  if (a.use_bf16)
+    kern = st ? (g4 ? k_bforward<V, true, true, 4> : k_bforward<V, true, true, 8>)
+              : (g4 ? k_bforward<V, true, false, 4> : k_bforward<V, true, false, 8>);
+  else
+    kern = st ? (g4 ? k_bforward<V, false, true, 4> : k_bforward<V, false, true, 8>)
+              : (g4 ? k_bforward<V, false, false, 4> : k_bforward<V, false, false, 8>);
+  kern<<<grid, B_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <int V>
@@ -957,10 +960,10 @@ cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
   int nb = (a.At.rows + B_WARPS - 1) / B_WARPS;
   const int cap = sms * clamp_per_sm(a.blocks_per_sm, kSpmvPerSm);
   if (nb > cap) nb = cap;
-  if (a.use_bf16)
-    k_bpixel<V, true><<<nb, B_THREADS, 0, s>>>(a);
-  else
-    k_bpixel<V, false><<<nb, B_THREADS, 0, s>>>(a);
+  const bool g4 = a.gather_rows == 4;
+  void (*kern)(BPixArgs) = a.use_bf16 ? (g4 ? k_bpixel<V, true, 4> : k_bpixel<V, true, 8>)
+                                      : (g4 ? k_bpixel<V, false, 4> : k_bpixel<V, false, 8>);
+  kern<<<nb, B_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 

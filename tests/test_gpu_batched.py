@@ -233,10 +233,14 @@ def test_launch_schedule_never_changes_images(A, ctx):
     f0, _ = run_batched(A, ctx, mat, sls, max_iters=20, omega=1.0)
     try:
         for sch in (dict(chunk=32), dict(spmv_per_sm=3, pixel_per_sm=5, stencil_per_sm=1),
-                    dict(chunk=32, spmv_per_sm=16, pixel_per_sm=16, stencil_per_sm=16)):
+                    dict(chunk=32, spmv_per_sm=16, pixel_per_sm=16, stencil_per_sm=16),
+                    dict(gather_rows_fw=4), dict(gather_rows_px=4),
+                    dict(chunk=32, gather_rows_fw=4, gather_rows_px=4, spmv_per_sm=5)):
             A.appga_batch_schedule_set(mat.handle, A.appga_batch_tuning(K=40, a_precision=0, **sch))
             got = A.appga_batch_schedule_get(mat.handle, 40)
             assert (got.chunk, got.spmv_per_sm) == (sch.get("chunk", 0), sch.get("spmv_per_sm", 0))
+            assert (got.gather_rows_fw, got.gather_rows_px) == (sch.get("gather_rows_fw", 0),
+                                                                sch.get("gather_rows_px", 0))
             f1, _ = run_batched(A, ctx, mat, sls, max_iters=20, omega=1.0)
             np.testing.assert_array_equal(f1, f0)
     finally:
@@ -255,6 +259,9 @@ def test_autotune_batched(A, ctx):
         kept = A.appga_batch_schedule_get(mat.handle, 64)
         assert (kept.spmv_per_sm, kept.stencil_per_sm, kept.pixel_per_sm, kept.chunk) == (
             t.spmv_per_sm, t.stencil_per_sm, t.pixel_per_sm, t.chunk)
+        assert t.gather_rows_fw in (4, 8) and t.gather_rows_px in (4, 8)
+        assert (kept.gather_rows_fw or 8, kept.gather_rows_px or 8) == (t.gather_rows_fw,
+                                                                        t.gather_rows_px)
         f1, _ = run_batched(A, ctx, mat, sls, max_iters=12)
         np.testing.assert_array_equal(f1, f0)
     finally:
@@ -264,7 +271,8 @@ def test_autotune_batched(A, ctx):
 def test_batch_schedule_rejects_bad_values(A, ctx):
     geom, Amat, mat = matrix(A, ctx, "64")
     for bad in (dict(K=0), dict(K=129), dict(K=8, chunk=48), dict(K=8, spmv_per_sm=17),
-                dict(K=8, pixel_per_sm=-1), dict(K=8, a_precision=3)):
+                dict(K=8, pixel_per_sm=-1), dict(K=8, a_precision=3),
+                dict(K=8, gather_rows_fw=6), dict(K=8, gather_rows_px=16)):
         with pytest.raises(A.AppgaError) as ei:
             A.appga_batch_schedule_set(mat.handle, A.appga_batch_tuning(**bad))
         assert ei.value.status == A.APPGA_EINVAL
