@@ -66,3 +66,94 @@ def test_fom_rejects_bad_arguments(A, ctx):
         with pytest.raises(A.AppgaError) as ei:
             A.appga_figures_of_merit(ctx.handle, *args)
         assert ei.value.status == A.APPGA_EINVAL
+
+
+def test_nofv_curves_and_omega_ordering_on_the_uniform_phantom(A, ctx):
+    """Sec. 4.1-4.2 on synthetic data: the paper's uniform phantom (a disk
+    with six hot disks at 4:1) on the 128^2 geometry with its settings for
+    that phantom (TC 6.8e6, eps 1e-3, lambda1 0.4, lambda2 0, beta 0.1), for
+    omega 1/4, 1/2, 3/4 and 1.  NOFV at every map uses Phi_ref from a long
+    FP64 oracle run (2000 maps, omega 1); the GPU's curve matches the
+    oracle's, larger omega reaches NOFV <= 1e-2 in fewer maps on both, and
+    NRC of the largest and smallest hot disks and the central line profile
+    after 50 and 100 maps match the oracle's images."""
+    from oracle import appga_oracle as O
+    from paper_2409_13344_gb300 import workload as W
+    geom = W.GEOMETRIES["128"]
+    Amat = W.system_matrix("128")
+    sl = W.make_slice(Amat, geom, 6.8e6, W.seed_for(1), phantom="uniform")
+    kw = dict(lambda1=0.4, lambda2=0.0, eps=1e-3, beta=0.1)
+    prob = O.Problem(Amat, sl.g, sl.gamma, geom.n)
+    ref = O.appga(prob, O.Params(max_iters=2000, omega=1.0, **kw), n_angles=geom.n_angles,
+                  track_phi=True)
+    phi_ref = min(ref.phi)
+    n, d = geom.n, geom.d
+    R = n / 2.0
+    s = n / 256.0
+    # hot disks k = 0 (smallest) and 5 (largest) at 0.5 R, angle 2 pi k / 6; background
+    # ROI of the same radius at the centre (uniform background there)
+    rois = {}
+    for k, rad in ((0, 4), (5, 14)):
+        th = 2 * np.pi * k / 6.0
+        r_in = 0.8 * max(rad * s, 1.0)
+        rois[k] = (F.disk_roi(n, 0.5 * R * np.cos(th), 0.5 * R * np.sin(th), r_in),
+                   F.disk_roi(n, 0.0, 0.0, r_in))
+    mat = A.Matrix(ctx, Amat, n, geom.n_angles)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+    g, gamma, f_true = dev(sl.g), dev(sl.gamma), dev(sl.f_true.astype(np.float32))
+    K, tau = 170, 1e-2
+    cross = {}
+    try:
+        for om in (0.25, 0.5, 0.75, 1.0):
+            # one map per call, chained through appga_resume (bit-identical to
+            # an uninterrupted run); Phi of each result from the call's stats
+            bufs = [torch.empty(d, dtype=torch.float32, device=DEV) for _ in range(4)]
+            A.appga_initial_image(ctx.handle, mat.handle, g, gamma, bufs[0])
+            bufs[1].copy_(bufs[0])
+            st0 = A.appga_resume(ctx.handle, mat.handle, g, gamma, bufs[0], bufs[1], 1,
+                                 A.default_params(max_iters=0, omega=om, track_objective=1, **kw),
+                                 None, bufs[2])
+            phis, snaps = [st0.phi], {}
+            prev, cur = bufs[0], bufs[1]
+            for k in range(1, K + 1):
+                op, oc = (bufs[2], bufs[3]) if k % 2 else (bufs[0], bufs[1])
+                st = A.appga_resume(ctx.handle, mat.handle, g, gamma, prev, cur, k,
+                                    A.default_params(max_iters=1, omega=om, track_objective=1,
+                                                     **kw), op, oc)
+                assert st.iters == 1 and st.result_k == k + 1
+                phis.append(st.phi)
+                prev, cur = op, oc
+                if k in (50, 100):
+                    snaps[k] = cur.clone()
+            nofv_gpu = np.array([A.appga_nofv(p, phis[0], phi_ref) for p in phis])
+            ora = O.appga(prob, O.Params(max_iters=K, omega=om, **kw), n_angles=geom.n_angles,
+                          track_phi=True)
+            nofv_ora = np.array([F.nofv(p, ora.phi[0], phi_ref) for p in ora.phi])
+            assert np.max(np.abs(nofv_gpu - nofv_ora)) <= 1e-6, om
+            first = lambda c: int(np.argmax(c <= tau)) if np.any(c <= tau) else None
+            cross[om] = (first(nofv_gpu), first(nofv_ora))
+            for k, img in snaps.items():
+                fk = O.appga(prob, O.Params(max_iters=k, omega=om, **kw), n_angles=geom.n_angles,
+                             track_phi=False).f
+                for hot, (rh, rb) in rois.items():
+                    got = A.appga_figures_of_merit(ctx.handle, d, img, f_true,
+                                                   dev(rh.astype(np.uint8)),
+                                                   dev(rb.astype(np.uint8)), 4.0)
+                    want = F.nrc(fk, sl.f_true, rh, rb)
+                    assert got.nrc == pytest.approx(want, rel=1e-4), (om, k, hot)
+                clp = torch.empty(n, dtype=torch.float32, device=DEV)
+                A.appga_central_line_profile(ctx.handle, n, img, clp)
+                torch.cuda.synchronize()
+                want = F.central_line_profile(fk, n)
+                assert np.linalg.norm(clp.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
+    finally:
+        mat.close()
+    oms = (0.25, 0.5, 0.75, 1.0)
+    gpu = [cross[o][0] for o in oms]
+    ora = [cross[o][1] for o in oms]
+    print("maps to NOFV <= 1e-2 (omega 1/4, 1/2, 3/4, 1): GPU", gpu, "oracle", ora)
+    assert None not in gpu and None not in ora
+    # larger omega, fewer maps (Sec. 4.2), on the GPU as on the oracle
+    assert gpu[0] > gpu[1] > gpu[2] > gpu[3]
+    assert ora[0] > ora[1] > ora[2] > ora[3]
+    assert all(abs(a - b) <= 1 for a, b in zip(gpu, ora))
