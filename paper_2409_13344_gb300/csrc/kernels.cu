@@ -86,11 +86,6 @@ struct Shape {
 #ifndef APPGA_SELL_PEEL
 #define APPGA_SELL_PEEL 1
 #endif
-// the sliced pixel phase issues its update's four vector loads before the
-// back-projection streams (1) or after it (0)
-#ifndef APPGA_PX_PREFETCH
-#define APPGA_PX_PREFETCH 0
-#endif
 // steps in flight per warp in the sliced layout's forward and pixel phases
 #ifndef APPGA_SELL_FW_PF
 #define APPGA_SELL_FW_PF 2
@@ -789,25 +784,11 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
 
 // EM-preconditioned projected update of pixel j (Eq. EM, Eq. cloformproiota)
 // given the back-projection bp = (A^T w)_j; returns the preconditioner entry.
-// The update's inputs of pixel j: f^k_j, f^{k-1}_j, (B^T grad phi~)_j, 1/Lambda_j.
-struct PixIn {
-  float vk, vkm, gr, il;
-};
-__device__ __forceinline__ float ld_keep(const float* p) {
-  float v;
-  asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
-// Issued before the back-projection streams (with APPGA_PX_PREFETCH), so the
-// four loads' latency hides behind it; the volatile loads stay where they are.
-__device__ __forceinline__ PixIn pixel_inputs(const PixArgs& a, int kk, int j) {
-  return {ld_keep(a.f[kk % 3] + j), ld_keep(a.f[(kk + 2) % 3] + j), ld_keep(a.gR + j),
-          ld_keep(a.inv_lambda + j)};
-}
 __device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, float bp,
-                                              int& bad, const PixIn* pre = nullptr) {
-  const float vk = pre ? pre->vk : a.f[kk % 3][j];
-  const float ft = fmaf(a.st->theta_hi, vk - (pre ? pre->vkm : a.f[(kk + 2) % 3][j]), vk);
+                                              int& bad) {
+  const float* fk = a.f[kk % 3];
+  const float vk = fk[j];
+  const float ft = fmaf(a.st->theta_hi, vk - a.f[(kk + 2) % 3][j], vk);
   float pk = vk;
   if (a.ip.freeze_iter >= 0) {
     if (kk == a.ip.freeze_iter) {
@@ -816,8 +797,8 @@ __device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, f
       pk = a.pfreeze[j];
     }
   }
-  const float p = a.ip.beta * pk * (pre ? pre->il : a.inv_lambda[j]);
-  const float grad = bp + (pre ? pre->gr : a.gR[j]);
+  const float p = a.ip.beta * pk * a.inv_lambda[j];
+  const float grad = bp + a.gR[j];
   const float xv = __fmaf_rn(-p, grad, ft);
   if (!isfinite(xv)) bad = 1;
   const float fn = fmaxf(xv, 0.f);
@@ -940,22 +921,8 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   float bp = 0.f, unused = 0.f;
   int j = -1;  // the pixel whose update this lane makes
   if constexpr (SL) {
-    if ((lane % SELL_LANES) == 0 && lane / SELL_LANES < np) j = j0 + lane / SELL_LANES;
-#if APPGA_PX_PREFETCH
-    PixIn pre{0.f, 0.f, 0.f, 0.f};
-    if (j >= 0) pre = pixel_inputs(a, kk, j);
-#endif
     if (np > 0) bp = sg.stream(a.S, a.w, pol);
-#if APPGA_PX_PREFETCH
-    float pj = 0.f;
-    if (j >= 0) pj = pixel_update(a, kk, j, bp, bad, &pre);
-    if (a.want_pmax) {
-      const unsigned pm = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(pj, 0.f)));
-      if (lane == 0 && pm > 0u) atomicMax(&st->pmax_bits, pm);
-    }
-    warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
-    return;
-#endif
+    if ((lane % SELL_LANES) == 0 && lane / SELL_LANES < np) j = j0 + lane / SELL_LANES;
   } else {
     if (np > 0) {
       rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
