@@ -135,17 +135,24 @@ def test_nofv_curves_and_omega_ordering_on_the_uniform_phantom(A, ctx):
             for k, img in snaps.items():
                 fk = O.appga(prob, O.Params(max_iters=k, omega=om, **kw), n_angles=geom.n_angles,
                              track_phi=False).f
+                im = img.cpu().numpy().astype(np.float64)
+                assert np.linalg.norm(im - fk) <= 1e-5 * np.linalg.norm(fk), (om, k)
                 for hot, (rh, rb) in rois.items():
                     got = A.appga_figures_of_merit(ctx.handle, d, img, f_true,
                                                    dev(rh.astype(np.uint8)),
                                                    dev(rb.astype(np.uint8)), 4.0)
+                    # of the GPU image itself: the library's reduction
+                    assert got.nrc == pytest.approx(F.nrc(im, sl.f_true, rh, rb), rel=1e-9)
+                    # against the oracle's image: NRC divides the difference of two
+                    # small-ROI means (8 pixels for the smallest disk here) by the
+                    # truth's, which amplifies the images' 1e-6 relative differences
                     want = F.nrc(fk, sl.f_true, rh, rb)
-                    assert got.nrc == pytest.approx(want, rel=1e-4), (om, k, hot)
+                    assert got.nrc == pytest.approx(want, rel=1e-3), (om, k, hot)
                 clp = torch.empty(n, dtype=torch.float32, device=DEV)
                 A.appga_central_line_profile(ctx.handle, n, img, clp)
                 torch.cuda.synchronize()
                 want = F.central_line_profile(fk, n)
-                assert np.linalg.norm(clp.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
+                assert np.linalg.norm(clp.cpu().numpy() - want) <= 1e-4 * np.linalg.norm(want)
     finally:
         mat.close()
     oms = (0.25, 0.5, 0.75, 1.0)
