@@ -4,6 +4,8 @@ import pytest
 
 from oracle import figures_of_merit as F
 
+from fp32_spread import oracle_fp32_noisy
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -132,27 +134,36 @@ def test_nofv_curves_and_omega_ordering_on_the_uniform_phantom(A, ctx):
             assert np.max(np.abs(nofv_gpu - nofv_ora)) <= 1e-6, om
             first = lambda c: int(np.argmax(c <= tau)) if np.any(c <= tau) else None
             cross[om] = (first(nofv_gpu), first(nofv_ora))
+            # with eps = 1e-3 the smoothed TV of the flat phantom is nearly
+            # non-smooth and the FP64 oracle does not fix the image to 1e-5 from
+            # FP32-sized rounding (its own spread is 1e-4 at 50 maps), so the GPU
+            # image is bounded by 10x that spread, measured here per checkpoint
+            f0 = O.initial_image(sl.g, sl.gamma, n, geom.n_angles)
+            _, noisy = oracle_fp32_noisy(prob, O.Params(max_iters=100, omega=om, **kw), f0,
+                                         seed=1, keep=(50, 100))
             for k, img in snaps.items():
-                fk = O.appga(prob, O.Params(max_iters=k, omega=om, **kw), n_angles=geom.n_angles,
+                fk = O.appga(prob, O.Params(max_iters=k, omega=om, **kw), f_init=f0,
                              track_phi=False).f
                 im = img.cpu().numpy().astype(np.float64)
-                assert np.linalg.norm(im - fk) <= 1e-5 * np.linalg.norm(fk), (om, k)
+                spread = np.linalg.norm(noisy[k] - fk) / np.linalg.norm(fk)
+                dist = np.linalg.norm(im - fk) / np.linalg.norm(fk)
+                assert 1e-6 < spread and dist <= 10.0 * spread, (om, k, dist, spread)
                 for hot, (rh, rb) in rois.items():
                     got = A.appga_figures_of_merit(ctx.handle, d, img, f_true,
                                                    dev(rh.astype(np.uint8)),
                                                    dev(rb.astype(np.uint8)), 4.0)
-                    # of the GPU image itself: the library's reduction
+                    # the library's reduction, of the GPU image itself
                     assert got.nrc == pytest.approx(F.nrc(im, sl.f_true, rh, rb), rel=1e-9)
-                    # against the oracle's image: NRC divides the difference of two
-                    # small-ROI means (8 pixels for the smallest disk here) by the
-                    # truth's, which amplifies the images' 1e-6 relative differences
+                    # against the oracle's: NRC over a few-pixel region moves with
+                    # the image by more than the L2 spread, by the same rule
                     want = F.nrc(fk, sl.f_true, rh, rb)
-                    assert got.nrc == pytest.approx(want, rel=1e-3), (om, k, hot)
+                    wobble = abs(F.nrc(noisy[k], sl.f_true, rh, rb) - want)
+                    assert abs(got.nrc - want) <= 10.0 * wobble + 1e-4 * abs(want), (om, k, hot)
                 clp = torch.empty(n, dtype=torch.float32, device=DEV)
                 A.appga_central_line_profile(ctx.handle, n, img, clp)
                 torch.cuda.synchronize()
-                want = F.central_line_profile(fk, n)
-                assert np.linalg.norm(clp.cpu().numpy() - want) <= 1e-4 * np.linalg.norm(want)
+                want = F.central_line_profile(im, n)
+                assert np.linalg.norm(clp.cpu().numpy() - want) <= 1e-6 * np.linalg.norm(want)
     finally:
         mat.close()
     oms = (0.25, 0.5, 0.75, 1.0)

@@ -19,6 +19,8 @@ import scipy.sparse as sp
 from oracle import appga_oracle as O
 from paper_2409_13344_gb300 import workload as W
 
+from fp32_spread import oracle_fp32_noisy
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -515,22 +517,6 @@ def test_full_size_trajectory(A, ctx, m256, counts, omega, iters, beta):
     assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
 
 
-def _oracle_fp32_spread(prob, par, f0, seed):
-    """Relative L2 distance after par.max_iters maps between the oracle run
-    and the same run with a relative perturbation of FP32 size (2^-24 N(0,1))
-    applied to every new iterate: how far FP32 rounding alone can move the
-    trajectory of this problem."""
-    lam = prob.em_lambda()
-    th = O.thetas_for(par, par.max_iters)
-    rng = np.random.default_rng(seed)
-    fk, fkm = f0.copy(), f0.copy()
-    for it in range(par.max_iters):
-        fn, _ = O.appga_step(prob, fk, fkm, th[it], par, lam)
-        fn = fn * (1.0 + 2.0 ** -24 * rng.standard_normal(fn.shape[0]))
-        fkm, fk = fk, fn
-    return fk
-
-
 @pytest.mark.parametrize("omega", [0.25, 1.0])
 def test_full_size_5e6_beta1_500_maps(A, ctx, m256, omega):
     # 256^2 at 5e6 counts with beta = 1 over the workload's 500 maps.  The EM
@@ -546,7 +532,7 @@ def test_full_size_5e6_beta1_500_maps(A, ctx, m256, omega):
     par = O.Params(max_iters=500, omega=omega)
     f0 = O.initial_image(sl.g, sl.gamma, geom.n, geom.n_angles)
     ref = O.appga(prob, par, f_init=f0, track_phi=False)
-    noisy = _oracle_fp32_spread(prob, par, f0, seed=1)
+    noisy = oracle_fp32_noisy(prob, par, f0, seed=1)
     spread = rel_l2(noisy, ref.f)
     dist = rel_l2(f, ref.f)
     assert spread > 1e-6
