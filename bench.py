@@ -155,16 +155,21 @@ class ClockSampler:
 
 # ------------------------------------------------------------- roofline data
 
-def kernel_bytes(m: int, d: int, nnz: int, per_nnz: int = 8, sliced: bool = False):
-    """Algorithmic bytes per launch of the two iteration kernels: the matrix
-    stream at `per_nnz` bytes per nonzero (8: FP32 values and 4-byte column
-    indices; 6: FP32 values and 2-byte packed columns, or BF16 values and
-    4-byte columns), its row (or slice) offsets, and every vector once."""
+def kernel_bytes(m: int, d: int, nnz: int, per_nnz: int = 8, sliced: bool = False,
+                 folded: bool = False):
+    """Algorithmic bytes per launch of the two iteration kernels: the stored
+    matrix stream at `per_nnz` bytes per nonzero (8: FP32 values and 4-byte
+    column indices; 6: FP32 values and 2-byte packed columns, or BF16 values
+    and 4-byte columns), its row (or slice) offsets, and every vector once.
+    Folded (the quarter-turn symmetry): the loop stores and streams the first
+    half of A's rows and their transpose, nnz/2 entries each."""
     rows_per_offset = 4 if sliced else 1   # the sliced layout keeps one offset per 4 rows
-    fwd = (per_nnz * nnz + 4 * (m // rows_per_offset + 1)
+    stored = nnz // 2 if folded else nnz
+    m_rows = m // 2 if folded else m
+    fwd = (per_nnz * stored + 4 * (m_rows // rows_per_offset + 1)
            + 4 * d + 28 * m               # f gathered once; g, gamma, y_prev (8 B), y (8 B), w
            + 12 * d)                      # stencil: f^k, f^{k-1} in, B^T grad phi~ out
-    pix = (per_nnz * nnz + 4 * (d // rows_per_offset + 1)
+    pix = (per_nnz * stored + 4 * (d // rows_per_offset + 1)
            + 4 * m                        # w gathered once
            + 20 * d)                      # f^k, f^{k-1}, B^T grad phi~, 1/Lambda in; f^{k+1} out
     return fwd, pix
@@ -737,7 +742,9 @@ def run_ours(args):
     tp, tf = AP.appga_kernel_times(ctx.handle, mat.handle, g, gamma, params(300), 300)
     info = mat.info()
     per_nnz = 6 if info.packed_columns else 8
-    b_fwd, b_pix = kernel_bytes(geom.m, geom.d, int(info.nnz), per_nnz, bool(info.sliced_layout))
+    folded = bool(info.quarter_turn_folded)
+    b_fwd, b_pix = kernel_bytes(geom.m, geom.d, int(info.nnz), per_nnz, bool(info.sliced_layout),
+                                folded)
     c_fwd, c_pix = kernel_bytes(geom.m, geom.d, int(info.nnz))  # plain FP32 + int32 CSR
     peaks, peak_src = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -751,11 +758,12 @@ def run_ours(args):
         "timed_as": dom[0],
         "ms_per_launch": dom[1], "algorithmic_bytes_per_launch": dom[2],
         "bytes_per_nnz": per_nnz,
-        "layout": ("sliced, packed 2-byte columns + FP32 values" if info.packed_columns
-                   else ("sliced, 4-byte columns" if info.sliced_layout else "CSR")),
+        "layout": ("quarter-turn folded (half of A and A^T stored), " if folded else "")
+                  + ("sliced, packed 2-byte columns + FP32 values" if info.packed_columns
+                     else ("sliced, 4-byte columns" if info.sliced_layout else "CSR")),
         # the same launch measured against the plain CSR format's bytes
-        # (FP32 values + int32 columns, 8 B per nonzero): the rate at which
-        # it does that format's work
+        # (the whole A, FP32 values + int32 columns, 8 B per nonzero): the
+        # rate at which it does that format's work
         "csr32_equivalent": {"achieved_gbs": (c_fwd if dom[0] == "k_forward" else c_pix)
                              / (dom[1] * 1e-3) / 1e9,
                              "frac": (c_fwd if dom[0] == "k_forward" else c_pix)

@@ -53,6 +53,7 @@ typedef struct appga_matrix appga_matrix;
 
 /* Matrix-creation flags. */
 #define APPGA_A_BF16_COPY 1u /* also keep a BF16 copy of A's values */
+#define APPGA_A_NO_FOLD 2u   /* do not fold A by its quarter-turn symmetry */
 
 /* Precision of A's values inside the projectors. */
 #define APPGA_PREC_FP32 0
@@ -87,13 +88,23 @@ appga_status appga_ctx_destroy(appga_ctx* ctx);
  *     entries so rows start on 16-byte boundaries),
  *   - A^T as a row-padded CSR (built on the host by a stable counting sort,
  *     so the back-projection needs no atomics),
- *   - 1/Lambda with Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM).
+ *   - 1/Lambda with Lambda_j = (A^T 1)_j if positive, else 1 (Eq. EM),
+ *   - the quarter-turn folded copies of the solver loop, when A has that
+ *     symmetry bit for bit: for a parallel-beam scanner with NPA angles
+ *     a*pi/NPA (NPA even) stored angle-major (row a*nb + b, m = NPA*nb) over
+ *     an N x N image (N even), the ray of angle a + NPA/2 and bin nb-1-b is
+ *     the ray of angle a and bin b turned a quarter turn, which moves pixel
+ *     (r, c) to (N-1-c, r).  The loop then streams only the first m/2 rows of
+ *     A and of its transpose, each entry serving two products per projection;
+ *     the results are those of the whole A up to the order of FP32 sums.
+ *     The check is exact (same columns after the turn, same value bits); any
+ *     other A, or flags with APPGA_A_NO_FOLD, keeps the unfolded loop.
  * n_side is N (d must equal N*N); n_angles is the number of projection
- * angles (NPA, used only by the default initial image, Sec. 4.1).
+ * angles (NPA, used by the default initial image, Sec. 4.1, and the fold).
  * row_ptr_host: int32[m+1], col_host: int32[nnz], val_host: float[nnz]; the
  * host arrays are only read during the call.  Validation: row_ptr[0] = 0,
  * nondecreasing, row_ptr[m] = nnz; 0 <= col < d; values finite and >= 0
- * (EINVAL / EDOMAIN otherwise).  flags: APPGA_A_BF16_COPY. */
+ * (EINVAL / EDOMAIN otherwise).  flags: APPGA_A_BF16_COPY, APPGA_A_NO_FOLD. */
 appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n_side,
                                  int32_t n_angles, const int32_t* row_ptr_host,
                                  const int32_t* col_host, const float* val_host,
@@ -113,6 +124,9 @@ typedef struct {
                              pack's first column); 0: 4-byte indices */
   int32_t sliced_layout;  /* 1 if the solver loop's projections stream A and
                              A^T in the sliced (ELLPACK-like) layout; 0: CSR */
+  int32_t quarter_turn_folded; /* 1 if the solver loop streams the quarter-turn
+                                  folded halves of A and A^T (see above) */
+  int32_t reserved;
 } appga_matrix_info;
 appga_status appga_matrix_get_info(const appga_matrix* mat, appga_matrix_info* out);
 

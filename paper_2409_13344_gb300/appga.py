@@ -28,6 +28,7 @@ APPGA_ENODEV = 6
 APPGA_EBUSY = 7
 APPGA_ENUMERIC = 8
 APPGA_A_BF16_COPY = 1
+APPGA_A_NO_FOLD = 2
 APPGA_PREC_FP32 = 0
 APPGA_PREC_BF16 = 1
 APPGA_MOMENTUM_GN = 0
@@ -63,7 +64,8 @@ class appga_matrix_info(ctypes.Structure):
         ("n_angles", ctypes.c_int32), ("nnz", ctypes.c_int64), ("nnz_padded_a", ctypes.c_int64),
         ("nnz_padded_t", ctypes.c_int64), ("has_bf16", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64), ("packed_columns", ctypes.c_int32),
-        ("sliced_layout", ctypes.c_int32),
+        ("sliced_layout", ctypes.c_int32), ("quarter_turn_folded", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -596,14 +598,15 @@ class Context:
 class Matrix:
     """Device copy of a system matrix (scipy CSR, FP32 values)."""
 
-    def __init__(self, ctx: Context, A, n_side: int, n_angles: int, bf16: bool = False):
+    def __init__(self, ctx: Context, A, n_side: int, n_angles: int, bf16: bool = False,
+                 fold: bool = True):
         self.ctx = ctx
         self.m, self.d = A.shape
         self.n_side = n_side
         self.n_angles = n_angles
+        flags = (APPGA_A_BF16_COPY if bf16 else 0) | (0 if fold else APPGA_A_NO_FOLD)
         self.handle = appga_matrix_create(ctx.handle, self.m, self.d, n_side, n_angles, A.indptr,
-                                          A.indices, A.data,
-                                          APPGA_A_BF16_COPY if bf16 else 0)
+                                          A.indices, A.data, flags)
 
     def info(self) -> appga_matrix_info:
         return appga_matrix_get_info(self.handle)

@@ -131,18 +131,12 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   fa.n = M->n;
   fa.ip = iter_params(p, false);
   fa.theta_tab = ws.theta_tab;
-  const bool tiled = tiled_gather_enabled();
-  if (tiled) {
-    // the loop's projector gathers f^k from its 8 x 8-tiled copy (through
-    // the sliced layout, as the APPGA loop does)
-    fa.A.col = M->A_tiled.col;
-    fa.S = M->sell_a;
-    fa.ft = ws.ft;
-    CK(launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
-  }
+  // the APPGA loop's projection layout (tiled gathers, sliced or folded)
+  PixArgs pa{};
+  loop_layout(M, &fa, &pa);
+  CK(loop_gather_copy(M, ws.f[k0 % 3], s));
   CK(launch_forward(fa, s));
 
-  PixArgs pa{};
   pa.At = M->At;
   pa.n = M->n;
   for (int i = 0; i < 3; ++i) pa.f[i] = ws.f[i];
@@ -150,8 +144,6 @@ extern "C" appga_status appga_afppa_reconstruct(appga_ctx* ctx, const appga_matr
   pa.gR = ws.gR;
   pa.inv_lambda = bf16 ? M->inv_lambda_bf16 : M->inv_lambda;
   pa.pfreeze = ws.pfreeze;
-  pa.ft = tiled ? ws.ft : nullptr;
-  if (tiled) pa.S = M->sell_t;
   pa.st = ws.st;
   pa.partial = ws.partial_p;
   pa.gtick = ws.gtick;

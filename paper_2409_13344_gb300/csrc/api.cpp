@@ -113,6 +113,7 @@ void free_workspace(Workspace& ws) {
   cudaFree(ws.gR);
   cudaFree(ws.pfreeze);
   cudaFree(ws.ft);
+  cudaFree(ws.fpair);
   cudaFree(ws.partial_p);
   cudaFree(ws.partial_r);
   cudaFree(ws.partial_aux);
@@ -181,6 +182,8 @@ appga_status ensure_workspace(appga_matrix* M) {
   if (e == cudaSuccess) e = dalloc(&ws.gR, (size_t)d, b);
   if (e == cudaSuccess) e = dalloc(&ws.pfreeze, (size_t)d, b);
   if (e == cudaSuccess) e = dalloc(&ws.ft, (size_t)appga::tiled_size(M->n), b);
+  if (e == cudaSuccess && M->fold_t.off != nullptr)
+    e = dalloc(&ws.fpair, (size_t)appga::tiled_size(M->n), b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_p, (size_t)np, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_r, (size_t)np, b);
   if (e == cudaSuccess) e = dalloc(&ws.partial_aux, (size_t)np, b);
@@ -224,6 +227,38 @@ appga::IterParams iter_params(const appga_params* p, bool track) {
 
 bool bf16_requested(const appga_matrix* M, const appga_params* p) {
   return p->a_precision == APPGA_PREC_BF16 && M->has_bf16;
+}
+
+bool loop_gathers_copy() { return tiled_gather_enabled(); }
+
+void loop_layout(const appga_matrix* M, FwdArgs* fa, PixArgs* pa) {
+  if (!tiled_gather_enabled()) return;  // the CSR with row-major columns
+  const Workspace& ws = M->ws;
+  // the loop's projector gathers f^k from its 8 x 8-tiled copy (as pairs
+  // when folded)
+  fa->A.col = M->A_tiled.col;
+  if (M->fold_t.off != nullptr && ws.fpair != nullptr) {
+    fa->S = M->fold_a;
+    fa->fpair = ws.fpair;
+    fa->fold_half = M->m / 2;
+    fa->fold_nb = M->fold_nb;
+    fa->ft = nullptr;
+    pa->S = M->fold_t;
+    pa->fpair = ws.fpair;
+    pa->ft = nullptr;
+  } else {
+    fa->S = M->sell_a;
+    fa->ft = ws.ft;
+    pa->S = M->sell_t;
+    pa->ft = ws.ft;
+  }
+}
+
+cudaError_t loop_gather_copy(const appga_matrix* M, const float* f, cudaStream_t s) {
+  if (!tiled_gather_enabled()) return cudaSuccess;
+  if (M->fold_t.off != nullptr && M->ws.fpair != nullptr)
+    return launch_to_fold_pairs(f, M->ws.fpair, M->n, s);
+  return launch_to_tiled(f, M->ws.ft, M->n, s);
 }
 
 appga::FwdArgs fwd_args(appga_matrix* M, bool bf16) {
@@ -272,7 +307,6 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   const bool track = p->track_objective != 0 || p->rel_obj_tol > 0.0;
   const bool bf16 = bf16_requested(M, p);
 
-  const bool tiled = appga::tiled_gather_enabled();
   if (!fresh) {
     // y^{k0-1} = A f^{k0-1}, with the loop's projection (the same matrix
     // layout, gather order and accumulation), so a resumed run continues an
@@ -289,12 +323,9 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
     init.loop = 0;
     init.solver_acc = 1;
     init.n = M->n;
-    if (tiled) {
-      init.A.col = M->A_tiled.col;
-      init.S = M->sell_a;
-      init.ft = ws.ft;
-      CK(appga::launch_to_tiled(ws.f[(k0 + 2) % 3], ws.ft, M->n, s));
-    }
+    appga::PixArgs unused{};
+    appga::loop_layout(M, &init, &unused);
+    CK(appga::loop_gather_copy(M, ws.f[(k0 + 2) % 3], s));
     CK(appga::launch_forward(init, s));
   }
 
@@ -331,16 +362,10 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   pa.ip = iter_params(p, track);
   pa.use_bf16 = bf16 ? 1 : 0;
   pa.fuse_fin = APPGA_FUSE_FIN;
-  if (tiled) {
-    // the loop's projector gathers f^k from its 8 x 8-tiled copy
-    fa.A.col = M->A_tiled.col;
-    fa.S = M->sell_a;
-    fa.ft = ws.ft;
-    pa.ft = ws.ft;
-    pa.S = M->sell_t;
-    if (!tiled_ready) CK(appga::launch_to_tiled(ws.f[k0 % 3], ws.ft, M->n, s));
-  }
-  pa.n_fwd_partial = appga::forward_blocks(M->m, M->n, fa.S.off != nullptr);
+  appga::loop_layout(M, &fa, &pa);
+  if (!tiled_ready) CK(appga::loop_gather_copy(M, ws.f[k0 % 3], s));
+  pa.n_fwd_partial =
+      appga::forward_blocks(fa.S.off != nullptr ? fa.S.rows : M->m, M->n, fa.S.off != nullptr);
 
   // w^{k0}, y^{k0}, B^T grad phi~(B f~^{k0}) and Phi(f^{k0})
   appga::FwdArgs first = fa;
@@ -624,15 +649,17 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
   const size_t fb = (size_t)M->d * sizeof(float);
   float* slot_cur = ws.f[k0 % 3];
   float* slot_prev = ws.f[(k0 + 2) % 3];
-  const bool tiled = appga::tiled_gather_enabled();
   bool tiled_ready = false;
   if (fresh && f_cur == nullptr) {
-    // TMC * 1_disk into f^{k0}, f^{k0-1} and the tiled copy; g and gamma are
-    // checked in the same pass
+    // TMC * 1_disk into f^{k0}, f^{k0-1} and the loop's gather copy; g and
+    // gamma are checked in the same pass
+    appga::FwdArgs lf{};
+    appga::PixArgs lp{};
+    appga::loop_layout(M, &lf, &lp);
     CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux,
-                                   ws.gtick, ws.st_scratch, slot_cur, s, slot_prev,
-                                   tiled ? ws.ft : nullptr, ws.st));
-    tiled_ready = tiled;
+                                   ws.gtick, ws.st_scratch, slot_cur, s, slot_prev, lp.ft, ws.st,
+                                   lp.fpair));
+    tiled_ready = appga::loop_gathers_copy();
   } else {
     CK(appga::launch_check_inputs(g, gamma, M->m, f_cur, fresh ? nullptr : f_prev, M->d, ws.st,
                                   s));
@@ -778,7 +805,8 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
     return fail(APPGA_EINVAL, "d must equal n_side * n_side");
   if (n_angles <= 0) return fail(APPGA_EINVAL, "n_angles must be > 0");
   if (m <= 0) return fail(APPGA_EINVAL, "m must be > 0");
-  if ((flags & ~APPGA_A_BF16_COPY) != 0) return fail(APPGA_EINVAL, "unknown flags");
+  if ((flags & ~(APPGA_A_BF16_COPY | APPGA_A_NO_FOLD)) != 0)
+    return fail(APPGA_EINVAL, "unknown flags");
   std::string why;
   appga_status rc = appga::validate_csr(m, d, row_ptr_host, col_host, val_host, &why);
   if (rc != APPGA_OK) return fail(rc, why);
@@ -841,6 +869,27 @@ appga_status appga_matrix_create(appga_ctx* ctx, int32_t m, int32_t d, int32_t n
         if (r1 != APPGA_OK) e = cudaErrorMemoryAllocation;
       }
     }
+    // the folded loop: A's first half (its rows are a prefix of pa) and the
+    // transpose of that half in orbit order
+    if (M->sell_a.off != nullptr && e == cudaSuccess && (flags & APPGA_A_NO_FOLD) == 0 &&
+        appga::quarter_turn_symmetric(m, n_side, n_angles, row_ptr_host, col_host, val_host)) {
+      appga::HostCSR ft, pft;
+      appga::fold_transpose(at, m / 2, n_side, &ft);
+      appga::pad_rows(d, m / 2, ft.row_ptr.data(), ft.col.data(), ft.val.data(), appga::ROW_PAD,
+                      &pft);
+      appga::HostSell fa, fb;
+      if (!pft.col.empty() && appga::build_sell(m / 2, pa.row_ptr, ct, pa.val, &fa) &&
+          appga::build_sell(d, pft.row_ptr, pft.col, pft.val, &fb)) {
+        appga_status r1 = upload_sell(fa, want_bf16, &M->fold_a, &M->bytes);
+        if (r1 == APPGA_OK) r1 = upload_sell(fb, want_bf16, &M->fold_t, &M->bytes);
+        if (r1 != APPGA_OK) {
+          free_sell(M->fold_a);
+          free_sell(M->fold_t);
+          e = cudaErrorMemoryAllocation;
+        }
+        M->fold_nb = m / n_angles;
+      }
+    }
     if (e != cudaSuccess) rc = cuda_fail(e, "tiled column indices and sliced layout");
   }
   if (rc == APPGA_OK) {
@@ -866,6 +915,8 @@ appga_status appga_matrix_destroy(appga_matrix* M) {
   cudaFree(M->A_tiled.col);  // its other arrays belong to A
   free_sell(M->sell_a);
   free_sell(M->sell_t);
+  free_sell(M->fold_a);
+  free_sell(M->fold_t);
   free_csr(M->A);
   free_csr(M->At);
   cudaFree(M->inv_lambda);
@@ -896,6 +947,7 @@ appga_status appga_matrix_get_info(const appga_matrix* M, appga_matrix_info* out
   out->device_bytes = M->bytes;
   out->packed_columns = M->sell_t.cols != nullptr ? 1 : 0;
   out->sliced_layout = (M->sell_t.cols != nullptr || M->sell_t.cols32 != nullptr) ? 1 : 0;
+  out->quarter_turn_folded = M->fold_t.off != nullptr ? 1 : 0;
   return APPGA_OK;
 }
 

@@ -40,6 +40,38 @@ struct DevSell {
   uint2* vals_bf16 = nullptr;
 };
 
+// Quarter-turn folding of a parallel-beam A.  With NPA angles a*pi/NPA
+// (NPA even) stored angle-major (row i = a*nb + b) over an N x N image (N
+// even), the ray of angle a + NPA/2 and bin nb-1-b is the ray of angle a and
+// bin b turned a quarter turn about the image centre, a turn that moves pixel
+// (r, c) to (N-1-c, r).  When A has this symmetry bit for bit,
+//   A[fold_partner(i), quarter_turn(j)] = A[i, j]   for every i < m/2 and j,
+// the solver loop streams only the first m/2 rows (and their transpose):
+//   (A f)_i               = sum_j A[i,j] f_j
+//   (A f)_fold_partner(i) = sum_j A[i,j] f_{quarter_turn(j)}
+//   (A^T w)_j = s1(j) + s2(quarter_turn^-1(j)),  s1(p) = sum_{i<m/2} A[i,p] w_i,
+//                                              s2(p) = sum_{i<m/2} A[i,p] w_{fold_partner(i)}
+// so each stored entry serves two products of each projection.
+__host__ __device__ inline int32_t fold_partner(int32_t i, int32_t half, int32_t nb) {
+  return i + half + nb - 1 - 2 * (i % nb);
+}
+__host__ __device__ inline int32_t quarter_turn(int32_t j, int32_t n) {
+  return (n - 1 - j % n) * n + j / n;
+}
+// Member r (0..3) of pixel orbit o under the quarter turn: o runs over the
+// (N/2) x (N/2) top-left quadrant row-major; member r is that pixel turned r
+// times.  Returns (row, column).
+__host__ __device__ inline void orbit_pixel(int32_t o, int32_t r, int32_t n, int32_t* pr,
+                                            int32_t* pc) {
+  const int32_t h = n / 2, R = o / h, C = o % h;
+  switch (r & 3) {
+    case 0: *pr = R; *pc = C; break;
+    case 1: *pr = n - 1 - C; *pc = R; break;
+    case 2: *pr = n - 1 - R; *pc = n - 1 - C; break;
+    default: *pr = C; *pc = n - 1 - R; break;
+  }
+}
+
 struct DevCSR {
   int32_t rows = 0, cols = 0;
   int64_t nnz_padded = 0;
@@ -135,6 +167,13 @@ struct FwdArgs {
   // the sliced layout of A (solver projections with FP32 accumulation; its
   // columns index ft); S.cols == NULL: the CSR A
   DevSell S;
+  // quarter-turn folded loop (fpair != NULL): S holds A's first fold_half
+  // rows, the projector gathers fpair[t] = (f_j, f_{quarter_turn(j)}) at the
+  // tiled index t of pixel j, and w is written as pairs (w_i,
+  // w_{fold_partner(i)}) for the stored rows i
+  const float2* fpair;
+  int32_t fold_half;  // m / 2
+  int32_t fold_nb;    // bins per angle
 };
 
 // Fused pixel-phase arguments (steps a0, a3, a4, a5).
@@ -165,6 +204,11 @@ struct PixArgs {
   int32_t fuse_fin;
   // the sliced layout of A^T (S.cols == NULL: the CSR At)
   DevSell S;
+  // quarter-turn folded loop (fpair != NULL): S holds the folded A^T (slice o
+  // = the four pixels of orbit o, columns the stored rows), w holds pairs
+  // (w_i, w_{fold_partner(i)}), and f^{k+1} is also written as the gather
+  // pairs of the next forward phase
+  float2* fpair;
 };
 
 // ---- launchers (kernels.cu) ----
@@ -208,19 +252,22 @@ __host__ __device__ inline int32_t tiled_index(int r, int c, int n) {
 }
 // ft[tiled_index(j)] = f[j] for the d = n * n pixels
 cudaError_t launch_to_tiled(const float* f, float* ft, int n, cudaStream_t s);
+// fpair[tiled_index(j)] = (f[j], f[quarter_turn(j)]) for the d = n * n pixels
+cudaError_t launch_to_fold_pairs(const float* f, float2* fpair, int n, cudaStream_t s);
 bool tiled_gather_enabled();  // the solver loop gathers from the tiled copy
 // (with init: *st = *init first, so one launch starts a run)
 cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
                                double a, double b, double omega, cudaStream_t s,
                                const SolverState* init = nullptr);
 long long disk_pixels(int n);
-// f_out = TMC * 1_disk; also into f_out2 and (8 x 8-tiled) ft when not NULL;
-// with check_st set, g and gamma are checked as launch_check_inputs does.
+// f_out = TMC * 1_disk; also into f_out2, (8 x 8-tiled) ft and the folded
+// gather pairs fpair when not NULL (the disk is invariant under the quarter
+// turn); with check_st set, g and gamma are checked as launch_check_inputs does.
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
                                  long long npfov, float2* partial, unsigned int* gtick,
                                  SolverState* st, float* f_out, cudaStream_t s,
                                  float* f_out2 = nullptr, float* ft = nullptr,
-                                 SolverState* check_st = nullptr);
+                                 SolverState* check_st = nullptr, float2* fpair = nullptr);
 
 // ---- host CSR helpers (csr_host.cpp) ----
 struct HostCSR {
@@ -239,6 +286,16 @@ void transpose_csr(int32_t m, int32_t d, const int32_t* row_ptr, const int32_t* 
 void pad_rows(int32_t rows, int32_t cols, const int32_t* row_ptr, const int32_t* col,
               const float* val, int mult, HostCSR* out);
 
+// True if the CSR A (m x n*n) has the quarter-turn symmetry above bit for
+// bit: n and n_angles even, m = n_angles * nb, no repeated column in a row,
+// and every row i < m/2 equal to row fold_partner(i) with its columns turned.
+bool quarter_turn_symmetric(int32_t m, int32_t n, int32_t n_angles, const int32_t* row_ptr,
+                            const int32_t* col, const float* val);
+// Transposed first half of A in orbit order: row 4*o + r lists the entries
+// (i, A[i, p]) with i < half of pixel p = orbit_pixel(o, r), in ascending i,
+// from the stable transpose `at` of the whole A.
+void fold_transpose(const HostCSR& at, int32_t half, int32_t n, HostCSR* out);
+
 // Round-to-nearest-even FP32 -> BF16 bits.
 uint16_t float_to_bf16(float x);
 // Packs a row-padded column array (a multiple of PACK_ENTRIES entries) into
@@ -255,7 +312,7 @@ bool encode_pack(const int32_t* c, uint64_t* word);
 // 32 packs of a step stored consecutively.  Positions are counted in packs;
 // padding packs have value 0 (and column 0).
 #ifndef APPGA_SELL_LANES
-#define APPGA_SELL_LANES 8
+#define APPGA_SELL_LANES 4
 #endif
 constexpr int SELL_LANES = APPGA_SELL_LANES;  // 1, 2, 4, 8, 16 or 32
 static_assert(SELL_LANES >= 1 && SELL_LANES <= 32 && 32 % SELL_LANES == 0, "lanes per row");

@@ -164,6 +164,59 @@ bool build_sell(int32_t rows, const std::vector<int32_t>& row_ptr, const std::ve
   return true;
 }
 
+bool quarter_turn_symmetric(int32_t m, int32_t n, int32_t n_angles, const int32_t* row_ptr,
+                            const int32_t* col, const float* val) {
+  if (n < 2 || n % 2 != 0 || n_angles < 2 || n_angles % 2 != 0 || m % n_angles != 0)
+    return false;
+  const int32_t nb = m / n_angles, half = m / 2, d = n * n;
+  // pos[c]: entry of the partner row at column c (-1 none); an entry matched
+  // by a turned column of row i is marked -2, so a repeat fails
+  std::vector<int32_t> pos((size_t)d, -1);
+  for (int32_t i = 0; i < half; ++i) {
+    const int32_t k = fold_partner(i, half, nb);
+    const int32_t len = row_ptr[i + 1] - row_ptr[i];
+    if (row_ptr[k + 1] - row_ptr[k] != len) return false;
+    bool ok = true;
+    int32_t p = row_ptr[k];
+    for (; p < row_ptr[k + 1]; ++p) {
+      if (pos[(size_t)col[p]] != -1) {
+        ok = false;
+        break;
+      }
+      pos[(size_t)col[p]] = p;
+    }
+    for (int32_t q = row_ptr[i]; ok && q < row_ptr[i + 1]; ++q) {
+      const int32_t t = quarter_turn(col[q], n);
+      const int32_t at = pos[(size_t)t];
+      ok = at >= 0 && std::memcmp(&val[at], &val[q], sizeof(float)) == 0;
+      if (ok) pos[(size_t)t] = -2;
+    }
+    for (int32_t r = row_ptr[k]; r < p; ++r) pos[(size_t)col[r]] = -1;
+    if (!ok) return false;
+  }
+  return true;
+}
+
+void fold_transpose(const HostCSR& at, int32_t half, int32_t n, HostCSR* out) {
+  const int32_t d = at.rows;
+  out->rows = d;
+  out->cols = half;
+  out->row_ptr.assign((size_t)d + 1, 0);
+  out->col.clear();
+  out->val.clear();
+  for (int32_t k = 0; k < d; ++k) {
+    int32_t r, c;
+    orbit_pixel(k / 4, k % 4, n, &r, &c);
+    const int32_t p = r * n + c;
+    // rows of at list ray indices ascending: the first half is a prefix
+    for (int32_t q = at.row_ptr[p]; q < at.row_ptr[p + 1] && at.col[q] < half; ++q) {
+      out->col.push_back(at.col[q]);
+      out->val.push_back(at.val[q]);
+    }
+    out->row_ptr[(size_t)k + 1] = (int32_t)out->col.size();
+  }
+}
+
 uint16_t float_to_bf16(float x) {
   uint32_t u;
   std::memcpy(&u, &x, 4);

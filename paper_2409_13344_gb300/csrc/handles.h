@@ -29,6 +29,7 @@ struct Workspace {
   unsigned int* gtick = nullptr;  // group tickets of the grid reductions
   double* scalars = nullptr;      // device doubles for standalone results
   float* ft = nullptr;  // the current iterate in the 8 x 8-tiled pixel order (loop gathers)
+  float2* fpair = nullptr;  // folded loop: (f_j, f_{quarter_turn(j)}) in the tiled order
   ThetaEntry* theta_tab = nullptr;  // momentum scalars of the current run
   int theta_cap = 0;                // entries of theta_tab
   SolverState* st = nullptr;
@@ -160,6 +161,11 @@ struct appga_matrix {
   // columns, and A^T (both or neither, cols == NULL when the matrix's
   // columns do not fit the packed words)
   appga::DevSell sell_a, sell_t;
+  // the quarter-turn folded loop (when A has the symmetry bit for bit and it
+  // was not turned off): the first m/2 rows of A with tiled columns, and
+  // their transpose in orbit order, both sliced (off == NULL: not folded)
+  appga::DevSell fold_a, fold_t;
+  int32_t fold_nb = 0;  // bins per angle of the folded matrix
   float* inv_lambda = nullptr;       // 1/Lambda of the FP32 values
   float* inv_lambda_bf16 = nullptr;  // 1/Lambda of the BF16-rounded values
   int32_t has_bf16 = 0;
@@ -198,6 +204,16 @@ appga_status check_params_and_mat(appga_ctx* ctx, const appga_matrix* M, const a
 appga_status validate_inputs(appga_matrix* M, const float* g, const float* gamma, const float* f,
                              cudaStream_t s);
 void free_afppa_workspace(AfppaWorkspace* aw);
+
+// The solver loop's projection layout in fa / pa: the folded sliced
+// layout, the sliced layout or the CSR (its tiled columns when the loop
+// gathers from the tiled copy); the gather copy is ws.fpair, ws.ft or the
+// iterate ring.
+void loop_layout(const appga_matrix* M, FwdArgs* fa, PixArgs* pa);
+// True if the loop gathers from a copy of f (tiled or folded pairs).
+bool loop_gathers_copy();
+// Fills the loop's gather copy of f^k (tiled or folded pairs), if it has one.
+cudaError_t loop_gather_copy(const appga_matrix* M, const float* f, cudaStream_t s);
 
 // Orders ctx->stream after the caller's stream / the caller's after ctx->stream.
 appga_status enter_stream(appga_ctx* ctx, void* stream);

@@ -88,10 +88,23 @@ struct Shape {
 #endif
 // steps in flight per warp in the sliced layout's forward and pixel phases
 #ifndef APPGA_SELL_FW_PF
-#define APPGA_SELL_FW_PF 2
+#define APPGA_SELL_FW_PF 3
 #endif
 #ifndef APPGA_SELL_PX_PF
-#define APPGA_SELL_PX_PF 3
+#define APPGA_SELL_PX_PF 4
+#endif
+// Slices each warp of the sliced projections streams in turn (the loads of
+// the next slice are issued before the epilogue of the current one, which
+// hides that epilogue's latency); the grids shrink by the same factor.
+// Gather-ahead depth of the sliced stream (see SellGroup::stream).
+#ifndef APPGA_SELL_GA
+#define APPGA_SELL_GA 1
+#endif
+#ifndef APPGA_FW_SPW
+#define APPGA_FW_SPW 1
+#endif
+#ifndef APPGA_PX_SPW
+#define APPGA_PX_SPW 1
 #endif
 using FW = Shape<APPGA_FW_W, APPGA_FW_RPW, APPGA_FW_PF>;
 using PX = Shape<APPGA_PX_W, APPGA_PX_RPW, APPGA_PX_PF>;
@@ -356,6 +369,49 @@ __device__ __forceinline__ int4 sell_cols(SellCols c) { return c; }
 __device__ __forceinline__ SellCols sell_cols_zero() { return make_int4(0, 0, 0, 0); }
 #endif
 
+// The four gathered vector entries of a pack: one float each, or a pair
+// (the quarter-turn folded loop gathers two vectors at once).
+template <class V>
+struct Quad {
+  V x, y, z, w;
+};
+template <class V>
+__device__ __forceinline__ Quad<V> gather_quad(const V* __restrict__ x, int4 c) {
+  return {__ldg(x + c.x), __ldg(x + c.y), __ldg(x + c.z), __ldg(x + c.w)};
+}
+template <class V>
+__device__ __forceinline__ Quad<V> zero_quad() {
+  return {V{}, V{}, V{}, V{}};
+}
+// Entries 0, 2 of a pack into a0 and 1, 3 into a1.
+__device__ __forceinline__ void fma_quad(float4 v, const Quad<float>& g, float& a0, float& a1) {
+  a0 = fmaf(v.x, g.x, a0);
+  a1 = fmaf(v.y, g.y, a1);
+  a0 = fmaf(v.z, g.z, a0);
+  a1 = fmaf(v.w, g.w, a1);
+}
+__device__ __forceinline__ void fma_quad(float4 v, const Quad<float2>& g, float2& a0,
+                                         float2& a1) {
+  a0.x = fmaf(v.x, g.x.x, a0.x);
+  a0.y = fmaf(v.x, g.x.y, a0.y);
+  a1.x = fmaf(v.y, g.y.x, a1.x);
+  a1.y = fmaf(v.y, g.y.y, a1.y);
+  a0.x = fmaf(v.z, g.z.x, a0.x);
+  a0.y = fmaf(v.z, g.z.y, a0.y);
+  a1.x = fmaf(v.w, g.w.x, a1.x);
+  a1.y = fmaf(v.w, g.w.y, a1.y);
+}
+__device__ __forceinline__ float add_v(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 add_v(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ float shfl_xor_v(float a, int o) {
+  return __shfl_xor_sync(0xffffffffu, a, o);
+}
+__device__ __forceinline__ float2 shfl_xor_v(float2 a, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+}
+
 template <bool BF16, int PF>
 struct SellGroup {
   int q0, steps;
@@ -387,11 +443,18 @@ struct SellGroup {
     }
   }
 
-  __device__ __forceinline__ float stream(const DevSell& S, const float* __restrict__ x,
-                                          uint64_t pol) {
-    float a0 = 0.f, a1 = 0.f;
-    float4 xg = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (steps > 0) xg = gather4(x, sell_cols(c[0]));
+  // Row sums of the slice times x (V = float), or times both halves of x
+  // (V = float2), in every lane of the row.  The gathers of step t + GA are
+  // issued while step t accumulates (GA = 1 or 2; GA = 2 needs PF >= 3 so
+  // that step t + 2's columns are already in registers).
+  template <class V>
+  __device__ __forceinline__ V stream(const DevSell& S, const V* __restrict__ x, uint64_t pol) {
+    constexpr int GA = APPGA_SELL_GA;
+    static_assert(GA == 1 || (GA == 2 && PF >= 3), "gather-ahead depth");
+    V a0{}, a1{};
+    Quad<V> xg = zero_quad<V>(), xg2 = zero_quad<V>();
+    if (steps > 0) xg = gather_quad(x, sell_cols(c[0]));
+    if (GA == 2 && steps > 1) xg2 = gather_quad(x, sell_cols(c[1 % PF]));
     int t0 = 0;
 #if APPGA_SELL_PEEL
     // whole groups of PF steps whose refills and next gathers all exist: no
@@ -401,14 +464,18 @@ struct SellGroup {
       for (int u = 0; u < PF; ++u) {
         const int t = t0 + u;
         const float4 vv = v[u];
-        c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
-        v[u] = vals(S, q0 + ((t + PF) << 5), pol);
-        const float4 xx = xg;
-        xg = gather4(x, sell_cols(c[(u + 1) % PF]));
-        a0 = fmaf(vv.x, xx.x, a0);
-        a1 = fmaf(vv.y, xx.y, a1);
-        a0 = fmaf(vv.z, xx.z, a0);
-        a1 = fmaf(vv.w, xx.w, a1);
+        const Quad<V> xx = xg;
+        if constexpr (GA == 2) {
+          xg = xg2;
+          xg2 = gather_quad(x, sell_cols(c[(u + 2) % PF]));
+          c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+          v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+        } else {
+          c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+          v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+          xg = gather_quad(x, sell_cols(c[(u + 1) % PF]));
+        }
+        fma_quad(vv, xx, a0, a1);
       }
     }
 #endif
@@ -418,23 +485,29 @@ struct SellGroup {
         const int t = t0 + u;
         if (t < steps) {
           const float4 vv = v[u];
-          if (t + PF < steps) {  // refill this slot with step t + PF
-            c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
-            v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+          const Quad<V> xx = xg;
+          if constexpr (GA == 2) {
+            xg = xg2;
+            if (t + 2 < steps) xg2 = gather_quad(x, sell_cols(c[(u + 2) % PF]));
+            if (t + PF < steps) {  // refill this slot with step t + PF
+              c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+              v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+            }
+          } else {
+            if (t + PF < steps) {  // refill this slot with step t + PF
+              c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+              v[u] = vals(S, q0 + ((t + PF) << 5), pol);
+            }
+            // step t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
+            if (t + 1 < steps) xg = gather_quad(x, sell_cols(c[(u + 1) % PF]));
           }
-          const float4 xx = xg;
-          // step t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
-          if (t + 1 < steps) xg = gather4(x, sell_cols(c[(u + 1) % PF]));
-          a0 = fmaf(vv.x, xx.x, a0);
-          a1 = fmaf(vv.y, xx.y, a1);
-          a0 = fmaf(vv.z, xx.z, a0);
-          a1 = fmaf(vv.w, xx.w, a1);
+          fma_quad(vv, xx, a0, a1);
         }
       }
     }
-    float r = a0 + a1;
+    V r = add_v(a0, a1);
 #pragma unroll
-    for (int o = 1; o < SELL_LANES; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    for (int o = 1; o < SELL_LANES; o <<= 1) r = add_v(r, shfl_xor_v(r, o));
     return r;
   }
 };
@@ -595,11 +668,13 @@ __device__ __forceinline__ void load_theta(SolverState* st, const ThetaEntry& e)
 // ------------------------------------------------------------ k_forward
 
 // Per-row epilogue of the forward phase (steps a1, a2, a6): stores y (and in
-// the loop y~ by linearity), the guarded weight w = 1 - g/den, and adds the
-// data term y - g ln(y + gamma) of the objective to (acc_hi, acc_lo).
-__device__ __forceinline__ void forward_row(const FwdArgs& a, df th, int kk, int row, float hi,
-                                            float lo, int& hits, int& bad, float& acc_hi,
-                                            float& acc_lo) {
+// the loop y~ by linearity), the guarded weight w = 1 - g/den (returned, and
+// stored at w[row] if store_w), and adds the data term y - g ln(y + gamma) of
+// the objective to (acc_hi, acc_lo).
+__device__ __forceinline__ float forward_row(const FwdArgs& a, df th, int kk, int row, float hi,
+                                             float lo, int& hits, int& bad, float& acc_hi,
+                                             float& acc_lo, bool store_w = true) {
+  float wv = 0.f;
   const df y = quick_renorm(hi, lo);
   const float gam = a.gamma[row], gg = a.g[row];
   if (a.loop) {
@@ -625,8 +700,8 @@ __device__ __forceinline__ void forward_row(const FwdArgs& a, df th, int kk, int
     }
     // w = 1 - g/den = (den - g)/den, numerator in double-float so the
     // weight keeps its relative accuracy when den ~ g
-    const float wv = __fdiv_rn(df_to_f(df_add_f(den, -gg)), df_to_f(den));
-    a.w[row] = wv;
+    wv = __fdiv_rn(df_to_f(df_add_f(den, -gg)), df_to_f(den));
+    if (store_w) a.w[row] = wv;
     if (!isfinite(wv)) bad = 1;
   }
   if (!isfinite(y.hi)) bad = 1;
@@ -635,21 +710,39 @@ __device__ __forceinline__ void forward_row(const FwdArgs& a, df th, int kk, int
     const df term = df_add(y, df_neg(df_mul_f(df_log(df_add_f(y, gam)), gg)));
     acc_add(acc_hi, acc_lo, term.hi, term.lo);
   }
+  return wv;
 }
 
-// Blocks [0, proj_blocks<FW>(m)) project rows; in the solver loop the blocks
-// after them run the stencil tiles.
 // Rows per forward block: FW::W warps of FW::R CSR rows, or of one slice of
-// SELL_ROWS rows in the sliced layout.
+// SELL_ROWS rows in the sliced layout (per trip of the slice loop).
 template <bool SL>
 __host__ __device__ __forceinline__ constexpr int fw_block_rows() {
   return SL ? FW::W * SELL_ROWS : FW::ROWS;
+}
+// Projector blocks of the forward phase over `rows` rows: CSR row groups, or
+// sliced with each warp taking APPGA_FW_SPW slices in turn.
+__host__ __device__ __forceinline__ int fw_proj_blocks(int rows, bool sliced) {
+  if (!sliced) return (rows + FW::ROWS - 1) / FW::ROWS;
+  const int ns = (rows + SELL_ROWS - 1) / SELL_ROWS;
+  return (ns + FW::W * APPGA_FW_SPW - 1) / (FW::W * APPGA_FW_SPW);
+}
+// Blocks of the pixel phase over d pixel rows (as fw_proj_blocks).
+__host__ __device__ __forceinline__ int px_blocks(int d, bool sliced) {
+  if (!sliced) return (d + PX::ROWS - 1) / PX::ROWS;
+  const int ns = (d + SELL_ROWS - 1) / SELL_ROWS;
+  return (ns + PX::W * APPGA_PX_SPW - 1) / (PX::W * APPGA_PX_SPW);
 }
 
 // Blocks [0, nproj) project rows (CSR row groups, or slices of the sliced
 // layout when SL); in the solver loop the blocks after them run the stencil
 // tiles.
-template <bool BF16, bool DFA, bool SL>
+//
+// FOLD (quarter-turn folded loop, sliced): the slices hold A's first m/2
+// rows; each stored row i gathers the pairs fpair and yields y_i and
+// y_{fold_partner(i)}, so the block's 16 stored rows give 32 row epilogues,
+// one per lane of warp 0, and w is stored as the pairs the folded
+// back-projection gathers.
+template <bool BF16, bool DFA, bool SL, bool FOLD>
 __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   __shared__ union {
     struct {
@@ -660,12 +753,15 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     StencilSmem st;
   } sm;
   static_assert(!(SL && DFA), "the sliced layout serves the FP32-accumulated projections");
+  static_assert(!FOLD || SL, "the folded loop streams the sliced layout");
   pdl_trigger();
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int m = a.A.rows;
+  // rows streamed (FOLD: the stored first half)
+  const int m = SL ? a.S.rows : a.A.rows;
   constexpr int BROWS = fw_block_rows<SL>();
-  const int nproj = (m + BROWS - 1) / BROWS;
+  const int nproj = fw_proj_blocks(m, SL);
+  const int ns = SL ? a.S.slices : 0;
 #if APPGA_SFIRST
   // stencil tiles take the first blocks, so the projector blocks end the grid
   const int pb = (int)blockIdx.x - ((int)gridDim.x - nproj);
@@ -675,7 +771,7 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   const int sb = (int)blockIdx.x - nproj;
 #endif
   const bool proj = pb >= 0 && pb < nproj;
-  // CSR: this warp's rows; sliced: this warp's slice
+  // CSR: this warp's rows; sliced: this warp's first slice
   const int row0 = SL ? (pb * FW::W + warp) * SELL_ROWS : pb * FW::ROWS + warp * FW::R;
   const int nrows = proj ? max(0, min(SL ? SELL_ROWS : FW::R, m - row0)) : 0;
   // The warp's row bounds and first chunks of A: no kernel writes them, so
@@ -683,8 +779,8 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   RowGroup<BF16, DFA, FW::R, FW::PF> rg;
   SellGroup<BF16, APPGA_SELL_FW_PF> sg;
   uint64_t pol = 0;
+  if (proj) pol = evict_first_policy();
   if (nrows > 0) {
-    pol = evict_first_policy();
     if constexpr (SL) {
       sg.prologue(a.S, pb * FW::W + warp, lane, pol);
     } else {
@@ -717,41 +813,85 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
   }
   float acc_hi = 0.f, acc_lo = 0.f;  // this thread's share of the objective
   int hits = 0, bad = 0;
-  if (proj) {
+  if (proj && SL) {
+    // slices pb*W + warp + t*G, t = 0, 1, ...: the block's trip t covers
+    // FW::W consecutive slices, whose row sums go to warp 0, so the
+    // double-float epilogue (with the logarithm of the data term) runs once
+    // per block trip; the next slice's loads are issued before it
+    static_assert(!SL || APPGA_FEPI, "the sliced forward phase uses the block epilogue");
+    const float* f = a.ft ? a.ft : (a.loop ? a.f[kk % 3] : a.f[0]);
+    const int G = nproj * FW::W;
+    __shared__ float2 ysum[BROWS];
+    for (int base = pb * FW::W; base < ns; base += G) {  // uniform over the block
+      const int sl = base + warp;
+      const int nr = sl < ns ? min(SELL_ROWS, m - sl * SELL_ROWS) : 0;
+      float2 yy = make_float2(0.f, 0.f);  // (y, 0), or FOLD (y, y of the partner row)
+      if (nr > 0) {
+        if constexpr (FOLD) {
+          yy = sg.stream(a.S, a.fpair, pol);
+        } else {
+          yy.x = sg.stream(a.S, f, pol);
+        }
+      }
+      if (APPGA_FW_SPW > 1 && sl + G < ns) sg.prologue(a.S, sl + G, lane, pol);
+      const int wrow = lane / SELL_LANES;
+      if ((lane % SELL_LANES) == 0 && wrow < nr) ysum[warp * SELL_ROWS + wrow] = yy;
+      __syncthreads();
+      if (warp == 0) {
+        const int brow0 = base * SELL_ROWS, bn = min(BROWS, m - brow0);
+        if constexpr (FOLD) {
+          static_assert(!FOLD || BROWS % 16 == 0, "folded row epilogues in passes of 16");
+          // per pass, lanes 0-15 take 16 stored rows and lanes 16-31 their
+          // partner rows
+#pragma unroll
+          for (int p0 = 0; p0 < BROWS; p0 += 16) {
+            const int q = p0 + lane % 16;
+            const bool partner = lane >= 16;
+            float wv = 0.f;
+            if (q < bn) {
+              const float2 v = ysum[q];
+              const int row =
+                  partner ? fold_partner(brow0 + q, a.fold_half, a.fold_nb) : brow0 + q;
+              wv = forward_row(a, th, kk, row, partner ? v.y : v.x, 0.f, hits, bad, acc_hi,
+                               acc_lo, false);
+            }
+            const float wp = __shfl_down_sync(0xffffffffu, wv, 16);
+            if (!partner && q < bn && a.w != nullptr)
+              reinterpret_cast<float2*>(a.w)[brow0 + q] = make_float2(wv, wp);
+          }
+        } else {
+          for (int q = lane; q < bn; q += 32) {
+            const float2 v = ysum[q];
+            forward_row(a, th, kk, brow0 + q, v.x, v.y, hits, bad, acc_hi, acc_lo);
+          }
+        }
+      }
+      if (APPGA_FW_SPW == 1) break;  // one trip: the grid covers every slice
+      __syncthreads();  // ysum is refilled by the next trip
+    }
+  } else if (proj) {
     // the tiled copy when given (the solver's projections), else the image
     const float* f = a.ft ? a.ft : (a.loop ? a.f[kk % 3] : a.f[0]);
     float hi = 0.f, lo = 0.f;
-    // lanes holding a row sum, and which row of the warp's rows
-    bool has_row;
-    int wrow;
-    if constexpr (SL) {
-      if (nrows > 0) hi = sg.stream(a.S, f, pol);
-      wrow = lane / SELL_LANES;
-      has_row = (lane % SELL_LANES) == 0 && wrow < nrows;
-    } else {
-      if (nrows > 0) {
-        rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
-        slot_reduce<DFA>(lane, nrows, sm.slot.hi[warp], sm.slot.lo[warp], hi, lo);
-      }
-      wrow = lane;
-      has_row = lane < nrows;
+    if (nrows > 0) {
+      rg.stream(a.A, f, lane, pol, sm.slot.hi[warp], sm.slot.lo[warp]);
+      slot_reduce<DFA>(lane, nrows, sm.slot.hi[warp], sm.slot.lo[warp], hi, lo);
     }
-    constexpr int WROWS = SL ? SELL_ROWS : FW::R;
 #if APPGA_FEPI
-    // the block's row sums go to warp 0, so the double-float epilogue (with
-    // the logarithm of the data term) runs once per block, not once per warp
-    __shared__ float2 ysum[BROWS];
-    if (has_row) ysum[warp * WROWS + wrow] = make_float2(hi, lo);
+    // the block's row sums go to warp 0, so the double-float epilogue runs
+    // once per block, not once per warp
+    __shared__ float2 ysum_csr[BROWS];
+    if (lane < nrows) ysum_csr[warp * FW::R + lane] = make_float2(hi, lo);
     __syncthreads();
     if (warp == 0) {
       const int brow0 = pb * BROWS, bn = min(BROWS, m - brow0);
       for (int q = lane; q < bn; q += 32) {
-        const float2 v = ysum[q];
+        const float2 v = ysum_csr[q];
         forward_row(a, th, kk, brow0 + q, v.x, v.y, hits, bad, acc_hi, acc_lo);
       }
     }
 #else
-    if (has_row) forward_row(a, th, kk, row0 + wrow, hi, lo, hits, bad, acc_hi, acc_lo);
+    if (lane < nrows) forward_row(a, th, kk, row0 + lane, hi, lo, hits, bad, acc_hi, acc_lo);
 #endif
   } else {
     // SHOITV gradient at f~^kk and the regulariser of Phi(f^kk)
@@ -783,9 +923,10 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
 // -------------------------------------------------------------- k_pixel
 
 // EM-preconditioned projected update of pixel j (Eq. EM, Eq. cloformproiota)
-// given the back-projection bp = (A^T w)_j; returns the preconditioner entry.
+// given the back-projection bp = (A^T w)_j; returns the preconditioner entry
+// and leaves f_j^{k+1} in fn.
 __device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, float bp,
-                                              int& bad) {
+                                              int& bad, float& fn_out) {
   const float* fk = a.f[kk % 3];
   const float vk = fk[j];
   const float ft = fmaf(a.st->theta_hi, vk - a.f[(kk + 2) % 3][j], vk);
@@ -804,6 +945,7 @@ __device__ __forceinline__ float pixel_update(const PixArgs& a, int kk, int j, f
   const float fn = fmaxf(xv, 0.f);
   a.f[(kk + 1) % 3][j] = fn;
   if (a.ft) a.ft[tiled_index(j / a.n, j % a.n, a.n)] = fn;  // the next forward's gathers
+  fn_out = fn;
   return p;
 }
 
@@ -878,17 +1020,17 @@ __device__ void fused_finalize(const PixArgs& a, SolverState* st, int kk) {
   }
 }
 
-// Pixel rows per block: PX::W warps of PX::R CSR rows of A^T, or of one
-// slice of SELL_ROWS rows in the sliced layout.
-template <bool SL>
-__host__ __device__ __forceinline__ constexpr int px_block_rows() {
-  return SL ? PX::W * SELL_ROWS : PX::ROWS;
-}
 
-template <bool BF16, bool SL>
+// FOLD (quarter-turn folded loop, sliced): warp o streams the folded A^T
+// rows of orbit o's four pixels q_r = turn^r(q_0), one per SELL_LANES lanes,
+// gathering the w pairs; (A^T w)_{q_r} = s1(q_r) + s2(q_{r-1}), the second
+// term from the lanes of member r-1, and f^{k+1} at q_r goes out with its
+// turned neighbour f^{k+1} at q_{r+1} as the next forward phase's pair.
+template <bool BF16, bool SL, bool FOLD>
 __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   __shared__ float slot[PX::W][PX::R * SLOT_W];
   __shared__ int4 sbnd[PX::W][4];
+  static_assert(!FOLD || (SL && SELL_ROWS % 4 == 0), "a folded slice is whole orbits of four");
   pdl_trigger();
   SolverState* st = a.st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -899,9 +1041,8 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   // row bounds and first chunks of A^T before waiting (no kernel writes them)
   RowGroup<BF16, false, PX::R, PX::PF> rg;
   SellGroup<BF16, APPGA_SELL_PX_PF> sg;
-  uint64_t pol = 0;
+  uint64_t pol = evict_first_policy();
   if (np > 0) {
-    pol = evict_first_policy();
     if constexpr (SL) {
       sg.prologue(a.S, blockIdx.x * PX::W + warp, lane, pol);
     } else {
@@ -918,23 +1059,58 @@ __global__ void PX_BOUNDS k_pixel(PixArgs a) {
   const int kk = st->k;
   if (a.fuse_fin) fused_finalize(a, st, kk);
   int bad = 0;
-  float bp = 0.f, unused = 0.f;
-  int j = -1;  // the pixel whose update this lane makes
+  float pmax = 0.f;  // largest preconditioner entry this lane met
   if constexpr (SL) {
-    if (np > 0) bp = sg.stream(a.S, a.w, pol);
-    if ((lane % SELL_LANES) == 0 && lane / SELL_LANES < np) j = j0 + lane / SELL_LANES;
+    // slices blockIdx.x * W + warp + t*G, t = 0, 1, ... (warp-uniform); the
+    // next slice's loads are issued before this slice's pixel updates
+    const int ns = a.S.slices, G = gridDim.x * PX::W;
+    for (int sl = blockIdx.x * PX::W + warp; sl < ns; sl += G) {
+      const int npr = min(SELL_ROWS, d - sl * SELL_ROWS);
+      float bp;
+      int j = -1;  // the pixel whose update this lane makes
+      int jr = 0, jc = 0;
+      if constexpr (FOLD) {
+        const float2 sp = sg.stream(a.S, reinterpret_cast<const float2*>(a.w), pol);
+        if (APPGA_PX_SPW > 1 && sl + G < ns) sg.prologue(a.S, sl + G, lane, pol);
+        // row q of the slice is member q % 4 of orbit sl * SELL_ROWS / 4 + q / 4;
+        // member q - 1 (mod 4) of its orbit sits in row qm (a last slice may
+        // hold fewer orbits: npr rows)
+        const int q = lane / SELL_LANES, sub = lane % SELL_LANES;
+        const int qm = (q & ~3) | ((q + 3) & 3);
+        const float s2 = __shfl_sync(0xffffffffu, sp.y, qm * SELL_LANES + sub);
+        bp = sp.x + s2;
+        if (sub == 0 && q < npr) {
+          orbit_pixel(sl * (SELL_ROWS / 4) + q / 4, q & 3, a.n, &jr, &jc);
+          j = jr * a.n + jc;
+        }
+      } else {
+        bp = sg.stream(a.S, a.w, pol);
+        if (APPGA_PX_SPW > 1 && sl + G < ns) sg.prologue(a.S, sl + G, lane, pol);
+        if ((lane % SELL_LANES) == 0 && lane / SELL_LANES < npr)
+          j = sl * SELL_ROWS + lane / SELL_LANES;
+      }
+      float fn = 0.f;
+      if (j >= 0) pmax = fmaxf(pmax, pixel_update(a, kk, j, bp, bad, fn));
+      if constexpr (FOLD) {
+        // member q + 1 (mod 4) of the orbit: row qp
+        const int qp = ((lane / SELL_LANES) & ~3) | ((lane / SELL_LANES + 1) & 3);
+        const float fturn = __shfl_sync(0xffffffffu, fn, qp * SELL_LANES + lane % SELL_LANES);
+        if (j >= 0) a.fpair[tiled_index(jr, jc, a.n)] = make_float2(fn, fturn);
+      }
+      if (APPGA_PX_SPW == 1) break;  // one trip: the grid covers every slice
+    }
   } else {
+    float bp = 0.f, unused = 0.f;
     if (np > 0) {
       rg.stream(a.At, a.w, lane, pol, slot[warp], nullptr);
       slot_reduce<false>(lane, np, slot[warp], nullptr, bp, unused);
     }
-    if (lane < np) j = j0 + lane;
+    float fn = 0.f;
+    if (lane < np) pmax = fmaxf(pmax, pixel_update(a, kk, j0 + lane, bp, bad, fn));
   }
-  float pj = 0.f;
-  if (j >= 0) pj = pixel_update(a, kk, j, bp, bad);
   if (a.want_pmax) {
     // largest preconditioner entry of this step (order-independent)
-    const unsigned pm = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(pj, 0.f)));
+    const unsigned pm = __reduce_max_sync(0xffffffffu, __float_as_uint(pmax));
     if (lane == 0 && pm > 0u) atomicMax(&st->pmax_bits, pm);
   }
   warp_flag_or(&st->flags, bad ? APPGA_FLAG_NONFINITE : 0);
@@ -1160,9 +1336,11 @@ __device__ __forceinline__ bool in_disk(int r, int c, int n) {
   const long long dx = 2ll * c + 1 - n, dy = 2ll * r + 1 - n;
   return dx * dx + dy * dy <= (long long)n * n;
 }
-// f_out (and f_out2, ft if not NULL; ft in the 8 x 8-tiled pixel order)
+// f_out (and f_out2, ft, fpair if not NULL; ft and fpair in the 8 x 8-tiled
+// pixel order; the disk test is invariant under the quarter turn, so a
+// folded pair holds the value twice)
 __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, float* f_out,
-                            float* f_out2, float* ft) {
+                            float* f_out2, float* ft, float2* fpair) {
   const double tmc = *actc / ((double)npfov * (double)n_angles);
   const float v = (float)tmc;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n * n; j += gridDim.x * blockDim.x) {
@@ -1171,6 +1349,7 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
     f_out[j] = x;
     if (f_out2) f_out2[j] = x;
     if (ft) ft[tiled_index(r, c, n)] = x;
+    if (fpair) fpair[tiled_index(r, c, n)] = make_float2(x, x);
   }
 }
 
@@ -1198,6 +1377,12 @@ __global__ void k_to_tiled(const float* __restrict__ f, float* __restrict__ ft, 
     ft[tiled_index(j / n, j % n, n)] = f[j];
 }
 
+__global__ void k_to_fold_pairs(const float* __restrict__ f, float2* __restrict__ fpair, int n) {
+  const int d = n * n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+    fpair[tiled_index(j / n, j % n, n)] = make_float2(f[j], f[quarter_turn(j, n)]);
+}
+
 // ------------------------------------------------------------- launchers
 
 // The solver loop's forward projection gathers f^k from a copy in the 8 x 8-
@@ -1212,6 +1397,13 @@ cudaError_t launch_to_tiled(const float* f, float* ft, int n, cudaStream_t s) {
   const int d = n * n;
   const int grid = (d + 255) / 256 < 1024 ? (d + 255) / 256 : 1024;
   k_to_tiled<<<grid, 256, 0, s>>>(f, ft, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_fold_pairs(const float* f, float2* fpair, int n, cudaStream_t s) {
+  const int d = n * n;
+  const int grid = (d + 255) / 256 < 1024 ? (d + 255) / 256 : 1024;
+  k_to_fold_pairs<<<grid, 256, 0, s>>>(f, fpair, n);
   return cudaGetLastError();
 }
 
@@ -1262,8 +1454,7 @@ cudaError_t launch_dep(void (*kern)(P...), int grid, int block, cudaStream_t s, 
 
 int stencil_tiles(int n) { return st_tiles(n); }
 int forward_blocks_of(int m, int n, bool sliced, bool stencil) {
-  const int rows = sliced ? fw_block_rows<true>() : fw_block_rows<false>();
-  return (m + rows - 1) / rows + (stencil ? st_tiles(n) : 0);
+  return fw_proj_blocks(m, sliced) + (stencil ? st_tiles(n) : 0);
 }
 int forward_blocks(int m, int n, bool sliced) { return forward_blocks_of(m, n, sliced, true); }
 
@@ -1285,48 +1476,60 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s) {
   const bool dfa = (a.loop || a.solver_acc) ? APPGA_LOOP_DF != 0 : true;
   static PerDeviceOnce carve_once;
   const cudaError_t carve = carve_once.run([] {
-    cudaError_t r = set_carveout(k_forward<true, true, false>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, false>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<false, true, false>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, false>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, true>, APPGA_CARVEOUT_FW);
-    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, true>, APPGA_CARVEOUT_FW);
+    cudaError_t r = set_carveout(k_forward<true, true, false, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, false, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, true, false, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, false, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, true, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, true, false>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<true, false, true, true>, APPGA_CARVEOUT_FW);
+    if (r == cudaSuccess) r = set_carveout(k_forward<false, false, true, true>, APPGA_CARVEOUT_FW);
     return r;
   });
   if (carve != cudaSuccess) return carve;
   // the sliced layout serves the solver's FP32-accumulated projections
   if (a.S.off != nullptr && !dfa) {
-    const int sgrid = forward_blocks_of(a.A.rows, a.n, true, a.loop && !a.no_stencil);
-    return a.use_bf16 ? launch_dep(k_forward<true, false, true>, sgrid, FW::THREADS, s, a)
-                      : launch_dep(k_forward<false, false, true>, sgrid, FW::THREADS, s, a);
+    const int sgrid = forward_blocks_of(a.S.rows, a.n, true, a.loop && !a.no_stencil);
+    if (a.fpair != nullptr)
+      return a.use_bf16 ? launch_dep(k_forward<true, false, true, true>, sgrid, FW::THREADS, s, a)
+                        : launch_dep(k_forward<false, false, true, true>, sgrid, FW::THREADS, s, a);
+    return a.use_bf16 ? launch_dep(k_forward<true, false, true, false>, sgrid, FW::THREADS, s, a)
+                      : launch_dep(k_forward<false, false, true, false>, sgrid, FW::THREADS, s, a);
   }
+  if (a.fpair != nullptr) return cudaErrorInvalidValue;  // the folded loop is sliced
   if (a.use_bf16)
-    return dfa ? launch_dep(k_forward<true, true, false>, grid, FW::THREADS, s, a)
-               : launch_dep(k_forward<true, false, false>, grid, FW::THREADS, s, a);
-  return dfa ? launch_dep(k_forward<false, true, false>, grid, FW::THREADS, s, a)
-             : launch_dep(k_forward<false, false, false>, grid, FW::THREADS, s, a);
+    return dfa ? launch_dep(k_forward<true, true, false, false>, grid, FW::THREADS, s, a)
+               : launch_dep(k_forward<true, false, false, false>, grid, FW::THREADS, s, a);
+  return dfa ? launch_dep(k_forward<false, true, false, false>, grid, FW::THREADS, s, a)
+             : launch_dep(k_forward<false, false, false, false>, grid, FW::THREADS, s, a);
 }
 
 cudaError_t launch_pixel(const PixArgs& a, cudaStream_t s) {
   static PerDeviceOnce carve_once;
   const cudaError_t carve = carve_once.run([] {
-    cudaError_t r = set_carveout(k_pixel<true, false>, APPGA_CARVEOUT_PX);
-    if (r == cudaSuccess) r = set_carveout(k_pixel<false, false>, APPGA_CARVEOUT_PX);
-    if (r == cudaSuccess) r = set_carveout(k_pixel<true, true>, APPGA_CARVEOUT_PX);
-    if (r == cudaSuccess) r = set_carveout(k_pixel<false, true>, APPGA_CARVEOUT_PX);
+    cudaError_t r = set_carveout(k_pixel<true, false, false>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<false, false, false>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<true, true, false>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<false, true, false>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<true, true, true>, APPGA_CARVEOUT_PX);
+    if (r == cudaSuccess) r = set_carveout(k_pixel<false, true, true>, APPGA_CARVEOUT_PX);
     return r;
   });
   if (carve != cudaSuccess) return carve;
   const bool sl = a.S.off != nullptr;
-  const int rows_pb = sl ? px_block_rows<true>() : px_block_rows<false>();
-  const int grid = (a.At.rows + rows_pb - 1) / rows_pb;
+  const bool fold = a.fpair != nullptr;
+  if (fold && (!sl || a.S.rows != a.At.rows || a.n % 2 != 0)) return cudaErrorInvalidValue;
+  const int grid = px_blocks(a.At.rows, sl);
   cudaError_t e;
-  if (a.use_bf16)
-    e = sl ? launch_dep(k_pixel<true, true>, grid, PX::THREADS, s, a)
-           : launch_dep(k_pixel<true, false>, grid, PX::THREADS, s, a);
+  if (fold)
+    e = a.use_bf16 ? launch_dep(k_pixel<true, true, true>, grid, PX::THREADS, s, a)
+                   : launch_dep(k_pixel<false, true, true>, grid, PX::THREADS, s, a);
+  else if (a.use_bf16)
+    e = sl ? launch_dep(k_pixel<true, true, false>, grid, PX::THREADS, s, a)
+           : launch_dep(k_pixel<true, false, false>, grid, PX::THREADS, s, a);
   else
-    e = sl ? launch_dep(k_pixel<false, true>, grid, PX::THREADS, s, a)
-           : launch_dep(k_pixel<false, false>, grid, PX::THREADS, s, a);
+    e = sl ? launch_dep(k_pixel<false, true, false>, grid, PX::THREADS, s, a)
+           : launch_dep(k_pixel<false, false, false>, grid, PX::THREADS, s, a);
   if (e != cudaSuccess || a.theta_tab == nullptr || a.fuse_fin) return e;
   return launch_dep(k_finalize, 1, FIN_THREADS, s, a);
 }
@@ -1401,14 +1604,14 @@ long long disk_pixels(int n) {
 cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int n, int n_angles,
                                  long long npfov, float2* partial, unsigned int* gtick,
                                  SolverState* st, float* f_out, cudaStream_t s, float* f_out2,
-                                 float* ft, SolverState* check_st) {
+                                 float* ft, SolverState* check_st, float2* fpair) {
   // the ACTc scalar is parked in the last partial slot (as raw bytes of a double)
   double* actc = reinterpret_cast<double*>(partial + max_partials(m, n) - 1);
   k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, gtick, st, actc, check_st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_fill_disk<<<(n * n + 255) / 256 < 1024 ? (n * n + 255) / 256 : 1024, 256, 0, s>>>(
-      n, n_angles, (int)npfov, actc, f_out, f_out2, ft);
+      n, n_angles, (int)npfov, actc, f_out, f_out2, ft, fpair);
   return cudaGetLastError();
 }
 

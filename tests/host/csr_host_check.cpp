@@ -15,6 +15,12 @@
 //          sliced layout (build_sell): int32 ok, slices, n_packs,
 //          int32 off[slices+1], uint64 cols[n_packs], float vals[4 n_packs]
 //          (only the ok flag when it is 0).
+//          Then, if the input ends with int32 fold_n, fold_na (fold_n > 0):
+//          int32 quarter_turn_symmetric(m, fold_n, fold_na, A); int32
+//          orbit_pixel(k / 4, k % 4) as r * n + c for k < d; int32
+//          quarter_turn(j) for j < d; and if symmetric, int32
+//          fold_partner(i) for i < m / 2 and the folded transpose
+//          (fold_transpose of A^T, half = m / 2) as a CSR as above.
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -55,6 +61,8 @@ int main(int argc, char** argv) {
   if (!read_n(in, &nsides, 1) || nsides < 0) return 7;
   std::vector<int32_t> sides((size_t)nsides);
   if (!read_n(in, sides.data(), sides.size())) return 8;
+  int32_t fold[2] = {0, 0};
+  if (!read_n(in, fold, 2)) fold[0] = 0;
   std::fclose(in);
 
   std::string why;
@@ -92,6 +100,30 @@ int main(int argc, char** argv) {
     std::fwrite(sl.off.data(), 4, sl.off.size(), out);
     std::fwrite(sl.cols.data(), 8, sl.cols.size(), out);
     std::fwrite(sl.vals.data(), 4, sl.vals.size(), out);
+  }
+  if (fold[0] > 0) {
+    const int32_t n = fold[0], na = fold[1];
+    const int32_t sym =
+        appga::quarter_turn_symmetric(m, n, na, row_ptr.data(), col.data(), val.data()) ? 1 : 0;
+    std::fwrite(&sym, 4, 1, out);
+    std::vector<int32_t> orb((size_t)d), turn((size_t)d);
+    for (int32_t k = 0; k < d; ++k) {
+      int32_t r = 0, c = 0;
+      if (n % 2 == 0) appga::orbit_pixel(k / 4, k % 4, n, &r, &c);
+      orb[(size_t)k] = r * n + c;
+      turn[(size_t)k] = appga::quarter_turn(k, n);
+    }
+    std::fwrite(orb.data(), 4, orb.size(), out);
+    std::fwrite(turn.data(), 4, turn.size(), out);
+    if (sym) {
+      const int32_t half = m / 2, nb = m / na;
+      std::vector<int32_t> partner((size_t)half);
+      for (int32_t i = 0; i < half; ++i) partner[(size_t)i] = appga::fold_partner(i, half, nb);
+      std::fwrite(partner.data(), 4, partner.size(), out);
+      appga::HostCSR ft;
+      appga::fold_transpose(at, half, n, &ft);
+      write_csr(out, ft);
+    }
   }
   std::fclose(out);
   return 0;

@@ -395,6 +395,71 @@ def test_guard_hits_counted(A, ctx, mats):
     assert rel_l2(out.cpu().numpy(), f_next) <= 1e-5
 
 
+ODD_ORBITS = W.Geometry(18, 12, 27)  # 81 pixel orbits: the last pixel block is partial
+
+
+@pytest.mark.parametrize("gk", ["64", RAGGED, SPARSE, ODD_ORBITS],
+                         ids=["64", "ragged40", "sparse16", "orbits81"])
+@pytest.mark.parametrize("bf16", [False, True], ids=["fp32", "bf16"])
+def test_quarter_turn_fold(A, ctx, gk, bf16):
+    # The Siddon matrices have the scanner's quarter-turn symmetry, so the
+    # solver loop streams the folded halves of A and A^T; turned off, it
+    # streams the whole matrices.  Both are the same method: images agree to
+    # FP32 rounding of the sums, and both match the oracle.
+    geom, Amat, sl = problem(gk)
+    mf = A.Matrix(ctx, Amat, geom.n, geom.n_angles, bf16=bf16)
+    mu = A.Matrix(ctx, Amat, geom.n, geom.n_angles, bf16=bf16, fold=False)
+    try:
+        assert mf.info().quarter_turn_folded == 1
+        assert mu.info().quarter_turn_folded == 0
+        kw = dict(max_iters=30, track_objective=1, beta=0.1,
+                  a_precision=A.APPGA_PREC_BF16 if bf16 else A.APPGA_PREC_FP32)
+        ff, sf = run_gpu(A, ctx, mf, sl, **kw)
+        fu, su = run_gpu(A, ctx, mu, sl, **kw)
+        assert sf.iters == su.iters == 30
+        assert rel_l2(ff, fu) <= 2e-6
+        assert abs(sf.phi - su.phi) <= 1e-9 * abs(su.phi)
+        Aref = Amat
+        if bf16:
+            Aref = Amat.copy()
+            Aref.data = bf16_round(Amat.data)
+        prob, ref = run_oracle(geom, Aref, sl, max_iters=30, beta=0.1)
+        assert rel_l2(ff, ref.f) <= 1e-5
+        # the folded loop's resume continues an uninterrupted run bit for bit
+        g, gamma = to_dev(sl.g), to_dev(sl.gamma)
+        p = A.default_params(max_iters=30, beta=0.1, a_precision=kw["a_precision"])
+        full = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+        A.appga_reconstruct(ctx.handle, mf.handle, g, gamma, None, p, full)
+        f0 = torch.empty_like(full)
+        A.appga_initial_image(ctx.handle, mf.handle, g, gamma, f0)
+        p13 = A.default_params(max_iters=13, beta=0.1, a_precision=kw["a_precision"])
+        p17 = A.default_params(max_iters=17, beta=0.1, a_precision=kw["a_precision"])
+        a_prev, a_cur, out = (torch.empty_like(full) for _ in range(3))
+        A.appga_resume(ctx.handle, mf.handle, g, gamma, f0, f0, 1, p13, a_prev, a_cur)
+        A.appga_resume(ctx.handle, mf.handle, g, gamma, a_prev, a_cur, 14, p17, None, out)
+        assert torch.equal(out, full)
+    finally:
+        mf.close()
+        mu.close()
+
+
+def test_quarter_turn_fold_only_where_it_holds(A, ctx, mats):
+    assert mats["64"].info().quarter_turn_folded == 1
+    assert mats[mkey(TINY)].info().quarter_turn_folded == 0  # odd side
+    geom, Amat, sl = problem("64")
+    B = Amat.copy()
+    B.data = B.data.copy()
+    B.data[12345] = np.nextafter(B.data[12345], np.float32(10.0))  # one value bit
+    mb = A.Matrix(ctx, B, geom.n, geom.n_angles)
+    try:
+        assert mb.info().quarter_turn_folded == 0
+        f, st = run_gpu(A, ctx, mb, sl, max_iters=20, beta=0.1)
+        prob, ref = run_oracle(geom, B, sl, max_iters=20, beta=0.1)
+        assert rel_l2(f, ref.f) <= 1e-5
+    finally:
+        mb.close()
+
+
 def test_resume_is_bitwise_continuation(A, ctx, mats):
     geom, Amat, sl = problem("64")
     mat = mats["64"]

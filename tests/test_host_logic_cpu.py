@@ -18,7 +18,14 @@ independent implementations:
   and pixels within a block in raster order;
 * the sliced layout of the solver loop's projections, decoded here from its
   documented word format and position rule, holds every padded row's
-  entries in order and zero values everywhere else.
+  entries in order and zero values everywhere else;
+* the quarter-turn fold: the symmetry check accepts the Siddon matrices and
+  rejects every matrix that breaks the symmetry by one column, one value bit,
+  a repeated column or an odd size; the turn is NumPy's rot90 of the image;
+  the orbit order lists each pixel once, in orbits of four turned pixels; and
+  the two identities the folded loop rests on hold on the matrix, A f over
+  the partner rows from the first half of A and the turned image, and A^T w
+  from the folded transpose's two sums.
 """
 import os
 import shutil
@@ -47,7 +54,7 @@ def harness(tmp_path_factory):
     return exe
 
 
-def _run(exe, tmp_path, m, d, row_ptr, col, val, bf_in):
+def _run(exe, tmp_path, m, d, row_ptr, col, val, bf_in, fold=None):
     inp, out = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(inp, "wb") as f:
         np.array([m, d, len(col), len(bf_in)], np.int32).tofile(f)
@@ -56,6 +63,8 @@ def _run(exe, tmp_path, m, d, row_ptr, col, val, bf_in):
         np.asarray(val, np.float32).tofile(f)
         np.asarray(bf_in, np.float32).tofile(f)
         np.array([len(SIDES)] + list(SIDES), np.int32).tofile(f)
+        if fold is not None:
+            np.array(fold, np.int32).tofile(f)
     subprocess.run([exe, inp, out], check=True)
     raw = open(out, "rb").read()
     pos = 0
@@ -83,6 +92,15 @@ def _run(exe, tmp_path, m, d, row_ptr, col, val, bf_in):
             continue
         slices, npk = take(np.int32, 2)
         res[key] = (take(np.int32, slices + 1), take(np.uint64, npk), take(np.float32, 4 * npk))
+    if fold is not None:
+        res["sym"] = int(take(np.int32, 1)[0])
+        res["orbit"] = take(np.int32, d)
+        res["turn"] = take(np.int32, d)
+        if res["sym"]:
+            res["partner"] = take(np.int32, m // 2)
+            rows, nnz = take(np.int32, 2)
+            res["fold_t"] = (take(np.int32, rows + 1), take(np.int32, nnz),
+                             take(np.float32, nnz))
     assert pos == len(raw)
     return res
 
@@ -211,7 +229,7 @@ def test_tiled_pixel_order(harness, tmp_path):
                     np.testing.assert_array_equal(np.sort(blk.reshape(-1) % 64), np.arange(64))
 
 
-SELL_LANES = 8
+SELL_LANES = 4   # lanes per row of the sliced layout (APPGA_SELL_LANES)
 SELL_ROWS = 32 // SELL_LANES
 
 
@@ -267,3 +285,106 @@ def test_sliced_layout_refuses_columns_beyond_the_word(harness, tmp_path):
     res = _run(harness, tmp_path, 1, 9001, [0, 2], [0, 9000], [1.0, 2.0],
                np.zeros(0, np.float32))
     assert res["sell_a"] is None
+
+
+def _fold_run(harness, tmp_path, A, n, na):
+    m, d = A.shape
+    return _run(harness, tmp_path, m, d, A.indptr, A.indices, A.data.astype(np.float32), [],
+                fold=(n, na))
+
+
+@pytest.mark.parametrize("name", ["64", "128"])
+def test_quarter_turn_fold_of_siddon_matrix(harness, tmp_path, name):
+    from paper_2409_13344_gb300 import workload as W
+    geom = W.GEOMETRIES[name]
+    A = W.system_matrix(name).tocsr()
+    n, na, nb = geom.n, geom.n_angles, geom.n_bins
+    m, d = A.shape
+    res = _fold_run(harness, tmp_path, A, n, na)
+    assert res["sym"] == 1
+    # the turn: the pixel that rot90 (a quarter turn of the image array)
+    # moves pixel j to
+    idx = np.arange(d).reshape(n, n)
+    turned = np.rot90(idx)               # turned[p] = the pixel that lands on p
+    to = np.empty(d, np.int64)
+    to[turned.reshape(-1)] = np.arange(d)
+    np.testing.assert_array_equal(res["turn"], to)
+    # orbit order: every pixel once, each group of four is j, turn(j), ...
+    orb = res["orbit"]
+    assert sorted(orb.tolist()) == list(range(d))
+    grp = orb.reshape(-1, 4)
+    for r in range(4):
+        np.testing.assert_array_equal(to[grp[:, r]], grp[:, (r + 1) % 4])
+    # partner rows: angle a + NPA/2, bin nb-1-b
+    half = m // 2
+    i = np.arange(half)
+    np.testing.assert_array_equal(res["partner"], (i // nb + na // 2) * nb + nb - 1 - i % nb)
+    # identity of the folded forward projection: (A f)_partner(i) equals row
+    # i of A times the turned image, (f o turn)_j = f_turn(j)
+    rng = np.random.default_rng(11)
+    f = rng.uniform(0.0, 2.0, d)
+    A64 = A.astype(np.float64)
+    A1 = A64[:half]
+    y = A64 @ f
+    np.testing.assert_allclose(y[res["partner"]], A1 @ f[to], rtol=1e-12, atol=1e-12)
+    # identity of the folded back-projection: (A^T w)_q = s1(q) + s2(turn^-1 q)
+    # with s1, s2 the folded transpose's sums over w and w o partner
+    w = rng.uniform(-1.0, 1.0, m)
+    t_ptr, t_col, t_val = res["fold_t"]
+    FT = sp.csr_matrix((t_val.astype(np.float64), t_col, t_ptr), shape=(d, half))
+    s1 = FT @ w[:half]
+    s2 = FT @ w[res["partner"]]
+    bp = np.empty(d)
+    for r in range(4):
+        bp[grp[:, r]] = s1.reshape(-1, 4)[:, r] + s2.reshape(-1, 4)[:, (r + 3) % 4]
+    np.testing.assert_allclose(bp, A64.T @ w, rtol=1e-12, atol=1e-12)
+    # each folded transposed row: the rays of the first half through its pixel
+    At1 = A1.T.tocsr()
+    for k in (0, 1, 2, 3, d // 2 + 5, d - 1):
+        p = orb[k]
+        np.testing.assert_array_equal(t_col[t_ptr[k]:t_ptr[k + 1]],
+                                      At1.indices[At1.indptr[p]:At1.indptr[p + 1]])
+
+
+def test_quarter_turn_check_rejects_broken_symmetry(harness, tmp_path):
+    from paper_2409_13344_gb300 import workload as W
+    geom = W.GEOMETRIES["64"]
+    A = W.system_matrix("64").tocsr()
+    n, na, nb = geom.n, geom.n_angles, geom.n_bins
+    m = A.shape[0]
+    rng = np.random.default_rng(5)
+    p = int(rng.integers(0, A.nnz))
+    # one value one bit up
+    B = A.copy()
+    B.data = B.data.copy()
+    B.data[p] = np.nextafter(B.data[p], np.float32(np.inf))
+    assert _fold_run(harness, tmp_path, B, n, na)["sym"] == 0
+    # one entry moved to a column its row does not have
+    B = A.copy()
+    B.indices = B.indices.copy()
+    row = int(np.searchsorted(B.indptr, p, side="right") - 1)
+    have = set(B.indices[B.indptr[row]:B.indptr[row + 1]].tolist())
+    B.indices[p] = next(x for x in range(n * n) if x not in have)
+    assert _fold_run(harness, tmp_path, B, n, na)["sym"] == 0
+    # a repeated column, added to a row and, turned, to its partner row
+    i = int(np.argmax(np.diff(A.indptr)[:m // 2] > 3))
+    k = (i // nb + na // 2) * nb + nb - 1 - i % nb
+    ci, vi = int(A.indices[A.indptr[i]]), A.data[A.indptr[i]]
+    coo = A.tocoo()
+    rows = np.concatenate([coo.row, [i, k]])
+    cols = np.concatenate([coo.col, [ci, (n - 1 - ci % n) * n + ci // n]])
+    vals = np.concatenate([coo.data, [vi, vi]]).astype(np.float32)
+    order = np.argsort(rows, kind="stable")
+    D = sp.csr_matrix((vals[order], cols[order],
+                       np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))])),
+                      shape=A.shape)
+    assert D.nnz == A.nnz + 2
+    assert _fold_run(harness, tmp_path, D, n, na)["sym"] == 0
+    # odd numbers of angles and an odd image side have no fold
+    A5 = W.siddon_matrix(W.Geometry(8, 5, 11))
+    assert _fold_run(harness, tmp_path, A5, 8, 5)["sym"] == 0
+    A9 = W.siddon_matrix(W.Geometry(9, 4, 13))
+    assert _fold_run(harness, tmp_path, A9, 9, 4)["sym"] == 0
+    # another even side and even number of angles has it
+    A10 = W.siddon_matrix(W.Geometry(10, 6, 15))
+    assert _fold_run(harness, tmp_path, A10, 10, 6)["sym"] == 1

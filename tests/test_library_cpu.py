@@ -52,7 +52,7 @@ def test_struct_layouts_match_header(lib):
     from paper_2409_13344_gb300 import appga
     assert ctypes.sizeof(appga.appga_params) == 96
     assert ctypes.sizeof(appga.appga_stats) == 40
-    assert ctypes.sizeof(appga.appga_matrix_info) == 64
+    assert ctypes.sizeof(appga.appga_matrix_info) == 72
 
 
 def test_struct_layouts_match_c_compiler(lib, tmp_path):
