@@ -65,11 +65,15 @@ def test_algorithmic_bytes_match_the_committed_record():
     ffw, fpx = b.kernel_bytes(m, d, nnz, 6, True, True)
     assert ffw == 6 * (nnz // 2) + 4 * (m // 2 // 4 + 1) + 4 * d + 28 * m + 12 * d
     assert fpx == 6 * (nnz // 2) + 4 * (d // 4 + 1) + 4 * m + 20 * d
+    # the record of the committed capture: algorithmic bytes in the plain
+    # format, and the bytes its layout streams
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    if rec.get("bytes_per_nnz") == 6:
-        want = (ffw, fpx) if rec.get("folded") else (fwd, pix)
-        assert want[0] == rec["kernels"]["k_forward"]["algorithmic_bytes_per_launch"]
-        assert want[1] == rec["kernels"]["k_pixel"]["algorithmic_bytes_per_launch"]
+    cfw, cpx = b.kernel_bytes(m, d, nnz)
+    assert cfw == rec["kernels"]["k_forward"]["algorithmic_bytes_per_launch"]
+    assert cpx == rec["kernels"]["k_pixel"]["algorithmic_bytes_per_launch"]
+    sfw, spx = b.kernel_bytes(m, d, nnz, rec["bytes_per_nnz"], True, rec["folded"])
+    assert sfw == rec["kernels"]["k_forward"]["stored_bytes_per_launch"]
+    assert spx == rec["kernels"]["k_pixel"]["stored_bytes_per_launch"]
     # both streams dominate: 12 B per nonzero is 97-98 % of an iteration's bytes
     assert 0.97 < 12 * nnz / (fwd + pix) < 0.99
     # a batched iteration of 64 slices reads the matrix once: far below 64 iterations
@@ -78,20 +82,26 @@ def test_algorithmic_bytes_match_the_committed_record():
 
 
 def test_traffic_is_reported_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
-    """ncu traffic is attached to the roofline only while kernels.cu is the
-    source the capture was taken on (its SHA-256 is in the record)."""
+    """ncu traffic is attached to the roofline only while the loop kernels'
+    sources are those the capture was taken on (their SHA-256 is in the
+    record)."""
     import hashlib
     b = _bench_module()
     src = tmp_path / "paper_2409_13344_gb300" / "csrc"
     src.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
-    code = b"// kernel source\n"
-    (src / "kernels.cu").write_bytes(code)
-    rec = {"kernels_cu_sha256": hashlib.sha256(code).hexdigest(),
+    files = {name: f"// {name}\n".encode() for name in b.KERNEL_SOURCES}
+    for name, code in files.items():
+        (src / name).write_bytes(code)
+    sha = hashlib.sha256(b"".join(files[n] for n in b.KERNEL_SOURCES)).hexdigest()
+    rec = {"kernel_sources_sha256": sha,
            "kernels": {"k_pixel": {"dram_bytes_per_launch": 123}}}
     (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.committed_traffic("k_pixel") == 123
     assert b.committed_traffic("k_forward") is None
-    (src / "kernels.cu").write_bytes(code + b"// changed\n")
-    assert b.committed_traffic("k_pixel") is None
+    for name in b.KERNEL_SOURCES:  # a change to any of them drops the figure
+        (src / name).write_bytes(files[name] + b"// changed\n")
+        assert b.committed_traffic("k_pixel") is None
+        (src / name).write_bytes(files[name])
+    assert b.committed_traffic("k_pixel") == 123
