@@ -163,7 +163,7 @@ def kernel_bytes(m: int, d: int, nnz: int, per_nnz: int = 8, sliced: bool = Fals
     and 4-byte columns), its row (or slice) offsets, and every vector once.
     Folded (the quarter-turn symmetry): the loop stores and streams the first
     half of A's rows and their transpose, nnz/2 entries each."""
-    rows_per_offset = 4 if sliced else 1   # the sliced layout keeps one offset per 4 rows
+    rows_per_offset = 8 if sliced else 1   # the sliced layout keeps one offset per 8 rows
     stored = nnz // 2 if folded else nnz
     m_rows = m // 2 if folded else m
     fwd = (per_nnz * stored + 4 * (m_rows // rows_per_offset + 1)

@@ -57,14 +57,15 @@ def test_algorithmic_bytes_match_the_committed_record():
     b = _bench_module()
     m, d, nnz = 66060, 65536, 15017956
     fwd, pix = b.kernel_bytes(m, d, nnz, 6, True)
-    # written out: matrix, offsets (one per 4 rows), f, g, gamma, y_prev, y, w, stencil vectors
-    assert fwd == 6 * nnz + 4 * (m // 4 + 1) + 4 * d + (4 + 4 + 8 + 8 + 4) * m + 12 * d
-    assert pix == 6 * nnz + 4 * (d // 4 + 1) + 4 * m + 20 * d
+    # written out: matrix, offsets (one per slice of 8 rows), f, g, gamma, y_prev, y, w,
+    # stencil vectors
+    assert fwd == 6 * nnz + 4 * (m // 8 + 1) + 4 * d + (4 + 4 + 8 + 8 + 4) * m + 12 * d
+    assert pix == 6 * nnz + 4 * (d // 8 + 1) + 4 * m + 20 * d
     assert b.kernel_bytes(m, d, nnz)[1] == 8 * nnz + 4 * (d + 1) + 4 * m + 20 * d
     # folded by the quarter-turn symmetry: half the stored entries and rows
     ffw, fpx = b.kernel_bytes(m, d, nnz, 6, True, True)
-    assert ffw == 6 * (nnz // 2) + 4 * (m // 2 // 4 + 1) + 4 * d + 28 * m + 12 * d
-    assert fpx == 6 * (nnz // 2) + 4 * (d // 4 + 1) + 4 * m + 20 * d
+    assert ffw == 6 * (nnz // 2) + 4 * (m // 2 // 8 + 1) + 4 * d + 28 * m + 12 * d
+    assert fpx == 6 * (nnz // 2) + 4 * (d // 8 + 1) + 4 * m + 20 * d
     # the record of the committed capture: algorithmic bytes in the plain
     # format, and the bytes its layout streams
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
