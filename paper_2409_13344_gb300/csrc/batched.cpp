@@ -40,6 +40,9 @@ void free_batch_workspace(BatchWorkspace* bw) {
   cudaFreeHost(bw->slots_host);
   cudaFreeHost(bw->bst_host);
   cudaFreeHost(bw->flag_host);
+  if (bw->side) cudaStreamDestroy(bw->side);
+  if (bw->ev_fork) cudaEventDestroy(bw->ev_fork);
+  if (bw->ev_join) cudaEventDestroy(bw->ev_join);
   *bw = BatchWorkspace();
 }
 
@@ -150,10 +153,20 @@ cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, c
     if (e == cudaSuccess && vb)
       e = launch_slots_to_slices(vb->slot_ring, vb->slice_ring, vb->d, vb->Kp, vb->nz,
                                  vb->va.bst, 0, s);
+    if (vb) {
+      // the 3-D stencil needs only the iterate: its branch runs beside the
+      // forward phase (which reads the same iterate and writes w, y and the
+      // objective rows before the stencil's) and joins before the update
+      if (e == cudaSuccess) e = cudaEventRecord(vb->ev_fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(vb->side, vb->ev_fork, 0);
+      if (e == cudaSuccess) e = launch_stencil3d(vb->va, vb->side);
+      if (e == cudaSuccess)
+        e = launch_slices_to_slots(vb->va.gR, fa.gR, vb->d, vb->Kp, vb->nz, vb->va.bst,
+                                   vb->side);
+      if (e == cudaSuccess) e = cudaEventRecord(vb->ev_join, vb->side);
+    }
     if (e == cudaSuccess) e = launch_bforward(fa, s);
-    if (e == cudaSuccess && vb) e = launch_stencil3d(vb->va, s);
-    if (e == cudaSuccess && vb)
-      e = launch_slices_to_slots(vb->va.gR, fa.gR, vb->d, vb->Kp, vb->nz, vb->va.bst, s);
+    if (e == cudaSuccess && vb) e = cudaStreamWaitEvent(s, vb->ev_join, 0);
   }
   const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   if (e == cudaSuccess) e = e2;
@@ -189,6 +202,13 @@ SlotState slot_from_params(const appga_params* p, int k0, bool active) {
 namespace {
 
 constexpr int kBatchGraphIters = 8;
+// forward-phase blocks per SM in volume mode: 5 (one resident wave at 48
+// registers per thread) measured fastest with the 3-D stencil's branch
+// beside it (680.6 us per 64 x 256^2 volume iteration; 4: 725.9, 3: 842.7,
+// the batched default of 8: 727.3); 0 keeps the batched default
+#ifndef APPGA_VOL_SPMV_PER_SM
+#define APPGA_VOL_SPMV_PER_SM 5
+#endif
 
 int padded_width(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
 
@@ -286,7 +306,15 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
     for (int i = 0; i < 3; ++i)
       if (!b.fsm[i]) CK(cudaMalloc((void**)&b.fsm[i], (size_t)d * Kp * sizeof(float)));
     if (!b.gsm) CK(cudaMalloc((void**)&b.gsm, (size_t)d * Kp * sizeof(float)));
+    if (!b.side) CK(cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking));
+    if (!b.ev_fork) CK(cudaEventCreateWithFlags(&b.ev_fork, cudaEventDisableTiming));
+    if (!b.ev_join) CK(cudaEventCreateWithFlags(&b.ev_join, cudaEventDisableTiming));
+    vb.side = b.side;
+    vb.ev_fork = b.ev_fork;
+    vb.ev_join = b.ev_join;
     fa.no_stencil = 1;
+    // leave room on each SM for a stencil block beside the forward phase's
+    if (sch.spmv_per_sm == 0) fa.spmv_per_sm = APPGA_VOL_SPMV_PER_SM;
     pa.joint = 1;
     const int nfw = bforward_grid(fa);
     Vol3Args& va = vb.va;

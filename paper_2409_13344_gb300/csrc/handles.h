@@ -98,6 +98,10 @@ struct BatchWorkspace {
   double* vscal_host = nullptr;  // pinned mirror
   cudaGraphExec_t gexec = nullptr;
   std::string gkey;
+  // volume mode: the 3-D stencil's branch of the captured step (a second
+  // stream forked from and joined to the solver's stream by two events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 void free_batch_workspace(BatchWorkspace* bw);
@@ -123,6 +127,10 @@ struct VolumeSteps {
   float* slot_ring[3];
   float* slice_ring[3];
   int d, Kp, nz;
+  // the stencil branch runs on `side`, forked after the iterate's transpose
+  // and joined before the next pixel update, beside the forward phase
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
 };
 cudaError_t capture_batch_graph(const BFwdArgs& fa, const BPixArgs& pa, int S, cudaStream_t s,
                                 cudaGraphExec_t* out, const VolumeSteps* vb = nullptr);

@@ -48,17 +48,17 @@ struct Vol3Smem {
   float T[3][HR][HC];        // f~ ring
   float K[3][HR][HC];        // f^k ring (regulariser value)
   float W[3][NF][WR][HC];    // grad phi~ field ring (columns WC.. unused)
-  float reg_hi[NWARP][MAXZ], reg_lo[NWARP][MAXZ];
+  float regv[NT];            // the regulariser of the current plane, one value per thread
+  float reg_hi[MAXZ], reg_lo[MAXZ];  // per-slice sums of the block (double-float)
 };
 
 __device__ __forceinline__ int ring3(int p) { return (p + 6) % 3; }  // p >= -6
 
+// Which neighbours of a voxel exist: D has a zero first row along each axis,
+// so a difference towards a missing neighbour is zero.
 struct Edges {
   bool c_lo, c_hi, r_lo, r_hi, z_lo, z_hi;
 };
-__device__ __forceinline__ Edges edges(int z, int r, int c, int nz, int n) {
-  return {c >= 1, c <= n - 2, r >= 1, r <= n - 2, z >= 1, z <= nz - 2};
-}
 
 // Component Q of B x at a voxel, X(dz, dr, dc) reading x at the offset.
 // The forms are the matrix rows written out from the definition of D.
@@ -158,6 +158,21 @@ struct Planes3 {
   }
 };
 
+// What a thread knows of its points for a whole z-run (everything but z):
+// its tile pixel, its two field points of a plane and its plane loads.
+struct InPlane {
+  bool c_lo, c_hi, r_lo, r_hi, ok;  // edges of the voxel's column and row; inside the image
+};
+__device__ __forceinline__ InPlane in_plane(int r, int c, int n) {
+  return {c >= 1, c <= n - 2, r >= 1, r <= n - 2, r >= 0 && r < n && c >= 0 && c < n};
+}
+__device__ __forceinline__ Edges with_z(const InPlane& p, bool z_lo, bool z_hi) {
+  return {p.c_lo, p.c_hi, p.r_lo, p.r_hi, z_lo, z_hi};
+}
+constexpr int NFP = WR * WC;               // field points of a plane
+constexpr int FPT = (NFP + NT - 1) / NT;   // field points per thread
+constexpr int LPT = (HR * HC + NT - 1) / NT;  // plane elements per thread
+
 __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Vol3Smem& S = *reinterpret_cast<Vol3Smem*>(smem_raw);
@@ -175,9 +190,9 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
     fk = a.f[0];
     fkm = nullptr;
   }
-  for (int s = tid; s < NWARP * MAXZ; s += NT) {
-    (&S.reg_hi[0][0])[s] = 0.f;
-    (&S.reg_lo[0][0])[s] = 0.f;
+  for (int s = tid; s < MAXZ; s += NT) {
+    S.reg_hi[s] = 0.f;
+    S.reg_lo[s] = 0.f;
   }
   const int ntx = (n + TC - 1) / TC, nty = (n + TR - 1) / TR, nzr = (nz + ZRUN - 1) / ZRUN;
   const int items = ntx * nty * nzr;
@@ -186,10 +201,29 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
     const int zb = zr * ZRUN, ze = min(nz, zb + ZRUN);
     const int r0 = (txy / ntx) * TR, c0 = (txy % ntx) * TC;
     const int r = r0 + tr, c = c0 + tc;
-    // plane loads are issued one step ahead into registers (each thread
-    // holds at most LPT elements of a plane), so their latency overlaps the
-    // field and gradient work of the current step
-    constexpr int LPT = (HR * HC + NT - 1) / NT;
+    // the run's invariants: this thread's voxel column, its field points and
+    // its plane elements (2-D offset in the image, -1 outside)
+    const InPlane vox = in_plane(r, c, n);
+    const int vox_off = r * n + c;
+    InPlane fp[FPT];
+    int fp_o[FPT];  // offset of the point in the f planes; -1: no point
+#pragma unroll
+    for (int u = 0; u < FPT; ++u) {
+      const int q = tid + u * NT;
+      const int i = q / WC, j = q % WC;
+      fp[u] = in_plane(r0 - 1 + i, c0 - 1 + j, n);
+      fp_o[u] = q < NFP ? (i + 1) * HC + (j + 1) : -1;
+    }
+    int ld_off[LPT];
+#pragma unroll
+    for (int u = 0; u < LPT; ++u) {
+      const int t = tid + u * NT;
+      const int i = t / HC, j = t % HC;
+      const int rr = r0 - 2 + i, cc = c0 - 2 + j;
+      ld_off[u] = (t < HR * HC && rr >= 0 && rr < n && cc >= 0 && cc < n) ? rr * n + cc : -1;
+    }
+    // plane loads are issued one step ahead into registers, so their latency
+    // overlaps the field and gradient work of the current step
     float pk[LPT], pm[LPT];
     auto fetch = [&](int s) {
       const bool s_in = s >= 0 && s < nz;
@@ -197,25 +231,23 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
       const float* fms = fkm != nullptr ? fkm + (long long)(s_in ? s : 0) * d : nullptr;
 #pragma unroll
       for (int u = 0; u < LPT; ++u) {
-        const int t = tid + u * NT;
-        const int i = t / HC, j = t % HC;
-        const int rr = r0 - 2 + i, cc = c0 - 2 + j;
         pk[u] = 0.f;
         pm[u] = 0.f;
-        if (t < HR * HC && s_in && rr >= 0 && rr < n && cc >= 0 && cc < n) {
-          const long long o = (long long)rr * n + cc;
-          pk[u] = fks[o];
-          if (fms != nullptr) pm[u] = fms[o];
+        if (s_in && ld_off[u] >= 0) {
+          pk[u] = fks[ld_off[u]];
+          if (fms != nullptr) pm[u] = fms[ld_off[u]];
         }
       }
     };
     fetch(zb - 2);
+    // ring slots of planes s, s - 1 and s - 2 (plane s - 3 shares s's slot)
+    int ra = ring3(zb - 2), rb = ring3(zb - 3), rc = ring3(zb - 4);
     for (int s = zb - 2; s <= ze + 1; ++s) {
       // plane s of f~ = f^k + theta_s (f^k - f^{k-1}) and of f^k (zero outside
       // the volume).  The ring slot it replaces (plane s - 3) was last read
       // before the previous step's second barrier.
       {
-        const int ls = ring3(s);
+        const int ls = ra;
         const bool s_in = s >= 0 && s < nz;
         const float th = (s_in && fkm != nullptr) ? a.slots[s].theta_hi : 0.f;
 #pragma unroll
@@ -234,6 +266,7 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
       const int P = s - 1;
       if (P >= zb - 1 && P <= ze) {
         const bool inside = P >= 0 && P < nz;
+        const bool z_lo = P >= 1, z_hi = P <= nz - 2;
         float lam1 = a.lam1, lam2 = a.lam2, eps = a.eps;
         if (inside && a.slots) {
           lam1 = a.slots[P].lambda1;
@@ -241,21 +274,20 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
           eps = a.slots[P].eps;
         }
         const float inv_eps = 1.f / eps;
-        const float* Tm = &S.T[ring3(P - 1)][0][0];
-        const float* T0 = &S.T[ring3(P)][0][0];
-        const float* Tp = &S.T[ring3(P + 1)][0][0];
-        float* Wo = &S.W[ring3(P)][0][0][0];
-        for (int t = tid; t < WR * HC; t += NT) {
-          const int i = t / HC, j = t % HC;
-          if (j >= WC) continue;  // padding columns of the field planes
-          const int rr = r0 - 1 + i, cc = c0 - 1 + j;
+        const float* Tm = &S.T[rc][0][0];
+        const float* T0 = &S.T[rb][0][0];
+        const float* Tp = &S.T[ra][0][0];
+        float* Wo = &S.W[rb][0][0][0];
+#pragma unroll
+        for (int u = 0; u < FPT; ++u) {
+          if (fp_o[u] < 0) continue;
           float v[NF];
 #pragma unroll
           for (int q = 0; q < NF; ++q) v[q] = 0.f;
-          if (inside && rr >= 0 && rr < n && cc >= 0 && cc < n) {
-            const Edges e = edges(P, rr, cc, nz, n);
+          if (inside && fp[u].ok) {
+            const Edges e = with_z(fp[u], z_lo, z_hi);
             Nbr X;
-            X.load(Tm, T0, Tp, (i + 1) * HC + (j + 1));
+            X.load(Tm, T0, Tp, fp_o[u]);
             all_comps(X, e, v);
             float n1, n2;
             norms(v, n1, n2);
@@ -267,39 +299,47 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
 #pragma unroll
             for (int q = 3; q < NF; ++q) v[q] *= s2;
           }
+          const int wo = fp_o[u] - HC - 1;  // the field planes' in-plane index
 #pragma unroll
-          for (int q = 0; q < NF; ++q) Wo[q * (WR * HC) + i * HC + j] = v[q];
+          for (int q = 0; q < NF; ++q) Wo[q * (WR * HC) + wo] = v[q];
         }
-        // the regulariser at plane P from f^k (planes P - 1 .. P + 1)
+        // the regulariser at plane P from f^k (planes P - 1 .. P + 1): one
+        // value per thread, summed by one warp after the barrier
         if (a.want_reg && P >= zb && P < ze) {
           float reg = 0.f;
-          if (r < n && c < n) {
-            const Edges e = edges(P, r, c, nz, n);
+          if (vox.ok) {
+            const Edges e = with_z(vox, z_lo, z_hi);
             Nbr Xk;
-            Xk.load(&S.K[ring3(P - 1)][0][0], &S.K[ring3(P)][0][0], &S.K[ring3(P + 1)][0][0],
-                    (tr + 2) * HC + (tc + 2));
-            float u[NF];
-            all_comps(Xk, e, u);
+            Xk.load(&S.K[rc][0][0], &S.K[rb][0][0], &S.K[ra][0][0], (tr + 2) * HC + (tc + 2));
+            float uu[NF];
+            all_comps(Xk, e, uu);
             float n1, n2;
-            norms(u, n1, n2);
+            norms(uu, n1, n2);
             reg = lam1 * s_eps_f(n1, eps) + lam2 * s_eps_f(n2, eps);
           }
-          float h = reg, l = 0.f;
-          warp_sum_acc(h, l);
-          if (lane == 0) acc_add(S.reg_hi[warp][P], S.reg_lo[warp][P], h, l);
+          S.regv[tid] = reg;
         }
       }
       __syncthreads();
+      // the regulariser of plane P: warp P mod NWARP sums the block's values
+      // in a fixed order (double-float)
+      if (a.want_reg && P >= zb && P < ze && warp == (P & (NWARP - 1))) {
+        float h = 0.f, l = 0.f;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) acc_add(h, l, S.regv[k * 32 + lane], 0.f);
+        warp_sum_acc(h, l);
+        if (lane == 0) acc_add(S.reg_hi[P], S.reg_lo[P], h, l);
+      }
       // gradient at plane O = s - 2 (needs field planes O - 1 .. O + 1):
       // D^T for the first-order fields; each second-order block's transpose
       // is the block of the same form (symmetric ones) or of its partner
       // (4 <-> 6, 8 <-> 9, 10 <-> 11)
       const int O = s - 2;
-      if (O >= zb && O < ze && r < n && c < n) {
-        const Edges e = edges(O, r, c, nz, n);
-        const float* Wm = &S.W[ring3(O - 1)][0][0][0];
-        const float* W0 = &S.W[ring3(O)][0][0][0];
-        const float* Wp = &S.W[ring3(O + 1)][0][0][0];
+      if (O >= zb && O < ze && vox.ok) {
+        const Edges e = with_z(vox, O >= 1, O <= nz - 2);
+        const float* Wm = &S.W[ra][0][0][0];  // plane O - 1 = s - 3
+        const float* W0 = &S.W[rc][0][0][0];
+        const float* Wp = &S.W[rb][0][0][0];
         const int o = (tr + 1) * HC + (tc + 1);
         constexpr int FS = WR * HC;  // field stride in a plane
         auto F = [&](int q) { return Planes3{Wm + q * FS, W0 + q * FS, Wp + q * FS, o}; };
@@ -319,17 +359,23 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
         g += comp<8>(F(9), e);
         g += comp<11>(F(10), e);
         g += comp<10>(F(11), e);
-        a.gR[(long long)O * d + (long long)r * n + c] = g;
+        a.gR[(long long)O * d + vox_off] = g;
       }
+      const int rn = rc;  // plane s + 1 takes the slot of plane s - 2
+      rc = rb;
+      rb = ra;
+      ra = rn;
     }
   }
   if (!a.want_reg) return;
   __syncthreads();
-  // the block's per-slice sums: warps in a fixed order
+  // the block's per-slice sums
   for (int s = tid; s < a.pstride; s += NT) {
     float h = 0.f, l = 0.f;
-    if (s < MAXZ)
-      for (int w = 0; w < NWARP; ++w) acc_add(h, l, S.reg_hi[w][s], S.reg_lo[w][s]);
+    if (s < MAXZ) {
+      h = S.reg_hi[s];
+      l = S.reg_lo[s];
+    }
     a.partial[(long long)blockIdx.x * a.pstride + s] = make_float2(h, l);
   }
 }
