@@ -96,10 +96,6 @@ struct Shape {
 // Slices each warp of the sliced projections streams in turn (the loads of
 // the next slice are issued before the epilogue of the current one, which
 // hides that epilogue's latency); the grids shrink by the same factor.
-// Gather-ahead depth of the sliced stream (see SellGroup::stream).
-#ifndef APPGA_SELL_GA
-#define APPGA_SELL_GA 1
-#endif
 #ifndef APPGA_FW_SPW
 #define APPGA_FW_SPW 1
 #endif
@@ -444,17 +440,12 @@ struct SellGroup {
   }
 
   // Row sums of the slice times x (V = float), or times both halves of x
-  // (V = float2), in every lane of the row.  The gathers of step t + GA are
-  // issued while step t accumulates (GA = 1 or 2; GA = 2 needs PF >= 3 so
-  // that step t + 2's columns are already in registers).
+  // (V = float2), in every lane of the row.
   template <class V>
   __device__ __forceinline__ V stream(const DevSell& S, const V* __restrict__ x, uint64_t pol) {
-    constexpr int GA = APPGA_SELL_GA;
-    static_assert(GA == 1 || (GA == 2 && PF >= 3), "gather-ahead depth");
     V a0{}, a1{};
-    Quad<V> xg = zero_quad<V>(), xg2 = zero_quad<V>();
+    Quad<V> xg = zero_quad<V>();
     if (steps > 0) xg = gather_quad(x, sell_cols(c[0]));
-    if (GA == 2 && steps > 1) xg2 = gather_quad(x, sell_cols(c[1 % PF]));
     int t0 = 0;
 #if APPGA_SELL_PEEL
     // whole groups of PF steps whose refills and next gathers all exist: no
@@ -464,17 +455,10 @@ struct SellGroup {
       for (int u = 0; u < PF; ++u) {
         const int t = t0 + u;
         const float4 vv = v[u];
+        c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+        v[u] = vals(S, q0 + ((t + PF) << 5), pol);
         const Quad<V> xx = xg;
-        if constexpr (GA == 2) {
-          xg = xg2;
-          xg2 = gather_quad(x, sell_cols(c[(u + 2) % PF]));
-          c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
-          v[u] = vals(S, q0 + ((t + PF) << 5), pol);
-        } else {
-          c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
-          v[u] = vals(S, q0 + ((t + PF) << 5), pol);
-          xg = gather_quad(x, sell_cols(c[(u + 1) % PF]));
-        }
+        xg = gather_quad(x, sell_cols(c[(u + 1) % PF]));
         fma_quad(vv, xx, a0, a1);
       }
     }
@@ -485,22 +469,13 @@ struct SellGroup {
         const int t = t0 + u;
         if (t < steps) {
           const float4 vv = v[u];
-          const Quad<V> xx = xg;
-          if constexpr (GA == 2) {
-            xg = xg2;
-            if (t + 2 < steps) xg2 = gather_quad(x, sell_cols(c[(u + 2) % PF]));
-            if (t + PF < steps) {  // refill this slot with step t + PF
-              c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
-              v[u] = vals(S, q0 + ((t + PF) << 5), pol);
-            }
-          } else {
-            if (t + PF < steps) {  // refill this slot with step t + PF
-              c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
-              v[u] = vals(S, q0 + ((t + PF) << 5), pol);
-            }
-            // step t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
-            if (t + 1 < steps) xg = gather_quad(x, sell_cols(c[(u + 1) % PF]));
+          if (t + PF < steps) {  // refill this slot with step t + PF
+            c[u] = sell_cols_load(S, q0 + ((t + PF) << 5), pol);
+            v[u] = vals(S, q0 + ((t + PF) << 5), pol);
           }
+          const Quad<V> xx = xg;
+          // step t + 1 sits in slot (u + 1) % PF (refilled above when PF = 1)
+          if (t + 1 < steps) xg = gather_quad(x, sell_cols(c[(u + 1) % PF]));
           fma_quad(vv, xx, a0, a1);
         }
       }
@@ -818,7 +793,6 @@ __global__ void FW_BOUNDS k_forward(FwdArgs a) {
     // FW::W consecutive slices, whose row sums go to warp 0, so the
     // double-float epilogue (with the logarithm of the data term) runs once
     // per block trip; the next slice's loads are issued before it
-    static_assert(!SL || APPGA_FEPI, "the sliced forward phase uses the block epilogue");
     const float* f = a.ft ? a.ft : (a.loop ? a.f[kk % 3] : a.f[0]);
     const int G = nproj * FW::W;
     __shared__ float2 ysum[BROWS];
