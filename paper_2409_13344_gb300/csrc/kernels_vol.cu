@@ -205,14 +205,29 @@ __global__ void __launch_bounds__(NT) k_stencil3d(Vol3Args a) {
     // its plane elements (2-D offset in the image, -1 outside)
     const InPlane vox = in_plane(r, c, n);
     const int vox_off = r * n + c;
+    // field points row-aligned so a warp's 32 points are consecutive in a
+    // plane row (no shared-memory bank conflicts): first pass, field rows
+    // 0..7 at columns 0..31, one warp per row; second pass, rows 8 and 9 at
+    // columns 0..31 and the 20 points of columns 32 and 33
+    static_assert(TR == 8 && TC == 32 && NT == 256 && WR == 10 && WC == 34 && FPT == 2,
+                  "the field-point passes are laid out for 8 x 32 tiles");
     InPlane fp[FPT];
     int fp_o[FPT];  // offset of the point in the f planes; -1: no point
 #pragma unroll
     for (int u = 0; u < FPT; ++u) {
-      const int q = tid + u * NT;
-      const int i = q / WC, j = q % WC;
+      int i = -1, j = 0;
+      if (u == 0) {
+        i = tid >> 5;
+        j = tid & 31;
+      } else if (tid < 64) {
+        i = 8 + (tid >> 5);
+        j = tid & 31;
+      } else if (tid < 84) {
+        i = (tid - 64) >> 1;
+        j = 32 + ((tid - 64) & 1);
+      }
       fp[u] = in_plane(r0 - 1 + i, c0 - 1 + j, n);
-      fp_o[u] = q < NFP ? (i + 1) * HC + (j + 1) : -1;
+      fp_o[u] = i >= 0 ? (i + 1) * HC + (j + 1) : -1;
     }
     int ld_off[LPT];
 #pragma unroll
