@@ -60,10 +60,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=1000)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fold", choices=("auto", "on", "off"), default="auto",
+                    help="quarter-turn folded loop for the main single-slice leg: auto folds "
+                         "only when the folded streams still exceed L2 (the timed inputs stay "
+                         "larger than L2); the other layout is reported beside it")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="wall-time bound of the reference arm's timed oracle steps")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-slice batched leg")
+    ap.add_argument("--no-other-layout", action="store_true",
+                    help="skip the single-slice loop in the other matrix layout")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 120 x 512^2 batched leg")
     ap.add_argument("--no-volume", action="store_true",
@@ -188,9 +194,10 @@ def kernel_sources_sha256(root: str) -> str:
     return h.hexdigest()
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def committed_traffic(kernel: str, layout: str = "unfolded"):
+    """DRAM bytes per launch of `kernel` in the loop's `layout` ("unfolded" or
+    "folded") from the committed ncu summary, if it was taken on the current
+    kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as fh:
@@ -200,7 +207,7 @@ def committed_traffic(kernel: str):
         return None
     if rec.get("kernel_sources_sha256") != sha:
         return None
-    ent = rec.get("kernels", {}).get(kernel)
+    ent = rec.get("layouts", {}).get(layout, {}).get("kernels", {}).get(kernel)
     return None if ent is None else ent.get("dram_bytes_per_launch")
 
 
@@ -386,7 +393,57 @@ def bench_volume(AP, ctx, geom, A, dev, batched_rate, nz=64, counts=6.4e7, iters
     return out
 
 
-def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
+def bench_other_layout(AP, ctx, geom, A, g, gamma, params, fold, l2_bytes, fold_stream,
+                       plain_stream, iters=4000):
+    """The single-slice loop in the other matrix layout of the main leg
+    (quarter-turn folded or not), timed as the main leg: 500-iteration
+    reconstructions back to back, CUDA events on the launching stream, and
+    each loop kernel timed alone.  When its streams fit in L2 the iterations
+    reuse part of the matrix from L2, which the entry states."""
+    import torch
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, fold=fold)
+    try:
+        info = mat.info()
+        if fold and not info.quarter_turn_folded:
+            return {"unavailable": "the matrix has no exact quarter-turn symmetry"}
+        f = torch.empty(geom.d, dtype=torch.float32, device=g.device)
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            AP.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, params(ITERS_PER_RECON), f)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = 0
+        while done < iters:
+            it = min(ITERS_PER_RECON, iters - done)
+            AP.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, params(it), f)
+            done += it
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        AP.appga_kernel_times(ctx.handle, mat.handle, g, gamma, params(50), 50)
+        tp, tf = AP.appga_kernel_times(ctx.handle, mat.handle, g, gamma, params(300), 300)
+        stream_bytes = fold_stream if fold else plain_stream
+        return {
+            "layout": ("quarter-turn folded (half of A and A^T stored), " if fold else "")
+                      + "sliced, packed 2-byte columns + FP32 values",
+            "iters_per_s": iters / (ms * 1e-3), "us_per_iter": ms * 1e3 / iters,
+            "k_pixel_us": tp * 1e3, "k_forward_us": tf * 1e3,
+            "stream_bytes_per_iter": stream_bytes,
+            "l2": (f"the loop streams {stream_bytes / 1e6:.0f} MB per iteration, "
+                   + ("below" if stream_bytes < l2_bytes else "above")
+                   + f" L2 ({l2_bytes / 1e6:.0f} MB)"
+                   + ("; iterations reuse part of the matrix from L2 (measured at 256x256 "
+                      "without cache flushes: 38-40 MB of DRAM reads per launch of the "
+                      "47-48 MB stored), so this rate is not the main leg's"
+                      if stream_bytes < l2_bytes else "")),
+        }
+    finally:
+        mat.close()
+
+
+def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200, fold=True):
     """AFPPA with GN momentum for the non-smooth HOITV model (Sec. 4.4) on the
     main slice: time per step on the GPU (projectors + dual-update kernel)
     against one APPGA iteration, the FP64 oracle's step on the host, and the
@@ -394,7 +451,7 @@ def bench_afppa(AP, ctx, geom, A, sl, dev, appga_ms, cpu: bool, iters=200):
     central line profile) with their own call time."""
     import numpy as np
     import torch
-    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, fold=fold)
     g = torch.from_numpy(sl.g).to(dev)
     gam = torch.from_numpy(sl.gamma).to(dev)
     f = torch.empty(geom.d, dtype=torch.float32, device=dev)
@@ -667,7 +724,14 @@ def run_ours(args):
                                                    args.serve_geom_pools)}), flush=True)
         ctx.close()
         return 0
-    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles)
+    # the main leg's layout: its per-iteration streams must exceed L2, so the
+    # timed iterations do not reuse the matrix from L2
+    l2_bytes = int(torch.cuda.get_device_properties(dev).L2_cache_size)
+    nnz = int(A.nnz)
+    fold_stream = sum(kernel_bytes(geom.m, geom.d, nnz, 6, True, True))
+    plain_stream = sum(kernel_bytes(geom.m, geom.d, nnz, 6, True, False))
+    fold = args.fold == "on" or (args.fold == "auto" and fold_stream > l2_bytes)
+    mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, fold=fold)
     g = torch.from_numpy(sl.g).to(dev)
     gamma = torch.from_numpy(sl.gamma).to(dev)
     f_out = torch.empty(geom.d, dtype=torch.float32, device=dev)
@@ -690,12 +754,12 @@ def run_ours(args):
     def launches(total):
         # per run: the start-state/momentum kernel, the initial image (two
         # kernels, with the input check), the first forward phase, then per
-        # iteration the pixel kernel, its one-block finalisation and the
-        # forward kernel (exactly `it` maps), the last finalisation (objective
-        # of the result) and the result copy
+        # iteration the pixel kernel (which also finalises the previous step)
+        # and the forward kernel (exactly `it` maps), the last finalisation
+        # (objective of the result) and the result copy
         n = 0
         for it in chunks(total):
-            n += 6 + 3 * it
+            n += 6 + 2 * it
         return n
 
     def barrier():
@@ -769,7 +833,8 @@ def run_ours(args):
     achieved = dom[2] / (dom[1] * 1e-3) / 1e9
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-        "traffic": committed_traffic(dom[0]), "kernel": dom[0], "peak_source": peak_src,
+        "traffic": committed_traffic(dom[0], "folded" if folded else "unfolded"),
+        "kernel": dom[0], "peak_source": peak_src,
         # each launch timed alone (the step finalisation runs inside k_pixel)
         "timed_as": dom[0],
         "ms_per_launch": dom[1], "algorithmic_bytes_per_launch": dom[2],
@@ -795,6 +860,12 @@ def run_ours(args):
                       "frac": (c_fwd + c_pix) * args.steps / (ms * 1e-3) / 1e9 / hbm},
     }
 
+    # the loop in the other layout (folded when the main leg is not, and the
+    # reverse), timed the same way
+    other_layout = None
+    if world == 1 and not args.no_other_layout:
+        other_layout = bench_other_layout(AP, ctx, geom, A, g, gamma, params, not fold,
+                                          l2_bytes, fold_stream, plain_stream)
     batched = serving = None
     large = None
     if world == 1 and not args.no_batched:
@@ -813,7 +884,7 @@ def run_ours(args):
     afppa = None
     if world == 1 and not args.no_afppa:
         afppa = bench_afppa(AP, ctx, geom, A, sl, dev, ms_max / args.steps,
-                            cpu=rank == 0 and not args.no_cpu_baseline)
+                            cpu=rank == 0 and not args.no_cpu_baseline, fold=fold)
     volume = None
     if world == 1 and not args.no_volume:
         brate = None
@@ -842,8 +913,13 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "geometry": "256x256, 180 x 367",
-                       "nnz": int(info.nnz), "l2": "inputs larger than L2: A + A^T stream "
-                       f"{2 * 8 * int(info.nnz) / 1e6:.0f} MB per iteration (L2 129 MB)",
+                       "nnz": int(info.nnz),
+                       "l2": "inputs larger than L2: the loop streams "
+                             + ("the folded halves of A and A^T, " if folded
+                                else "A and A^T, ")
+                             + f"{(fold_stream if folded else plain_stream) / 1e6:.0f} MB per "
+                             f"iteration (L2 {l2_bytes / 1e6:.0f} MB)",
+                       "layout": roofline["stored_stream"]["layout"],
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -856,6 +932,7 @@ def run_ours(args):
             "large_batch": large,
             "volume": volume,
             "afppa": afppa,
+            "other_layout": other_layout,
             "serving": serving,
             "serving_saturated": serving_sat,
         }

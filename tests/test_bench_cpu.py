@@ -70,11 +70,16 @@ def test_algorithmic_bytes_match_the_committed_record():
     # format, and the bytes its layout streams
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
     cfw, cpx = b.kernel_bytes(m, d, nnz)
-    assert cfw == rec["kernels"]["k_forward"]["algorithmic_bytes_per_launch"]
-    assert cpx == rec["kernels"]["k_pixel"]["algorithmic_bytes_per_launch"]
-    sfw, spx = b.kernel_bytes(m, d, nnz, rec["bytes_per_nnz"], True, rec["folded"])
-    assert sfw == rec["kernels"]["k_forward"]["stored_bytes_per_launch"]
-    assert spx == rec["kernels"]["k_pixel"]["stored_bytes_per_launch"]
+    for layout, ent in rec["layouts"].items():
+        ks = ent["kernels"]
+        assert cfw == ks["k_forward"]["algorithmic_bytes_per_launch"]
+        assert cpx == ks["k_pixel"]["algorithmic_bytes_per_launch"]
+        sfw, spx = b.kernel_bytes(m, d, nnz, rec["bytes_per_nnz"], True, layout == "folded")
+        assert sfw == ks["k_forward"]["stored_bytes_per_launch"]
+        assert spx == ks["k_pixel"]["stored_bytes_per_launch"]
+        # the captured traffic is near the bytes the layout streams
+        for k in ("k_forward", "k_pixel"):
+            assert 1.0 <= ks[k]["dram_bytes_per_launch"] / ks[k]["stored_bytes_per_launch"] < 1.2
     # both streams dominate: 12 B per nonzero is 97-98 % of an iteration's bytes
     assert 0.97 < 12 * nnz / (fwd + pix) < 0.99
     # a batched iteration of 64 slices reads the matrix once: far below 64 iterations
@@ -96,10 +101,11 @@ def test_traffic_is_reported_only_for_the_captured_kernel_source(tmp_path, monke
         (src / name).write_bytes(code)
     sha = hashlib.sha256(b"".join(files[n] for n in b.KERNEL_SOURCES)).hexdigest()
     rec = {"kernel_sources_sha256": sha,
-           "kernels": {"k_pixel": {"dram_bytes_per_launch": 123}}}
+           "layouts": {"unfolded": {"kernels": {"k_pixel": {"dram_bytes_per_launch": 123}}}}}
     (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.committed_traffic("k_pixel") == 123
+    assert b.committed_traffic("k_pixel", "folded") is None
     assert b.committed_traffic("k_forward") is None
     for name in b.KERNEL_SOURCES:  # a change to any of them drops the figure
         (src / name).write_bytes(files[name] + b"// changed\n")
