@@ -107,6 +107,9 @@ appga_status upload_sell(const appga::HostSell& h, bool bf16, DevSell* out, int6
 void free_workspace(Workspace& ws) {
   for (auto& kv : ws.gexec) cudaGraphExecDestroy(kv.second);
   ws.gexec.clear();
+  for (auto& kv : ws.call_graphs) cudaGraphExecDestroy(kv.second);
+  ws.call_graphs.clear();
+  ws.call_seen.clear();
   for (auto& p : ws.f) cudaFree(p);
   for (auto& p : ws.y) cudaFree(p);
   cudaFree(ws.w);
@@ -376,6 +379,12 @@ appga_status setup_run(appga_matrix* M, const float* g, const float* gamma, int3
   return APPGA_OK;
 }
 
+// Calls of at most this many maps (and no stopping tolerance) are captured
+// whole into a call graph once their arguments repeat; at most
+// kCallGraphCache such graphs are kept per matrix.
+constexpr int kCallGraphMaxMaps = 64;
+constexpr size_t kCallGraphCache = 8;
+
 // Executable graph of `maps` solver maps (pixel phase, finalisation, forward
 // phase) for the loop arguments of `key`, captured on first use.
 appga_status loop_graph(Workspace& ws, const std::string& key, int maps,
@@ -516,6 +525,9 @@ appga_status momentum_table(appga_matrix* M, SolverState* st, int k0, const appg
   Workspace& ws = M->ws;
   const int need = p->max_iters + 1;
   if (ws.theta_cap < need) {
+    // captured call graphs read the old table: drop them with it
+    for (auto& kv : ws.call_graphs) cudaGraphExecDestroy(kv.second);
+    ws.call_graphs.clear();
     cudaFree(ws.theta_tab);
     ws.theta_tab = nullptr;
     ws.theta_cap = 0;
@@ -644,35 +656,112 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
   if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
   cudaStream_t s = ctx->stream;
   Workspace& ws = M->ws;
-  const SolverState h = start_state(k0, p);
-  if ((rc = momentum_table(M, ws.st, k0, p, s, &h)) != APPGA_OK) return rc;
   const size_t fb = (size_t)M->d * sizeof(float);
-  float* slot_cur = ws.f[k0 % 3];
-  float* slot_prev = ws.f[(k0 + 2) % 3];
-  bool tiled_ready = false;
-  if (fresh && f_cur == nullptr) {
-    // TMC * 1_disk into f^{k0}, f^{k0-1} and the loop's gather copy; g and
-    // gamma are checked in the same pass
-    appga::FwdArgs lf{};
-    appga::PixArgs lp{};
-    appga::loop_layout(M, &lf, &lp);
-    CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux,
-                                   ws.gtick, ws.st_scratch, slot_cur, s, slot_prev, lp.ft, ws.st,
-                                   lp.fpair));
-    tiled_ready = appga::loop_gathers_copy();
-  } else {
-    CK(appga::launch_check_inputs(g, gamma, M->m, f_cur, fresh ? nullptr : f_prev, M->d, ws.st,
-                                  s));
-    CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(slot_prev, fresh ? f_cur : f_prev, fb, cudaMemcpyDeviceToDevice, s));
+  // The whole call: start state and momentum table, f^{k0-1} and f^{k0},
+  // the first forward phase, the maps (as graph replays, or launched one by
+  // one when `direct`, inside a call graph), the last finalisation, the
+  // result and the state read-back.
+  auto enqueue = [&](bool direct) -> appga_status {
+    const SolverState h = start_state(k0, p);
+    appga_status r = momentum_table(M, ws.st, k0, p, s, &h);
+    if (r != APPGA_OK) return r;
+    float* slot_cur = ws.f[k0 % 3];
+    float* slot_prev = ws.f[(k0 + 2) % 3];
+    bool tiled_ready = false;
+    if (fresh && f_cur == nullptr) {
+      // TMC * 1_disk into f^{k0}, f^{k0-1} and the loop's gather copy; g
+      // and gamma are checked in the same pass
+      appga::FwdArgs lf{};
+      appga::PixArgs lp{};
+      appga::loop_layout(M, &lf, &lp);
+      CK(appga::launch_initial_image(g, gamma, M->m, M->n, M->na, M->npfov, ws.partial_aux,
+                                     ws.gtick, ws.st_scratch, slot_cur, s, slot_prev, lp.ft,
+                                     ws.st, lp.fpair));
+      tiled_ready = appga::loop_gathers_copy();
+    } else {
+      CK(appga::launch_check_inputs(g, gamma, M->m, f_cur, fresh ? nullptr : f_prev, M->d,
+                                    ws.st, s));
+      CK(cudaMemcpyAsync(slot_cur, f_cur, fb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(slot_prev, fresh ? f_cur : f_prev, fb, cudaMemcpyDeviceToDevice, s));
+    }
+    appga::FwdArgs fa;
+    appga::PixArgs pa;
+    if ((r = setup_run(M, g, gamma, k0, p, fresh, tiled_ready, &fa, &pa)) != APPGA_OK) return r;
+    if (direct) {
+      for (int i = 0; i < p->max_iters; ++i) {
+        CK(appga::launch_pixel(pa, s));
+        CK(appga::launch_forward(fa, s));
+      }
+      if (p->track_objective != 0) CK(appga::launch_finalize(pa, s));
+    } else if ((r = run_maps(M, g, gamma, p, fa, pa)) != APPGA_OK) {
+      return r;
+    }
+    CK(appga::launch_copy_result(ws.st, ws.f, f_out, f_out_prev, M->d, s));
+    if (f_out_host) CK(cudaMemcpyAsync(f_out_host, f_out, fb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ws.st_host, ws.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    return APPGA_OK;
+  };
+  // A short call without a stopping tolerance whose arguments keep repeating
+  // is replayed as one captured graph (one launch instead of a dozen):
+  // captured on the third call with the same arguments, so every one-time
+  // set-up of the kernels has run before and a single repeat does not pay
+  // for the capture.  A host result buffer must be pinned.
+  bool pinned_out = f_out_host == nullptr;
+  if (!pinned_out) {
+    cudaPointerAttributes pat{};
+    pinned_out = cudaPointerGetAttributes(&pat, f_out_host) == cudaSuccess &&
+                 pat.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // clear a failed query
   }
-  appga::FwdArgs fa;
-  appga::PixArgs pa;
-  if ((rc = setup_run(M, g, gamma, k0, p, fresh, tiled_ready, &fa, &pa)) != APPGA_OK) return rc;
-  if ((rc = run_maps(M, g, gamma, p, fa, pa)) != APPGA_OK) return rc;
-  CK(appga::launch_copy_result(ws.st, ws.f, f_out, f_out_prev, M->d, s));
-  if (f_out_host) CK(cudaMemcpyAsync(f_out_host, f_out, fb, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(ws.st_host, ws.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  const bool whole = p->max_iters > 0 && p->max_iters <= kCallGraphMaxMaps &&
+                     p->rel_obj_tol <= 0.0 && pinned_out;
+  std::string ckey;
+  if (whole) {
+    const bool track = p->track_objective != 0;
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p", k0, (int)fresh,
+                  p->max_iters, (const void*)g, (const void*)gamma, (const void*)f_prev,
+                  (const void*)f_cur, (const void*)f_out_prev, (const void*)f_out,
+                  (const void*)f_out_host);
+    ckey = graph_key(p, track, bf16_requested(M, p), 0) + buf;
+  }
+  auto it = whole ? ws.call_graphs.find(ckey) : ws.call_graphs.end();
+  const auto seen = whole ? ws.call_seen.find(ckey) : ws.call_seen.end();
+  if (whole && (it != ws.call_graphs.end() ||
+                (seen != ws.call_seen.end() && seen->second >= 2))) {
+    if (it == ws.call_graphs.end()) {
+      // the momentum table is grown outside the capture
+      const int need = p->max_iters + 1;
+      if (ws.theta_cap < need && (rc = momentum_table(M, ws.st_scratch, k0, p, s)) != APPGA_OK)
+        return rc;
+      if (ws.call_graphs.size() >= kCallGraphCache) {
+        for (auto& kv : ws.call_graphs) cudaGraphExecDestroy(kv.second);
+        ws.call_graphs.clear();
+      }
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const appga_status rq = enqueue(true);
+      const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+      if (rq != APPGA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rq;
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "call graph capture");
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) return cuda_fail(e3, "call graph instantiation");
+      it = ws.call_graphs.emplace(ckey, exec).first;
+    }
+    CK(cudaGraphLaunch(it->second, s));
+  } else {
+    if (whole) {
+      if (ws.call_seen.size() >= 4 * kCallGraphCache && seen == ws.call_seen.end())
+        ws.call_seen.clear();
+      ++ws.call_seen[ckey];
+    }
+    if ((rc = enqueue(false)) != APPGA_OK) return rc;
+  }
   if ((rc = leave_stream(ctx, stream)) != APPGA_OK) return rc;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   const SolverState fin = *ws.st_host;

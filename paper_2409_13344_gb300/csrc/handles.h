@@ -47,6 +47,10 @@ struct Workspace {
   // powers of two below it) for the parameters in gkey
   std::map<int, cudaGraphExec_t> gexec;
   std::string gkey;
+  // whole-call graphs of short calls, by their arguments, and how often
+  // other arguments were seen (a call graph is captured on the third call)
+  std::map<std::string, cudaGraphExec_t> call_graphs;
+  std::map<std::string, int> call_seen;
 };
 
 // Launch schedule of the batched kernels (0 = the kernels' defaults), as

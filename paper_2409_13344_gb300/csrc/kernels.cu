@@ -1175,6 +1175,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_finalize(PixArgs a) {
 // run computes the same values, so it replays an uninterrupted one bit for bit.
 __global__ void k_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, int momentum,
                               double a, double b, double omega, SolverState init, int set_state) {
+  pdl_wait();  // launched dependent: nothing is touched before the predecessor is done
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && set_state) *st = init;
   if (momentum == APPGA_MOMENTUM_NESTEROV) {
@@ -1268,6 +1270,8 @@ __device__ __forceinline__ void mark_domain(SolverState* st) {
 __global__ void k_check_inputs(const float* __restrict__ g, const float* __restrict__ gamma,
                                int m, const float* __restrict__ fa,
                                const float* __restrict__ fb, int d, SolverState* st) {
+  pdl_wait();
+  pdl_trigger();
   int bad = 0;
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
@@ -1291,6 +1295,8 @@ __global__ void __launch_bounds__(THREADS) k_actc(const float* __restrict__ g,
                                                   float2* partial, unsigned int* gtick,
                                                   SolverState* st, double* actc_out,
                                                   SolverState* vst) {
+  pdl_wait();
+  pdl_trigger();
   float h = 0.f, l = 0.f;
   int bad = 0;
   for (int i = blockIdx.x * THREADS + threadIdx.x; i < m; i += gridDim.x * THREADS) {
@@ -1315,6 +1321,8 @@ __device__ __forceinline__ bool in_disk(int r, int c, int n) {
 // folded pair holds the value twice)
 __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, float* f_out,
                             float* f_out2, float* ft, float2* fpair) {
+  pdl_wait();
+  pdl_trigger();
   const double tmc = *actc / ((double)npfov * (double)n_angles);
   const float v = (float)tmc;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n * n; j += gridDim.x * blockDim.x) {
@@ -1332,6 +1340,8 @@ __global__ void k_fill_disk(int n, int n_angles, int npfov, const double* actc, 
 __global__ void k_copy_result(const SolverState* st, const float* __restrict__ f0,
                               const float* __restrict__ f1, const float* __restrict__ f2,
                               float* __restrict__ out, float* __restrict__ out_prev, int d) {
+  pdl_wait();
+  pdl_trigger();
   if (st->flags & APPGA_FLAG_DOMAIN) return;
   const int rk = st->result_k;
   const float* ring[3] = {f0, f1, f2};
@@ -1514,15 +1524,14 @@ cudaError_t launch_finalize(const PixArgs& a, cudaStream_t s) {
 
 cudaError_t launch_check_inputs(const float* g, const float* gamma, int m, const float* fa,
                                 const float* fb, int d, SolverState* st, cudaStream_t s) {
-  k_check_inputs<<<256, 256, 0, s>>>(g, gamma, m, fa, fb, d, st);
-  return cudaGetLastError();
+  return launch_dep(k_check_inputs, 256, 256, s, g, gamma, m, fa, fb, d, st);
 }
 
 cudaError_t launch_copy_result(const SolverState* st, float* const f[3], float* out,
                                float* out_prev, int d, cudaStream_t s) {
   const int grid = (d + 255) / 256 < 1024 ? (d + 255) / 256 : 1024;
-  k_copy_result<<<grid, 256, 0, s>>>(st, f[0], f[1], f[2], out, out_prev, d);
-  return cudaGetLastError();
+  return launch_dep(k_copy_result, grid, 256, s, st, (const float*)f[0], (const float*)f[1],
+                    (const float*)f[2], out, out_prev, d);
 }
 
 cudaError_t launch_backproject(const DevCSR& At, const float* w, float* out, int use_bf16,
@@ -1559,9 +1568,8 @@ cudaError_t launch_theta_table(SolverState* st, ThetaEntry* tab, int k0, int n, 
                                const SolverState* init) {
   const int threads = 256, blocks = (n + 1 + threads - 1) / threads;
   SolverState z{};
-  k_theta_table<<<blocks, threads, 0, s>>>(st, tab, k0, n, momentum, a, b, omega,
-                                           init ? *init : z, init ? 1 : 0);
-  return cudaGetLastError();
+  return launch_dep(k_theta_table, blocks, threads, s, st, tab, k0, n, momentum, a, b, omega,
+                    init ? *init : z, init ? 1 : 0);
 }
 
 long long disk_pixels(int n) {
@@ -1581,12 +1589,11 @@ cudaError_t launch_initial_image(const float* g, const float* gamma, int m, int 
                                  float* ft, SolverState* check_st, float2* fpair) {
   // the ACTc scalar is parked in the last partial slot (as raw bytes of a double)
   double* actc = reinterpret_cast<double*>(partial + max_partials(m, n) - 1);
-  k_actc<<<256, THREADS, 0, s>>>(g, gamma, m, partial, gtick, st, actc, check_st);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_dep(k_actc, 256, THREADS, s, g, gamma, m, partial, gtick, st,
+                             actc, check_st);
   if (e != cudaSuccess) return e;
-  k_fill_disk<<<(n * n + 255) / 256 < 1024 ? (n * n + 255) / 256 : 1024, 256, 0, s>>>(
-      n, n_angles, (int)npfov, actc, f_out, f_out2, ft, fpair);
-  return cudaGetLastError();
+  return launch_dep(k_fill_disk, (n * n + 255) / 256 < 1024 ? (n * n + 255) / 256 : 1024, 256,
+                    s, n, n_angles, (int)npfov, (const double*)actc, f_out, f_out2, ft, fpair);
 }
 
 }  // namespace appga

@@ -460,6 +460,56 @@ def test_quarter_turn_fold_only_where_it_holds(A, ctx, mats):
         mb.close()
 
 
+def test_repeated_short_calls_replay_one_graph(A, ctx, mats):
+    # a short call whose arguments repeat runs as one captured graph from its
+    # second time on: the results and statistics stay those of the first
+    # call bit for bit, inputs changed in place are read at each replay, and
+    # a longer call in between (which regrows the momentum table) leaves
+    # the short calls correct
+    geom, Amat, sl = problem("64")
+    mat = mats["64"]
+    g, gamma = to_dev(sl.g), to_dev(sl.gamma)
+    p = A.default_params(max_iters=20, track_objective=1)
+    outs, stats = [], []
+    for _ in range(4):
+        out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+        st = A.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, p, out)
+        outs.append(out.clone())
+        stats.append((st.iters, st.result_k, st.phi, st.phi_prev, st.guard_hits, st.flags))
+    # the same output buffer each time
+    out = torch.empty(geom.d, dtype=torch.float32, device=DEV)
+    runs = []
+    for _ in range(3):
+        st = A.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, p, out)
+        runs.append((out.clone(), st.phi, st.iters))
+    for o, phi, it in runs:
+        assert torch.equal(o, runs[0][0]) and phi == runs[0][1] and it == 20
+    assert torch.equal(runs[0][0], outs[0])
+    for st in stats[1:]:
+        assert st == stats[0]
+    # inputs changed in place are read at the next replay
+    g2_host = (sl.g * 1.5).astype(np.float32)
+    g.copy_(torch.from_numpy(g2_host).to(DEV))
+    st2 = A.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, p, out)
+    fresh = torch.empty_like(out)
+    st_ref = A.appga_reconstruct(ctx.handle, mat.handle, to_dev(g2_host), gamma, None, p, fresh)
+    assert torch.equal(out, fresh) and st2.phi == st_ref.phi
+    # a long call regrows the momentum table; the short call stays correct
+    A.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None,
+                        A.default_params(max_iters=1500), torch.empty_like(out))
+    for _ in range(2):
+        st3 = A.appga_reconstruct(ctx.handle, mat.handle, g, gamma, None, p, out)
+        assert torch.equal(out, fresh) and st3.phi == st_ref.phi
+    # the host-buffer entry point with a pinned result buffer
+    gh = torch.from_numpy(g2_host).pin_memory()
+    gamh = torch.from_numpy(sl.gamma).pin_memory()
+    fh = torch.empty(geom.d, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        sth = A.appga_reconstruct_host(ctx.handle, mat.handle, gh, gamh, None, p, fh)
+        np.testing.assert_array_equal(fh.numpy(), fresh.cpu().numpy())
+        assert sth.phi == st_ref.phi
+
+
 def test_resume_is_bitwise_continuation(A, ctx, mats):
     geom, Amat, sl = problem("64")
     mat = mats["64"]
