@@ -691,12 +691,24 @@ def test_largest_geometry_single_slice_sampled(A, ctx):
     geom, Amat, sl = problem("512", counts=1e6, phantom="lesions")
     mat = A.Matrix(ctx, Amat, geom.n, geom.n_angles)
     try:
+        # the Siddon matrix has the quarter-turn symmetry: the loop is folded
+        assert mat.info().quarter_turn_folded == 1
         f, st = run_gpu(A, ctx, mat, sl, max_iters=4, omega=1.0, track_objective=1)
         prob, ref = run_oracle(geom, Amat, sl, max_iters=4, omega=1.0)
         assert st.iters == 4
         assert rel_l2(f, ref.f) <= 1e-5
         phi_same = prob.objective(f.astype(np.float64), 0.1, 0.05, 1e-3)
         assert abs(st.phi - phi_same) <= 1e-9 * abs(phi_same)
+        # 30 maps folded and over the whole matrices agree to FP32 rounding
+        mu = A.Matrix(ctx, Amat, geom.n, geom.n_angles, fold=False)
+        try:
+            assert mu.info().quarter_turn_folded == 0
+            ff, sf = run_gpu(A, ctx, mat, sl, max_iters=30, omega=1.0, track_objective=1)
+            fu, su = run_gpu(A, ctx, mu, sl, max_iters=30, omega=1.0, track_objective=1)
+            assert rel_l2(ff, fu) <= 2e-6
+            assert abs(sf.phi - su.phi) <= 1e-9 * abs(su.phi)
+        finally:
+            mu.close()
     finally:
         mat.close()
 
