@@ -596,7 +596,11 @@ class Context:
 
 
 class Matrix:
-    """Device copy of a system matrix (scipy CSR, FP32 values)."""
+    """Device copy of a system matrix (scipy CSR, FP32 values).
+
+    bf16 also keeps a BF16 copy of the values; fold=False keeps the solver
+    loop on the whole matrices even when A has the quarter-turn symmetry of a
+    parallel-beam scanner (see appga_matrix_create)."""
 
     def __init__(self, ctx: Context, A, n_side: int, n_angles: int, bf16: bool = False,
                  fold: bool = True):
