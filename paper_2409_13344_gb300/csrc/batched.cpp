@@ -209,6 +209,13 @@ constexpr int kBatchGraphIters = 8;
 #ifndef APPGA_VOL_SPMV_PER_SM
 #define APPGA_VOL_SPMV_PER_SM 5
 #endif
+// pixel-phase blocks per SM in volume mode (0: the batched default): 5, the
+// 2-D autotuner's choice for 64 slices of 256^2, measured fastest here too
+// (650.7 us per 64 x 256^2 volume iteration; 4: 682.6, 6: 736.4, default:
+// 679.3)
+#ifndef APPGA_VOL_PIXEL_PER_SM
+#define APPGA_VOL_PIXEL_PER_SM 5
+#endif
 
 int padded_width(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
 
@@ -315,6 +322,7 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
     fa.no_stencil = 1;
     // leave room on each SM for a stencil block beside the forward phase's
     if (sch.spmv_per_sm == 0) fa.spmv_per_sm = APPGA_VOL_SPMV_PER_SM;
+    if (sch.pixel_per_sm == 0 && APPGA_VOL_PIXEL_PER_SM > 0) pa.blocks_per_sm = APPGA_VOL_PIXEL_PER_SM;
     pa.joint = 1;
     const int nfw = bforward_grid(fa);
     Vol3Args& va = vb.va;
