@@ -44,6 +44,14 @@ constexpr int kMaxPerSm = 16;                // upper bound of either tuned valu
 __host__ __forceinline__ int clamp_per_sm(int v, int dflt) {
   return v <= 0 ? dflt : (v > kMaxPerSm ? kMaxPerSm : v);
 }
+// Blocks per SM when no tuned schedule is given: at 64 slots the
+// autotuner's choice on 64 slices of 256^2 (forward 4, pixel 5, stencil 8),
+// other widths the caps above.
+__host__ __forceinline__ int default_spmv_per_sm(int Kp) { return Kp == 64 ? 4 : kSpmvPerSm; }
+__host__ __forceinline__ int default_pixel_per_sm(int Kp) { return Kp == 64 ? 5 : kSpmvPerSm; }
+__host__ __forceinline__ int default_stencil_per_sm(int Kp) {
+  return Kp == 64 ? 8 : kStencilPerSm;
+}
 constexpr int BST_R = 2, BST_C = 32, BST_S = 8;  // stencil item: 2 x 32 pixels x 8 slots
 constexpr int BTW = BST_C + 4, BVW = BST_C + 2;
 static_assert(BST_C * BST_S == B_THREADS, "stencil: one thread per (column, slot)");
@@ -893,13 +901,13 @@ int sm_count() { return current_sm_count(); }
 int bforward_grid_n(const BFwdArgs& a, int* n_spmv) {
   const int sms = sm_count();
   int nsp = (a.A.rows + B_WARPS - 1) / B_WARPS;
-  const int cap = sms * clamp_per_sm(a.spmv_per_sm, kSpmvPerSm);
+  const int cap = sms * clamp_per_sm(a.spmv_per_sm, default_spmv_per_sm(a.Kp));
   if (nsp > cap) nsp = cap;
   int nst = 0;
   if (a.mode != 1 && !a.no_stencil) {
     // equal tile counts per stencil block
     const int tiles = ((a.n + BST_C - 1) / BST_C) * ((a.n + BST_R - 1) / BST_R);
-    const int scap = sms * clamp_per_sm(a.stencil_per_sm, kStencilPerSm);
+    const int scap = sms * clamp_per_sm(a.stencil_per_sm, default_stencil_per_sm(a.Kp));
     const int per = (tiles + scap - 1) / scap;
     nst = (tiles + per - 1) / per;
   }
@@ -958,7 +966,7 @@ template <int V>
 cudaError_t bpixel_v(const BPixArgs& a, cudaStream_t s) {
   const int sms = sm_count();
   int nb = (a.At.rows + B_WARPS - 1) / B_WARPS;
-  const int cap = sms * clamp_per_sm(a.blocks_per_sm, kSpmvPerSm);
+  const int cap = sms * clamp_per_sm(a.blocks_per_sm, default_pixel_per_sm(a.Kp));
   if (nb > cap) nb = cap;
   const bool g4 = a.gather_rows == 4;
   void (*kern)(BPixArgs) = a.use_bf16 ? (g4 ? k_bpixel<V, true, 4> : k_bpixel<V, true, 8>)
