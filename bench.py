@@ -194,6 +194,18 @@ def kernel_sources_sha256(root: str) -> str:
     return h.hexdigest()
 
 
+def main_leg_folds(choice: str, fold_stream_bytes: int, l2_bytes: int) -> bool:
+    """Whether the main single-slice leg runs the quarter-turn folded loop:
+    `choice` "on" / "off" decides; "auto" folds only when the folded streams
+    of an iteration still exceed L2, so the timed iterations never reuse the
+    matrix from L2."""
+    if choice == "on":
+        return True
+    if choice == "off":
+        return False
+    return fold_stream_bytes > l2_bytes
+
+
 def committed_traffic(kernel: str, layout: str = "unfolded"):
     """DRAM bytes per launch of `kernel` in the loop's `layout` ("unfolded" or
     "folded") from the committed ncu summary, if it was taken on the current
@@ -730,7 +742,7 @@ def run_ours(args):
     nnz = int(A.nnz)
     fold_stream = sum(kernel_bytes(geom.m, geom.d, nnz, 6, True, True))
     plain_stream = sum(kernel_bytes(geom.m, geom.d, nnz, 6, True, False))
-    fold = args.fold == "on" or (args.fold == "auto" and fold_stream > l2_bytes)
+    fold = main_leg_folds(args.fold, fold_stream, l2_bytes)
     mat = AP.Matrix(ctx, A, geom.n, geom.n_angles, fold=fold)
     g = torch.from_numpy(sl.g).to(dev)
     gamma = torch.from_numpy(sl.gamma).to(dev)

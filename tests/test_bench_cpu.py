@@ -112,3 +112,20 @@ def test_traffic_is_reported_only_for_the_captured_kernel_source(tmp_path, monke
         assert b.committed_traffic("k_pixel") is None
         (src / name).write_bytes(files[name])
     assert b.committed_traffic("k_pixel") == 123
+
+
+def test_main_leg_layout_keeps_timed_streams_above_l2():
+    """The main single-slice leg folds only when the folded streams still
+    exceed L2: at 256x256 (95 MB folded, L2 136 MB) it streams the whole
+    matrices (185 MB), at 512x512 the folded halves (about 740 MB)."""
+    b = _bench_module()
+    l2 = 136314880
+    for (m, d, nnz), folds in (((66060, 65536, 15017956), False),
+                               ((263160, 262144, 120155712), True)):
+        fold_stream = sum(b.kernel_bytes(m, d, nnz, 6, True, True))
+        plain_stream = sum(b.kernel_bytes(m, d, nnz, 6, True, False))
+        assert plain_stream > l2
+        assert b.main_leg_folds("auto", fold_stream, l2) == folds
+        streamed = fold_stream if folds else plain_stream
+        assert streamed > l2
+    assert b.main_leg_folds("on", 1, l2) and not b.main_leg_folds("off", 10 ** 12, l2)
