@@ -582,27 +582,36 @@ appga_status leave_stream(appga_ctx* ctx, void* stream) {
   return APPGA_OK;
 }
 
-appga_status data_term_on(appga_matrix* M, const float* f, const float* g, const float* gamma,
-                          bool bf16, double* dev_out, cudaStream_t s) {
+appga_status objective_terms(appga_matrix* M, int K, const float* f, const float* g,
+                             const float* gamma, const appga_params* p, bool with_reg,
+                             double* dev_out, cudaStream_t s) {
   appga_status rc = ensure_workspace(M);
   if (rc != APPGA_OK) return rc;
   Workspace& ws = M->ws;
-  appga::FwdArgs a = fwd_args(M, bf16);
-  a.f[0] = f;
-  a.y[0] = nullptr;
-  a.y_out = nullptr;
-  a.g = g;
-  a.gamma = gamma;
-  a.st = ws.st_scratch;
-  a.partial = ws.partial_aux;
-  a.gtick = ws.gtick;
-  a.data_out = dev_out;
-  a.loop = 0;
-  a.want_data = 1;
-  a.n = M->n;
-  CK(appga::launch_forward(a, s));
+  const bool bf16 = bf16_requested(M, p);
+  for (int i = 0; i < K; ++i) {
+    const float* fi = f + (size_t)i * M->d;
+    FwdArgs a = fwd_args(M, bf16);
+    a.f[0] = fi;
+    a.y[0] = nullptr;
+    a.y_out = nullptr;
+    a.g = g + (size_t)i * M->m;
+    a.gamma = gamma + (size_t)i * M->m;
+    a.st = ws.st_scratch;
+    a.partial = ws.partial_aux;
+    a.gtick = ws.gtick;
+    a.data_out = dev_out + 2 * i;
+    a.loop = 0;
+    a.want_data = 1;
+    a.n = M->n;
+    CK(launch_forward(a, s));
+    if (with_reg)
+      CK(launch_reg_term(M->n, fi, (float)p->lambda1, (float)p->lambda2, (float)p->eps,
+                         ws.partial_aux, ws.gtick, ws.st_scratch, dev_out + 2 * i + 1, s));
+  }
   return APPGA_OK;
 }
+
 }  // namespace appga
 
 namespace {

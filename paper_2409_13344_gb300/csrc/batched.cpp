@@ -77,8 +77,8 @@ cudaError_t alloc_batch_workspace(BatchWorkspace& b, int m, int d, int Kp) {
   if (e == cudaSuccess) e = dalloc(&b.fpartial, (size_t)maxb * Kp);
   if (e == cudaSuccess) e = dalloc(&b.gtick, (size_t)ngroups);
   if (e == cudaSuccess) e = dalloc(&b.flag, 1);
-  if (e == cudaSuccess) e = dalloc(&b.vscal, (size_t)Kp + 2);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&b.vscal_host, (Kp + 2) * sizeof(double));
+  if (e == cudaSuccess) e = dalloc(&b.vscal, (size_t)2 * Kp + 2);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b.vscal_host, (2 * Kp + 2) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(b.gtick, 0, (size_t)ngroups * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(b.bst, 0, sizeof(BatchState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b.slots_host, Kp * sizeof(SlotState));
@@ -253,7 +253,6 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
                            float* f_out, appga_stats* stats_host, const BatchSchedule& sch,
                            void* stream, int min_width = 0, bool volume = false) {
   appga_status rc = APPGA_OK;
-  const appga_matrix* mat = M;
   const int Kp = std::max(padded_width(K), min_width);
   if ((rc = ensure_batch_workspace(M, Kp)) != APPGA_OK) return rc;
   if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
@@ -412,6 +411,17 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
   CK(cudaStreamSynchronize(s));
   const int Gf = b.bst_host->gstep;
   CK(launch_from_slot_minor(b.f[Gf % 3], K, d, Kp, 0, nullptr, f_out, s));
+  if (track) {
+    // the objective terms of every result image, in the arithmetic of
+    // appga_objective, with one host round trip for all of them (2-D: data
+    // term and regulariser per slice; volume: the data terms, the 3-D
+    // regulariser follows with the statistics)
+    if ((rc = objective_terms(M, K, f_out, g, gamma, params, !volume, b.vscal, s)) != APPGA_OK)
+      return rc;
+    CK(cudaMemcpyAsync(b.vscal_host, b.vscal, (size_t)2 * K * sizeof(double),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
   rc = APPGA_OK;
   if (b.bst_host->flags & APPGA_FLAG_NONFINITE) rc = fail(APPGA_ENUMERIC, "a non-finite value appeared");
   if (stats_host) {
@@ -427,17 +437,8 @@ appga_status batched_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const flo
       st.phi_prev = std::numeric_limits<double>::quiet_NaN();
       if (track) st.phi_prev = sl.stopped_early ? sl.phi_prev : sl.phi_cur;
     }
-    if (track) {
-      // Phi of every result image in FP64 (single-slice objective)
-      CK(cudaStreamSynchronize(s));
-      for (int i = 0; i < K; ++i) {
-        double phi = 0.0;
-        appga_status r2 = appga_objective(ctx, mat, f_out + (size_t)i * d, g + (size_t)i * m,
-                                          gamma + (size_t)i * m, params, &phi, (void*)s);
-        if (r2 != APPGA_OK) return r2;
-        stats_host[i].phi = phi;
-      }
-    }
+    if (track && !volume)
+      for (int i = 0; i < K; ++i) stats_host[i].phi = b.vscal_host[2 * i] + b.vscal_host[2 * i + 1];
   }
   appga_status r3 = leave_stream(ctx, stream);
   if (r3 != APPGA_OK) return r3;

@@ -148,10 +148,6 @@ appga_status volume_solve(appga_ctx* ctx, appga_matrix* M, int32_t K, const floa
 // row in 32 bits: APPGA_OK when max(m, d) * Kp stays below 2^31, else
 // APPGA_EINVAL (with the library's error message set).
 appga_status check_slot_width(const appga_matrix* M, int Kp);
-// Data term sum_i (A f)_i - g_i ln((A f)_i + gamma_i) of one slice in FP64
-// (double-float accumulation) into the device double *dev_out.
-appga_status data_term_on(appga_matrix* M, const float* f, const float* g, const float* gamma,
-                          bool bf16, double* dev_out, cudaStream_t s);
 
 }  // namespace appga
 
@@ -226,6 +222,14 @@ void loop_layout(const appga_matrix* M, FwdArgs* fa, PixArgs* pa);
 bool loop_gathers_copy();
 // Fills the loop's gather copy of f^k (tiled or folded pairs), if it has one.
 cudaError_t loop_gather_copy(const appga_matrix* M, const float* f, cudaStream_t s);
+
+// The objective terms of K slices (f [K][d], g and gamma [K][m]) enqueued on
+// s without a host round trip, in the arithmetic of appga_objective: slice
+// i's data term into dev_out[2i] (double-float projection) and, with_reg, its
+// SHOITV regulariser into dev_out[2i + 1].
+appga_status objective_terms(appga_matrix* M, int K, const float* f, const float* g,
+                             const float* gamma, const appga_params* p, bool with_reg,
+                             double* dev_out, cudaStream_t s);
 
 // Orders ctx->stream after the caller's stream / the caller's after ctx->stream.
 appga_status enter_stream(appga_ctx* ctx, void* stream);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <limits>
 #include <string>
+#include <vector>
 
 #include "appga.h"
 #include "appga_internal.h"
@@ -18,20 +19,16 @@ namespace {
 
 #define CK(call) APPGA_CK(call)
 
-// Phi of a slice-major volume: the slices' data terms (double-float) plus the
-// 3-D regulariser, summed in FP64 on the host in slice order.
+// Phi of the result volume f (slice-major): the slices' data terms, which the
+// solve left in the workspace's host mirror (entries 2z, double-float
+// projections), plus the 3-D regulariser of f, summed in FP64 on the host in
+// slice order.
 appga_status volume_objective(appga_ctx* ctx, appga_matrix* M, int nz, const float* f,
-                              const float* g, const float* gamma, const appga_params* p,
-                              double* phi) {
+                              const appga_params* p, double* phi) {
   BatchWorkspace& b = *M->bw;
   cudaStream_t s = ctx->stream;
-  const bool bf16 = p->a_precision == APPGA_PREC_BF16 && M->has_bf16;
-  const int d = M->d, m = M->m;
-  for (int z = 0; z < nz; ++z) {
-    appga_status rc = data_term_on(M, f + (size_t)z * d, g + (size_t)z * m,
-                                   gamma + (size_t)z * m, bf16, b.vscal + z, s);
-    if (rc != APPGA_OK) return rc;
-  }
+  std::vector<double> data((size_t)nz);
+  for (int z = 0; z < nz; ++z) data[(size_t)z] = b.vscal_host[2 * z];
   Vol3Args va{};
   va.n = M->n;
   va.nz = nz;
@@ -44,12 +41,13 @@ appga_status volume_objective(appga_ctx* ctx, appga_matrix* M, int nz, const flo
   va.gR = b.gR;           // scratch: the batched workspace holds d * Kp >= d * nz floats
   va.partial = b.fpartial;
   CK(launch_stencil3d(va, s));
-  CK(launch_sum_pairs(b.fpartial, stencil3d_grid(M->n, nz), nz, nz, b.vscal + nz, s));
-  CK(cudaMemcpyAsync(b.vscal_host, b.vscal, (nz + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double* reg = b.vscal + 2 * nz;
+  CK(launch_sum_pairs(b.fpartial, stencil3d_grid(M->n, nz), nz, nz, reg, s));
+  CK(cudaMemcpyAsync(b.vscal_host + 2 * nz, reg, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   double tot = 0.0;
-  for (int z = 0; z < nz; ++z) tot += b.vscal_host[z];
-  *phi = tot + b.vscal_host[nz];
+  for (int z = 0; z < nz; ++z) tot += data[(size_t)z];
+  *phi = tot + b.vscal_host[2 * nz];
   return APPGA_OK;
 }
 
@@ -124,7 +122,7 @@ extern "C" appga_status appga_reconstruct_volume(appga_ctx* ctx, const appga_mat
     st.phi_prev = s0.stopped_early ? b.bst_host->phi_tot_prev : b.bst_host->phi_tot_cur;
     if ((rc = enter_stream(ctx, stream)) != APPGA_OK) return rc;
     double phi = 0.0;
-    rc = volume_objective(ctx, M, nz, f_out, g, gamma, params, &phi);
+    rc = volume_objective(ctx, M, nz, f_out, params, &phi);
     if (rc != APPGA_OK) return rc;
     st.phi = phi;
     if ((rc = leave_stream(ctx, stream)) != APPGA_OK) return rc;
