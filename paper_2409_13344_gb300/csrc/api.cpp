@@ -271,12 +271,23 @@ appga::FwdArgs fwd_args(appga_matrix* M, bool bf16) {
   return a;
 }
 
+// A cache key as the raw bytes of the values it depends on (exact, and no
+// text formatting on the per-call path).
+struct KeyBytes {
+  std::string s;
+  template <class T>
+  KeyBytes& add(const T& v) {
+    s.append(reinterpret_cast<const char*>(&v), sizeof v);
+    return *this;
+  }
+};
+
 std::string graph_key(const appga_params* p, bool track, bool bf16, int S) {
-  char buf[512];
-  std::snprintf(buf, sizeof buf, "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%.17g|%d|%d",
-                (int)track, (int)bf16, S, p->lambda1, p->lambda2, p->eps, p->beta, p->omega, p->a,
-                p->b, p->rel_obj_tol, p->momentum, p->precond_freeze_iter);
-  return buf;
+  KeyBytes k;
+  k.add((int)track).add((int)bf16).add(S).add(p->lambda1).add(p->lambda2).add(p->eps);
+  k.add(p->beta).add(p->omega).add(p->a).add(p->b).add(p->rel_obj_tol).add(p->momentum);
+  k.add(p->precond_freeze_iter);
+  return k.s;
 }
 
 // Device state of a run at its start (iteration index k0).  A run of zero
@@ -445,9 +456,10 @@ appga_status run_maps(appga_matrix* M, const float* g, const float* gamma,
   const int S = p->graph_iters > 0 ? p->graph_iters : kDefaultGraphIters;
   if (p->max_iters > 0) {
     // the captured kernel arguments hold the g / gamma addresses
-    const std::string key = graph_key(p, track, bf16, S) + "|" +
-                            std::to_string((uintptr_t)g) + "|" + std::to_string((uintptr_t)gamma) +
-                            "|" + std::to_string((uintptr_t)ws.theta_tab);
+    KeyBytes kb;
+    kb.s = graph_key(p, track, bf16, S);
+    kb.add(g).add(gamma).add(ws.theta_tab);
+    const std::string& key = kb.s;
     // the whole ladder (S and every power of two below it) is captured on
     // first use of these arguments, so later calls of any length find their
     // graphs cached
@@ -727,12 +739,11 @@ appga_status solve_common(appga_ctx* ctx, appga_matrix* M, const float* g, const
   std::string ckey;
   if (whole) {
     const bool track = p->track_objective != 0;
-    char buf[256];
-    std::snprintf(buf, sizeof buf, "|%d|%d|%d|%p|%p|%p|%p|%p|%p|%p", k0, (int)fresh,
-                  p->max_iters, (const void*)g, (const void*)gamma, (const void*)f_prev,
-                  (const void*)f_cur, (const void*)f_out_prev, (const void*)f_out,
-                  (const void*)f_out_host);
-    ckey = graph_key(p, track, bf16_requested(M, p), 0) + buf;
+    KeyBytes kb;
+    kb.s = graph_key(p, track, bf16_requested(M, p), 0);
+    kb.add(k0).add((int)fresh).add(p->max_iters).add(g).add(gamma).add(f_prev).add(f_cur);
+    kb.add(f_out_prev).add(f_out).add(f_out_host);
+    ckey = std::move(kb.s);
   }
   auto it = whole ? ws.call_graphs.find(ckey) : ws.call_graphs.end();
   const auto seen = whole ? ws.call_seen.find(ckey) : ws.call_seen.end();
