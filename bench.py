@@ -748,9 +748,15 @@ def run_ours(args):
     gamma = torch.from_numpy(sl.gamma).to(dev)
     f_out = torch.empty(geom.d, dtype=torch.float32, device=dev)
 
+    param_cache = {}
+
     def params(iters):
-        return AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS, omega=OMEGA,
-                                 max_iters=iters, track_objective=1)
+        # one parameter block per length, built once (as a caller would)
+        if iters not in param_cache:
+            param_cache[iters] = AP.default_params(lambda1=LAM1, lambda2=LAM2, eps=EPS,
+                                                   omega=OMEGA, max_iters=iters,
+                                                   track_objective=1)
+        return param_cache[iters]
 
     def chunks(total):
         out = []
