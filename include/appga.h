@@ -66,7 +66,8 @@ typedef struct appga_matrix appga_matrix;
 
 /* Device sticky flags reported in appga_stats.flags. */
 #define APPGA_FLAG_NONFINITE 1 /* a non-finite value met in a projector */
-#define APPGA_FLAG_TIMEOUT 2   /* a bounded device wait ran out; the run stopped */
+#define APPGA_FLAG_TIMEOUT 2   /* reserved: a bounded device wait ran out (no kernel of this
+                                  version waits on another block, so it is not raised) */
 #define APPGA_FLAG_DOMAIN 4    /* an input failed the device-side check; no map ran */
 
 const char* appga_status_string(appga_status s);
@@ -237,8 +238,8 @@ appga_status appga_initial_image(appga_ctx* ctx, const appga_matrix* mat, const 
  * (EDOMAIN for negative or non-finite g, non-positive or non-finite gamma).
  * Arithmetic: FP32 projections and updates, y = A f accumulated in FP32,
  * the objective's logarithm and sums in double-float, the momentum scalars,
- * Phi and the stopping test in FP64.  ETIMEOUT if a bounded device wait ran
- * out; ENUMERIC if a non-finite value appeared. */
+ * Phi and the stopping test in FP64.  ENUMERIC if a non-finite value
+ * appeared. */
 appga_status appga_reconstruct(appga_ctx* ctx, const appga_matrix* mat, const float* g,
                                const float* gamma, const float* f_init,
                                const appga_params* params, float* f_out,
