@@ -19,14 +19,19 @@
 //                the FP64 table k_theta_table fills once per run (step a6;
 //                Eq. GNtheta)
 //
-// Projector layout: a warp owns R consecutive CSR rows, whose row-padded
-// entries form one contiguous range, and streams it linearly in 128-entry
-// chunks (a 16-byte pack of columns and one of values per lane), keeping PF
-// chunks in flight in registers and gathering the x values of the next chunk
-// while it accumulates the current one.  Lanes accumulate into their current
-// row and park partials in per-warp shared-memory slots; lane q sums row q.
-// No block-wide barrier sits on the streaming path.  The block shapes (warps
-// per block, R, PF) differ for the two projections (Shape below).
+// Projector layouts.  The solver loop streams its matrices in the sliced
+// layout (SellGroup): a warp owns a slice of SELL_ROWS rows, SELL_LANES lanes
+// per row take the row's 4-entry packs in turn (packed 2-byte columns and
+// value quads, PF steps in flight in registers, the next step's gathers
+// issued while the current one accumulates), and a butterfly leaves each
+// row's sum in all of its lanes.  When A has the quarter-turn symmetry the
+// loop streams only its folded halves (FOLD): each stored entry serves two
+// products, gathered as pairs (see fold_partner in appga_internal.h).  The
+// stand-alone projections and objective stream the row-padded CSR
+// (RowGroup): a warp owns R consecutive rows, whose entries form one
+// contiguous range streamed in 128-entry chunks; lanes park per-row partials
+// in shared-memory slots and lane q sums row q.  No block-wide barrier sits
+// on either streaming path.
 //
 // The per-row epilogue runs on the FP32 pipe only: double-float (FP32 pair)
 // arithmetic for y, y~, the guarded denominator, and a double-float natural
@@ -34,8 +39,9 @@
 // its FP32 rate, so FP64 is used only for a handful of scalars per launch.
 //
 // Kernels read the iteration index and theta from a device-resident
-// SolverState, so a captured graph of (k_pixel, k_finalize, k_forward)
-// triples replays without host involvement.  Block partials (double-float
+// SolverState, so a captured graph of (k_pixel, k_forward) pairs (the step
+// finalisation runs in k_pixel's first blocks) replays without host
+// involvement.  Block partials (double-float
 // pairs) are combined in a fixed order (k_finalize, or a two-level ticketed
 // reduction in the stand-alone calls), so every reduction is deterministic.
 #include <cuda_runtime.h>
